@@ -1,0 +1,424 @@
+"""Plain FP64 CPU oracle of restarted PDHCG (Huang et al., arXiv 2405.16160).
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, obviously-correct
+statement of what the CUDA solver computes.  Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of
+``bench.py`` may import it; the product path never does.  It shares no code
+with the CUDA library: it receives plain numpy arrays and follows the paper's
+steps in the paper's order, using numpy / scipy.sparse primitives
+(CSR mat-vec, dot, norms) as the only building blocks.
+
+Problem (paper Eq. (1)):   min 1/2 x'Qx + c'x   s.t.  Ax <= b,  Q PSD.
+Saddle form (paper Eq. (2)): L(x, y) = 1/2 x'Qx + c'x + y'Ax - b'y, y >= 0.
+The first ``m_eq`` rows are equalities G x = q (Section 4, augmented-penalty
+paragraph) whose multipliers are free.
+
+Readings of the paper taken here (each is a documented choice; the CUDA
+path implements the same one):
+
+* Dual step sign (Algorithm 1, y-update).  Eq. (2) and the KKT measure of
+  Section 4 fix the convention Ax <= b, y >= 0, so the projected ascent step
+  is y+ = proj(y + sigma (A(2x+ - x) - b)); the primal subproblem of
+  Algorithm 1 is (Q + I/tau) x = x^k/tau - c - A'y^k.
+* Averages (Algorithm 1 with beta_k = k, Lemma A.1(2)): uniform mean of the
+  iterates x^{n,1..k}, y^{n,1..k} of the current epoch.
+* Adaptive CG stop (Section 4, BB/CG paragraph): epsilon_0 = 0 and
+  epsilon_{k+1} = epsilon_k + 0.05 relKKT(z^{n,k}), with relKKT(z^{n,k}) the
+  most recent evaluated relKKT of the current iterate; CG (at least one step)
+  stops when tau ||r_l||_2 <= epsilon, which implies the Section 2 criterion
+  ||x_l - x_*|| <= epsilon because lambda_min(Q + I/tau) >= 1/tau; or at
+  ``cg_max`` steps.  Fixed-N mode (PDHCG-fixed, Section 2) runs exactly N.
+* Restart (Section 4 "Adaptive restart", the three tests of the cited
+  rAPDHG Section 6 with beta_suff=0.2, beta_nec=0.8, beta_art=0.2): every
+  ``eval_freq`` iterations the candidate is whichever of the current iterate
+  and the average has the lower relKKT; restart to it if
+  (i) relKKT(cand) <= beta_suff relKKT(z^{n,0}), or
+  (ii) relKKT(cand) <= beta_nec relKKT(z^{n,0}) and relKKT(cand) exceeds the
+       candidate's relKKT at the previous evaluation of the epoch, or
+  (iii) the epoch length is >= beta_art times the total iteration count.
+* Primal weight (Section 4): omega <- exp(theta log(dy/dx) + (1-theta) log
+  omega) when both distances exceed eps_zero (the printed formula lacks the
+  log on omega); tau = eta/omega, sigma = eta*omega.
+* Step size (Section 3.2): eta = 1/(2 ||A||_2), ||A||_2 from 30 power
+  iterations on A'A from the normalised all-ones vector.  If ||A||_2 is not
+  above eps_zero (no coupling), ||A||_2 is replaced by eps_zero.
+* omega_0 = ||c||_2 / ||b||_2 when both exceed eps_zero, else 1; x0 = y0 = 0.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+CG_ADAPTIVE = 0
+CG_FIXED = 1
+
+RESTART_ADAPTIVE = 0
+RESTART_FIXED = 1  # restart to the average every K iterations (Algorithm 1)
+RESTART_NONE = 2
+
+SOLVED = 0
+ITER_LIMIT = 1
+TIME_LIMIT = 2
+NUMERICAL_ERROR = 3
+
+
+class NumericalError(RuntimeError):
+    pass
+
+
+@dataclass
+class OracleProblem:
+    Q: sp.csr_matrix
+    A: sp.csr_matrix
+    c: np.ndarray
+    b: np.ndarray
+    m_eq: int = 0
+
+    @property
+    def n(self) -> int:
+        return self.Q.shape[0]
+
+    @property
+    def m(self) -> int:
+        return self.A.shape[0]
+
+
+def problem_from_csr(n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b):
+    """Build the oracle's problem from raw CSR arrays (duplicates are summed)."""
+    Q = sp.csr_matrix((np.asarray(Q_val, np.float64), np.asarray(Q_col), np.asarray(Q_rowptr)),
+                      shape=(n, n))
+    A = sp.csr_matrix((np.asarray(A_val, np.float64), np.asarray(A_col), np.asarray(A_rowptr)),
+                      shape=(m, n))
+    Q.sum_duplicates()
+    A.sum_duplicates()
+    return OracleProblem(Q, A, np.asarray(c, np.float64).copy(),
+                         np.asarray(b, np.float64).copy(), int(m_eq))
+
+
+def problem_from_instance(inst) -> OracleProblem:
+    return problem_from_csr(inst.n, inst.m, inst.m_eq, inst.Q_rowptr, inst.Q_col, inst.Q_val,
+                            inst.A_rowptr, inst.A_col, inst.A_val, inst.c, inst.b)
+
+
+# --------------------------------------------------------------------------
+# Progress metric: relative KKT error (Section 4, "Progress metric").
+# --------------------------------------------------------------------------
+@dataclass
+class KKT:
+    r_primal: float
+    r_dual: float
+    r_gap: float
+    relkkt: float
+    primal_obj: float
+    dual_obj: float
+
+
+def _inf_norm(v: np.ndarray) -> float:
+    return float(np.max(np.abs(v))) if v.size else 0.0
+
+
+def relkkt(P: OracleProblem, x: np.ndarray, y: np.ndarray) -> KKT:
+    """r_primal, r_dual, r_gap and their maximum as defined in Section 4.
+
+    r_primal = ||[Ax - b]^+||_inf / (1 + max(||Ax||_inf, ||b||_inf))
+               (|Ax - b| on the equality rows)
+    r_dual   = ||Qx + A'y + c||_inf / (1 + max(||Qx||_inf, ||A'y||_inf, ||c||_inf))
+    r_gap    = |x'Qx + c'x + b'y| / (1 + max(|1/2 x'Qx + c'x|, |1/2 x'Qx + b'y|))
+    """
+    Qx = P.Q @ x
+    Ax = P.A @ x
+    Aty = P.A.T @ y
+    viol = Ax - P.b
+    viol[P.m_eq:] = np.maximum(viol[P.m_eq:], 0.0)
+    viol[:P.m_eq] = np.abs(viol[:P.m_eq])
+    r_primal = _inf_norm(viol) / (1.0 + max(_inf_norm(Ax), _inf_norm(P.b)))
+    r_dual = _inf_norm(Qx + Aty + P.c) / (
+        1.0 + max(_inf_norm(Qx), _inf_norm(Aty), _inf_norm(P.c)))
+    xQx = float(x @ Qx)
+    cx = float(P.c @ x)
+    by = float(P.b @ y)
+    pobj = 0.5 * xQx + cx
+    dobj = -0.5 * xQx - by
+    r_gap = abs(xQx + cx + by) / (1.0 + max(abs(0.5 * xQx + cx), abs(0.5 * xQx + by)))
+    return KKT(r_primal, r_dual, r_gap, max(r_primal, r_dual, r_gap), pobj, dobj)
+
+
+# --------------------------------------------------------------------------
+# Setup: spectral norm and step size (Section 3.2: sigma = tau = 1/(2||A||)).
+# --------------------------------------------------------------------------
+def spectral_norm(A: sp.csr_matrix, iters: int = 30) -> float:
+    """||A||_2 by power iteration on A'A, started at ones/sqrt(n).
+
+    lambda_t = ||A'A v_{t-1}||_2, v_t = A'A v_{t-1} / lambda_t; returns sqrt(lambda_iters).
+    """
+    n = A.shape[1]
+    if n == 0 or A.shape[0] == 0:
+        return 0.0
+    v = np.ones(n) / math.sqrt(n)
+    lam = 0.0
+    for _ in range(iters):
+        w = A.T @ (A @ v)
+        lam = float(np.linalg.norm(w))
+        if lam == 0.0:
+            return 0.0
+        v = w / lam
+    return math.sqrt(lam)
+
+
+# --------------------------------------------------------------------------
+# Inexact primal solve: CG on (Q + I/tau) x = rhs (Section 2).
+# --------------------------------------------------------------------------
+def cg(Q: sp.csr_matrix, tau: float, rhs: np.ndarray, x0: np.ndarray, mode: int,
+       n_fixed: int = 0, eps: float = 0.0, cg_max: int = 100, history: list | None = None):
+    """Textbook conjugate gradients on the SPD system (Q + I/tau) x = rhs, from x0.
+
+    FIXED: exactly ``n_fixed`` steps.  ADAPTIVE: at least one step, stop when
+    tau*||r||_2 <= eps or after cg_max steps.  Either mode stops early when the
+    residual is exactly zero.  Returns (x, steps).
+    """
+    x = x0.copy()
+    if mode == CG_FIXED and n_fixed <= 0:
+        return x, 0
+    r = rhs - (Q @ x + x / tau)
+    rr = float(r @ r)
+    if history is not None:
+        history.append(x.copy())
+    if rr == 0.0:
+        return x, 0
+    p = r.copy()
+    steps = 0
+    while True:
+        q = Q @ p + p / tau
+        pq = float(p @ q)
+        if not pq > 0.0:
+            raise NumericalError("p'(Q + I/tau)p <= 0: Q is not PSD or the data is not finite")
+        alpha = rr / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        rr_new = float(r @ r)
+        steps += 1
+        if history is not None:
+            history.append(x.copy())
+        if mode == CG_FIXED:
+            stop = steps >= n_fixed
+        else:
+            stop = tau * math.sqrt(rr_new) <= eps or steps >= cg_max
+        if stop or rr_new == 0.0:
+            return x, steps
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+
+
+# --------------------------------------------------------------------------
+# Solver state and one inner iteration (Algorithm 1 loop body).
+# --------------------------------------------------------------------------
+@dataclass
+class OracleOptions:
+    tol: float = 1e-4
+    max_iter: int = 100_000
+    time_limit: float = math.inf
+    eval_freq: int = 64
+    cg_mode: int = CG_ADAPTIVE
+    cg_fixed_n: int = 5
+    cg_max: int = 100
+    cg_eps_factor: float = 0.05
+    restart_mode: int = RESTART_ADAPTIVE
+    restart_k: int = 64  # restart frequency K for RESTART_FIXED
+    beta_suff: float = 0.2
+    beta_nec: float = 0.8
+    beta_art: float = 0.2
+    theta_pw: float = 0.2
+    eps_zero: float = 1e-10
+    primal_weight_update: bool = True
+    power_iters: int = 30
+    omega0: float = 0.0  # <= 0: ||c||/||b|| rule
+    eta: float = 0.0  # <= 0: 1/(2||A||)
+
+
+@dataclass
+class OracleState:
+    x: np.ndarray
+    y: np.ndarray
+    x_avg: np.ndarray
+    y_avg: np.ndarray
+    x_anchor: np.ndarray
+    y_anchor: np.ndarray
+    eta: float
+    omega: float
+    eps: float = 0.0  # adaptive CG precision epsilon_k
+    j: int = 0  # iterates averaged in this epoch
+    k_total: int = 0
+    relkkt_last: float = math.inf  # latest evaluated relKKT of the current iterate
+    kkt_anchor: float = math.inf  # relKKT of the epoch's restart point
+    kkt_prev_cand: float = math.inf  # candidate relKKT at the previous evaluation
+    n_restarts: int = 0
+    cg_total: int = 0
+    last_cg_steps: int = 0
+
+    @property
+    def tau(self) -> float:
+        return self.eta / self.omega
+
+    @property
+    def sigma(self) -> float:
+        return self.eta * self.omega
+
+    def copy(self) -> "OracleState":
+        return OracleState(**{k: (v.copy() if isinstance(v, np.ndarray) else v)
+                              for k, v in self.__dict__.items()})
+
+
+def initial_state(P: OracleProblem, o: OracleOptions) -> OracleState:
+    """x0 = y0 = 0, eta = 1/(2||A||_2), omega0 = ||c||/||b||."""
+    normA = spectral_norm(P.A, o.power_iters)
+    eta = o.eta if o.eta > 0 else 1.0 / (2.0 * max(normA, o.eps_zero))
+    if o.omega0 > 0:
+        omega = o.omega0
+    else:
+        nc, nb = float(np.linalg.norm(P.c)), float(np.linalg.norm(P.b))
+        omega = nc / nb if (nc > o.eps_zero and nb > o.eps_zero) else 1.0
+    z = lambda k: np.zeros(k)
+    return OracleState(z(P.n), z(P.m), z(P.n), z(P.m), z(P.n), z(P.m), eta, omega)
+
+
+def inner_step(P: OracleProblem, st: OracleState, o: OracleOptions) -> None:
+    """One PDHCG iteration z^{n,k} -> z^{n,k+1} (Algorithm 1 loop body), in place."""
+    tau, sigma = st.tau, st.sigma
+    # epsilon_{k+1} = epsilon_k + 0.05 relKKT(z^{n,k})   (Section 4)
+    if o.cg_mode == CG_ADAPTIVE:
+        st.eps = st.eps + o.cg_eps_factor * st.relkkt_last
+    # x^{k+1} ~ argmin_x L(x, y^k) + ||x - x^k||^2/(2 tau):  (Q + I/tau) x = x^k/tau - c - A'y^k
+    rhs = st.x / tau - P.c - P.A.T @ st.y
+    x_new, steps = cg(P.Q, tau, rhs, st.x, o.cg_mode, o.cg_fixed_n, st.eps, o.cg_max)
+    # y^{k+1} = proj(y^k + sigma (A(2x^{k+1} - x^k) - b)); equality rows unprojected
+    y_new = st.y + sigma * (P.A @ (2.0 * x_new - st.x) - P.b)
+    y_new[P.m_eq:] = np.maximum(y_new[P.m_eq:], 0.0)
+    # running averages with beta = j (uniform mean of the epoch's iterates)
+    st.j += 1
+    st.x_avg = st.x_avg + (x_new - st.x_avg) / st.j
+    st.y_avg = st.y_avg + (y_new - st.y_avg) / st.j
+    st.x, st.y = x_new, y_new
+    st.k_total += 1
+    st.cg_total += steps
+    st.last_cg_steps = steps
+
+
+def restart_to(P: OracleProblem, st: OracleState, o: OracleOptions, use_avg: bool,
+               kkt_cand: float) -> None:
+    """Start a new epoch at the candidate; update the primal weight (Section 4)."""
+    xc = st.x_avg.copy() if use_avg else st.x.copy()
+    yc = st.y_avg.copy() if use_avg else st.y.copy()
+    if o.primal_weight_update:
+        dx = float(np.linalg.norm(xc - st.x_anchor))
+        dy = float(np.linalg.norm(yc - st.y_anchor))
+        if dx > o.eps_zero and dy > o.eps_zero:
+            st.omega = math.exp(o.theta_pw * math.log(dy / dx)
+                                + (1.0 - o.theta_pw) * math.log(st.omega))
+    st.x, st.y = xc, yc
+    st.x_anchor, st.y_anchor = xc.copy(), yc.copy()
+    st.j = 0
+    st.eps = 0.0
+    st.kkt_anchor = kkt_cand
+    st.kkt_prev_cand = math.inf
+    st.relkkt_last = kkt_cand
+    st.n_restarts += 1
+
+
+def restart_test(kkt_cand: float, st: OracleState, o: OracleOptions) -> bool:
+    """The three restart conditions (sufficient, necessary+stall, artificial)."""
+    if kkt_cand <= o.beta_suff * st.kkt_anchor:
+        return True
+    if kkt_cand <= o.beta_nec * st.kkt_anchor and kkt_cand > st.kkt_prev_cand:
+        return True
+    return st.j >= o.beta_art * st.k_total
+
+
+@dataclass
+class OracleResult:
+    x: np.ndarray
+    y: np.ndarray
+    termination: int
+    kkt: KKT
+    iterations: int
+    cg_steps: int
+    restarts: int
+    returned_avg: bool
+    state: OracleState
+    trace: list = field(default_factory=list)
+    seconds: float = 0.0
+
+
+def evaluate(P: OracleProblem, st: OracleState, o: OracleOptions, record: list) -> tuple:
+    """relKKT of the current iterate and of the average, then the restart logic.
+
+    Returns (done, kkt, use_avg) where done is True when relKKT <= tol.
+    """
+    kc = relkkt(P, st.x, st.y)
+    ka = relkkt(P, st.x_avg, st.y_avg) if st.j > 0 else None
+    rec = {"k": st.k_total, "kkt_cur": kc.relkkt, "kkt_avg": ka.relkkt if ka else None,
+           "restart": False, "cand_avg": False, "omega": st.omega}
+    record.append(rec)
+    best_avg = ka is not None and ka.relkkt <= kc.relkkt
+    best = ka if best_avg else kc
+    if best.relkkt <= o.tol:
+        return True, best, best_avg
+    st.relkkt_last = kc.relkkt
+    if o.restart_mode == RESTART_ADAPTIVE and ka is not None:
+        if restart_test(best.relkkt, st, o):
+            restart_to(P, st, o, best_avg, best.relkkt)
+            rec["restart"], rec["cand_avg"] = True, best_avg
+        else:
+            st.kkt_prev_cand = best.relkkt
+    return False, best, best_avg
+
+
+def solve(P: OracleProblem, o: OracleOptions | None = None,
+          state: OracleState | None = None, step_hook=None) -> OracleResult:
+    """Restarted PDHCG (Algorithm 1 with the Section 4 heuristics)."""
+    o = o or OracleOptions()
+    t0 = time.perf_counter()
+    st = state.copy() if state is not None else initial_state(P, o)
+    trace: list = []
+    if state is None:
+        k0 = relkkt(P, st.x, st.y)
+        trace.append({"k": 0, "kkt_cur": k0.relkkt, "kkt_avg": None, "restart": False,
+                      "cand_avg": False, "omega": st.omega})
+        st.relkkt_last = k0.relkkt
+        st.kkt_anchor = k0.relkkt
+        if k0.relkkt <= o.tol:
+            return OracleResult(st.x, st.y, SOLVED, k0, 0, 0, 0, False, st, trace,
+                                time.perf_counter() - t0)
+    term = ITER_LIMIT
+    kkt = None
+    use_avg = False
+    try:
+        while st.k_total < o.max_iter:
+            inner_step(P, st, o)
+            if step_hook is not None:
+                step_hook(st)
+            if o.restart_mode == RESTART_FIXED and st.j >= o.restart_k:
+                kc = relkkt(P, st.x_avg, st.y_avg)
+                restart_to(P, st, o, True, kc.relkkt)
+            if st.k_total % o.eval_freq == 0:
+                done, kkt, use_avg = evaluate(P, st, o, trace)
+                if done:
+                    term = SOLVED
+                    break
+            if time.perf_counter() - t0 > o.time_limit:
+                term = TIME_LIMIT
+                break
+    except NumericalError:
+        term = NUMERICAL_ERROR
+    if term != SOLVED:
+        kc = relkkt(P, st.x, st.y)
+        ka = relkkt(P, st.x_avg, st.y_avg) if st.j > 0 else None
+        use_avg = ka is not None and ka.relkkt <= kc.relkkt
+        kkt = ka if use_avg else kc
+    x = st.x_avg if use_avg else st.x
+    y = st.y_avg if use_avg else st.y
+    return OracleResult(x.copy(), y.copy(), term, kkt, st.k_total, st.cg_total, st.n_restarts,
+                        use_avg, st, trace, time.perf_counter() - t0)

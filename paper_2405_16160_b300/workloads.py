@@ -1,0 +1,234 @@
+"""Seeded synthetic QP instances shaped like the paper's workloads.
+
+This module only draws random numbers and assembles CSR arrays.  It holds
+none of the solver's arithmetic, so both the CUDA path and the CPU oracle can
+be fed from it without sharing any of the method.
+
+Problem form (paper Eq. (1)): min 1/2 x'Qx + c'x  s.t.  Ax <= b, Q PSD.
+The first ``m_eq`` rows of A are equalities (the "Gx = q inside Ax <= b"
+reading of the augmented-penalty paragraph of Section 4).
+
+Instances
+---------
+``dense_small``  n=200, m=100 (the small latency-bound case):
+    Q = D + M'M/50, D = diag U[0.1, 1], M 50x200 with Bernoulli(0.05) N(0,1)
+    entries; A 100x200 with Bernoulli(0.05) N(0,1) entries; c ~ N(0,1);
+    b = A x0 + s, x0 ~ N(0,1), s ~ U[0,1] (strictly feasible at x0).
+``sparse_dd``  n=1e6, m=5e5 by default (the large sparse case):
+    Q = diag(u) + S, u ~ U[0.5, 2]; S symmetric, every row draws 4 partners
+    j != i uniformly with N(0, 0.1) values (std 0.1) and the pattern is
+    mirrored (~8 off-diagonals per row); Q_ii = u_i + sum_j |S_ij| so Q is
+    strictly diagonally dominant, hence positive definite.  A has exactly
+    ``a_row_nnz`` (10) distinct uniform columns per row with N(0,1) values.
+    c, b as above.  The same recipe at smaller n gives the parity cases.
+``zipf_dd``  n=1e7, m=5e6 (the largest single QP):
+    as ``sparse_dd`` with 2-3 partners per row (~5 nnz/row of Q) and A with
+    8 distinct columns per row drawn from a Zipf(1.1) law over column ranks,
+    mapped to columns by a seeded permutation.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+
+@dataclass
+class QPInstance:
+    """A QP in CSR form: min 1/2 x'Qx + c'x s.t. A x <= b (first m_eq rows =)."""
+
+    n: int
+    m: int
+    m_eq: int
+    Q_rowptr: np.ndarray  # int32 [n+1]
+    Q_col: np.ndarray  # int32 [nnz_Q]
+    Q_val: np.ndarray  # float64 [nnz_Q]
+    A_rowptr: np.ndarray  # int32 [m+1]
+    A_col: np.ndarray  # int32 [nnz_A]
+    A_val: np.ndarray  # float64 [nnz_A]
+    c: np.ndarray  # float64 [n]
+    b: np.ndarray  # float64 [m]
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nnz_Q(self) -> int:
+        return int(self.Q_rowptr[-1])
+
+    @property
+    def nnz_A(self) -> int:
+        return int(self.A_rowptr[-1])
+
+    def scipy_Q(self) -> sp.csr_matrix:
+        return sp.csr_matrix((self.Q_val, self.Q_col, self.Q_rowptr), shape=(self.n, self.n))
+
+    def scipy_A(self) -> sp.csr_matrix:
+        return sp.csr_matrix((self.A_val, self.A_col, self.A_rowptr), shape=(self.m, self.n))
+
+
+def _csr_arrays(M: sp.spmatrix):
+    M = sp.csr_matrix(M)
+    M.sum_duplicates()
+    M.sort_indices()
+    return (M.indptr.astype(np.int32), M.indices.astype(np.int32),
+            M.data.astype(np.float64))
+
+
+def _bernoulli_normal(rng: np.random.Generator, rows: int, cols: int, density: float):
+    mask = rng.random((rows, cols)) < density
+    vals = rng.standard_normal((rows, cols))
+    return np.where(mask, vals, 0.0)
+
+
+def _feasible_rhs(rng, A: sp.csr_matrix, n: int, m_eq: int):
+    x0 = rng.standard_normal(n)
+    s = rng.random(A.shape[0])
+    s[:m_eq] = 0.0  # equality rows hold exactly at x0
+    return A @ x0 + s
+
+
+def dense_small(seed: int = 0, n: int = 200, m: int = 100, k: int = 50,
+                density: float = 0.05, m_eq: int = 0) -> QPInstance:
+    """The n=200, m=100 instance (Q = D + M'M/50; A Bernoulli(0.05) N(0,1))."""
+    rng = np.random.default_rng(seed)
+    D = rng.uniform(0.1, 1.0, n)
+    M = _bernoulli_normal(rng, k, n, density)
+    Qd = np.diag(D) + M.T @ M / 50.0
+    Ad = _bernoulli_normal(rng, m, n, density)
+    c = rng.standard_normal(n)
+    A = sp.csr_matrix(Ad)
+    b = _feasible_rhs(rng, A, n, m_eq)
+    Qr, Qc, Qv = _csr_arrays(sp.csr_matrix(Qd))
+    Ar, Ac, Av = _csr_arrays(A)
+    return QPInstance(n, m, m_eq, Qr, Qc, Qv, Ar, Ac, Av, c, b,
+                      name=f"dense_small(n={n},m={m},seed={seed})")
+
+
+def _sym_dd_Q(rng, n: int, partners: int, std: float = 0.1) -> sp.csr_matrix:
+    """diag(U[0.5,2]) + S, S mirrored random pattern, made diagonally dominant."""
+    rows = np.repeat(np.arange(n, dtype=np.int64), partners)
+    # j = i + U{1..n-1} mod n is uniform over j != i
+    cols = (rows + rng.integers(1, n, size=rows.size)) % n
+    vals = rng.normal(0.0, std, size=rows.size)
+    S = sp.coo_matrix((np.concatenate([vals, vals]),
+                       (np.concatenate([rows, cols]), np.concatenate([cols, rows]))),
+                      shape=(n, n)).tocsr()
+    S.sum_duplicates()
+    u = rng.uniform(0.5, 2.0, n)
+    absrow = np.asarray(abs(S).sum(axis=1)).ravel()
+    return (S + sp.diags(u + absrow)).tocsr()
+
+
+def _distinct_columns(rng, m: int, d: int, draw) -> np.ndarray:
+    """m x d column indices, distinct within each row; duplicates are redrawn."""
+    cols = draw(m * d).reshape(m, d)
+    while True:
+        cols.sort(axis=1)
+        dup = np.zeros((m, d), dtype=bool)
+        dup[:, 1:] = cols[:, 1:] == cols[:, :-1]
+        bad_rows = np.nonzero(dup.any(axis=1))[0]
+        if bad_rows.size == 0:
+            return cols
+        sub = cols[bad_rows]
+        subdup = dup[bad_rows]
+        sub[subdup] = draw(int(subdup.sum()))
+        cols[bad_rows] = sub
+
+
+def _row_csr(m: int, n: int, cols: np.ndarray, vals: np.ndarray) -> sp.csr_matrix:
+    d = cols.shape[1]
+    rowptr = np.arange(0, (m + 1) * d, d, dtype=np.int64)
+    return sp.csr_matrix((vals.ravel(), cols.ravel(), rowptr), shape=(m, n))
+
+
+def sparse_dd(seed: int = 0, n: int = 1_000_000, m: int = 500_000, q_partners: int = 4,
+              a_row_nnz: int = 10, m_eq: int = 0) -> QPInstance:
+    """The large sparse instance (Q diagonally dominant, A uniform columns)."""
+    rng = np.random.default_rng(seed)
+    Q = _sym_dd_Q(rng, n, q_partners)
+    d = min(a_row_nnz, n)
+    cols = _distinct_columns(rng, m, d, lambda k: rng.integers(0, n, size=k))
+    A = _row_csr(m, n, cols, rng.standard_normal((m, d)))
+    c = rng.standard_normal(n)
+    b = _feasible_rhs(rng, A, n, m_eq)
+    Qr, Qc, Qv = _csr_arrays(Q)
+    Ar, Ac, Av = _csr_arrays(A)
+    return QPInstance(n, m, m_eq, Qr, Qc, Qv, Ar, Ac, Av, c, b,
+                      name=f"sparse_dd(n={n},m={m},seed={seed})")
+
+
+def zipf_dd(seed: int = 0, n: int = 10_000_000, m: int = 5_000_000, s: float = 1.1,
+            a_row_nnz: int = 8, m_eq: int = 0) -> QPInstance:
+    """The largest instance: power-law (Zipf s) column popularity in A."""
+    rng = np.random.default_rng(seed)
+    Q = _sym_dd_Q(rng, n, 2) if n > 2 else sp.identity(n, format="csr")
+    # a third partner for half of the rows gives ~5 nnz/row on average
+    extra = rng.random(n) < 0.5
+    if n > 2 and extra.any():
+        rows = np.nonzero(extra)[0]
+        cols = (rows + rng.integers(1, n, size=rows.size)) % n
+        vals = rng.normal(0.0, 0.1, size=rows.size)
+        E = sp.coo_matrix((np.concatenate([vals, vals]),
+                           (np.concatenate([rows, cols]), np.concatenate([cols, rows]))),
+                          shape=(n, n)).tocsr()
+        E.sum_duplicates()
+        Q = (Q + E + sp.diags(np.asarray(abs(E).sum(axis=1)).ravel())).tocsr()
+    ranks = np.arange(1, n + 1, dtype=np.float64)
+    cdf = np.cumsum(ranks ** (-s))
+    cdf /= cdf[-1]
+    perm = rng.permutation(n)
+    d = min(a_row_nnz, n)
+
+    def draw(k):
+        r = np.searchsorted(cdf, rng.random(k), side="right")
+        return perm[np.minimum(r, n - 1)]
+
+    cols = _distinct_columns(rng, m, d, draw)
+    A = _row_csr(m, n, cols, rng.standard_normal((m, d)))
+    c = rng.standard_normal(n)
+    b = _feasible_rhs(rng, A, n, m_eq)
+    Qr, Qc, Qv = _csr_arrays(Q)
+    Ar, Ac, Av = _csr_arrays(A)
+    return QPInstance(n, m, m_eq, Qr, Qc, Qv, Ar, Ac, Av, c, b,
+                      name=f"zipf_dd(n={n},m={m},seed={seed})")
+
+
+def box_diag(seed: int = 0, n: int = 50) -> QPInstance:
+    """Diagonal Q with the box l <= x <= u written as rows [I; -I] (closed form)."""
+    rng = np.random.default_rng(seed)
+    q = rng.uniform(0.5, 2.0, n)
+    c = rng.standard_normal(n) * 2.0
+    lo = -rng.uniform(0.1, 1.0, n)
+    hi = rng.uniform(0.1, 1.0, n)
+    A = sp.vstack([sp.identity(n), -sp.identity(n)]).tocsr()
+    b = np.concatenate([hi, -lo])
+    Qr, Qc, Qv = _csr_arrays(sp.diags(q))
+    Ar, Ac, Av = _csr_arrays(A)
+    return QPInstance(n, 2 * n, 0, Qr, Qc, Qv, Ar, Ac, Av, c, b,
+                      name=f"box_diag(n={n},seed={seed})", meta={"q": q, "lo": lo, "hi": hi})
+
+
+def from_dense(Qd: np.ndarray, Ad: np.ndarray, c: np.ndarray, b: np.ndarray,
+               m_eq: int = 0, name: str = "dense") -> QPInstance:
+    """Wrap dense arrays as a CSR instance (explicit zeros dropped)."""
+    Qr, Qc, Qv = _csr_arrays(sp.csr_matrix(Qd))
+    A = sp.csr_matrix(Ad) if Ad.size else sp.csr_matrix((Ad.shape[0], Qd.shape[0]))
+    Ar, Ac, Av = _csr_arrays(A)
+    return QPInstance(Qd.shape[0], Ad.shape[0], m_eq, Qr, Qc, Qv, Ar, Ac, Av,
+                      np.asarray(c, np.float64), np.asarray(b, np.float64), name=name)
+
+
+# Named configurations used by the bench and the parity tests.
+def make(name: str, seed: int = 0) -> QPInstance:
+    if name == "dense_small":
+        return dense_small(seed)
+    if name == "sparse_dd":
+        return sparse_dd(seed)
+    if name == "sparse_dd_small":
+        return sparse_dd(seed, n=20_000, m=10_000)
+    if name == "zipf_dd":
+        return zipf_dd(seed)
+    if name == "zipf_dd_small":
+        return zipf_dd(seed, n=20_000, m=10_000)
+    raise KeyError(name)
