@@ -1,0 +1,319 @@
+"""Benchmark: time to relKKT <= 1e-4 of FP64 restarted PDHCG on the large sparse QP.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one complete qp_solve (set-up power iteration, every PDHCG
+iteration, relKKT evaluations, restarts) of the seeded n=1e6, m=5e5 sparse
+QP (Q diagonally dominant with ~9 nnz/row, A with 10 uniform nnz/row), with
+the problem already resident on the device.  The same solve measured end to
+end through the C ABI from host arrays (qp_create with the host-to-device
+copies, qp_solve, qp_get_solution, qp_destroy) is reported as ``e2e``.
+
+``--impl reference`` times the CPU FP64 oracle (the reference arm of this
+build) on a bounded sample of the same workload and scales it to the metric.
+Under torchrun (N > 1) every rank solves its own instance (replicas; the
+path has no cross-GPU exchange) and rank 0 prints the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "large sparse QP: n=1e6, m=5e5, Q = diag U[0.5,2] + mirrored N(0,0.1) "
+                        "(~9 nnz/row, diagonally dominant), A 10 uniform N(0,1) nnz/row, "
+                        "c ~ N(0,1), b = A x0 + U[0,1]",
+            "n": 1_000_000, "m": 500_000, "seed": 0, "tol": 1e-4, "precision": "fp64",
+            "l2": "inputs larger than L2 (~470 MB resident working set vs 126 MB L2)"}
+METRIC = "time to 1e-4 rel. KKT (restarted PDHCG, FP64)"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "sparse_dd_n1000000_m500000_seed0_trace.json")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _max_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def cg_kernel_bytes(nnz_q: int, n: int, launches: int, spmvs: int, cg_steps: int) -> float:
+    """Algorithmic DRAM bytes of the CG kernel (each array touched once per phase).
+
+    Q product (per SpMV): 12 B/nnz (FP64 value + int32 column) + 4 B/row
+    (row pointer) + 8 B/row gathered vector + 8 B/row written result.
+    Phase 0 adds reads of c, A'y (16 B/row) and the write of p (8 B/row).
+    Phase B (per step) reads x, p, q, r and writes x, r: 48 B/row.
+    Phase C (per continued step) reads r, p and writes p: 24 B/row.
+    """
+    spmv = 12.0 * nnz_q + 20.0 * n
+    phase0_extra = 24.0 * n
+    return (spmvs * spmv + launches * phase0_extra + cg_steps * 48.0 * n
+            + max(cg_steps - launches, 0) * 24.0 * n)
+
+
+def oracle_sample(inst, iters: int):
+    """The oracle as it stands: set-up plus `iters` PDHCG iterations (with the
+    relKKT evaluations they contain).  Returns (setup_s, per_iter_s)."""
+    from oracle import pdhcg_oracle as O
+    P = O.problem_from_instance(inst)
+    o = O.OracleOptions(tol=WORKLOAD["tol"], max_iter=iters, eval_freq=64)
+    t0 = time.perf_counter()
+    st = O.initial_state(P, o)
+    k0 = O.relkkt(P, st.x, st.y)
+    st.relkkt_last = st.kkt_anchor = k0.relkkt
+    t1 = time.perf_counter()
+    trace = []
+    for _ in range(iters):
+        O.inner_step(P, st, o)
+        if st.k_total % o.eval_freq == 0:
+            O.evaluate(P, st, o, trace)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / iters
+
+
+def _oracle_iterations():
+    with open(GOLDEN) as f:
+        return int(json.load(f)["iterations"])
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    from paper_2405_16160_b300 import workloads as W
+    inst = W.sparse_dd(WORKLOAD["seed"], n=WORKLOAD["n"], m=WORKLOAD["m"])
+    n_iter = _oracle_iterations()
+    sample_iters = 8
+    vals = []
+    for s in range(args.warmup + args.steps):
+        setup, per_it = oracle_sample(inst, sample_iters)
+        if s >= args.warmup:
+            vals.append(setup + per_it * n_iter)
+    v = statistics.mean(vals)
+    sample = (f"oracle set-up + {sample_iters} iterations per step on the full instance, "
+              f"scaled by the oracle's own iteration count to 1e-4 ({n_iter})")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": WORKLOAD,
+        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2405_16160_b300 import build as B
+    from paper_2405_16160_b300 import workloads as W
+    from paper_2405_16160_b300.solver import QPSolver
+
+    B.build()
+    inst = W.sparse_dd(WORKLOAD["seed"] + rank, n=WORKLOAD["n"], m=WORKLOAD["m"])
+    tol = WORKLOAD["tol"]
+    stream = torch.cuda.current_stream()
+
+    # ---- device-resident solves (value)
+    solver = QPSolver(inst)
+    for _ in range(args.warmup):
+        solver.solve(tol=tol, kernel_timing=1)
+    torch.cuda.synchronize()
+    infos, times = [], []
+    with ClockSampler(local) as clocks:
+        _barrier(ws)
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = solver.solve(tol=tol, kernel_timing=1)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            infos.append(info)
+        torch.cuda.synchronize()
+        _barrier(ws)
+    trace_len = len(solver.trace())
+    solver.close()
+    per_solve = _max_over_ranks(statistics.mean(times), ws)
+
+    # ---- end to end through the C ABI from host arrays
+    e2e_times = []
+    h2d = (inst.Q_rowptr.nbytes + inst.Q_col.nbytes + inst.Q_val.nbytes
+           + 2 * (inst.A_rowptr.nbytes + inst.A_col.nbytes + inst.A_val.nbytes)
+           + inst.c.nbytes + inst.b.nbytes + 4 * (inst.n - inst.m))
+    d2h = 8 * (inst.n + inst.m)
+    e2e_steps = max(1, min(args.steps, 3))
+    for s in range(1 + e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with QPSolver(inst) as s2:
+            s2.solve(tol=tol)
+            x, y = s2.solution()
+        torch.cuda.synchronize()
+        if s > 0:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e = _max_over_ranks(statistics.mean(e2e_times), ws)
+
+    if rank != 0:
+        return 0
+    info = infos[-1]
+    peak, peak_kind = _peaks()
+    bytes_total = sum(cg_kernel_bytes(inst.nnz_Q, inst.n, i["cg_kernel_launches"],
+                                      i["cg_kernel_spmvs"], i["cg_steps"]) for i in infos)
+    launches = sum(i["cg_kernel_launches"] for i in infos)
+    kernel_s = sum(i["cg_kernel_ms"] for i in infos) / 1e3
+    achieved = bytes_total / kernel_s / 1e9 if kernel_s > 0 else None
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "k_cg_traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            traffic = json.load(f).get("dram_bytes_per_launch_full_size")
+    setup_launches = 1 + 2 + 1 + 3 * 30 + 1 + 4
+    chunk_launches = 3 * 64 + 4 + 3
+    gpu_launches = args.steps * (setup_launches + trace_len * chunk_launches)
+
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        setup_s, per_it = oracle_sample(inst, 64)
+        n_iter = _oracle_iterations()
+        cpu = {"value": setup_s + per_it * n_iter, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle set-up + 64 PDHCG iterations of the same instance "
+                         f"({setup_s + 64 * per_it:.1f} s), scaled by the oracle's iteration "
+                         f"count to 1e-4 ({n_iter})"}
+    out = {
+        "metric": METRIC, "value": per_solve, "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, iterations=info["iterations"], cg_steps=info["cg_steps"],
+                       restarts=info["restarts"], relkkt=info["relkkt"],
+                       parallelism=f"replicas x{ws}"),
+        "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": {"kernel": "k_cg (persistent CG: Q SpMVs + vector phases)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": bytes_total / max(launches, 1),
+                     "avg_launch_us": kernel_s / max(launches, 1) * 1e6},
+        "cpu_baseline": cpu,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,262 @@
+/*
+ * pdhcg.h - C ABI of the B300 restarted PDHCG solver for convex QP.
+ *
+ * Method: Huang, Zhang, Li, Ge, Liu, Ye, "Restarted Primal-Dual Hybrid
+ * Conjugate Gradient Method for Large-Scale Quadratic Programming",
+ * arXiv 2405.16160.
+ *
+ *   minimize 1/2 x'Qx + c'x   subject to   A x <= b          (paper Eq. (1))
+ *
+ * with Q symmetric positive semidefinite.  The first m_eq rows of A are
+ * equalities (the "Gx = q inside Ax <= b" rows of Section 4); their
+ * multipliers are free, the others are >= 0.  Every entry point returns a
+ * qp_status; nothing aborts, exits or traps.  All floating point is IEEE
+ * binary64.  All index arrays are int32 CSR (row pointer of length rows+1
+ * starting at 0, then column indices and values in row order).
+ *
+ * Threading: calls on one handle must not overlap; separate handles are
+ * independent.  A handle is bound to the CUDA device that was current when
+ * it was created.
+ */
+#ifndef PDHCG_H
+#define PDHCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PDHCG_ABI_VERSION 1
+
+typedef struct qp_handle qp_handle;
+
+typedef enum {
+  QP_OK = 0,
+  QP_ERR_INVALID_ARG = 1,     /* a size, pointer, index or value is out of range */
+  QP_ERR_OOM = 2,             /* device allocation failed */
+  QP_ERR_CUDA = 3,            /* a CUDA runtime call failed (see qp_last_error) */
+  QP_ERR_NOT_SOLVED = 4,      /* a result was requested before any solve */
+  QP_ERR_DEVICE_TIMEOUT = 5,  /* a bounded device-side grid barrier gave up */
+  QP_ERR_NO_DEVICE = 6        /* no CUDA device is visible */
+} qp_status;
+
+typedef enum {
+  QP_TERM_NONE = -1,
+  QP_TERM_SOLVED = 0,         /* relKKT <= tol (Section 4, progress metric) */
+  QP_TERM_ITER_LIMIT = 1,
+  QP_TERM_TIME_LIMIT = 2,
+  QP_TERM_NUMERICAL_ERROR = 3 /* p'(Q + I/tau)p <= 0 or a non-finite value in CG */
+} qp_termination;
+
+enum { QP_CG_ADAPTIVE = 0, QP_CG_FIXED = 1 };
+enum { QP_RESTART_ADAPTIVE = 0, QP_RESTART_NONE = 2 };
+
+/* qp_create flags */
+#define QP_CREATE_CHECK_SYMMETRY 1u /* reject Q unless |Q - Q'| <= 1e-12 max|Q| entrywise */
+
+/* debug_flags (fault injection; never used by default) */
+#define QP_DEBUG_BARRIER_NEVER_RELEASES 1u /* the CG kernel's first grid barrier is never
+                                              released, so its bounded wait runs out */
+
+/*
+ * Device memory and stream supplied by the caller (e.g. PyTorch's caching
+ * allocator and current stream).  alloc must return 256-byte aligned device
+ * memory usable on `stream`, or NULL on failure; free releases it.  A NULL
+ * context, or NULL alloc/free, means cudaMalloc/cudaFree; a NULL stream
+ * means a non-blocking stream owned by the handle.
+ */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user, void* stream);
+  void (*free)(void* ptr, size_t bytes, void* user, void* stream);
+  void* user;
+  void* stream; /* cudaStream_t */
+} qp_device_ctx;
+
+/*
+ * Solver options.  Defaults (qp_options_default) follow the paper where it
+ * gives a value and the documented readings where it does not.
+ */
+typedef struct {
+  double tol;                 /* relKKT tolerance (Section 4); default 1e-4 */
+  int64_t max_iter;           /* limit on inner PDHCG iterations; default 100000 */
+  double time_limit_s;        /* wall-clock limit checked between chunks; default 3600 */
+  int32_t eval_freq;          /* iterations between relKKT evaluations; default 64 */
+  int32_t cg_mode;            /* QP_CG_ADAPTIVE (Section 4 rule) or QP_CG_FIXED (PDHCG-fixed) */
+  int32_t cg_fixed_n;         /* N for QP_CG_FIXED (Section 2); default 5 */
+  int32_t cg_max;             /* cap on CG steps in adaptive mode; default 100 */
+  double cg_eps_factor;       /* eps_k = eps_{k-1} + factor*relKKT (Section 4); default 0.05 */
+  int32_t restart_mode;       /* QP_RESTART_ADAPTIVE or QP_RESTART_NONE */
+  int32_t power_iters;        /* power iterations for ||A||_2 (Section 3.2 step); default 30 */
+  double beta_suff;           /* restart parameters of Section 4: 0.2 */
+  double beta_nec;            /* 0.8 */
+  double beta_art;            /* 0.2 */
+  double theta_pw;            /* primal weight smoothing of Section 4: 0.2 */
+  double eps_zero;            /* threshold of the primal weight update; default 1e-10 */
+  int32_t primal_weight_update; /* 1: update omega at restarts (Section 4); default 1 */
+  int32_t warm_start;         /* 1: start from qp_set_warm_start / qp_set_state data */
+  double omega0;              /* > 0 overrides omega_0 = ||c||_2/||b||_2 */
+  double eta;                 /* > 0 overrides eta = 1/(2||A||_2) */
+  int32_t kernel_timing;      /* 1: time every CG-kernel launch with CUDA events */
+  uint32_t debug_flags;       /* QP_DEBUG_* fault injection, 0 by default */
+  int64_t reserved[8];
+} qp_options;
+
+/* Result of a solve (also returned by qp_get_stats). */
+typedef struct {
+  int32_t termination;        /* qp_termination */
+  int32_t returned_avg;       /* 1: the solution is the epoch average (x~, y~) */
+  int64_t iterations;         /* inner PDHCG iterations */
+  int64_t cg_steps;           /* CG steps (matrix products with Q + I/tau) */
+  int64_t restarts;
+  int64_t evaluations;        /* relKKT evaluations (incl. the one at x0) */
+  double relkkt, r_primal, r_dual, r_gap; /* of the returned iterate (Section 4) */
+  double primal_obj, dual_obj;            /* 1/2x'Qx + c'x and -1/2x'Qx - b'y */
+  double norm_A, eta, omega, tau, sigma;  /* final step-size state */
+  double setup_ms;            /* power iteration + initial evaluation, device time */
+  double solve_ms;            /* whole qp_solve wall time */
+  double cg_kernel_ms;        /* kernel_timing: summed CUDA-event time of CG launches */
+  int64_t cg_kernel_launches; /* kernel_timing: CG launches that did work */
+  int64_t cg_kernel_spmvs;    /* kernel_timing: Q products inside those launches */
+  int32_t device_error;       /* nonzero: a bounded device wait gave up */
+  int32_t cooperative;        /* 1: the CG kernel ran as a cooperative launch */
+} qp_info;
+
+/* Scalar part of the iteration state (for checkpoint / resume and parity). */
+typedef struct {
+  double eta, omega;          /* tau = eta/omega, sigma = eta*omega */
+  double eps;                 /* adaptive CG precision eps_k */
+  double relkkt_last;         /* latest evaluated relKKT of the current iterate */
+  double kkt_anchor;          /* relKKT at the epoch's restart point */
+  double kkt_prev_cand;       /* candidate relKKT at the previous evaluation */
+  int64_t j;                  /* iterates in the running average */
+  int64_t k_total;            /* inner iterations so far */
+  int64_t restarts;
+  int64_t cg_total;
+} qp_state_scalars;
+
+/* Host vectors of the iteration state; NULL entries are skipped on get and
+ * read as zeros on set.  x, x_avg, x_anchor have n entries; the y's have m. */
+typedef struct {
+  double* x;
+  double* y;
+  double* x_avg;
+  double* y_avg;
+  double* x_anchor;
+  double* y_anchor;
+} qp_state_vectors;
+
+/* One relKKT evaluation record, produced every eval_freq iterations. */
+typedef struct {
+  int64_t k;                  /* iteration count at the evaluation */
+  double kkt_cur, kkt_avg;    /* relKKT of the current iterate and of the average */
+  double omega;               /* primal weight after this evaluation */
+  int32_t restart;            /* 0 none, 1 restart to current, 2 restart to average */
+  int32_t cg_last;            /* CG steps of the last iteration before it */
+} qp_trace_entry;
+
+/* ---------------------------------------------------------------- lifecycle */
+
+const char* qp_status_string(qp_status s);
+int qp_abi_version(void);
+/* Message of the last failed call on this thread (CUDA error text etc.). */
+const char* qp_last_error(void);
+
+void qp_options_default(qp_options* o);
+
+/*
+ * Copy a QP to the current CUDA device (paper Eq. (1)).
+ * Q_*: n x n CSR, both triangles stored; A_*: m x n CSR; c: n; b: m (host
+ * pointers, read only during the call; the caller keeps ownership).
+ * Validation: n > 0, m >= 0, 0 <= m_eq <= m, nnz < 2^31, rowptr[0] = 0 and
+ * monotone, columns in [0, cols), all values finite.  Duplicate (i, j)
+ * entries are summed; rows are sorted.  A' is built on the host (stable
+ * counting sort) and stored explicitly.  ctx may be NULL.
+ * Errors: QP_ERR_INVALID_ARG, QP_ERR_NO_DEVICE, QP_ERR_OOM, QP_ERR_CUDA;
+ * *out is NULL on failure.
+ */
+qp_status qp_create(qp_handle** out, int32_t n, int32_t m, int32_t m_eq,
+                    const int32_t* Q_rowptr, const int32_t* Q_col, const double* Q_val,
+                    const int32_t* A_rowptr, const int32_t* A_col, const double* A_val,
+                    const double* c, const double* b, const qp_device_ctx* ctx,
+                    uint32_t flags);
+
+/* Free the handle and its device memory (after synchronising its stream). */
+void qp_destroy(qp_handle* h);
+
+/* ---------------------------------------------------------------- solving */
+
+/*
+ * Restarted PDHCG (Algorithm 1 with the Section 4 heuristics).  Runs on the
+ * handle's stream; returns after the solve has finished.  Starts from x = y = 0
+ * unless o->warm_start.  info may be NULL.  QP_OK is returned also when the
+ * solve stops early: see info->termination.  QP_ERR_DEVICE_TIMEOUT when a
+ * bounded device barrier gave up (the handle stays usable).
+ */
+qp_status qp_solve(qp_handle* h, const qp_options* o, qp_info* info);
+
+/* Copy the returned iterate to host arrays x (n) and y (m); either may be NULL. */
+qp_status qp_get_solution(const qp_handle* h, double* x, double* y);
+
+/* Info of the last qp_solve (QP_ERR_NOT_SOLVED before the first). */
+qp_status qp_get_stats(const qp_handle* h, qp_info* info);
+
+/* Evaluation records of the last qp_solve.  Writes up to `cap` entries and
+ * stores the total count in *count. */
+qp_status qp_get_trace(const qp_handle* h, qp_trace_entry* out, int64_t cap, int64_t* count);
+
+/* ------------------------------------------------- state (checkpoint / parity) */
+
+/* Warm start (x0, y0); NULL means zeros.  Used when o->warm_start = 1:
+ * the anchors become (x0, y0), the averages are empty and the step sizes
+ * are recomputed by the solve's set-up. */
+qp_status qp_set_warm_start(qp_handle* h, const double* x0, const double* y0);
+
+/* Read / write the full iteration state.  qp_set_state recomputes A x and
+ * A' y on the device.  A solve with o->warm_start = 2 continues from a set
+ * state without recomputing the set-up. */
+qp_status qp_get_state(const qp_handle* h, const qp_state_vectors* v, qp_state_scalars* s);
+qp_status qp_set_state(qp_handle* h, const qp_state_vectors* v, const qp_state_scalars* s);
+
+/*
+ * Run exactly `iters` inner PDHCG iterations (Algorithm 1 loop body: CG
+ * primal step, projected dual step, averages) from the current state, with
+ * no relKKT evaluation, restart or termination test.  Only o's CG settings
+ * and its debug_flags are used.
+ */
+qp_status qp_iterate(qp_handle* h, const qp_options* o, int64_t iters);
+
+/*
+ * relKKT terms (Section 4) of the current iterate and of the running
+ * average.  Each output holds {r_primal, r_dual, r_gap, relKKT, primal_obj,
+ * dual_obj}; either may be NULL.  The state is not changed.
+ */
+qp_status qp_evaluate(qp_handle* h, double kkt_cur[6], double kkt_avg[6]);
+
+/* Estimate ||A||_2 by `iters` power iterations on A'A from ones/sqrt(n). */
+qp_status qp_norm_A(qp_handle* h, int32_t iters, double* out);
+
+/* ------------------------------------------------- host-only helpers (no GPU) */
+
+/*
+ * Validate a CSR matrix (rows x cols): rowptr[0] = 0, monotone, nnz =
+ * rowptr[rows] < 2^31, columns in range, values finite.  Host pointers.
+ */
+qp_status qp_csr_validate(int32_t rows, int32_t cols, const int32_t* rowptr,
+                          const int32_t* col, const double* val);
+
+/*
+ * Transpose a valid CSR matrix (rows x cols) into caller-allocated arrays
+ * t_rowptr[cols + 1], t_col[nnz], t_val[nnz] with a stable counting sort:
+ * within each output row the entries keep the input row order.
+ */
+qp_status qp_csr_transpose(int32_t rows, int32_t cols, const int32_t* rowptr,
+                           const int32_t* col, const double* val, int32_t* t_rowptr,
+                           int32_t* t_col, double* t_val);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDHCG_H */

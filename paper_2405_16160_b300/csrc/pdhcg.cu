@@ -1,0 +1,966 @@
+// Host side of the C ABI declared in include/pdhcg.h: handle lifecycle,
+// device memory, CUDA-graph capture of a chunk of PDHCG iterations and the
+// solve loop (Algorithm 1 with the Section 4 heuristics of arXiv 2405.16160).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pdhcg.h"
+#include "host_csr.h"
+#include "kernels.cuh"
+
+using namespace pdhcg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+#define CUDA_TRY(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return QP_ERR_CUDA;                                                               \
+    }                                                                                   \
+  } while (0)
+
+#define QP_TRY(call)                  \
+  do {                                \
+    qp_status s_ = (call);            \
+    if (s_ != QP_OK) return s_;       \
+  } while (0)
+
+int group_size_for(int64_t nnz, int64_t rows) {
+  const double avg = rows > 0 ? double(nnz) / double(rows) : 0.0;
+  if (avg <= 3.0) return 2;
+  if (avg <= 12.0) return 4;
+  if (avg <= 24.0) return 8;
+  if (avg <= 48.0) return 16;
+  return 32;
+}
+
+struct DevMat {
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  int32_t rows = 0;
+  int64_t nnz = 0;
+  int G = 4;
+  DevCsr view() const { return DevCsr{rowptr, col, val, rows}; }
+};
+
+}  // namespace
+
+struct qp_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;  // the handle's own stream (capturable)
+  cudaStream_t user_stream = nullptr;
+  qp_device_ctx ctx{};
+  bool has_alloc = false;
+  int32_t n = 0, m = 0, m_eq = 0;
+  DevMat Q, A, At;
+  double *c = nullptr, *b = nullptr;
+  double *x = nullptr, *y = nullptr, *ax = nullptr, *aty = nullptr;
+  double *x_avg = nullptr, *y_avg = nullptr, *x_anchor = nullptr, *y_anchor = nullptr;
+  double *ax_avg = nullptr, *aty_avg = nullptr;
+  double *r = nullptr, *p = nullptr, *q = nullptr;
+  double *x0 = nullptr, *y0 = nullptr;  // warm start
+  double *pw_v = nullptr, *pw_u = nullptr, *pw_w = nullptr;
+  double *part_cg = nullptr, *part_n = nullptr, *part_m = nullptr, *part_rn = nullptr,
+         *part_rm = nullptr, *part_pow = nullptr, *part2 = nullptr;
+  DevState* st = nullptr;
+  GridBarrier* bar = nullptr;
+  DevState* h_st = nullptr;  // pinned mirror
+  int num_sms = 0;
+  int grid_n = 1, grid_m = 1, grid_cg = 1, grid_vec = 1;
+  bool coop_ok = true;
+  bool warm_set = false;
+  // captured chunk graph
+  cudaGraphExec_t chunk_exec = nullptr;
+  int chunk_iters = 0;
+  bool chunk_timing = false;
+  std::vector<cudaEvent_t> ev;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  std::vector<qp_trace_entry> trace;
+  qp_info info{};
+  bool solved = false;
+  std::vector<std::pair<void*, size_t>> allocs;
+};
+
+namespace {
+
+qp_status dev_alloc(qp_handle* h, void** out, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 256);
+  bytes = (bytes + 255) & ~size_t(255);
+  void* ptr = nullptr;
+  if (h->has_alloc) {
+    ptr = h->ctx.alloc(bytes, h->ctx.user, h->ctx.stream);
+    if (!ptr) {
+      set_error("device allocator callback returned NULL for %zu bytes", bytes);
+      return QP_ERR_OOM;
+    }
+  } else {
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+      return QP_ERR_OOM;
+    }
+  }
+  h->allocs.emplace_back(ptr, bytes);
+  *out = ptr;
+  return QP_OK;
+}
+
+template <class T>
+qp_status dalloc(qp_handle* h, T** out, size_t count) {
+  return dev_alloc(h, reinterpret_cast<void**>(out), count * sizeof(T));
+}
+
+template <class F>
+qp_status dispatch_g(int G, F&& f) {
+  switch (G) {
+    case 2: f(std::integral_constant<int, 2>{}); return QP_OK;
+    case 4: f(std::integral_constant<int, 4>{}); return QP_OK;
+    case 8: f(std::integral_constant<int, 8>{}); return QP_OK;
+    case 16: f(std::integral_constant<int, 16>{}); return QP_OK;
+    case 32: f(std::integral_constant<int, 32>{}); return QP_OK;
+    default: set_error("unsupported group size %d", G); return QP_ERR_INVALID_ARG;
+  }
+}
+
+int blocks_for_rows(int64_t rows, int G, int cap) {
+  const int64_t rows_per_block = int64_t(kBlock / 32) * (32 / G);
+  int64_t g = (rows + rows_per_block - 1) / rows_per_block;
+  return int(std::max<int64_t>(1, std::min<int64_t>(g, cap)));
+}
+
+void fill_dev_options(qp_handle* h, const qp_options* o, DevOptions* d) {
+  d->tol = o->tol;
+  d->max_iter = o->max_iter;
+  d->cg_mode = o->cg_mode;
+  d->cg_fixed_n = o->cg_fixed_n;
+  d->cg_max = o->cg_max;
+  d->restart_mode = o->restart_mode;
+  d->cg_eps_factor = o->cg_eps_factor;
+  d->beta_suff = o->beta_suff;
+  d->beta_nec = o->beta_nec;
+  d->beta_art = o->beta_art;
+  d->theta_pw = o->theta_pw;
+  d->eps_zero = o->eps_zero;
+  d->omega0 = o->omega0;
+  d->eta_override = o->eta;
+  d->pw_update = o->primal_weight_update;
+  d->m_eq = h->m_eq;
+  d->debug_flags = o->debug_flags;
+  d->barrier_timeout_ms = (o->debug_flags & QP_DEBUG_BARRIER_NEVER_RELEASES) ? 200 : 2000;
+}
+
+qp_status validate_options(const qp_options* o) {
+  if (!o) {
+    set_error("options is NULL");
+    return QP_ERR_INVALID_ARG;
+  }
+  if (!(o->tol >= 0.0) || o->max_iter < 0 || o->eval_freq < 1 || o->eval_freq > 4096 ||
+      (o->cg_mode != QP_CG_ADAPTIVE && o->cg_mode != QP_CG_FIXED) || o->cg_fixed_n < 0 ||
+      o->cg_max < 1 ||
+      (o->restart_mode != QP_RESTART_ADAPTIVE && o->restart_mode != QP_RESTART_NONE) ||
+      o->power_iters < 1 || o->power_iters > 100000 || !(o->eps_zero >= 0.0) ||
+      !(o->theta_pw >= 0.0 && o->theta_pw <= 1.0) || !(o->time_limit_s > 0.0)) {
+    set_error("invalid option value");
+    return QP_ERR_INVALID_ARG;
+  }
+  return QP_OK;
+}
+
+// --------------------------------------------------------------- launches
+qp_status launch_cg(qp_handle* h, bool coop) {
+  return dispatch_g(h->Q.G, [&](auto g) {
+    constexpr int G = decltype(g)::value;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(h->grid_cg);
+    cfg.blockDim = dim3(kBlock);
+    cfg.stream = h->stream;
+    if (coop) {
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+    }
+    cudaLaunchKernelEx(&cfg, k_cg<G>, h->Q.view(), (const double*)h->c, (const double*)h->aty,
+                       h->x, h->r, h->p, h->q, h->part_cg, h->st, h->bar, (int)h->n);
+  });
+}
+
+qp_status launch_dual(qp_handle* h) {
+  return dispatch_g(h->A.G, [&](auto g) {
+    constexpr int G = decltype(g)::value;
+    k_dual<G><<<h->grid_m, kBlock, 0, h->stream>>>(h->A.view(), h->x, h->b, h->y, h->ax,
+                                                   h->y_avg, h->st);
+  });
+}
+
+qp_status launch_atv(qp_handle* h) {
+  return dispatch_g(h->At.G, [&](auto g) {
+    constexpr int G = decltype(g)::value;
+    k_atv<G><<<h->grid_n, kBlock, 0, h->stream>>>(h->At.view(), h->y, h->aty, h->x, h->x_avg,
+                                                  h->st);
+  });
+}
+
+qp_status launch_spmv(qp_handle* h, const DevMat& M, const double* v, double* out, double* part,
+                      int grid) {
+  return dispatch_g(M.G, [&](auto g) {
+    constexpr int G = decltype(g)::value;
+    k_spmv<G><<<grid, kBlock, 0, h->stream>>>(M.view(), v, out, part);
+  });
+}
+
+// relKKT of (x, y) and (x~, y~); mode as in k_control.
+qp_status launch_eval(qp_handle* h, int mode) {
+  QP_TRY(launch_spmv(h, h->At, h->y_avg, h->aty_avg, nullptr, h->grid_n));
+  QP_TRY(dispatch_g(h->Q.G, [&](auto g) {
+    constexpr int G = decltype(g)::value;
+    k_kkt_n<G><<<h->grid_n, kBlock, 0, h->stream>>>(h->Q.view(), h->x, h->x_avg, h->aty,
+                                                     h->aty_avg, h->c, h->part_n);
+  }));
+  QP_TRY(dispatch_g(h->A.G, [&](auto g) {
+    constexpr int G = decltype(g)::value;
+    k_kkt_m<G><<<h->grid_m, kBlock, 0, h->stream>>>(h->A.view(), h->x_avg, h->ax, h->ax_avg, h->b,
+                                                    h->y, h->y_avg, h->m_eq, h->part_m);
+  }));
+  k_control<<<1, 32, 0, h->stream>>>(h->part_n, h->grid_n, h->part_m, h->grid_m, h->st, mode);
+  return QP_OK;
+}
+
+qp_status launch_restart(qp_handle* h) {
+  k_restart_n<<<h->grid_vec, kBlock, 0, h->stream>>>(h->x, h->x_avg, h->x_anchor, h->aty,
+                                                     h->aty_avg, h->st, h->n, h->part_rn);
+  k_restart_m<<<h->grid_vec, kBlock, 0, h->stream>>>(h->y, h->y_avg, h->y_anchor, h->ax,
+                                                     h->ax_avg, h->st, h->m, h->part_rm);
+  k_restart_finish<<<1, 32, 0, h->stream>>>(h->part_rn, h->grid_vec, h->part_rm, h->grid_vec,
+                                            h->st);
+  return QP_OK;
+}
+
+qp_status launch_iteration(qp_handle* h, bool coop) {
+  QP_TRY(launch_cg(h, coop));
+  QP_TRY(launch_dual(h));
+  QP_TRY(launch_atv(h));
+  return QP_OK;
+}
+
+// Power iteration for ||A||_2 (30 steps by default) and the step sizes.
+qp_status launch_setup(qp_handle* h, int power_iters, int reset) {
+  k_pow_start<<<h->grid_vec, kBlock, 0, h->stream>>>(h->pw_v, h->n, h->c, h->b, h->m, h->part2);
+  for (int t = 0; t < power_iters; ++t) {
+    QP_TRY(launch_spmv(h, h->A, h->pw_v, h->pw_u, nullptr, h->grid_m));
+    QP_TRY(launch_spmv(h, h->At, h->pw_u, h->pw_w, h->part_pow, h->grid_n));
+    k_pow_scale<<<h->grid_vec, kBlock, 0, h->stream>>>(h->pw_w, h->pw_v, h->n, h->part_pow,
+                                                       h->grid_n, h->st);
+  }
+  k_setup_finish<<<1, 32, 0, h->stream>>>(h->part2, h->grid_vec, h->st, reset);
+  return QP_OK;
+}
+
+qp_status recompute_caches(qp_handle* h) {
+  QP_TRY(launch_spmv(h, h->A, h->x, h->ax, nullptr, h->grid_m));
+  QP_TRY(launch_spmv(h, h->At, h->y, h->aty, nullptr, h->grid_n));
+  return QP_OK;
+}
+
+qp_status check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("kernel launch failed: %s", cudaGetErrorString(e));
+    return QP_ERR_CUDA;
+  }
+  return QP_OK;
+}
+
+void destroy_chunk(qp_handle* h) {
+  if (h->chunk_exec) cudaGraphExecDestroy(h->chunk_exec);
+  h->chunk_exec = nullptr;
+  for (auto e : h->ev) cudaEventDestroy(e);
+  h->ev.clear();
+}
+
+// Capture eval_freq iterations + one evaluation + restart + status copy.
+qp_status capture_chunk(qp_handle* h, int iters, bool timing, bool coop) {
+  destroy_chunk(h);
+  if (timing) {
+    h->ev.resize(size_t(2) * iters);
+    for (auto& e : h->ev) CUDA_TRY(cudaEventCreate(&e));
+  }
+  cudaGraph_t graph = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  qp_status s = QP_OK;
+  for (int k = 0; k < iters && s == QP_OK; ++k) {
+    if (timing) cudaEventRecord(h->ev[2 * k], h->stream);
+    s = launch_cg(h, coop);
+    if (timing) cudaEventRecord(h->ev[2 * k + 1], h->stream);
+    if (s == QP_OK) s = launch_dual(h);
+    if (s == QP_OK) s = launch_atv(h);
+  }
+  if (s == QP_OK) s = launch_eval(h, 1);
+  if (s == QP_OK) s = launch_restart(h);
+  if (s == QP_OK)
+    cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t le = cudaGetLastError();
+  cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+  if (s != QP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (le != cudaSuccess || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    set_error("graph capture failed: %s / %s", cudaGetErrorString(le), cudaGetErrorString(ce));
+    return QP_ERR_CUDA;
+  }
+  cudaError_t ie = cudaGraphInstantiate(&h->chunk_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    h->chunk_exec = nullptr;
+    set_error("graph instantiate failed: %s", cudaGetErrorString(ie));
+    return QP_ERR_CUDA;
+  }
+  h->chunk_iters = iters;
+  h->chunk_timing = timing;
+  return QP_OK;
+}
+
+qp_status ensure_chunk(qp_handle* h, int iters, bool timing) {
+  if (h->chunk_exec && h->chunk_iters == iters && h->chunk_timing == timing) return QP_OK;
+  if (h->coop_ok) {
+    qp_status s = capture_chunk(h, iters, timing, true);
+    if (s == QP_OK) return QP_OK;
+    // The grid is sized to be co-resident, so an ordinary launch also
+    // satisfies the barrier; record that the cooperative form was refused.
+    h->coop_ok = false;
+  }
+  return capture_chunk(h, iters, timing, false);
+}
+
+qp_status begin_call(qp_handle* h) {
+  CUDA_TRY(cudaSetDevice(h->device));
+  if (h->user_stream) {
+    CUDA_TRY(cudaEventRecord(h->ev_a, h->user_stream));
+    CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_a, 0));
+  }
+  return QP_OK;
+}
+
+qp_status end_call(qp_handle* h) {
+  if (h->user_stream) {
+    CUDA_TRY(cudaEventRecord(h->ev_b, h->stream));
+    CUDA_TRY(cudaStreamWaitEvent(h->user_stream, h->ev_b, 0));
+  }
+  return QP_OK;
+}
+
+qp_status sync(qp_handle* h) {
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return QP_OK;
+}
+
+qp_status write_options(qp_handle* h, const qp_options* o) {
+  fill_dev_options(h, o, &h->h_st->opt);
+  CUDA_TRY(cudaMemcpyAsync(&h->st->opt, &h->h_st->opt, sizeof(DevOptions), cudaMemcpyHostToDevice,
+                           h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->stream));
+  return QP_OK;
+}
+
+qp_status read_state(qp_handle* h) {
+  CUDA_TRY(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  return sync(h);
+}
+
+qp_status write_state(qp_handle* h) {
+  CUDA_TRY(cudaMemcpyAsync(h->st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+  return sync(h);
+}
+
+qp_status upload(qp_handle* h, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return QP_OK;
+  CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream));
+  return QP_OK;
+}
+
+qp_status upload_matrix(qp_handle* h, DevMat* M, const HostCsr& H) {
+  M->rows = H.rows;
+  M->nnz = H.nnz();
+  M->G = group_size_for(M->nnz, H.rows);
+  QP_TRY(dalloc(h, &M->rowptr, size_t(H.rows) + 1));
+  QP_TRY(dalloc(h, &M->col, size_t(M->nnz)));
+  QP_TRY(dalloc(h, &M->val, size_t(M->nnz)));
+  QP_TRY(upload(h, M->rowptr, H.rowptr.data(), (size_t(H.rows) + 1) * sizeof(int32_t)));
+  QP_TRY(upload(h, M->col, H.col.data(), size_t(M->nnz) * sizeof(int32_t)));
+  QP_TRY(upload(h, M->val, H.val.data(), size_t(M->nnz) * sizeof(double)));
+  return QP_OK;
+}
+
+void fill_info_from_state(qp_handle* h, qp_info* info) {
+  const DevState& s = *h->h_st;
+  const double* k = s.kkt_ret;
+  info->returned_avg = s.returned_avg;
+  info->iterations = s.k_total;
+  info->cg_steps = s.cg_total;
+  info->restarts = s.n_restarts;
+  info->evaluations = s.n_evals;
+  info->r_primal = k[0];
+  info->r_dual = k[1];
+  info->r_gap = k[2];
+  info->relkkt = k[3];
+  info->primal_obj = k[4];
+  info->dual_obj = k[5];
+  info->norm_A = s.norm_A;
+  info->eta = s.eta;
+  info->omega = s.omega;
+  info->tau = s.tau;
+  info->sigma = s.sigma;
+  info->cooperative = h->coop_ok ? 1 : 0;
+}
+
+qp_status validate_problem(int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr,
+                           const int32_t* Qc, const double* Qv, const int32_t* Ar,
+                           const int32_t* Ac, const double* Av, const double* c,
+                           const double* b) {
+  std::string why;
+  if (n <= 0 || m < 0 || m_eq < 0 || m_eq > m) {
+    set_error("bad sizes n=%d m=%d m_eq=%d", n, m, m_eq);
+    return QP_ERR_INVALID_ARG;
+  }
+  if (!c || (m > 0 && !b)) {
+    set_error("c or b is NULL");
+    return QP_ERR_INVALID_ARG;
+  }
+  if (!csr_validate(n, n, Qr, Qc, Qv, &why)) {
+    set_error("Q: %s", why.c_str());
+    return QP_ERR_INVALID_ARG;
+  }
+  if (!csr_validate(m, n, Ar, Ac, Av, &why)) {
+    set_error("A: %s", why.c_str());
+    return QP_ERR_INVALID_ARG;
+  }
+  for (int32_t i = 0; i < n; ++i)
+    if (!std::isfinite(c[i])) {
+      set_error("c[%d] is not finite", i);
+      return QP_ERR_INVALID_ARG;
+    }
+  for (int32_t i = 0; i < m; ++i)
+    if (!std::isfinite(b[i])) {
+      set_error("b[%d] is not finite", i);
+      return QP_ERR_INVALID_ARG;
+    }
+  return QP_OK;
+}
+
+qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr,
+                      const int32_t* Qc, const double* Qv, const int32_t* Ar, const int32_t* Ac,
+                      const double* Av, const double* c, const double* b, uint32_t flags) {
+  HostCsr Qh = csr_canonical(n, n, Qr, Qc, Qv);
+  if ((flags & QP_CREATE_CHECK_SYMMETRY) && !csr_is_symmetric(Qh, 1e-12)) {
+    set_error("Q is not symmetric");
+    return QP_ERR_INVALID_ARG;
+  }
+  HostCsr Ah = csr_canonical(m, n, Ar, Ac, Av);
+  HostCsr Th;
+  Th.rows = n;
+  Th.cols = m;
+  Th.rowptr.resize(size_t(n) + 1);
+  Th.col.resize(size_t(Ah.nnz()));
+  Th.val.resize(size_t(Ah.nnz()));
+  csr_transpose(m, n, Ah.rowptr.data(), Ah.col.data(), Ah.val.data(), Th.rowptr.data(),
+                Th.col.data(), Th.val.data());
+
+  h->n = n;
+  h->m = m;
+  h->m_eq = m_eq;
+  CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  QP_TRY(upload_matrix(h, &h->Q, Qh));
+  QP_TRY(upload_matrix(h, &h->A, Ah));
+  QP_TRY(upload_matrix(h, &h->At, Th));
+  const size_t N = size_t(n), M = size_t(m);
+  double** nvecs[] = {&h->c, &h->x, &h->aty, &h->x_avg, &h->x_anchor, &h->aty_avg, &h->r,
+                      &h->p, &h->q, &h->x0, &h->pw_v, &h->pw_w};
+  for (double** v : nvecs) QP_TRY(dalloc(h, v, N));
+  double** mvecs[] = {&h->b, &h->y, &h->ax, &h->y_avg, &h->y_anchor, &h->ax_avg, &h->y0, &h->pw_u};
+  for (double** v : mvecs) QP_TRY(dalloc(h, v, M));
+  QP_TRY(upload(h, h->c, c, N * sizeof(double)));
+  QP_TRY(upload(h, h->b, b, M * sizeof(double)));
+
+  // Launch geometry: one resident wave for the streaming/SpMV kernels; the CG
+  // kernel is persistent, sized to the co-resident block count.
+  const int wave = h->num_sms * 8;
+  h->grid_n = blocks_for_rows(std::max(n, 1), std::max(h->Q.G, h->At.G), wave);
+  h->grid_m = blocks_for_rows(std::max(m, 1), h->A.G, wave);
+  h->grid_vec = int(std::max<int64_t>(1, std::min<int64_t>((std::max(n, m) + kBlock - 1) / kBlock, wave)));
+  int occ = 0;
+  QP_TRY(dispatch_g(h->Q.G, [&](auto g) {
+    constexpr int G = decltype(g)::value;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<G>, kBlock, 0);
+  }));
+  CUDA_TRY(cudaGetLastError());
+  if (occ < 1) {
+    set_error("CG kernel cannot be resident");
+    return QP_ERR_CUDA;
+  }
+  h->grid_cg = std::min(occ * h->num_sms, blocks_for_rows(n, h->Q.G, occ * h->num_sms));
+  const int gmax = std::max({h->grid_n, h->grid_m, h->grid_vec, h->grid_cg});
+  QP_TRY(dalloc(h, &h->part_cg, size_t(2) * h->grid_cg));
+  QP_TRY(dalloc(h, &h->part_n, size_t(h->grid_n) * kPartStride));
+  QP_TRY(dalloc(h, &h->part_m, size_t(h->grid_m) * kPartStride));
+  QP_TRY(dalloc(h, &h->part_rn, size_t(gmax)));
+  QP_TRY(dalloc(h, &h->part_rm, size_t(gmax)));
+  QP_TRY(dalloc(h, &h->part_pow, size_t(gmax)));
+  QP_TRY(dalloc(h, &h->part2, size_t(2) * gmax));
+  QP_TRY(dalloc(h, &h->st, 1));
+  QP_TRY(dalloc(h, &h->bar, 1));
+  CUDA_TRY(cudaMallocHost(&h->h_st, sizeof(DevState)));
+  std::memset(h->h_st, 0, sizeof(DevState));
+  CUDA_TRY(cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->x0, 0, N * sizeof(double), h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->y0, 0, std::max<size_t>(M, 1) * sizeof(double), h->stream));
+  return sync(h);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* qp_status_string(qp_status s) {
+  switch (s) {
+    case QP_OK: return "ok";
+    case QP_ERR_INVALID_ARG: return "invalid argument";
+    case QP_ERR_OOM: return "out of device memory";
+    case QP_ERR_CUDA: return "CUDA error";
+    case QP_ERR_NOT_SOLVED: return "not solved yet";
+    case QP_ERR_DEVICE_TIMEOUT: return "device barrier timeout";
+    case QP_ERR_NO_DEVICE: return "no CUDA device";
+  }
+  return "unknown status";
+}
+
+int qp_abi_version(void) { return PDHCG_ABI_VERSION; }
+
+const char* qp_last_error(void) { return g_last_error.c_str(); }
+
+void qp_options_default(qp_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-4;
+  o->max_iter = 100000;
+  o->time_limit_s = 3600.0;
+  o->eval_freq = 64;
+  o->cg_mode = QP_CG_ADAPTIVE;
+  o->cg_fixed_n = 5;
+  o->cg_max = 100;
+  o->cg_eps_factor = 0.05;
+  o->restart_mode = QP_RESTART_ADAPTIVE;
+  o->power_iters = 30;
+  o->beta_suff = 0.2;
+  o->beta_nec = 0.8;
+  o->beta_art = 0.2;
+  o->theta_pw = 0.2;
+  o->eps_zero = 1e-10;
+  o->primal_weight_update = 1;
+  o->warm_start = 0;
+  o->omega0 = 0.0;
+  o->eta = 0.0;
+  o->kernel_timing = 0;
+  o->debug_flags = 0;
+}
+
+qp_status qp_create(qp_handle** out, int32_t n, int32_t m, int32_t m_eq, const int32_t* Q_rowptr,
+                    const int32_t* Q_col, const double* Q_val, const int32_t* A_rowptr,
+                    const int32_t* A_col, const double* A_val, const double* c, const double* b,
+                    const qp_device_ctx* ctx, uint32_t flags) {
+  if (!out) {
+    set_error("out is NULL");
+    return QP_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  QP_TRY(validate_problem(n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b));
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    set_error("no CUDA device visible");
+    return QP_ERR_NO_DEVICE;
+  }
+  qp_handle* h = new qp_handle();
+  cudaGetDevice(&h->device);
+  if (ctx) {
+    h->ctx = *ctx;
+    h->has_alloc = ctx->alloc && ctx->free;
+    h->user_stream = static_cast<cudaStream_t>(ctx->stream);
+  }
+  qp_status s = QP_OK;
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_a, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_b, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("stream/event creation failed");
+    s = QP_ERR_CUDA;
+  }
+  if (s == QP_OK) s = begin_call(h);
+  if (s == QP_OK)
+    s = create_impl(h, n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b, flags);
+  if (s == QP_OK) s = end_call(h);
+  if (s != QP_OK) {
+    std::string keep = g_last_error;
+    qp_destroy(h);
+    g_last_error = keep;
+    return s;
+  }
+  *out = h;
+  return QP_OK;
+}
+
+void qp_destroy(qp_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  destroy_chunk(h);
+  for (auto& a : h->allocs) {
+    if (h->has_alloc)
+      h->ctx.free(a.first, a.second, h->ctx.user, h->ctx.stream);
+    else
+      cudaFree(a.first);
+  }
+  if (h->h_st) cudaFreeHost(h->h_st);
+  if (h->ev_a) cudaEventDestroy(h->ev_a);
+  if (h->ev_b) cudaEventDestroy(h->ev_b);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  cudaGetLastError();
+  delete h;
+}
+
+qp_status qp_solve(qp_handle* h, const qp_options* o, qp_info* info_out) {
+  if (!h) {
+    set_error("handle is NULL");
+    return QP_ERR_INVALID_ARG;
+  }
+  QP_TRY(validate_options(o));
+  const auto t0 = std::chrono::steady_clock::now();
+  QP_TRY(begin_call(h));
+  h->trace.clear();
+  h->solved = false;
+  qp_info info{};
+  info.termination = QP_TERM_NONE;
+  const bool timing = o->kernel_timing != 0;
+
+  // ---- set-up: options, start point, ||A||_2, step sizes, relKKT(z0)
+  QP_TRY(write_options(h, o));
+  if (o->warm_start == 2) {
+    // resume a state set by qp_set_state: keep every scalar, clear flags
+    QP_TRY(read_state(h));
+    h->h_st->done = 0;
+    h->h_st->err = 0;
+    h->h_st->restart_pending = 0;
+    fill_dev_options(h, o, &h->h_st->opt);
+    QP_TRY(write_state(h));
+  } else {
+    const double* x0 = (o->warm_start == 1 && h->warm_set) ? h->x0 : nullptr;
+    const double* y0 = (o->warm_start == 1 && h->warm_set) ? h->y0 : nullptr;
+    k_init_vectors<<<h->grid_vec, kBlock, 0, h->stream>>>(h->x, h->x_avg, h->x_anchor, x0, h->n,
+                                                          h->y, h->y_avg, h->y_anchor, y0, h->m);
+    QP_TRY(recompute_caches(h));
+    QP_TRY(launch_setup(h, o->power_iters, 1));
+    QP_TRY(launch_eval(h, 0));
+    QP_TRY(check_launch());
+  }
+  QP_TRY(read_state(h));
+  const auto t_setup = std::chrono::steady_clock::now();
+  info.setup_ms = std::chrono::duration<double, std::milli>(t_setup - t0).count();
+
+  qp_status status = QP_OK;
+  int term = -1;
+  if (h->h_st->err) status = QP_ERR_DEVICE_TIMEOUT;
+  else if (h->h_st->done) term = h->h_st->done - 1;
+
+  // ---- chunks of eval_freq iterations, one relKKT evaluation each
+  if (status == QP_OK && term < 0) {
+    QP_TRY(ensure_chunk(h, o->eval_freq, timing));
+    while (true) {
+      CUDA_TRY(cudaGraphLaunch(h->chunk_exec, h->stream));
+      QP_TRY(sync(h));
+      const DevState& s = *h->h_st;
+      qp_trace_entry te{};
+      te.k = s.k_total;
+      te.kkt_cur = s.kkt_cur[3];
+      te.kkt_avg = s.kkt_avg[3];
+      te.omega = s.omega;
+      te.restart = s.last_restart;
+      te.cg_last = int32_t(s.last_cg);
+      h->trace.push_back(te);
+      if (timing) {
+        for (int k = 0; k < h->chunk_iters; ++k) {
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]) == cudaSuccess &&
+              ms > 0.0f) {
+            info.cg_kernel_ms += ms;
+          }
+        }
+        cudaGetLastError();
+      }
+      if (s.err) {
+        status = QP_ERR_DEVICE_TIMEOUT;
+        break;
+      }
+      if (s.done) {
+        term = s.done - 1;
+        break;
+      }
+      const double el =
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > o->time_limit_s) {
+        term = QP_TERM_TIME_LIMIT;  // returned_avg / kkt_ret describe the last evaluation
+        break;
+      }
+    }
+  }
+  QP_TRY(end_call(h));
+  fill_info_from_state(h, &info);
+  info.termination = term;
+  info.device_error = h->h_st->err;
+  if (timing) {
+    // launches that did work, and the Q products inside them
+    info.cg_kernel_launches = h->h_st->k_total;
+    info.cg_kernel_spmvs = h->h_st->spmv_total;
+  }
+  info.solve_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  h->info = info;
+  h->solved = (status == QP_OK);
+  if (info_out) *info_out = info;
+  if (status == QP_ERR_DEVICE_TIMEOUT) set_error("a device grid barrier timed out");
+  return status;
+}
+
+qp_status qp_get_solution(const qp_handle* h, double* x, double* y) {
+  if (!h) return QP_ERR_INVALID_ARG;
+  if (!h->solved) {
+    set_error("no successful solve on this handle");
+    return QP_ERR_NOT_SOLVED;
+  }
+  qp_handle* hh = const_cast<qp_handle*>(h);
+  CUDA_TRY(cudaSetDevice(h->device));
+  const bool avg = h->info.returned_avg != 0;
+  if (x)
+    CUDA_TRY(cudaMemcpyAsync(x, avg ? h->x_avg : h->x, size_t(h->n) * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+  if (y && h->m > 0)
+    CUDA_TRY(cudaMemcpyAsync(y, avg ? h->y_avg : h->y, size_t(h->m) * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+  return sync(hh);
+}
+
+qp_status qp_get_stats(const qp_handle* h, qp_info* info) {
+  if (!h || !info) return QP_ERR_INVALID_ARG;
+  if (!h->solved) return QP_ERR_NOT_SOLVED;
+  *info = h->info;
+  return QP_OK;
+}
+
+qp_status qp_get_trace(const qp_handle* h, qp_trace_entry* out, int64_t cap, int64_t* count) {
+  if (!h || !count || (cap > 0 && !out)) return QP_ERR_INVALID_ARG;
+  *count = int64_t(h->trace.size());
+  for (int64_t i = 0; i < std::min<int64_t>(cap, *count); ++i) out[i] = h->trace[size_t(i)];
+  return QP_OK;
+}
+
+qp_status qp_set_warm_start(qp_handle* h, const double* x0, const double* y0) {
+  if (!h) return QP_ERR_INVALID_ARG;
+  QP_TRY(begin_call(h));
+  if (x0) QP_TRY(upload(h, h->x0, x0, size_t(h->n) * sizeof(double)));
+  else CUDA_TRY(cudaMemsetAsync(h->x0, 0, size_t(h->n) * sizeof(double), h->stream));
+  if (h->m > 0) {
+    if (y0) QP_TRY(upload(h, h->y0, y0, size_t(h->m) * sizeof(double)));
+    else CUDA_TRY(cudaMemsetAsync(h->y0, 0, size_t(h->m) * sizeof(double), h->stream));
+  }
+  h->warm_set = true;
+  QP_TRY(sync(h));
+  return end_call(h);
+}
+
+qp_status qp_get_state(const qp_handle* hc, const qp_state_vectors* v, qp_state_scalars* s) {
+  if (!hc) return QP_ERR_INVALID_ARG;
+  qp_handle* h = const_cast<qp_handle*>(hc);
+  QP_TRY(begin_call(h));
+  const size_t nb = size_t(h->n) * sizeof(double), mb = size_t(h->m) * sizeof(double);
+  if (v) {
+    const std::pair<double*, double*> nv[] = {{v->x, h->x}, {v->x_avg, h->x_avg}, {v->x_anchor, h->x_anchor}};
+    const std::pair<double*, double*> mv[] = {{v->y, h->y}, {v->y_avg, h->y_avg}, {v->y_anchor, h->y_anchor}};
+    for (auto& pr : nv)
+      if (pr.first) CUDA_TRY(cudaMemcpyAsync(pr.first, pr.second, nb, cudaMemcpyDeviceToHost, h->stream));
+    for (auto& pr : mv)
+      if (pr.first && mb) CUDA_TRY(cudaMemcpyAsync(pr.first, pr.second, mb, cudaMemcpyDeviceToHost, h->stream));
+  }
+  QP_TRY(read_state(h));
+  if (s) {
+    const DevState& d = *h->h_st;
+    s->eta = d.eta;
+    s->omega = d.omega;
+    s->eps = d.eps;
+    s->relkkt_last = d.relkkt_last;
+    s->kkt_anchor = d.kkt_anchor;
+    s->kkt_prev_cand = d.kkt_prev_cand;
+    s->j = d.j;
+    s->k_total = d.k_total;
+    s->restarts = d.n_restarts;
+    s->cg_total = d.cg_total;
+  }
+  return end_call(h);
+}
+
+qp_status qp_set_state(qp_handle* h, const qp_state_vectors* v, const qp_state_scalars* s) {
+  if (!h || !v || !s) return QP_ERR_INVALID_ARG;
+  if (!(s->omega > 0.0) || !(s->eta > 0.0) || s->j < 0 || s->k_total < 0) {
+    set_error("invalid state scalars");
+    return QP_ERR_INVALID_ARG;
+  }
+  QP_TRY(begin_call(h));
+  const size_t nb = size_t(h->n) * sizeof(double), mb = size_t(h->m) * sizeof(double);
+  const std::pair<const double*, double*> nv[] = {{v->x, h->x}, {v->x_avg, h->x_avg}, {v->x_anchor, h->x_anchor}};
+  const std::pair<const double*, double*> mv[] = {{v->y, h->y}, {v->y_avg, h->y_avg}, {v->y_anchor, h->y_anchor}};
+  for (auto& pr : nv) {
+    if (pr.first) QP_TRY(upload(h, pr.second, pr.first, nb));
+    else CUDA_TRY(cudaMemsetAsync(pr.second, 0, nb, h->stream));
+  }
+  for (auto& pr : mv) {
+    if (!mb) continue;
+    if (pr.first) QP_TRY(upload(h, pr.second, pr.first, mb));
+    else CUDA_TRY(cudaMemsetAsync(pr.second, 0, mb, h->stream));
+  }
+  QP_TRY(recompute_caches(h));
+  QP_TRY(check_launch());
+  QP_TRY(read_state(h));
+  DevState& d = *h->h_st;
+  d.eta = s->eta;
+  d.omega = s->omega;
+  d.tau = s->eta / s->omega;
+  d.sigma = s->eta * s->omega;
+  d.eps = s->eps;
+  d.relkkt_last = s->relkkt_last;
+  d.kkt_anchor = s->kkt_anchor;
+  d.kkt_prev_cand = s->kkt_prev_cand;
+  d.j = s->j;
+  d.k_total = s->k_total;
+  d.n_restarts = s->restarts;
+  d.cg_total = s->cg_total;
+  d.done = 0;
+  d.err = 0;
+  d.restart_pending = 0;
+  d.iter_active = 0;
+  QP_TRY(write_state(h));
+  return end_call(h);
+}
+
+qp_status qp_iterate(qp_handle* h, const qp_options* o, int64_t iters) {
+  if (!h || iters < 0) return QP_ERR_INVALID_ARG;
+  QP_TRY(validate_options(o));
+  QP_TRY(begin_call(h));
+  QP_TRY(read_state(h));
+  DevState& d = *h->h_st;
+  fill_dev_options(h, o, &d.opt);
+  d.opt.max_iter = d.k_total + iters;
+  d.done = 0;
+  d.err = 0;
+  QP_TRY(write_state(h));
+  CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->stream));
+  for (int64_t k = 0; k < iters; ++k) {
+    qp_status s = launch_iteration(h, h->coop_ok);
+    if (s == QP_OK) s = check_launch();
+    if (s != QP_OK && h->coop_ok) {
+      h->coop_ok = false;
+      s = launch_iteration(h, false);
+      if (s == QP_OK) s = check_launch();
+    }
+    if (s != QP_OK) return s;
+  }
+  QP_TRY(read_state(h));
+  QP_TRY(end_call(h));
+  if (h->h_st->err) {
+    set_error("a device grid barrier timed out");
+    return QP_ERR_DEVICE_TIMEOUT;
+  }
+  return QP_OK;
+}
+
+qp_status qp_evaluate(qp_handle* h, double kkt_cur[6], double kkt_avg[6]) {
+  if (!h) return QP_ERR_INVALID_ARG;
+  QP_TRY(begin_call(h));
+  QP_TRY(launch_eval(h, 2));
+  QP_TRY(check_launch());
+  QP_TRY(read_state(h));
+  for (int k = 0; k < 6; ++k) {
+    if (kkt_cur) kkt_cur[k] = h->h_st->kkt_cur[k];
+    if (kkt_avg) kkt_avg[k] = h->h_st->kkt_avg[k];
+  }
+  return end_call(h);
+}
+
+qp_status qp_norm_A(qp_handle* h, int32_t iters, double* out) {
+  if (!h || !out || iters < 1) return QP_ERR_INVALID_ARG;
+  QP_TRY(begin_call(h));
+  QP_TRY(read_state(h));
+  const DevState saved = *h->h_st;
+  QP_TRY(launch_setup(h, iters, 0));
+  QP_TRY(check_launch());
+  QP_TRY(read_state(h));
+  *out = h->h_st->norm_A;
+  // restore the step-size state the set-up kernel overwrote
+  DevState& d = *h->h_st;
+  d.eta = saved.eta;
+  d.omega = saved.omega;
+  d.tau = saved.tau;
+  d.sigma = saved.sigma;
+  d.norm_A = saved.norm_A;
+  d.lam = saved.lam;
+  d.done = saved.done;
+  d.err = saved.err;
+  QP_TRY(write_state(h));
+  return end_call(h);
+}
+
+qp_status qp_csr_validate(int32_t rows, int32_t cols, const int32_t* rowptr, const int32_t* col,
+                          const double* val) {
+  std::string why;
+  if (!csr_validate(rows, cols, rowptr, col, val, &why)) {
+    set_error("%s", why.c_str());
+    return QP_ERR_INVALID_ARG;
+  }
+  return QP_OK;
+}
+
+qp_status qp_csr_transpose(int32_t rows, int32_t cols, const int32_t* rowptr, const int32_t* col,
+                           const double* val, int32_t* t_rowptr, int32_t* t_col, double* t_val) {
+  QP_TRY(qp_csr_validate(rows, cols, rowptr, col, val));
+  if (!t_rowptr || (rowptr[rows] > 0 && (!t_col || !t_val))) return QP_ERR_INVALID_ARG;
+  csr_transpose(rows, cols, rowptr, col, val, t_rowptr, t_col, t_val);
+  return QP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,214 @@
+"""Python face of the C ABI: argument marshalling only.
+
+Every step of the solve runs in libpdhcg.so's CUDA kernels; this module
+converts numpy arrays to the C types, lends PyTorch's caching allocator and
+current stream to the library, and turns status codes into exceptions.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, byref, c_double, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} entries, got {a.size}")
+    return a
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(POINTER(ctype)) if a is not None else None
+
+
+class QPOptions:
+    """Solver options (see qp_options in include/pdhcg.h); defaults from the library."""
+
+    def __init__(self, **overrides):
+        lib = L.load_library()
+        self._c = L.QPOptionsC()
+        lib.qp_options_default(byref(self._c))
+        for k, v in overrides.items():
+            setattr(self, k, v)
+
+    def __getattr__(self, name):
+        c = self.__dict__.get("_c")
+        if c is not None and name in dict(L.QPOptionsC._fields_):
+            return getattr(c, name)
+        raise AttributeError(name)
+
+    def __setattr__(self, name, value):
+        if name == "_c":
+            object.__setattr__(self, name, value)
+        elif name in dict(L.QPOptionsC._fields_):
+            setattr(self._c, name, value)
+        else:
+            raise AttributeError(f"unknown option {name}")
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self._c, n) for n, _ in L.QPOptionsC._fields_ if n != "reserved"}
+
+
+class QPSolver:
+    """One QP resident on the current CUDA device.
+
+    ``QPSolver(inst)`` copies the instance (``workloads.QPInstance`` or any
+    object with the same CSR fields) through ``qp_create``.  With
+    ``torch_memory=True`` (default) the device buffers come from PyTorch's
+    caching allocator and the work is ordered after PyTorch's current stream.
+    """
+
+    def __init__(self, inst, torch_memory: bool = True, check_symmetry: bool = False):
+        self.lib = L.load_library()
+        self.n, self.m, self.m_eq = int(inst.n), int(inst.m), int(inst.m_eq)
+        self._keep = []
+        ctx = None
+        if torch_memory:
+            ctx = self._torch_ctx()
+        Qr, Qc, Qv = _i32(inst.Q_rowptr), _i32(inst.Q_col), _f64(inst.Q_val)
+        Ar, Ac, Av = _i32(inst.A_rowptr), _i32(inst.A_col), _f64(inst.A_val)
+        c, b = _f64(inst.c, self.n), _f64(inst.b, self.m)
+        h = c_void_p()
+        st = self.lib.qp_create(byref(h), self.n, self.m, self.m_eq,
+                                _ptr(Qr, c_int32), _ptr(Qc, c_int32), _ptr(Qv, c_double),
+                                _ptr(Ar, c_int32), _ptr(Ac, c_int32), _ptr(Av, c_double),
+                                _ptr(c, c_double), _ptr(b, c_double),
+                                byref(ctx) if ctx is not None else None,
+                                L.CREATE_CHECK_SYMMETRY if check_symmetry else 0)
+        L.check(st, "qp_create")
+        self.h = h
+        self._ctx = ctx
+
+    def _torch_ctx(self):
+        import torch
+
+        dev = torch.cuda.current_device()
+        stream = torch.cuda.current_stream()
+
+        def _alloc(nbytes, user, s):
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+
+        def _free(ptr, nbytes, user, s):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        fa, ff = L.ALLOC_FN(_alloc), L.FREE_FN(_free)
+        self._keep += [fa, ff, stream]
+        return L.QPDeviceCtxC(fa, ff, None, c_void_p(stream.cuda_stream))
+
+    # ------------------------------------------------------------------ solve
+    def solve(self, options: QPOptions | None = None, **overrides) -> dict:
+        o = options or QPOptions()
+        for k, v in overrides.items():
+            setattr(o, k, v)
+        info = L.QPInfoC()
+        st = self.lib.qp_solve(self.h, byref(o._c), byref(info))
+        L.check(st, "qp_solve")
+        return info.as_dict()
+
+    def solution(self):
+        x = np.empty(self.n)
+        y = np.empty(self.m)
+        L.check(self.lib.qp_get_solution(self.h, _ptr(x, c_double), _ptr(y, c_double)),
+                "qp_get_solution")
+        return x, y
+
+    def stats(self) -> dict:
+        info = L.QPInfoC()
+        L.check(self.lib.qp_get_stats(self.h, byref(info)), "qp_get_stats")
+        return info.as_dict()
+
+    def trace(self) -> list:
+        cnt = c_int64()
+        L.check(self.lib.qp_get_trace(self.h, None, 0, byref(cnt)), "qp_get_trace")
+        buf = (L.QPTraceEntryC * max(cnt.value, 1))()
+        L.check(self.lib.qp_get_trace(self.h, buf, cnt.value, byref(cnt)), "qp_get_trace")
+        return [{n: getattr(buf[i], n) for n, _ in L.QPTraceEntryC._fields_}
+                for i in range(cnt.value)]
+
+    # ----------------------------------------------------------------- state
+    _VEC = ("x", "y", "x_avg", "y_avg", "x_anchor", "y_anchor")
+
+    def get_state(self) -> dict:
+        arrs = {k: np.empty(self.n if k.startswith("x") else self.m) for k in self._VEC}
+        v = L.QPStateVectorsC(*[_ptr(arrs[k], c_double) for k in self._VEC])
+        s = L.QPStateScalarsC()
+        L.check(self.lib.qp_get_state(self.h, byref(v), byref(s)), "qp_get_state")
+        arrs.update({n: getattr(s, n) for n, _ in L.QPStateScalarsC._fields_})
+        return arrs
+
+    def set_state(self, state: dict) -> None:
+        arrs = {k: (_f64(state[k], self.n if k.startswith("x") else self.m)
+                    if state.get(k) is not None else None) for k in self._VEC}
+        v = L.QPStateVectorsC(*[_ptr(arrs[k], c_double) for k in self._VEC])
+        s = L.QPStateScalarsC(*[state[n] for n, _ in L.QPStateScalarsC._fields_])
+        L.check(self.lib.qp_set_state(self.h, byref(v), byref(s)), "qp_set_state")
+
+    def set_warm_start(self, x0=None, y0=None) -> None:
+        x0 = _f64(x0, self.n) if x0 is not None else None
+        y0 = _f64(y0, self.m) if y0 is not None else None
+        L.check(self.lib.qp_set_warm_start(self.h, _ptr(x0, c_double), _ptr(y0, c_double)),
+                "qp_set_warm_start")
+
+    def iterate(self, iters: int, options: QPOptions | None = None, **overrides) -> None:
+        o = options or QPOptions()
+        for k, v in overrides.items():
+            setattr(o, k, v)
+        L.check(self.lib.qp_iterate(self.h, byref(o._c), int(iters)), "qp_iterate")
+
+    def evaluate(self):
+        kc = np.empty(6)
+        ka = np.empty(6)
+        L.check(self.lib.qp_evaluate(self.h, _ptr(kc, c_double), _ptr(ka, c_double)), "qp_evaluate")
+        keys = ("r_primal", "r_dual", "r_gap", "relkkt", "primal_obj", "dual_obj")
+        return dict(zip(keys, kc)), dict(zip(keys, ka))
+
+    def norm_A(self, iters: int = 30) -> float:
+        out = c_double()
+        L.check(self.lib.qp_norm_A(self.h, int(iters), byref(out)), "qp_norm_A")
+        return out.value
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.qp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ------------------------------------------------------------ host-only helpers
+def csr_validate(rows, cols, rowptr, col, val) -> int:
+    lib = L.load_library()
+    rp, cc, vv = _i32(rowptr), _i32(col), _f64(val)
+    return lib.qp_csr_validate(int(rows), int(cols), _ptr(rp, c_int32), _ptr(cc, c_int32),
+                               _ptr(vv, c_double))
+
+
+def csr_transpose(rows, cols, rowptr, col, val):
+    lib = L.load_library()
+    rp, cc, vv = _i32(rowptr), _i32(col), _f64(val)
+    nnz = int(rp[-1])
+    tr = np.empty(cols + 1, np.int32)
+    tc = np.empty(max(nnz, 1), np.int32)
+    tv = np.empty(max(nnz, 1), np.float64)
+    L.check(lib.qp_csr_transpose(int(rows), int(cols), _ptr(rp, c_int32), _ptr(cc, c_int32),
+                                 _ptr(vv, c_double), _ptr(tr, c_int32), _ptr(tc, c_int32),
+                                 _ptr(tv, c_double)), "qp_csr_transpose")
+    return tr, tc[:nnz], tv[:nnz]

@@ -1,0 +1,143 @@
+"""Host-side tests of the C ABI (no GPU needed).
+
+The library must load on a machine without a GPU, export every function
+include/pdhcg.h declares, agree with the ctypes mirror on struct layouts, and
+do its host work (CSR validation, the stable transpose behind the explicit
+A', option defaults) correctly.
+"""
+import os
+import re
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_2405_16160_b300 import _lib as L
+from paper_2405_16160_b300 import solver as S
+from paper_2405_16160_b300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2405_16160_b300 import build
+    build.build()
+    return L.load_library()
+
+
+def _declared_functions():
+    text = open(L.HEADER_PATH).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qp_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_function_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(n for n, _, _ in L.SIGNATURES) == names
+
+
+def test_abi_version_and_status_strings(lib):
+    assert lib.qp_abi_version() == 1
+    assert lib.qp_status_string(0) == b"ok"
+    assert lib.qp_status_string(5) == b"device barrier timeout"
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc not available")
+def test_struct_layouts_match_ctypes(tmp_path):
+    structs = {"qp_options": L.QPOptionsC, "qp_info": L.QPInfoC,
+               "qp_state_scalars": L.QPStateScalarsC, "qp_state_vectors": L.QPStateVectorsC,
+               "qp_trace_entry": L.QPTraceEntryC, "qp_device_ctx": L.QPDeviceCtxC}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdhcg.h"', "int main(void){"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = dict(line.rsplit(" ", 1) for line in out if line)
+    for cname, py in structs.items():
+        assert int(got[f"{cname} size"]) == __import__("ctypes").sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
+
+
+def test_option_defaults_follow_the_paper(lib):
+    o = S.QPOptions()
+    # Section 4: beta_suff, beta_nec, beta_art, theta; 0.05 relKKT increments of eps_k
+    assert (o.beta_suff, o.beta_nec, o.beta_art, o.theta_pw) == (0.2, 0.8, 0.2, 0.2)
+    assert o.cg_eps_factor == 0.05
+    assert o.power_iters == 30 and o.eval_freq == 64 and o.tol == 1e-4
+    assert o.cg_mode == L.CG_ADAPTIVE and o.restart_mode == L.RESTART_ADAPTIVE
+
+
+def test_csr_validate_rejects_bad_inputs(lib):
+    ok = S.csr_validate(2, 3, [0, 1, 3], [0, 1, 2], [1.0, 2.0, 3.0])
+    assert ok == 0
+    bad = [
+        (2, 3, [1, 1, 3], [0, 1, 2], [1.0, 2.0, 3.0]),  # rowptr[0] != 0
+        (2, 3, [0, 2, 1], [0, 1, 2], [1.0, 2.0, 3.0]),  # not monotone
+        (2, 3, [0, 1, 3], [0, 3, 2], [1.0, 2.0, 3.0]),  # column out of range
+        (2, 3, [0, 1, 3], [0, -1, 2], [1.0, 2.0, 3.0]),  # negative column
+        (2, 3, [0, 1, 3], [0, 1, 2], [1.0, np.nan, 3.0]),  # NaN
+        (2, 3, [0, 1, 3], [0, 1, 2], [1.0, np.inf, 3.0]),  # Inf
+    ]
+    for args in bad:
+        assert S.csr_validate(*args) == 1, args
+
+
+def test_csr_transpose_is_stable_and_exact(lib):
+    rng = np.random.default_rng(0)
+    M = sp.random(300, 170, density=0.03, random_state=1, format="csr")
+    M.data = rng.standard_normal(M.nnz)
+    tr, tc, tv = S.csr_transpose(300, 170, M.indptr, M.indices, M.data)
+    T = sp.csr_matrix((tv, tc, tr), shape=(170, 300))
+    assert (T != M.T).nnz == 0
+    for j in range(170):  # entries keep increasing input-row order
+        assert np.all(np.diff(tc[tr[j]:tr[j + 1]]) > 0)
+    # empty matrix and empty rows
+    tr, tc, tv = S.csr_transpose(3, 4, [0, 0, 0, 0], [], [])
+    assert list(tr) == [0, 0, 0, 0, 0] and tc.size == 0
+
+
+def test_create_validates_before_touching_a_device(lib):
+    inst = W.dense_small(0)
+    bad = W.dense_small(0)
+    bad.c = bad.c.copy()
+    bad.c[3] = np.nan
+    with pytest.raises(L.QPError) as e:
+        S.QPSolver(bad, torch_memory=False)
+    assert e.value.status == 1
+    bad2 = W.dense_small(0)
+    bad2.A_col = bad2.A_col.copy()
+    bad2.A_col[0] = inst.n  # out of range
+    with pytest.raises(L.QPError) as e:
+        S.QPSolver(bad2, torch_memory=False)
+    assert e.value.status == 1
+    with pytest.raises(L.QPError) as e:  # m_eq > m
+        inst.m_eq = inst.m + 1
+        S.QPSolver(inst, torch_memory=False)
+    assert e.value.status == 1
+
+
+def test_create_without_gpu_reports_no_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(L.QPError) as e:
+        S.QPSolver(W.dense_small(0), torch_memory=False)
+    assert e.value.status == 6
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    with pytest.raises(FileNotFoundError):
+        L.load_library(str(tmp_path / "libpdhcg.so"))

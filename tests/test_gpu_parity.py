@@ -1,0 +1,302 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerances (FP64 on both sides; the two differ only in summation order and
+in fused multiply-adds):
+  * ||A||_2, relKKT terms: 1e-12 relative;
+  * one iteration from a shared state: 1e-10 relative (infinity norm);
+  * end to end: both reach relKKT <= tol, the oracle re-scores the GPU
+    solution at <= tol, the restart decisions agree, and the objectives
+    agree within 1e-4 relative.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import pdhcg_oracle as O
+from paper_2405_16160_b300 import _lib as L
+from paper_2405_16160_b300 import workloads as W
+from paper_2405_16160_b300.solver import QPOptions, QPSolver
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2405_16160_b300 import build
+    build.build()
+
+
+def _ragged_eq():
+    return W.sparse_dd(3, n=1237, m=611, m_eq=17)
+
+
+def _unconstrained():
+    rng = np.random.default_rng(5)
+    n = 37
+    M = rng.standard_normal((n, n))
+    Qd = M @ M.T / n + np.eye(n)
+    return W.from_dense(Qd, np.zeros((0, n)), rng.standard_normal(n), np.zeros(0), name="m=0")
+
+
+def _all_equalities():
+    rng = np.random.default_rng(6)
+    n, m = 40, 12
+    Qd = np.diag(rng.uniform(0.5, 2, n))
+    Ad = W._bernoulli_normal(rng, m, n, 0.3)
+    return W.from_dense(Qd, Ad, rng.standard_normal(n), Ad @ rng.standard_normal(n), m_eq=m,
+                        name="all equalities")
+
+
+def _empty_rows():
+    rng = np.random.default_rng(7)
+    n, m = 50, 30
+    Qd = np.diag(rng.uniform(0.5, 2, n))
+    Qd[3, 3] = 0.0  # an empty row/column of Q (PSD)
+    Ad = W._bernoulli_normal(rng, m, n, 0.2)
+    Ad[[0, 7, 29], :] = 0.0  # empty rows of A
+    Ad[:, [4, 9]] = 0.0  # empty rows of A'
+    return W.from_dense(Qd, Ad, rng.standard_normal(n), Ad @ rng.standard_normal(n) + 0.5,
+                        name="empty rows")
+
+
+def _single():
+    return W.from_dense(np.array([[2.0]]), np.array([[1.0]]), np.array([-3.0]), np.array([1.0]),
+                        name="n=1")
+
+
+CASES = {
+    "dense_small": lambda: W.dense_small(0),
+    "dense_small_eq": lambda: W.dense_small(1, m_eq=10),
+    "sparse_small": lambda: W.sparse_dd(0, n=20_000, m=10_000),
+    "ragged_eq": _ragged_eq,
+    "unconstrained": _unconstrained,
+    "all_equalities": _all_equalities,
+    "empty_rows": _empty_rows,
+    "single": _single,
+}
+
+
+def _relerr(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    if a.size == 0:
+        return 0.0
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _shared_state(inst, P, seed):
+    rng = np.random.default_rng(seed)
+    n, m, me = inst.n, inst.m, inst.m_eq
+
+    def yv():
+        y = np.abs(rng.standard_normal(m))
+        y[:me] = rng.standard_normal(me)
+        return y
+
+    eta = 1.0 / (2.0 * max(O.spectral_norm(P.A, 30), 1e-10))
+    return {"x": rng.standard_normal(n), "y": yv(), "x_avg": rng.standard_normal(n),
+            "y_avg": yv(), "x_anchor": rng.standard_normal(n), "y_anchor": yv(),
+            "eta": eta, "omega": 1.3, "eps": 1e-3, "relkkt_last": 0.2, "kkt_anchor": 0.5,
+            "kkt_prev_cand": math.inf, "j": 3, "k_total": 10, "restarts": 0, "cg_total": 0}
+
+
+def _oracle_state(s):
+    return O.OracleState(x=s["x"].copy(), y=s["y"].copy(), x_avg=s["x_avg"].copy(),
+                         y_avg=s["y_avg"].copy(), x_anchor=s["x_anchor"].copy(),
+                         y_anchor=s["y_anchor"].copy(), eta=s["eta"], omega=s["omega"],
+                         eps=s["eps"], j=s["j"], k_total=s["k_total"],
+                         relkkt_last=s["relkkt_last"], kkt_anchor=s["kkt_anchor"],
+                         kkt_prev_cand=s["kkt_prev_cand"])
+
+
+@pytest.fixture(scope="module")
+def built():
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            inst = CASES[name]()
+            cache[name] = (inst, O.problem_from_instance(inst), QPSolver(inst))
+        return cache[name]
+
+    yield get
+    for _, _, s in cache.values():
+        s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_norm_A_matches_oracle(built, name):
+    inst, P, s = built(name)
+    assert s.norm_A(30) == pytest.approx(O.spectral_norm(P.A, 30), rel=1e-12, abs=1e-300)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_relkkt_terms_match_oracle(built, name):
+    inst, P, s = built(name)
+    st = _shared_state(inst, P, 1)
+    s.set_state(st)
+    kc, ka = s.evaluate()
+    for got, (x, y) in ((kc, (st["x"], st["y"])), (ka, (st["x_avg"], st["y_avg"]))):
+        ref = O.relkkt(P, x, y)
+        for key in ("r_primal", "r_dual", "r_gap", "relkkt", "primal_obj", "dual_obj"):
+            assert got[key] == pytest.approx(getattr(ref, key), rel=1e-12, abs=1e-14), key
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("mode,iters", [("fixed3", 1), ("adaptive", 1), ("adaptive", 4)])
+def test_iterations_match_oracle(built, name, mode, iters):
+    inst, P, s = built(name)
+    st = _shared_state(inst, P, 2)
+    s.set_state(st)
+    kw = dict(cg_mode=L.CG_FIXED, cg_fixed_n=3) if mode == "fixed3" else {}
+    s.iterate(iters, **kw)
+    got = s.get_state()
+    o = O.OracleOptions(**({"cg_mode": O.CG_FIXED, "cg_fixed_n": 3} if mode == "fixed3" else {}))
+    ost = _oracle_state(st)
+    for _ in range(iters):
+        O.inner_step(P, ost, o)
+    for key in ("x", "y", "x_avg", "y_avg"):
+        assert _relerr(got[key], getattr(ost, key)) <= 1e-10, key
+    assert got["cg_total"] == ost.cg_total
+    assert got["j"] == ost.j and got["k_total"] == ost.k_total
+    assert got["eps"] == pytest.approx(ost.eps, rel=1e-15)
+    if inst.m > inst.m_eq:
+        assert np.all(got["y"][inst.m_eq:] >= 0.0)
+
+
+@pytest.mark.parametrize("name,tol", [("dense_small", 1e-6), ("dense_small_eq", 1e-6),
+                                      ("sparse_small", 1e-4), ("ragged_eq", 1e-4),
+                                      ("unconstrained", 1e-6), ("all_equalities", 1e-6),
+                                      ("empty_rows", 1e-6), ("single", 1e-8)])
+def test_end_to_end_matches_oracle(built, name, tol):
+    inst, P, s = built(name)
+    ores = O.solve(P, O.OracleOptions(tol=tol))
+    info = s.solve(tol=tol)
+    x, y = s.solution()
+    assert ores.termination == O.SOLVED
+    assert info["termination"] == L.TERM_SOLVED
+    rescored = O.relkkt(P, x, y)
+    assert rescored.relkkt <= tol
+    assert info["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-15)
+    assert rescored.primal_obj == pytest.approx(ores.kkt.primal_obj, rel=1e-4, abs=1e-8)
+    # same trajectory: iteration count, restarts, CG steps and restart decisions
+    trace = s.trace()
+    orestarts = [(r["k"], int(r["restart"]) * (2 if r["cand_avg"] else 1)) for r in ores.trace[1:]]
+    grestarts = [(t["k"], t["restart"]) for t in trace]
+    assert grestarts == orestarts
+    assert info["iterations"] == ores.iterations
+    assert info["restarts"] == ores.restarts
+    assert info["cg_steps"] == ores.cg_steps
+    assert _relerr(x, ores.x) <= 1e-8
+
+
+def test_solves_are_deterministic_and_allocator_independent(built):
+    inst, P, s = built("sparse_small")
+    s.solve(tol=1e-4)
+    x1, y1 = s.solution()
+    s.solve(tol=1e-4)
+    x2, y2 = s.solution()
+    with QPSolver(inst, torch_memory=False) as s2:
+        s2.solve(tol=1e-4)
+        x3, y3 = s2.solution()
+    assert np.array_equal(x1, x2) and np.array_equal(y1, y2)
+    assert np.array_equal(x1, x3) and np.array_equal(y1, y3)
+
+
+def test_checkpoint_resume_is_bit_identical(built):
+    inst, P, s = built("sparse_small")
+    s.solve(tol=0.0, max_iter=256)
+    full = s.get_state()
+    s.solve(tol=0.0, max_iter=128)
+    mid = s.get_state()
+    with QPSolver(inst) as s2:
+        s2.set_state(mid)
+        s2.solve(tol=0.0, max_iter=256, warm_start=2)
+        resumed = s2.get_state()
+    for key in ("x", "y", "x_avg", "y_avg", "x_anchor", "y_anchor"):
+        assert np.array_equal(full[key], resumed[key]), key
+    for key in ("omega", "eps", "j", "k_total", "restarts", "cg_total"):
+        assert full[key] == resumed[key], key
+
+
+def test_warm_start_from_solution_stops_at_once(built):
+    inst, P, s = built("dense_small")
+    s.solve(tol=1e-6)
+    x, y = s.solution()
+    s.set_warm_start(x, y)
+    info = s.solve(tol=1e-6, warm_start=1)
+    assert info["termination"] == L.TERM_SOLVED and info["iterations"] == 0
+
+
+def test_iteration_limit_returns_best_iterate(built):
+    inst, P, s = built("sparse_small")
+    info = s.solve(tol=1e-12, max_iter=100)
+    assert info["termination"] == L.TERM_ITER_LIMIT and info["iterations"] == 100
+    x, y = s.solution()
+    assert O.relkkt(P, x, y).relkkt == pytest.approx(info["relkkt"], rel=1e-9)
+
+
+def test_numerical_error_on_indefinite_q():
+    n = 20
+    inst = W.from_dense(-100.0 * np.eye(n), np.ones((1, n)), np.ones(n), np.array([1.0]))
+    ores = O.solve(O.problem_from_instance(inst), O.OracleOptions())
+    assert ores.termination == O.NUMERICAL_ERROR
+    with QPSolver(inst) as s:
+        info = s.solve()
+    assert info["termination"] == L.TERM_NUMERICAL
+
+
+def test_barrier_timeout_returns_status_and_context_survives(built):
+    inst, P, s = built("sparse_small")
+    with pytest.raises(L.QPError) as e:
+        s.solve(debug_flags=L.DEBUG_BARRIER_NEVER_RELEASES)
+    assert e.value.status == 5
+    info = s.solve(tol=1e-4)  # the same handle keeps working
+    assert info["termination"] == L.TERM_SOLVED
+
+
+# ------------------------------------------------------------- full size
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden",
+                      "sparse_dd_n1000000_m500000_seed0_trace.json")
+
+
+@pytest.fixture(scope="module")
+def big():
+    inst = W.sparse_dd(0)
+    s = QPSolver(inst)
+    yield inst, O.problem_from_instance(inst), s
+    s.close()
+
+
+def test_full_size_one_iteration_parity(big):
+    inst, P, s = big
+    st = _shared_state(inst, P, 3)
+    s.set_state(st)
+    s.iterate(1)
+    got = s.get_state()
+    ost = _oracle_state(st)
+    O.inner_step(P, ost, O.OracleOptions())
+    for key in ("x", "y", "x_avg", "y_avg"):
+        assert _relerr(got[key], getattr(ost, key)) <= 1e-10, key
+    assert got["cg_total"] == ost.cg_total
+
+
+def test_full_size_solve_matches_oracle_trace(big):
+    inst, P, s = big
+    info = s.solve(tol=1e-4)
+    x, y = s.solution()
+    assert info["termination"] == L.TERM_SOLVED
+    rescored = O.relkkt(P, x, y)
+    assert rescored.relkkt <= 1e-4
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    assert info["iterations"] == g["iterations"]
+    assert info["restarts"] == g["restarts"]
+    assert info["cg_steps"] == g["cg_steps"]
+    assert rescored.primal_obj == pytest.approx(g["primal_obj"], rel=1e-4)
+    assert info["norm_A"] == pytest.approx(1.0 / (2.0 * g["eta"]), rel=1e-12)
