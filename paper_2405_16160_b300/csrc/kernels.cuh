@@ -25,6 +25,7 @@
 namespace pdhcg {
 
 constexpr int kBlock = 256;
+constexpr int kCgBlock = 512;  // persistent CG kernel: fewer, larger blocks
 constexpr int kPartStride = 16;  // doubles per block in the multi-value partial buffers
 constexpr int kCgAdaptive = 0;
 constexpr int kCgFixed = 1;
@@ -107,8 +108,9 @@ __device__ __forceinline__ double warp_max(double v) {
 // (of non-negative values) instead of sum.  Thread 0 writes out[0..K).
 template <int K>
 __device__ __forceinline__ void block_reduce_store(double (&v)[K], unsigned max_mask, double* out) {
-  __shared__ double sh[K][kBlock / 32];
+  __shared__ double sh[K][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const double x = ((max_mask >> k) & 1u) ? warp_max(v[k]) : warp_sum(v[k]);
@@ -118,7 +120,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[K], unsigned max_
   if (wid == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      double x = lane < (kBlock / 32) ? sh[k][lane] : 0.0;
+      double x = lane < nwarps ? sh[k][lane] : 0.0;
       x = ((max_mask >> k) & 1u) ? warp_max(x) : warp_sum(x);
       if (lane == 0) out[k] = x;
     }
@@ -267,7 +269,7 @@ __device__ __forceinline__ long long grid_threads() { return (long long)gridDim.
 // step: [A] q = Qp + p/tau, p'q  | [B] x += a p, r -= a q, r'r  | [C] p = r + b p.
 // part holds 2 * gridDim.x doubles.
 template <int G>
-__global__ void __launch_bounds__(kBlock, 6) k_cg(DevCsr Q, const double* __restrict__ c,
+__global__ void __launch_bounds__(kCgBlock, 3) k_cg(DevCsr Q, const double* __restrict__ c,
                                                const double* __restrict__ aty, double* x,
                                                double* r, double* p, double* q, double* part,
                                                DevState* st, GridBarrier* bar, int n) {
@@ -279,6 +281,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_cg(DevCsr Q, const double* __rest
   // Every read of st happens before the first barrier; block 0 writes the
   // counters only after the last one.
   const double tau = st->tau;
+  const double inv_tau = 1.0 / tau;
   const int mode = st->opt.cg_mode, nfix = st->opt.cg_fixed_n, cgmax = st->opt.cg_max;
   const int tmo = st->opt.barrier_timeout_ms;
   const bool never_release = (st->opt.debug_flags & kDebugBarrierNeverReleases) != 0u;
@@ -309,7 +312,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_cg(DevCsr Q, const double* __rest
     spmv_rows<G>(Q, p, [&](int i, double s, bool lead) {
       if (lead) {
         const double pi = p[i];
-        const double qi = s + pi / tau;
+        const double qi = s + pi * inv_tau;
         q[i] = qi;
         acc = fma(pi, qi, acc);
       }
@@ -323,9 +326,11 @@ __global__ void __launch_bounds__(kBlock, 6) k_cg(DevCsr Q, const double* __rest
     }
     const double alpha = rr / pq;
     acc = 0.0;
+    // x += alpha p, r -= alpha q with a rounded product then a rounded sum,
+    // exactly as the elementwise vector statements of textbook CG.
     for (long long i = t0; i < n; i += nt) {
-      x[i] = fma(alpha, p[i], x[i]);
-      const double ri = fma(-alpha, q[i], r[i]);
+      x[i] = __dadd_rn(x[i], __dmul_rn(alpha, p[i]));
+      const double ri = __dsub_rn(r[i], __dmul_rn(alpha, q[i]));
       r[i] = ri;
       acc = fma(ri, ri, acc);
     }
@@ -337,7 +342,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_cg(DevCsr Q, const double* __rest
     if (stop || rr_new == 0.0) break;
     const double beta = rr_new / rr;
     rr = rr_new;
-    for (long long i = t0; i < n; i += nt) p[i] = fma(beta, p[i], r[i]);
+    for (long long i = t0; i < n; i += nt) p[i] = __dadd_rn(r[i], __dmul_rn(beta, p[i]));
     if (!grid_sync(bar, st, tmo, false)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -365,7 +370,7 @@ __global__ void __launch_bounds__(kBlock) k_dual(DevCsr A, const double* __restr
                                                  double* ax, double* y_avg, const DevState* st) {
   if (!st->iter_active) return;
   const double sigma = st->sigma;
-  const double jf = (double)st->j;
+  const double inv_j = 1.0 / (double)st->j;
   const int m_eq = st->opt.m_eq;
   spmv_rows<G>(A, x, [&](int i, double s, bool lead) {
     if (lead) {
@@ -373,7 +378,7 @@ __global__ void __launch_bounds__(kBlock) k_dual(DevCsr A, const double* __restr
       if (i >= m_eq && yn < 0.0) yn = 0.0;
       y[i] = yn;
       ax[i] = s;
-      y_avg[i] += (yn - y_avg[i]) / jf;
+      y_avg[i] += (yn - y_avg[i]) * inv_j;
     }
   });
 }
@@ -384,11 +389,11 @@ __global__ void __launch_bounds__(kBlock) k_atv(DevCsr At, const double* __restr
                                                 double* aty, const double* __restrict__ x,
                                                 double* x_avg, const DevState* st) {
   if (!st->iter_active) return;
-  const double jf = (double)st->j;
+  const double inv_j = 1.0 / (double)st->j;
   spmv_rows<G>(At, y, [&](int i, double s, bool lead) {
     if (lead) {
       aty[i] = s;
-      x_avg[i] += (x[i] - x_avg[i]) / jf;
+      x_avg[i] += (x[i] - x_avg[i]) * inv_j;
     }
   });
 }
@@ -653,7 +658,8 @@ __global__ void k_pow_start(double* v, int n, const double* __restrict__ c,
 __global__ void k_pow_scale(const double* __restrict__ w, double* v, int n, const double* part,
                             int gp, DevState* st) {
   const double lam = sqrt(block_all_reduce_partials(part, gp));
-  for (long long i = grid_tid(); i < n; i += grid_threads()) v[i] = lam > 0.0 ? w[i] / lam : 0.0;
+  const double inv_lam = lam > 0.0 ? 1.0 / lam : 0.0;
+  for (long long i = grid_tid(); i < n; i += grid_threads()) v[i] = w[i] * inv_lam;
   if (blockIdx.x == 0 && threadIdx.x == 0) st->lam = lam;
 }
 

@@ -46,12 +46,15 @@ void set_error(const char* fmt, ...) {
     if (s_ != QP_OK) return s_;       \
   } while (0)
 
+// Lanes per row.  FP64 arithmetic is the scarce resource on this GPU (the
+// FP64 pipe runs at ~1/58 of FP32), so short rows get one lane each: every
+// DFMA issues with most lanes busy and no shuffle-add tree is needed.  Long
+// rows share lanes so one row does not serialise a warp.
 int group_size_for(int64_t nnz, int64_t rows) {
   const double avg = rows > 0 ? double(nnz) / double(rows) : 0.0;
-  if (avg <= 3.0) return 2;
-  if (avg <= 12.0) return 4;
-  if (avg <= 24.0) return 8;
-  if (avg <= 48.0) return 16;
+  if (avg <= 24.0) return 1;
+  if (avg <= 64.0) return 4;
+  if (avg <= 256.0) return 8;
   return 32;
 }
 
@@ -94,7 +97,6 @@ struct qp_handle {
   // captured chunk graph
   cudaGraphExec_t chunk_exec = nullptr;
   int chunk_iters = 0;
-  bool chunk_timing = false;
   std::vector<cudaEvent_t> ev;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   std::vector<qp_trace_entry> trace;
@@ -136,6 +138,7 @@ qp_status dalloc(qp_handle* h, T** out, size_t count) {
 template <class F>
 qp_status dispatch_g(int G, F&& f) {
   switch (G) {
+    case 1: f(std::integral_constant<int, 1>{}); return QP_OK;
     case 2: f(std::integral_constant<int, 2>{}); return QP_OK;
     case 4: f(std::integral_constant<int, 4>{}); return QP_OK;
     case 8: f(std::integral_constant<int, 8>{}); return QP_OK;
@@ -145,8 +148,8 @@ qp_status dispatch_g(int G, F&& f) {
   }
 }
 
-int blocks_for_rows(int64_t rows, int G, int cap) {
-  const int64_t rows_per_block = int64_t(kBlock / 32) * (32 / G);
+int blocks_for_rows(int64_t rows, int G, int cap, int block = kBlock) {
+  const int64_t rows_per_block = int64_t(block / 32) * (32 / G);
   int64_t g = (rows + rows_per_block - 1) / rows_per_block;
   return int(std::max<int64_t>(1, std::min<int64_t>(g, cap)));
 }
@@ -196,7 +199,7 @@ qp_status launch_cg(qp_handle* h, bool coop) {
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3(h->grid_cg);
-    cfg.blockDim = dim3(kBlock);
+    cfg.blockDim = dim3(kCgBlock);
     cfg.stream = h->stream;
     if (coop) {
       attr[0].id = cudaLaunchAttributeCooperative;
@@ -298,24 +301,18 @@ qp_status check_launch() {
 void destroy_chunk(qp_handle* h) {
   if (h->chunk_exec) cudaGraphExecDestroy(h->chunk_exec);
   h->chunk_exec = nullptr;
-  for (auto e : h->ev) cudaEventDestroy(e);
-  h->ev.clear();
 }
 
 // Capture eval_freq iterations + one evaluation + restart + status copy.
-qp_status capture_chunk(qp_handle* h, int iters, bool timing, bool coop) {
-  destroy_chunk(h);
-  if (timing) {
-    h->ev.resize(size_t(2) * iters);
-    for (auto& e : h->ev) CUDA_TRY(cudaEventCreate(&e));
-  }
-  cudaGraph_t graph = nullptr;
-  CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+// One chunk: `iters` PDHCG iterations, one relKKT evaluation with the restart
+// logic, and the copy of the scalar state to the pinned host mirror.  With
+// `ev` (2*iters events) every CG launch is bracketed by CUDA events.
+qp_status enqueue_chunk(qp_handle* h, int iters, bool coop, cudaEvent_t* ev) {
   qp_status s = QP_OK;
   for (int k = 0; k < iters && s == QP_OK; ++k) {
-    if (timing) cudaEventRecord(h->ev[2 * k], h->stream);
+    if (ev) cudaEventRecord(ev[2 * k], h->stream);
     s = launch_cg(h, coop);
-    if (timing) cudaEventRecord(h->ev[2 * k + 1], h->stream);
+    if (ev) cudaEventRecord(ev[2 * k + 1], h->stream);
     if (s == QP_OK) s = launch_dual(h);
     if (s == QP_OK) s = launch_atv(h);
   }
@@ -323,6 +320,14 @@ qp_status capture_chunk(qp_handle* h, int iters, bool timing, bool coop) {
   if (s == QP_OK) s = launch_restart(h);
   if (s == QP_OK)
     cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream);
+  return s;
+}
+
+qp_status capture_chunk(qp_handle* h, int iters, bool coop) {
+  destroy_chunk(h);
+  cudaGraph_t graph = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  qp_status s = enqueue_chunk(h, iters, coop, nullptr);
   cudaError_t le = cudaGetLastError();
   cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
   if (s != QP_OK) {
@@ -344,20 +349,27 @@ qp_status capture_chunk(qp_handle* h, int iters, bool timing, bool coop) {
     return QP_ERR_CUDA;
   }
   h->chunk_iters = iters;
-  h->chunk_timing = timing;
   return QP_OK;
 }
 
-qp_status ensure_chunk(qp_handle* h, int iters, bool timing) {
-  if (h->chunk_exec && h->chunk_iters == iters && h->chunk_timing == timing) return QP_OK;
+qp_status ensure_chunk(qp_handle* h, int iters) {
+  if (h->chunk_exec && h->chunk_iters == iters) return QP_OK;
   if (h->coop_ok) {
-    qp_status s = capture_chunk(h, iters, timing, true);
+    qp_status s = capture_chunk(h, iters, true);
     if (s == QP_OK) return QP_OK;
     // The grid is sized to be co-resident, so an ordinary launch also
     // satisfies the barrier; record that the cooperative form was refused.
     h->coop_ok = false;
   }
-  return capture_chunk(h, iters, timing, false);
+  return capture_chunk(h, iters, false);
+}
+
+qp_status ensure_events(qp_handle* h, int iters) {
+  if (int(h->ev.size()) >= 2 * iters) return QP_OK;
+  for (auto e : h->ev) cudaEventDestroy(e);
+  h->ev.assign(size_t(2) * iters, nullptr);
+  for (auto& e : h->ev) CUDA_TRY(cudaEventCreate(&e));
+  return QP_OK;
 }
 
 qp_status begin_call(qp_handle* h) {
@@ -518,14 +530,14 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   int occ = 0;
   QP_TRY(dispatch_g(h->Q.G, [&](auto g) {
     constexpr int G = decltype(g)::value;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<G>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<G>, kCgBlock, 0);
   }));
   CUDA_TRY(cudaGetLastError());
   if (occ < 1) {
     set_error("CG kernel cannot be resident");
     return QP_ERR_CUDA;
   }
-  h->grid_cg = std::min(occ * h->num_sms, blocks_for_rows(n, h->Q.G, occ * h->num_sms));
+  h->grid_cg = blocks_for_rows(n, h->Q.G, occ * h->num_sms, kCgBlock);
   const int gmax = std::max({h->grid_n, h->grid_m, h->grid_vec, h->grid_cg});
   QP_TRY(dalloc(h, &h->part_cg, size_t(2) * h->grid_cg));
   QP_TRY(dalloc(h, &h->part_n, size_t(h->grid_n) * kPartStride));
@@ -643,6 +655,7 @@ void qp_destroy(qp_handle* h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   destroy_chunk(h);
+  for (auto e : h->ev) cudaEventDestroy(e);
   for (auto& a : h->allocs) {
     if (h->has_alloc)
       h->ctx.free(a.first, a.second, h->ctx.user, h->ctx.stream);
@@ -670,6 +683,7 @@ qp_status qp_solve(qp_handle* h, const qp_options* o, qp_info* info_out) {
   qp_info info{};
   info.termination = QP_TERM_NONE;
   const bool timing = o->kernel_timing != 0;
+  cudaError_t timing_error = cudaSuccess;
 
   // ---- set-up: options, start point, ||A||_2, step sizes, relKKT(z0)
   QP_TRY(write_options(h, o));
@@ -702,9 +716,17 @@ qp_status qp_solve(qp_handle* h, const qp_options* o, qp_info* info_out) {
 
   // ---- chunks of eval_freq iterations, one relKKT evaluation each
   if (status == QP_OK && term < 0) {
-    QP_TRY(ensure_chunk(h, o->eval_freq, timing));
+    // Graph replay normally; with kernel_timing the same chunk is launched
+    // directly so that events can bracket each CG launch on its stream.
+    if (timing) QP_TRY(ensure_events(h, o->eval_freq));
+    else QP_TRY(ensure_chunk(h, o->eval_freq));
     while (true) {
-      CUDA_TRY(cudaGraphLaunch(h->chunk_exec, h->stream));
+      if (timing) {
+        QP_TRY(enqueue_chunk(h, o->eval_freq, h->coop_ok, h->ev.data()));
+        QP_TRY(check_launch());
+      } else {
+        CUDA_TRY(cudaGraphLaunch(h->chunk_exec, h->stream));
+      }
       QP_TRY(sync(h));
       const DevState& s = *h->h_st;
       qp_trace_entry te{};
@@ -716,11 +738,13 @@ qp_status qp_solve(qp_handle* h, const qp_options* o, qp_info* info_out) {
       te.cg_last = int32_t(s.last_cg);
       h->trace.push_back(te);
       if (timing) {
-        for (int k = 0; k < h->chunk_iters; ++k) {
+        for (int k = 0; k < o->eval_freq; ++k) {
           float ms = 0.f;
-          if (cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]) == cudaSuccess &&
-              ms > 0.0f) {
+          const cudaError_t te = cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]);
+          if (te == cudaSuccess) {
             info.cg_kernel_ms += ms;
+          } else if (timing_error == cudaSuccess) {
+            timing_error = te;
           }
         }
         cudaGetLastError();
@@ -745,6 +769,9 @@ qp_status qp_solve(qp_handle* h, const qp_options* o, qp_info* info_out) {
   fill_info_from_state(h, &info);
   info.termination = term;
   info.device_error = h->h_st->err;
+  if (timing && timing_error != cudaSuccess) {
+    info.cg_kernel_ms = -double(int(timing_error));  // timing unavailable: negative error code
+  }
   if (timing) {
     // launches that did work, and the Q products inside them
     info.cg_kernel_launches = h->h_st->k_total;
