@@ -43,6 +43,12 @@ path implements the same one):
   iterations on A'A from the normalised all-ones vector.  If ||A||_2 is not
   above eps_zero (no coupling), ||A||_2 is replaced by eps_zero.
 * omega_0 = ||c||_2 / ||b||_2 when both exceed eps_zero, else 1; x0 = y0 = 0.
+
+Parity unpinned: ``restart_test`` (the exact restart decisions), the
+primal-weight formula inside ``restart_to`` and the omega_0 rule of
+``initial_state`` have no value in the paper to be pinned against; the
+solver's end results with them enabled are pinned by the closed-form and
+brute-force tests.  Every other function is pinned (tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 
