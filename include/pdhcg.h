@@ -237,6 +237,44 @@ qp_status qp_evaluate(qp_handle* h, double kkt_cur[6], double kkt_avg[6]);
 /* Estimate ||A||_2 by `iters` power iterations on A'A from ones/sqrt(n). */
 qp_status qp_norm_A(qp_handle* h, int32_t iters, double* out);
 
+/* ------------------------------------------------- allocation-free variant */
+
+/* Capacity, in doubles, of the static device scratch of qp_norm_A_static (8 MiB). */
+#define QP_NORM_A_STATIC_MAX_DOUBLES (1u << 20)
+
+/*
+ * The paper has no counterpart of this entry point; it serves callers that
+ * cannot allocate device memory at all - a control loop held to a device
+ * memory budget fixed at start-up, code running while another framework
+ * owns every byte of device memory, or code that must not risk the
+ * device-wide synchronisation an allocation can cause.
+ *
+ * Computes the same estimate as qp_norm_A: `iters` power iterations on A'A
+ * from ones/sqrt(n), writing ||A||_2 to norm_out (device pointer, one
+ * double) in stream order on `stream` (cudaStream_t; NULL = legacy default
+ * stream).  It calls no cudaMalloc, cudaFree or other allocating routine:
+ * its work vectors live in one static __device__ array of
+ * QP_NORM_A_STATIC_MAX_DOUBLES doubles that every GPU loading this library
+ * holds until the process exits.
+ *
+ * Inputs are device arrays the caller owns: A (m x n CSR, nnz entries) and
+ * its transpose At (n x m CSR), both valid as qp_csr_validate would check
+ * (not re-checked here); nnz only selects lanes per row.  Sizes with
+ * 2n + m > QP_NORM_A_STATIC_MAX_DOUBLES - 1185 are rejected with
+ * QP_ERR_INVALID_ARG and a message in qp_last_error.
+ *
+ * The first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents; every value a call reads is written earlier by
+ * the same call.  Calls whose work overlaps on the GPU (other streams,
+ * other threads) race on the array: serialise them.
+ */
+qp_status qp_norm_A_static(int32_t m, int32_t n, int64_t nnz, const int32_t* A_rowptr,
+                           const int32_t* A_col, const double* A_val, const int32_t* At_rowptr,
+                           const int32_t* At_col, const double* At_val, int32_t iters,
+                           double* norm_out, void* stream);
+
 /* ------------------------------------------------- host-only helpers (no GPU) */
 
 /*

@@ -19,6 +19,7 @@ CG_ADAPTIVE, CG_FIXED = 0, 1
 RESTART_ADAPTIVE, RESTART_NONE = 0, 2
 CREATE_CHECK_SYMMETRY = 1
 DEBUG_BARRIER_NEVER_RELEASES = 1
+QP_NORM_A_STATIC_MAX_DOUBLES = 1 << 20  # capacity of qp_norm_A_static's static scratch
 
 
 class QPOptionsC(Structure):
@@ -98,6 +99,8 @@ SIGNATURES = [
     ("qp_iterate", c_int32, [_H, POINTER(QPOptionsC), c_int64]),
     ("qp_evaluate", c_int32, [_H, _F64P, _F64P]),
     ("qp_norm_A", c_int32, [_H, c_int32, _F64P]),
+    ("qp_norm_A_static", c_int32, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p,
+                                   c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     ("qp_csr_validate", c_int32, [c_int32, c_int32, _I32P, _I32P, _F64P]),
     ("qp_csr_transpose", c_int32, [c_int32, c_int32, _I32P, _I32P, _F64P, _I32P, _I32P, _F64P]),
 ]

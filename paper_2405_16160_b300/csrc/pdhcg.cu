@@ -70,6 +70,10 @@ struct DevMat {
 
 }  // namespace
 
+// Lets other translation units of this library report a message through
+// qp_last_error.
+void pdhcg_set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 struct qp_handle {
   int device = 0;
   cudaStream_t stream = nullptr;  // the handle's own stream (capturable)
