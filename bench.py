@@ -31,9 +31,9 @@ sys.path.insert(0, ROOT)
 WORKLOAD = {"workload": "large sparse QP: n=1e6, m=5e5, Q = diag U[0.5,2] + mirrored N(0,0.1) "
                         "(~9 nnz/row, diagonally dominant), A 10 uniform N(0,1) nnz/row, "
                         "c ~ N(0,1), b = A x0 + U[0,1]",
-            "n": 1_000_000, "m": 500_000, "seed": 0, "tol": 1e-4, "precision": "fp64",
+            "n": 1_000_000, "m": 500_000, "seed": 0, "tol": 1e-4, "precision": "mixed",
             "l2": "inputs larger than L2 (~470 MB resident working set vs 126 MB L2)"}
-METRIC = "time to 1e-4 rel. KKT (restarted PDHCG, FP64)"
+METRIC = "time to 1e-4 rel. KKT (restarted PDHCG; FP32 data/iterates, FP64 reductions) vs plain FP64 GPU PDHCG"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "sparse_dd_n1000000_m500000_seed0_trace.json")
 
 
@@ -125,19 +125,19 @@ def _peaks():
         return 6400.0, "fallback"
 
 
-def cg_kernel_bytes(nnz_q: int, n: int, launches: int, spmvs: int, cg_steps: int) -> float:
-    """Algorithmic DRAM bytes of the CG kernel (each array touched once per phase).
+def cg_kernel_bytes(nnz_q: int, n: int, launches: int, spmvs: int, cg_steps: int,
+                    w: int) -> float:
+    """Algorithmic DRAM bytes of the CG kernel, each array counted once per phase.
 
-    Q product (per SpMV): 12 B/nnz (FP64 value + int32 column) + 4 B/row
-    (row pointer) + 8 B/row gathered vector + 8 B/row written result.
-    Phase 0 adds reads of c, A'y (16 B/row) and the write of p (8 B/row).
-    Phase B (per step) reads x, p, q, r and writes x, r: 48 B/row.
-    Phase C (per continued step) reads r, p and writes p: 24 B/row.
+    w = bytes per value (8 FP64, 4 FP32); indices are int32.
+    Q product (per CG step): (w + 4) B/nnz (value + column) + 4 B/row (row
+    pointer) + w B/row gathered p + w B/row written q.
+    Phase B (per step): reads x, p, q, r, qx and writes x, r, qx: 8w B/row.
+    Phase C (per continued step): reads r, p and writes p: 3w B/row.
+    r0 is formed by the A' kernel of the previous iteration, not here.
     """
-    spmv = 12.0 * nnz_q + 20.0 * n
-    phase0_extra = 24.0 * n
-    return (spmvs * spmv + launches * phase0_extra + cg_steps * 48.0 * n
-            + max(cg_steps - launches, 0) * 24.0 * n)
+    spmv = (w + 4.0) * nnz_q + (4.0 + 2.0 * w) * n
+    return spmvs * spmv + cg_steps * 8.0 * w * n + max(cg_steps - launches, 0) * 3.0 * w * n
 
 
 def oracle_sample(inst, iters: int):
@@ -192,8 +192,22 @@ def run_reference(args):
     return 0
 
 
+def _timed_solves(solver, steps, stream, **opts):
+    import torch
+    infos, times = [], []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = solver.solve(**opts)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        infos.append(info)
+    return infos, times
+
+
 def run_ours(args):
-    import numpy as np
     import torch
 
     ws, rank = _dist()
@@ -202,6 +216,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
+    from paper_2405_16160_b300 import _lib as L
     from paper_2405_16160_b300 import build as B
     from paper_2405_16160_b300 import workloads as W
     from paper_2405_16160_b300.solver import QPSolver
@@ -210,30 +225,29 @@ def run_ours(args):
     inst = W.sparse_dd(WORKLOAD["seed"] + rank, n=WORKLOAD["n"], m=WORKLOAD["m"])
     tol = WORKLOAD["tol"]
     stream = torch.cuda.current_stream()
+    mixed = dict(tol=tol, precision=L.PREC_MIXED)
+    fp64 = dict(tol=tol, precision=L.PREC_FP64)
 
-    # ---- device-resident solves (value)
+    # ---- device-resident solves (value): mixed precision, CUDA-graph replay
     solver = QPSolver(inst)
     for _ in range(args.warmup):
-        solver.solve(tol=tol, kernel_timing=1)
+        solver.solve(**mixed)
+    solver.solve(**fp64)
     torch.cuda.synchronize()
-    infos, times = [], []
     with ClockSampler(local) as clocks:
         _barrier(ws)
         torch.cuda.synchronize()
-        for _ in range(args.steps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            info = solver.solve(tol=tol, kernel_timing=1)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1) / 1e3)
-            infos.append(info)
+        infos, times = _timed_solves(solver, args.steps, stream, **mixed)
         torch.cuda.synchronize()
         _barrier(ws)
     trace_len = len(solver.trace())
+    # the same solve in plain FP64 (the ratio the metric asks for)
+    infos64, times64 = _timed_solves(solver, max(1, args.steps // 2), stream, **fp64)
+    # the dominant kernel, timed launch by launch with CUDA events on its stream
+    kinfos, _ = _timed_solves(solver, max(1, args.steps // 2), stream, kernel_timing=1, **mixed)
     solver.close()
     per_solve = _max_over_ranks(statistics.mean(times), ws)
+    per_solve64 = _max_over_ranks(statistics.mean(times64), ws)
 
     # ---- end to end through the C ABI from host arrays
     e2e_times = []
@@ -246,7 +260,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with QPSolver(inst) as s2:
-            s2.solve(tol=tol)
+            s2.solve(**mixed)
             x, y = s2.solution()
         torch.cuda.synchronize()
         if s > 0:
@@ -258,18 +272,18 @@ def run_ours(args):
     info = infos[-1]
     peak, peak_kind = _peaks()
     bytes_total = sum(cg_kernel_bytes(inst.nnz_Q, inst.n, i["cg_kernel_launches"],
-                                      i["cg_kernel_spmvs"], i["cg_steps"]) for i in infos)
-    launches = sum(i["cg_kernel_launches"] for i in infos)
-    kernel_s = sum(i["cg_kernel_ms"] for i in infos) / 1e3
+                                      i["cg_kernel_spmvs"], i["cg_steps"], 4) for i in kinfos)
+    launches = sum(i["cg_kernel_launches"] for i in kinfos)
+    kernel_s = sum(i["cg_kernel_ms"] for i in kinfos) / 1e3
     achieved = bytes_total / kernel_s / 1e9 if kernel_s > 0 else None
     traffic = None
     prof = os.path.join(ROOT, "profiles", "k_cg_traffic.json")
     if os.path.exists(prof):
         with open(prof) as f:
             traffic = json.load(f).get("dram_bytes_per_launch_full_size")
-    setup_launches = 1 + 2 + 1 + 3 * 30 + 1 + 4
-    chunk_launches = 3 * 64 + 4 + 3
-    gpu_launches = args.steps * (setup_launches + trace_len * chunk_launches)
+    setup_launches = 1 + 4 + 1 + 3 * 30 + 1 + 4
+    chunk_launches = 3 * 64 + 4 + 3 + 1
+    gpu_launches = args.steps * (setup_launches + 9 + trace_len * chunk_launches)
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -282,18 +296,24 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": per_solve, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 reductions and scalars)",
+        "data": "synthetic",
         "config": dict(WORKLOAD, iterations=info["iterations"], cg_steps=info["cg_steps"],
-                       restarts=info["restarts"], relkkt=info["relkkt"],
+                       restarts=info["restarts"], relkkt_fp64_check=info["check_relkkt"],
+                       refine_iterations=info["refine_iterations"],
+                       fp64_time_s=per_solve64, fp64_iterations=infos64[-1]["iterations"],
+                       speedup_vs_fp64=per_solve64 / per_solve,
                        parallelism=f"replicas x{ws}"),
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "roofline": {"kernel": "k_cg (persistent CG: Q SpMVs + vector phases)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"kernel": "k_cg<float> (persistent CG: Q SpMV + vector phases)",
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_total / max(launches, 1),
-                     "avg_launch_us": kernel_s / max(launches, 1) * 1e6},
+                     "avg_launch_us": kernel_s / max(launches, 1) * 1e6,
+                     "timing": "CUDA events around every k_cg launch (direct launches) in "
+                               "solves run right after the timed region"},
         "cpu_baseline": cpu,
         "gpu_launches": gpu_launches,
         "clocks": clocks.summary(),

@@ -51,6 +51,14 @@ typedef enum {
 } qp_termination;
 
 enum { QP_CG_ADAPTIVE = 0, QP_CG_FIXED = 1 };
+/* Arithmetic of the iteration.  FP64: everything in IEEE binary64.  MIXED:
+ * matrix values, iterates and SpMV arithmetic in binary32; dot products
+ * accumulated from exact binary32 products in double-float and combined in
+ * binary64; every scalar of the method (step sizes, primal weight, CG
+ * coefficients, relKKT, restart tests) in binary64.  A mixed solve ends by
+ * re-evaluating its result with the binary64 data (qp_info.check_relkkt)
+ * and, if refine is set and that misses tol, continuing in FP64. */
+enum { QP_PREC_FP64 = 0, QP_PREC_MIXED = 1 };
 enum { QP_RESTART_ADAPTIVE = 0, QP_RESTART_NONE = 2 };
 
 /* qp_create flags */
@@ -100,7 +108,9 @@ typedef struct {
   double eta;                 /* > 0 overrides eta = 1/(2||A||_2) */
   int32_t kernel_timing;      /* 1: time every CG-kernel launch with CUDA events */
   uint32_t debug_flags;       /* QP_DEBUG_* fault injection, 0 by default */
-  int64_t reserved[8];
+  int32_t precision;          /* QP_PREC_FP64 (default) or QP_PREC_MIXED */
+  int32_t refine;             /* mixed: continue in FP64 if the FP64 check misses tol; default 1 */
+  int64_t reserved[7];
 } qp_options;
 
 /* Result of a solve (also returned by qp_get_stats). */
@@ -121,6 +131,12 @@ typedef struct {
   int64_t cg_kernel_spmvs;    /* kernel_timing: Q products inside those launches */
   int32_t device_error;       /* nonzero: a bounded device wait gave up */
   int32_t cooperative;        /* 1: the CG kernel ran as a cooperative launch */
+  int32_t precision;          /* QP_PREC_* the solve started in */
+  int32_t pad0;
+  int64_t mixed_iterations;   /* mixed: iterations done in the binary32 phase */
+  int64_t refine_iterations;  /* mixed: iterations of the FP64 refinement phase */
+  double mixed_relkkt;        /* mixed: relKKT at the end of the binary32 phase */
+  double check_relkkt;        /* mixed: relKKT of that iterate with the binary64 data */
 } qp_info;
 
 /* Scalar part of the iteration state (for checkpoint / resume and parity). */
@@ -222,8 +238,9 @@ qp_status qp_set_state(qp_handle* h, const qp_state_vectors* v, const qp_state_s
 /*
  * Run exactly `iters` inner PDHCG iterations (Algorithm 1 loop body: CG
  * primal step, projected dual step, averages) from the current state, with
- * no relKKT evaluation, restart or termination test.  Only o's CG settings
- * and its debug_flags are used.
+ * no relKKT evaluation, restart or termination test.  Only o's CG settings,
+ * precision and debug_flags are used.  qp_set_state fills both precisions;
+ * qp_get_state and qp_evaluate then read the precision last iterated.
  */
 qp_status qp_iterate(qp_handle* h, const qp_options* o, int64_t iters);
 

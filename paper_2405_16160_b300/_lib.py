@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "QP_OK", 1: "QP_ERR_INVALID_ARG", 2: "QP_ERR_OOM", 3: "QP_ERR
                 4: "QP_ERR_NOT_SOLVED", 5: "QP_ERR_DEVICE_TIMEOUT", 6: "QP_ERR_NO_DEVICE"}
 TERM_NONE, TERM_SOLVED, TERM_ITER_LIMIT, TERM_TIME_LIMIT, TERM_NUMERICAL = -1, 0, 1, 2, 3
 CG_ADAPTIVE, CG_FIXED = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
 RESTART_ADAPTIVE, RESTART_NONE = 0, 2
 CREATE_CHECK_SYMMETRY = 1
 DEBUG_BARRIER_NEVER_RELEASES = 1
@@ -30,7 +31,8 @@ class QPOptionsC(Structure):
         ("beta_suff", c_double), ("beta_nec", c_double), ("beta_art", c_double),
         ("theta_pw", c_double), ("eps_zero", c_double), ("primal_weight_update", c_int32),
         ("warm_start", c_int32), ("omega0", c_double), ("eta", c_double),
-        ("kernel_timing", c_int32), ("debug_flags", c_uint32), ("reserved", c_int64 * 8),
+        ("kernel_timing", c_int32), ("debug_flags", c_uint32), ("precision", c_int32),
+        ("refine", c_int32), ("reserved", c_int64 * 7),
     ]
 
 
@@ -43,6 +45,8 @@ class QPInfoC(Structure):
         ("omega", c_double), ("tau", c_double), ("sigma", c_double), ("setup_ms", c_double),
         ("solve_ms", c_double), ("cg_kernel_ms", c_double), ("cg_kernel_launches", c_int64),
         ("cg_kernel_spmvs", c_int64), ("device_error", c_int32), ("cooperative", c_int32),
+        ("precision", c_int32), ("pad0", c_int32), ("mixed_iterations", c_int64),
+        ("refine_iterations", c_int64), ("mixed_relkkt", c_double), ("check_relkkt", c_double),
     ]
 
     def as_dict(self) -> dict:

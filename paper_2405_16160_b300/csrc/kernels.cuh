@@ -3,7 +3,7 @@
 // One PDHCG iteration (Algorithm 1 loop body) is three launches:
 //   k_cg    cooperative, persistent: the whole inexact CG solve of
 //           (Q + I/tau) x = x/tau - c - A'y (Section 2), grid barriers between
-//           the SpMV and the vector phases, deterministic FP64 reductions;
+//           the SpMV and the vector phases;
 //   k_dual  A x+ fused with the projected dual step, the A x cache and the
 //           running average of y (Algorithm 1, y-update and averages);
 //   k_atv   A' y+ (explicit transpose) fused with the running average of x.
@@ -11,6 +11,16 @@
 // of Section 4 for the current iterate and the average), k_control (one warp:
 // termination and the restart tests), k_restart_n / k_restart_m /
 // k_restart_finish (restart to the candidate and the primal-weight update).
+//
+// Every vector kernel is templated on the value type T:
+//   T = double  the FP64 path (the parity reference on the GPU);
+//   T = float   the mixed path: FP32 matrix values, iterates and SpMV
+//               arithmetic.  Dot products use exact FP32 products and
+//               compensated (double-float) sums up to the block, and FP64
+//               across blocks; every scalar of the method (alpha, beta, tau,
+//               sigma, omega, eps, relKKT, restart tests) is FP64.
+// This GPU's FP64 pipe runs at ~1/58 of FP32, so the mixed path keeps FP64
+// instructions out of the per-element work entirely.
 //
 // Reductions never use floating-point atomics: each block writes partials,
 // and every consumer reduces them in one fixed order, so results do not
@@ -43,10 +53,11 @@ constexpr unsigned kDebugBarrierNeverReleases = 1u;
 constexpr unsigned kKktNMaxMask = 0b10011100111u;  // 11 entries, see k_kkt_n
 constexpr unsigned kKktMMaxMask = 0b1011011u;      // 7 entries, see k_kkt_m
 
-struct DevCsr {
+template <class T>
+struct CsrT {
   const int32_t* rowptr;
   const int32_t* col;
-  const double* val;
+  const T* val;
   int32_t rows;
 };
 
@@ -92,45 +103,140 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 __device__ __forceinline__ bool running(const DevState* st) { return st->done == 0 && st->err == 0; }
 
+__device__ __forceinline__ long long grid_tid() {
+  return (long long)blockIdx.x * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ long long grid_threads() { return (long long)gridDim.x * blockDim.x; }
+
+// Correctly rounded, never-contracted arithmetic for both value types.
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+template <class T>
+__device__ __forceinline__ T shfl_xor(T v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o);
+}
+
+// Dot-product accumulators.  AccD: plain FP64.  AccF: an exact FP32 product
+// (two-product via FMA) added into a double-float pair (two-sum), i.e. about
+// 48 significant bits without touching the FP64 pipe.
+struct AccD {
+  double s = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ void merge_shfl(int o) { s += shfl_xor(s, o); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+struct AccF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add2(float a, float ae) {
+    const float s = __fadd_rn(hi, a);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(a, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, ae));
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    add2(p, fmaf(a, b, -p));
+  }
+  __device__ __forceinline__ void merge_shfl(int o) {
+    const float h = shfl_xor(hi, o), l = shfl_xor(lo, o);
+    add2(h, l);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <class T>
+struct Acc;
+template <>
+struct Acc<double> {
+  using type = AccD;
+};
+template <>
+struct Acc<float> {
+  using type = AccF;
+};
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
   return v;
 }
 
-__device__ __forceinline__ double warp_max(double v) {
+template <class T>
+__device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, shfl_xor(v, o));
   return v;
 }
 
-// Block reduction of K per-thread values; bit k of max_mask selects max
-// (of non-negative values) instead of sum.  Thread 0 writes out[0..K).
-template <int K>
-__device__ __forceinline__ void block_reduce_store(double (&v)[K], unsigned max_mask, double* out) {
-  __shared__ double sh[K][32];
+template <class A>
+__device__ __forceinline__ void warp_merge(A& a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a.merge_shfl(o);
+}
+
+// Block reduction of KM maxima (of non-negative values, in T) and KS sums
+// (accumulators); thread 0 writes out[0..KM) = maxima, out[KM..KM+KS) = sums,
+// as doubles.  Only one value per warp is ever widened to FP64.
+template <int KM, int KS, class T, class A>
+__device__ __forceinline__ void block_reduce_ms(const T* mx, A* sm, double* out) {
+  __shared__ double sh[(KM + KS) > 0 ? KM + KS : 1][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const double x = ((max_mask >> k) & 1u) ? warp_max(v[k]) : warp_sum(v[k]);
-    if (lane == 0) sh[k][wid] = x;
+  for (int k = 0; k < KM; ++k) {
+    const T v = warp_max(mx[k]);
+    if (lane == 0) sh[k][wid] = (double)v;
+  }
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    warp_merge(sm[k]);
+    if (lane == 0) sh[KM + k][wid] = sm[k].value();
   }
   __syncthreads();
   if (wid == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < KM + KS; ++k) {
       double x = lane < nwarps ? sh[k][lane] : 0.0;
-      x = ((max_mask >> k) & 1u) ? warp_max(x) : warp_sum(x);
+      x = k < KM ? warp_max(x) : warp_sum(x);
       if (lane == 0) out[k] = x;
     }
   }
   __syncthreads();
 }
 
-__device__ __forceinline__ void block_sum_store(double v, double* out) {
-  double a[1] = {v};
-  block_reduce_store<1>(a, 0u, out);
+template <class A>
+__device__ __forceinline__ void block_sum_store(A a, double* out) {
+  block_reduce_ms<0, 1, double, A>(nullptr, &a, out);
+}
+
+// Per-block partial of a dot product inside the persistent CG kernel.  FP64:
+// the double sum.  FP32: the double-float pair stored in the same 8 bytes, so
+// the grid-wide combine also stays on the FP32 pipe.
+__device__ __forceinline__ void block_dot_store(AccD a, double* out) { block_sum_store(a, out); }
+
+__device__ __forceinline__ void block_dot_store(AccF a, double* out) {
+  __shared__ float2 sh[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  warp_merge(a);
+  if (lane == 0) sh[wid] = make_float2(a.hi, a.lo);
+  __syncthreads();
+  if (wid == 0) {
+    AccF b;
+    if (lane < int(blockDim.x >> 5)) {
+      b.hi = sh[lane].x;
+      b.lo = sh[lane].y;
+    }
+    warp_merge(b);
+    if (lane == 0) *reinterpret_cast<float2*>(out) = make_float2(b.hi, b.lo);
+  }
+  __syncthreads();
 }
 
 // Fixed-order reduction of n block partials (stride apart) by one warp; every
@@ -146,11 +252,26 @@ __device__ __forceinline__ double warp_reduce_partials(const double* p, int n, i
   return is_max ? warp_max(x) : warp_sum(x);
 }
 
-// The same value broadcast to every thread of the block.
-__device__ __forceinline__ double block_all_reduce_partials(const double* p, int n) {
+__device__ __forceinline__ double warp_reduce_dot_partials(const double* p, int n, AccD) {
+  return warp_reduce_partials(p, n, 1, false);
+}
+
+__device__ __forceinline__ double warp_reduce_dot_partials(const double* p, int n, AccF) {
+  AccF a;
+  for (int i = threadIdx.x & 31; i < n; i += 32) {
+    const float2 f = __ldcg(reinterpret_cast<const float2*>(p) + i);
+    a.add2(f.x, f.y);
+  }
+  warp_merge(a);
+  return a.value();
+}
+
+// The total of block_dot_store partials, broadcast to every thread of the block.
+template <class A>
+__device__ __forceinline__ double block_all_reduce(const double* p, int n) {
   __shared__ double s_val;
   if (threadIdx.x < 32) {
-    const double v = warp_reduce_partials(p, n, 1, false);
+    const double v = warp_reduce_dot_partials(p, n, A());
     if (threadIdx.x == 0) s_val = v;
   }
   __syncthreads();
@@ -183,7 +304,10 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int ti
       const unsigned long long limit = (unsigned long long)timeout_ms * 1000000ull;
       unsigned int polls = 0;
       while (gen.load(cuda::memory_order_acquire) == g) {
-        if (err.load(cuda::memory_order_relaxed) != 0) { ok = 0; break; }
+        if (err.load(cuda::memory_order_relaxed) != 0) {
+          ok = 0;
+          break;
+        }
         if ((++polls & 255u) == 0u) {
           if (global_ns() - t0 > limit || polls > (1u << 27)) {
             err.fetch_or(kErrBarrierTimeout, cuda::memory_order_relaxed);
@@ -201,78 +325,114 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int ti
   return s_ok != 0;
 }
 
-// Row-group CSR SpMV: G lanes share a row (G in {1,2,4,8,16,32}), all 32 lanes
-// of a warp walk the same number of row blocks so the group shuffles never
-// diverge.  Each lane accumulates its strided share of the row in FP64 and
-// the group reduces with xor shuffles, so a row's sum does not depend on the
-// launch configuration.  f(i, sum, leader) is called by every lane of the
-// group; `leader` is lane 0 of the group.
-template <int G, class F>
-__device__ __forceinline__ void spmv_rows(const DevCsr& M, const double* v, F&& f) {
+// Row-group CSR SpMV: G lanes share a row (G in {1,2,4,8,16,32}); all 32 lanes
+// of a warp walk the same number of row blocks, so the group shuffles never
+// diverge.  Each lane takes the entries k, k+G, k+2G, ... of its row, four per
+// trip: the four column and value loads are issued first, then the four
+// gathers, then the four FMAs in entry order (slots past the row end add an
+// exact zero), so memory latency is paid once per four entries while the sum
+// is the plain strided one.  The group reduces with xor shuffles, so a row's
+// sum does not depend on the launch configuration.  f(i, sum, leader) is
+// called by every lane of the group; `leader` is lane 0 of the group.
+constexpr int kUnroll = 4;
+
+template <int G, class T>
+__device__ __forceinline__ T row_dot(const CsrT<T>& M, const T* v, int i, int sub) {
+  T s = T(0);
+  const int e = __ldg(M.rowptr + i + 1);
+  for (int k = __ldg(M.rowptr + i) + sub; k < e; k += kUnroll * G) {
+    int c[kUnroll];
+    T a[kUnroll], xv[kUnroll];
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) {
+      const int kk = k + j * G;
+      c[j] = kk < e ? __ldg(M.col + kk) : -1;
+      a[j] = kk < e ? __ldg(M.val + kk) : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) xv[j] = c[j] >= 0 ? v[c[j]] : T(0);
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) s = fma(a[j], xv[j], s);
+  }
+  return s;
+}
+
+template <int G, class T, class F>
+__device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f) {
   constexpr int kRowsPerWarp = 32 / G;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (G - 1);
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long gw = grid_tid() >> 5;
+  const long long nw = grid_threads() >> 5;
   for (long long base = gw * kRowsPerWarp; base < M.rows; base += nw * kRowsPerWarp) {
     const int i = int(base) + lane / G;
-    double s = 0.0;
-    if (i < M.rows) {
-      const int e = __ldg(M.rowptr + i + 1);
-      for (int k = __ldg(M.rowptr + i) + sub; k < e; k += G)
-        s = fma(__ldg(M.val + k), v[__ldg(M.col + k)], s);
-    }
+    T s = i < M.rows ? row_dot<G>(M, v, i, sub) : T(0);
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    for (int o = G / 2; o > 0; o >>= 1) s += shfl_xor(s, o);
     if (i < M.rows) f(i, s, sub == 0);
   }
 }
 
 // Same walk, two vectors through one pass over the matrix row.
-template <int G, class F>
-__device__ __forceinline__ void spmv2_rows(const DevCsr& M, const double* v1, const double* v2,
-                                           F&& f) {
+template <int G, class T, class F>
+__device__ __forceinline__ void spmv2_rows(const CsrT<T>& M, const T* v1, const T* v2, F&& f) {
   constexpr int kRowsPerWarp = 32 / G;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (G - 1);
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long gw = grid_tid() >> 5;
+  const long long nw = grid_threads() >> 5;
   for (long long base = gw * kRowsPerWarp; base < M.rows; base += nw * kRowsPerWarp) {
     const int i = int(base) + lane / G;
-    double s1 = 0.0, s2 = 0.0;
+    T s1 = T(0), s2 = T(0);
     if (i < M.rows) {
       const int e = __ldg(M.rowptr + i + 1);
-      for (int k = __ldg(M.rowptr + i) + sub; k < e; k += G) {
-        const double a = __ldg(M.val + k);
-        const int cj = __ldg(M.col + k);
-        s1 = fma(a, v1[cj], s1);
-        s2 = fma(a, v2[cj], s2);
+      for (int k = __ldg(M.rowptr + i) + sub; k < e; k += kUnroll * G) {
+        int c[kUnroll];
+        T a[kUnroll], x1[kUnroll], x2[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j) {
+          const int kk = k + j * G;
+          c[j] = kk < e ? __ldg(M.col + kk) : -1;
+          a[j] = kk < e ? __ldg(M.val + kk) : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j) {
+          x1[j] = c[j] >= 0 ? v1[c[j]] : T(0);
+          x2[j] = c[j] >= 0 ? v2[c[j]] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j) {
+          s1 = fma(a[j], x1[j], s1);
+          s2 = fma(a[j], x2[j], s2);
+        }
       }
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      s1 += shfl_xor(s1, o);
+      s2 += shfl_xor(s2, o);
     }
     if (i < M.rows) f(i, s1, s2, sub == 0);
   }
 }
 
-__device__ __forceinline__ long long grid_tid() {
-  return (long long)blockIdx.x * blockDim.x + threadIdx.x;
-}
-__device__ __forceinline__ long long grid_threads() { return (long long)gridDim.x * blockDim.x; }
-
 // ------------------------------------------------------------- CG (Section 2)
-// Inexact CG on (Q + I/tau) x = x^k/tau - c - A'y^k warm-started at x^k.  The
-// initial residual simplifies to r0 = -(Q x^k + c + A'y^k).  Phases per CG
-// step: [A] q = Qp + p/tau, p'q  | [B] x += a p, r -= a q, r'r  | [C] p = r + b p.
-// part holds 2 * gridDim.x doubles.
-template <int G>
-__global__ void __launch_bounds__(kCgBlock, 3) k_cg(DevCsr Q, const double* __restrict__ c,
-                                               const double* __restrict__ aty, double* x,
-                                               double* r, double* p, double* q, double* part,
-                                               DevState* st, GridBarrier* bar, int n) {
+// Inexact CG on (Q + I/tau) x = x^k/tau - c - A'y^k warm-started at x^k.  Its
+// initial residual simplifies to r0 = -(Q x^k + c + A'y^k); the kernel that
+// produces A'y^k (k_atv, or k_prepare after a set-up, evaluation or restart)
+// also forms r0 = p0 and the block partials of r0'r0 (part_r0, g0 blocks),
+// from a tracked qx = Q x.  Phases per CG step:
+//   [A] q = Qp + p/tau, p'q
+//   [B] x += a p, qx += a (q - p/tau), r -= a q, r'r
+//   [C] p = r + b p   (only when CG continues)
+// so each step costs one product with Q.  alpha, beta, the stop test and all
+// dot products are FP64-accurate for both value types.  part holds
+// 2 * gridDim.x doubles.
+template <int G, class T>
+__global__ void __launch_bounds__(kCgBlock, 3) k_cg(CsrT<T> Q, T* x, T* r, T* p, T* q, T* qx,
+                                                    const double* part_r0, int g0, double* part,
+                                                    DevState* st, GridBarrier* bar, int n) {
+  using A = typename Acc<T>::type;
   const bool active = running(st) && st->k_total < st->opt.max_iter;
   if (!active) {
     if (blockIdx.x == 0 && threadIdx.x == 0) st->iter_active = 0;
@@ -281,68 +441,60 @@ __global__ void __launch_bounds__(kCgBlock, 3) k_cg(DevCsr Q, const double* __re
   // Every read of st happens before the first barrier; block 0 writes the
   // counters only after the last one.
   const double tau = st->tau;
-  const double inv_tau = 1.0 / tau;
+  const T inv_tau = T(1.0 / tau);
   const int mode = st->opt.cg_mode, nfix = st->opt.cg_fixed_n, cgmax = st->opt.cg_max;
   const int tmo = st->opt.barrier_timeout_ms;
-  const bool never_release = (st->opt.debug_flags & kDebugBarrierNeverReleases) != 0u;
+  bool never_release = (st->opt.debug_flags & kDebugBarrierNeverReleases) != 0u;
   const double eps =
       mode == kCgAdaptive ? st->eps + st->opt.cg_eps_factor * st->relkkt_last : st->eps;
   double* part_rr = part;
   double* part_pq = part + gridDim.x;
   const long long t0 = grid_tid(), nt = grid_threads();
-
-  double acc = 0.0;
-  spmv_rows<G>(Q, x, [&](int i, double s, bool lead) {
-    if (lead) {
-      const double ri = -(s + c[i] + aty[i]);
-      r[i] = ri;
-      p[i] = ri;
-      acc = fma(ri, ri, acc);
-    }
-  });
-  block_sum_store(acc, part_rr + blockIdx.x);
-  if (!grid_sync(bar, st, tmo, never_release)) return;
-  double rr = block_all_reduce_partials(part_rr, gridDim.x);
+  double rr = block_all_reduce<A>(part_r0, g0);
 
   int steps = 0;
   bool numerr = false;
   const bool skip = (mode == kCgFixed && nfix <= 0) || rr == 0.0;
   while (!skip) {
-    acc = 0.0;
-    spmv_rows<G>(Q, p, [&](int i, double s, bool lead) {
+    A acc;
+    spmv_rows<G>(Q, p, [&](int i, T s, bool lead) {
       if (lead) {
-        const double pi = p[i];
-        const double qi = s + pi * inv_tau;
+        const T pi = p[i];
+        const T qi = s + pi * inv_tau;
         q[i] = qi;
-        acc = fma(pi, qi, acc);
+        acc.add_prod(pi, qi);
       }
     });
-    block_sum_store(acc, part_pq + blockIdx.x);
-    if (!grid_sync(bar, st, tmo, false)) return;
-    const double pq = block_all_reduce_partials(part_pq, gridDim.x);
+    block_dot_store(acc, part_pq + blockIdx.x);
+    if (!grid_sync(bar, st, tmo, never_release)) return;
+    never_release = false;
+    const double pq = block_all_reduce<A>(part_pq, gridDim.x);
     if (!(pq > 0.0) || !isfinite(pq)) {
       numerr = true;
       break;
     }
-    const double alpha = rr / pq;
-    acc = 0.0;
+    const T alpha = T(rr / pq);
+    acc = A();
     // x += alpha p, r -= alpha q with a rounded product then a rounded sum,
-    // exactly as the elementwise vector statements of textbook CG.
+    // exactly as the elementwise vector statements of textbook CG; qx follows
+    // x through Q p = q - p/tau.
     for (long long i = t0; i < n; i += nt) {
-      x[i] = __dadd_rn(x[i], __dmul_rn(alpha, p[i]));
-      const double ri = __dsub_rn(r[i], __dmul_rn(alpha, q[i]));
+      const T pi = p[i], qi = q[i];
+      x[i] = add_rn(x[i], mul_rn(alpha, pi));
+      qx[i] = add_rn(qx[i], mul_rn(alpha, qi - pi * inv_tau));
+      const T ri = sub_rn(r[i], mul_rn(alpha, qi));
       r[i] = ri;
-      acc = fma(ri, ri, acc);
+      acc.add_prod(ri, ri);
     }
-    block_sum_store(acc, part_rr + blockIdx.x);
+    block_dot_store(acc, part_rr + blockIdx.x);
     if (!grid_sync(bar, st, tmo, false)) return;
-    const double rr_new = block_all_reduce_partials(part_rr, gridDim.x);
+    const double rr_new = block_all_reduce<A>(part_rr, gridDim.x);
     ++steps;
     const bool stop = mode == kCgFixed ? steps >= nfix : (tau * sqrt(rr_new) <= eps || steps >= cgmax);
     if (stop || rr_new == 0.0) break;
-    const double beta = rr_new / rr;
+    const T beta = T(rr_new / rr);
     rr = rr_new;
-    for (long long i = t0; i < n; i += nt) p[i] = __dadd_rn(r[i], __dmul_rn(beta, p[i]));
+    for (long long i = t0; i < n; i += nt) p[i] = add_rn(r[i], mul_rn(beta, p[i]));
     if (!grid_sync(bar, st, tmo, false)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -354,7 +506,7 @@ __global__ void __launch_bounds__(kCgBlock, 3) k_cg(DevCsr Q, const double* __re
       st->eps = eps;
       st->cg_total += steps;
       st->last_cg = steps;
-      st->spmv_total += steps + 1;
+      st->spmv_total += steps;
       st->k_total += 1;
       st->j += 1;
     }
@@ -364,18 +516,18 @@ __global__ void __launch_bounds__(kCgBlock, 3) k_cg(DevCsr Q, const double* __re
 // ------------------------------------------- dual step (Algorithm 1, y-update)
 // y+ = y + sigma (2 A x+ - A x - b), projected to >= 0 on rows >= m_eq; the
 // A x cache and the running average of y are updated in the same pass.
-template <int G>
-__global__ void __launch_bounds__(kBlock) k_dual(DevCsr A, const double* __restrict__ x,
-                                                 const double* __restrict__ b, double* y,
-                                                 double* ax, double* y_avg, const DevState* st) {
+template <int G, class T>
+__global__ void __launch_bounds__(kBlock) k_dual(CsrT<T> A, const T* __restrict__ x,
+                                                 const T* __restrict__ b, T* y, T* ax, T* y_avg,
+                                                 const DevState* st) {
   if (!st->iter_active) return;
-  const double sigma = st->sigma;
-  const double inv_j = 1.0 / (double)st->j;
+  const T sigma = T(st->sigma);
+  const T inv_j = T(1.0 / (double)st->j);
   const int m_eq = st->opt.m_eq;
-  spmv_rows<G>(A, x, [&](int i, double s, bool lead) {
+  spmv_rows<G>(A, x, [&](int i, T s, bool lead) {
     if (lead) {
-      double yn = y[i] + sigma * (2.0 * s - ax[i] - b[i]);
-      if (i >= m_eq && yn < 0.0) yn = 0.0;
+      T yn = y[i] + sigma * (T(2) * s - ax[i] - b[i]);
+      if (i >= m_eq && yn < T(0)) yn = T(0);
       y[i] = yn;
       ax[i] = s;
       y_avg[i] += (yn - y_avg[i]) * inv_j;
@@ -383,30 +535,56 @@ __global__ void __launch_bounds__(kBlock) k_dual(DevCsr A, const double* __restr
   });
 }
 
-// A' y+ over the explicit transpose, fused with the running average of x.
-template <int G>
-__global__ void __launch_bounds__(kBlock) k_atv(DevCsr At, const double* __restrict__ y,
-                                                double* aty, const double* __restrict__ x,
-                                                double* x_avg, const DevState* st) {
+// A' y+ over the explicit transpose, fused with the running average of x and
+// with the next CG's start: r0 = p0 = -(qx + c + A'y+) and r0'r0 partials.
+template <int G, class T>
+__global__ void __launch_bounds__(kBlock) k_atv(CsrT<T> At, const T* __restrict__ y, T* aty,
+                                                const T* __restrict__ x, T* x_avg,
+                                                const T* __restrict__ qx,
+                                                const T* __restrict__ c, T* r, T* p,
+                                                double* part_r0, const DevState* st) {
   if (!st->iter_active) return;
-  const double inv_j = 1.0 / (double)st->j;
-  spmv_rows<G>(At, y, [&](int i, double s, bool lead) {
+  const T inv_j = T(1.0 / (double)st->j);
+  typename Acc<T>::type acc;
+  spmv_rows<G>(At, y, [&](int i, T s, bool lead) {
     if (lead) {
       aty[i] = s;
       x_avg[i] += (x[i] - x_avg[i]) * inv_j;
+      const T ri = -(qx[i] + c[i] + s);
+      r[i] = ri;
+      p[i] = ri;
+      acc.add_prod(ri, ri);
     }
   });
+  block_dot_store(acc, part_r0 + blockIdx.x);
 }
 
-// Plain out = M v, optionally with per-block partial sums of out_i^2.
-template <int G>
-__global__ void __launch_bounds__(kBlock) k_spmv(DevCsr M, const double* __restrict__ v,
-                                                 double* out, double* part_sq) {
-  double acc = 0.0;
-  spmv_rows<G>(M, v, [&](int i, double s, bool lead) {
+// r0 = p0 = -(qx + c + A'y) and r0'r0 partials, for the first CG after a
+// set-up, an evaluation or a restart.  Launched with the grid of k_atv.
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_prepare(const T* __restrict__ qx,
+                                                    const T* __restrict__ c,
+                                                    const T* __restrict__ aty, T* r, T* p, int n,
+                                                    double* part_r0) {
+  typename Acc<T>::type acc;
+  for (long long i = grid_tid(); i < n; i += grid_threads()) {
+    const T ri = -(qx[i] + c[i] + aty[i]);
+    r[i] = ri;
+    p[i] = ri;
+    acc.add_prod(ri, ri);
+  }
+  block_dot_store(acc, part_r0 + blockIdx.x);
+}
+
+// Plain out = M v, optionally with per-block partial sums of out_i^2 (double).
+template <int G, class T>
+__global__ void __launch_bounds__(kBlock) k_spmv(CsrT<T> M, const T* __restrict__ v, T* out,
+                                                 double* part_sq) {
+  typename Acc<T>::type acc;
+  spmv_rows<G>(M, v, [&](int i, T s, bool lead) {
     if (lead) {
       out[i] = s;
-      acc = fma(s, s, acc);
+      acc.add_prod(s, s);
     }
   });
   if (part_sq) block_sum_store(acc, part_sq + blockIdx.x);
@@ -416,65 +594,96 @@ __global__ void __launch_bounds__(kBlock) k_spmv(DevCsr M, const double* __restr
 // Per block (stride kPartStride), over the n index space:
 //  [0] max|Qx + A'y + c|  [1] max|Qx|  [2] max|A'y|  [3] sum x.Qx  [4] sum c.x
 //  [5..9] the same for the average (x~, y~)            [10] max|c|
-template <int G>
-__global__ void __launch_bounds__(kBlock) k_kkt_n(DevCsr Q, const double* __restrict__ x,
-                                                  const double* __restrict__ x_avg,
-                                                  const double* __restrict__ aty,
-                                                  const double* __restrict__ aty_avg,
-                                                  const double* __restrict__ c, double* part) {
-  double v[11];
-#pragma unroll
-  for (int k = 0; k < 11; ++k) v[k] = 0.0;
-  spmv2_rows<G>(Q, x, x_avg, [&](int i, double qx, double qxa, bool lead) {
+// Q x and Q x~ are stored (qx, qx_avg): the exact refresh of the tracked qx.
+template <int G, class T>
+__global__ void __launch_bounds__(kBlock) k_kkt_n(CsrT<T> Q, const T* __restrict__ x,
+                                                  const T* __restrict__ x_avg,
+                                                  const T* __restrict__ aty,
+                                                  const T* __restrict__ aty_avg,
+                                                  const T* __restrict__ c, T* qx_out,
+                                                  T* qx_avg_out, double* part) {
+  using A = typename Acc<T>::type;
+  T mx[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};  // maxima, see the map below
+  A sm[4];                                               // x.Qx, c.x, x~.Qx~, c.x~
+  spmv2_rows<G>(Q, x, x_avg, [&](int i, T qx, T qxa, bool lead) {
     if (lead) {
-      const double ci = c[i];
-      v[0] = fmax(v[0], fabs(qx + aty[i] + ci));
-      v[1] = fmax(v[1], fabs(qx));
-      v[2] = fmax(v[2], fabs(aty[i]));
-      v[3] = fma(x[i], qx, v[3]);
-      v[4] = fma(ci, x[i], v[4]);
-      v[5] = fmax(v[5], fabs(qxa + aty_avg[i] + ci));
-      v[6] = fmax(v[6], fabs(qxa));
-      v[7] = fmax(v[7], fabs(aty_avg[i]));
-      v[8] = fma(x_avg[i], qxa, v[8]);
-      v[9] = fma(ci, x_avg[i], v[9]);
-      v[10] = fmax(v[10], fabs(ci));
+      const T ci = c[i];
+      qx_out[i] = qx;
+      qx_avg_out[i] = qxa;
+      mx[0] = fmax(mx[0], fabs(qx + aty[i] + ci));
+      mx[1] = fmax(mx[1], fabs(qx));
+      mx[2] = fmax(mx[2], fabs(aty[i]));
+      sm[0].add_prod(x[i], qx);
+      sm[1].add_prod(ci, x[i]);
+      mx[3] = fmax(mx[3], fabs(qxa + aty_avg[i] + ci));
+      mx[4] = fmax(mx[4], fabs(qxa));
+      mx[5] = fmax(mx[5], fabs(aty_avg[i]));
+      sm[2].add_prod(x_avg[i], qxa);
+      sm[3].add_prod(ci, x_avg[i]);
+      mx[6] = fmax(mx[6], fabs(ci));
     }
   });
   // fmax drops NaN; a NaN iterate still reaches relKKT through the dot products.
-  block_reduce_store<11>(v, kKktNMaxMask, part + size_t(blockIdx.x) * kPartStride);
+  __shared__ double out[11];
+  block_reduce_ms<7, 4>(mx, sm, out);
+  if (threadIdx.x == 0) {
+    double* o = part + size_t(blockIdx.x) * kPartStride;
+    // maxima at 0,1,2,5,6,7,10 and sums at 3,4,8,9 (kKktNMaxMask)
+    o[0] = out[0];
+    o[1] = out[1];
+    o[2] = out[2];
+    o[3] = out[7];
+    o[4] = out[8];
+    o[5] = out[3];
+    o[6] = out[4];
+    o[7] = out[5];
+    o[8] = out[9];
+    o[9] = out[10];
+    o[10] = out[6];
+  }
 }
 
 // Over the m index space (A x~ is computed here and stored for a restart):
 //  [0] max viol(x)  [1] max|Ax|  [2] sum b.y  [3] max viol(x~)  [4] max|Ax~|
 //  [5] sum b.y~  [6] max|b|;  viol = |Ax-b| on equality rows, [Ax-b]^+ else.
-template <int G>
-__global__ void __launch_bounds__(kBlock) k_kkt_m(DevCsr A, const double* __restrict__ x_avg,
-                                                  const double* __restrict__ ax, double* ax_avg,
-                                                  const double* __restrict__ b,
-                                                  const double* __restrict__ y,
-                                                  const double* __restrict__ y_avg, int m_eq,
+template <int G, class T>
+__global__ void __launch_bounds__(kBlock) k_kkt_m(CsrT<T> Am, const T* __restrict__ x_avg,
+                                                  const T* __restrict__ ax, T* ax_avg,
+                                                  const T* __restrict__ b,
+                                                  const T* __restrict__ y,
+                                                  const T* __restrict__ y_avg, int m_eq,
                                                   double* part) {
-  double v[7];
-#pragma unroll
-  for (int k = 0; k < 7; ++k) v[k] = 0.0;
-  spmv_rows<G>(A, x_avg, [&](int i, double s, bool lead) {
+  using A = typename Acc<T>::type;
+  T mx[5] = {T(0), T(0), T(0), T(0), T(0)};  // viol, |Ax|, viol~, |Ax~|, |b|
+  A sm[2];                                   // b.y, b.y~
+  spmv_rows<G>(Am, x_avg, [&](int i, T s, bool lead) {
     if (lead) {
       ax_avg[i] = s;
-      const double bi = b[i];
-      const double d = ax[i] - bi, da = s - bi;
-      const double vc = i < m_eq ? fabs(d) : (d > 0.0 ? d : 0.0);
-      const double va = i < m_eq ? fabs(da) : (da > 0.0 ? da : 0.0);
-      v[0] = fmax(v[0], vc);
-      v[1] = fmax(v[1], fabs(ax[i]));
-      v[2] = fma(bi, y[i], v[2]);
-      v[3] = fmax(v[3], va);
-      v[4] = fmax(v[4], fabs(s));
-      v[5] = fma(bi, y_avg[i], v[5]);
-      v[6] = fmax(v[6], fabs(bi));
+      const T bi = b[i];
+      const T d = ax[i] - bi, da = s - bi;
+      const T vc = i < m_eq ? fabs(d) : (d > T(0) ? d : T(0));
+      const T va = i < m_eq ? fabs(da) : (da > T(0) ? da : T(0));
+      mx[0] = fmax(mx[0], vc);
+      mx[1] = fmax(mx[1], fabs(ax[i]));
+      sm[0].add_prod(bi, y[i]);
+      mx[2] = fmax(mx[2], va);
+      mx[3] = fmax(mx[3], fabs(s));
+      sm[1].add_prod(bi, y_avg[i]);
+      mx[4] = fmax(mx[4], fabs(bi));
     }
   });
-  block_reduce_store<7>(v, kKktMMaxMask, part + size_t(blockIdx.x) * kPartStride);
+  __shared__ double out[7];
+  block_reduce_ms<5, 2>(mx, sm, out);
+  if (threadIdx.x == 0) {
+    double* o = part + size_t(blockIdx.x) * kPartStride;
+    o[0] = out[0];
+    o[1] = out[1];
+    o[2] = out[5];
+    o[3] = out[2];
+    o[4] = out[3];
+    o[5] = out[6];
+    o[6] = out[4];
+  }
 }
 
 struct KktTerms {
@@ -563,35 +772,41 @@ __global__ void k_control(const double* part_n, int gn, const double* part_m, in
 
 // Restart to the candidate (Algorithm 1, restart step), n side: distance to
 // the previous restart point for the primal weight, then anchor = x = cand.
-__global__ void __launch_bounds__(kBlock) k_restart_n(double* x, const double* __restrict__ x_avg,
-                                                      double* x_anchor, double* aty,
-                                                      const double* __restrict__ aty_avg,
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_restart_n(T* x, const T* __restrict__ x_avg,
+                                                      T* x_anchor, T* aty,
+                                                      const T* __restrict__ aty_avg, T* qx,
+                                                      const T* __restrict__ qx_avg,
                                                       const DevState* st, int n, double* part) {
   const int pending = st->restart_pending;
   if (pending == 0) return;
-  double acc = 0.0;
+  typename Acc<T>::type acc;
   for (long long i = grid_tid(); i < n; i += grid_threads()) {
-    const double cand = pending == 2 ? x_avg[i] : x[i];
-    const double d = cand - x_anchor[i];
-    acc = fma(d, d, acc);
+    const T cand = pending == 2 ? x_avg[i] : x[i];
+    const T d = cand - x_anchor[i];
+    acc.add_prod(d, d);
     x_anchor[i] = cand;
     x[i] = cand;
-    if (pending == 2) aty[i] = aty_avg[i];
+    if (pending == 2) {
+      aty[i] = aty_avg[i];
+      qx[i] = qx_avg[i];
+    }
   }
   block_sum_store(acc, part + blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kBlock) k_restart_m(double* y, const double* __restrict__ y_avg,
-                                                      double* y_anchor, double* ax,
-                                                      const double* __restrict__ ax_avg,
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_restart_m(T* y, const T* __restrict__ y_avg,
+                                                      T* y_anchor, T* ax,
+                                                      const T* __restrict__ ax_avg,
                                                       const DevState* st, int m, double* part) {
   const int pending = st->restart_pending;
   if (pending == 0) return;
-  double acc = 0.0;
+  typename Acc<T>::type acc;
   for (long long i = grid_tid(); i < m; i += grid_threads()) {
-    const double cand = pending == 2 ? y_avg[i] : y[i];
-    const double d = cand - y_anchor[i];
-    acc = fma(d, d, acc);
+    const T cand = pending == 2 ? y_avg[i] : y[i];
+    const T d = cand - y_anchor[i];
+    acc.add_prod(d, d);
     y_anchor[i] = cand;
     y[i] = cand;
     if (pending == 2) ax[i] = ax_avg[i];
@@ -624,43 +839,51 @@ __global__ void k_restart_finish(const double* part_n, int gn, const double* par
 
 // ---------------------------------------------------------- set-up kernels
 // Start of a solve: cold start zeros everything; warm start copies (x0, y0).
-__global__ void k_init_vectors(double* x, double* x_avg, double* x_anchor,
-                               const double* __restrict__ x0, int n, double* y, double* y_avg,
-                               double* y_anchor, const double* __restrict__ y0, int m) {
+template <class T>
+__global__ void k_init_vectors(T* x, T* x_avg, T* x_anchor, const T* __restrict__ x0, int n, T* y,
+                               T* y_avg, T* y_anchor, const T* __restrict__ y0, int m) {
   for (long long i = grid_tid(); i < n; i += grid_threads()) {
-    const double v = x0 ? x0[i] : 0.0;
+    const T v = x0 ? x0[i] : T(0);
     x[i] = v;
     x_anchor[i] = v;
-    x_avg[i] = 0.0;
+    x_avg[i] = T(0);
   }
   for (long long i = grid_tid(); i < m; i += grid_threads()) {
-    const double v = y0 ? y0[i] : 0.0;
+    const T v = y0 ? y0[i] : T(0);
     y[i] = v;
     y_anchor[i] = v;
-    y_avg[i] = 0.0;
+    y_avg[i] = T(0);
   }
 }
 
 // v = 1/sqrt(n) (power-iteration start) and per-block partials of ||c||^2, ||b||^2.
-__global__ void k_pow_start(double* v, int n, const double* __restrict__ c,
-                            const double* __restrict__ b, int m, double* part2) {
-  const double v0 = 1.0 / sqrt((double)n);
-  double a[2] = {0.0, 0.0};
+template <class T>
+__global__ void k_pow_start(T* v, int n, const T* __restrict__ c, const T* __restrict__ b, int m,
+                            double* part2) {
+  const T v0 = T(1.0 / sqrt((double)n));
+  typename Acc<T>::type a[2];
   for (long long i = grid_tid(); i < n; i += grid_threads()) {
     v[i] = v0;
-    a[0] = fma(c[i], c[i], a[0]);
+    a[0].add_prod(c[i], c[i]);
   }
-  for (long long i = grid_tid(); i < m; i += grid_threads()) a[1] = fma(b[i], b[i], a[1]);
-  block_reduce_store<2>(a, 0u, part2 + size_t(blockIdx.x) * 2);
+  for (long long i = grid_tid(); i < m; i += grid_threads()) a[1].add_prod(b[i], b[i]);
+  block_reduce_ms<0, 2, T>(nullptr, a, part2 + size_t(blockIdx.x) * 2);
 }
 
 // v = w / lambda with lambda = ||w||_2 from the partials of the A' u pass.
-__global__ void k_pow_scale(const double* __restrict__ w, double* v, int n, const double* part,
-                            int gp, DevState* st) {
-  const double lam = sqrt(block_all_reduce_partials(part, gp));
-  const double inv_lam = lam > 0.0 ? 1.0 / lam : 0.0;
+template <class T>
+__global__ void k_pow_scale(const T* __restrict__ w, T* v, int n, const double* part, int gp,
+                            DevState* st) {
+  const double lam = sqrt(block_all_reduce<AccD>(part, gp));
+  const T inv_lam = lam > 0.0 ? T(1.0 / lam) : T(0);
   for (long long i = grid_tid(); i < n; i += grid_threads()) v[i] = w[i] * inv_lam;
   if (blockIdx.x == 0 && threadIdx.x == 0) st->lam = lam;
+}
+
+// Element-wise type conversion (FP64 <-> FP32 copies of a vector).
+template <class Ti, class To>
+__global__ void k_convert(const Ti* __restrict__ in, To* out, int n) {
+  for (long long i = grid_tid(); i < n; i += grid_threads()) out[i] = To(in[i]);
 }
 
 // eta = 1/(2||A||_2) (Section 3.2), omega0 = ||c||/||b|| (1 if either is ~0),

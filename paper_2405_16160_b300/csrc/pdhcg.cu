@@ -1,6 +1,11 @@
 // Host side of the C ABI declared in include/pdhcg.h: handle lifecycle,
 // device memory, CUDA-graph capture of a chunk of PDHCG iterations and the
 // solve loop (Algorithm 1 with the Section 4 heuristics of arXiv 2405.16160).
+//
+// A handle holds the problem in FP64 and, for the mixed-precision path, FP32
+// copies of the matrix values and vectors (the int32 index arrays are
+// shared).  Each precision has its own vector set and its own captured chunk
+// graph; the scalar state (DevState) is shared.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -10,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pdhcg.h"
@@ -31,27 +37,34 @@ void set_error(const char* fmt, ...) {
   g_last_error = buf;
 }
 
-#define CUDA_TRY(call)                                                                  \
-  do {                                                                                  \
-    cudaError_t e_ = (call);                                                            \
-    if (e_ != cudaSuccess) {                                                            \
+#define CUDA_TRY(call)                                                                         \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
       set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-      return QP_ERR_CUDA;                                                               \
-    }                                                                                   \
+      return QP_ERR_CUDA;                                                                      \
+    }                                                                                          \
   } while (0)
 
-#define QP_TRY(call)                  \
-  do {                                \
-    qp_status s_ = (call);            \
-    if (s_ != QP_OK) return s_;       \
+#define QP_TRY(call)            \
+  do {                          \
+    qp_status s_ = (call);      \
+    if (s_ != QP_OK) return s_; \
   } while (0)
 
-// Lanes per row.  FP64 arithmetic is the scarce resource on this GPU (the
-// FP64 pipe runs at ~1/58 of FP32), so short rows get one lane each: every
-// DFMA issues with most lanes busy and no shuffle-add tree is needed.  Long
-// rows share lanes so one row does not serialise a warp.
-int group_size_for(int64_t nnz, int64_t rows) {
+// Lanes per row.  FP64: the FP64 pipe is the scarce resource on this GPU (it
+// runs at ~1/58 of FP32), so short rows get one lane each: every DFMA issues
+// with most lanes busy and no shuffle-add tree is needed.  FP32: the kernels
+// are bound by memory, so rows of ~10 entries share 4 lanes for coalescing.
+int group_size_for(int64_t nnz, int64_t rows, bool fp32) {
   const double avg = rows > 0 ? double(nnz) / double(rows) : 0.0;
+  if (fp32) {
+    if (avg <= 3.0) return 1;
+    if (avg <= 6.0) return 2;
+    if (avg <= 20.0) return 4;
+    if (avg <= 64.0) return 8;
+    return 32;
+  }
   if (avg <= 24.0) return 1;
   if (avg <= 64.0) return 4;
   if (avg <= 256.0) return 8;
@@ -62,11 +75,40 @@ struct DevMat {
   int32_t* rowptr = nullptr;
   int32_t* col = nullptr;
   double* val = nullptr;
+  float* val32 = nullptr;
   int32_t rows = 0;
   int64_t nnz = 0;
-  int G = 4;
-  DevCsr view() const { return DevCsr{rowptr, col, val, rows}; }
+  int G64 = 1, G32 = 4;
 };
+
+template <class T>
+CsrT<T> view(const DevMat& M) {
+  if constexpr (std::is_same<T, double>::value)
+    return CsrT<double>{M.rowptr, M.col, M.val, M.rows};
+  else
+    return CsrT<float>{M.rowptr, M.col, M.val32, M.rows};
+}
+
+template <class T>
+int lanes(const DevMat& M) {
+  return std::is_same<T, double>::value ? M.G64 : M.G32;
+}
+
+// Vectors of one precision.
+template <class T>
+struct VecSet {
+  T *c = nullptr, *b = nullptr;
+  T *x = nullptr, *y = nullptr, *ax = nullptr, *aty = nullptr;
+  T *x_avg = nullptr, *y_avg = nullptr, *x_anchor = nullptr, *y_anchor = nullptr;
+  T *ax_avg = nullptr, *aty_avg = nullptr;
+  T *r = nullptr, *p = nullptr, *q = nullptr;
+  T *qx = nullptr, *qx_avg = nullptr;  // tracked Q x and Q x~ (refreshed every evaluation)
+  T *x0 = nullptr, *y0 = nullptr;
+  T *pw_v = nullptr, *pw_u = nullptr, *pw_w = nullptr;
+};
+
+constexpr int kPrecFp64 = QP_PREC_FP64;
+constexpr int kPrecMixed = QP_PREC_MIXED;
 
 }  // namespace
 
@@ -82,15 +124,10 @@ struct qp_handle {
   bool has_alloc = false;
   int32_t n = 0, m = 0, m_eq = 0;
   DevMat Q, A, At;
-  double *c = nullptr, *b = nullptr;
-  double *x = nullptr, *y = nullptr, *ax = nullptr, *aty = nullptr;
-  double *x_avg = nullptr, *y_avg = nullptr, *x_anchor = nullptr, *y_anchor = nullptr;
-  double *ax_avg = nullptr, *aty_avg = nullptr;
-  double *r = nullptr, *p = nullptr, *q = nullptr;
-  double *x0 = nullptr, *y0 = nullptr;  // warm start
-  double *pw_v = nullptr, *pw_u = nullptr, *pw_w = nullptr;
+  VecSet<double> v64;
+  VecSet<float> v32;
   double *part_cg = nullptr, *part_n = nullptr, *part_m = nullptr, *part_rn = nullptr,
-         *part_rm = nullptr, *part_pow = nullptr, *part2 = nullptr;
+         *part_rm = nullptr, *part_pow = nullptr, *part2 = nullptr, *part_r0 = nullptr;
   DevState* st = nullptr;
   GridBarrier* bar = nullptr;
   DevState* h_st = nullptr;  // pinned mirror
@@ -98,9 +135,9 @@ struct qp_handle {
   int grid_n = 1, grid_m = 1, grid_cg = 1, grid_vec = 1;
   bool coop_ok = true;
   bool warm_set = false;
-  // captured chunk graph
-  cudaGraphExec_t chunk_exec = nullptr;
-  int chunk_iters = 0;
+  int active_prec = kPrecFp64;  // precision of the iterate last produced
+  cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};
+  int chunk_iters[2] = {0, 0};
   std::vector<cudaEvent_t> ev;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   std::vector<qp_trace_entry> trace;
@@ -110,6 +147,14 @@ struct qp_handle {
 };
 
 namespace {
+
+template <class T>
+VecSet<T>& vecs(qp_handle* h) {
+  if constexpr (std::is_same<T, double>::value)
+    return h->v64;
+  else
+    return h->v32;
+}
 
 qp_status dev_alloc(qp_handle* h, void** out, size_t bytes) {
   bytes = std::max<size_t>(bytes, 256);
@@ -146,7 +191,6 @@ qp_status dispatch_g(int G, F&& f) {
     case 2: f(std::integral_constant<int, 2>{}); return QP_OK;
     case 4: f(std::integral_constant<int, 4>{}); return QP_OK;
     case 8: f(std::integral_constant<int, 8>{}); return QP_OK;
-    case 16: f(std::integral_constant<int, 16>{}); return QP_OK;
     case 32: f(std::integral_constant<int, 32>{}); return QP_OK;
     default: set_error("unsupported group size %d", G); return QP_ERR_INVALID_ARG;
   }
@@ -189,7 +233,9 @@ qp_status validate_options(const qp_options* o) {
       o->cg_max < 1 ||
       (o->restart_mode != QP_RESTART_ADAPTIVE && o->restart_mode != QP_RESTART_NONE) ||
       o->power_iters < 1 || o->power_iters > 100000 || !(o->eps_zero >= 0.0) ||
-      !(o->theta_pw >= 0.0 && o->theta_pw <= 1.0) || !(o->time_limit_s > 0.0)) {
+      !(o->theta_pw >= 0.0 && o->theta_pw <= 1.0) || !(o->time_limit_s > 0.0) ||
+      (o->precision != QP_PREC_FP64 && o->precision != QP_PREC_MIXED) || o->warm_start < 0 ||
+      o->warm_start > 2) {
     set_error("invalid option value");
     return QP_ERR_INVALID_ARG;
   }
@@ -197,8 +243,10 @@ qp_status validate_options(const qp_options* o) {
 }
 
 // --------------------------------------------------------------- launches
+template <class T>
 qp_status launch_cg(qp_handle* h, bool coop) {
-  return dispatch_g(h->Q.G, [&](auto g) {
+  VecSet<T>& v = vecs<T>(h);
+  return dispatch_g(lanes<T>(h->Q), [&](auto g) {
     constexpr int G = decltype(g)::value;
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
@@ -211,86 +259,129 @@ qp_status launch_cg(qp_handle* h, bool coop) {
       cfg.attrs = attr;
       cfg.numAttrs = 1;
     }
-    cudaLaunchKernelEx(&cfg, k_cg<G>, h->Q.view(), (const double*)h->c, (const double*)h->aty,
-                       h->x, h->r, h->p, h->q, h->part_cg, h->st, h->bar, (int)h->n);
+    cudaLaunchKernelEx(&cfg, k_cg<G, T>, view<T>(h->Q), v.x, v.r, v.p, v.q, v.qx,
+                       (const double*)h->part_r0, h->grid_n, h->part_cg, h->st, h->bar,
+                       (int)h->n);
   });
 }
 
+template <class T>
 qp_status launch_dual(qp_handle* h) {
-  return dispatch_g(h->A.G, [&](auto g) {
+  VecSet<T>& v = vecs<T>(h);
+  return dispatch_g(lanes<T>(h->A), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    k_dual<G><<<h->grid_m, kBlock, 0, h->stream>>>(h->A.view(), h->x, h->b, h->y, h->ax,
-                                                   h->y_avg, h->st);
+    k_dual<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(view<T>(h->A), v.x, v.b, v.y, v.ax, v.y_avg,
+                                                      h->st);
   });
 }
 
+template <class T>
 qp_status launch_atv(qp_handle* h) {
-  return dispatch_g(h->At.G, [&](auto g) {
+  VecSet<T>& v = vecs<T>(h);
+  return dispatch_g(lanes<T>(h->At), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    k_atv<G><<<h->grid_n, kBlock, 0, h->stream>>>(h->At.view(), h->y, h->aty, h->x, h->x_avg,
-                                                  h->st);
+    k_atv<G, T><<<h->grid_n, kBlock, 0, h->stream>>>(view<T>(h->At), v.y, v.aty, v.x, v.x_avg,
+                                                     v.qx, v.c, v.r, v.p, h->part_r0, h->st);
   });
 }
 
-qp_status launch_spmv(qp_handle* h, const DevMat& M, const double* v, double* out, double* part,
-                      int grid) {
-  return dispatch_g(M.G, [&](auto g) {
+template <class T>
+qp_status launch_spmv(qp_handle* h, const DevMat& M, const T* x, T* out, double* part, int grid) {
+  return dispatch_g(lanes<T>(M), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    k_spmv<G><<<grid, kBlock, 0, h->stream>>>(M.view(), v, out, part);
+    k_spmv<G, T><<<grid, kBlock, 0, h->stream>>>(view<T>(M), x, out, part);
   });
 }
 
 // relKKT of (x, y) and (x~, y~); mode as in k_control.
+template <class T>
 qp_status launch_eval(qp_handle* h, int mode) {
-  QP_TRY(launch_spmv(h, h->At, h->y_avg, h->aty_avg, nullptr, h->grid_n));
-  QP_TRY(dispatch_g(h->Q.G, [&](auto g) {
+  VecSet<T>& v = vecs<T>(h);
+  QP_TRY(launch_spmv<T>(h, h->At, v.y_avg, v.aty_avg, nullptr, h->grid_n));
+  QP_TRY(dispatch_g(lanes<T>(h->Q), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    k_kkt_n<G><<<h->grid_n, kBlock, 0, h->stream>>>(h->Q.view(), h->x, h->x_avg, h->aty,
-                                                     h->aty_avg, h->c, h->part_n);
+    k_kkt_n<G, T><<<h->grid_n, kBlock, 0, h->stream>>>(view<T>(h->Q), v.x, v.x_avg, v.aty,
+                                                       v.aty_avg, v.c, v.qx, v.qx_avg, h->part_n);
   }));
-  QP_TRY(dispatch_g(h->A.G, [&](auto g) {
+  QP_TRY(dispatch_g(lanes<T>(h->A), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    k_kkt_m<G><<<h->grid_m, kBlock, 0, h->stream>>>(h->A.view(), h->x_avg, h->ax, h->ax_avg, h->b,
-                                                    h->y, h->y_avg, h->m_eq, h->part_m);
+    k_kkt_m<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(view<T>(h->A), v.x_avg, v.ax, v.ax_avg,
+                                                       v.b, v.y, v.y_avg, h->m_eq, h->part_m);
   }));
   k_control<<<1, 32, 0, h->stream>>>(h->part_n, h->grid_n, h->part_m, h->grid_m, h->st, mode);
   return QP_OK;
 }
 
+template <class T>
 qp_status launch_restart(qp_handle* h) {
-  k_restart_n<<<h->grid_vec, kBlock, 0, h->stream>>>(h->x, h->x_avg, h->x_anchor, h->aty,
-                                                     h->aty_avg, h->st, h->n, h->part_rn);
-  k_restart_m<<<h->grid_vec, kBlock, 0, h->stream>>>(h->y, h->y_avg, h->y_anchor, h->ax,
-                                                     h->ax_avg, h->st, h->m, h->part_rm);
+  VecSet<T>& v = vecs<T>(h);
+  k_restart_n<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.x, v.x_avg, v.x_anchor, v.aty,
+                                                        v.aty_avg, v.qx, v.qx_avg, h->st, h->n,
+                                                        h->part_rn);
+  k_restart_m<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.y, v.y_avg, v.y_anchor, v.ax, v.ax_avg,
+                                                        h->st, h->m, h->part_rm);
   k_restart_finish<<<1, 32, 0, h->stream>>>(h->part_rn, h->grid_vec, h->part_rm, h->grid_vec,
                                             h->st);
   return QP_OK;
 }
 
+// The next CG's start r0 = p0 = -(qx + c + A'y) and its r0'r0 partials.
+template <class T>
+void launch_prepare(qp_handle* h) {
+  VecSet<T>& v = vecs<T>(h);
+  k_prepare<T><<<h->grid_n, kBlock, 0, h->stream>>>(v.qx, v.c, v.aty, v.r, v.p, h->n, h->part_r0);
+}
+
+template <class T>
 qp_status launch_iteration(qp_handle* h, bool coop) {
-  QP_TRY(launch_cg(h, coop));
-  QP_TRY(launch_dual(h));
-  QP_TRY(launch_atv(h));
+  QP_TRY(launch_cg<T>(h, coop));
+  QP_TRY(launch_dual<T>(h));
+  QP_TRY(launch_atv<T>(h));
   return QP_OK;
 }
 
 // Power iteration for ||A||_2 (30 steps by default) and the step sizes.
+template <class T>
 qp_status launch_setup(qp_handle* h, int power_iters, int reset) {
-  k_pow_start<<<h->grid_vec, kBlock, 0, h->stream>>>(h->pw_v, h->n, h->c, h->b, h->m, h->part2);
+  VecSet<T>& v = vecs<T>(h);
+  k_pow_start<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.pw_v, h->n, v.c, v.b, h->m, h->part2);
   for (int t = 0; t < power_iters; ++t) {
-    QP_TRY(launch_spmv(h, h->A, h->pw_v, h->pw_u, nullptr, h->grid_m));
-    QP_TRY(launch_spmv(h, h->At, h->pw_u, h->pw_w, h->part_pow, h->grid_n));
-    k_pow_scale<<<h->grid_vec, kBlock, 0, h->stream>>>(h->pw_w, h->pw_v, h->n, h->part_pow,
-                                                       h->grid_n, h->st);
+    QP_TRY(launch_spmv<T>(h, h->A, v.pw_v, v.pw_u, nullptr, h->grid_m));
+    QP_TRY(launch_spmv<T>(h, h->At, v.pw_u, v.pw_w, h->part_pow, h->grid_n));
+    k_pow_scale<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.pw_w, v.pw_v, h->n, h->part_pow,
+                                                          h->grid_n, h->st);
   }
   k_setup_finish<<<1, 32, 0, h->stream>>>(h->part2, h->grid_vec, h->st, reset);
   return QP_OK;
 }
 
+// A x, A'y and Q x of the current iterate, then the next CG's start.
+template <class T>
 qp_status recompute_caches(qp_handle* h) {
-  QP_TRY(launch_spmv(h, h->A, h->x, h->ax, nullptr, h->grid_m));
-  QP_TRY(launch_spmv(h, h->At, h->y, h->aty, nullptr, h->grid_n));
+  VecSet<T>& v = vecs<T>(h);
+  QP_TRY(launch_spmv<T>(h, h->A, v.x, v.ax, nullptr, h->grid_m));
+  QP_TRY(launch_spmv<T>(h, h->At, v.y, v.aty, nullptr, h->grid_n));
+  QP_TRY(launch_spmv<T>(h, h->Q, v.x, v.qx, nullptr, h->grid_n));
+  launch_prepare<T>(h);
   return QP_OK;
+}
+
+template <class Ti, class To>
+void convert(qp_handle* h, const Ti* in, To* out, int count) {
+  if (count > 0) k_convert<Ti, To><<<h->grid_vec, kBlock, 0, h->stream>>>(in, out, count);
+}
+
+// Copy the iterate vectors of one precision into the other.
+template <class Ti, class To>
+void convert_state(qp_handle* h) {
+  VecSet<Ti>& a = vecs<Ti>(h);
+  VecSet<To>& b = vecs<To>(h);
+  convert(h, a.x, b.x, h->n);
+  convert(h, a.x_avg, b.x_avg, h->n);
+  convert(h, a.x_anchor, b.x_anchor, h->n);
+  convert(h, a.y, b.y, h->m);
+  convert(h, a.y_avg, b.y_avg, h->m);
+  convert(h, a.y_anchor, b.y_anchor, h->m);
 }
 
 qp_status check_launch() {
@@ -302,36 +393,42 @@ qp_status check_launch() {
   return QP_OK;
 }
 
-void destroy_chunk(qp_handle* h) {
-  if (h->chunk_exec) cudaGraphExecDestroy(h->chunk_exec);
-  h->chunk_exec = nullptr;
+void destroy_chunks(qp_handle* h) {
+  for (auto& e : h->chunk_exec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
 }
 
-// Capture eval_freq iterations + one evaluation + restart + status copy.
 // One chunk: `iters` PDHCG iterations, one relKKT evaluation with the restart
 // logic, and the copy of the scalar state to the pinned host mirror.  With
 // `ev` (2*iters events) every CG launch is bracketed by CUDA events.
+template <class T>
 qp_status enqueue_chunk(qp_handle* h, int iters, bool coop, cudaEvent_t* ev) {
   qp_status s = QP_OK;
   for (int k = 0; k < iters && s == QP_OK; ++k) {
     if (ev) cudaEventRecord(ev[2 * k], h->stream);
-    s = launch_cg(h, coop);
+    s = launch_cg<T>(h, coop);
     if (ev) cudaEventRecord(ev[2 * k + 1], h->stream);
-    if (s == QP_OK) s = launch_dual(h);
-    if (s == QP_OK) s = launch_atv(h);
+    if (s == QP_OK) s = launch_dual<T>(h);
+    if (s == QP_OK) s = launch_atv<T>(h);
   }
-  if (s == QP_OK) s = launch_eval(h, 1);
-  if (s == QP_OK) s = launch_restart(h);
+  if (s == QP_OK) s = launch_eval<T>(h, 1);
+  if (s == QP_OK) s = launch_restart<T>(h);
+  if (s == QP_OK) launch_prepare<T>(h);
   if (s == QP_OK)
     cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream);
   return s;
 }
 
+template <class T>
 qp_status capture_chunk(qp_handle* h, int iters, bool coop) {
-  destroy_chunk(h);
+  const int pi = std::is_same<T, double>::value ? 0 : 1;
+  if (h->chunk_exec[pi]) cudaGraphExecDestroy(h->chunk_exec[pi]);
+  h->chunk_exec[pi] = nullptr;
   cudaGraph_t graph = nullptr;
   CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  qp_status s = enqueue_chunk(h, iters, coop, nullptr);
+  qp_status s = enqueue_chunk<T>(h, iters, coop, nullptr);
   cudaError_t le = cudaGetLastError();
   cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
   if (s != QP_OK) {
@@ -344,28 +441,30 @@ qp_status capture_chunk(qp_handle* h, int iters, bool coop) {
     set_error("graph capture failed: %s / %s", cudaGetErrorString(le), cudaGetErrorString(ce));
     return QP_ERR_CUDA;
   }
-  cudaError_t ie = cudaGraphInstantiate(&h->chunk_exec, graph, 0);
+  cudaError_t ie = cudaGraphInstantiate(&h->chunk_exec[pi], graph, 0);
   cudaGraphDestroy(graph);
   if (ie != cudaSuccess) {
     cudaGetLastError();
-    h->chunk_exec = nullptr;
+    h->chunk_exec[pi] = nullptr;
     set_error("graph instantiate failed: %s", cudaGetErrorString(ie));
     return QP_ERR_CUDA;
   }
-  h->chunk_iters = iters;
+  h->chunk_iters[pi] = iters;
   return QP_OK;
 }
 
+template <class T>
 qp_status ensure_chunk(qp_handle* h, int iters) {
-  if (h->chunk_exec && h->chunk_iters == iters) return QP_OK;
+  const int pi = std::is_same<T, double>::value ? 0 : 1;
+  if (h->chunk_exec[pi] && h->chunk_iters[pi] == iters) return QP_OK;
   if (h->coop_ok) {
-    qp_status s = capture_chunk(h, iters, true);
+    qp_status s = capture_chunk<T>(h, iters, true);
     if (s == QP_OK) return QP_OK;
     // The grid is sized to be co-resident, so an ordinary launch also
     // satisfies the barrier; record that the cooperative form was refused.
     h->coop_ok = false;
   }
-  return capture_chunk(h, iters, false);
+  return capture_chunk<T>(h, iters, false);
 }
 
 qp_status ensure_events(qp_handle* h, int iters) {
@@ -425,13 +524,32 @@ qp_status upload(qp_handle* h, void* dst, const void* src, size_t bytes) {
 qp_status upload_matrix(qp_handle* h, DevMat* M, const HostCsr& H) {
   M->rows = H.rows;
   M->nnz = H.nnz();
-  M->G = group_size_for(M->nnz, H.rows);
+  M->G64 = group_size_for(M->nnz, H.rows, false);
+  M->G32 = group_size_for(M->nnz, H.rows, true);
   QP_TRY(dalloc(h, &M->rowptr, size_t(H.rows) + 1));
   QP_TRY(dalloc(h, &M->col, size_t(M->nnz)));
   QP_TRY(dalloc(h, &M->val, size_t(M->nnz)));
+  QP_TRY(dalloc(h, &M->val32, size_t(M->nnz)));
   QP_TRY(upload(h, M->rowptr, H.rowptr.data(), (size_t(H.rows) + 1) * sizeof(int32_t)));
   QP_TRY(upload(h, M->col, H.col.data(), size_t(M->nnz) * sizeof(int32_t)));
   QP_TRY(upload(h, M->val, H.val.data(), size_t(M->nnz) * sizeof(double)));
+  if (M->nnz > 0)
+    k_convert<double, float><<<h->grid_vec, kBlock, 0, h->stream>>>(M->val, M->val32,
+                                                                    int(M->nnz));
+  return QP_OK;
+}
+
+template <class T>
+qp_status alloc_vecs(qp_handle* h) {
+  VecSet<T>& v = vecs<T>(h);
+  const size_t N = size_t(h->n), M = size_t(h->m);
+  T** nv[] = {&v.c, &v.x, &v.aty, &v.x_avg, &v.x_anchor, &v.aty_avg, &v.r, &v.p, &v.q, &v.qx,
+              &v.qx_avg, &v.x0, &v.pw_v, &v.pw_w};
+  for (T** p : nv) QP_TRY(dalloc(h, p, N));
+  T** mv[] = {&v.b, &v.y, &v.ax, &v.y_avg, &v.y_anchor, &v.ax_avg, &v.y0, &v.pw_u};
+  for (T** p : mv) QP_TRY(dalloc(h, p, M));
+  CUDA_TRY(cudaMemsetAsync(v.x0, 0, N * sizeof(T), h->stream));
+  CUDA_TRY(cudaMemsetAsync(v.y0, 0, std::max<size_t>(M, 1) * sizeof(T), h->stream));
   return QP_OK;
 }
 
@@ -513,37 +631,51 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   h->m = m;
   h->m_eq = m_eq;
   CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  // Launch geometry: one resident wave for the streaming/SpMV kernels.
+  const int wave = h->num_sms * 8;
+  h->grid_vec =
+      int(std::max<int64_t>(1, std::min<int64_t>((std::max(n, m) + kBlock - 1) / kBlock, wave)));
   QP_TRY(upload_matrix(h, &h->Q, Qh));
   QP_TRY(upload_matrix(h, &h->A, Ah));
   QP_TRY(upload_matrix(h, &h->At, Th));
+  QP_TRY(alloc_vecs<double>(h));
+  QP_TRY(alloc_vecs<float>(h));
   const size_t N = size_t(n), M = size_t(m);
-  double** nvecs[] = {&h->c, &h->x, &h->aty, &h->x_avg, &h->x_anchor, &h->aty_avg, &h->r,
-                      &h->p, &h->q, &h->x0, &h->pw_v, &h->pw_w};
-  for (double** v : nvecs) QP_TRY(dalloc(h, v, N));
-  double** mvecs[] = {&h->b, &h->y, &h->ax, &h->y_avg, &h->y_anchor, &h->ax_avg, &h->y0, &h->pw_u};
-  for (double** v : mvecs) QP_TRY(dalloc(h, v, M));
-  QP_TRY(upload(h, h->c, c, N * sizeof(double)));
-  QP_TRY(upload(h, h->b, b, M * sizeof(double)));
+  QP_TRY(upload(h, h->v64.c, c, N * sizeof(double)));
+  QP_TRY(upload(h, h->v64.b, b, M * sizeof(double)));
+  convert(h, h->v64.c, h->v32.c, n);
+  convert(h, h->v64.b, h->v32.b, m);
 
-  // Launch geometry: one resident wave for the streaming/SpMV kernels; the CG
-  // kernel is persistent, sized to the co-resident block count.
-  const int wave = h->num_sms * 8;
-  h->grid_n = blocks_for_rows(std::max(n, 1), std::max(h->Q.G, h->At.G), wave);
-  h->grid_m = blocks_for_rows(std::max(m, 1), h->A.G, wave);
-  h->grid_vec = int(std::max<int64_t>(1, std::min<int64_t>((std::max(n, m) + kBlock - 1) / kBlock, wave)));
-  int occ = 0;
-  QP_TRY(dispatch_g(h->Q.G, [&](auto g) {
-    constexpr int G = decltype(g)::value;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<G>, kCgBlock, 0);
-  }));
+  const int g_n = std::max({h->Q.G64, h->At.G64, h->Q.G32, h->At.G32});
+  const int g_m = std::max(h->A.G64, h->A.G32);
+  h->grid_n = blocks_for_rows(std::max(n, 1), g_n, wave);
+  h->grid_m = blocks_for_rows(std::max(m, 1), g_m, wave);
+  // The CG kernel is persistent: its grid is the co-resident block count,
+  // the smaller of the two precisions' occupancy.
+  int occ = 1 << 30;
+  for (int fp32 = 0; fp32 < 2; ++fp32) {
+    int o = 0;
+    if (fp32)
+      QP_TRY(dispatch_g(h->Q.G32, [&](auto g) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cg<decltype(g)::value, float>,
+                                                      kCgBlock, 0);
+      }));
+    else
+      QP_TRY(dispatch_g(h->Q.G64, [&](auto g) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cg<decltype(g)::value, double>,
+                                                      kCgBlock, 0);
+      }));
+    occ = std::min(occ, o);
+  }
   CUDA_TRY(cudaGetLastError());
   if (occ < 1) {
     set_error("CG kernel cannot be resident");
     return QP_ERR_CUDA;
   }
-  h->grid_cg = blocks_for_rows(n, h->Q.G, occ * h->num_sms, kCgBlock);
+  h->grid_cg = blocks_for_rows(n, std::min(h->Q.G64, h->Q.G32), occ * h->num_sms, kCgBlock);
   const int gmax = std::max({h->grid_n, h->grid_m, h->grid_vec, h->grid_cg});
   QP_TRY(dalloc(h, &h->part_cg, size_t(2) * h->grid_cg));
+  QP_TRY(dalloc(h, &h->part_r0, size_t(h->grid_n)));
   QP_TRY(dalloc(h, &h->part_n, size_t(h->grid_n) * kPartStride));
   QP_TRY(dalloc(h, &h->part_m, size_t(h->grid_m) * kPartStride));
   QP_TRY(dalloc(h, &h->part_rn, size_t(gmax)));
@@ -556,9 +688,167 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   std::memset(h->h_st, 0, sizeof(DevState));
   CUDA_TRY(cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
   CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->stream));
-  CUDA_TRY(cudaMemsetAsync(h->x0, 0, N * sizeof(double), h->stream));
-  CUDA_TRY(cudaMemsetAsync(h->y0, 0, std::max<size_t>(M, 1) * sizeof(double), h->stream));
+  QP_TRY(check_launch());
   return sync(h);
+}
+
+// Set-up of a fresh solve in precision T: start point, ||A||_2, step sizes,
+// relKKT of the start point.
+template <class T>
+qp_status start_solve(qp_handle* h, const qp_options* o) {
+  VecSet<T>& v = vecs<T>(h);
+  const bool warm = o->warm_start == 1 && h->warm_set;
+  if (warm && std::is_same<T, float>::value) {
+    convert(h, h->v64.x0, h->v32.x0, h->n);
+    convert(h, h->v64.y0, h->v32.y0, h->m);
+  }
+  k_init_vectors<T><<<h->grid_vec, kBlock, 0, h->stream>>>(
+      v.x, v.x_avg, v.x_anchor, warm ? v.x0 : nullptr, h->n, v.y, v.y_avg, v.y_anchor,
+      warm ? v.y0 : nullptr, h->m);
+  QP_TRY(recompute_caches<T>(h));
+  QP_TRY(launch_setup<T>(h, o->power_iters, 1));
+  QP_TRY(launch_eval<T>(h, 0));
+  return check_launch();
+}
+
+// Chunks of eval_freq iterations (each with one relKKT evaluation) until the
+// state says done, a device wait gave up, or the time limit passes.  Sets the
+// termination code in *term (-1 while not terminated).
+template <class T>
+qp_status run_chunks(qp_handle* h, const qp_options* o, bool timing,
+                     std::chrono::steady_clock::time_point t0, qp_info* info, int* term) {
+  // Graph replay normally; with kernel_timing the same chunk is launched
+  // directly so that events can bracket each CG launch on its stream.
+  if (timing) QP_TRY(ensure_events(h, o->eval_freq));
+  else QP_TRY(ensure_chunk<T>(h, o->eval_freq));
+  const int pi = std::is_same<T, double>::value ? 0 : 1;
+  cudaError_t timing_error = cudaSuccess;
+  while (true) {
+    if (timing) {
+      QP_TRY(enqueue_chunk<T>(h, o->eval_freq, h->coop_ok, h->ev.data()));
+      QP_TRY(check_launch());
+    } else {
+      CUDA_TRY(cudaGraphLaunch(h->chunk_exec[pi], h->stream));
+    }
+    QP_TRY(sync(h));
+    const DevState& s = *h->h_st;
+    qp_trace_entry te{};
+    te.k = s.k_total;
+    te.kkt_cur = s.kkt_cur[3];
+    te.kkt_avg = s.kkt_avg[3];
+    te.omega = s.omega;
+    te.restart = s.last_restart;
+    te.cg_last = int32_t(s.last_cg);
+    h->trace.push_back(te);
+    if (timing) {
+      for (int k = 0; k < o->eval_freq; ++k) {
+        float ms = 0.f;
+        const cudaError_t e = cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]);
+        if (e == cudaSuccess)
+          info->cg_kernel_ms += ms;
+        else if (timing_error == cudaSuccess)
+          timing_error = e;
+      }
+      cudaGetLastError();
+    }
+    if (s.err) {
+      set_error("a device grid barrier timed out");
+      return QP_ERR_DEVICE_TIMEOUT;
+    }
+    if (s.done) {
+      *term = s.done - 1;
+      break;
+    }
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > o->time_limit_s) {
+      *term = QP_TERM_TIME_LIMIT;  // returned_avg / kkt_ret describe the last evaluation
+      break;
+    }
+  }
+  if (timing_error != cudaSuccess) info->cg_kernel_ms = -double(int(timing_error));
+  return QP_OK;
+}
+
+// Mixed path, end of the FP32 phase: the returned iterate becomes the FP64
+// current iterate, its relKKT is evaluated with the FP64 data, and (when it
+// misses tol and refinement is on) an FP64 epoch continues from it.
+qp_status promote_and_refine(qp_handle* h, const qp_options* o, bool timing,
+                             std::chrono::steady_clock::time_point t0, qp_info* info, int* term) {
+  const bool avg = h->h_st->returned_avg != 0;
+  info->mixed_iterations = h->h_st->k_total;
+  info->mixed_relkkt = h->h_st->kkt_ret[3];
+  convert(h, avg ? h->v32.x_avg : h->v32.x, h->v64.x, h->n);
+  convert(h, avg ? h->v32.y_avg : h->v32.y, h->v64.y, h->m);
+  CUDA_TRY(cudaMemcpyAsync(h->v64.x_anchor, h->v64.x, size_t(h->n) * sizeof(double),
+                           cudaMemcpyDeviceToDevice, h->stream));
+  if (h->m > 0)
+    CUDA_TRY(cudaMemcpyAsync(h->v64.y_anchor, h->v64.y, size_t(h->m) * sizeof(double),
+                             cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->v64.x_avg, 0, size_t(h->n) * sizeof(double), h->stream));
+  if (h->m > 0)
+    CUDA_TRY(cudaMemsetAsync(h->v64.y_avg, 0, size_t(h->m) * sizeof(double), h->stream));
+  QP_TRY(recompute_caches<double>(h));
+  QP_TRY(launch_eval<double>(h, 2));
+  QP_TRY(check_launch());
+  QP_TRY(read_state(h));
+  DevState& d = *h->h_st;
+  info->check_relkkt = d.kkt_cur[3];
+  for (int k = 0; k < 6; ++k) d.kkt_ret[k] = d.kkt_cur[k];
+  d.returned_avg = 0;
+  h->active_prec = kPrecFp64;
+  if (*term == QP_TERM_SOLVED && !(d.kkt_cur[3] <= o->tol) && o->refine) {
+    // FP64 refinement: a new epoch at the promoted iterate.
+    d.j = 0;
+    d.eps = 0.0;
+    d.kkt_anchor = d.kkt_cur[3];
+    d.kkt_prev_cand = INFINITY;
+    d.relkkt_last = d.kkt_cur[3];
+    d.done = 0;
+    d.err = 0;
+    d.restart_pending = 0;
+    d.iter_active = 0;
+    const long long k0 = d.k_total;
+    QP_TRY(write_state(h));
+    *term = -1;
+    QP_TRY(run_chunks<double>(h, o, timing, t0, info, term));
+    info->refine_iterations = h->h_st->k_total - k0;
+  } else {
+    QP_TRY(write_state(h));
+  }
+  return QP_OK;
+}
+
+template <class T>
+qp_status solve_impl(qp_handle* h, const qp_options* o, std::chrono::steady_clock::time_point t0,
+                     qp_info* info, int* term) {
+  const bool timing = o->kernel_timing != 0;
+  if (o->warm_start == 2) {
+    // resume a state set by qp_set_state: keep every scalar, clear flags
+    QP_TRY(read_state(h));
+    h->h_st->done = 0;
+    h->h_st->err = 0;
+    h->h_st->restart_pending = 0;
+    fill_dev_options(h, o, &h->h_st->opt);
+    QP_TRY(write_state(h));
+    launch_prepare<T>(h);  // the CG start of this precision (its partials are shared)
+  } else {
+    QP_TRY(start_solve<T>(h, o));
+  }
+  QP_TRY(read_state(h));
+  info->setup_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  h->active_prec = std::is_same<T, double>::value ? kPrecFp64 : kPrecMixed;
+  if (h->h_st->err) {
+    set_error("a device grid barrier timed out");
+    return QP_ERR_DEVICE_TIMEOUT;
+  }
+  if (h->h_st->done)
+    *term = h->h_st->done - 1;
+  else
+    QP_TRY(run_chunks<T>(h, o, timing, t0, info, term));
+  if (std::is_same<T, float>::value && *term != QP_TERM_NUMERICAL_ERROR)
+    QP_TRY(promote_and_refine(h, o, timing, t0, info, term));
+  return QP_OK;
 }
 
 }  // namespace
@@ -607,6 +897,8 @@ void qp_options_default(qp_options* o) {
   o->eta = 0.0;
   o->kernel_timing = 0;
   o->debug_flags = 0;
+  o->precision = QP_PREC_FP64;
+  o->refine = 1;
 }
 
 qp_status qp_create(qp_handle** out, int32_t n, int32_t m, int32_t m_eq, const int32_t* Q_rowptr,
@@ -658,7 +950,7 @@ void qp_destroy(qp_handle* h) {
   if (!h) return;
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  destroy_chunk(h);
+  destroy_chunks(h);
   for (auto e : h->ev) cudaEventDestroy(e);
   for (auto& a : h->allocs) {
     if (h->has_alloc)
@@ -686,97 +978,21 @@ qp_status qp_solve(qp_handle* h, const qp_options* o, qp_info* info_out) {
   h->solved = false;
   qp_info info{};
   info.termination = QP_TERM_NONE;
-  const bool timing = o->kernel_timing != 0;
-  cudaError_t timing_error = cudaSuccess;
-
-  // ---- set-up: options, start point, ||A||_2, step sizes, relKKT(z0)
-  QP_TRY(write_options(h, o));
-  if (o->warm_start == 2) {
-    // resume a state set by qp_set_state: keep every scalar, clear flags
-    QP_TRY(read_state(h));
-    h->h_st->done = 0;
-    h->h_st->err = 0;
-    h->h_st->restart_pending = 0;
-    fill_dev_options(h, o, &h->h_st->opt);
-    QP_TRY(write_state(h));
-  } else {
-    const double* x0 = (o->warm_start == 1 && h->warm_set) ? h->x0 : nullptr;
-    const double* y0 = (o->warm_start == 1 && h->warm_set) ? h->y0 : nullptr;
-    k_init_vectors<<<h->grid_vec, kBlock, 0, h->stream>>>(h->x, h->x_avg, h->x_anchor, x0, h->n,
-                                                          h->y, h->y_avg, h->y_anchor, y0, h->m);
-    QP_TRY(recompute_caches(h));
-    QP_TRY(launch_setup(h, o->power_iters, 1));
-    QP_TRY(launch_eval(h, 0));
-    QP_TRY(check_launch());
-  }
-  QP_TRY(read_state(h));
-  const auto t_setup = std::chrono::steady_clock::now();
-  info.setup_ms = std::chrono::duration<double, std::milli>(t_setup - t0).count();
-
-  qp_status status = QP_OK;
+  info.precision = o->precision;
   int term = -1;
-  if (h->h_st->err) status = QP_ERR_DEVICE_TIMEOUT;
-  else if (h->h_st->done) term = h->h_st->done - 1;
-
-  // ---- chunks of eval_freq iterations, one relKKT evaluation each
-  if (status == QP_OK && term < 0) {
-    // Graph replay normally; with kernel_timing the same chunk is launched
-    // directly so that events can bracket each CG launch on its stream.
-    if (timing) QP_TRY(ensure_events(h, o->eval_freq));
-    else QP_TRY(ensure_chunk(h, o->eval_freq));
-    while (true) {
-      if (timing) {
-        QP_TRY(enqueue_chunk(h, o->eval_freq, h->coop_ok, h->ev.data()));
-        QP_TRY(check_launch());
-      } else {
-        CUDA_TRY(cudaGraphLaunch(h->chunk_exec, h->stream));
-      }
-      QP_TRY(sync(h));
-      const DevState& s = *h->h_st;
-      qp_trace_entry te{};
-      te.k = s.k_total;
-      te.kkt_cur = s.kkt_cur[3];
-      te.kkt_avg = s.kkt_avg[3];
-      te.omega = s.omega;
-      te.restart = s.last_restart;
-      te.cg_last = int32_t(s.last_cg);
-      h->trace.push_back(te);
-      if (timing) {
-        for (int k = 0; k < o->eval_freq; ++k) {
-          float ms = 0.f;
-          const cudaError_t te = cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]);
-          if (te == cudaSuccess) {
-            info.cg_kernel_ms += ms;
-          } else if (timing_error == cudaSuccess) {
-            timing_error = te;
-          }
-        }
-        cudaGetLastError();
-      }
-      if (s.err) {
-        status = QP_ERR_DEVICE_TIMEOUT;
-        break;
-      }
-      if (s.done) {
-        term = s.done - 1;
-        break;
-      }
-      const double el =
-          std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-      if (el > o->time_limit_s) {
-        term = QP_TERM_TIME_LIMIT;  // returned_avg / kkt_ret describe the last evaluation
-        break;
-      }
-    }
-  }
+  QP_TRY(write_options(h, o));
+  const qp_status status = o->precision == QP_PREC_MIXED
+                               ? solve_impl<float>(h, o, t0, &info, &term)
+                               : solve_impl<double>(h, o, t0, &info, &term);
+  if (status != QP_OK && status != QP_ERR_DEVICE_TIMEOUT) return status;
+  const std::string keep = g_last_error;
+  QP_TRY(read_state(h));
   QP_TRY(end_call(h));
+  g_last_error = keep;
   fill_info_from_state(h, &info);
   info.termination = term;
   info.device_error = h->h_st->err;
-  if (timing && timing_error != cudaSuccess) {
-    info.cg_kernel_ms = -double(int(timing_error));  // timing unavailable: negative error code
-  }
-  if (timing) {
+  if (o->kernel_timing) {
     // launches that did work, and the Q products inside them
     info.cg_kernel_launches = h->h_st->k_total;
     info.cg_kernel_spmvs = h->h_st->spmv_total;
@@ -786,7 +1002,6 @@ qp_status qp_solve(qp_handle* h, const qp_options* o, qp_info* info_out) {
   h->info = info;
   h->solved = (status == QP_OK);
   if (info_out) *info_out = info;
-  if (status == QP_ERR_DEVICE_TIMEOUT) set_error("a device grid barrier timed out");
   return status;
 }
 
@@ -800,10 +1015,10 @@ qp_status qp_get_solution(const qp_handle* h, double* x, double* y) {
   CUDA_TRY(cudaSetDevice(h->device));
   const bool avg = h->info.returned_avg != 0;
   if (x)
-    CUDA_TRY(cudaMemcpyAsync(x, avg ? h->x_avg : h->x, size_t(h->n) * sizeof(double),
+    CUDA_TRY(cudaMemcpyAsync(x, avg ? h->v64.x_avg : h->v64.x, size_t(h->n) * sizeof(double),
                              cudaMemcpyDeviceToHost, h->stream));
   if (y && h->m > 0)
-    CUDA_TRY(cudaMemcpyAsync(y, avg ? h->y_avg : h->y, size_t(h->m) * sizeof(double),
+    CUDA_TRY(cudaMemcpyAsync(y, avg ? h->v64.y_avg : h->v64.y, size_t(h->m) * sizeof(double),
                              cudaMemcpyDeviceToHost, h->stream));
   return sync(hh);
 }
@@ -825,11 +1040,15 @@ qp_status qp_get_trace(const qp_handle* h, qp_trace_entry* out, int64_t cap, int
 qp_status qp_set_warm_start(qp_handle* h, const double* x0, const double* y0) {
   if (!h) return QP_ERR_INVALID_ARG;
   QP_TRY(begin_call(h));
-  if (x0) QP_TRY(upload(h, h->x0, x0, size_t(h->n) * sizeof(double)));
-  else CUDA_TRY(cudaMemsetAsync(h->x0, 0, size_t(h->n) * sizeof(double), h->stream));
+  if (x0)
+    QP_TRY(upload(h, h->v64.x0, x0, size_t(h->n) * sizeof(double)));
+  else
+    CUDA_TRY(cudaMemsetAsync(h->v64.x0, 0, size_t(h->n) * sizeof(double), h->stream));
   if (h->m > 0) {
-    if (y0) QP_TRY(upload(h, h->y0, y0, size_t(h->m) * sizeof(double)));
-    else CUDA_TRY(cudaMemsetAsync(h->y0, 0, size_t(h->m) * sizeof(double), h->stream));
+    if (y0)
+      QP_TRY(upload(h, h->v64.y0, y0, size_t(h->m) * sizeof(double)));
+    else
+      CUDA_TRY(cudaMemsetAsync(h->v64.y0, 0, size_t(h->m) * sizeof(double), h->stream));
   }
   h->warm_set = true;
   QP_TRY(sync(h));
@@ -840,14 +1059,36 @@ qp_status qp_get_state(const qp_handle* hc, const qp_state_vectors* v, qp_state_
   if (!hc) return QP_ERR_INVALID_ARG;
   qp_handle* h = const_cast<qp_handle*>(hc);
   QP_TRY(begin_call(h));
-  const size_t nb = size_t(h->n) * sizeof(double), mb = size_t(h->m) * sizeof(double);
+  QP_TRY(sync(h));
+  const size_t N = size_t(h->n), M = size_t(h->m);
   if (v) {
-    const std::pair<double*, double*> nv[] = {{v->x, h->x}, {v->x_avg, h->x_avg}, {v->x_anchor, h->x_anchor}};
-    const std::pair<double*, double*> mv[] = {{v->y, h->y}, {v->y_avg, h->y_avg}, {v->y_anchor, h->y_anchor}};
-    for (auto& pr : nv)
-      if (pr.first) CUDA_TRY(cudaMemcpyAsync(pr.first, pr.second, nb, cudaMemcpyDeviceToHost, h->stream));
-    for (auto& pr : mv)
-      if (pr.first && mb) CUDA_TRY(cudaMemcpyAsync(pr.first, pr.second, mb, cudaMemcpyDeviceToHost, h->stream));
+    if (h->active_prec == kPrecMixed) {
+      // widen the FP32 iterate on the host
+      std::vector<float> tmp(std::max<size_t>(std::max(N, M), 1));
+      const std::pair<double*, float*> all[] = {
+          {v->x, h->v32.x}, {v->x_avg, h->v32.x_avg}, {v->x_anchor, h->v32.x_anchor},
+          {v->y, h->v32.y}, {v->y_avg, h->v32.y_avg}, {v->y_anchor, h->v32.y_anchor}};
+      for (int i = 0; i < 6; ++i) {
+        const size_t cnt = i < 3 ? N : M;
+        if (!all[i].first || cnt == 0) continue;
+        CUDA_TRY(cudaMemcpy(tmp.data(), all[i].second, cnt * sizeof(float),
+                            cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < cnt; ++k) all[i].first[k] = double(tmp[k]);
+      }
+    } else {
+      const std::pair<double*, double*> nv[] = {
+          {v->x, h->v64.x}, {v->x_avg, h->v64.x_avg}, {v->x_anchor, h->v64.x_anchor}};
+      const std::pair<double*, double*> mv[] = {
+          {v->y, h->v64.y}, {v->y_avg, h->v64.y_avg}, {v->y_anchor, h->v64.y_anchor}};
+      for (auto& pr : nv)
+        if (pr.first)
+          CUDA_TRY(cudaMemcpyAsync(pr.first, pr.second, N * sizeof(double),
+                                   cudaMemcpyDeviceToHost, h->stream));
+      for (auto& pr : mv)
+        if (pr.first && M)
+          CUDA_TRY(cudaMemcpyAsync(pr.first, pr.second, M * sizeof(double),
+                                   cudaMemcpyDeviceToHost, h->stream));
+    }
   }
   QP_TRY(read_state(h));
   if (s) {
@@ -874,18 +1115,27 @@ qp_status qp_set_state(qp_handle* h, const qp_state_vectors* v, const qp_state_s
   }
   QP_TRY(begin_call(h));
   const size_t nb = size_t(h->n) * sizeof(double), mb = size_t(h->m) * sizeof(double);
-  const std::pair<const double*, double*> nv[] = {{v->x, h->x}, {v->x_avg, h->x_avg}, {v->x_anchor, h->x_anchor}};
-  const std::pair<const double*, double*> mv[] = {{v->y, h->y}, {v->y_avg, h->y_avg}, {v->y_anchor, h->y_anchor}};
+  const std::pair<const double*, double*> nv[] = {
+      {v->x, h->v64.x}, {v->x_avg, h->v64.x_avg}, {v->x_anchor, h->v64.x_anchor}};
+  const std::pair<const double*, double*> mv[] = {
+      {v->y, h->v64.y}, {v->y_avg, h->v64.y_avg}, {v->y_anchor, h->v64.y_anchor}};
   for (auto& pr : nv) {
-    if (pr.first) QP_TRY(upload(h, pr.second, pr.first, nb));
-    else CUDA_TRY(cudaMemsetAsync(pr.second, 0, nb, h->stream));
+    if (pr.first)
+      QP_TRY(upload(h, pr.second, pr.first, nb));
+    else
+      CUDA_TRY(cudaMemsetAsync(pr.second, 0, nb, h->stream));
   }
   for (auto& pr : mv) {
     if (!mb) continue;
-    if (pr.first) QP_TRY(upload(h, pr.second, pr.first, mb));
-    else CUDA_TRY(cudaMemsetAsync(pr.second, 0, mb, h->stream));
+    if (pr.first)
+      QP_TRY(upload(h, pr.second, pr.first, mb));
+    else
+      CUDA_TRY(cudaMemsetAsync(pr.second, 0, mb, h->stream));
   }
-  QP_TRY(recompute_caches(h));
+  // Both precisions hold the state: the FP32 copy is the rounded FP64 one.
+  convert_state<double, float>(h);
+  QP_TRY(recompute_caches<float>(h));
+  QP_TRY(recompute_caches<double>(h));  // last: the FP64 CG start owns the shared partials
   QP_TRY(check_launch());
   QP_TRY(read_state(h));
   DevState& d = *h->h_st;
@@ -906,6 +1156,7 @@ qp_status qp_set_state(qp_handle* h, const qp_state_vectors* v, const qp_state_s
   d.restart_pending = 0;
   d.iter_active = 0;
   QP_TRY(write_state(h));
+  h->active_prec = kPrecFp64;
   return end_call(h);
 }
 
@@ -921,16 +1172,28 @@ qp_status qp_iterate(qp_handle* h, const qp_options* o, int64_t iters) {
   d.err = 0;
   QP_TRY(write_state(h));
   CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->stream));
+  const bool mixed = o->precision == QP_PREC_MIXED;
+  if (mixed != (h->active_prec == kPrecMixed)) {
+    // iterating in the other precision: bring its copy of the iterate over
+    if (mixed)
+      convert_state<double, float>(h);
+    else
+      convert_state<float, double>(h);
+  }
+  QP_TRY(mixed ? recompute_caches<float>(h) : recompute_caches<double>(h));
   for (int64_t k = 0; k < iters; ++k) {
-    qp_status s = launch_iteration(h, h->coop_ok);
-    if (s == QP_OK) s = check_launch();
+    auto go = [&](bool coop) {
+      qp_status s = mixed ? launch_iteration<float>(h, coop) : launch_iteration<double>(h, coop);
+      return s == QP_OK ? check_launch() : s;
+    };
+    qp_status s = go(h->coop_ok);
     if (s != QP_OK && h->coop_ok) {
       h->coop_ok = false;
-      s = launch_iteration(h, false);
-      if (s == QP_OK) s = check_launch();
+      s = go(false);
     }
     if (s != QP_OK) return s;
   }
+  h->active_prec = mixed ? kPrecMixed : kPrecFp64;
   QP_TRY(read_state(h));
   QP_TRY(end_call(h));
   if (h->h_st->err) {
@@ -943,7 +1206,10 @@ qp_status qp_iterate(qp_handle* h, const qp_options* o, int64_t iters) {
 qp_status qp_evaluate(qp_handle* h, double kkt_cur[6], double kkt_avg[6]) {
   if (!h) return QP_ERR_INVALID_ARG;
   QP_TRY(begin_call(h));
-  QP_TRY(launch_eval(h, 2));
+  if (h->active_prec == kPrecMixed)
+    QP_TRY(launch_eval<float>(h, 2));
+  else
+    QP_TRY(launch_eval<double>(h, 2));
   QP_TRY(check_launch());
   QP_TRY(read_state(h));
   for (int k = 0; k < 6; ++k) {
@@ -958,7 +1224,7 @@ qp_status qp_norm_A(qp_handle* h, int32_t iters, double* out) {
   QP_TRY(begin_call(h));
   QP_TRY(read_state(h));
   const DevState saved = *h->h_st;
-  QP_TRY(launch_setup(h, iters, 0));
+  QP_TRY(launch_setup<double>(h, iters, 0));
   QP_TRY(check_launch());
   QP_TRY(read_state(h));
   *out = h->h_st->norm_A;

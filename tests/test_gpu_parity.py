@@ -6,7 +6,11 @@ in fused multiply-adds):
   * one iteration from a shared state: 1e-10 relative (infinity norm);
   * end to end: both reach relKKT <= tol, the oracle re-scores the GPU
     solution at <= tol, the restart decisions agree, and the objectives
-    agree within 1e-4 relative.
+    agree within 1e-4 relative.  The solver's own relKKT of its result
+    agrees with the oracle's re-score to 1e-9 relative or 1e-12 absolute:
+    relKKT's numerators (Ax - b, Qx + A'y + c, the gap) cancel near a
+    solution, and two FP64 evaluations that sum in different orders agree
+    to a few ulps of the terms, not of the small difference.
 """
 import json
 import math
@@ -182,8 +186,14 @@ def test_end_to_end_matches_oracle(built, name, tol):
     assert info["termination"] == L.TERM_SOLVED
     rescored = O.relkkt(P, x, y)
     assert rescored.relkkt <= tol
-    assert info["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-15)
+    assert info["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-12)
     assert rescored.primal_obj == pytest.approx(ores.kkt.primal_obj, rel=1e-4, abs=1e-8)
+    if name == "unconstrained":
+        # m = 0 gives ||A|| = 0, so tau = 1/(2 eps_zero) = 5e9 and the adaptive CG
+        # tolerance eps/tau sits at the rounding level of r0: step counts then
+        # depend on summation order and only the result is comparable.
+        assert _relerr(x, ores.x) <= 1e-6
+        return
     # same trajectory: iteration count, restarts, CG steps and restart decisions
     trace = s.trace()
     orestarts = [(r["k"], int(r["restart"]) * (2 if r["cand_avg"] else 1)) for r in ores.trace[1:]]
@@ -300,3 +310,55 @@ def test_full_size_solve_matches_oracle_trace(big):
     assert info["cg_steps"] == g["cg_steps"]
     assert rescored.primal_obj == pytest.approx(g["primal_obj"], rel=1e-4)
     assert info["norm_A"] == pytest.approx(1.0 / (2.0 * g["eta"]), rel=1e-12)
+
+
+# ------------------------------------------------------------- mixed precision
+# FP32 values/iterates/SpMVs with FP64-accurate reductions: one iteration
+# from a shared state agrees with the FP64 oracle to 1e-5 relative; a solve
+# ends with an FP64 re-evaluation (and FP64 refinement if needed), so the
+# oracle re-scores its result at <= tol.
+MIXED_ITER_CASES = ["dense_small", "dense_small_eq", "sparse_small", "ragged_eq", "empty_rows"]
+
+
+@pytest.mark.parametrize("name", MIXED_ITER_CASES)
+@pytest.mark.parametrize("n_cg", [1, 3])
+def test_mixed_one_iteration_matches_oracle(built, name, n_cg):
+    inst, P, s = built(name)
+    st = _shared_state(inst, P, 4)
+    s.set_state(st)
+    s.iterate(1, cg_mode=L.CG_FIXED, cg_fixed_n=n_cg, precision=L.PREC_MIXED)
+    got = s.get_state()
+    ost = _oracle_state(st)
+    O.inner_step(P, ost, O.OracleOptions(cg_mode=O.CG_FIXED, cg_fixed_n=n_cg))
+    for key in ("x", "y", "x_avg", "y_avg"):
+        assert _relerr(got[key], getattr(ost, key)) <= 1e-5, key
+    assert got["cg_total"] == ost.cg_total
+
+
+@pytest.mark.parametrize("name,tol", [("dense_small", 1e-6), ("dense_small_eq", 1e-6),
+                                      ("sparse_small", 1e-4), ("ragged_eq", 1e-4),
+                                      ("unconstrained", 1e-6), ("all_equalities", 1e-6),
+                                      ("empty_rows", 1e-6), ("single", 1e-8)])
+def test_mixed_solve_meets_tolerance_in_fp64(built, name, tol):
+    inst, P, s = built(name)
+    ores = O.solve(P, O.OracleOptions(tol=tol))
+    info = s.solve(tol=tol, precision=L.PREC_MIXED)
+    x, y = s.solution()
+    assert info["termination"] == L.TERM_SOLVED
+    rescored = O.relkkt(P, x, y)
+    assert rescored.relkkt <= tol
+    assert info["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-12)
+    assert info["check_relkkt"] >= 0.0 and info["mixed_iterations"] > 0
+    assert rescored.primal_obj == pytest.approx(ores.kkt.primal_obj, rel=1e-4, abs=1e-8)
+
+
+def test_mixed_full_size_meets_tolerance(big):
+    inst, P, s = big
+    info = s.solve(tol=1e-4, precision=L.PREC_MIXED)
+    x, y = s.solution()
+    assert info["termination"] == L.TERM_SOLVED
+    rescored = O.relkkt(P, x, y)
+    assert rescored.relkkt <= 1e-4
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    assert rescored.primal_obj == pytest.approx(g["primal_obj"], rel=1e-4)
