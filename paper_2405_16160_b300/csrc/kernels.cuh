@@ -416,22 +416,50 @@ __device__ __forceinline__ void spmv2_rows(const CsrT<T>& M, const T* v1, const 
   }
 }
 
+// Block partial of r0'r0, and the grid total written by the last block to
+// finish (ticket counter, reset by that block) into part[gridDim.x], so the
+// CG kernel reads one value.  The summation order is fixed: the last block
+// reduces all partials in index order.
+template <class A>
+__device__ __forceinline__ void store_and_finish_dot(A acc, double* part, unsigned int* ticket) {
+  __shared__ int s_last;
+  block_dot_store(acc, part + blockIdx.x);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x < 32) {
+    __threadfence();
+    const double total = warp_reduce_dot_partials(part, gridDim.x, A());
+    if (threadIdx.x == 0) {
+      part[gridDim.x] = total;
+      *ticket = 0u;
+      __threadfence();
+    }
+  }
+}
+
 // ------------------------------------------------------------- CG (Section 2)
 // Inexact CG on (Q + I/tau) x = x^k/tau - c - A'y^k warm-started at x^k.  Its
 // initial residual simplifies to r0 = -(Q x^k + c + A'y^k); the kernel that
 // produces A'y^k (k_atv, or k_prepare after a set-up, evaluation or restart)
-// also forms r0 = p0 and the block partials of r0'r0 (part_r0, g0 blocks),
-// from a tracked qx = Q x.  Phases per CG step:
+// also forms r0 = p0 and r0'r0 (one value, r0r0) from a tracked qx = Q x.  Phases per CG step:
 //   [A] q = Qp + p/tau, p'q
 //   [B] x += a p, qx += a (q - p/tau), r -= a q, r'r
 //   [C] p = r + b p   (only when CG continues)
 // so each step costs one product with Q.  alpha, beta, the stop test and all
 // dot products are FP64-accurate for both value types.  part holds
 // 2 * gridDim.x doubles.
+// Resident CG blocks of 512 threads per SM (register budget per thread =
+// 65536 / (512 * blocks)).  Four FP32 blocks would need 32 registers and
+// spill; three measured faster.
+constexpr int kCgBlocksPerSm = 3;
+
 template <int G, class T>
-__global__ void __launch_bounds__(kCgBlock, 3) k_cg(CsrT<T> Q, T* x, T* r, T* p, T* q, T* qx,
-                                                    const double* part_r0, int g0, double* part,
-                                                    DevState* st, GridBarrier* bar, int n) {
+__global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
+    k_cg(CsrT<T> Q, T* x, T* r, T* p, T* q, T* qx, const double* r0r0, double* part,
+         DevState* st, GridBarrier* bar, int n) {
   using A = typename Acc<T>::type;
   const bool active = running(st) && st->k_total < st->opt.max_iter;
   if (!active) {
@@ -450,7 +478,7 @@ __global__ void __launch_bounds__(kCgBlock, 3) k_cg(CsrT<T> Q, T* x, T* r, T* p,
   double* part_rr = part;
   double* part_pq = part + gridDim.x;
   const long long t0 = grid_tid(), nt = grid_threads();
-  double rr = block_all_reduce<A>(part_r0, g0);
+  double rr = __ldcg(r0r0);
 
   int steps = 0;
   bool numerr = false;
@@ -542,7 +570,8 @@ __global__ void __launch_bounds__(kBlock) k_atv(CsrT<T> At, const T* __restrict_
                                                 const T* __restrict__ x, T* x_avg,
                                                 const T* __restrict__ qx,
                                                 const T* __restrict__ c, T* r, T* p,
-                                                double* part_r0, const DevState* st) {
+                                                double* part_r0, unsigned int* ticket,
+                                                const DevState* st) {
   if (!st->iter_active) return;
   const T inv_j = T(1.0 / (double)st->j);
   typename Acc<T>::type acc;
@@ -556,7 +585,7 @@ __global__ void __launch_bounds__(kBlock) k_atv(CsrT<T> At, const T* __restrict_
       acc.add_prod(ri, ri);
     }
   });
-  block_dot_store(acc, part_r0 + blockIdx.x);
+  store_and_finish_dot(acc, part_r0, ticket);
 }
 
 // r0 = p0 = -(qx + c + A'y) and r0'r0 partials, for the first CG after a
@@ -565,7 +594,7 @@ template <class T>
 __global__ void __launch_bounds__(kBlock) k_prepare(const T* __restrict__ qx,
                                                     const T* __restrict__ c,
                                                     const T* __restrict__ aty, T* r, T* p, int n,
-                                                    double* part_r0) {
+                                                    double* part_r0, unsigned int* ticket) {
   typename Acc<T>::type acc;
   for (long long i = grid_tid(); i < n; i += grid_threads()) {
     const T ri = -(qx[i] + c[i] + aty[i]);
@@ -573,7 +602,7 @@ __global__ void __launch_bounds__(kBlock) k_prepare(const T* __restrict__ qx,
     p[i] = ri;
     acc.add_prod(ri, ri);
   }
-  block_dot_store(acc, part_r0 + blockIdx.x);
+  store_and_finish_dot(acc, part_r0, ticket);
 }
 
 // Plain out = M v, optionally with per-block partial sums of out_i^2 (double).

@@ -132,7 +132,9 @@ struct qp_handle {
   GridBarrier* bar = nullptr;
   DevState* h_st = nullptr;  // pinned mirror
   int num_sms = 0;
-  int grid_n = 1, grid_m = 1, grid_cg = 1, grid_vec = 1;
+  int grid_n = 1, grid_m = 1, grid_vec = 1;
+  int grid_cg[2] = {1, 1};  // persistent CG grid per precision (FP64, FP32)
+  unsigned int* ticket = nullptr;  // last-block counter of the r0'r0 reduction
   bool coop_ok = true;
   bool warm_set = false;
   int active_prec = kPrecFp64;  // precision of the iterate last produced
@@ -250,7 +252,7 @@ qp_status launch_cg(qp_handle* h, bool coop) {
     constexpr int G = decltype(g)::value;
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3(h->grid_cg);
+    cfg.gridDim = dim3(h->grid_cg[std::is_same<T, double>::value ? 0 : 1]);
     cfg.blockDim = dim3(kCgBlock);
     cfg.stream = h->stream;
     if (coop) {
@@ -260,7 +262,7 @@ qp_status launch_cg(qp_handle* h, bool coop) {
       cfg.numAttrs = 1;
     }
     cudaLaunchKernelEx(&cfg, k_cg<G, T>, view<T>(h->Q), v.x, v.r, v.p, v.q, v.qx,
-                       (const double*)h->part_r0, h->grid_n, h->part_cg, h->st, h->bar,
+                       (const double*)(h->part_r0 + h->grid_n), h->part_cg, h->st, h->bar,
                        (int)h->n);
   });
 }
@@ -281,7 +283,8 @@ qp_status launch_atv(qp_handle* h) {
   return dispatch_g(lanes<T>(h->At), [&](auto g) {
     constexpr int G = decltype(g)::value;
     k_atv<G, T><<<h->grid_n, kBlock, 0, h->stream>>>(view<T>(h->At), v.y, v.aty, v.x, v.x_avg,
-                                                     v.qx, v.c, v.r, v.p, h->part_r0, h->st);
+                                                     v.qx, v.c, v.r, v.p, h->part_r0, h->ticket,
+                                                     h->st);
   });
 }
 
@@ -329,7 +332,8 @@ qp_status launch_restart(qp_handle* h) {
 template <class T>
 void launch_prepare(qp_handle* h) {
   VecSet<T>& v = vecs<T>(h);
-  k_prepare<T><<<h->grid_n, kBlock, 0, h->stream>>>(v.qx, v.c, v.aty, v.r, v.p, h->n, h->part_r0);
+  k_prepare<T><<<h->grid_n, kBlock, 0, h->stream>>>(v.qx, v.c, v.aty, v.r, v.p, h->n, h->part_r0,
+                                                    h->ticket);
 }
 
 template <class T>
@@ -650,32 +654,33 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   const int g_m = std::max(h->A.G64, h->A.G32);
   h->grid_n = blocks_for_rows(std::max(n, 1), g_n, wave);
   h->grid_m = blocks_for_rows(std::max(m, 1), g_m, wave);
-  // The CG kernel is persistent: its grid is the co-resident block count,
-  // the smaller of the two precisions' occupancy.
-  int occ = 1 << 30;
+  // The CG kernel is persistent: its grid is the co-resident block count of
+  // each precision's instantiation.
   for (int fp32 = 0; fp32 < 2; ++fp32) {
-    int o = 0;
+    int occ = 0;
     if (fp32)
       QP_TRY(dispatch_g(h->Q.G32, [&](auto g) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cg<decltype(g)::value, float>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<decltype(g)::value, float>,
                                                       kCgBlock, 0);
       }));
     else
       QP_TRY(dispatch_g(h->Q.G64, [&](auto g) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cg<decltype(g)::value, double>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<decltype(g)::value, double>,
                                                       kCgBlock, 0);
       }));
-    occ = std::min(occ, o);
+    CUDA_TRY(cudaGetLastError());
+    if (occ < 1) {
+      set_error("CG kernel cannot be resident");
+      return QP_ERR_CUDA;
+    }
+    h->grid_cg[fp32] = blocks_for_rows(n, fp32 ? h->Q.G32 : h->Q.G64, occ * h->num_sms, kCgBlock);
   }
-  CUDA_TRY(cudaGetLastError());
-  if (occ < 1) {
-    set_error("CG kernel cannot be resident");
-    return QP_ERR_CUDA;
-  }
-  h->grid_cg = blocks_for_rows(n, std::min(h->Q.G64, h->Q.G32), occ * h->num_sms, kCgBlock);
-  const int gmax = std::max({h->grid_n, h->grid_m, h->grid_vec, h->grid_cg});
-  QP_TRY(dalloc(h, &h->part_cg, size_t(2) * h->grid_cg));
-  QP_TRY(dalloc(h, &h->part_r0, size_t(h->grid_n)));
+  const int gcg = std::max(h->grid_cg[0], h->grid_cg[1]);
+  const int gmax = std::max({h->grid_n, h->grid_m, h->grid_vec, gcg});
+  QP_TRY(dalloc(h, &h->part_cg, size_t(2) * gcg));
+  QP_TRY(dalloc(h, &h->part_r0, size_t(h->grid_n) + 1));
+  QP_TRY(dalloc(h, &h->ticket, 1));
+  CUDA_TRY(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream));
   QP_TRY(dalloc(h, &h->part_n, size_t(h->grid_n) * kPartStride));
   QP_TRY(dalloc(h, &h->part_m, size_t(h->grid_m) * kPartStride));
   QP_TRY(dalloc(h, &h->part_rn, size_t(gmax)));
