@@ -140,6 +140,23 @@ def cg_kernel_bytes(nnz_q: int, n: int, launches: int, spmvs: int, cg_steps: int
     return spmvs * spmv + cg_steps * 8.0 * w * n + max(cg_steps - launches, 0) * 3.0 * w * n
 
 
+def _profiled_traffic():
+    """DRAM bytes per k_cg launch from the committed ncu capture, or None when
+    the kernel source has changed since that capture."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "k_cg_traffic.json")
+    src = os.path.join(ROOT, "paper_2405_16160_b300", "csrc", "kernels.cuh")
+    try:
+        with open(prof) as f:
+            rec = json.load(f)
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec.get("dram_bytes_per_launch_full_size") if rec.get("kernels_cuh_sha256_16") == sha \
+        else None
+
+
 def oracle_sample(inst, iters: int):
     """The oracle as it stands: set-up plus `iters` PDHCG iterations (with the
     relKKT evaluations they contain).  Returns (setup_s, per_iter_s)."""
@@ -276,11 +293,7 @@ def run_ours(args):
     launches = sum(i["cg_kernel_launches"] for i in kinfos)
     kernel_s = sum(i["cg_kernel_ms"] for i in kinfos) / 1e3
     achieved = bytes_total / kernel_s / 1e9 if kernel_s > 0 else None
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "k_cg_traffic.json")
-    if os.path.exists(prof):
-        with open(prof) as f:
-            traffic = json.load(f).get("dram_bytes_per_launch_full_size")
+    traffic = _profiled_traffic()
     setup_launches = 1 + 4 + 1 + 3 * 30 + 1 + 4
     chunk_launches = 3 * 64 + 4 + 3 + 1
     gpu_launches = args.steps * (setup_launches + 9 + trace_len * chunk_launches)
@@ -311,6 +324,9 @@ def run_ours(args):
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_total / max(launches, 1),
+                     "gathers_per_s": (sum(i["cg_kernel_spmvs"] for i in kinfos) * inst.nnz_Q
+                                       / kernel_s) if kernel_s > 0 else None,
+                     "gather_ceiling_per_s": 2.15e11,
                      "avg_launch_us": kernel_s / max(launches, 1) * 1e6,
                      "timing": "CUDA events around every k_cg launch (direct launches) in "
                                "solves run right after the timed region"},
