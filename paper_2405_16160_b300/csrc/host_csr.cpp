@@ -1,10 +1,44 @@
 #include "host_csr.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <numeric>
+#include <thread>
 
 namespace pdhcg {
+
+namespace {
+
+// Worker threads for `work` items: at most the hardware threads (<= 32) and
+// at least ~256K items each.
+int worker_count(int64_t work) {
+  const unsigned hc = std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
+  return int(std::max<int64_t>(1, std::min<int64_t>(hc, work / (int64_t(1) << 18))));
+}
+
+template <class F>
+void parallel_for(int T, F&& f) {
+  std::vector<std::thread> th;
+  for (int t = 1; t < T; ++t) th.emplace_back(f, t);
+  f(0);
+  for (auto& x : th) x.join();
+}
+
+// Row ranges [b[t], b[t+1]) holding about nnz/T entries each.
+std::vector<int32_t> split_rows(const int32_t* rowptr, int32_t rows, int T) {
+  std::vector<int32_t> b(size_t(T) + 1, rows);
+  b[0] = 0;
+  const int64_t nnz = rowptr[rows];
+  for (int t = 1; t < T; ++t) {
+    const int64_t target = nnz * t / T;
+    b[size_t(t)] = int32_t(std::lower_bound(rowptr, rowptr + rows + 1, target) - rowptr);
+    b[size_t(t)] = std::min(std::max(b[size_t(t)], b[size_t(t) - 1]), rows);
+  }
+  return b;
+}
+
+}  // namespace
 
 bool csr_validate(int32_t rows, int32_t cols, const int32_t* rowptr, const int32_t* col,
                   const double* val, std::string* why) {
@@ -20,12 +54,41 @@ bool csr_validate(int32_t rows, int32_t cols, const int32_t* rowptr, const int32
   const int64_t nnz = rowptr[rows];
   if (nnz < 0 || nnz >= (int64_t(1) << 31)) return fail("nnz out of int32 range");
   if (nnz > 0 && (!col || !val)) return fail("col or val is NULL");
-  for (int64_t k = 0; k < nnz; ++k) {
+  // Entries are checked in parallel chunks; the first bad entry is reported.
+  const int T = worker_count(nnz);
+  std::atomic<int64_t> first_bad(nnz);
+  parallel_for(T, [&](int t) {
+    const int64_t lo = nnz * t / T, hi = nnz * (t + 1) / T;
+    for (int64_t k = lo; k < hi; ++k)
+      if (col[k] < 0 || col[k] >= cols || !std::isfinite(val[k])) {
+        int64_t cur = first_bad.load();
+        while (k < cur && !first_bad.compare_exchange_weak(cur, k)) {
+        }
+        break;
+      }
+  });
+  const int64_t k = first_bad.load();
+  if (k < nnz) {
     if (col[k] < 0 || col[k] >= cols)
       return fail("column index out of range at entry " + std::to_string(k));
-    if (!std::isfinite(val[k])) return fail("non-finite value at entry " + std::to_string(k));
+    return fail("non-finite value at entry " + std::to_string(k));
   }
   return true;
+}
+
+bool csr_is_canonical(int32_t rows, const int32_t* rowptr, const int32_t* col) {
+  const int T = worker_count(rowptr[rows]);
+  const std::vector<int32_t> b = split_rows(rowptr, rows, T);
+  std::atomic<bool> ok(true);
+  parallel_for(T, [&](int t) {
+    for (int32_t i = b[size_t(t)]; i < b[size_t(t) + 1] && ok.load(std::memory_order_relaxed); ++i)
+      for (int64_t k = int64_t(rowptr[i]) + 1; k < rowptr[i + 1]; ++k)
+        if (col[k] <= col[k - 1]) {
+          ok = false;
+          break;
+        }
+  });
+  return ok.load();
 }
 
 HostCsr csr_canonical(int32_t rows, int32_t cols, const int32_t* rowptr, const int32_t* col,
@@ -68,16 +131,60 @@ HostCsr csr_canonical(int32_t rows, int32_t cols, const int32_t* rowptr, const i
 void csr_transpose(int32_t rows, int32_t cols, const int32_t* rowptr, const int32_t* col,
                    const double* val, int32_t* t_rowptr, int32_t* t_col, double* t_val) {
   const int64_t nnz = rowptr[rows];
-  std::fill(t_rowptr, t_rowptr + cols + 1, 0);
-  for (int64_t k = 0; k < nnz; ++k) t_rowptr[col[k] + 1]++;
-  for (int32_t j = 0; j < cols; ++j) t_rowptr[j + 1] += t_rowptr[j];
-  std::vector<int32_t> next(t_rowptr, t_rowptr + cols);
-  for (int32_t i = 0; i < rows; ++i)
-    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-      const int32_t dst = next[col[k]]++;
-      t_col[dst] = i;
-      t_val[dst] = val[k];
-    }
+  // Threads own row ranges; each keeps a column histogram of its range, so
+  // its entries land after those of every earlier range: the output is the
+  // stable (row-ordered) transpose for any thread count.
+  int T = worker_count(nnz);
+  T = int(std::max<int64_t>(1, std::min<int64_t>(T, (int64_t(1) << 26) / std::max(cols, 1))));
+  const std::vector<int32_t> b = split_rows(rowptr, rows, T);
+  std::vector<int32_t> cnt(size_t(T) * size_t(cols));
+  parallel_for(T, [&](int t) {
+    int32_t* c = cnt.data() + size_t(t) * cols;
+    std::fill(c, c + cols, 0);
+    for (int64_t k = rowptr[b[size_t(t)]]; k < rowptr[b[size_t(t) + 1]]; ++k) c[col[k]]++;
+  });
+  // Column totals and their exclusive scan, then per-thread start offsets.
+  t_rowptr[0] = 0;
+  {
+    const int TC = worker_count(int64_t(cols) * T);
+    std::vector<int64_t> block_sum(size_t(TC) + 1, 0);
+    parallel_for(TC, [&](int u) {
+      const int64_t lo = int64_t(cols) * u / TC, hi = int64_t(cols) * (u + 1) / TC;
+      int64_t s = 0;
+      for (int64_t j = lo; j < hi; ++j) {
+        int32_t tot = 0;
+        for (int t = 0; t < T; ++t) tot += cnt[size_t(t) * cols + j];
+        t_rowptr[j + 1] = tot;
+        s += tot;
+      }
+      block_sum[size_t(u) + 1] = s;
+    });
+    for (int u = 0; u < TC; ++u) block_sum[size_t(u) + 1] += block_sum[size_t(u)];
+    parallel_for(TC, [&](int u) {
+      const int64_t lo = int64_t(cols) * u / TC, hi = int64_t(cols) * (u + 1) / TC;
+      int64_t s = block_sum[size_t(u)];
+      for (int64_t j = lo; j < hi; ++j) {
+        int64_t start = s;
+        s += t_rowptr[j + 1];
+        t_rowptr[j + 1] = int32_t(s);
+        for (int t = 0; t < T; ++t) {
+          int32_t& c = cnt[size_t(t) * cols + j];
+          const int32_t here = c;
+          c = int32_t(start);
+          start += here;
+        }
+      }
+    });
+  }
+  parallel_for(T, [&](int t) {
+    int32_t* next = cnt.data() + size_t(t) * cols;
+    for (int32_t i = b[size_t(t)]; i < b[size_t(t) + 1]; ++i)
+      for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        const int32_t dst = next[col[k]]++;
+        t_col[dst] = i;
+        t_val[dst] = val[k];
+      }
+  });
 }
 
 bool csr_is_symmetric(const HostCsr& M, double rtol) {

@@ -525,7 +525,7 @@ qp_status upload(qp_handle* h, void* dst, const void* src, size_t bytes) {
   return QP_OK;
 }
 
-qp_status upload_matrix(qp_handle* h, DevMat* M, const HostCsr& H) {
+qp_status upload_matrix(qp_handle* h, DevMat* M, const CsrView& H) {
   M->rows = H.rows;
   M->nnz = H.nnz();
   M->G64 = group_size_for(M->nnz, H.rows, false);
@@ -534,9 +534,9 @@ qp_status upload_matrix(qp_handle* h, DevMat* M, const HostCsr& H) {
   QP_TRY(dalloc(h, &M->col, size_t(M->nnz)));
   QP_TRY(dalloc(h, &M->val, size_t(M->nnz)));
   QP_TRY(dalloc(h, &M->val32, size_t(M->nnz)));
-  QP_TRY(upload(h, M->rowptr, H.rowptr.data(), (size_t(H.rows) + 1) * sizeof(int32_t)));
-  QP_TRY(upload(h, M->col, H.col.data(), size_t(M->nnz) * sizeof(int32_t)));
-  QP_TRY(upload(h, M->val, H.val.data(), size_t(M->nnz) * sizeof(double)));
+  QP_TRY(upload(h, M->rowptr, H.rowptr, (size_t(H.rows) + 1) * sizeof(int32_t)));
+  QP_TRY(upload(h, M->col, H.col, size_t(M->nnz) * sizeof(int32_t)));
+  QP_TRY(upload(h, M->val, H.val, size_t(M->nnz) * sizeof(double)));
   if (M->nnz > 0)
     k_convert<double, float><<<h->grid_vec, kBlock, 0, h->stream>>>(M->val, M->val32,
                                                                     int(M->nnz));
@@ -616,20 +616,32 @@ qp_status validate_problem(int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr
 qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr,
                       const int32_t* Qc, const double* Qv, const int32_t* Ar, const int32_t* Ac,
                       const double* Av, const double* c, const double* b, uint32_t flags) {
-  HostCsr Qh = csr_canonical(n, n, Qr, Qc, Qv);
-  if ((flags & QP_CREATE_CHECK_SYMMETRY) && !csr_is_symmetric(Qh, 1e-12)) {
-    set_error("Q is not symmetric");
-    return QP_ERR_INVALID_ARG;
+  // Rows that are already sorted without duplicates are used in place;
+  // otherwise a canonical copy (sorted, duplicates summed) is made.
+  HostCsr Qc_, Ac_;
+  CsrView Qh{n, n, Qr, Qc, Qv}, Ah{m, n, Ar, Ac, Av};
+  if (!csr_is_canonical(n, Qr, Qc)) {
+    Qc_ = csr_canonical(n, n, Qr, Qc, Qv);
+    Qh = view_of(Qc_);
   }
-  HostCsr Ah = csr_canonical(m, n, Ar, Ac, Av);
+  if ((flags & QP_CREATE_CHECK_SYMMETRY)) {
+    if (Qc_.rowptr.empty()) Qc_ = csr_canonical(n, n, Qr, Qc, Qv);
+    if (!csr_is_symmetric(Qc_, 1e-12)) {
+      set_error("Q is not symmetric");
+      return QP_ERR_INVALID_ARG;
+    }
+  }
+  if (!csr_is_canonical(m, Ar, Ac)) {
+    Ac_ = csr_canonical(m, n, Ar, Ac, Av);
+    Ah = view_of(Ac_);
+  }
   HostCsr Th;
   Th.rows = n;
   Th.cols = m;
   Th.rowptr.resize(size_t(n) + 1);
   Th.col.resize(size_t(Ah.nnz()));
   Th.val.resize(size_t(Ah.nnz()));
-  csr_transpose(m, n, Ah.rowptr.data(), Ah.col.data(), Ah.val.data(), Th.rowptr.data(),
-                Th.col.data(), Th.val.data());
+  csr_transpose(m, n, Ah.rowptr, Ah.col, Ah.val, Th.rowptr.data(), Th.col.data(), Th.val.data());
 
   h->n = n;
   h->m = m;
@@ -641,7 +653,7 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
       int(std::max<int64_t>(1, std::min<int64_t>((std::max(n, m) + kBlock - 1) / kBlock, wave)));
   QP_TRY(upload_matrix(h, &h->Q, Qh));
   QP_TRY(upload_matrix(h, &h->A, Ah));
-  QP_TRY(upload_matrix(h, &h->At, Th));
+  QP_TRY(upload_matrix(h, &h->At, view_of(Th)));
   QP_TRY(alloc_vecs<double>(h));
   QP_TRY(alloc_vecs<float>(h));
   const size_t N = size_t(n), M = size_t(m);

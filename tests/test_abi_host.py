@@ -141,3 +141,23 @@ def test_create_without_gpu_reports_no_device(lib):
 def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(FileNotFoundError):
         L.load_library(str(tmp_path / "libpdhcg.so"))
+
+
+def test_parallel_transpose_matches_scipy_and_is_stable(lib):
+    # large enough for several worker threads (>= 2^18 entries each)
+    rng = np.random.default_rng(3)
+    rows, cols, per = 200_000, 150_000, 8
+    colidx = np.sort(rng.integers(0, cols, size=(rows, per)), axis=1)
+    keep = np.ones_like(colidx, dtype=bool)
+    keep[:, 1:] = colidx[:, 1:] != colidx[:, :-1]
+    counts = keep.sum(axis=1)
+    rowptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    col = colidx[keep].astype(np.int32)
+    val = rng.standard_normal(col.size)
+    tr, tc, tv = S.csr_transpose(rows, cols, rowptr, col, val)
+    M = sp.csr_matrix((val, col, rowptr), shape=(rows, cols))
+    ref = M.T.tocsr()
+    ref.sort_indices()
+    assert np.array_equal(tr, ref.indptr)
+    assert np.array_equal(tc, ref.indices)  # stable: each output row in input-row order
+    assert np.array_equal(tv, ref.data)
