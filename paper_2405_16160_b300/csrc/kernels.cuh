@@ -7,8 +7,9 @@
 //   k_dual  A x+ fused with the projected dual step, the A x cache and the
 //           running average of y (Algorithm 1, y-update and averages);
 //   k_atv   A' y+ (explicit transpose) fused with the running average of x.
-// Every eval_freq iterations: k_spmv (A' y~), k_kkt_n, k_kkt_m (relKKT terms
-// of Section 4 for the current iterate and the average), k_control (one warp:
+// Every eval_freq iterations: k_spmv (Q x, Q x~, A x~, A' y~), k_kkt_n, k_kkt_m
+// (relKKT terms of Section 4 for the current iterate and the average),
+// k_control (one warp:
 // termination and the restart tests), k_restart_n / k_restart_m /
 // k_restart_finish (restart to the candidate and the primal-weight update).
 //
@@ -53,12 +54,30 @@ constexpr unsigned kDebugBarrierNeverReleases = 1u;
 constexpr unsigned kKktNMaxMask = 0b10011100111u;  // 11 entries, see k_kkt_n
 constexpr unsigned kKktMMaxMask = 0b1011011u;      // 7 entries, see k_kkt_m
 
+// Rows with more than kLongRow entries are "long": a pre-pass splits them
+// into segments of kSegLen entries, one warp per segment, sums each row's
+// segments in index order (long_val), and the row kernels read that value.
+constexpr int kLongRow = 4096;
+constexpr int kSegLen = 2048;
+
 template <class T>
 struct CsrT {
   const int32_t* rowptr;
   const int32_t* col;
   const T* val;
   int32_t rows;
+  const int32_t* long_rows = nullptr;  // ascending ids of the long rows
+  const T* long_val = nullptr;         // their products, from the pre-pass
+  int32_t nlong = 0;
+};
+
+// Segment table of a matrix's long rows: segment s covers entries
+// [seg_begin[s], seg_end[s]); long row r owns segments [seg_ptr[r], seg_ptr[r+1]).
+struct LongRows {
+  const int32_t* seg_begin = nullptr;
+  const int32_t* seg_end = nullptr;
+  const int32_t* seg_ptr = nullptr;
+  int32_t nseg = 0, nlong = 0;
 };
 
 struct DevOptions {
@@ -337,10 +356,9 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int ti
 constexpr int kUnroll = 4;
 
 template <int G, class T>
-__device__ __forceinline__ T row_dot(const CsrT<T>& M, const T* v, int i, int sub) {
+__device__ __forceinline__ T row_dot(const CsrT<T>& M, const T* v, int b, int e, int sub) {
   T s = T(0);
-  const int e = __ldg(M.rowptr + i + 1);
-  for (int k = __ldg(M.rowptr + i) + sub; k < e; k += kUnroll * G) {
+  for (int k = b + sub; k < e; k += kUnroll * G) {
     int c[kUnroll];
     T a[kUnroll], xv[kUnroll];
 #pragma unroll
@@ -357,6 +375,20 @@ __device__ __forceinline__ T row_dot(const CsrT<T>& M, const T* v, int i, int su
   return s;
 }
 
+// Index of long row i in M.long_rows (binary search; only called for long rows).
+template <class T>
+__device__ __forceinline__ int long_slot(const CsrT<T>& M, int i) {
+  int lo = 0, hi = M.nlong - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(M.long_rows + mid) < i)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
 template <int G, class T, class F>
 __device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f) {
   constexpr int kRowsPerWarp = 32 / G;
@@ -366,54 +398,65 @@ __device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f) {
   const long long nw = grid_threads() >> 5;
   for (long long base = gw * kRowsPerWarp; base < M.rows; base += nw * kRowsPerWarp) {
     const int i = int(base) + lane / G;
-    T s = i < M.rows ? row_dot<G>(M, v, i, sub) : T(0);
+    T s = T(0);
+    if (i < M.rows) {
+      const int b = __ldg(M.rowptr + i), e = __ldg(M.rowptr + i + 1);
+      if (e - b > kLongRow) {
+        if (sub == 0) s = M.long_val[long_slot(M, i)];
+      } else {
+        s = row_dot<G>(M, v, b, e, sub);
+      }
+    }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += shfl_xor(s, o);
     if (i < M.rows) f(i, s, sub == 0);
   }
 }
 
-// Same walk, two vectors through one pass over the matrix row.
-template <int G, class T, class F>
-__device__ __forceinline__ void spmv2_rows(const CsrT<T>& M, const T* v1, const T* v2, F&& f) {
-  constexpr int kRowsPerWarp = 32 / G;
+template <class T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
+  return v;
+}
+
+// Long-row pre-pass, phase 1: one warp per segment (grid-stride over warps).
+template <class T>
+__device__ __forceinline__ void long_segments(const CsrT<T>& M, const T* v, const LongRows& L,
+                                              T* seg_part) {
   const int lane = threadIdx.x & 31;
-  const int sub = lane & (G - 1);
-  const long long gw = grid_tid() >> 5;
   const long long nw = grid_threads() >> 5;
-  for (long long base = gw * kRowsPerWarp; base < M.rows; base += nw * kRowsPerWarp) {
-    const int i = int(base) + lane / G;
-    T s1 = T(0), s2 = T(0);
-    if (i < M.rows) {
-      const int e = __ldg(M.rowptr + i + 1);
-      for (int k = __ldg(M.rowptr + i) + sub; k < e; k += kUnroll * G) {
-        int c[kUnroll];
-        T a[kUnroll], x1[kUnroll], x2[kUnroll];
-#pragma unroll
-        for (int j = 0; j < kUnroll; ++j) {
-          const int kk = k + j * G;
-          c[j] = kk < e ? __ldg(M.col + kk) : -1;
-          a[j] = kk < e ? __ldg(M.val + kk) : T(0);
-        }
-#pragma unroll
-        for (int j = 0; j < kUnroll; ++j) {
-          x1[j] = c[j] >= 0 ? v1[c[j]] : T(0);
-          x2[j] = c[j] >= 0 ? v2[c[j]] : T(0);
-        }
-#pragma unroll
-        for (int j = 0; j < kUnroll; ++j) {
-          s1 = fma(a[j], x1[j], s1);
-          s2 = fma(a[j], x2[j], s2);
-        }
-      }
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      s1 += shfl_xor(s1, o);
-      s2 += shfl_xor(s2, o);
-    }
-    if (i < M.rows) f(i, s1, s2, sub == 0);
+  for (long long sg = grid_tid() >> 5; sg < L.nseg; sg += nw) {
+    const int e = __ldg(L.seg_end + sg);
+    const T s = warp_sum_t(row_dot<32>(M, v, __ldg(L.seg_begin + sg), e, lane));
+    if (lane == 0) seg_part[sg] = s;
   }
+}
+
+// Phase 2: one warp per long row sums its segments in index order.
+template <class T>
+__device__ __forceinline__ void long_finish(const LongRows& L, const T* seg_part, T* long_val) {
+  const int lane = threadIdx.x & 31;
+  const long long nw = grid_threads() >> 5;
+  for (long long r = grid_tid() >> 5; r < L.nlong; r += nw) {
+    T s = T(0);
+    for (int k = __ldg(L.seg_ptr + r) + lane; k < __ldg(L.seg_ptr + r + 1); k += 32)
+      s += __ldcg(seg_part + k);
+    s = warp_sum_t(s);
+    if (lane == 0) long_val[r] = s;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_long_segments(CsrT<T> M, const T* __restrict__ v,
+                                                          LongRows L, T* seg_part) {
+  long_segments(M, v, L, seg_part);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_long_finish(LongRows L, const T* seg_part,
+                                                        T* long_val) {
+  long_finish(L, seg_part, long_val);
 }
 
 // Block partial of r0'r0, and the grid total written by the last block to
@@ -458,8 +501,8 @@ constexpr int kCgBlocksPerSm = 3;
 
 template <int G, class T>
 __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
-    k_cg(CsrT<T> Q, T* x, T* r, T* p, T* q, T* qx, const double* r0r0, double* part,
-         DevState* st, GridBarrier* bar, int n) {
+    k_cg(CsrT<T> Q, LongRows LQ, T* qseg, T* qlong, T* x, T* r, T* p, T* q, T* qx,
+         const double* r0r0, double* part, DevState* st, GridBarrier* bar, int n) {
   using A = typename Acc<T>::type;
   const bool active = running(st) && st->k_total < st->opt.max_iter;
   if (!active) {
@@ -484,6 +527,14 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
   bool numerr = false;
   const bool skip = (mode == kCgFixed && nfix <= 0) || rr == 0.0;
   while (!skip) {
+    if (LQ.nlong > 0) {
+      // long rows of Q: segment sums, then per-row totals, before the row pass
+      long_segments(Q, p, LQ, qseg);
+      if (!grid_sync(bar, st, tmo, never_release)) return;
+      never_release = false;
+      long_finish(LQ, qseg, qlong);
+      if (!grid_sync(bar, st, tmo, false)) return;
+    }
     A acc;
     spmv_rows<G>(Q, p, [&](int i, T s, bool lead) {
       if (lead) {
@@ -620,38 +671,35 @@ __global__ void __launch_bounds__(kBlock) k_spmv(CsrT<T> M, const T* __restrict_
 }
 
 // ------------------------------------------------ relKKT terms (Section 4)
-// Per block (stride kPartStride), over the n index space:
+// Per block (stride kPartStride), over the n index space, from the products
+// qx = Q x, qxa = Q x~ and A'y, A'y~ computed just before:
 //  [0] max|Qx + A'y + c|  [1] max|Qx|  [2] max|A'y|  [3] sum x.Qx  [4] sum c.x
 //  [5..9] the same for the average (x~, y~)            [10] max|c|
-// Q x and Q x~ are stored (qx, qx_avg): the exact refresh of the tracked qx.
-template <int G, class T>
-__global__ void __launch_bounds__(kBlock) k_kkt_n(CsrT<T> Q, const T* __restrict__ x,
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_kkt_n(const T* __restrict__ x,
                                                   const T* __restrict__ x_avg,
+                                                  const T* __restrict__ qx,
+                                                  const T* __restrict__ qxa,
                                                   const T* __restrict__ aty,
                                                   const T* __restrict__ aty_avg,
-                                                  const T* __restrict__ c, T* qx_out,
-                                                  T* qx_avg_out, double* part) {
+                                                  const T* __restrict__ c, int n, double* part) {
   using A = typename Acc<T>::type;
   T mx[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};  // maxima, see the map below
   A sm[4];                                               // x.Qx, c.x, x~.Qx~, c.x~
-  spmv2_rows<G>(Q, x, x_avg, [&](int i, T qx, T qxa, bool lead) {
-    if (lead) {
-      const T ci = c[i];
-      qx_out[i] = qx;
-      qx_avg_out[i] = qxa;
-      mx[0] = fmax(mx[0], fabs(qx + aty[i] + ci));
-      mx[1] = fmax(mx[1], fabs(qx));
-      mx[2] = fmax(mx[2], fabs(aty[i]));
-      sm[0].add_prod(x[i], qx);
-      sm[1].add_prod(ci, x[i]);
-      mx[3] = fmax(mx[3], fabs(qxa + aty_avg[i] + ci));
-      mx[4] = fmax(mx[4], fabs(qxa));
-      mx[5] = fmax(mx[5], fabs(aty_avg[i]));
-      sm[2].add_prod(x_avg[i], qxa);
-      sm[3].add_prod(ci, x_avg[i]);
-      mx[6] = fmax(mx[6], fabs(ci));
-    }
-  });
+  for (long long i = grid_tid(); i < n; i += grid_threads()) {
+    const T ci = c[i], q1 = qx[i], q2 = qxa[i];
+    mx[0] = fmax(mx[0], fabs(q1 + aty[i] + ci));
+    mx[1] = fmax(mx[1], fabs(q1));
+    mx[2] = fmax(mx[2], fabs(aty[i]));
+    sm[0].add_prod(x[i], q1);
+    sm[1].add_prod(ci, x[i]);
+    mx[3] = fmax(mx[3], fabs(q2 + aty_avg[i] + ci));
+    mx[4] = fmax(mx[4], fabs(q2));
+    mx[5] = fmax(mx[5], fabs(aty_avg[i]));
+    sm[2].add_prod(x_avg[i], q2);
+    sm[3].add_prod(ci, x_avg[i]);
+    mx[6] = fmax(mx[6], fabs(ci));
+  }
   // fmax drops NaN; a NaN iterate still reaches relKKT through the dot products.
   __shared__ double out[11];
   block_reduce_ms<7, 4>(mx, sm, out);
@@ -672,35 +720,32 @@ __global__ void __launch_bounds__(kBlock) k_kkt_n(CsrT<T> Q, const T* __restrict
   }
 }
 
-// Over the m index space (A x~ is computed here and stored for a restart):
+// Over the m index space, from ax = A x (cached) and ax_avg = A x~:
 //  [0] max viol(x)  [1] max|Ax|  [2] sum b.y  [3] max viol(x~)  [4] max|Ax~|
 //  [5] sum b.y~  [6] max|b|;  viol = |Ax-b| on equality rows, [Ax-b]^+ else.
-template <int G, class T>
-__global__ void __launch_bounds__(kBlock) k_kkt_m(CsrT<T> Am, const T* __restrict__ x_avg,
-                                                  const T* __restrict__ ax, T* ax_avg,
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_kkt_m(const T* __restrict__ ax,
+                                                  const T* __restrict__ ax_avg,
                                                   const T* __restrict__ b,
                                                   const T* __restrict__ y,
-                                                  const T* __restrict__ y_avg, int m_eq,
+                                                  const T* __restrict__ y_avg, int m, int m_eq,
                                                   double* part) {
   using A = typename Acc<T>::type;
   T mx[5] = {T(0), T(0), T(0), T(0), T(0)};  // viol, |Ax|, viol~, |Ax~|, |b|
   A sm[2];                                   // b.y, b.y~
-  spmv_rows<G>(Am, x_avg, [&](int i, T s, bool lead) {
-    if (lead) {
-      ax_avg[i] = s;
-      const T bi = b[i];
-      const T d = ax[i] - bi, da = s - bi;
-      const T vc = i < m_eq ? fabs(d) : (d > T(0) ? d : T(0));
-      const T va = i < m_eq ? fabs(da) : (da > T(0) ? da : T(0));
-      mx[0] = fmax(mx[0], vc);
-      mx[1] = fmax(mx[1], fabs(ax[i]));
-      sm[0].add_prod(bi, y[i]);
-      mx[2] = fmax(mx[2], va);
-      mx[3] = fmax(mx[3], fabs(s));
-      sm[1].add_prod(bi, y_avg[i]);
-      mx[4] = fmax(mx[4], fabs(bi));
-    }
-  });
+  for (long long i = grid_tid(); i < m; i += grid_threads()) {
+    const T bi = b[i], s = ax_avg[i];
+    const T d = ax[i] - bi, da = s - bi;
+    const T vc = i < m_eq ? fabs(d) : (d > T(0) ? d : T(0));
+    const T va = i < m_eq ? fabs(da) : (da > T(0) ? da : T(0));
+    mx[0] = fmax(mx[0], vc);
+    mx[1] = fmax(mx[1], fabs(ax[i]));
+    sm[0].add_prod(bi, y[i]);
+    mx[2] = fmax(mx[2], va);
+    mx[3] = fmax(mx[3], fabs(s));
+    sm[1].add_prod(bi, y_avg[i]);
+    mx[4] = fmax(mx[4], fabs(bi));
+  }
   __shared__ double out[7];
   block_reduce_ms<5, 2>(mx, sm, out);
   if (threadIdx.x == 0) {

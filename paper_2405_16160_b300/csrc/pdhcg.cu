@@ -79,14 +79,45 @@ struct DevMat {
   int32_t rows = 0;
   int64_t nnz = 0;
   int G64 = 1, G32 = 4;
+  // rows longer than kLongRow: segment table and per-precision work buffers
+  int32_t nlong = 0, nseg = 0;
+  int32_t *long_rows = nullptr, *seg_begin = nullptr, *seg_end = nullptr, *seg_ptr = nullptr;
+  double *seg64 = nullptr, *long64 = nullptr;
+  float *seg32 = nullptr, *long32 = nullptr;
 };
 
 template <class T>
 CsrT<T> view(const DevMat& M) {
   if constexpr (std::is_same<T, double>::value)
-    return CsrT<double>{M.rowptr, M.col, M.val, M.rows};
+    return CsrT<double>{M.rowptr, M.col, M.val, M.rows, M.long_rows, M.long64, M.nlong};
   else
-    return CsrT<float>{M.rowptr, M.col, M.val32, M.rows};
+    return CsrT<float>{M.rowptr, M.col, M.val32, M.rows, M.long_rows, M.long32, M.nlong};
+}
+
+LongRows long_rows_of(const DevMat& M) {
+  LongRows L;
+  L.seg_begin = M.seg_begin;
+  L.seg_end = M.seg_end;
+  L.seg_ptr = M.seg_ptr;
+  L.nseg = M.nseg;
+  L.nlong = M.nlong;
+  return L;
+}
+
+template <class T>
+T* seg_buf(const DevMat& M) {
+  if constexpr (std::is_same<T, double>::value)
+    return M.seg64;
+  else
+    return M.seg32;
+}
+
+template <class T>
+T* long_buf(const DevMat& M) {
+  if constexpr (std::is_same<T, double>::value)
+    return M.long64;
+  else
+    return M.long32;
 }
 
 template <class T>
@@ -245,6 +276,18 @@ qp_status validate_options(const qp_options* o) {
 }
 
 // --------------------------------------------------------------- launches
+// Segment pass over the long rows of M for the product M v (nothing for
+// matrices without long rows).
+template <class T>
+void launch_long(qp_handle* h, const DevMat& M, const T* v) {
+  if (M.nlong == 0) return;
+  const int wave = h->num_sms * 8;
+  const int gs = std::max(1, std::min(wave, (M.nseg + kBlock / 32 - 1) / (kBlock / 32)));
+  const int gl = std::max(1, std::min(wave, (M.nlong + kBlock / 32 - 1) / (kBlock / 32)));
+  k_long_segments<T><<<gs, kBlock, 0, h->stream>>>(view<T>(M), v, long_rows_of(M), seg_buf<T>(M));
+  k_long_finish<T><<<gl, kBlock, 0, h->stream>>>(long_rows_of(M), seg_buf<T>(M), long_buf<T>(M));
+}
+
 template <class T>
 qp_status launch_cg(qp_handle* h, bool coop) {
   VecSet<T>& v = vecs<T>(h);
@@ -261,7 +304,8 @@ qp_status launch_cg(qp_handle* h, bool coop) {
       cfg.attrs = attr;
       cfg.numAttrs = 1;
     }
-    cudaLaunchKernelEx(&cfg, k_cg<G, T>, view<T>(h->Q), v.x, v.r, v.p, v.q, v.qx,
+    cudaLaunchKernelEx(&cfg, k_cg<G, T>, view<T>(h->Q), long_rows_of(h->Q), seg_buf<T>(h->Q),
+                       long_buf<T>(h->Q), v.x, v.r, v.p, v.q, v.qx,
                        (const double*)(h->part_r0 + h->grid_n), h->part_cg, h->st, h->bar,
                        (int)h->n);
   });
@@ -270,6 +314,7 @@ qp_status launch_cg(qp_handle* h, bool coop) {
 template <class T>
 qp_status launch_dual(qp_handle* h) {
   VecSet<T>& v = vecs<T>(h);
+  launch_long<T>(h, h->A, v.x);
   return dispatch_g(lanes<T>(h->A), [&](auto g) {
     constexpr int G = decltype(g)::value;
     k_dual<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(view<T>(h->A), v.x, v.b, v.y, v.ax, v.y_avg,
@@ -280,6 +325,7 @@ qp_status launch_dual(qp_handle* h) {
 template <class T>
 qp_status launch_atv(qp_handle* h) {
   VecSet<T>& v = vecs<T>(h);
+  launch_long<T>(h, h->At, v.y);
   return dispatch_g(lanes<T>(h->At), [&](auto g) {
     constexpr int G = decltype(g)::value;
     k_atv<G, T><<<h->grid_n, kBlock, 0, h->stream>>>(view<T>(h->At), v.y, v.aty, v.x, v.x_avg,
@@ -290,27 +336,27 @@ qp_status launch_atv(qp_handle* h) {
 
 template <class T>
 qp_status launch_spmv(qp_handle* h, const DevMat& M, const T* x, T* out, double* part, int grid) {
+  launch_long<T>(h, M, x);
   return dispatch_g(lanes<T>(M), [&](auto g) {
     constexpr int G = decltype(g)::value;
     k_spmv<G, T><<<grid, kBlock, 0, h->stream>>>(view<T>(M), x, out, part);
   });
 }
 
-// relKKT of (x, y) and (x~, y~); mode as in k_control.
+// relKKT of (x, y) and (x~, y~); mode as in k_control.  The products Q x,
+// Q x~ (the exact refresh of the tracked qx, qx_avg), A x~ and A' y~ come
+// first; A x and A' y are the caches of the current iterate.
 template <class T>
 qp_status launch_eval(qp_handle* h, int mode) {
   VecSet<T>& v = vecs<T>(h);
   QP_TRY(launch_spmv<T>(h, h->At, v.y_avg, v.aty_avg, nullptr, h->grid_n));
-  QP_TRY(dispatch_g(lanes<T>(h->Q), [&](auto g) {
-    constexpr int G = decltype(g)::value;
-    k_kkt_n<G, T><<<h->grid_n, kBlock, 0, h->stream>>>(view<T>(h->Q), v.x, v.x_avg, v.aty,
-                                                       v.aty_avg, v.c, v.qx, v.qx_avg, h->part_n);
-  }));
-  QP_TRY(dispatch_g(lanes<T>(h->A), [&](auto g) {
-    constexpr int G = decltype(g)::value;
-    k_kkt_m<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(view<T>(h->A), v.x_avg, v.ax, v.ax_avg,
-                                                       v.b, v.y, v.y_avg, h->m_eq, h->part_m);
-  }));
+  QP_TRY(launch_spmv<T>(h, h->Q, v.x, v.qx, nullptr, h->grid_n));
+  QP_TRY(launch_spmv<T>(h, h->Q, v.x_avg, v.qx_avg, nullptr, h->grid_n));
+  QP_TRY(launch_spmv<T>(h, h->A, v.x_avg, v.ax_avg, nullptr, h->grid_m));
+  k_kkt_n<T><<<h->grid_n, kBlock, 0, h->stream>>>(v.x, v.x_avg, v.qx, v.qx_avg, v.aty,
+                                                  v.aty_avg, v.c, h->n, h->part_n);
+  k_kkt_m<T><<<h->grid_m, kBlock, 0, h->stream>>>(v.ax, v.ax_avg, v.b, v.y, v.y_avg, h->m,
+                                                  h->m_eq, h->part_m);
   k_control<<<1, 32, 0, h->stream>>>(h->part_n, h->grid_n, h->part_m, h->grid_m, h->st, mode);
   return QP_OK;
 }
@@ -540,6 +586,36 @@ qp_status upload_matrix(qp_handle* h, DevMat* M, const CsrView& H) {
   if (M->nnz > 0)
     k_convert<double, float><<<h->grid_vec, kBlock, 0, h->stream>>>(M->val, M->val32,
                                                                     int(M->nnz));
+  // Long rows: fixed-length segments in row order.
+  std::vector<int32_t> lr, sb, se, sp(1, 0);
+  for (int32_t i = 0; i < H.rows; ++i) {
+    const int32_t b = H.rowptr[i], e = H.rowptr[i + 1];
+    if (e - b <= kLongRow) continue;
+    lr.push_back(i);
+    for (int32_t k = b; k < e; k += kSegLen) {
+      sb.push_back(k);
+      se.push_back(std::min(e, k + kSegLen));
+    }
+    sp.push_back(int32_t(sb.size()));
+  }
+  M->nlong = int32_t(lr.size());
+  M->nseg = int32_t(sb.size());
+  if (M->nlong > 0) {
+    QP_TRY(dalloc(h, &M->long_rows, lr.size()));
+    QP_TRY(dalloc(h, &M->seg_begin, sb.size()));
+    QP_TRY(dalloc(h, &M->seg_end, se.size()));
+    QP_TRY(dalloc(h, &M->seg_ptr, sp.size()));
+    QP_TRY(dalloc(h, &M->seg64, sb.size()));
+    QP_TRY(dalloc(h, &M->seg32, sb.size()));
+    QP_TRY(dalloc(h, &M->long64, lr.size()));
+    QP_TRY(dalloc(h, &M->long32, lr.size()));
+    QP_TRY(upload(h, M->long_rows, lr.data(), lr.size() * sizeof(int32_t)));
+    QP_TRY(upload(h, M->seg_begin, sb.data(), sb.size() * sizeof(int32_t)));
+    QP_TRY(upload(h, M->seg_end, se.data(), se.size() * sizeof(int32_t)));
+    QP_TRY(upload(h, M->seg_ptr, sp.data(), sp.size() * sizeof(int32_t)));
+    // the host vectors die with this call: finish the copies first
+    QP_TRY(sync(h));
+  }
   return QP_OK;
 }
 

@@ -74,6 +74,27 @@ def _single():
                         name="n=1")
 
 
+def _long_rows():
+    """Rows longer than the 4096-entry long-row threshold in A, A' and Q."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(8)
+    n, m = 10_000, 6_000
+    A = sp.random(m, n, density=6 / n, random_state=8, data_rvs=rng.standard_normal).tolil()
+    A[:, 3] = rng.standard_normal((m, 1))        # A' row 3: 6000 entries
+    A[0, :5000] = rng.standard_normal(5000)      # A rows 0, 1: 5000 entries
+    A[1, 2000:7000] = rng.standard_normal(5000)
+    A = A.tocsr()
+    S = sp.random(n, n, density=3 / n, random_state=9, data_rvs=lambda k: rng.normal(0, 0.1, k))
+    S = sp.lil_matrix(S + S.T)
+    S[5, 100:5100] = rng.normal(0, 0.01, 5000)   # Q row/column 5: > 5000 entries
+    S[100:5100, 5] = S[5, 100:5100].T
+    S = S.tocsr()
+    Q = S + sp.diags(np.asarray(abs(S).sum(axis=1)).ravel() + rng.uniform(0.5, 2, n))
+    x0 = rng.standard_normal(n)
+    b = A @ x0 + rng.uniform(0, 1, m)
+    return W.from_dense(Q.toarray(), A.toarray(), rng.standard_normal(n), b, name="long rows")
+
+
 CASES = {
     "dense_small": lambda: W.dense_small(0),
     "dense_small_eq": lambda: W.dense_small(1, m_eq=10),
@@ -83,6 +104,8 @@ CASES = {
     "all_equalities": _all_equalities,
     "empty_rows": _empty_rows,
     "single": _single,
+    "long_rows": _long_rows,
+    "zipf_small": lambda: W.zipf_dd(0, n=20_000, m=10_000),
 }
 
 
@@ -176,7 +199,8 @@ def test_iterations_match_oracle(built, name, mode, iters):
 @pytest.mark.parametrize("name,tol", [("dense_small", 1e-6), ("dense_small_eq", 1e-6),
                                       ("sparse_small", 1e-4), ("ragged_eq", 1e-4),
                                       ("unconstrained", 1e-6), ("all_equalities", 1e-6),
-                                      ("empty_rows", 1e-6), ("single", 1e-8)])
+                                      ("empty_rows", 1e-6), ("single", 1e-8),
+                                      ("long_rows", 1e-5)])
 def test_end_to_end_matches_oracle(built, name, tol):
     inst, P, s = built(name)
     ores = O.solve(P, O.OracleOptions(tol=tol))
@@ -317,7 +341,8 @@ def test_full_size_solve_matches_oracle_trace(big):
 # from a shared state agrees with the FP64 oracle to 1e-5 relative; a solve
 # ends with an FP64 re-evaluation (and FP64 refinement if needed), so the
 # oracle re-scores its result at <= tol.
-MIXED_ITER_CASES = ["dense_small", "dense_small_eq", "sparse_small", "ragged_eq", "empty_rows"]
+MIXED_ITER_CASES = ["dense_small", "dense_small_eq", "sparse_small", "ragged_eq", "empty_rows",
+                    "long_rows", "zipf_small"]
 
 
 @pytest.mark.parametrize("name", MIXED_ITER_CASES)
