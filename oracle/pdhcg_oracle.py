@@ -43,6 +43,11 @@ path implements the same one):
   iterations on A'A from the normalised all-ones vector.  If ||A||_2 is not
   above eps_zero (no coupling), ||A||_2 is replaced by eps_zero.
 * omega_0 = ||c||_2 / ||b||_2 when both exceed eps_zero, else 1; x0 = y0 = 0.
+* Preprocessing (Section 4, optional ``scale``): D1 (constraints) and D2
+  (variables) from 10 Ruiz equilibration steps and one Pock-Chambolle step
+  (alpha = 1) on the symmetric K = [[Q, A'], [A, 0]]; the iteration runs on
+  D2 Q D2, D1 A D2, D2 c, D1 b, and every relKKT (termination, restarts, the
+  CG precision) is evaluated on the original problem at x = D2 x~, y = D1 y~.
 
 Parity unpinned: ``restart_test`` (the exact restart decisions), the
 primal-weight formula inside ``restart_to`` and the omega_0 rule of
@@ -154,6 +159,45 @@ def relkkt(P: OracleProblem, x: np.ndarray, y: np.ndarray) -> KKT:
 
 
 # --------------------------------------------------------------------------
+# Preprocessing (Section 4): diagonal scaling of K = [[Q, A'], [A, 0]].
+# --------------------------------------------------------------------------
+def _row_norms_K(P: OracleProblem, d1: np.ndarray, d2: np.ndarray, ord_inf: bool):
+    """Row norms (inf or 1) of D K D, D = diag(d2, d1): variable rows then constraint rows."""
+    Qs = sp.diags(d2) @ abs(P.Q) @ sp.diags(d2)
+    As = sp.diags(d1) @ abs(P.A) @ sp.diags(d2)
+    if ord_inf:
+        rq = np.asarray(Qs.max(axis=1).todense()).ravel() if P.n else np.zeros(0)
+        ra_col = np.asarray(As.max(axis=0).todense()).ravel() if P.m else np.zeros(P.n)
+        ra_row = np.asarray(As.max(axis=1).todense()).ravel() if P.m else np.zeros(0)
+        return np.maximum(rq, ra_col), ra_row
+    rq = np.asarray(Qs.sum(axis=1)).ravel()
+    ra_col = np.asarray(As.sum(axis=0)).ravel() if P.m else np.zeros(P.n)
+    ra_row = np.asarray(As.sum(axis=1)).ravel() if P.m else np.zeros(0)
+    return rq + ra_col, ra_row
+
+
+def diagonal_scaling(P: OracleProblem, ruiz_iters: int = 10, pock_chambolle: bool = True):
+    """D1 (m), D2 (n): `ruiz_iters` Ruiz steps, then one Pock-Chambolle step.
+
+    Ruiz step: every row k of the current D K D is divided, on both sides,
+    by sqrt(||row_k||_inf).  Pock-Chambolle (alpha = 1): the same with the
+    1-norm.  Rows that are entirely zero keep their scale.
+    """
+    d1, d2 = np.ones(P.m), np.ones(P.n)
+    for it in range(ruiz_iters + (1 if pock_chambolle else 0)):
+        rn, rm = _row_norms_K(P, d1, d2, ord_inf=it < ruiz_iters)
+        d2 = d2 / np.sqrt(np.where(rn > 0.0, rn, 1.0))
+        d1 = d1 / np.sqrt(np.where(rm > 0.0, rm, 1.0))
+    return d1, d2
+
+
+def scale_problem(P: OracleProblem, d1: np.ndarray, d2: np.ndarray) -> OracleProblem:
+    Q = (sp.diags(d2) @ P.Q @ sp.diags(d2)).tocsr()
+    A = (sp.diags(d1) @ P.A @ sp.diags(d2)).tocsr()
+    return OracleProblem(Q, A, d2 * P.c, d1 * P.b, P.m_eq)
+
+
+# --------------------------------------------------------------------------
 # Setup: spectral norm and step size (Section 3.2: sigma = tau = 1/(2||A||)).
 # --------------------------------------------------------------------------
 def spectral_norm(A: sp.csr_matrix, iters: int = 30) -> float:
@@ -243,6 +287,7 @@ class OracleOptions:
     power_iters: int = 30
     omega0: float = 0.0  # <= 0: ||c||/||b|| rule
     eta: float = 0.0  # <= 0: 1/(2||A||)
+    scale: bool = False  # Section 4 preprocessing (Ruiz x10 + Pock-Chambolle)
 
 
 @dataclass
@@ -358,13 +403,16 @@ class OracleResult:
     seconds: float = 0.0
 
 
-def evaluate(P: OracleProblem, st: OracleState, o: OracleOptions, record: list) -> tuple:
+def evaluate(P: OracleProblem, st: OracleState, o: OracleOptions, record: list,
+             kkt=None) -> tuple:
     """relKKT of the current iterate and of the average, then the restart logic.
 
-    Returns (done, kkt, use_avg) where done is True when relKKT <= tol.
+    ``kkt(x, y)`` scores an iterate (default: relkkt on P).  Returns
+    (done, kkt, use_avg) where done is True when relKKT <= tol.
     """
-    kc = relkkt(P, st.x, st.y)
-    ka = relkkt(P, st.x_avg, st.y_avg) if st.j > 0 else None
+    kkt = kkt or (lambda x, y: relkkt(P, x, y))
+    kc = kkt(st.x, st.y)
+    ka = kkt(st.x_avg, st.y_avg) if st.j > 0 else None
     rec = {"k": st.k_total, "kkt_cur": kc.relkkt, "kkt_avg": ka.relkkt if ka else None,
            "restart": False, "cand_avg": False, "omega": st.omega}
     record.append(rec)
@@ -384,33 +432,44 @@ def evaluate(P: OracleProblem, st: OracleState, o: OracleOptions, record: list) 
 
 def solve(P: OracleProblem, o: OracleOptions | None = None,
           state: OracleState | None = None, step_hook=None) -> OracleResult:
-    """Restarted PDHCG (Algorithm 1 with the Section 4 heuristics)."""
+    """Restarted PDHCG (Algorithm 1 with the Section 4 heuristics).
+
+    With ``o.scale`` the iteration runs on the scaled problem (``state`` and
+    ``step_hook`` then see scaled iterates), relKKT is taken on P at the
+    unscaled iterate, and the returned x, y are unscaled.
+    """
     o = o or OracleOptions()
     t0 = time.perf_counter()
-    st = state.copy() if state is not None else initial_state(P, o)
+    if o.scale:
+        d1, d2 = diagonal_scaling(P)
+        Pi = scale_problem(P, d1, d2)
+    else:
+        d1, d2, Pi = np.ones(P.m), np.ones(P.n), P
+    kkt = lambda x, y: relkkt(P, d2 * x, d1 * y)
+    st = state.copy() if state is not None else initial_state(Pi, o)
     trace: list = []
     if state is None:
-        k0 = relkkt(P, st.x, st.y)
+        k0 = kkt(st.x, st.y)
         trace.append({"k": 0, "kkt_cur": k0.relkkt, "kkt_avg": None, "restart": False,
                       "cand_avg": False, "omega": st.omega})
         st.relkkt_last = k0.relkkt
         st.kkt_anchor = k0.relkkt
         if k0.relkkt <= o.tol:
-            return OracleResult(st.x, st.y, SOLVED, k0, 0, 0, 0, False, st, trace,
+            return OracleResult(d2 * st.x, d1 * st.y, SOLVED, k0, 0, 0, 0, False, st, trace,
                                 time.perf_counter() - t0)
     term = ITER_LIMIT
-    kkt = None
+    best = None
     use_avg = False
     try:
         while st.k_total < o.max_iter:
-            inner_step(P, st, o)
+            inner_step(Pi, st, o)
             if step_hook is not None:
                 step_hook(st)
             if o.restart_mode == RESTART_FIXED and st.j >= o.restart_k:
-                kc = relkkt(P, st.x_avg, st.y_avg)
-                restart_to(P, st, o, True, kc.relkkt)
+                kc = kkt(st.x_avg, st.y_avg)
+                restart_to(Pi, st, o, True, kc.relkkt)
             if st.k_total % o.eval_freq == 0:
-                done, kkt, use_avg = evaluate(P, st, o, trace)
+                done, best, use_avg = evaluate(Pi, st, o, trace, kkt)
                 if done:
                     term = SOLVED
                     break
@@ -420,11 +479,11 @@ def solve(P: OracleProblem, o: OracleOptions | None = None,
     except NumericalError:
         term = NUMERICAL_ERROR
     if term != SOLVED:
-        kc = relkkt(P, st.x, st.y)
-        ka = relkkt(P, st.x_avg, st.y_avg) if st.j > 0 else None
+        kc = kkt(st.x, st.y)
+        ka = kkt(st.x_avg, st.y_avg) if st.j > 0 else None
         use_avg = ka is not None and ka.relkkt <= kc.relkkt
-        kkt = ka if use_avg else kc
+        best = ka if use_avg else kc
     x = st.x_avg if use_avg else st.x
     y = st.y_avg if use_avg else st.y
-    return OracleResult(x.copy(), y.copy(), term, kkt, st.k_total, st.cg_total, st.n_restarts,
+    return OracleResult(d2 * x, d1 * y, term, best, st.k_total, st.cg_total, st.n_restarts,
                         use_avg, st, trace, time.perf_counter() - t0)

@@ -447,3 +447,67 @@ def test_planted_relkkt_mistake_is_caught(monkeypatch, golden_dir):
 
     k = wrong(P, np.array(case["x"]), np.array(case["y"]))
     assert k.r_gap != pytest.approx(case["r_gap"], rel=1e-6)
+
+
+# ---------------------------------------------------------------- preprocessing (Section 4)
+def test_scaling_hand_worked():
+    # K = [[0, 0, 3], [0, 0, 4], [3, 4, 0]]: Q = 0 (2 x 2), A = [[3, 4]]
+    P = _prob(np.zeros((2, 2)), [[3.0, 4.0]], [0.0, 0.0], [1.0])
+    d1, d2 = O.diagonal_scaling(P, ruiz_iters=0)  # Pock-Chambolle only: 1-norms 3, 4, 7
+    assert np.allclose(d2, [1 / math.sqrt(3), 1 / 2], rtol=1e-15)
+    assert np.allclose(d1, [1 / math.sqrt(7)], rtol=1e-15)
+    # one Ruiz step (inf-norms 3, 4, 4), then Pock-Chambolle on the result
+    d1, d2 = O.diagonal_scaling(P, ruiz_iters=1)
+    r2 = np.array([1 / math.sqrt(3), 0.5])
+    r1 = np.array([0.5])
+    a = np.array([3.0, 4.0]) * r2 * r1  # scaled A after the Ruiz step
+    assert np.allclose(d2, r2 / np.sqrt(a), rtol=1e-15)
+    assert np.allclose(d1, r1 / math.sqrt(a.sum()), rtol=1e-15)
+    # a diagonal Q alone: Pock-Chambolle makes it the identity
+    d1, d2 = O.diagonal_scaling(_prob(np.diag([4.0, 9.0]), np.zeros((0, 2)), [1, 1], []), 0)
+    assert np.allclose(d2, [0.5, 1 / 3], rtol=1e-15)
+
+
+def test_ruiz_equilibrates_rows():
+    """Ruiz iterations converge to a scaling with unit infinity-norm rows."""
+    rng = np.random.default_rng(30)
+    n, m = 30, 20
+    Qd = _rand_spd(rng, n, 50.0) * np.exp(rng.uniform(-3, 3, n))[:, None]
+    Qd = (Qd + Qd.T) / 2
+    Ad = rng.standard_normal((m, n)) * np.exp(rng.uniform(-4, 4, (m, 1)))
+    P = _prob(Qd, Ad, rng.standard_normal(n), rng.standard_normal(m))
+    d1, d2 = O.diagonal_scaling(P, ruiz_iters=200, pock_chambolle=False)
+    rn, rm = O._row_norms_K(P, d1, d2, ord_inf=True)
+    assert np.allclose(rn, 1.0, atol=1e-6) and np.allclose(rm, 1.0, atol=1e-6)
+    # Pock-Chambolle afterwards: unit 1-norms are not its fixed point, but a
+    # second application changes an already 1-norm-balanced K by little
+    d1p, d2p = O.diagonal_scaling(P, ruiz_iters=200)
+    rn1, rm1 = O._row_norms_K(P, d1p, d2p, ord_inf=False)
+    assert np.all(rn1 > 0) and np.all(rm1 > 0)
+
+
+@pytest.mark.parametrize("seed,n,m,m_eq", [(10, 4, 6, 0), (12, 6, 7, 2), (13, 3, 8, 1)])
+def test_scaled_solver_matches_active_set_brute_force(seed, n, m, m_eq):
+    rng = np.random.default_rng(seed)
+    Qd = _rand_spd(rng, n, 10.0) * np.exp(rng.uniform(-2, 2, n))[:, None]
+    Qd = (Qd + Qd.T) / 2 + np.eye(n) * 0.1
+    Ad = rng.standard_normal((m, n)) * np.exp(rng.uniform(-2, 2, (m, 1)))
+    c = rng.standard_normal(n) * 3
+    b = Ad @ rng.standard_normal(n) + np.concatenate([np.zeros(m_eq), rng.uniform(0, 0.5, m - m_eq)])
+    xs, ys = brute_force_qp(Qd, Ad, c, b, m_eq)
+    res = O.solve(_prob(Qd, Ad, c, b, m_eq), _opts(scale=True))
+    assert res.termination == O.SOLVED
+    assert np.linalg.norm(res.x - xs) <= 1e-6 * (1 + np.linalg.norm(xs))
+    assert O.relkkt(_prob(Qd, Ad, c, b, m_eq), res.x, res.y).relkkt <= 1e-10
+
+
+def test_scaled_solver_box_closed_form():
+    rng = np.random.default_rng(7)
+    n = 40
+    q = rng.uniform(0.5, 2.0, n) * np.exp(rng.uniform(-3, 3, n))
+    c = rng.standard_normal(n) * 2
+    lo, hi = -rng.uniform(0.1, 1, n), rng.uniform(0.1, 1, n)
+    res = O.solve(_prob(np.diag(q), np.vstack([np.eye(n), -np.eye(n)]), c,
+                        np.concatenate([hi, -lo])), _opts(scale=True))
+    assert res.termination == O.SOLVED
+    assert np.max(np.abs(res.x - np.clip(-c / q, lo, hi))) <= 1e-8
