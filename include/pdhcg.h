@@ -63,6 +63,10 @@ enum { QP_RESTART_ADAPTIVE = 0, QP_RESTART_NONE = 2 };
 
 /* qp_create flags */
 #define QP_CREATE_CHECK_SYMMETRY 1u /* reject Q unless |Q - Q'| <= 1e-12 max|Q| entrywise */
+#define QP_CREATE_SCALE 2u          /* Section 4 preprocessing: diagonal D1, D2 from 10 Ruiz
+                                       steps and one Pock-Chambolle step on [[Q, A'], [A, 0]];
+                                       the solver iterates on D2 Q D2, D1 A D2, D2 c, D1 b and
+                                       measures relKKT on the original problem */
 
 /* debug_flags (fault injection; never used by default) */
 #define QP_DEBUG_BARRIER_NEVER_RELEASES 1u /* the CG kernel's first grid barrier is never
@@ -212,8 +216,13 @@ void qp_destroy(qp_handle* h);
  */
 qp_status qp_solve(qp_handle* h, const qp_options* o, qp_info* info);
 
-/* Copy the returned iterate to host arrays x (n) and y (m); either may be NULL. */
+/* Copy the returned iterate to host arrays x (n) and y (m); either may be NULL.
+ * With QP_CREATE_SCALE these are the caller's variables (x = D2 x~, y = D1 y~). */
 qp_status qp_get_solution(const qp_handle* h, double* x, double* y);
+
+/* The diagonal scaling of QP_CREATE_SCALE: d1 (m) for constraints and d2 (n)
+ * for variables (all ones without it); either may be NULL.  Host memory. */
+qp_status qp_get_scaling(const qp_handle* h, double* d1, double* d2);
 
 /* Info of the last qp_solve (QP_ERR_NOT_SOLVED before the first). */
 qp_status qp_get_stats(const qp_handle* h, qp_info* info);
@@ -224,12 +233,14 @@ qp_status qp_get_trace(const qp_handle* h, qp_trace_entry* out, int64_t cap, int
 
 /* ------------------------------------------------- state (checkpoint / parity) */
 
-/* Warm start (x0, y0); NULL means zeros.  Used when o->warm_start = 1:
+/* Warm start (x0, y0) in the caller's variables; NULL means zeros.  Used when
+ * o->warm_start = 1:
  * the anchors become (x0, y0), the averages are empty and the step sizes
  * are recomputed by the solve's set-up. */
 qp_status qp_set_warm_start(qp_handle* h, const double* x0, const double* y0);
 
-/* Read / write the full iteration state.  qp_set_state recomputes A x and
+/* Read / write the full iteration state (the solver's variables: with
+ * QP_CREATE_SCALE the scaled x~, y~).  qp_set_state recomputes A x and
  * A' y on the device.  A solve with o->warm_start = 2 continues from a set
  * state without recomputing the set-up. */
 qp_status qp_get_state(const qp_handle* h, const qp_state_vectors* v, qp_state_scalars* s);

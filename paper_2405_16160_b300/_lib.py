@@ -19,6 +19,7 @@ CG_ADAPTIVE, CG_FIXED = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 RESTART_ADAPTIVE, RESTART_NONE = 0, 2
 CREATE_CHECK_SYMMETRY = 1
+CREATE_SCALE = 2
 DEBUG_BARRIER_NEVER_RELEASES = 1
 QP_NORM_A_STATIC_MAX_DOUBLES = 1 << 20  # capacity of qp_norm_A_static's static scratch
 
@@ -95,6 +96,7 @@ SIGNATURES = [
     ("qp_destroy", None, [_H]),
     ("qp_solve", c_int32, [_H, POINTER(QPOptionsC), POINTER(QPInfoC)]),
     ("qp_get_solution", c_int32, [_H, _F64P, _F64P]),
+    ("qp_get_scaling", c_int32, [_H, _F64P, _F64P]),
     ("qp_get_stats", c_int32, [_H, POINTER(QPInfoC)]),
     ("qp_get_trace", c_int32, [_H, POINTER(QPTraceEntryC), c_int64, POINTER(c_int64)]),
     ("qp_set_warm_start", c_int32, [_H, _F64P, _F64P]),

@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
       if (lead) {
         const T pi = p[i];
         const T qi = s + pi * inv_tau;
-        q[i] = qi;
+        q[i] = s;  // Q p itself; q = Q p + p/tau is re-formed from it below
         acc.add_prod(pi, qi);
       }
     });
@@ -556,11 +556,13 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     acc = A();
     // x += alpha p, r -= alpha q with a rounded product then a rounded sum,
     // exactly as the elementwise vector statements of textbook CG; qx follows
-    // x through Q p = q - p/tau.
+    // x through the stored Q p (recovering it as q - p/tau would cancel badly
+    // in FP32 when 1/tau dominates Q).
     for (long long i = t0; i < n; i += nt) {
-      const T pi = p[i], qi = q[i];
+      const T pi = p[i], qpi = q[i];
+      const T qi = qpi + pi * inv_tau;
       x[i] = add_rn(x[i], mul_rn(alpha, pi));
-      qx[i] = add_rn(qx[i], mul_rn(alpha, qi - pi * inv_tau));
+      qx[i] = add_rn(qx[i], mul_rn(alpha, qpi));
       const T ri = sub_rn(r[i], mul_rn(alpha, qi));
       r[i] = ri;
       acc.add_prod(ri, ri);
@@ -675,6 +677,10 @@ __global__ void __launch_bounds__(kBlock) k_spmv(CsrT<T> M, const T* __restrict_
 // qx = Q x, qxa = Q x~ and A'y, A'y~ computed just before:
 //  [0] max|Qx + A'y + c|  [1] max|Qx|  [2] max|A'y|  [3] sum x.Qx  [4] sum c.x
 //  [5..9] the same for the average (x~, y~)            [10] max|c|
+// With diagonal scaling (inv_d2 != nullptr) the iterate is the scaled x~ and
+// the infinity norms are of the original quantities: row j of Qx, A'y, c and
+// Qx + A'y + c is inv_d2[j] times the scaled one; the dot products are
+// invariant under the scaling.
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_kkt_n(const T* __restrict__ x,
                                                   const T* __restrict__ x_avg,
@@ -682,23 +688,26 @@ __global__ void __launch_bounds__(kBlock) k_kkt_n(const T* __restrict__ x,
                                                   const T* __restrict__ qxa,
                                                   const T* __restrict__ aty,
                                                   const T* __restrict__ aty_avg,
-                                                  const T* __restrict__ c, int n, double* part) {
+                                                  const T* __restrict__ c,
+                                                  const T* __restrict__ inv_d2, int n,
+                                                  double* part) {
   using A = typename Acc<T>::type;
   T mx[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};  // maxima, see the map below
   A sm[4];                                               // x.Qx, c.x, x~.Qx~, c.x~
   for (long long i = grid_tid(); i < n; i += grid_threads()) {
     const T ci = c[i], q1 = qx[i], q2 = qxa[i];
-    mx[0] = fmax(mx[0], fabs(q1 + aty[i] + ci));
-    mx[1] = fmax(mx[1], fabs(q1));
-    mx[2] = fmax(mx[2], fabs(aty[i]));
+    const T w = inv_d2 ? inv_d2[i] : T(1);
+    mx[0] = fmax(mx[0], w * fabs(q1 + aty[i] + ci));
+    mx[1] = fmax(mx[1], w * fabs(q1));
+    mx[2] = fmax(mx[2], w * fabs(aty[i]));
     sm[0].add_prod(x[i], q1);
     sm[1].add_prod(ci, x[i]);
-    mx[3] = fmax(mx[3], fabs(q2 + aty_avg[i] + ci));
-    mx[4] = fmax(mx[4], fabs(q2));
-    mx[5] = fmax(mx[5], fabs(aty_avg[i]));
+    mx[3] = fmax(mx[3], w * fabs(q2 + aty_avg[i] + ci));
+    mx[4] = fmax(mx[4], w * fabs(q2));
+    mx[5] = fmax(mx[5], w * fabs(aty_avg[i]));
     sm[2].add_prod(x_avg[i], q2);
     sm[3].add_prod(ci, x_avg[i]);
-    mx[6] = fmax(mx[6], fabs(ci));
+    mx[6] = fmax(mx[6], w * fabs(ci));
   }
   // fmax drops NaN; a NaN iterate still reaches relKKT through the dot products.
   __shared__ double out[11];
@@ -723,28 +732,32 @@ __global__ void __launch_bounds__(kBlock) k_kkt_n(const T* __restrict__ x,
 // Over the m index space, from ax = A x (cached) and ax_avg = A x~:
 //  [0] max viol(x)  [1] max|Ax|  [2] sum b.y  [3] max viol(x~)  [4] max|Ax~|
 //  [5] sum b.y~  [6] max|b|;  viol = |Ax-b| on equality rows, [Ax-b]^+ else.
+// With diagonal scaling (inv_d1 != nullptr) row i of Ax - b, Ax and b is
+// inv_d1[i] times the scaled one.
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_kkt_m(const T* __restrict__ ax,
                                                   const T* __restrict__ ax_avg,
                                                   const T* __restrict__ b,
                                                   const T* __restrict__ y,
-                                                  const T* __restrict__ y_avg, int m, int m_eq,
+                                                  const T* __restrict__ y_avg,
+                                                  const T* __restrict__ inv_d1, int m, int m_eq,
                                                   double* part) {
   using A = typename Acc<T>::type;
   T mx[5] = {T(0), T(0), T(0), T(0), T(0)};  // viol, |Ax|, viol~, |Ax~|, |b|
   A sm[2];                                   // b.y, b.y~
   for (long long i = grid_tid(); i < m; i += grid_threads()) {
     const T bi = b[i], s = ax_avg[i];
+    const T w = inv_d1 ? inv_d1[i] : T(1);
     const T d = ax[i] - bi, da = s - bi;
     const T vc = i < m_eq ? fabs(d) : (d > T(0) ? d : T(0));
     const T va = i < m_eq ? fabs(da) : (da > T(0) ? da : T(0));
-    mx[0] = fmax(mx[0], vc);
-    mx[1] = fmax(mx[1], fabs(ax[i]));
+    mx[0] = fmax(mx[0], w * vc);
+    mx[1] = fmax(mx[1], w * fabs(ax[i]));
     sm[0].add_prod(bi, y[i]);
-    mx[2] = fmax(mx[2], va);
-    mx[3] = fmax(mx[3], fabs(s));
+    mx[2] = fmax(mx[2], w * va);
+    mx[3] = fmax(mx[3], w * fabs(s));
     sm[1].add_prod(bi, y_avg[i]);
-    mx[4] = fmax(mx[4], fabs(bi));
+    mx[4] = fmax(mx[4], w * fabs(bi));
   }
   __shared__ double out[7];
   block_reduce_ms<5, 2>(mx, sm, out);

@@ -136,6 +136,7 @@ struct VecSet {
   T *qx = nullptr, *qx_avg = nullptr;  // tracked Q x and Q x~ (refreshed every evaluation)
   T *x0 = nullptr, *y0 = nullptr;
   T *pw_v = nullptr, *pw_u = nullptr, *pw_w = nullptr;
+  T *inv_d1 = nullptr, *inv_d2 = nullptr;  // 1/D1, 1/D2 with diagonal scaling, else null
 };
 
 constexpr int kPrecFp64 = QP_PREC_FP64;
@@ -169,6 +170,8 @@ struct qp_handle {
   bool coop_ok = true;
   bool warm_set = false;
   int active_prec = kPrecFp64;  // precision of the iterate last produced
+  bool scaled = false;           // Section 4 diagonal scaling applied at create
+  std::vector<double> d1, d2;    // the scaling (x = D2 x~, y = D1 y~)
   cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};
   int chunk_iters[2] = {0, 0};
   std::vector<cudaEvent_t> ev;
@@ -354,9 +357,9 @@ qp_status launch_eval(qp_handle* h, int mode) {
   QP_TRY(launch_spmv<T>(h, h->Q, v.x_avg, v.qx_avg, nullptr, h->grid_n));
   QP_TRY(launch_spmv<T>(h, h->A, v.x_avg, v.ax_avg, nullptr, h->grid_m));
   k_kkt_n<T><<<h->grid_n, kBlock, 0, h->stream>>>(v.x, v.x_avg, v.qx, v.qx_avg, v.aty,
-                                                  v.aty_avg, v.c, h->n, h->part_n);
-  k_kkt_m<T><<<h->grid_m, kBlock, 0, h->stream>>>(v.ax, v.ax_avg, v.b, v.y, v.y_avg, h->m,
-                                                  h->m_eq, h->part_m);
+                                                  v.aty_avg, v.c, v.inv_d2, h->n, h->part_n);
+  k_kkt_m<T><<<h->grid_m, kBlock, 0, h->stream>>>(v.ax, v.ax_avg, v.b, v.y, v.y_avg, v.inv_d1,
+                                                  h->m, h->m_eq, h->part_m);
   k_control<<<1, 32, 0, h->stream>>>(h->part_n, h->grid_n, h->part_m, h->grid_m, h->st, mode);
   return QP_OK;
 }
@@ -718,6 +721,28 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   Th.col.resize(size_t(Ah.nnz()));
   Th.val.resize(size_t(Ah.nnz()));
   csr_transpose(m, n, Ah.rowptr, Ah.col, Ah.val, Th.rowptr.data(), Th.col.data(), Th.val.data());
+  // Section 4 preprocessing: the solver works on D2 Q D2, D1 A D2, D2 c, D1 b.
+  HostCsr Qs_, As_, Ts_;
+  std::vector<double> cs, bs;
+  h->scaled = (flags & QP_CREATE_SCALE) != 0;
+  if (h->scaled) {
+    diagonal_scaling(Qh, Ah, view_of(Th), 10, &h->d1, &h->d2);
+    Qs_ = scaled_copy(Qh, h->d2.data(), h->d2.data());
+    As_ = scaled_copy(Ah, h->d1.data(), h->d2.data());
+    Ts_ = scaled_copy(view_of(Th), h->d2.data(), h->d1.data());
+    Qh = view_of(Qs_);
+    Ah = view_of(As_);
+    Th = std::move(Ts_);
+    cs.resize(size_t(n));
+    bs.resize(size_t(m));
+    for (int32_t j = 0; j < n; ++j) cs[size_t(j)] = h->d2[size_t(j)] * c[j];
+    for (int32_t i = 0; i < m; ++i) bs[size_t(i)] = h->d1[size_t(i)] * b[i];
+    c = cs.data();
+    b = bs.data();
+  } else {
+    h->d1.assign(size_t(m), 1.0);
+    h->d2.assign(size_t(n), 1.0);
+  }
 
   h->n = n;
   h->m = m;
@@ -737,6 +762,20 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   QP_TRY(upload(h, h->v64.b, b, M * sizeof(double)));
   convert(h, h->v64.c, h->v32.c, n);
   convert(h, h->v64.b, h->v32.b, m);
+  if (h->scaled) {
+    std::vector<double> i1(static_cast<size_t>(m)), i2(static_cast<size_t>(n));
+    for (int32_t i = 0; i < m; ++i) i1[size_t(i)] = 1.0 / h->d1[size_t(i)];
+    for (int32_t j = 0; j < n; ++j) i2[size_t(j)] = 1.0 / h->d2[size_t(j)];
+    QP_TRY(dalloc(h, &h->v64.inv_d1, M));
+    QP_TRY(dalloc(h, &h->v64.inv_d2, N));
+    QP_TRY(dalloc(h, &h->v32.inv_d1, M));
+    QP_TRY(dalloc(h, &h->v32.inv_d2, N));
+    QP_TRY(upload(h, h->v64.inv_d1, i1.data(), M * sizeof(double)));
+    QP_TRY(upload(h, h->v64.inv_d2, i2.data(), N * sizeof(double)));
+    convert(h, h->v64.inv_d1, h->v32.inv_d1, m);
+    convert(h, h->v64.inv_d2, h->v32.inv_d2, n);
+    QP_TRY(sync(h));
+  }
 
   const int g_n = std::max({h->Q.G64, h->At.G64, h->Q.G32, h->At.G32});
   const int g_m = std::max(h->A.G64, h->A.G32);
@@ -1113,7 +1152,21 @@ qp_status qp_get_solution(const qp_handle* h, double* x, double* y) {
   if (y && h->m > 0)
     CUDA_TRY(cudaMemcpyAsync(y, avg ? h->v64.y_avg : h->v64.y, size_t(h->m) * sizeof(double),
                              cudaMemcpyDeviceToHost, h->stream));
-  return sync(hh);
+  QP_TRY(sync(hh));
+  if (h->scaled) {  // back to the caller's variables: x = D2 x~, y = D1 y~
+    if (x)
+      for (int32_t j = 0; j < h->n; ++j) x[j] *= h->d2[size_t(j)];
+    if (y)
+      for (int32_t i = 0; i < h->m; ++i) y[i] *= h->d1[size_t(i)];
+  }
+  return QP_OK;
+}
+
+qp_status qp_get_scaling(const qp_handle* h, double* d1, double* d2) {
+  if (!h) return QP_ERR_INVALID_ARG;
+  if (d1) std::copy(h->d1.begin(), h->d1.end(), d1);
+  if (d2) std::copy(h->d2.begin(), h->d2.end(), d2);
+  return QP_OK;
 }
 
 qp_status qp_get_stats(const qp_handle* h, qp_info* info) {
@@ -1133,6 +1186,17 @@ qp_status qp_get_trace(const qp_handle* h, qp_trace_entry* out, int64_t cap, int
 qp_status qp_set_warm_start(qp_handle* h, const double* x0, const double* y0) {
   if (!h) return QP_ERR_INVALID_ARG;
   QP_TRY(begin_call(h));
+  std::vector<double> xs, ys;  // into the solver's variables: x~ = x / D2, y~ = y / D1
+  if (x0 && h->scaled) {
+    xs.resize(size_t(h->n));
+    for (int32_t j = 0; j < h->n; ++j) xs[size_t(j)] = x0[j] / h->d2[size_t(j)];
+    x0 = xs.data();
+  }
+  if (y0 && h->scaled) {
+    ys.resize(size_t(h->m));
+    for (int32_t i = 0; i < h->m; ++i) ys[size_t(i)] = y0[i] / h->d1[size_t(i)];
+    y0 = ys.data();
+  }
   if (x0)
     QP_TRY(upload(h, h->v64.x0, x0, size_t(h->n) * sizeof(double)));
   else

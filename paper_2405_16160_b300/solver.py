@@ -66,7 +66,8 @@ class QPSolver:
     caching allocator and the work is ordered after PyTorch's current stream.
     """
 
-    def __init__(self, inst, torch_memory: bool = True, check_symmetry: bool = False):
+    def __init__(self, inst, torch_memory: bool = True, check_symmetry: bool = False,
+                 scale: bool = False):
         self.lib = L.load_library()
         self.n, self.m, self.m_eq = int(inst.n), int(inst.m), int(inst.m_eq)
         self._keep = []
@@ -82,7 +83,8 @@ class QPSolver:
                                 _ptr(Ar, c_int32), _ptr(Ac, c_int32), _ptr(Av, c_double),
                                 _ptr(c, c_double), _ptr(b, c_double),
                                 byref(ctx) if ctx is not None else None,
-                                L.CREATE_CHECK_SYMMETRY if check_symmetry else 0)
+                                (L.CREATE_CHECK_SYMMETRY if check_symmetry else 0)
+                                | (L.CREATE_SCALE if scale else 0))
         L.check(st, "qp_create")
         self.h = h
         self._ctx = ctx
@@ -119,6 +121,13 @@ class QPSolver:
         L.check(self.lib.qp_get_solution(self.h, _ptr(x, c_double), _ptr(y, c_double)),
                 "qp_get_solution")
         return x, y
+
+    def scaling(self):
+        d1 = np.empty(self.m)
+        d2 = np.empty(self.n)
+        L.check(self.lib.qp_get_scaling(self.h, _ptr(d1, c_double), _ptr(d2, c_double)),
+                "qp_get_scaling")
+        return d1, d2
 
     def stats(self) -> dict:
         info = L.QPInfoC()

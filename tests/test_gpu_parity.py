@@ -387,3 +387,89 @@ def test_mixed_full_size_meets_tolerance(big):
     with open(GOLDEN) as f:
         g = json.load(f)
     assert rescored.primal_obj == pytest.approx(g["primal_obj"], rel=1e-4)
+
+
+# ------------------------------------------------------- Section 4 scaling
+# QP_CREATE_SCALE: D1, D2 from 10 Ruiz steps and one Pock-Chambolle step;
+# the solver iterates on the scaled problem and measures relKKT on the
+# original one.  The oracle computes its own scaling from the paper's steps.
+SCALED_CASES = ["dense_small", "sparse_small", "ragged_eq", "empty_rows", "long_rows",
+                "zipf_small"]
+
+
+@pytest.fixture(scope="module")
+def built_scaled():
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            inst = CASES[name]()
+            P = O.problem_from_instance(inst)
+            d1, d2 = O.diagonal_scaling(P)
+            cache[name] = (inst, P, d1, d2, QPSolver(inst, scale=True))
+        return cache[name]
+
+    yield get
+    for v in cache.values():
+        v[-1].close()
+
+
+@pytest.mark.parametrize("name", SCALED_CASES)
+def test_scaling_matches_oracle(built_scaled, name):
+    inst, P, d1, d2, s = built_scaled(name)
+    g1, g2 = s.scaling()
+    assert _relerr(g1, d1) <= 1e-12 and _relerr(g2, d2) <= 1e-12
+
+
+@pytest.mark.parametrize("name", SCALED_CASES)
+def test_scaled_relkkt_is_measured_on_the_original_problem(built_scaled, name):
+    inst, P, d1, d2, s = built_scaled(name)
+    st = _shared_state(inst, P, 5)  # taken as scaled iterates
+    s.set_state(st)
+    kc, ka = s.evaluate()
+    for got, (x, y) in ((kc, (st["x"], st["y"])), (ka, (st["x_avg"], st["y_avg"]))):
+        ref = O.relkkt(P, d2 * x, d1 * y)
+        for key in ("r_primal", "r_dual", "r_gap", "relkkt", "primal_obj", "dual_obj"):
+            assert got[key] == pytest.approx(getattr(ref, key), rel=1e-12, abs=1e-14), key
+
+
+@pytest.mark.parametrize("name", SCALED_CASES)
+def test_scaled_iteration_matches_oracle(built_scaled, name):
+    inst, P, d1, d2, s = built_scaled(name)
+    Ps = O.scale_problem(P, d1, d2)
+    st = _shared_state(inst, Ps, 6)
+    s.set_state(st)
+    s.iterate(1, cg_mode=L.CG_FIXED, cg_fixed_n=3)
+    got = s.get_state()
+    ost = _oracle_state(st)
+    O.inner_step(Ps, ost, O.OracleOptions(cg_mode=O.CG_FIXED, cg_fixed_n=3))
+    for key in ("x", "y", "x_avg", "y_avg"):
+        assert _relerr(got[key], getattr(ost, key)) <= 1e-10, key
+
+
+@pytest.mark.parametrize("name,tol", [("dense_small", 1e-6), ("sparse_small", 1e-4),
+                                      ("ragged_eq", 1e-4), ("long_rows", 1e-5),
+                                      ("zipf_small", 1e-4)])
+def test_scaled_end_to_end_matches_oracle(built_scaled, name, tol):
+    inst, P, d1, d2, s = built_scaled(name)
+    ores = O.solve(P, O.OracleOptions(tol=tol, scale=True))
+    info = s.solve(tol=tol)
+    x, y = s.solution()
+    assert ores.termination == O.SOLVED and info["termination"] == L.TERM_SOLVED
+    rescored = O.relkkt(P, x, y)
+    assert rescored.relkkt <= tol
+    assert info["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-12)
+    assert rescored.primal_obj == pytest.approx(ores.kkt.primal_obj, rel=1e-4, abs=1e-8)
+    assert info["iterations"] == ores.iterations and info["restarts"] == ores.restarts
+    assert info["cg_steps"] == ores.cg_steps
+    assert _relerr(x, ores.x) <= 1e-8
+
+
+@pytest.mark.parametrize("name,tol", [("sparse_small", 1e-4), ("long_rows", 1e-5),
+                                      ("zipf_small", 1e-4)])
+def test_scaled_mixed_solve_meets_tolerance(built_scaled, name, tol):
+    inst, P, d1, d2, s = built_scaled(name)
+    info = s.solve(tol=tol, precision=L.PREC_MIXED)
+    x, y = s.solution()
+    assert info["termination"] == L.TERM_SOLVED
+    assert O.relkkt(P, x, y).relkkt <= tol
