@@ -216,8 +216,11 @@ void qp_destroy(qp_handle* h);
  */
 qp_status qp_solve(qp_handle* h, const qp_options* o, qp_info* info);
 
-/* Copy the returned iterate to host arrays x (n) and y (m); either may be NULL.
- * With QP_CREATE_SCALE these are the caller's variables (x = D2 x~, y = D1 y~). */
+/* Copy the iterate returned by the last qp_solve to host arrays x (n) and y
+ * (m); either may be NULL.  With QP_CREATE_SCALE these are the caller's
+ * variables (x = D2 x~, y = D1 y~).  QP_ERR_NOT_SOLVED before a successful
+ * qp_solve and after qp_iterate or qp_set_state (read those with
+ * qp_get_state). */
 qp_status qp_get_solution(const qp_handle* h, double* x, double* y);
 
 /* The diagonal scaling of QP_CREATE_SCALE: d1 (m) for constraints and d2 (n)

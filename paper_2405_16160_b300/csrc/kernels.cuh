@@ -33,6 +33,8 @@
 #include <math_constants.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace pdhcg {
 
 constexpr int kBlock = 256;
@@ -134,6 +136,24 @@ __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+// Compensated FP32 storage of the accumulating iterates (x, y and their
+// running averages) on the mixed path: the value is hi + lo, the SpMVs read
+// hi, and lo keeps the rounding error of every update (two-sum, then the
+// pair renormalised so that |lo| <= ulp(hi)/2).  Without it a step below half
+// an ulp of hi is lost, which stalls the iteration on coordinates whose
+// diagonal scaling makes the iterate large and its residual small.
+__device__ __forceinline__ void split_add(float& hi, float& lo, float d) {
+  const float s = __fadd_rn(hi, d);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+  const float t = __fadd_rn(lo, e);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+template <class T>
+constexpr bool kSplit = std::is_same<T, float>::value;
 
 template <class T>
 __device__ __forceinline__ T shfl_xor(T v, int o) {
@@ -501,7 +521,7 @@ constexpr int kCgBlocksPerSm = 3;
 
 template <int G, class T>
 __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
-    k_cg(CsrT<T> Q, LongRows LQ, T* qseg, T* qlong, T* x, T* r, T* p, T* q, T* qx,
+    k_cg(CsrT<T> Q, LongRows LQ, T* qseg, T* qlong, T* x, T* x_lo, T* r, T* p, T* q, T* qx,
          const double* r0r0, double* part, DevState* st, GridBarrier* bar, int n) {
   using A = typename Acc<T>::type;
   const bool active = running(st) && st->k_total < st->opt.max_iter;
@@ -561,7 +581,14 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     for (long long i = t0; i < n; i += nt) {
       const T pi = p[i], qpi = q[i];
       const T qi = qpi + pi * inv_tau;
-      x[i] = add_rn(x[i], mul_rn(alpha, pi));
+      if constexpr (kSplit<T>) {
+        T hi = x[i], lo = x_lo[i];
+        split_add(hi, lo, mul_rn(alpha, pi));
+        x[i] = hi;
+        x_lo[i] = lo;
+      } else {
+        x[i] = add_rn(x[i], mul_rn(alpha, pi));
+      }
       qx[i] = add_rn(qx[i], mul_rn(alpha, qpi));
       const T ri = sub_rn(r[i], mul_rn(alpha, qi));
       r[i] = ri;
@@ -599,19 +626,37 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
 // A x cache and the running average of y are updated in the same pass.
 template <int G, class T>
 __global__ void __launch_bounds__(kBlock) k_dual(CsrT<T> A, const T* __restrict__ x,
-                                                 const T* __restrict__ b, T* y, T* ax, T* y_avg,
-                                                 const DevState* st) {
+                                                 const T* __restrict__ b, T* y, T* y_lo, T* ax,
+                                                 T* y_avg, T* ya_lo, const DevState* st) {
   if (!st->iter_active) return;
   const T sigma = T(st->sigma);
   const T inv_j = T(1.0 / (double)st->j);
+  const bool first = st->j == 1;
   const int m_eq = st->opt.m_eq;
   spmv_rows<G>(A, x, [&](int i, T s, bool lead) {
     if (lead) {
-      T yn = y[i] + sigma * (T(2) * s - ax[i] - b[i]);
-      if (i >= m_eq && yn < T(0)) yn = T(0);
-      y[i] = yn;
-      ax[i] = s;
-      y_avg[i] += (yn - y_avg[i]) * inv_j;
+      if constexpr (kSplit<T>) {
+        T hi = y[i], lo = y_lo[i];
+        split_add(hi, lo, sigma * (T(2) * s - ax[i] - b[i]));
+        if (i >= m_eq && hi < T(0)) hi = lo = T(0);
+        y[i] = hi;
+        y_lo[i] = lo;
+        ax[i] = s;
+        T ah = hi, al = lo;
+        if (!first) {
+          ah = y_avg[i];
+          al = ya_lo[i];
+          split_add(ah, al, ((hi - ah) + (lo - al)) * inv_j);
+        }
+        y_avg[i] = ah;
+        ya_lo[i] = al;
+      } else {
+        T yn = y[i] + sigma * (T(2) * s - ax[i] - b[i]);
+        if (i >= m_eq && yn < T(0)) yn = T(0);
+        y[i] = yn;
+        ax[i] = s;
+        y_avg[i] += (yn - y_avg[i]) * inv_j;
+      }
     }
   });
 }
@@ -620,18 +665,32 @@ __global__ void __launch_bounds__(kBlock) k_dual(CsrT<T> A, const T* __restrict_
 // with the next CG's start: r0 = p0 = -(qx + c + A'y+) and r0'r0 partials.
 template <int G, class T>
 __global__ void __launch_bounds__(kBlock) k_atv(CsrT<T> At, const T* __restrict__ y, T* aty,
-                                                const T* __restrict__ x, T* x_avg,
+                                                const T* __restrict__ x,
+                                                const T* __restrict__ x_lo, T* x_avg, T* xa_lo,
                                                 const T* __restrict__ qx,
                                                 const T* __restrict__ c, T* r, T* p,
                                                 double* part_r0, unsigned int* ticket,
                                                 const DevState* st) {
   if (!st->iter_active) return;
   const T inv_j = T(1.0 / (double)st->j);
+  const bool first = st->j == 1;
   typename Acc<T>::type acc;
   spmv_rows<G>(At, y, [&](int i, T s, bool lead) {
     if (lead) {
       aty[i] = s;
-      x_avg[i] += (x[i] - x_avg[i]) * inv_j;
+      if constexpr (kSplit<T>) {
+        const T xh = x[i], xl = x_lo[i];
+        T ah = xh, al = xl;
+        if (!first) {
+          ah = x_avg[i];
+          al = xa_lo[i];
+          split_add(ah, al, ((xh - ah) + (xl - al)) * inv_j);
+        }
+        x_avg[i] = ah;
+        xa_lo[i] = al;
+      } else {
+        x_avg[i] += (x[i] - x_avg[i]) * inv_j;
+      }
       const T ri = -(qx[i] + c[i] + s);
       r[i] = ri;
       p[i] = ri;
@@ -860,7 +919,8 @@ __global__ void k_control(const double* part_n, int gn, const double* part_m, in
 // Restart to the candidate (Algorithm 1, restart step), n side: distance to
 // the previous restart point for the primal weight, then anchor = x = cand.
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_restart_n(T* x, const T* __restrict__ x_avg,
+__global__ void __launch_bounds__(kBlock) k_restart_n(T* x, T* x_lo, const T* __restrict__ x_avg,
+                                                      const T* __restrict__ xa_lo,
                                                       T* x_anchor, T* aty,
                                                       const T* __restrict__ aty_avg, T* qx,
                                                       const T* __restrict__ qx_avg,
@@ -877,13 +937,15 @@ __global__ void __launch_bounds__(kBlock) k_restart_n(T* x, const T* __restrict_
     if (pending == 2) {
       aty[i] = aty_avg[i];
       qx[i] = qx_avg[i];
+      if constexpr (kSplit<T>) x_lo[i] = xa_lo[i];
     }
   }
   block_sum_store(acc, part + blockIdx.x);
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_restart_m(T* y, const T* __restrict__ y_avg,
+__global__ void __launch_bounds__(kBlock) k_restart_m(T* y, T* y_lo, const T* __restrict__ y_avg,
+                                                      const T* __restrict__ ya_lo,
                                                       T* y_anchor, T* ax,
                                                       const T* __restrict__ ax_avg,
                                                       const DevState* st, int m, double* part) {
@@ -896,7 +958,10 @@ __global__ void __launch_bounds__(kBlock) k_restart_m(T* y, const T* __restrict_
     acc.add_prod(d, d);
     y_anchor[i] = cand;
     y[i] = cand;
-    if (pending == 2) ax[i] = ax_avg[i];
+    if (pending == 2) {
+      ax[i] = ax_avg[i];
+      if constexpr (kSplit<T>) y_lo[i] = ya_lo[i];
+    }
   }
   block_sum_store(acc, part + blockIdx.x);
 }
@@ -926,20 +991,30 @@ __global__ void k_restart_finish(const double* part_n, int gn, const double* par
 
 // ---------------------------------------------------------- set-up kernels
 // Start of a solve: cold start zeros everything; warm start copies (x0, y0).
+// The compensation words (FP32 only; null for FP64) start at zero.
 template <class T>
 __global__ void k_init_vectors(T* x, T* x_avg, T* x_anchor, const T* __restrict__ x0, int n, T* y,
-                               T* y_avg, T* y_anchor, const T* __restrict__ y0, int m) {
+                               T* y_avg, T* y_anchor, const T* __restrict__ y0, int m, T* x_lo,
+                               T* xa_lo, T* y_lo, T* ya_lo) {
   for (long long i = grid_tid(); i < n; i += grid_threads()) {
     const T v = x0 ? x0[i] : T(0);
     x[i] = v;
     x_anchor[i] = v;
     x_avg[i] = T(0);
+    if (x_lo) {
+      x_lo[i] = T(0);
+      xa_lo[i] = T(0);
+    }
   }
   for (long long i = grid_tid(); i < m; i += grid_threads()) {
     const T v = y0 ? y0[i] : T(0);
     y[i] = v;
     y_anchor[i] = v;
     y_avg[i] = T(0);
+    if (y_lo) {
+      y_lo[i] = T(0);
+      ya_lo[i] = T(0);
+    }
   }
 }
 
@@ -971,6 +1046,20 @@ __global__ void k_pow_scale(const T* __restrict__ w, T* v, int n, const double* 
 template <class Ti, class To>
 __global__ void k_convert(const Ti* __restrict__ in, To* out, int n) {
   for (long long i = grid_tid(); i < n; i += grid_threads()) out[i] = To(in[i]);
+}
+
+// Conversion of an iterate that may carry a compensation word on either
+// side: v = in + in_lo (in_lo may be null), out = round(v), out_lo = the
+// rounding error of out when out_lo is not null.
+template <class Ti, class To>
+__global__ void k_convert_split(const Ti* __restrict__ in, const Ti* __restrict__ in_lo, To* out,
+                                To* out_lo, int n) {
+  for (long long i = grid_tid(); i < n; i += grid_threads()) {
+    const double v = in_lo ? (double)in[i] + (double)in_lo[i] : (double)in[i];
+    const To o = To(v);
+    out[i] = o;
+    if (out_lo) out_lo[i] = To(v - (double)o);
+  }
 }
 
 // eta = 1/(2||A||_2) (Section 3.2), omega0 = ||c||/||b|| (1 if either is ~0),

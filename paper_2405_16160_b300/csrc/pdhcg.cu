@@ -137,6 +137,8 @@ struct VecSet {
   T *x0 = nullptr, *y0 = nullptr;
   T *pw_v = nullptr, *pw_u = nullptr, *pw_w = nullptr;
   T *inv_d1 = nullptr, *inv_d2 = nullptr;  // 1/D1, 1/D2 with diagonal scaling, else null
+  // compensation words of x, x~, y, y~ (FP32 set only; the value is hi + lo)
+  T *x_lo = nullptr, *xa_lo = nullptr, *y_lo = nullptr, *ya_lo = nullptr;
 };
 
 constexpr int kPrecFp64 = QP_PREC_FP64;
@@ -308,7 +310,7 @@ qp_status launch_cg(qp_handle* h, bool coop) {
       cfg.numAttrs = 1;
     }
     cudaLaunchKernelEx(&cfg, k_cg<G, T>, view<T>(h->Q), long_rows_of(h->Q), seg_buf<T>(h->Q),
-                       long_buf<T>(h->Q), v.x, v.r, v.p, v.q, v.qx,
+                       long_buf<T>(h->Q), v.x, v.x_lo, v.r, v.p, v.q, v.qx,
                        (const double*)(h->part_r0 + h->grid_n), h->part_cg, h->st, h->bar,
                        (int)h->n);
   });
@@ -320,8 +322,8 @@ qp_status launch_dual(qp_handle* h) {
   launch_long<T>(h, h->A, v.x);
   return dispatch_g(lanes<T>(h->A), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    k_dual<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(view<T>(h->A), v.x, v.b, v.y, v.ax, v.y_avg,
-                                                      h->st);
+    k_dual<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(view<T>(h->A), v.x, v.b, v.y, v.y_lo, v.ax,
+                                                      v.y_avg, v.ya_lo, h->st);
   });
 }
 
@@ -331,8 +333,8 @@ qp_status launch_atv(qp_handle* h) {
   launch_long<T>(h, h->At, v.y);
   return dispatch_g(lanes<T>(h->At), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    k_atv<G, T><<<h->grid_n, kBlock, 0, h->stream>>>(view<T>(h->At), v.y, v.aty, v.x, v.x_avg,
-                                                     v.qx, v.c, v.r, v.p, h->part_r0, h->ticket,
+    k_atv<G, T><<<h->grid_n, kBlock, 0, h->stream>>>(view<T>(h->At), v.y, v.aty, v.x, v.x_lo,
+                                                     v.x_avg, v.xa_lo, v.qx, v.c, v.r, v.p, h->part_r0, h->ticket,
                                                      h->st);
   });
 }
@@ -367,11 +369,13 @@ qp_status launch_eval(qp_handle* h, int mode) {
 template <class T>
 qp_status launch_restart(qp_handle* h) {
   VecSet<T>& v = vecs<T>(h);
-  k_restart_n<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.x, v.x_avg, v.x_anchor, v.aty,
+  k_restart_n<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.x, v.x_lo, v.x_avg, v.xa_lo,
+                                                        v.x_anchor, v.aty,
                                                         v.aty_avg, v.qx, v.qx_avg, h->st, h->n,
                                                         h->part_rn);
-  k_restart_m<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.y, v.y_avg, v.y_anchor, v.ax, v.ax_avg,
-                                                        h->st, h->m, h->part_rm);
+  k_restart_m<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.y, v.y_lo, v.y_avg, v.ya_lo,
+                                                        v.y_anchor, v.ax, v.ax_avg, h->st, h->m,
+                                                        h->part_rm);
   k_restart_finish<<<1, 32, 0, h->stream>>>(h->part_rn, h->grid_vec, h->part_rm, h->grid_vec,
                                             h->st);
   return QP_OK;
@@ -424,16 +428,24 @@ void convert(qp_handle* h, const Ti* in, To* out, int count) {
   if (count > 0) k_convert<Ti, To><<<h->grid_vec, kBlock, 0, h->stream>>>(in, out, count);
 }
 
+// Copy of an iterate across precisions, through the compensation words of
+// the FP32 side (in_lo / out_lo, null on the FP64 side).
+template <class Ti, class To>
+void convert_split(qp_handle* h, const Ti* in, const Ti* in_lo, To* out, To* out_lo, int count) {
+  if (count > 0)
+    k_convert_split<Ti, To><<<h->grid_vec, kBlock, 0, h->stream>>>(in, in_lo, out, out_lo, count);
+}
+
 // Copy the iterate vectors of one precision into the other.
 template <class Ti, class To>
 void convert_state(qp_handle* h) {
   VecSet<Ti>& a = vecs<Ti>(h);
   VecSet<To>& b = vecs<To>(h);
-  convert(h, a.x, b.x, h->n);
-  convert(h, a.x_avg, b.x_avg, h->n);
+  convert_split(h, a.x, a.x_lo, b.x, b.x_lo, h->n);
+  convert_split(h, a.x_avg, a.xa_lo, b.x_avg, b.xa_lo, h->n);
   convert(h, a.x_anchor, b.x_anchor, h->n);
-  convert(h, a.y, b.y, h->m);
-  convert(h, a.y_avg, b.y_avg, h->m);
+  convert_split(h, a.y, a.y_lo, b.y, b.y_lo, h->m);
+  convert_split(h, a.y_avg, a.ya_lo, b.y_avg, b.ya_lo, h->m);
   convert(h, a.y_anchor, b.y_anchor, h->m);
 }
 
@@ -631,6 +643,16 @@ qp_status alloc_vecs(qp_handle* h) {
   for (T** p : nv) QP_TRY(dalloc(h, p, N));
   T** mv[] = {&v.b, &v.y, &v.ax, &v.y_avg, &v.y_anchor, &v.ax_avg, &v.y0, &v.pw_u};
   for (T** p : mv) QP_TRY(dalloc(h, p, M));
+  if (std::is_same<T, float>::value) {
+    QP_TRY(dalloc(h, &v.x_lo, N));
+    QP_TRY(dalloc(h, &v.xa_lo, N));
+    QP_TRY(dalloc(h, &v.y_lo, M));
+    QP_TRY(dalloc(h, &v.ya_lo, M));
+    CUDA_TRY(cudaMemsetAsync(v.x_lo, 0, N * sizeof(T), h->stream));
+    CUDA_TRY(cudaMemsetAsync(v.xa_lo, 0, N * sizeof(T), h->stream));
+    CUDA_TRY(cudaMemsetAsync(v.y_lo, 0, std::max<size_t>(M, 1) * sizeof(T), h->stream));
+    CUDA_TRY(cudaMemsetAsync(v.ya_lo, 0, std::max<size_t>(M, 1) * sizeof(T), h->stream));
+  }
   CUDA_TRY(cudaMemsetAsync(v.x0, 0, N * sizeof(T), h->stream));
   CUDA_TRY(cudaMemsetAsync(v.y0, 0, std::max<size_t>(M, 1) * sizeof(T), h->stream));
   return QP_OK;
@@ -836,7 +858,7 @@ qp_status start_solve(qp_handle* h, const qp_options* o) {
   }
   k_init_vectors<T><<<h->grid_vec, kBlock, 0, h->stream>>>(
       v.x, v.x_avg, v.x_anchor, warm ? v.x0 : nullptr, h->n, v.y, v.y_avg, v.y_anchor,
-      warm ? v.y0 : nullptr, h->m);
+      warm ? v.y0 : nullptr, h->m, v.x_lo, v.xa_lo, v.y_lo, v.ya_lo);
   QP_TRY(recompute_caches<T>(h));
   QP_TRY(launch_setup<T>(h, o->power_iters, 1));
   QP_TRY(launch_eval<T>(h, 0));
@@ -909,8 +931,10 @@ qp_status promote_and_refine(qp_handle* h, const qp_options* o, bool timing,
   const bool avg = h->h_st->returned_avg != 0;
   info->mixed_iterations = h->h_st->k_total;
   info->mixed_relkkt = h->h_st->kkt_ret[3];
-  convert(h, avg ? h->v32.x_avg : h->v32.x, h->v64.x, h->n);
-  convert(h, avg ? h->v32.y_avg : h->v32.y, h->v64.y, h->m);
+  convert_split(h, avg ? h->v32.x_avg : h->v32.x, avg ? h->v32.xa_lo : h->v32.x_lo, h->v64.x,
+                (double*)nullptr, h->n);
+  convert_split(h, avg ? h->v32.y_avg : h->v32.y, avg ? h->v32.ya_lo : h->v32.y_lo, h->v64.y,
+                (double*)nullptr, h->m);
   CUDA_TRY(cudaMemcpyAsync(h->v64.x_anchor, h->v64.x, size_t(h->n) * sizeof(double),
                            cudaMemcpyDeviceToDevice, h->stream));
   if (h->m > 0)
@@ -1220,17 +1244,28 @@ qp_status qp_get_state(const qp_handle* hc, const qp_state_vectors* v, qp_state_
   const size_t N = size_t(h->n), M = size_t(h->m);
   if (v) {
     if (h->active_prec == kPrecMixed) {
-      // widen the FP32 iterate on the host
-      std::vector<float> tmp(std::max<size_t>(std::max(N, M), 1));
-      const std::pair<double*, float*> all[] = {
-          {v->x, h->v32.x}, {v->x_avg, h->v32.x_avg}, {v->x_anchor, h->v32.x_anchor},
-          {v->y, h->v32.y}, {v->y_avg, h->v32.y_avg}, {v->y_anchor, h->v32.y_anchor}};
+      // widen the FP32 iterate (hi + lo) on the host
+      std::vector<float> tmp(std::max<size_t>(std::max(N, M), 1)), tlo(tmp.size());
+      struct Src {
+        double* out;
+        const float* hi;
+        const float* lo;
+      };
+      const Src all[] = {{v->x, h->v32.x, h->v32.x_lo},
+                         {v->x_avg, h->v32.x_avg, h->v32.xa_lo},
+                         {v->x_anchor, h->v32.x_anchor, nullptr},
+                         {v->y, h->v32.y, h->v32.y_lo},
+                         {v->y_avg, h->v32.y_avg, h->v32.ya_lo},
+                         {v->y_anchor, h->v32.y_anchor, nullptr}};
       for (int i = 0; i < 6; ++i) {
         const size_t cnt = i < 3 ? N : M;
-        if (!all[i].first || cnt == 0) continue;
-        CUDA_TRY(cudaMemcpy(tmp.data(), all[i].second, cnt * sizeof(float),
-                            cudaMemcpyDeviceToHost));
-        for (size_t k = 0; k < cnt; ++k) all[i].first[k] = double(tmp[k]);
+        if (!all[i].out || cnt == 0) continue;
+        CUDA_TRY(cudaMemcpy(tmp.data(), all[i].hi, cnt * sizeof(float), cudaMemcpyDeviceToHost));
+        if (all[i].lo)
+          CUDA_TRY(cudaMemcpy(tlo.data(), all[i].lo, cnt * sizeof(float),
+                              cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < cnt; ++k)
+          all[i].out[k] = double(tmp[k]) + (all[i].lo ? double(tlo[k]) : 0.0);
       }
     } else {
       const std::pair<double*, double*> nv[] = {
@@ -1271,6 +1306,7 @@ qp_status qp_set_state(qp_handle* h, const qp_state_vectors* v, const qp_state_s
     return QP_ERR_INVALID_ARG;
   }
   QP_TRY(begin_call(h));
+  h->solved = false;  // the returned iterate of the last solve is gone
   const size_t nb = size_t(h->n) * sizeof(double), mb = size_t(h->m) * sizeof(double);
   const std::pair<const double*, double*> nv[] = {
       {v->x, h->v64.x}, {v->x_avg, h->v64.x_avg}, {v->x_anchor, h->v64.x_anchor}};
@@ -1321,6 +1357,7 @@ qp_status qp_iterate(qp_handle* h, const qp_options* o, int64_t iters) {
   if (!h || iters < 0) return QP_ERR_INVALID_ARG;
   QP_TRY(validate_options(o));
   QP_TRY(begin_call(h));
+  h->solved = false;  // the returned iterate of the last solve is gone
   QP_TRY(read_state(h));
   DevState& d = *h->h_st;
   fill_dev_options(h, o, &d.opt);
