@@ -19,9 +19,16 @@
 //               arithmetic.  Dot products use exact FP32 products and
 //               compensated (double-float) sums up to the block, and FP64
 //               across blocks; every scalar of the method (alpha, beta, tau,
-//               sigma, omega, eps, relKKT, restart tests) is FP64.
+//               sigma, omega, eps, relKKT, restart tests) is FP64.  x is held
+//               as the restart point x_a (a compensated FP32 pair, fixed for
+//               an epoch) plus the FP32 displacement dx, and the iteration
+//               runs on dx with b - A x_a in place of b; y and its average
+//               are compensated pairs.  A column of A shared by millions of
+//               rows would otherwise move all of their dual steps at once
+//               each time its FP32 value stepped by an ulp.
 // This GPU's FP64 pipe runs at ~1/58 of FP32, so the mixed path keeps FP64
-// instructions out of the per-element work entirely.
+// instructions out of the per-iteration element work (long-row segment sums
+// aside, which are a small part of any SpMV).
 //
 // Reductions never use floating-point atomics: each block writes partials,
 // and every consumer reduces them in one fixed order, so results do not
@@ -137,12 +144,10 @@ __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 
-// Compensated FP32 storage of the accumulating iterates (x, y and their
-// running averages) on the mixed path: the value is hi + lo, the SpMVs read
-// hi, and lo keeps the rounding error of every update (two-sum, then the
-// pair renormalised so that |lo| <= ulp(hi)/2).  Without it a step below half
-// an ulp of hi is lost, which stalls the iteration on coordinates whose
-// diagonal scaling makes the iterate large and its residual small.
+// Compensated FP32 storage on the mixed path (y, its running average and the
+// x restart point): the value is hi + lo, the SpMVs read hi, and lo keeps the
+// rounding error of every update (two-sum, then the pair renormalised so that
+// |lo| <= ulp(hi)/2).  Without it a step below half an ulp of hi is lost.
 __device__ __forceinline__ void split_add(float& hi, float& lo, float d) {
   const float s = __fadd_rn(hi, d);
   const float bb = __fsub_rn(s, hi);
@@ -433,14 +438,34 @@ __device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f) {
   }
 }
 
+// Segment sum of a long row with the products and the sum carried in FP64
+// (a product of two FP32 numbers is exact in FP64).  A row of millions of
+// entries would otherwise pick up an FP32 rounding error that grows with its
+// length, on exactly the coordinates (high-degree columns of A, i.e. long
+// rows of A') where the scaled residual is smallest.
 template <class T>
-__device__ __forceinline__ T warp_sum_t(T v) {
+__device__ __forceinline__ double row_dot_wide(const CsrT<T>& M, const T* v, int b, int e,
+                                               int lane) {
+  double s = 0.0;
+  for (int k = b + lane; k < e; k += kUnroll * 32) {
+    int c[kUnroll];
+    T a[kUnroll], xv[kUnroll];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
-  return v;
+    for (int j = 0; j < kUnroll; ++j) {
+      const int kk = k + j * 32;
+      c[j] = kk < e ? __ldg(M.col + kk) : -1;
+      a[j] = kk < e ? __ldg(M.val + kk) : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) xv[j] = c[j] >= 0 ? v[c[j]] : T(0);
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) s = fma((double)a[j], (double)xv[j], s);
+  }
+  return s;
 }
 
 // Long-row pre-pass, phase 1: one warp per segment (grid-stride over warps).
+// The segment sums are accumulated in FP64 for both value types.
 template <class T>
 __device__ __forceinline__ void long_segments(const CsrT<T>& M, const T* v, const LongRows& L,
                                               T* seg_part) {
@@ -448,22 +473,22 @@ __device__ __forceinline__ void long_segments(const CsrT<T>& M, const T* v, cons
   const long long nw = grid_threads() >> 5;
   for (long long sg = grid_tid() >> 5; sg < L.nseg; sg += nw) {
     const int e = __ldg(L.seg_end + sg);
-    const T s = warp_sum_t(row_dot<32>(M, v, __ldg(L.seg_begin + sg), e, lane));
-    if (lane == 0) seg_part[sg] = s;
+    const double s = warp_sum(row_dot_wide(M, v, __ldg(L.seg_begin + sg), e, lane));
+    if (lane == 0) seg_part[sg] = T(s);
   }
 }
 
-// Phase 2: one warp per long row sums its segments in index order.
+// Phase 2: one warp per long row sums its segments in index order (in FP64).
 template <class T>
 __device__ __forceinline__ void long_finish(const LongRows& L, const T* seg_part, T* long_val) {
   const int lane = threadIdx.x & 31;
   const long long nw = grid_threads() >> 5;
   for (long long r = grid_tid() >> 5; r < L.nlong; r += nw) {
-    T s = T(0);
+    double s = 0.0;
     for (int k = __ldg(L.seg_ptr + r) + lane; k < __ldg(L.seg_ptr + r + 1); k += 32)
-      s += __ldcg(seg_part + k);
-    s = warp_sum_t(s);
-    if (lane == 0) long_val[r] = s;
+      s += (double)__ldcg(seg_part + k);
+    s = warp_sum(s);
+    if (lane == 0) long_val[r] = T(s);
   }
 }
 
@@ -521,7 +546,7 @@ constexpr int kCgBlocksPerSm = 3;
 
 template <int G, class T>
 __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
-    k_cg(CsrT<T> Q, LongRows LQ, T* qseg, T* qlong, T* x, T* x_lo, T* r, T* p, T* q, T* qx,
+    k_cg(CsrT<T> Q, LongRows LQ, T* qseg, T* qlong, T* x, T* r, T* p, T* q, T* qx,
          const double* r0r0, double* part, DevState* st, GridBarrier* bar, int n) {
   using A = typename Acc<T>::type;
   const bool active = running(st) && st->k_total < st->opt.max_iter;
@@ -581,14 +606,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     for (long long i = t0; i < n; i += nt) {
       const T pi = p[i], qpi = q[i];
       const T qi = qpi + pi * inv_tau;
-      if constexpr (kSplit<T>) {
-        T hi = x[i], lo = x_lo[i];
-        split_add(hi, lo, mul_rn(alpha, pi));
-        x[i] = hi;
-        x_lo[i] = lo;
-      } else {
-        x[i] = add_rn(x[i], mul_rn(alpha, pi));
-      }
+      x[i] = add_rn(x[i], mul_rn(alpha, pi));
       qx[i] = add_rn(qx[i], mul_rn(alpha, qpi));
       const T ri = sub_rn(r[i], mul_rn(alpha, qi));
       r[i] = ri;
@@ -623,7 +641,10 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
 
 // ------------------------------------------- dual step (Algorithm 1, y-update)
 // y+ = y + sigma (2 A x+ - A x - b), projected to >= 0 on rows >= m_eq; the
-// A x cache and the running average of y are updated in the same pass.
+// A x cache and the running average of y are updated in the same pass.  The
+// mixed path passes the displacement dx = x - x_a from the restart point x_a
+// as x, b - A x_a as b and A dx as the cache: the same step, but every FP32
+// quantity it gathers or subtracts is small near convergence.
 template <int G, class T>
 __global__ void __launch_bounds__(kBlock) k_dual(CsrT<T> A, const T* __restrict__ x,
                                                  const T* __restrict__ b, T* y, T* y_lo, T* ax,
@@ -663,34 +684,21 @@ __global__ void __launch_bounds__(kBlock) k_dual(CsrT<T> A, const T* __restrict_
 
 // A' y+ over the explicit transpose, fused with the running average of x and
 // with the next CG's start: r0 = p0 = -(qx + c + A'y+) and r0'r0 partials.
+// (The mixed path averages the displacement dx, see k_dual.)
 template <int G, class T>
 __global__ void __launch_bounds__(kBlock) k_atv(CsrT<T> At, const T* __restrict__ y, T* aty,
-                                                const T* __restrict__ x,
-                                                const T* __restrict__ x_lo, T* x_avg, T* xa_lo,
+                                                const T* __restrict__ x, T* x_avg,
                                                 const T* __restrict__ qx,
                                                 const T* __restrict__ c, T* r, T* p,
                                                 double* part_r0, unsigned int* ticket,
                                                 const DevState* st) {
   if (!st->iter_active) return;
   const T inv_j = T(1.0 / (double)st->j);
-  const bool first = st->j == 1;
   typename Acc<T>::type acc;
   spmv_rows<G>(At, y, [&](int i, T s, bool lead) {
     if (lead) {
       aty[i] = s;
-      if constexpr (kSplit<T>) {
-        const T xh = x[i], xl = x_lo[i];
-        T ah = xh, al = xl;
-        if (!first) {
-          ah = x_avg[i];
-          al = xa_lo[i];
-          split_add(ah, al, ((xh - ah) + (xl - al)) * inv_j);
-        }
-        x_avg[i] = ah;
-        xa_lo[i] = al;
-      } else {
-        x_avg[i] += (x[i] - x_avg[i]) * inv_j;
-      }
+      x_avg[i] += (x[i] - x_avg[i]) * inv_j;
       const T ri = -(qx[i] + c[i] + s);
       r[i] = ri;
       p[i] = ri;
@@ -919,8 +927,7 @@ __global__ void k_control(const double* part_n, int gn, const double* part_m, in
 // Restart to the candidate (Algorithm 1, restart step), n side: distance to
 // the previous restart point for the primal weight, then anchor = x = cand.
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_restart_n(T* x, T* x_lo, const T* __restrict__ x_avg,
-                                                      const T* __restrict__ xa_lo,
+__global__ void __launch_bounds__(kBlock) k_restart_n(T* x, const T* __restrict__ x_avg,
                                                       T* x_anchor, T* aty,
                                                       const T* __restrict__ aty_avg, T* qx,
                                                       const T* __restrict__ qx_avg,
@@ -937,17 +944,51 @@ __global__ void __launch_bounds__(kBlock) k_restart_n(T* x, T* x_lo, const T* __
     if (pending == 2) {
       aty[i] = aty_avg[i];
       qx[i] = qx_avg[i];
-      if constexpr (kSplit<T>) x_lo[i] = xa_lo[i];
     }
   }
   block_sum_store(acc, part + blockIdx.x);
 }
 
+// Mixed path, n side: the candidate is the restart point plus dx (or plus the
+// average of dx), so its distance to the restart point is that displacement;
+// the restart point (x_a, x_a_lo) moves by it and dx and its average restart
+// from zero.
+__global__ void __launch_bounds__(kBlock) k_restart_n_delta(float* x_a, float* x_a_lo, float* dx,
+                                                            float* dx_avg, float* aty,
+                                                            const float* __restrict__ aty_avg,
+                                                            float* qx,
+                                                            const float* __restrict__ qx_avg,
+                                                            const DevState* st, int n,
+                                                            double* part) {
+  const int pending = st->restart_pending;
+  if (pending == 0) return;
+  AccF acc;
+  for (long long i = grid_tid(); i < n; i += grid_threads()) {
+    const float d = pending == 2 ? dx_avg[i] : dx[i];
+    acc.add_prod(d, d);
+    float hi = x_a[i], lo = x_a_lo[i];
+    split_add(hi, lo, d);
+    x_a[i] = hi;
+    x_a_lo[i] = lo;
+    dx[i] = 0.f;
+    dx_avg[i] = 0.f;
+    if (pending == 2) {
+      aty[i] = aty_avg[i];
+      qx[i] = qx_avg[i];
+    }
+  }
+  block_sum_store(acc, part + blockIdx.x);
+}
+
+// The mixed path passes A dx as ax and also b - A x_a (b_shift) with b: the
+// new restart point x_a' = x_a + dx (or + the average of dx, whose product
+// A x~ is ax_avg) gives b - A x_a' and A dx' = 0.
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_restart_m(T* y, T* y_lo, const T* __restrict__ y_avg,
                                                       const T* __restrict__ ya_lo,
                                                       T* y_anchor, T* ax,
-                                                      const T* __restrict__ ax_avg,
+                                                      const T* __restrict__ ax_avg, T* b_shift,
+                                                      const T* __restrict__ b,
                                                       const DevState* st, int m, double* part) {
   const int pending = st->restart_pending;
   if (pending == 0) return;
@@ -958,9 +999,16 @@ __global__ void __launch_bounds__(kBlock) k_restart_m(T* y, T* y_lo, const T* __
     acc.add_prod(d, d);
     y_anchor[i] = cand;
     y[i] = cand;
-    if (pending == 2) {
-      ax[i] = ax_avg[i];
-      if constexpr (kSplit<T>) y_lo[i] = ya_lo[i];
+    if constexpr (kSplit<T>) {
+      if (pending == 2) {
+        y_lo[i] = ya_lo[i];
+        b_shift[i] = b[i] - ax_avg[i];
+      } else {
+        b_shift[i] -= ax[i];
+      }
+      ax[i] = T(0);
+    } else {
+      if (pending == 2) ax[i] = ax_avg[i];
     }
   }
   block_sum_store(acc, part + blockIdx.x);
@@ -991,19 +1039,22 @@ __global__ void k_restart_finish(const double* part_n, int gn, const double* par
 
 // ---------------------------------------------------------- set-up kernels
 // Start of a solve: cold start zeros everything; warm start copies (x0, y0).
-// The compensation words (FP32 only; null for FP64) start at zero.
+// The mixed path's extra words (null for FP64) start at zero: the low word
+// of the restart point, the displacement dx and its average, and the low
+// words of y and of its average.
 template <class T>
 __global__ void k_init_vectors(T* x, T* x_avg, T* x_anchor, const T* __restrict__ x0, int n, T* y,
-                               T* y_avg, T* y_anchor, const T* __restrict__ y0, int m, T* x_lo,
-                               T* xa_lo, T* y_lo, T* ya_lo) {
+                               T* y_avg, T* y_anchor, const T* __restrict__ y0, int m, T* x_a_lo,
+                               T* dx, T* dx_avg, T* y_lo, T* ya_lo) {
   for (long long i = grid_tid(); i < n; i += grid_threads()) {
     const T v = x0 ? x0[i] : T(0);
     x[i] = v;
     x_anchor[i] = v;
     x_avg[i] = T(0);
-    if (x_lo) {
-      x_lo[i] = T(0);
-      xa_lo[i] = T(0);
+    if (x_a_lo) {
+      x_a_lo[i] = T(0);
+      dx[i] = T(0);
+      dx_avg[i] = T(0);
     }
   }
   for (long long i = grid_tid(); i < m; i += grid_threads()) {
@@ -1048,9 +1099,9 @@ __global__ void k_convert(const Ti* __restrict__ in, To* out, int n) {
   for (long long i = grid_tid(); i < n; i += grid_threads()) out[i] = To(in[i]);
 }
 
-// Conversion of an iterate that may carry a compensation word on either
-// side: v = in + in_lo (in_lo may be null), out = round(v), out_lo = the
-// rounding error of out when out_lo is not null.
+// Conversion of a vector that may carry a compensation word on either side:
+// v = in + in_lo (in_lo may be null), out = round(v), out_lo = the rounding
+// error of out when out_lo is not null.
 template <class Ti, class To>
 __global__ void k_convert_split(const Ti* __restrict__ in, const Ti* __restrict__ in_lo, To* out,
                                 To* out_lo, int n) {
@@ -1060,6 +1111,42 @@ __global__ void k_convert_split(const Ti* __restrict__ in, const Ti* __restrict_
     out[i] = o;
     if (out_lo) out_lo[i] = To(v - (double)o);
   }
+}
+
+// Mixed-path x in FP64: out = x_a + x_a_lo + d (d may be null).
+__global__ void k_delta_join(const float* __restrict__ x_a, const float* __restrict__ x_a_lo,
+                             const float* __restrict__ d, double* out, int n) {
+  for (long long i = grid_tid(); i < n; i += grid_threads())
+    out[i] = ((double)x_a[i] + (double)x_a_lo[i]) + (d ? (double)d[i] : 0.0);
+}
+
+// Displacement of an FP64 iterate from the FP64 restart point, in FP32.
+__global__ void k_delta_split(const double* __restrict__ v, const double* __restrict__ v_a,
+                              float* d, int n) {
+  for (long long i = grid_tid(); i < n; i += grid_threads()) d[i] = float(v[i] - v_a[i]);
+}
+
+// Mixed path, before an evaluation or a cache refresh: the full x~ = x_a + dx
+// and its average (rounded to FP32) for the products and relKKT terms, and,
+// when b is given, A x~ = (b - b_shift) + A dx.
+__global__ void k_materialize(const float* __restrict__ x_a, const float* __restrict__ x_a_lo,
+                              const float* __restrict__ dx, const float* __restrict__ dx_avg,
+                              float* x, float* x_avg, int n, const float* __restrict__ b,
+                              const float* __restrict__ b_shift, const float* __restrict__ ax_d,
+                              float* ax, int m) {
+  for (long long i = grid_tid(); i < n; i += grid_threads()) {
+    const double a = (double)x_a[i] + (double)x_a_lo[i];
+    x[i] = float(a + (double)dx[i]);
+    x_avg[i] = float(a + (double)dx_avg[i]);
+  }
+  if (b)
+    for (long long i = grid_tid(); i < m; i += grid_threads()) ax[i] = (b[i] - b_shift[i]) + ax_d[i];
+}
+
+// b_shift = b - A x_a with A x_a already in ax (cache refresh of the mixed path).
+__global__ void k_shift_rhs(const float* __restrict__ b, const float* __restrict__ ax,
+                            float* b_shift, int m) {
+  for (long long i = grid_tid(); i < m; i += grid_threads()) b_shift[i] = b[i] - ax[i];
 }
 
 // eta = 1/(2||A||_2) (Section 3.2), omega0 = ||c||/||b|| (1 if either is ~0),

@@ -137,9 +137,33 @@ struct VecSet {
   T *x0 = nullptr, *y0 = nullptr;
   T *pw_v = nullptr, *pw_u = nullptr, *pw_w = nullptr;
   T *inv_d1 = nullptr, *inv_d2 = nullptr;  // 1/D1, 1/D2 with diagonal scaling, else null
-  // compensation words of x, x~, y, y~ (FP32 set only; the value is hi + lo)
-  T *x_lo = nullptr, *xa_lo = nullptr, *y_lo = nullptr, *ya_lo = nullptr;
+  // FP32 set only.  x is the restart point x_anchor + x_a_lo plus the
+  // displacement dx (its running average dx_avg); x, x_avg and ax above are
+  // then filled from these before each evaluation.  The iteration uses
+  // b_shift = b - A x_anchor and ax_d = A dx.  y_lo, ya_lo: low words of y, y~.
+  T *x_a_lo = nullptr, *dx = nullptr, *dx_avg = nullptr;
+  T *b_shift = nullptr, *ax_d = nullptr;
+  T *y_lo = nullptr, *ya_lo = nullptr;
 };
+
+// The vectors the per-iteration kernels read as x, x~, A x and b: the
+// iterate itself on the FP64 path, its displacement form on the mixed path.
+template <class T>
+T* it_x(VecSet<T>& v) {
+  return std::is_same<T, float>::value ? v.dx : v.x;
+}
+template <class T>
+T* it_x_avg(VecSet<T>& v) {
+  return std::is_same<T, float>::value ? v.dx_avg : v.x_avg;
+}
+template <class T>
+T* it_ax(VecSet<T>& v) {
+  return std::is_same<T, float>::value ? v.ax_d : v.ax;
+}
+template <class T>
+T* it_b(VecSet<T>& v) {
+  return std::is_same<T, float>::value ? v.b_shift : v.b;
+}
 
 constexpr int kPrecFp64 = QP_PREC_FP64;
 constexpr int kPrecMixed = QP_PREC_MIXED;
@@ -310,7 +334,7 @@ qp_status launch_cg(qp_handle* h, bool coop) {
       cfg.numAttrs = 1;
     }
     cudaLaunchKernelEx(&cfg, k_cg<G, T>, view<T>(h->Q), long_rows_of(h->Q), seg_buf<T>(h->Q),
-                       long_buf<T>(h->Q), v.x, v.x_lo, v.r, v.p, v.q, v.qx,
+                       long_buf<T>(h->Q), it_x(v), v.r, v.p, v.q, v.qx,
                        (const double*)(h->part_r0 + h->grid_n), h->part_cg, h->st, h->bar,
                        (int)h->n);
   });
@@ -319,11 +343,11 @@ qp_status launch_cg(qp_handle* h, bool coop) {
 template <class T>
 qp_status launch_dual(qp_handle* h) {
   VecSet<T>& v = vecs<T>(h);
-  launch_long<T>(h, h->A, v.x);
+  launch_long<T>(h, h->A, it_x(v));
   return dispatch_g(lanes<T>(h->A), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    k_dual<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(view<T>(h->A), v.x, v.b, v.y, v.y_lo, v.ax,
-                                                      v.y_avg, v.ya_lo, h->st);
+    k_dual<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(view<T>(h->A), it_x(v), it_b(v), v.y,
+                                                      v.y_lo, it_ax(v), v.y_avg, v.ya_lo, h->st);
   });
 }
 
@@ -333,8 +357,9 @@ qp_status launch_atv(qp_handle* h) {
   launch_long<T>(h, h->At, v.y);
   return dispatch_g(lanes<T>(h->At), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    k_atv<G, T><<<h->grid_n, kBlock, 0, h->stream>>>(view<T>(h->At), v.y, v.aty, v.x, v.x_lo,
-                                                     v.x_avg, v.xa_lo, v.qx, v.c, v.r, v.p, h->part_r0, h->ticket,
+    k_atv<G, T><<<h->grid_n, kBlock, 0, h->stream>>>(view<T>(h->At), v.y, v.aty, it_x(v),
+                                                     it_x_avg(v), v.qx, v.c, v.r, v.p,
+                                                     h->part_r0, h->ticket,
                                                      h->st);
   });
 }
@@ -351,9 +376,19 @@ qp_status launch_spmv(qp_handle* h, const DevMat& M, const T* x, T* out, double*
 // relKKT of (x, y) and (x~, y~); mode as in k_control.  The products Q x,
 // Q x~ (the exact refresh of the tracked qx, qx_avg), A x~ and A' y~ come
 // first; A x and A' y are the caches of the current iterate.
+// Mixed path: x~ = x_anchor + x_a_lo + dx and its average into x, x_avg (and,
+// with_ax, A x~ into ax) for the products and relKKT terms that want them.
+void materialize(qp_handle* h, bool with_ax) {
+  VecSet<float>& v = h->v32;
+  k_materialize<<<h->grid_vec, kBlock, 0, h->stream>>>(
+      v.x_anchor, v.x_a_lo, v.dx, v.dx_avg, v.x, v.x_avg, h->n, with_ax ? v.b : nullptr,
+      v.b_shift, v.ax_d, v.ax, h->m);
+}
+
 template <class T>
 qp_status launch_eval(qp_handle* h, int mode) {
   VecSet<T>& v = vecs<T>(h);
+  if (std::is_same<T, float>::value) materialize(h, true);
   QP_TRY(launch_spmv<T>(h, h->At, v.y_avg, v.aty_avg, nullptr, h->grid_n));
   QP_TRY(launch_spmv<T>(h, h->Q, v.x, v.qx, nullptr, h->grid_n));
   QP_TRY(launch_spmv<T>(h, h->Q, v.x_avg, v.qx_avg, nullptr, h->grid_n));
@@ -369,12 +404,17 @@ qp_status launch_eval(qp_handle* h, int mode) {
 template <class T>
 qp_status launch_restart(qp_handle* h) {
   VecSet<T>& v = vecs<T>(h);
-  k_restart_n<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.x, v.x_lo, v.x_avg, v.xa_lo,
-                                                        v.x_anchor, v.aty,
-                                                        v.aty_avg, v.qx, v.qx_avg, h->st, h->n,
-                                                        h->part_rn);
+  if constexpr (std::is_same<T, float>::value)
+    k_restart_n_delta<<<h->grid_vec, kBlock, 0, h->stream>>>(
+        v.x_anchor, v.x_a_lo, v.dx, v.dx_avg, v.aty, v.aty_avg, v.qx, v.qx_avg, h->st, h->n,
+        h->part_rn);
+  else
+    k_restart_n<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.x, v.x_avg, v.x_anchor, v.aty,
+                                                          v.aty_avg, v.qx, v.qx_avg, h->st, h->n,
+                                                          h->part_rn);
   k_restart_m<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.y, v.y_lo, v.y_avg, v.ya_lo,
-                                                        v.y_anchor, v.ax, v.ax_avg, h->st, h->m,
+                                                        v.y_anchor, it_ax(v), v.ax_avg,
+                                                        v.b_shift, v.b, h->st, h->m,
                                                         h->part_rm);
   k_restart_finish<<<1, 32, 0, h->stream>>>(h->part_rn, h->grid_vec, h->part_rm, h->grid_vec,
                                             h->st);
@@ -416,7 +456,16 @@ qp_status launch_setup(qp_handle* h, int power_iters, int reset) {
 template <class T>
 qp_status recompute_caches(qp_handle* h) {
   VecSet<T>& v = vecs<T>(h);
-  QP_TRY(launch_spmv<T>(h, h->A, v.x, v.ax, nullptr, h->grid_m));
+  if constexpr (std::is_same<T, float>::value) {
+    // b_shift = b - A x_anchor, ax_d = A dx; x = the full iterate for Q x
+    materialize(h, false);
+    QP_TRY(launch_spmv<T>(h, h->A, v.x_anchor, v.ax, nullptr, h->grid_m));
+    if (h->m > 0)
+      k_shift_rhs<<<h->grid_vec, kBlock, 0, h->stream>>>(v.b, v.ax, v.b_shift, h->m);
+    QP_TRY(launch_spmv<T>(h, h->A, v.dx, v.ax_d, nullptr, h->grid_m));
+  } else {
+    QP_TRY(launch_spmv<T>(h, h->A, v.x, v.ax, nullptr, h->grid_m));
+  }
   QP_TRY(launch_spmv<T>(h, h->At, v.y, v.aty, nullptr, h->grid_n));
   QP_TRY(launch_spmv<T>(h, h->Q, v.x, v.qx, nullptr, h->grid_n));
   launch_prepare<T>(h);
@@ -436,14 +485,28 @@ void convert_split(qp_handle* h, const Ti* in, const Ti* in_lo, To* out, To* out
     k_convert_split<Ti, To><<<h->grid_vec, kBlock, 0, h->stream>>>(in, in_lo, out, out_lo, count);
 }
 
-// Copy the iterate vectors of one precision into the other.
+// Copy the iterate vectors of one precision into the other (the mixed side
+// in its restart-point + displacement form).
 template <class Ti, class To>
 void convert_state(qp_handle* h) {
   VecSet<Ti>& a = vecs<Ti>(h);
   VecSet<To>& b = vecs<To>(h);
-  convert_split(h, a.x, a.x_lo, b.x, b.x_lo, h->n);
-  convert_split(h, a.x_avg, a.xa_lo, b.x_avg, b.xa_lo, h->n);
-  convert(h, a.x_anchor, b.x_anchor, h->n);
+  const int n = h->n;
+  if constexpr (std::is_same<Ti, double>::value) {
+    if (n > 0) {
+      convert_split(h, a.x_anchor, (const double*)nullptr, b.x_anchor, b.x_a_lo, n);
+      k_delta_split<<<h->grid_vec, kBlock, 0, h->stream>>>(a.x, a.x_anchor, b.dx, n);
+      k_delta_split<<<h->grid_vec, kBlock, 0, h->stream>>>(a.x_avg, a.x_anchor, b.dx_avg, n);
+    }
+  } else {
+    if (n > 0) {
+      k_delta_join<<<h->grid_vec, kBlock, 0, h->stream>>>(a.x_anchor, a.x_a_lo, a.dx, b.x, n);
+      k_delta_join<<<h->grid_vec, kBlock, 0, h->stream>>>(a.x_anchor, a.x_a_lo, a.dx_avg,
+                                                          b.x_avg, n);
+      k_delta_join<<<h->grid_vec, kBlock, 0, h->stream>>>(a.x_anchor, a.x_a_lo, nullptr,
+                                                          b.x_anchor, n);
+    }
+  }
   convert_split(h, a.y, a.y_lo, b.y, b.y_lo, h->m);
   convert_split(h, a.y_avg, a.ya_lo, b.y_avg, b.ya_lo, h->m);
   convert(h, a.y_anchor, b.y_anchor, h->m);
@@ -644,14 +707,16 @@ qp_status alloc_vecs(qp_handle* h) {
   T** mv[] = {&v.b, &v.y, &v.ax, &v.y_avg, &v.y_anchor, &v.ax_avg, &v.y0, &v.pw_u};
   for (T** p : mv) QP_TRY(dalloc(h, p, M));
   if (std::is_same<T, float>::value) {
-    QP_TRY(dalloc(h, &v.x_lo, N));
-    QP_TRY(dalloc(h, &v.xa_lo, N));
-    QP_TRY(dalloc(h, &v.y_lo, M));
-    QP_TRY(dalloc(h, &v.ya_lo, M));
-    CUDA_TRY(cudaMemsetAsync(v.x_lo, 0, N * sizeof(T), h->stream));
-    CUDA_TRY(cudaMemsetAsync(v.xa_lo, 0, N * sizeof(T), h->stream));
-    CUDA_TRY(cudaMemsetAsync(v.y_lo, 0, std::max<size_t>(M, 1) * sizeof(T), h->stream));
-    CUDA_TRY(cudaMemsetAsync(v.ya_lo, 0, std::max<size_t>(M, 1) * sizeof(T), h->stream));
+    T** xn[] = {&v.x_a_lo, &v.dx, &v.dx_avg};
+    for (T** p : xn) {
+      QP_TRY(dalloc(h, p, N));
+      CUDA_TRY(cudaMemsetAsync(*p, 0, N * sizeof(T), h->stream));
+    }
+    T** xm[] = {&v.b_shift, &v.ax_d, &v.y_lo, &v.ya_lo};
+    for (T** p : xm) {
+      QP_TRY(dalloc(h, p, M));
+      CUDA_TRY(cudaMemsetAsync(*p, 0, std::max<size_t>(M, 1) * sizeof(T), h->stream));
+    }
   }
   CUDA_TRY(cudaMemsetAsync(v.x0, 0, N * sizeof(T), h->stream));
   CUDA_TRY(cudaMemsetAsync(v.y0, 0, std::max<size_t>(M, 1) * sizeof(T), h->stream));
@@ -858,7 +923,7 @@ qp_status start_solve(qp_handle* h, const qp_options* o) {
   }
   k_init_vectors<T><<<h->grid_vec, kBlock, 0, h->stream>>>(
       v.x, v.x_avg, v.x_anchor, warm ? v.x0 : nullptr, h->n, v.y, v.y_avg, v.y_anchor,
-      warm ? v.y0 : nullptr, h->m, v.x_lo, v.xa_lo, v.y_lo, v.ya_lo);
+      warm ? v.y0 : nullptr, h->m, v.x_a_lo, v.dx, v.dx_avg, v.y_lo, v.ya_lo);
   QP_TRY(recompute_caches<T>(h));
   QP_TRY(launch_setup<T>(h, o->power_iters, 1));
   QP_TRY(launch_eval<T>(h, 0));
@@ -931,8 +996,10 @@ qp_status promote_and_refine(qp_handle* h, const qp_options* o, bool timing,
   const bool avg = h->h_st->returned_avg != 0;
   info->mixed_iterations = h->h_st->k_total;
   info->mixed_relkkt = h->h_st->kkt_ret[3];
-  convert_split(h, avg ? h->v32.x_avg : h->v32.x, avg ? h->v32.xa_lo : h->v32.x_lo, h->v64.x,
-                (double*)nullptr, h->n);
+  if (h->n > 0)
+    k_delta_join<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v32.x_anchor, h->v32.x_a_lo,
+                                                        avg ? h->v32.dx_avg : h->v32.dx,
+                                                        h->v64.x, h->n);
   convert_split(h, avg ? h->v32.y_avg : h->v32.y, avg ? h->v32.ya_lo : h->v32.y_lo, h->v64.y,
                 (double*)nullptr, h->m);
   CUDA_TRY(cudaMemcpyAsync(h->v64.x_anchor, h->v64.x, size_t(h->n) * sizeof(double),
@@ -1244,28 +1311,40 @@ qp_status qp_get_state(const qp_handle* hc, const qp_state_vectors* v, qp_state_
   const size_t N = size_t(h->n), M = size_t(h->m);
   if (v) {
     if (h->active_prec == kPrecMixed) {
-      // widen the FP32 iterate (hi + lo) on the host
+      // widen the FP32 iterate on the host
       std::vector<float> tmp(std::max<size_t>(std::max(N, M), 1)), tlo(tmp.size());
       struct Src {
         double* out;
         const float* hi;
         const float* lo;
       };
-      const Src all[] = {{v->x, h->v32.x, h->v32.x_lo},
-                         {v->x_avg, h->v32.x_avg, h->v32.xa_lo},
-                         {v->x_anchor, h->v32.x_anchor, nullptr},
-                         {v->y, h->v32.y, h->v32.y_lo},
+      // x, x~ and the restart point from x_anchor + x_a_lo (+ dx, dx_avg)
+      std::vector<float> td(tmp.size());
+      if (N > 0 && (v->x || v->x_avg || v->x_anchor)) {
+        CUDA_TRY(cudaMemcpy(tmp.data(), h->v32.x_anchor, N * sizeof(float),
+                            cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(tlo.data(), h->v32.x_a_lo, N * sizeof(float),
+                            cudaMemcpyDeviceToHost));
+        const std::pair<double*, const float*> xs[] = {
+            {v->x, h->v32.dx}, {v->x_avg, h->v32.dx_avg}, {v->x_anchor, nullptr}};
+        for (auto& pr : xs) {
+          if (!pr.first) continue;
+          if (pr.second)
+            CUDA_TRY(cudaMemcpy(td.data(), pr.second, N * sizeof(float),
+                                cudaMemcpyDeviceToHost));
+          for (size_t k = 0; k < N; ++k)
+            pr.first[k] = (double(tmp[k]) + double(tlo[k])) + (pr.second ? double(td[k]) : 0.0);
+        }
+      }
+      const Src all[] = {{v->y, h->v32.y, h->v32.y_lo},
                          {v->y_avg, h->v32.y_avg, h->v32.ya_lo},
                          {v->y_anchor, h->v32.y_anchor, nullptr}};
-      for (int i = 0; i < 6; ++i) {
-        const size_t cnt = i < 3 ? N : M;
-        if (!all[i].out || cnt == 0) continue;
-        CUDA_TRY(cudaMemcpy(tmp.data(), all[i].hi, cnt * sizeof(float), cudaMemcpyDeviceToHost));
-        if (all[i].lo)
-          CUDA_TRY(cudaMemcpy(tlo.data(), all[i].lo, cnt * sizeof(float),
-                              cudaMemcpyDeviceToHost));
-        for (size_t k = 0; k < cnt; ++k)
-          all[i].out[k] = double(tmp[k]) + (all[i].lo ? double(tlo[k]) : 0.0);
+      for (const Src& sr : all) {
+        if (!sr.out || M == 0) continue;
+        CUDA_TRY(cudaMemcpy(tmp.data(), sr.hi, M * sizeof(float), cudaMemcpyDeviceToHost));
+        if (sr.lo)
+          CUDA_TRY(cudaMemcpy(tlo.data(), sr.lo, M * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < M; ++k) sr.out[k] = double(tmp[k]) + (sr.lo ? double(tlo[k]) : 0.0);
       }
     } else {
       const std::pair<double*, double*> nv[] = {
