@@ -1,13 +1,16 @@
-"""Benchmark: time to relKKT <= 1e-4 of FP64 restarted PDHCG on the large sparse QP.
+"""Benchmark: time to relKKT <= 1e-4 of restarted PDHCG on the large sparse QP.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One step = one complete qp_solve (set-up power iteration, every PDHCG
-iteration, relKKT evaluations, restarts) of the seeded n=1e6, m=5e5 sparse
-QP (Q diagonally dominant with ~9 nnz/row, A with 10 uniform nnz/row), with
-the problem already resident on the device.  The same solve measured end to
-end through the C ABI from host arrays (qp_create with the host-to-device
-copies, qp_solve, qp_get_solution, qp_destroy) is reported as ``e2e``.
+iteration, relKKT evaluations, restarts, the final FP64 check) of the seeded
+n=1e6, m=5e5 sparse QP (Q diagonally dominant with ~9 nnz/row, A with 10
+uniform nnz/row) in mixed precision, with the problem already resident on
+the device and diagonally scaled as Section 4 prescribes (10 Ruiz steps and
+one Pock-Chambolle step, done once by qp_create).  The same solve in plain
+FP64 is timed beside it.  The solve measured end to end through the C ABI
+from host arrays (qp_create with the scaling and the host-to-device copies,
+qp_solve, qp_get_solution, qp_destroy) is reported as ``e2e``.
 
 ``--impl reference`` times the CPU FP64 oracle (the reference arm of this
 build) on a bounded sample of the same workload and scales it to the metric.
@@ -32,9 +35,11 @@ WORKLOAD = {"workload": "large sparse QP: n=1e6, m=5e5, Q = diag U[0.5,2] + mirr
                         "(~9 nnz/row, diagonally dominant), A 10 uniform N(0,1) nnz/row, "
                         "c ~ N(0,1), b = A x0 + U[0,1]",
             "n": 1_000_000, "m": 500_000, "seed": 0, "tol": 1e-4, "precision": "mixed",
+            "scaling": "Section 4: 10 Ruiz steps + Pock-Chambolle on [[Q, A'], [A, 0]]",
             "l2": "inputs larger than L2 (~470 MB resident working set vs 126 MB L2)"}
 METRIC = "time to 1e-4 rel. KKT (restarted PDHCG; FP32 data/iterates, FP64 reductions) vs plain FP64 GPU PDHCG"
-GOLDEN = os.path.join(ROOT, "tests", "golden", "sparse_dd_n1000000_m500000_seed0_trace.json")
+GOLDEN = os.path.join(ROOT, "tests", "golden",
+                      "sparse_dd_n1000000_m500000_seed0_scaled_trace.json")
 
 
 def _dist():
@@ -140,6 +145,23 @@ def cg_kernel_bytes(nnz_q: int, n: int, launches: int, spmvs: int, cg_steps: int
     return spmvs * spmv + cg_steps * 8.0 * w * n + max(cg_steps - launches, 0) * 3.0 * w * n
 
 
+def mixed_solve_launches(chunks: int, power_iters: int, eval_freq: int) -> int:
+    """Kernel launches of one mixed-precision qp_solve on an instance without
+    long rows (each SpMV is then one launch).
+
+    set-up: k_init_vectors; cache refresh (k_materialize, A x_a, k_shift_rhs,
+    A dx, A'y, Q x, k_prepare); power iteration (k_pow_start, 3 per step,
+    k_setup_finish); the first evaluation (k_materialize, 4 SpMVs, k_kkt_n,
+    k_kkt_m, k_control).  Per chunk: 3 per iteration (k_cg, k_dual, k_atv),
+    an evaluation (8), the restart kernels (3) and k_prepare.  At the end the
+    FP64 check: 2 conversions, the FP64 cache refresh (3 SpMVs, k_prepare)
+    and an FP64 evaluation (4 SpMVs, k_kkt_n, k_kkt_m, k_control)."""
+    setup = 1 + 7 + (1 + 3 * power_iters + 1) + 8
+    chunk = 3 * eval_freq + 8 + 3 + 1
+    final = 2 + 4 + 7
+    return setup + chunks * chunk + final
+
+
 def _profiled_traffic():
     """DRAM bytes per k_cg launch from the committed ncu capture, or None when
     the kernel source has changed since that capture."""
@@ -158,23 +180,20 @@ def _profiled_traffic():
 
 
 def oracle_sample(inst, iters: int):
-    """The oracle as it stands: set-up plus `iters` PDHCG iterations (with the
-    relKKT evaluations they contain).  Returns (setup_s, per_iter_s)."""
+    """The oracle as it stands: its solve (scaling, set-up, iterations with
+    the relKKT evaluations they contain) stopped after `iters` iterations.
+    Returns (setup_s, per_iter_s, cores), split at the end of the first
+    iteration; cores = process CPU time / wall time (numpy and scipy pick
+    their own thread counts)."""
     from oracle import pdhcg_oracle as O
     P = O.problem_from_instance(inst)
-    o = O.OracleOptions(tol=WORKLOAD["tol"], max_iter=iters, eval_freq=64)
-    t0 = time.perf_counter()
-    st = O.initial_state(P, o)
-    k0 = O.relkkt(P, st.x, st.y)
-    st.relkkt_last = st.kkt_anchor = k0.relkkt
-    t1 = time.perf_counter()
-    trace = []
-    for _ in range(iters):
-        O.inner_step(P, st, o)
-        if st.k_total % o.eval_freq == 0:
-            O.evaluate(P, st, o, trace)
-    t2 = time.perf_counter()
-    return t1 - t0, (t2 - t1) / iters
+    o = O.OracleOptions(tol=WORKLOAD["tol"], max_iter=iters, eval_freq=64, scale=True)
+    stamps = []
+    c0, t0 = time.process_time(), time.perf_counter()
+    O.solve(P, o, step_hook=lambda st: stamps.append(time.perf_counter()))
+    cores = (time.process_time() - c0) / max(time.perf_counter() - t0, 1e-9)
+    per_it = (stamps[-1] - stamps[0]) / max(len(stamps) - 1, 1)
+    return stamps[0] - t0 - per_it, per_it, round(cores, 1)
 
 
 def _oracle_iterations():
@@ -190,20 +209,22 @@ def run_reference(args):
     inst = W.sparse_dd(WORKLOAD["seed"], n=WORKLOAD["n"], m=WORKLOAD["m"])
     n_iter = _oracle_iterations()
     sample_iters = 8
-    vals = []
+    vals, cores = [], []
     for s in range(args.warmup + args.steps):
-        setup, per_it = oracle_sample(inst, sample_iters)
+        setup, per_it, c = oracle_sample(inst, sample_iters)
         if s >= args.warmup:
             vals.append(setup + per_it * n_iter)
+            cores.append(c)
     v = statistics.mean(vals)
-    sample = (f"oracle set-up + {sample_iters} iterations per step on the full instance, "
-              f"scaled by the oracle's own iteration count to 1e-4 ({n_iter})")
+    sample = (f"oracle scaling + set-up + {sample_iters} iterations per step on the full "
+              f"instance, scaled by the oracle's own iteration count to 1e-4 ({n_iter})")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": WORKLOAD,
-        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": max(cores), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
     return 0
@@ -246,7 +267,7 @@ def run_ours(args):
     fp64 = dict(tol=tol, precision=L.PREC_FP64)
 
     # ---- device-resident solves (value): mixed precision, CUDA-graph replay
-    solver = QPSolver(inst)
+    solver = QPSolver(inst, scale=True)
     for _ in range(args.warmup):
         solver.solve(**mixed)
     solver.solve(**fp64)
@@ -276,7 +297,7 @@ def run_ours(args):
     for s in range(1 + e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with QPSolver(inst) as s2:
+        with QPSolver(inst, scale=True) as s2:
             s2.solve(**mixed)
             x, y = s2.solution()
         torch.cuda.synchronize()
@@ -294,16 +315,14 @@ def run_ours(args):
     kernel_s = sum(i["cg_kernel_ms"] for i in kinfos) / 1e3
     achieved = bytes_total / kernel_s / 1e9 if kernel_s > 0 else None
     traffic = _profiled_traffic()
-    setup_launches = 1 + 4 + 1 + 3 * 30 + 1 + 4
-    chunk_launches = 3 * 64 + 4 + 3 + 1
-    gpu_launches = args.steps * (setup_launches + 9 + trace_len * chunk_launches)
+    gpu_launches = args.steps * mixed_solve_launches(trace_len, 30, 64)
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        setup_s, per_it = oracle_sample(inst, 64)
+        setup_s, per_it, cores = oracle_sample(inst, 64)
         n_iter = _oracle_iterations()
-        cpu = {"value": setup_s + per_it * n_iter, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"oracle set-up + 64 PDHCG iterations of the same instance "
+        cpu = {"value": setup_s + per_it * n_iter, "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": f"oracle scaling + set-up + 64 PDHCG iterations of the same instance "
                          f"({setup_s + 64 * per_it:.1f} s), scaled by the oracle's iteration "
                          f"count to 1e-4 ({n_iter})"}
     out = {

@@ -473,3 +473,66 @@ def test_scaled_mixed_solve_meets_tolerance(built_scaled, name, tol):
     x, y = s.solution()
     assert info["termination"] == L.TERM_SOLVED
     assert O.relkkt(P, x, y).relkkt <= tol
+
+
+# ------------------------------------------- mixed path: state representation
+# The mixed path keeps x as the restart point (a compensated FP32 pair) plus
+# an FP32 displacement, and y as a compensated pair.  Moving a state into it
+# and reading it back therefore loses at most one FP32 rounding of the
+# displacement x - x_anchor and ~2^-47 of everything else.
+def test_mixed_state_round_trip_keeps_the_restart_point(built):
+    inst, P, s = built("sparse_small")
+    st = _shared_state(inst, P, 6)
+    st["x"] = st["x_anchor"] + 1e-3 * st["x"]      # an iterate near its restart point
+    st["x_avg"] = st["x_anchor"] + 1e-3 * st["x_avg"]
+    s.set_state(st)
+    s.iterate(0, precision=L.PREC_MIXED)
+    got = s.get_state()
+    a = st["x_anchor"]
+    assert np.all(np.abs(got["x_anchor"] - a) <= 2.0 ** -46 * np.abs(a))
+    for key in ("x", "x_avg"):
+        bound = 2.0 ** -24 * np.abs(st[key] - a) + 2.0 ** -46 * np.abs(a)
+        assert np.all(np.abs(got[key] - st[key]) <= bound), key
+    for key in ("y", "y_avg"):
+        assert np.all(np.abs(got[key] - st[key]) <= 2.0 ** -46 * np.abs(st[key])), key
+
+
+# A scaled instance with power-law column popularity: diagonal scaling makes
+# the iterate large on the popular columns, where thousands of rows share one
+# coordinate.  The mixed path must converge like FP64 there (it once stalled
+# near relKKT 1e-2 when those coordinates moved in FP32 ulp steps).
+def test_mixed_tracks_fp64_on_a_scaled_power_law_instance():
+    inst = W.zipf_dd(0, n=200_000, m=100_000)
+    with QPSolver(inst, scale=True) as s:
+        f64 = s.solve(tol=1e-4, precision=L.PREC_FP64, max_iter=20000)
+        mix = s.solve(tol=1e-4, precision=L.PREC_MIXED, max_iter=20000)
+    assert f64["termination"] == L.TERM_SOLVED and mix["termination"] == L.TERM_SOLVED
+    assert mix["check_relkkt"] <= 1e-4 and mix["refine_iterations"] == 0
+    assert mix["iterations"] <= 1.15 * f64["iterations"]
+
+
+# ------------------------------------------- full size, Section 4 scaling
+GOLDEN_SCALED = os.path.join(os.path.dirname(__file__), "golden",
+                             "sparse_dd_n1000000_m500000_seed0_scaled_trace.json")
+
+
+def test_full_size_scaled_solve_matches_oracle_trace():
+    inst = W.sparse_dd(0)
+    with open(GOLDEN_SCALED) as f:
+        g = json.load(f)
+    with QPSolver(inst, scale=True) as s:
+        info = s.solve(tol=1e-4)
+        x, y = s.solution()
+        mix = s.solve(tol=1e-4, precision=L.PREC_MIXED)
+        xm, ym = s.solution()
+    P = O.problem_from_instance(inst)
+    rescored = O.relkkt(P, x, y)
+    assert info["termination"] == L.TERM_SOLVED and rescored.relkkt <= 1e-4
+    assert info["iterations"] == g["iterations"]
+    assert info["restarts"] == g["restarts"]
+    assert info["cg_steps"] == g["cg_steps"]
+    assert rescored.primal_obj == pytest.approx(g["primal_obj"], rel=1e-4)
+    # mixed precision on the same scaled instance
+    assert mix["termination"] == L.TERM_SOLVED
+    assert O.relkkt(P, xm, ym).relkkt <= 1e-4
+    assert O.relkkt(P, xm, ym).primal_obj == pytest.approx(g["primal_obj"], rel=1e-4)
