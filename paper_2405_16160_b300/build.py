@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libpdhcg.so")
 SOURCES = ["pdhcg.cu", "norm_static.cu", "host_csr.cpp"]
-HEADERS = ["kernels.cuh", "host_csr.h"]
+HEADERS = ["kernels.cuh", "create_kernels.cuh", "host_csr.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

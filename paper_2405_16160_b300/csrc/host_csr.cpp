@@ -187,62 +187,6 @@ void csr_transpose(int32_t rows, int32_t cols, const int32_t* rowptr, const int3
   });
 }
 
-void diagonal_scaling(const CsrView& Q, const CsrView& A, const CsrView& At, int ruiz_iters,
-                      std::vector<double>* d1p, std::vector<double>* d2p) {
-  std::vector<double>& d1 = *d1p;
-  std::vector<double>& d2 = *d2p;
-  d1.assign(size_t(A.rows), 1.0);
-  d2.assign(size_t(Q.rows), 1.0);
-  std::vector<double> rn(size_t(Q.rows)), rm(size_t(A.rows));
-  for (int it = 0; it <= ruiz_iters; ++it) {
-    const bool inf = it < ruiz_iters;
-    auto acc = [inf](double a, double v) { return inf ? std::max(a, v) : a + v; };
-    // variable rows: Q row j, then A' row j (all norms from the same d)
-    const int Tn = worker_count(Q.nnz() + At.nnz());
-    parallel_for(Tn, [&](int t) {
-      const int64_t lo = int64_t(Q.rows) * t / Tn, hi = int64_t(Q.rows) * (t + 1) / Tn;
-      for (int64_t j = lo; j < hi; ++j) {
-        double r = 0.0;
-        for (int64_t k = Q.rowptr[j]; k < Q.rowptr[j + 1]; ++k)
-          r = acc(r, (d2[size_t(j)] * std::fabs(Q.val[k])) * d2[size_t(Q.col[k])]);
-        double ra = 0.0;
-        for (int64_t k = At.rowptr[j]; k < At.rowptr[j + 1]; ++k)
-          ra = acc(ra, (d1[size_t(At.col[k])] * std::fabs(At.val[k])) * d2[size_t(j)]);
-        rn[size_t(j)] = inf ? std::max(r, ra) : r + ra;
-      }
-    });
-    const int Tm = worker_count(A.nnz());
-    parallel_for(Tm, [&](int t) {
-      const int64_t lo = int64_t(A.rows) * t / Tm, hi = int64_t(A.rows) * (t + 1) / Tm;
-      for (int64_t i = lo; i < hi; ++i) {
-        double r = 0.0;
-        for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k)
-          r = acc(r, (d1[size_t(i)] * std::fabs(A.val[k])) * d2[size_t(A.col[k])]);
-        rm[size_t(i)] = r;
-      }
-    });
-    for (size_t j = 0; j < d2.size(); ++j) d2[j] /= std::sqrt(rn[j] > 0.0 ? rn[j] : 1.0);
-    for (size_t i = 0; i < d1.size(); ++i) d1[i] /= std::sqrt(rm[i] > 0.0 ? rm[i] : 1.0);
-  }
-}
-
-HostCsr scaled_copy(const CsrView& M, const double* dr, const double* dc) {
-  HostCsr out;
-  out.rows = M.rows;
-  out.cols = M.cols;
-  out.rowptr.assign(M.rowptr, M.rowptr + M.rows + 1);
-  out.col.assign(M.col, M.col + M.nnz());
-  out.val.resize(size_t(M.nnz()));
-  const int T = worker_count(M.nnz());
-  parallel_for(T, [&](int t) {
-    const int64_t lo = int64_t(M.rows) * t / T, hi = int64_t(M.rows) * (t + 1) / T;
-    for (int64_t i = lo; i < hi; ++i)
-      for (int64_t k = M.rowptr[i]; k < M.rowptr[i + 1]; ++k)
-        out.val[size_t(k)] = (dr[i] * M.val[k]) * dc[M.col[k]];
-  });
-  return out;
-}
-
 bool csr_is_symmetric(const HostCsr& M, double rtol) {
   if (M.rows != M.cols) return false;
   const int64_t nnz = M.nnz();

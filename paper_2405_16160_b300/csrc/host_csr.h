@@ -1,6 +1,7 @@
 // Host-side CSR utilities of the C ABI: validation, canonicalisation (sorted
-// rows, duplicates summed), the stable transpose that builds A' once at
-// create time, and the symmetry check of Q.  Plain C++, no CUDA.
+// rows, duplicates summed), a stable transpose (qp_csr_transpose and the
+// symmetry check of Q; qp_create builds A' on the device) and the symmetry
+// check itself.  Plain C++, no CUDA.
 #pragma once
 
 #include <cstdint>
@@ -47,16 +48,6 @@ HostCsr csr_canonical(int32_t rows, int32_t cols, const int32_t* rowptr, const i
 // any thread count).
 void csr_transpose(int32_t rows, int32_t cols, const int32_t* rowptr, const int32_t* col,
                    const double* val, int32_t* t_rowptr, int32_t* t_col, double* t_val);
-
-// Diagonal preconditioning of K = [[Q, A'], [A, 0]]: `ruiz_iters` Ruiz steps
-// (each row of the current D K D divided on both sides by the square root of
-// its infinity norm), then one Pock-Chambolle step (the same with the 1-norm).
-// At is A' (rows = columns of A).  Rows that are entirely zero keep scale 1.
-void diagonal_scaling(const CsrView& Q, const CsrView& A, const CsrView& At, int ruiz_iters,
-                      std::vector<double>* d1, std::vector<double>* d2);
-
-// Copy of M with entry (i, j) multiplied by (dr[i] * M_ij) * dc[j].
-HostCsr scaled_copy(const CsrView& M, const double* dr, const double* dc);
 
 // True when the canonical square matrix M satisfies |M_ij - M_ji| <= rtol * max|M|.
 bool csr_is_symmetric(const HostCsr& M, double rtol);

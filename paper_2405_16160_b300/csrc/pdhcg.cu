@@ -8,6 +8,9 @@
 // graph; the scalar state (DevState) is shared.
 #include <cuda_runtime.h>
 
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -20,6 +23,7 @@
 
 #include "../../include/pdhcg.h"
 #include "host_csr.h"
+#include "create_kernels.cuh"
 #include "kernels.cuh"
 
 using namespace pdhcg;
@@ -244,6 +248,20 @@ qp_status dev_alloc(qp_handle* h, void** out, size_t bytes) {
 template <class T>
 qp_status dalloc(qp_handle* h, T** out, size_t count) {
   return dev_alloc(h, reinterpret_cast<void**>(out), count * sizeof(T));
+}
+
+// Release a create-time temporary (the handle's stream must be idle).
+void dev_free(qp_handle* h, void* ptr) {
+  if (!ptr) return;
+  for (size_t k = 0; k < h->allocs.size(); ++k) {
+    if (h->allocs[k].first != ptr) continue;
+    if (h->has_alloc)
+      h->ctx.free(ptr, h->allocs[k].second, h->ctx.user, h->ctx.stream);
+    else
+      cudaFree(ptr);
+    h->allocs.erase(h->allocs.begin() + long(k));
+    return;
+  }
 }
 
 template <class F>
@@ -649,25 +667,37 @@ qp_status upload(qp_handle* h, void* dst, const void* src, size_t bytes) {
   return QP_OK;
 }
 
-qp_status upload_matrix(qp_handle* h, DevMat* M, const CsrView& H) {
-  M->rows = H.rows;
-  M->nnz = H.nnz();
-  M->G64 = group_size_for(M->nnz, H.rows, false);
-  M->G32 = group_size_for(M->nnz, H.rows, true);
-  QP_TRY(dalloc(h, &M->rowptr, size_t(H.rows) + 1));
-  QP_TRY(dalloc(h, &M->col, size_t(M->nnz)));
-  QP_TRY(dalloc(h, &M->val, size_t(M->nnz)));
-  QP_TRY(dalloc(h, &M->val32, size_t(M->nnz)));
+// Device storage of a CSR matrix with `rows` rows and `nnz` entries.
+qp_status alloc_matrix(qp_handle* h, DevMat* M, int32_t rows, int64_t nnz) {
+  M->rows = rows;
+  M->nnz = nnz;
+  M->G64 = group_size_for(nnz, rows, false);
+  M->G32 = group_size_for(nnz, rows, true);
+  QP_TRY(dalloc(h, &M->rowptr, size_t(rows) + 1));
+  QP_TRY(dalloc(h, &M->col, size_t(nnz)));
+  QP_TRY(dalloc(h, &M->val, size_t(nnz)));
+  QP_TRY(dalloc(h, &M->val32, size_t(nnz)));
+  return QP_OK;
+}
+
+qp_status upload_csr(qp_handle* h, DevMat* M, const CsrView& H) {
+  QP_TRY(alloc_matrix(h, M, H.rows, H.nnz()));
   QP_TRY(upload(h, M->rowptr, H.rowptr, (size_t(H.rows) + 1) * sizeof(int32_t)));
   QP_TRY(upload(h, M->col, H.col, size_t(M->nnz) * sizeof(int32_t)));
   QP_TRY(upload(h, M->val, H.val, size_t(M->nnz) * sizeof(double)));
+  return QP_OK;
+}
+
+// Once the FP64 values are final: their FP32 copy and the long-row segment
+// table (built from the host copy of the row pointers).
+qp_status finish_matrix(qp_handle* h, DevMat* M, const int32_t* host_rowptr) {
   if (M->nnz > 0)
     k_convert<double, float><<<h->grid_vec, kBlock, 0, h->stream>>>(M->val, M->val32,
                                                                     int(M->nnz));
   // Long rows: fixed-length segments in row order.
   std::vector<int32_t> lr, sb, se, sp(1, 0);
-  for (int32_t i = 0; i < H.rows; ++i) {
-    const int32_t b = H.rowptr[i], e = H.rowptr[i + 1];
+  for (int32_t i = 0; i < M->rows; ++i) {
+    const int32_t b = host_rowptr[i], e = host_rowptr[i + 1];
     if (e - b <= kLongRow) continue;
     lr.push_back(i);
     for (int32_t k = b; k < e; k += kSegLen) {
@@ -695,6 +725,119 @@ qp_status upload_matrix(qp_handle* h, DevMat* M, const CsrView& H) {
     QP_TRY(sync(h));
   }
   return QP_OK;
+}
+
+// A' on the device: the entries of A sorted stably by column (so each row of
+// A' lists increasing rows of A, the order of the host transpose), with the
+// row pointers from per-column counts.  The row pointers also come back to
+// the host for the long-row table.
+qp_status device_transpose(qp_handle* h, int32_t n, std::vector<int32_t>* t_rowptr) {
+  const DevMat& A = h->A;
+  const int64_t nnz = A.nnz;
+  QP_TRY(alloc_matrix(h, &h->At, n, nnz));
+  DevMat& T = h->At;
+  int32_t *count = nullptr, *row_of = nullptr, *perm_in = nullptr, *perm = nullptr;
+  int32_t* keys = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_sort = 0, tmp_scan = 0;
+  const int end_bit = std::max(1, 32 - __builtin_clz(uint32_t(std::max(n - 1, 1))));
+  CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_sort, A.col, keys, perm_in, perm,
+                                           int64_t(nnz), 0, end_bit, h->stream));
+  CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tmp_scan, count, T.rowptr, n + 1, h->stream));
+  qp_status st = QP_OK;
+  auto step = [&](qp_status s2) {
+    if (st == QP_OK) st = s2;
+  };
+  step(dalloc(h, &count, size_t(n) + 1));
+  step(dalloc(h, &row_of, size_t(nnz)));
+  step(dalloc(h, &perm_in, size_t(nnz)));
+  step(dalloc(h, &perm, size_t(nnz)));
+  step(dalloc(h, &keys, size_t(nnz)));
+  step(dev_alloc(h, &tmp, std::max(tmp_sort, tmp_scan)));
+  if (st == QP_OK) {
+    const int wave = h->num_sms * 8;
+    const int grid_rows = int(std::max<int64_t>(
+        1, std::min<int64_t>((int64_t(A.rows) + kBlock / 32 - 1) / (kBlock / 32), wave)));
+    CUDA_TRY(cudaMemsetAsync(count, 0, (size_t(n) + 1) * sizeof(int32_t), h->stream));
+    if (nnz > 0) {
+      k_row_of_entry<<<grid_rows, kBlock, 0, h->stream>>>(A.rowptr, A.rows, row_of);
+      k_iota<<<h->grid_vec, kBlock, 0, h->stream>>>(perm_in, nnz);
+      k_count_columns<<<h->grid_vec, kBlock, 0, h->stream>>>(A.col, nnz, count);
+      size_t b = tmp_sort;
+      CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, b, A.col, keys, perm_in, perm, int64_t(nnz), 0,
+                                               end_bit, h->stream));
+      k_gather_transpose<<<h->grid_vec, kBlock, 0, h->stream>>>(perm, row_of, A.val, nnz, T.col,
+                                                                T.val);
+    }
+    size_t b = tmp_scan;
+    CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, b, count, T.rowptr, n + 1, h->stream));
+    t_rowptr->resize(size_t(n) + 1);
+    CUDA_TRY(cudaMemcpyAsync(t_rowptr->data(), T.rowptr, (size_t(n) + 1) * sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, h->stream));
+    st = sync(h);
+  }
+  for (void* p : {(void*)count, (void*)row_of, (void*)perm_in, (void*)perm, (void*)keys, tmp})
+    dev_free(h, p);
+  return st;
+}
+
+// Section 4 diagonal scaling on the device: `ruiz_iters` Ruiz steps (each row
+// of the current D K D divided on both sides by the square root of its
+// inf-norm), then one Pock-Chambolle step (the same with the 1-norm), on
+// K = [[Q, A'], [A, 0]]; then Q, A, A', c, b are scaled in place (FP64) and
+// 1/D1, 1/D2 stored for the relKKT terms.  D1, D2 come back to the host.
+qp_status device_scaling(qp_handle* h, int ruiz_iters) {
+  const int n = h->n, m = h->m;
+  double *d1 = nullptr, *d2 = nullptr, *rn = nullptr, *rm = nullptr;
+  qp_status st = QP_OK;
+  auto step = [&](qp_status s2) {
+    if (st == QP_OK) st = s2;
+  };
+  step(dalloc(h, &d1, std::max(m, 1)));
+  step(dalloc(h, &d2, n));
+  step(dalloc(h, &rn, n));
+  step(dalloc(h, &rm, std::max(m, 1)));
+  step(dalloc(h, &h->v64.inv_d1, std::max(m, 1)));
+  step(dalloc(h, &h->v64.inv_d2, n));
+  step(dalloc(h, &h->v32.inv_d1, std::max(m, 1)));
+  step(dalloc(h, &h->v32.inv_d2, n));
+  if (st == QP_OK) {
+    const std::vector<double> ones(size_t(std::max(n, m)), 1.0);
+    step(upload(h, d1, ones.data(), size_t(m) * sizeof(double)));
+    step(upload(h, d2, ones.data(), size_t(n) * sizeof(double)));
+    const int wave = h->num_sms * 8;
+    auto warp_grid = [&](int64_t rows) {
+      return int(std::max<int64_t>(1, std::min<int64_t>((rows + kBlock / 32 - 1) / (kBlock / 32),
+                                                        wave)));
+    };
+    const CsrT<double> Q = view<double>(h->Q), A = view<double>(h->A), At = view<double>(h->At);
+    for (int it = 0; it <= ruiz_iters; ++it) {
+      const int inf = it < ruiz_iters ? 1 : 0;
+      k_scale_norms_n<<<warp_grid(n), kBlock, 0, h->stream>>>(Q, At, d1, d2, rn, inf);
+      if (m > 0) k_scale_norms_m<<<warp_grid(m), kBlock, 0, h->stream>>>(A, d1, d2, rm, inf);
+      k_scale_apply<<<h->grid_vec, kBlock, 0, h->stream>>>(d2, rn, n, d1, rm, m);
+    }
+    k_scale_matrix<<<warp_grid(n), kBlock, 0, h->stream>>>(Q, d2, d2, h->Q.val);
+    if (m > 0) {
+      k_scale_matrix<<<warp_grid(m), kBlock, 0, h->stream>>>(A, d1, d2, h->A.val);
+      k_scale_matrix<<<warp_grid(n), kBlock, 0, h->stream>>>(At, d2, d1, h->At.val);
+      k_scale_vector<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.b, d1, h->v64.inv_d1, m);
+    }
+    k_scale_vector<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.c, d2, h->v64.inv_d2, n);
+    convert(h, h->v64.inv_d1, h->v32.inv_d1, m);
+    convert(h, h->v64.inv_d2, h->v32.inv_d2, n);
+    h->d1.resize(size_t(m));
+    h->d2.resize(size_t(n));
+    if (m > 0)
+      CUDA_TRY(cudaMemcpyAsync(h->d1.data(), d1, size_t(m) * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d2.data(), d2, size_t(n) * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+    st = check_launch();
+    if (st == QP_OK) st = sync(h);
+  }
+  for (void* p : {(void*)d1, (void*)d2, (void*)rn, (void*)rm}) dev_free(h, p);
+  return st;
 }
 
 template <class T>
@@ -801,36 +944,6 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
     Ac_ = csr_canonical(m, n, Ar, Ac, Av);
     Ah = view_of(Ac_);
   }
-  HostCsr Th;
-  Th.rows = n;
-  Th.cols = m;
-  Th.rowptr.resize(size_t(n) + 1);
-  Th.col.resize(size_t(Ah.nnz()));
-  Th.val.resize(size_t(Ah.nnz()));
-  csr_transpose(m, n, Ah.rowptr, Ah.col, Ah.val, Th.rowptr.data(), Th.col.data(), Th.val.data());
-  // Section 4 preprocessing: the solver works on D2 Q D2, D1 A D2, D2 c, D1 b.
-  HostCsr Qs_, As_, Ts_;
-  std::vector<double> cs, bs;
-  h->scaled = (flags & QP_CREATE_SCALE) != 0;
-  if (h->scaled) {
-    diagonal_scaling(Qh, Ah, view_of(Th), 10, &h->d1, &h->d2);
-    Qs_ = scaled_copy(Qh, h->d2.data(), h->d2.data());
-    As_ = scaled_copy(Ah, h->d1.data(), h->d2.data());
-    Ts_ = scaled_copy(view_of(Th), h->d2.data(), h->d1.data());
-    Qh = view_of(Qs_);
-    Ah = view_of(As_);
-    Th = std::move(Ts_);
-    cs.resize(size_t(n));
-    bs.resize(size_t(m));
-    for (int32_t j = 0; j < n; ++j) cs[size_t(j)] = h->d2[size_t(j)] * c[j];
-    for (int32_t i = 0; i < m; ++i) bs[size_t(i)] = h->d1[size_t(i)] * b[i];
-    c = cs.data();
-    b = bs.data();
-  } else {
-    h->d1.assign(size_t(m), 1.0);
-    h->d2.assign(size_t(n), 1.0);
-  }
-
   h->n = n;
   h->m = m;
   h->m_eq = m_eq;
@@ -839,30 +952,29 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   const int wave = h->num_sms * 8;
   h->grid_vec =
       int(std::max<int64_t>(1, std::min<int64_t>((std::max(n, m) + kBlock - 1) / kBlock, wave)));
-  QP_TRY(upload_matrix(h, &h->Q, Qh));
-  QP_TRY(upload_matrix(h, &h->A, Ah));
-  QP_TRY(upload_matrix(h, &h->At, view_of(Th)));
+  // Q and A go to the device as given; A' is built there.
+  QP_TRY(upload_csr(h, &h->Q, Qh));
+  QP_TRY(upload_csr(h, &h->A, Ah));
+  std::vector<int32_t> t_rowptr;
+  QP_TRY(device_transpose(h, n, &t_rowptr));
   QP_TRY(alloc_vecs<double>(h));
   QP_TRY(alloc_vecs<float>(h));
   const size_t N = size_t(n), M = size_t(m);
   QP_TRY(upload(h, h->v64.c, c, N * sizeof(double)));
   QP_TRY(upload(h, h->v64.b, b, M * sizeof(double)));
+  // Section 4 preprocessing: the solver works on D2 Q D2, D1 A D2, D2 c, D1 b.
+  h->scaled = (flags & QP_CREATE_SCALE) != 0;
+  if (h->scaled) {
+    QP_TRY(device_scaling(h, 10));
+  } else {
+    h->d1.assign(M, 1.0);
+    h->d2.assign(N, 1.0);
+  }
+  QP_TRY(finish_matrix(h, &h->Q, Qh.rowptr));
+  QP_TRY(finish_matrix(h, &h->A, Ah.rowptr));
+  QP_TRY(finish_matrix(h, &h->At, t_rowptr.data()));
   convert(h, h->v64.c, h->v32.c, n);
   convert(h, h->v64.b, h->v32.b, m);
-  if (h->scaled) {
-    std::vector<double> i1(static_cast<size_t>(m)), i2(static_cast<size_t>(n));
-    for (int32_t i = 0; i < m; ++i) i1[size_t(i)] = 1.0 / h->d1[size_t(i)];
-    for (int32_t j = 0; j < n; ++j) i2[size_t(j)] = 1.0 / h->d2[size_t(j)];
-    QP_TRY(dalloc(h, &h->v64.inv_d1, M));
-    QP_TRY(dalloc(h, &h->v64.inv_d2, N));
-    QP_TRY(dalloc(h, &h->v32.inv_d1, M));
-    QP_TRY(dalloc(h, &h->v32.inv_d2, N));
-    QP_TRY(upload(h, h->v64.inv_d1, i1.data(), M * sizeof(double)));
-    QP_TRY(upload(h, h->v64.inv_d2, i2.data(), N * sizeof(double)));
-    convert(h, h->v64.inv_d1, h->v32.inv_d1, m);
-    convert(h, h->v64.inv_d2, h->v32.inv_d2, n);
-    QP_TRY(sync(h));
-  }
 
   const int g_n = std::max({h->Q.G64, h->At.G64, h->Q.G32, h->At.G32});
   const int g_m = std::max(h->A.G64, h->A.G32);
