@@ -80,7 +80,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -314,7 +314,11 @@ def run_ours(args):
     launches = sum(i["cg_kernel_launches"] for i in kinfos)
     kernel_s = sum(i["cg_kernel_ms"] for i in kinfos) / 1e3
     achieved = bytes_total / kernel_s / 1e9 if kernel_s > 0 else None
+    # the capture is of a one-CG-step launch; a launch averages spmvs/launches steps
     traffic = _profiled_traffic()
+    steps_per_launch = sum(i["cg_kernel_spmvs"] for i in kinfos) / max(launches, 1)
+    if traffic is not None:
+        traffic *= steps_per_launch
     gpu_launches = args.steps * mixed_solve_launches(trace_len, 30, 64)
 
     cpu = None
@@ -343,6 +347,9 @@ def run_ours(args):
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_total / max(launches, 1),
+                     "cg_steps_per_launch": steps_per_launch,
+                     "traffic_note": "ncu DRAM read+write of a one-CG-step k_cg launch "
+                                     "(profiles/k_cg_traffic.json) x CG steps per launch",
                      "gathers_per_s": (sum(i["cg_kernel_spmvs"] for i in kinfos) * inst.nnz_Q
                                        / kernel_s) if kernel_s > 0 else None,
                      "gather_ceiling_per_s": 2.15e11,
@@ -360,7 +367,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
