@@ -324,6 +324,78 @@ qp_status qp_csr_transpose(int32_t rows, int32_t cols, const int32_t* rowptr,
                            const int32_t* col, const double* val, int32_t* t_rowptr,
                            int32_t* t_col, double* t_val);
 
+/* ------------------------------------------------- batched small QPs */
+/*
+ * Many independent QPs solved in one persistent launch, one thread block per
+ * instance, each with its own restart, primal-weight and CG-precision state
+ * (Algorithm 1 with the Section 4 heuristics, the same readings as
+ * qp_solve).  Each instance has Q = F F' + diag(qd), the low-rank-plus-
+ * diagonal form whose products cost 2nk (the P'P acceleration of Section
+ * 5.2).  An instance's vectors (9 n + 6 m + k doubles) live in shared
+ * memory when the largest instance fits one block (about 225 KB on B300),
+ * else in a per-block slice of global memory.  No diagonal scaling.
+ */
+typedef struct qp_batch qp_batch;
+
+/* One instance (host pointers, read during qp_batch_create only).
+ * F: n x k row-major (NULL when k = 0); qd: n; A: m x n CSR with the first
+ * m_eq rows equalities (validated and canonicalised like qp_create's); c: n;
+ * b: m. */
+typedef struct {
+  int32_t n, m, m_eq, k;
+  const double* F;
+  const double* qd;
+  const int32_t* A_rowptr;
+  const int32_t* A_col;
+  const double* A_val;
+  const double* c;
+  const double* b;
+} qp_instance;
+
+/* Per-instance outcome of the last qp_batch_solve. */
+typedef struct {
+  int32_t termination;        /* QP_TERM_* */
+  int32_t returned_avg;       /* 1 if the returned iterate is the average */
+  int64_t iterations, cg_steps, restarts;
+  double r_primal, r_dual, r_gap, relkkt, primal_obj, dual_obj;  /* FP64 data */
+  double eta, omega, norm_A;
+} qp_instance_result;
+
+/* Copy count instances to the current device.  Errors: QP_ERR_INVALID_ARG
+ * (bad sizes or CSR, non-finite values, an instance too large for one
+ * block), QP_ERR_NO_DEVICE, QP_ERR_OOM, QP_ERR_CUDA; *out is NULL on failure. */
+qp_status qp_batch_create(qp_batch** out, int32_t count, const qp_instance* inst,
+                          const qp_device_ctx* ctx, uint32_t flags);
+void qp_batch_destroy(qp_batch* bt);
+
+/* Solve every instance with the same options (tol, max_iter, eval_freq, the
+ * CG, restart and primal-weight settings, power_iters, omega0, eta,
+ * precision; warm_start = 1 starts from qp_batch_set_warm_start's data).
+ * One kernel launch; *device_ms (may be NULL) receives its CUDA-event time.
+ * Per-instance outcomes: qp_batch_results. */
+qp_status qp_batch_solve(qp_batch* bt, const qp_options* o, double* device_ms);
+
+/* count entries. */
+qp_status qp_batch_results(const qp_batch* bt, qp_instance_result* out);
+
+/* The returned iterates, packed in instance order: x has sum n_i entries, y
+ * sum m_i; either may be NULL. */
+qp_status qp_batch_solution(const qp_batch* bt, double* x, double* y);
+
+/* Packed start points for warm_start = 1 (NULL: zeros). */
+qp_status qp_batch_set_warm_start(qp_batch* bt, const double* x0, const double* y0);
+
+/* Threads per block: 0 picks the built-in default; otherwise 64, 128, 256
+ * or 512.  Results can differ from another block size in the last bits
+ * (the reduction trees differ); a fixed size is bit-reproducible. */
+qp_status qp_batch_set_threads(qp_batch* bt, int32_t threads);
+
+/* Autotuner: times a bounded solve (o with max_iter capped at
+ * sample_iters) of the first sample_count instances for each block size and
+ * keeps the fastest; *threads_out (may be NULL) receives it. */
+qp_status qp_batch_tune(qp_batch* bt, const qp_options* o, int32_t sample_count,
+                        int32_t sample_iters, int32_t* threads_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,24 @@ class QPTraceEntryC(Structure):
                 ("restart", c_int32), ("cg_last", c_int32)]
 
 
+class QPInstanceC(Structure):
+    _fields_ = [("n", c_int32), ("m", c_int32), ("m_eq", c_int32), ("k", c_int32),
+                ("F", POINTER(c_double)), ("qd", POINTER(c_double)),
+                ("A_rowptr", POINTER(c_int32)), ("A_col", POINTER(c_int32)),
+                ("A_val", POINTER(c_double)), ("c", POINTER(c_double)), ("b", POINTER(c_double))]
+
+
+class QPInstanceResultC(Structure):
+    _fields_ = [("termination", c_int32), ("returned_avg", c_int32), ("iterations", c_int64),
+                ("cg_steps", c_int64), ("restarts", c_int64), ("r_primal", c_double),
+                ("r_dual", c_double), ("r_gap", c_double), ("relkkt", c_double),
+                ("primal_obj", c_double), ("dual_obj", c_double), ("eta", c_double),
+                ("omega", c_double), ("norm_A", c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 ALLOC_FN = CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
 FREE_FN = CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
 
@@ -109,6 +127,15 @@ SIGNATURES = [
                                    c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     ("qp_csr_validate", c_int32, [c_int32, c_int32, _I32P, _I32P, _F64P]),
     ("qp_csr_transpose", c_int32, [c_int32, c_int32, _I32P, _I32P, _F64P, _I32P, _I32P, _F64P]),
+    ("qp_batch_create", c_int32, [POINTER(_H), c_int32, POINTER(QPInstanceC),
+                                  POINTER(QPDeviceCtxC), c_uint32]),
+    ("qp_batch_destroy", None, [_H]),
+    ("qp_batch_solve", c_int32, [_H, POINTER(QPOptionsC), _F64P]),
+    ("qp_batch_results", c_int32, [_H, POINTER(QPInstanceResultC)]),
+    ("qp_batch_solution", c_int32, [_H, _F64P, _F64P]),
+    ("qp_batch_set_warm_start", c_int32, [_H, _F64P, _F64P]),
+    ("qp_batch_set_threads", c_int32, [_H, c_int32]),
+    ("qp_batch_tune", c_int32, [_H, POINTER(QPOptionsC), c_int32, c_int32, _I32P]),
 ]
 
 _lock = threading.Lock()

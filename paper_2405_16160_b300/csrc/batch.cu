@@ -1,0 +1,575 @@
+// Host side of the batched solver (qp_batch_* in include/pdhcg.h): packs
+// the instances into flat device arrays, launches the persistent batch
+// kernel (batch_kernels.cuh) and returns per-instance results.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/pdhcg.h"
+#include "batch_kernels.cuh"
+#include "host_csr.h"
+
+using namespace pdhcg;
+
+void pdhcg_set_last_error(const char* msg);
+
+namespace {
+
+void berror(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  pdhcg_set_last_error(buf);
+}
+
+#define BCUDA(call)                                                                       \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      berror("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return QP_ERR_CUDA;                                                                 \
+    }                                                                                     \
+  } while (0)
+
+#define BTRY(call)              \
+  do {                          \
+    qp_status s_ = (call);      \
+    if (s_ != QP_OK) return s_; \
+  } while (0)
+
+__global__ void k_to_float(const double* __restrict__ in, float* out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = float(in[i]);
+}
+
+constexpr int kThreadChoices[] = {64, 128, 256, 512};
+
+}  // namespace
+
+struct qp_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr, user_stream = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr, t0 = nullptr, t1 = nullptr;
+  qp_device_ctx ctx{};
+  bool has_alloc = false;
+  std::vector<std::pair<void*, size_t>> allocs;
+  int32_t count = 0;
+  int64_t n_total = 0, m_total = 0;
+  int max_n = 1, max_m = 1, max_k = 1;
+  int num_sms = 1, threads = 0;
+  size_t smem = 0;            // dynamic shared memory per block (0: global workspace)
+  size_t block_doubles = 0;   // vector space of one block
+  double* ws = nullptr;       // global workspace when the vectors do not fit shared memory
+  size_t ws_blocks = 0;
+  BatchDesc* desc = nullptr;
+  double *F64 = nullptr, *qd64 = nullptr, *c = nullptr, *b = nullptr;
+  double *Aval64 = nullptr, *Tval64 = nullptr;
+  float *F32 = nullptr, *qd32 = nullptr, *Aval32 = nullptr, *Tval32 = nullptr;
+  int32_t *Arp = nullptr, *Acol = nullptr, *Trp = nullptr, *Tcol = nullptr;
+  int32_t *Along = nullptr, *Tlong = nullptr;
+  double *x0 = nullptr, *y0 = nullptr, *x_out = nullptr, *y_out = nullptr;
+  BatchResult* res = nullptr;
+  int* next = nullptr;
+  bool warm_set = false, solved = false;
+  std::vector<BatchResult> h_res;
+};
+
+namespace {
+
+qp_status balloc(qp_batch* h, void** out, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 256);
+  bytes = (bytes + 255) & ~size_t(255);
+  void* ptr = nullptr;
+  if (h->has_alloc) {
+    ptr = h->ctx.alloc(bytes, h->ctx.user, h->ctx.stream);
+    if (!ptr) {
+      berror("device allocator callback returned NULL for %zu bytes", bytes);
+      return QP_ERR_OOM;
+    }
+  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    berror("cudaMalloc(%zu) failed", bytes);
+    return QP_ERR_OOM;
+  }
+  h->allocs.emplace_back(ptr, bytes);
+  *out = ptr;
+  return QP_OK;
+}
+
+template <class T>
+qp_status bupload(qp_batch* h, T** dst, const std::vector<T>& src) {
+  BTRY(balloc(h, reinterpret_cast<void**>(dst), src.size() * sizeof(T)));
+  if (!src.empty())
+    BCUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice,
+                          h->stream));
+  return QP_OK;
+}
+
+qp_status to_float(qp_batch* h, const double* in, float** out, size_t n) {
+  BTRY(balloc(h, reinterpret_cast<void**>(out), n * sizeof(float)));
+  if (n > 0) {
+    const int grid = int(std::min<size_t>((n + 255) / 256, size_t(h->num_sms) * 8));
+    k_to_float<<<grid, 256, 0, h->stream>>>(in, *out, (long long)n);
+  }
+  return QP_OK;
+}
+
+qp_status begin(qp_batch* h) {
+  BCUDA(cudaSetDevice(h->device));
+  if (h->user_stream) {
+    BCUDA(cudaEventRecord(h->ev_a, h->user_stream));
+    BCUDA(cudaStreamWaitEvent(h->stream, h->ev_a, 0));
+  }
+  return QP_OK;
+}
+
+qp_status finish(qp_batch* h) {
+  if (h->user_stream) {
+    BCUDA(cudaEventRecord(h->ev_b, h->stream));
+    BCUDA(cudaStreamWaitEvent(h->user_stream, h->ev_b, 0));
+  }
+  return QP_OK;
+}
+
+bool finite_all(const double* v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+template <class V, int NT>
+qp_status launch_batch_nt(qp_batch* h, BatchData<V> B) {
+  auto kern = k_batch<V, NT>;
+  BCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(h->smem)));
+  int occ = 0;
+  BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, h->smem));
+  if (occ < 1) {
+    berror("batch kernel with %d threads and %zu bytes of shared memory cannot be resident", NT,
+           h->smem);
+    return QP_ERR_INVALID_ARG;
+  }
+  const int grid = std::max(1, std::min(B.count, occ * h->num_sms));
+  if (h->smem == 0) {
+    if (h->ws_blocks < size_t(grid)) {
+      void* p = nullptr;
+      BTRY(balloc(h, &p, size_t(grid) * h->block_doubles * sizeof(double)));
+      h->ws = static_cast<double*>(p);
+      h->ws_blocks = size_t(grid);
+    }
+    B.ws = h->ws;
+    B.ws_stride = (long long)h->block_doubles;
+  }
+  kern<<<grid, NT, h->smem, h->stream>>>(B);
+  BCUDA(cudaGetLastError());
+  return QP_OK;
+}
+
+template <class V>
+qp_status launch_batch(qp_batch* h, const BatchData<V>& B, int threads) {
+  switch (threads) {
+    case 64: return launch_batch_nt<V, 64>(h, B);
+    case 128: return launch_batch_nt<V, 128>(h, B);
+    case 256: return launch_batch_nt<V, 256>(h, B);
+    case 512: return launch_batch_nt<V, 512>(h, B);
+  }
+  berror("unsupported block size %d", threads);
+  return QP_ERR_INVALID_ARG;
+}
+
+template <class V>
+BatchData<V> batch_data(qp_batch* h, const V* F, const V* qd, const V* Av, const V* Tv,
+                        const qp_options* o, int count) {
+  BatchData<V> B{};
+  B.desc = h->desc;
+  B.count = count;
+  B.F = F;
+  B.qd = qd;
+  B.F64 = h->F64;
+  B.qd64 = h->qd64;
+  B.c = h->c;
+  B.b = h->b;
+  B.Arp = h->Arp;
+  B.Acol = h->Acol;
+  B.Aval = Av;
+  B.Aval64 = h->Aval64;
+  B.Trp = h->Trp;
+  B.Tcol = h->Tcol;
+  B.Tval = Tv;
+  B.Tval64 = h->Tval64;
+  B.Along = h->Along;
+  B.Tlong = h->Tlong;
+  B.x0 = h->x0;
+  B.y0 = h->y0;
+  B.warm = (o->warm_start == 1 && h->warm_set) ? 1 : 0;
+  B.x_out = h->x_out;
+  B.y_out = h->y_out;
+  B.res = h->res;
+  B.next = h->next;
+  DevOptions& d = B.opt;
+  d.tol = o->tol;
+  d.max_iter = o->max_iter;
+  d.cg_mode = o->cg_mode;
+  d.cg_fixed_n = o->cg_fixed_n;
+  d.cg_max = o->cg_max;
+  d.restart_mode = o->restart_mode;
+  d.cg_eps_factor = o->cg_eps_factor;
+  d.beta_suff = o->beta_suff;
+  d.beta_nec = o->beta_nec;
+  d.beta_art = o->beta_art;
+  d.theta_pw = o->theta_pw;
+  d.eps_zero = o->eps_zero;
+  d.omega0 = o->omega0;
+  d.eta_override = o->eta;
+  d.pw_update = o->primal_weight_update;
+  d.m_eq = 0;
+  d.debug_flags = 0;
+  d.barrier_timeout_ms = 0;
+  B.power_iters = o->power_iters;
+  B.eval_freq = o->eval_freq;
+  B.max_n = h->max_n;
+  B.max_m = h->max_m;
+  B.max_k = h->max_k;
+  return B;
+}
+
+// One launch over the first `count` instances with the given block size.
+qp_status run_batch(qp_batch* h, const qp_options* o, int threads, int count, double* ms) {
+  BCUDA(cudaMemsetAsync(h->next, 0, sizeof(int), h->stream));
+  BCUDA(cudaEventRecord(h->t0, h->stream));
+  if (o->precision == QP_PREC_MIXED)
+    BTRY(launch_batch<float>(
+        h, batch_data<float>(h, h->F32, h->qd32, h->Aval32, h->Tval32, o, count), threads));
+  else
+    BTRY(launch_batch<double>(
+        h, batch_data<double>(h, h->F64, h->qd64, h->Aval64, h->Tval64, o, count), threads));
+  BCUDA(cudaEventRecord(h->t1, h->stream));
+  BCUDA(cudaEventSynchronize(h->t1));
+  float f = 0.f;
+  BCUDA(cudaEventElapsedTime(&f, h->t0, h->t1));
+  if (ms) *ms = f;
+  return QP_OK;
+}
+
+qp_status validate_batch_options(const qp_options* o) {
+  if (!o || !(o->tol >= 0.0) || o->max_iter < 0 || o->eval_freq < 1 || o->eval_freq > 4096 ||
+      (o->cg_mode != QP_CG_ADAPTIVE && o->cg_mode != QP_CG_FIXED) || o->cg_fixed_n < 0 ||
+      o->cg_max < 1 ||
+      (o->restart_mode != QP_RESTART_ADAPTIVE && o->restart_mode != QP_RESTART_NONE) ||
+      o->power_iters < 1 || o->power_iters > 100000 || !(o->eps_zero >= 0.0) ||
+      !(o->theta_pw >= 0.0 && o->theta_pw <= 1.0) ||
+      (o->precision != QP_PREC_FP64 && o->precision != QP_PREC_MIXED)) {
+    berror("invalid option value");
+    return QP_ERR_INVALID_ARG;
+  }
+  return QP_OK;
+}
+
+qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
+  std::vector<BatchDesc> desc(static_cast<size_t>(count));
+  std::vector<double> F, qd, c, b, Av, Tv;
+  std::vector<int32_t> Arp, Acol, Trp, Tcol, Along, Tlong;
+  std::string why;
+  for (int32_t i = 0; i < count; ++i) {
+    const qp_instance& q = inst[i];
+    if (q.n < 1 || q.m < 0 || q.m_eq < 0 || q.m_eq > q.m || q.k < 0 || !q.qd || !q.c ||
+        (q.k > 0 && !q.F) || (q.m > 0 && (!q.b || !q.A_rowptr))) {
+      berror("instance %d: bad sizes or NULL arrays", i);
+      return QP_ERR_INVALID_ARG;
+    }
+    if (q.m > 0 && !csr_validate(q.m, q.n, q.A_rowptr, q.A_col, q.A_val, &why)) {
+      berror("instance %d: A: %s", i, why.c_str());
+      return QP_ERR_INVALID_ARG;
+    }
+    if (!finite_all(q.qd, size_t(q.n)) || !finite_all(q.c, size_t(q.n)) ||
+        (q.m > 0 && !finite_all(q.b, size_t(q.m))) ||
+        (q.k > 0 && !finite_all(q.F, size_t(q.n) * size_t(q.k)))) {
+      berror("instance %d: a value is not finite", i);
+      return QP_ERR_INVALID_ARG;
+    }
+    HostCsr Ac;
+    if (q.m > 0) {
+      Ac = csr_canonical(q.m, q.n, q.A_rowptr, q.A_col, q.A_val);
+    } else {
+      Ac.rows = 0;
+      Ac.cols = q.n;
+      Ac.rowptr.assign(1, 0);
+    }
+    const int64_t nnz = Ac.nnz();
+    std::vector<int32_t> tr(size_t(q.n) + 1), tc(size_t(std::max<int64_t>(nnz, 1)));
+    std::vector<double> tv(size_t(std::max<int64_t>(nnz, 1)));
+    csr_transpose(q.m, q.n, Ac.rowptr.data(), Ac.col.data(), Ac.val.data(), tr.data(), tc.data(),
+                  tv.data());
+    BatchDesc& d = desc[size_t(i)];
+    d.n = q.n;
+    d.m = q.m;
+    d.m_eq = q.m_eq;
+    d.k = q.k;
+    d.off_n = int64_t(c.size());
+    d.off_m = int64_t(b.size());
+    d.off_F = int64_t(F.size());
+    d.off_Arp = int64_t(Arp.size());
+    d.off_Ann = int64_t(Acol.size());
+    d.off_Trp = int64_t(Trp.size());
+    d.off_Tnn = int64_t(Tcol.size());
+    d.off_Along = int32_t(Along.size());
+    d.off_Tlong = int32_t(Tlong.size());
+    for (int32_t l = 0; l < q.k; ++l)
+      for (int32_t j = 0; j < q.n; ++j) F.push_back(q.F[size_t(j) * q.k + l]);  // column-major
+    qd.insert(qd.end(), q.qd, q.qd + q.n);
+    c.insert(c.end(), q.c, q.c + q.n);
+    if (q.m > 0) b.insert(b.end(), q.b, q.b + q.m);
+    Arp.insert(Arp.end(), Ac.rowptr.begin(), Ac.rowptr.end());
+    Acol.insert(Acol.end(), Ac.col.begin(), Ac.col.end());
+    Av.insert(Av.end(), Ac.val.begin(), Ac.val.end());
+    Trp.insert(Trp.end(), tr.begin(), tr.end());
+    Tcol.insert(Tcol.end(), tc.begin(), tc.begin() + nnz);
+    Tv.insert(Tv.end(), tv.begin(), tv.begin() + nnz);
+    for (int32_t r = 0; r < q.m; ++r)
+      if (Ac.rowptr[size_t(r) + 1] - Ac.rowptr[size_t(r)] > kBatchLongRow) Along.push_back(r);
+    for (int32_t r = 0; r < q.n; ++r)
+      if (tr[size_t(r) + 1] - tr[size_t(r)] > kBatchLongRow) Tlong.push_back(r);
+    d.n_Along = int32_t(Along.size()) - d.off_Along;
+    d.n_Tlong = int32_t(Tlong.size()) - d.off_Tlong;
+    h->max_n = std::max(h->max_n, q.n);
+    h->max_m = std::max(h->max_m, q.m);
+    h->max_k = std::max(h->max_k, q.k);
+  }
+  h->n_total = int64_t(c.size());
+  h->m_total = int64_t(b.size());
+  h->block_doubles = batch_block_doubles(h->max_n, h->max_m, h->max_k);
+  int smem_optin = 0;
+  BCUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+  const size_t static_smem = sizeof(DevState) + 512 / 32 * 11 * sizeof(double) + 64;
+  const size_t need = h->block_doubles * sizeof(double);
+  h->smem = need + static_smem <= size_t(smem_optin) ? need : 0;
+  BCUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  BTRY(bupload(h, &h->desc, desc));
+  BTRY(bupload(h, &h->F64, F));
+  BTRY(bupload(h, &h->qd64, qd));
+  BTRY(bupload(h, &h->c, c));
+  BTRY(bupload(h, &h->b, b));
+  BTRY(bupload(h, &h->Arp, Arp));
+  BTRY(bupload(h, &h->Acol, Acol));
+  BTRY(bupload(h, &h->Aval64, Av));
+  BTRY(bupload(h, &h->Trp, Trp));
+  BTRY(bupload(h, &h->Tcol, Tcol));
+  BTRY(bupload(h, &h->Tval64, Tv));
+  BTRY(bupload(h, &h->Along, Along));
+  BTRY(bupload(h, &h->Tlong, Tlong));
+  BTRY(to_float(h, h->F64, &h->F32, F.size()));
+  BTRY(to_float(h, h->qd64, &h->qd32, qd.size()));
+  BTRY(to_float(h, h->Aval64, &h->Aval32, Av.size()));
+  BTRY(to_float(h, h->Tval64, &h->Tval32, Tv.size()));
+  const std::vector<double> zn(size_t(h->n_total), 0.0), zm(size_t(h->m_total), 0.0);
+  BTRY(bupload(h, &h->x0, zn));
+  BTRY(bupload(h, &h->y0, zm));
+  BTRY(bupload(h, &h->x_out, zn));
+  BTRY(bupload(h, &h->y_out, zm));
+  BTRY(balloc(h, reinterpret_cast<void**>(&h->res), size_t(count) * sizeof(BatchResult)));
+  BTRY(balloc(h, reinterpret_cast<void**>(&h->next), sizeof(int)));
+  h->threads = h->max_n <= 256 ? 128 : 256;
+  BCUDA(cudaStreamSynchronize(h->stream));  // the host staging vectors die here
+  return QP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qp_status qp_batch_create(qp_batch** out, int32_t count, const qp_instance* inst,
+                          const qp_device_ctx* ctx, uint32_t flags) {
+  if (!out) {
+    berror("out is NULL");
+    return QP_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (count < 1 || !inst || flags != 0) {
+    berror("bad batch: count %d, flags %u", count, flags);
+    return QP_ERR_INVALID_ARG;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    berror("no CUDA device visible");
+    return QP_ERR_NO_DEVICE;
+  }
+  qp_batch* h = new qp_batch();
+  h->count = count;
+  cudaGetDevice(&h->device);
+  if (ctx) {
+    h->ctx = *ctx;
+    h->has_alloc = ctx->alloc && ctx->free;
+    h->user_stream = static_cast<cudaStream_t>(ctx->stream);
+  }
+  qp_status s = QP_OK;
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_a, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_b, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&h->t0) != cudaSuccess || cudaEventCreate(&h->t1) != cudaSuccess) {
+    cudaGetLastError();
+    berror("stream/event creation failed");
+    s = QP_ERR_CUDA;
+  }
+  if (s == QP_OK) s = begin(h);
+  if (s == QP_OK) s = create_batch(h, count, inst);
+  if (s == QP_OK) s = finish(h);
+  if (s != QP_OK) {
+    qp_batch_destroy(h);
+    return s;
+  }
+  *out = h;
+  return QP_OK;
+}
+
+void qp_batch_destroy(qp_batch* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& a : h->allocs) {
+    if (h->has_alloc)
+      h->ctx.free(a.first, a.second, h->ctx.user, h->ctx.stream);
+    else
+      cudaFree(a.first);
+  }
+  for (cudaEvent_t e : {h->ev_a, h->ev_b, h->t0, h->t1})
+    if (e) cudaEventDestroy(e);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+qp_status qp_batch_solve(qp_batch* h, const qp_options* o, double* device_ms) {
+  if (!h) return QP_ERR_INVALID_ARG;
+  BTRY(validate_batch_options(o));
+  BTRY(begin(h));
+  h->solved = false;
+  double ms = 0.0;
+  BTRY(run_batch(h, o, h->threads, h->count, &ms));
+  h->h_res.resize(size_t(h->count));
+  BCUDA(cudaMemcpyAsync(h->h_res.data(), h->res, size_t(h->count) * sizeof(BatchResult),
+                        cudaMemcpyDeviceToHost, h->stream));
+  BCUDA(cudaStreamSynchronize(h->stream));
+  if (device_ms) *device_ms = ms;
+  h->solved = true;
+  return finish(h);
+}
+
+qp_status qp_batch_results(const qp_batch* h, qp_instance_result* out) {
+  if (!h || !out) return QP_ERR_INVALID_ARG;
+  if (!h->solved) {
+    berror("no successful batch solve");
+    return QP_ERR_NOT_SOLVED;
+  }
+  for (int32_t i = 0; i < h->count; ++i) {
+    const BatchResult& r = h->h_res[size_t(i)];
+    qp_instance_result& o = out[i];
+    o.termination = r.termination;
+    o.returned_avg = r.returned_avg;
+    o.iterations = r.iterations;
+    o.cg_steps = r.cg_steps;
+    o.restarts = r.restarts;
+    o.r_primal = r.kkt[0];
+    o.r_dual = r.kkt[1];
+    o.r_gap = r.kkt[2];
+    o.relkkt = r.kkt[3];
+    o.primal_obj = r.kkt[4];
+    o.dual_obj = r.kkt[5];
+    o.eta = r.eta;
+    o.omega = r.omega;
+    o.norm_A = r.norm_A;
+  }
+  return QP_OK;
+}
+
+qp_status qp_batch_solution(const qp_batch* hc, double* x, double* y) {
+  if (!hc) return QP_ERR_INVALID_ARG;
+  if (!hc->solved) {
+    berror("no successful batch solve");
+    return QP_ERR_NOT_SOLVED;
+  }
+  qp_batch* h = const_cast<qp_batch*>(hc);
+  BTRY(begin(h));
+  if (x && h->n_total > 0)
+    BCUDA(cudaMemcpyAsync(x, h->x_out, size_t(h->n_total) * sizeof(double),
+                          cudaMemcpyDeviceToHost, h->stream));
+  if (y && h->m_total > 0)
+    BCUDA(cudaMemcpyAsync(y, h->y_out, size_t(h->m_total) * sizeof(double),
+                          cudaMemcpyDeviceToHost, h->stream));
+  BCUDA(cudaStreamSynchronize(h->stream));
+  return finish(h);
+}
+
+qp_status qp_batch_set_warm_start(qp_batch* h, const double* x0, const double* y0) {
+  if (!h) return QP_ERR_INVALID_ARG;
+  if ((x0 && !finite_all(x0, size_t(h->n_total))) ||
+      (y0 && !finite_all(y0, size_t(h->m_total)))) {
+    berror("warm start holds a non-finite value");
+    return QP_ERR_INVALID_ARG;
+  }
+  BTRY(begin(h));
+  const size_t nb = size_t(h->n_total) * sizeof(double), mb = size_t(h->m_total) * sizeof(double);
+  if (x0)
+    BCUDA(cudaMemcpyAsync(h->x0, x0, nb, cudaMemcpyHostToDevice, h->stream));
+  else
+    BCUDA(cudaMemsetAsync(h->x0, 0, nb, h->stream));
+  if (mb) {
+    if (y0)
+      BCUDA(cudaMemcpyAsync(h->y0, y0, mb, cudaMemcpyHostToDevice, h->stream));
+    else
+      BCUDA(cudaMemsetAsync(h->y0, 0, mb, h->stream));
+  }
+  BCUDA(cudaStreamSynchronize(h->stream));
+  h->warm_set = true;
+  return finish(h);
+}
+
+qp_status qp_batch_set_threads(qp_batch* h, int32_t threads) {
+  if (!h) return QP_ERR_INVALID_ARG;
+  if (threads == 0) {
+    h->threads = h->max_n <= 256 ? 128 : 256;
+    return QP_OK;
+  }
+  for (int t : kThreadChoices)
+    if (t == threads) {
+      h->threads = threads;
+      return QP_OK;
+    }
+  berror("unsupported block size %d", threads);
+  return QP_ERR_INVALID_ARG;
+}
+
+qp_status qp_batch_tune(qp_batch* h, const qp_options* o, int32_t sample_count,
+                        int32_t sample_iters, int32_t* threads_out) {
+  if (!h || sample_count < 1 || sample_iters < 1) return QP_ERR_INVALID_ARG;
+  BTRY(validate_batch_options(o));
+  qp_options t = *o;
+  t.max_iter = std::min<int64_t>(o->max_iter, sample_iters);
+  const int count = std::min(sample_count, h->count);
+  BTRY(begin(h));
+  double best = INFINITY;
+  int best_t = h->threads;
+  for (int threads : kThreadChoices) {
+    double ms = 0.0;
+    qp_status s = run_batch(h, &t, threads, count, &ms);
+    if (s == QP_ERR_INVALID_ARG) continue;  // this block size cannot be resident
+    BTRY(s);
+    if (ms < best) {
+      best = ms;
+      best_t = threads;
+    }
+  }
+  h->threads = best_t;
+  h->solved = false;  // the sample runs overwrote the outputs
+  if (threads_out) *threads_out = best_t;
+  return finish(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,495 @@
+// Device side of the batched solver: many small QPs, each solved to the end
+// by one thread block in one persistent launch.
+//
+// An instance is min 1/2 x'Qx + c'x s.t. Ax <= b (first m_eq rows
+// equalities) with Q = F F' + diag(qd), F n x k: the low-rank-plus-diagonal
+// form of the paper's portfolio experiments, whose Q products cost 2nk
+// (the P'P acceleration of Section 5.2).  Every step is the single-QP
+// method: Algorithm 1 with the Section 4 heuristics (adaptive CG, restarts
+// every eval_freq iterations, primal weight), the same readings and the same
+// decision code (control_decide, restart_finish_decide,
+// setup_finish_decide).
+//
+// Per block: a work queue hands out instance ids (an integer atomic; an
+// instance's result does not depend on which block solves it).  All vectors
+// of the instance live in shared memory in FP64; the matrices stay in global
+// memory (read through L1); an instance too large for shared memory keeps
+// its vectors in a per-block slice of global memory instead.  The value type V of the data and of the Q, A,
+// A' products is FP64 (the plain path) or FP32 (mixed); reductions, vector
+// updates and every scalar are FP64 on both, and the relKKT of every
+// evaluation is computed with the FP64 data, so termination is decided on
+// the problem as given.
+#pragma once
+
+#include "state.cuh"
+
+namespace pdhcg {
+
+// Rows with more entries than this are summed by a whole warp.
+constexpr int kBatchLongRow = 32;
+
+struct BatchDesc {
+  int32_t n, m, m_eq, k;
+  int64_t off_n, off_m;      // packed n- and m-vectors
+  int64_t off_F;             // F, column-major (k x n: F[l * n + j])
+  int64_t off_Arp, off_Ann;  // A: row pointers (instance-local), entries
+  int64_t off_Trp, off_Tnn;  // A'
+  int32_t off_Along, n_Along, off_Tlong, n_Tlong;  // rows with > kBatchLongRow entries
+};
+
+struct BatchResult {
+  int32_t termination, returned_avg;
+  long long iterations, cg_steps, restarts;
+  double kkt[6];  // r_primal, r_dual, r_gap, relKKT, primal_obj, dual_obj
+  double eta, omega, norm_A;
+};
+
+template <class V>
+struct BatchData {
+  const BatchDesc* desc;
+  int count;
+  const V* F;
+  const V* qd;
+  const double* F64;
+  const double* qd64;
+  const double* c;
+  const double* b;
+  const int32_t* Arp;
+  const int32_t* Acol;
+  const V* Aval;
+  const double* Aval64;
+  const int32_t* Trp;
+  const int32_t* Tcol;
+  const V* Tval;
+  const double* Tval64;
+  const int32_t* Along;
+  const int32_t* Tlong;
+  const double* x0;
+  const double* y0;
+  int warm;
+  double* x_out;
+  double* y_out;
+  BatchResult* res;
+  int* next;
+  DevOptions opt;
+  int power_iters, eval_freq;
+  int max_n, max_m, max_k;
+  double* ws;          // per-block vector space in global memory, or null for shared memory
+  long long ws_stride;  // doubles per block in ws
+};
+
+// Vector space of one block, in doubles: shared memory when it fits, else
+// a slice of a global workspace (same layout, reached through L1).
+inline size_t batch_block_doubles(int max_n, int max_m, int max_k) {
+  return 9 * size_t(max_n) + 6 * size_t(max_m) + size_t(max_k) + 8;
+}
+
+template <class V>
+struct LocalCsr {
+  const int32_t* rp;
+  const int32_t* col;
+  const V* val;
+  int rows;
+  const int32_t* longr;
+  int nlong;
+};
+
+template <class V>
+__device__ __forceinline__ V warp_sum_v(V v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
+  return v;
+}
+
+// out = M v: a thread per short row (entries in order), a warp per long row.
+// The caller synchronises before reading out.
+template <class V, int NT>
+__device__ void cta_spmv(const LocalCsr<V>& M, const double* v, double* out) {
+  for (int i = threadIdx.x; i < M.rows; i += NT) {
+    const int b = M.rp[i], e = M.rp[i + 1];
+    if (e - b > kBatchLongRow) continue;
+    V s = V(0);
+    for (int k = b; k < e; ++k) s = fma(M.val[k], V(v[M.col[k]]), s);
+    out[i] = double(s);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = w; t < M.nlong; t += NT / 32) {
+    const int i = M.longr[t];
+    V s = V(0);
+    for (int k = M.rp[i] + lane; k < M.rp[i + 1]; k += 32) s = fma(M.val[k], V(v[M.col[k]]), s);
+    s = warp_sum_v(s);
+    if (lane == 0) out[i] = double(s);
+  }
+}
+
+// out = (F F' + diag(qd)) p with F column-major: t = F'p by a warp per
+// column, then a thread per row.  Two barriers; out is ready on return.
+template <class V, int NT>
+__device__ void cta_qprod(const V* F, const V* qd, int n, int k, const double* p, double* t,
+                          double* out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int l = w; l < k; l += NT / 32) {
+    const V* Fl = F + size_t(l) * n;
+    V s = V(0);
+    for (int j = lane; j < n; j += 32) s = fma(Fl[j], V(p[j]), s);
+    s = warp_sum_v(s);
+    if (lane == 0) t[l] = double(s);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += NT) {
+    V s = qd[j] * V(p[j]);
+    for (int l = 0; l < k; ++l) s = fma(F[size_t(l) * n + j], V(t[l]), s);
+    out[j] = double(s);
+  }
+  __syncthreads();
+}
+
+// Block-wide sums (S values) and maxima (M values) in one pass; every thread
+// gets the results.  Warp partials are combined in warp order.
+template <int NT, int S, int M>
+__device__ void cta_reduce(double (&sum)[S > 0 ? S : 1], double (&mx)[M > 0 ? M : 1],
+                           double* red) {
+  constexpr int NW = NT / 32, K = S + M;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const double v = warp_sum(sum[s]);
+    if (lane == 0) red[w * K + s] = v;
+  }
+#pragma unroll
+  for (int s = 0; s < M; ++s) {
+    double v = mx[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, shfl_xor(v, o));
+    if (lane == 0) red[w * K + S + s] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    double a = 0.0;
+    for (int i = 0; i < NW; ++i) a += red[i * K + s];
+    sum[s] = a;
+  }
+#pragma unroll
+  for (int s = 0; s < M; ++s) {
+    double a = 0.0;
+    for (int i = 0; i < NW; ++i) a = fmax(a, red[i * K + S + s]);
+    mx[s] = a;
+  }
+  __syncthreads();
+}
+
+template <int NT>
+__device__ __forceinline__ double cta_sum1(double v, double* red) {
+  double s[1] = {v}, m[1] = {0.0};
+  cta_reduce<NT, 1, 0>(s, m, red);
+  return s[0];
+}
+
+template <int NT>
+__device__ __forceinline__ double cta_sum2(double v0, double v1, double* red, double* second) {
+  double s[2] = {v0, v1}, m[1] = {0.0};
+  cta_reduce<NT, 2, 0>(s, m, red);
+  *second = s[1];
+  return s[0];
+}
+
+// One instance, solved by the whole block.
+template <class V, int NT>
+__device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevState& st,
+                                double* red) {
+  const BatchDesc d = B.desc[id];
+  const int n = d.n, m = d.m, k = d.k, tid = threadIdx.x;
+  // shared-memory vectors (FP64)
+  double* x = sm;
+  double* xa = x + B.max_n;   // average
+  double* x0 = xa + B.max_n;  // restart point
+  double* r = x0 + B.max_n;
+  double* p = r + B.max_n;
+  double* q = p + B.max_n;
+  double* qx = q + B.max_n;
+  double* aty = qx + B.max_n;
+  double* wv = aty + B.max_n;
+  double* y = wv + B.max_n;
+  double* ya = y + B.max_m;
+  double* y0 = ya + B.max_m;
+  double* ax = y0 + B.max_m;
+  double* axe = ax + B.max_m;
+  double* axa = axe + B.max_m;
+  double* t = axa + B.max_m;
+  // instance data
+  const double* c = B.c + d.off_n;
+  const double* b = B.b + d.off_m;
+  const V* F = B.F + d.off_F;
+  const V* qd = B.qd + d.off_n;
+  const double* F64 = B.F64 + d.off_F;
+  const double* qd64 = B.qd64 + d.off_n;
+  const LocalCsr<V> A{B.Arp + d.off_Arp, B.Acol + d.off_Ann, B.Aval + d.off_Ann, m,
+                      B.Along + d.off_Along, d.n_Along};
+  const LocalCsr<V> At{B.Trp + d.off_Trp, B.Tcol + d.off_Tnn, B.Tval + d.off_Tnn, n,
+                       B.Tlong + d.off_Tlong, d.n_Tlong};
+  const LocalCsr<double> A64{A.rp, A.col, B.Aval64 + d.off_Ann, m, A.longr, A.nlong};
+  const LocalCsr<double> At64{At.rp, At.col, B.Tval64 + d.off_Tnn, n, At.longr, At.nlong};
+
+  // ---- start: x = x0 (warm) or 0, empty averages (Algorithm 1 input)
+  for (int j = tid; j < n; j += NT) {
+    const double v = B.warm ? B.x0[d.off_n + j] : 0.0;
+    x[j] = v;
+    x0[j] = v;
+    xa[j] = 0.0;
+  }
+  for (int i = tid; i < m; i += NT) {
+    const double v = B.warm ? B.y0[d.off_m + i] : 0.0;
+    y[i] = v;
+    y0[i] = v;
+    ya[i] = 0.0;
+  }
+  if (tid == 0) {
+    st.opt = B.opt;
+    st.opt.m_eq = d.m_eq;
+    st.lam = 0.0;
+  }
+  __syncthreads();
+  // caches A x, A'y, Q x
+  cta_spmv<V, NT>(A, x, ax);
+  cta_spmv<V, NT>(At, y, aty);
+  __syncthreads();
+  cta_qprod<V, NT>(F, qd, n, k, x, t, qx);
+
+  // ---- ||A||_2 by power iteration on A'A from ones/sqrt(n) (Section 3.2)
+  {
+    const double v0 = 1.0 / sqrt((double)n);
+    double cc = 0.0, bb = 0.0;
+    for (int j = tid; j < n; j += NT) {
+      p[j] = v0;
+      cc = fma(c[j], c[j], cc);
+    }
+    for (int i = tid; i < m; i += NT) bb = fma(b[i], b[i], bb);
+    double nb2;
+    const double nc2 = cta_sum2<NT>(cc, bb, red, &nb2);
+    double lam = 0.0;
+    for (int it = 0; it < B.power_iters; ++it) {
+      cta_spmv<V, NT>(A, p, axa);  // u = A v
+      __syncthreads();
+      cta_spmv<V, NT>(At, axa, q);  // w = A'u
+      __syncthreads();
+      double ww = 0.0;
+      for (int j = tid; j < n; j += NT) ww = fma(q[j], q[j], ww);
+      lam = sqrt(cta_sum1<NT>(ww, red));
+      const double inv = lam > 0.0 ? 1.0 / lam : 0.0;
+      for (int j = tid; j < n; j += NT) p[j] = q[j] * inv;
+      __syncthreads();
+    }
+    if (tid == 0) {
+      st.lam = lam;
+      setup_finish_decide(&st, nc2, nb2, 1);
+    }
+    __syncthreads();
+  }
+
+  // ---- relKKT of (x, y) and (x~, y~) with the FP64 data (Section 4)
+  auto evaluate = [&](int mode) {
+    cta_qprod<double, NT>(F64, qd64, n, k, x, t, r);   // Q x
+    cta_qprod<double, NT>(F64, qd64, n, k, xa, t, p);  // Q x~
+    cta_spmv<double, NT>(At64, y, q);                  // A'y
+    cta_spmv<double, NT>(At64, ya, wv);                // A'y~
+    cta_spmv<double, NT>(A64, x, axe);                 // A x
+    cta_spmv<double, NT>(A64, xa, axa);                // A x~
+    __syncthreads();
+    double s4[4] = {0.0, 0.0, 0.0, 0.0}, m7[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int j = tid; j < n; j += NT) {
+      const double cj = c[j], q1 = r[j], q2 = p[j];
+      m7[0] = fmax(m7[0], fabs(q1 + q[j] + cj));
+      m7[1] = fmax(m7[1], fabs(q1));
+      m7[2] = fmax(m7[2], fabs(q[j]));
+      s4[0] = fma(x[j], q1, s4[0]);
+      s4[1] = fma(cj, x[j], s4[1]);
+      m7[3] = fmax(m7[3], fabs(q2 + wv[j] + cj));
+      m7[4] = fmax(m7[4], fabs(q2));
+      m7[5] = fmax(m7[5], fabs(wv[j]));
+      s4[2] = fma(xa[j], q2, s4[2]);
+      s4[3] = fma(cj, xa[j], s4[3]);
+      m7[6] = fmax(m7[6], fabs(cj));
+    }
+    cta_reduce<NT, 4, 7>(s4, m7, red);
+    double s2[2] = {0.0, 0.0}, m5[5] = {0, 0, 0, 0, 0};
+    for (int i = tid; i < m; i += NT) {
+      const double bi = b[i], dd = axe[i] - bi, da = axa[i] - bi;
+      const double vc = i < d.m_eq ? fabs(dd) : (dd > 0.0 ? dd : 0.0);
+      const double va = i < d.m_eq ? fabs(da) : (da > 0.0 ? da : 0.0);
+      m5[0] = fmax(m5[0], vc);
+      m5[1] = fmax(m5[1], fabs(axe[i]));
+      s2[0] = fma(bi, y[i], s2[0]);
+      m5[2] = fmax(m5[2], va);
+      m5[3] = fmax(m5[3], fabs(axa[i]));
+      s2[1] = fma(bi, ya[i], s2[1]);
+      m5[4] = fmax(m5[4], fabs(bi));
+    }
+    cta_reduce<NT, 2, 5>(s2, m5, red);
+    if (tid == 0) {
+      const KktTerms kc = kkt_from(m5[0], m5[1], m5[4], m7[0], m7[1], m7[2], m7[6], s4[0], s4[1],
+                                   s2[0]);
+      const KktTerms ka = kkt_from(m5[2], m5[3], m5[4], m7[3], m7[4], m7[5], m7[6], s4[2], s4[3],
+                                   s2[1]);
+      control_decide(&st, kc, ka, mode);
+    }
+    __syncthreads();
+  };
+  // r0 = p0 = -(Qx + c + A'y): the CG start of the next iteration
+  auto prepare = [&]() -> double {
+    double rr = 0.0;
+    for (int j = tid; j < n; j += NT) {
+      const double v = -(qx[j] + c[j] + aty[j]);
+      r[j] = v;
+      p[j] = v;
+      rr = fma(v, v, rr);
+    }
+    return cta_sum1<NT>(rr, red);
+  };
+
+  evaluate(0);
+  double rr0 = prepare();
+  const int efreq = B.eval_freq;
+  while (running(&st)) {
+    for (int it = 0; it < efreq && running(&st) && st.k_total < st.opt.max_iter; ++it) {
+      // ---- x-step: inexact CG on (Q + I/tau) x = x/tau - c - A'y (Section 2)
+      const double tau = st.tau, inv_tau = 1.0 / tau;
+      const int mode = st.opt.cg_mode, nfix = st.opt.cg_fixed_n, cgmax = st.opt.cg_max;
+      const double eps =
+          mode == kCgAdaptive ? st.eps + st.opt.cg_eps_factor * st.relkkt_last : st.eps;
+      double rr = rr0;
+      int steps = 0;
+      bool numerr = false;
+      const bool skip = (mode == kCgFixed && nfix <= 0) || rr == 0.0;
+      while (!skip) {
+        cta_qprod<V, NT>(F, qd, n, k, p, t, q);  // q = Q p
+        double pq = 0.0;
+        for (int j = tid; j < n; j += NT) pq = fma(p[j], q[j] + p[j] * inv_tau, pq);
+        pq = cta_sum1<NT>(pq, red);
+        if (!(pq > 0.0) || !isfinite(pq)) {
+          numerr = true;
+          break;
+        }
+        const double alpha = rr / pq;
+        double rn = 0.0;
+        for (int j = tid; j < n; j += NT) {
+          const double pj = p[j], qpj = q[j];
+          x[j] = __dadd_rn(x[j], __dmul_rn(alpha, pj));
+          qx[j] = __dadd_rn(qx[j], __dmul_rn(alpha, qpj));
+          const double rj = __dsub_rn(r[j], __dmul_rn(alpha, qpj + pj * inv_tau));
+          r[j] = rj;
+          rn = fma(rj, rj, rn);
+        }
+        const double rr_new = cta_sum1<NT>(rn, red);
+        ++steps;
+        const bool stop =
+            mode == kCgFixed ? steps >= nfix : (tau * sqrt(rr_new) <= eps || steps >= cgmax);
+        if (stop || rr_new == 0.0) break;
+        const double beta = rr_new / rr;
+        rr = rr_new;
+        for (int j = tid; j < n; j += NT) p[j] = __dadd_rn(r[j], __dmul_rn(beta, p[j]));
+        __syncthreads();
+      }
+      if (numerr) {
+        if (tid == 0) {
+          st.done = kDoneNumerical;
+          st.iter_active = 0;
+        }
+        __syncthreads();
+        break;
+      }
+      if (tid == 0) {
+        st.eps = eps;
+        st.cg_total += steps;
+        st.last_cg = steps;
+        st.k_total += 1;
+        st.j += 1;
+      }
+      __syncthreads();
+      // ---- y-step: y+ = proj(y + sigma(2 A x+ - A x - b)), A x cache, y~
+      const double sigma = st.sigma, inv_j = 1.0 / (double)st.j;
+      cta_spmv<V, NT>(A, x, axe);
+      __syncthreads();
+      for (int i = tid; i < m; i += NT) {
+        double yn = y[i] + sigma * (2.0 * axe[i] - ax[i] - b[i]);
+        if (i >= d.m_eq && yn < 0.0) yn = 0.0;
+        y[i] = yn;
+        ax[i] = axe[i];
+        ya[i] += (yn - ya[i]) * inv_j;
+      }
+      __syncthreads();
+      // ---- A'y+, x~ and the next CG start
+      cta_spmv<V, NT>(At, y, aty);
+      __syncthreads();
+      for (int j = tid; j < n; j += NT) xa[j] += (x[j] - xa[j]) * inv_j;
+      rr0 = prepare();
+    }
+    // ---- evaluation, termination, restart (Section 4)
+    evaluate(1);
+    const int pending = st.restart_pending;
+    if (pending != 0) {
+      double dx = 0.0, dy = 0.0;
+      for (int j = tid; j < n; j += NT) {
+        const double cand = pending == 2 ? xa[j] : x[j];
+        const double e = cand - x0[j];
+        dx = fma(e, e, dx);
+        x0[j] = cand;
+        x[j] = cand;
+      }
+      for (int i = tid; i < m; i += NT) {
+        const double cand = pending == 2 ? ya[i] : y[i];
+        const double e = cand - y0[i];
+        dy = fma(e, e, dy);
+        y0[i] = cand;
+        y[i] = cand;
+      }
+      double dy2;
+      const double dx2 = cta_sum2<NT>(dx, dy, red, &dy2);
+      if (tid == 0) restart_finish_decide(&st, dx2, dy2);
+      __syncthreads();
+      cta_spmv<V, NT>(A, x, ax);
+      cta_spmv<V, NT>(At, y, aty);
+      __syncthreads();
+    }
+    // exact Q x for the tracked cache, then the next CG start
+    cta_qprod<V, NT>(F, qd, n, k, x, t, qx);
+    rr0 = prepare();
+  }
+
+  // ---- the returned iterate and its statistics
+  const bool avg = st.returned_avg != 0;
+  for (int j = tid; j < n; j += NT) B.x_out[d.off_n + j] = avg ? xa[j] : x[j];
+  for (int i = tid; i < m; i += NT) B.y_out[d.off_m + i] = avg ? ya[i] : y[i];
+  if (tid == 0) {
+    BatchResult& o = B.res[id];
+    o.termination = st.done > 0 ? st.done - 1 : 1;
+    o.returned_avg = st.returned_avg;
+    o.iterations = st.k_total;
+    o.cg_steps = st.cg_total;
+    o.restarts = st.n_restarts;
+    for (int s = 0; s < 6; ++s) o.kkt[s] = st.kkt_ret[s];
+    o.eta = st.eta;
+    o.omega = st.omega;
+    o.norm_A = st.norm_A;
+  }
+  __syncthreads();
+}
+
+template <class V, int NT>
+__global__ void __launch_bounds__(NT) k_batch(BatchData<V> B) {
+  extern __shared__ double sm_dyn[];
+  double* sm = B.ws ? B.ws + (long long)blockIdx.x * B.ws_stride : sm_dyn;
+  __shared__ DevState st;
+  __shared__ double red[(NT / 32) * 11];
+  __shared__ int id_s;
+  for (;;) {
+    if (threadIdx.x == 0) id_s = atomicAdd(B.next, 1);
+    __syncthreads();
+    const int id = id_s;
+    __syncthreads();
+    if (id >= B.count) break;
+    batch_solve_one<V, NT>(B, id, sm, st, red);
+  }
+}
+
+}  // namespace pdhcg

@@ -202,6 +202,99 @@ class QPSolver:
         self.close()
 
 
+# ------------------------------------------------------------------ batches
+class QPBatch:
+    """Many small QPs with Q = F F' + diag(qd), solved in one launch.
+
+    ``instances`` is a list of ``workloads.LowRankQP`` (or objects with the
+    same fields).  Solutions and warm starts are lists of per-instance arrays.
+    """
+
+    def __init__(self, instances, torch_memory: bool = True):
+        self.lib = L.load_library()
+        self.count = len(instances)
+        self.ns = [int(q.n) for q in instances]
+        self.ms = [int(q.m) for q in instances]
+        self._keep = []  # the allocator callbacks (alive as long as the handle)
+        arrays = []      # instance arrays (read during qp_batch_create only)
+        arr = (L.QPInstanceC * self.count)()
+        for i, q in enumerate(instances):
+            F = _f64(q.F).reshape(-1) if q.k > 0 else None
+            qd, c = _f64(q.qd, q.n), _f64(q.c, q.n)
+            b = _f64(q.b, q.m)
+            Ar, Ac, Av = _i32(q.A_rowptr), _i32(q.A_col), _f64(q.A_val)
+            arrays += [F, qd, c, b, Ar, Ac, Av]
+            arr[i] = L.QPInstanceC(int(q.n), int(q.m), int(q.m_eq), int(q.k), _ptr(F, c_double),
+                                   _ptr(qd, c_double), _ptr(Ar, c_int32), _ptr(Ac, c_int32),
+                                   _ptr(Av, c_double), _ptr(c, c_double), _ptr(b, c_double))
+        ctx = QPSolver._torch_ctx(self) if torch_memory else None
+        h = c_void_p()
+        st = self.lib.qp_batch_create(byref(h), self.count, arr,
+                                      byref(ctx) if ctx is not None else None, 0)
+        del arrays
+        L.check(st, "qp_batch_create")
+        self.h = h
+        self._ctx = ctx
+
+    def solve(self, options: QPOptions | None = None, **overrides) -> float:
+        """Solve every instance; returns the launch's device time in ms."""
+        o = options or QPOptions()
+        for k, v in overrides.items():
+            setattr(o, k, v)
+        ms = c_double()
+        L.check(self.lib.qp_batch_solve(self.h, byref(o._c), byref(ms)), "qp_batch_solve")
+        return ms.value
+
+    def results(self) -> list:
+        out = (L.QPInstanceResultC * self.count)()
+        L.check(self.lib.qp_batch_results(self.h, out), "qp_batch_results")
+        return [out[i].as_dict() for i in range(self.count)]
+
+    def solution(self):
+        x = np.empty(sum(self.ns))
+        y = np.empty(max(sum(self.ms), 1))
+        L.check(self.lib.qp_batch_solution(self.h, _ptr(x, c_double), _ptr(y, c_double)),
+                "qp_batch_solution")
+        return np.split(x, np.cumsum(self.ns)[:-1]), np.split(y[:sum(self.ms)],
+                                                              np.cumsum(self.ms)[:-1])
+
+    def set_warm_start(self, xs=None, ys=None) -> None:
+        x0 = _f64(np.concatenate(xs), sum(self.ns)) if xs is not None else None
+        y0 = _f64(np.concatenate(ys), sum(self.ms)) if ys is not None else None
+        L.check(self.lib.qp_batch_set_warm_start(self.h, _ptr(x0, c_double), _ptr(y0, c_double)),
+                "qp_batch_set_warm_start")
+
+    def set_threads(self, threads: int) -> None:
+        L.check(self.lib.qp_batch_set_threads(self.h, int(threads)), "qp_batch_set_threads")
+
+    def tune(self, options: QPOptions | None = None, sample_count: int = 256,
+             sample_iters: int = 256, **overrides) -> int:
+        o = options or QPOptions()
+        for k, v in overrides.items():
+            setattr(o, k, v)
+        t = c_int32()
+        L.check(self.lib.qp_batch_tune(self.h, byref(o._c), int(sample_count), int(sample_iters),
+                                       byref(t)), "qp_batch_tune")
+        return t.value
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.qp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 # ------------------------------------------------------------ host-only helpers
 def csr_validate(rows, cols, rowptr, col, val) -> int:
     lib = L.load_library()

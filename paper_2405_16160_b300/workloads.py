@@ -25,6 +25,17 @@ Instances
     as ``sparse_dd`` with 2-3 partners per row (~5 nnz/row of Q) and A with
     8 distinct columns per row drawn from a Zipf(1.1) law over column ranks,
     mapped to columns by a seeded permutation.
+``portfolio_batch``  4096 Markowitz-style QPs for the batched solver:
+    instance i draws from the substream (seed, i): n ~ U{20..400}, k =
+    floor(n/10) factors, F n x k with N(0, 1/k) entries (variance 1/k), Q =
+    F F' + diag U[0.01, 0.1], c = -mu with mu ~ N(0.05, 0.02); A = the
+    budget row 1'x = 1 (equality), long-only rows -x <= 0 and s ~ U{5..20}
+    sector caps: every asset sits in one uniformly drawn sector j and
+    sum_{i in S_j} x_i <= 1.5 |S_j| / n (so x = 1/n is strictly feasible).
+``portfolio_family``  the parametric family of the learned warm start:
+    n = 2000, k = 50, 30 sectors, budget and long-only rows (m = 2031); a
+    base F0 and sector map from ``base_seed``, then per instance mu ~
+    N(0.05, 0.02) and F = F0 + 0.1 * (1/sqrt(k)) * G with G ~ N(0, 1).
 """
 from __future__ import annotations
 
@@ -217,6 +228,95 @@ def from_dense(Qd: np.ndarray, Ad: np.ndarray, c: np.ndarray, b: np.ndarray,
     Ar, Ac, Av = _csr_arrays(A)
     return QPInstance(Qd.shape[0], Ad.shape[0], m_eq, Qr, Qc, Qv, Ar, Ac, Av,
                       np.asarray(c, np.float64), np.asarray(b, np.float64), name=name)
+
+
+# ---------------------------------------------------------------- low rank
+@dataclass
+class LowRankQP:
+    """min 1/2 x'(F F' + diag(qd))x + c'x s.t. A x <= b (first m_eq rows =).
+
+    F is n x k, row-major.  ``to_instance`` writes Q out explicitly (for the
+    CPU oracle and the single-QP solver)."""
+
+    n: int
+    m: int
+    m_eq: int
+    k: int
+    F: np.ndarray  # float64 [n, k]
+    qd: np.ndarray  # float64 [n]
+    A_rowptr: np.ndarray
+    A_col: np.ndarray
+    A_val: np.ndarray
+    c: np.ndarray
+    b: np.ndarray
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    def to_instance(self) -> QPInstance:
+        Qd = self.F @ self.F.T + np.diag(self.qd)
+        Qr, Qc, Qv = _csr_arrays(sp.csr_matrix(Qd))
+        return QPInstance(self.n, self.m, self.m_eq, Qr, Qc, Qv, self.A_rowptr, self.A_col,
+                          self.A_val, self.c, self.b, name=self.name, meta=dict(self.meta))
+
+
+def _portfolio_rows(n: int, sector: np.ndarray, s: int):
+    """A = [budget 1'; -I; sector indicator rows], b = [1; 0; 1.5 |S_j| / n]."""
+    rows = [np.zeros(n, np.int64), np.arange(1, n + 1), 1 + n + sector]
+    cols = [np.arange(n), np.arange(n), np.arange(n)]
+    vals = [np.ones(n), -np.ones(n), np.ones(n)]
+    m = 1 + n + s
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(m, n))
+    A.sort_indices()
+    size = np.bincount(sector, minlength=s).astype(np.float64)
+    b = np.concatenate([[1.0], np.zeros(n), 1.5 * size / n])
+    return A, b
+
+
+def _low_rank_qp(F, qd, mu, sector, s, name, meta) -> LowRankQP:
+    n, k = F.shape
+    A, b = _portfolio_rows(n, sector, s)
+    Ar, Ac, Av = _csr_arrays(A)
+    return LowRankQP(n, A.shape[0], 1, k, np.ascontiguousarray(F, np.float64),
+                     np.asarray(qd, np.float64), Ar, Ac, Av, -np.asarray(mu, np.float64), b,
+                     name=name, meta=meta)
+
+
+def portfolio(seed: int, index: int, n_lo: int = 20, n_hi: int = 400) -> LowRankQP:
+    """Instance ``index`` of ``portfolio_batch`` (its own substream)."""
+    rng = np.random.default_rng([seed, index])
+    n = int(rng.integers(n_lo, n_hi + 1))
+    k = max(n // 10, 1)
+    s = int(rng.integers(5, 21))
+    F = rng.normal(0.0, np.sqrt(1.0 / k), size=(n, k))
+    qd = rng.uniform(0.01, 0.1, n)
+    mu = rng.normal(0.05, 0.02, n)
+    sector = rng.integers(0, s, n)
+    return _low_rank_qp(F, qd, mu, sector, s, f"portfolio(seed={seed},i={index},n={n})",
+                        {"sectors": s})
+
+
+def portfolio_batch(seed: int = 0, count: int = 4096, n_lo: int = 20,
+                    n_hi: int = 400) -> list:
+    return [portfolio(seed, i, n_lo, n_hi) for i in range(count)]
+
+
+def portfolio_family(base_seed: int = 0, seeds=range(1, 21), n: int = 2000, k: int = 50,
+                     sectors: int = 30) -> list:
+    """Instances of the parametric family: one per seed in ``seeds``."""
+    base = np.random.default_rng([base_seed, 0])
+    F0 = base.normal(0.0, np.sqrt(1.0 / k), size=(n, k))
+    qd = base.uniform(0.01, 0.1, n)
+    sector = base.integers(0, sectors, n)
+    out = []
+    for sd in seeds:
+        rng = np.random.default_rng([base_seed, 1, int(sd)])
+        mu = rng.normal(0.05, 0.02, n)
+        F = F0 + 0.1 * np.sqrt(1.0 / k) * rng.standard_normal((n, k))
+        out.append(_low_rank_qp(F, qd, mu, sector, sectors,
+                                f"portfolio_family(base={base_seed},seed={sd})",
+                                {"sectors": sectors, "mu": mu, "seed": int(sd)}))
+    return out
 
 
 # Named configurations used by the bench and the parity tests.

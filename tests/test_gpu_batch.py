@@ -1,0 +1,181 @@
+"""The batched solver (qp_batch_*) against the CPU FP64 oracle, per instance.
+
+Each instance Q = F F' + diag(qd) is handed to the oracle written out
+explicitly (``LowRankQP.to_instance``).  The device forms Q p as
+F (F'p) + qd*p, a different summation order, so trajectories agree to
+rounding: the tests compare results (relKKT re-scored by the oracle,
+objective, termination) and, for the plain FP64 path, the iteration and
+restart counts on most instances.
+"""
+import numpy as np
+import pytest
+
+from oracle import pdhcg_oracle as O
+from paper_2405_16160_b300 import _lib as L
+from paper_2405_16160_b300 import workloads as W
+from paper_2405_16160_b300.solver import QPBatch
+
+pytestmark = pytest.mark.gpu
+
+
+def _edge_instances():
+    rng = np.random.default_rng(5)
+    out = []
+    # k = 0: Q diagonal
+    p = W.portfolio(7, 0, 20, 40)
+    out.append(W.LowRankQP(p.n, p.m, p.m_eq, 0, np.zeros((p.n, 0)), p.qd, p.A_rowptr, p.A_col,
+                           p.A_val, p.c, p.b, name="k0"))
+    # m = 0: unconstrained, x* = -Q^{-1} c
+    n, k = 30, 3
+    F = rng.standard_normal((n, k)) * 0.3
+    out.append(W.LowRankQP(n, 0, 0, k, F, rng.uniform(0.5, 1.5, n), np.zeros(1, np.int32),
+                           np.zeros(0, np.int32), np.zeros(0), rng.standard_normal(n),
+                           np.zeros(0), name="m0"))
+    # n = 1
+    out.append(W.LowRankQP(1, 2, 0, 1, np.array([[0.5]]), np.array([0.2]),
+                           np.array([0, 1, 2], np.int32), np.array([0, 0], np.int32),
+                           np.array([1.0, -1.0]), np.array([-1.0]), np.array([2.0, 0.5]),
+                           name="n1"))
+    return out
+
+
+@pytest.fixture(scope="module")
+def batch():
+    insts = W.portfolio_batch(3, count=24, n_lo=20, n_hi=120) + _edge_instances()
+    bt = QPBatch(insts)
+    yield insts, bt
+    bt.close()
+
+
+def _oracle(inst, tol, **kw):
+    P = O.problem_from_instance(inst.to_instance())
+    return P, O.solve(P, O.OracleOptions(tol=tol, **kw))
+
+
+def test_batch_fp64_matches_oracle(batch):
+    insts, bt = batch
+    tol = 1e-6
+    bt.solve(tol=tol, precision=L.PREC_FP64)
+    res = bt.results()
+    xs, ys = bt.solution()
+    same_counts = 0
+    for q, r, x, y in zip(insts, res, xs, ys):
+        P, ores = _oracle(q, tol)
+        assert ores.termination == O.SOLVED, q.name
+        assert r["termination"] == L.TERM_SOLVED, q.name
+        rescored = O.relkkt(P, x, y)
+        assert rescored.relkkt <= tol, q.name
+        assert r["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-12), q.name
+        assert rescored.primal_obj == pytest.approx(ores.kkt.primal_obj, rel=1e-5, abs=1e-9)
+        assert r["norm_A"] == pytest.approx(O.spectral_norm(P.A, 30), rel=1e-12, abs=1e-300)
+        same_counts += (r["iterations"] == ores.iterations and r["restarts"] == ores.restarts)
+    assert same_counts >= 0.8 * len(insts)
+
+
+def test_batch_mixed_meets_tolerance_in_fp64(batch):
+    insts, bt = batch
+    tol = 1e-4
+    bt.solve(tol=tol, precision=L.PREC_MIXED)
+    res = bt.results()
+    xs, ys = bt.solution()
+    for q, r, x, y in zip(insts, res, xs, ys):
+        P = O.problem_from_instance(q.to_instance())
+        assert r["termination"] == L.TERM_SOLVED, q.name
+        rescored = O.relkkt(P, x, y)
+        assert rescored.relkkt <= tol, q.name
+        assert r["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-12), q.name
+
+
+def test_batch_unconstrained_instance_is_the_closed_form(batch):
+    insts, bt = batch
+    bt.solve(tol=1e-8, precision=L.PREC_FP64)
+    xs, _ = bt.solution()
+    i = [q.name for q in insts].index("m0")
+    q = insts[i]
+    Qd = q.F @ q.F.T + np.diag(q.qd)
+    assert np.allclose(xs[i], -np.linalg.solve(Qd, q.c), rtol=1e-6, atol=1e-8)
+
+
+def test_batch_is_deterministic_and_independent_of_order(batch):
+    insts, bt = batch
+    bt.solve(tol=1e-5, precision=L.PREC_MIXED)
+    x1, y1 = bt.solution()
+    bt.solve(tol=1e-5, precision=L.PREC_MIXED)
+    x2, y2 = bt.solution()
+    for a, b in zip(x1 + y1, x2 + y2):
+        assert np.array_equal(a, b)
+    # the same instances in reverse order give the same per-instance results
+    with QPBatch(list(reversed(insts))) as rb:
+        rb.solve(tol=1e-5, precision=L.PREC_MIXED)
+        x3, _ = rb.solution()
+    for a, b in zip(x1, reversed(x3)):
+        assert np.array_equal(a, b)
+
+
+def test_batch_warm_start_from_solution_stops_at_once(batch):
+    insts, bt = batch
+    bt.solve(tol=1e-6, precision=L.PREC_FP64)
+    xs, ys = bt.solution()
+    bt.set_warm_start(xs, ys)
+    bt.solve(tol=1e-6, precision=L.PREC_FP64, warm_start=1)
+    assert all(r["iterations"] == 0 and r["termination"] == L.TERM_SOLVED
+               for r in bt.results())
+    bt.set_warm_start(None, None)
+
+
+def test_batch_iteration_limit(batch):
+    insts, bt = batch
+    bt.solve(tol=1e-12, max_iter=10, precision=L.PREC_FP64)
+    res = bt.results()
+    for q, r in zip(insts, res):
+        if r["termination"] == L.TERM_SOLVED:  # trivial instances (n = 1) may finish first
+            assert r["iterations"] <= 10 and r["relkkt"] <= 1e-12, q.name
+        else:
+            assert r["termination"] == L.TERM_ITER_LIMIT and r["iterations"] == 10, q.name
+    assert sum(r["termination"] == L.TERM_ITER_LIMIT for r in res) >= len(res) - 2
+
+
+def test_batch_numerical_error_stays_in_its_instance():
+    good = W.portfolio_batch(4, count=3, n_lo=20, n_hi=60)
+    p = W.portfolio(4, 9, 20, 40)
+    bad = W.LowRankQP(p.n, p.m, p.m_eq, p.k, p.F, -np.ones(p.n) * 5.0, p.A_rowptr, p.A_col,
+                      p.A_val, p.c, p.b, name="indefinite")
+    with QPBatch(good + [bad]) as bt:
+        bt.solve(tol=1e-6, precision=L.PREC_FP64)
+        res = bt.results()
+    assert [r["termination"] for r in res[:3]] == [L.TERM_SOLVED] * 3
+    assert res[3]["termination"] == L.TERM_NUMERICAL
+
+
+@pytest.mark.parametrize("threads", [64, 128, 256, 512])
+def test_batch_every_block_size_solves(batch, threads):
+    insts, bt = batch
+    bt.set_threads(threads)
+    bt.solve(tol=1e-5, precision=L.PREC_MIXED)
+    xs, ys = bt.solution()
+    for q, r, x, y in zip(insts, bt.results(), xs, ys):
+        assert r["termination"] == L.TERM_SOLVED
+        assert O.relkkt(O.problem_from_instance(q.to_instance()), x, y).relkkt <= 1e-5
+    bt.set_threads(0)
+
+
+def test_batch_tune_picks_a_block_size(batch):
+    insts, bt = batch
+    t = bt.tune(tol=1e-5, precision=L.PREC_MIXED, sample_count=16, sample_iters=128)
+    assert t in (64, 128, 256, 512)
+    bt.solve(tol=1e-5, precision=L.PREC_MIXED)
+    assert all(r["termination"] == L.TERM_SOLVED for r in bt.results())
+    bt.set_threads(0)
+
+
+def test_batch_instance_larger_than_shared_memory():
+    # n = 2000 (the learned-warm-start family): vectors in global memory
+    fam = W.portfolio_family(0, seeds=[1])
+    small = W.portfolio_batch(5, count=2, n_lo=20, n_hi=40)
+    with QPBatch(small + fam) as bt:
+        bt.solve(tol=1e-4, precision=L.PREC_MIXED)
+        res = bt.results()
+        xs, ys = bt.solution()
+    for q, r, x, y in zip(small + fam, res, xs, ys):
+        assert r["termination"] == L.TERM_SOLVED, q.name
+        assert O.relkkt(O.problem_from_instance(q.to_instance()), x, y).relkkt <= 1e-4

@@ -1,0 +1,43 @@
+"""Host-side checks of the seeded generators (no GPU, no solver arithmetic)."""
+import numpy as np
+
+from paper_2405_16160_b300 import workloads as W
+
+
+def test_portfolio_instance_shape_and_strict_feasibility():
+    for i in range(5):
+        p = W.portfolio(0, i)
+        s = p.meta["sectors"]
+        assert 20 <= p.n <= 400 and p.k == max(p.n // 10, 1) and 5 <= s <= 20
+        assert p.m == 1 + p.n + s and p.m_eq == 1
+        inst = p.to_instance()
+        A = inst.scipy_A()
+        x = np.full(p.n, 1.0 / p.n)
+        r = A @ x - p.b
+        assert abs(r[0]) < 1e-12                   # budget row, equality
+        assert np.all(r[1:1 + p.n] < 0)            # long-only, strictly
+        nonempty = np.asarray(abs(A[1 + p.n:]).sum(axis=1)).ravel() > 0
+        assert np.all(r[1 + p.n:][nonempty] < 0)  # sector caps, strictly
+
+
+def test_portfolio_substreams_do_not_depend_on_the_batch():
+    a = W.portfolio_batch(2, count=6)
+    b = W.portfolio_batch(2, count=3)
+    for p, q in zip(a[:3], b):
+        assert p.n == q.n and np.array_equal(p.F, q.F) and np.array_equal(p.c, q.c)
+
+
+def test_low_rank_q_is_written_out_exactly():
+    p = W.portfolio(1, 0, 20, 30)
+    Q = p.to_instance().scipy_Q().toarray()
+    assert np.allclose(Q, p.F @ p.F.T + np.diag(p.qd), rtol=0, atol=1e-15)
+    assert np.allclose(Q, Q.T) and np.linalg.eigvalsh(Q).min() > 0
+
+
+def test_portfolio_family_perturbs_a_shared_base():
+    fam = W.portfolio_family(0, seeds=[1, 2])
+    f, g = fam
+    assert (f.n, f.m, f.k) == (2000, 2031, 50)
+    assert np.array_equal(f.qd, g.qd) and np.array_equal(f.A_col, g.A_col)
+    d = f.F - g.F  # two independent perturbations of std 0.1/sqrt(k)
+    assert abs(d.std() - np.sqrt(2) * 0.1 / np.sqrt(50)) < 0.002
