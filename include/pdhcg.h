@@ -385,14 +385,20 @@ qp_status qp_batch_solution(const qp_batch* bt, double* x, double* y);
 /* Packed start points for warm_start = 1 (NULL: zeros). */
 qp_status qp_batch_set_warm_start(qp_batch* bt, const double* x0, const double* y0);
 
-/* Threads per block: 0 picks the built-in default; otherwise 64, 128, 256
- * or 512.  Results can differ from another block size in the last bits
- * (the reduction trees differ); a fixed size is bit-reproducible. */
+/* qp_batch_create groups the instances by size (n, largest first) into up
+ * to 4 bins of equal count; each bin is one launch on its own stream, with
+ * shared memory and block size fitted to its largest instance.
+ * qp_batch_set_threads sets every bin's threads per block: 0 restores the
+ * built-in default (64 up to n = 128, else 128); otherwise 64, 128, 256 or
+ * 512.  Results can differ from another block size in the last bits (the
+ * reduction trees differ); a fixed configuration is bit-reproducible. */
 qp_status qp_batch_set_threads(qp_batch* bt, int32_t threads);
 
-/* Autotuner: times a bounded solve (o with max_iter capped at
- * sample_iters) of the first sample_count instances for each block size and
- * keeps the fastest; *threads_out (may be NULL) receives it. */
+/* Autotuner: for each bin, times a bounded solve (o with max_iter capped at
+ * sample_iters) of the bin's first sample_count instances for each block
+ * size and keeps the fastest; *threads_out (may be NULL) receives the
+ * choice for the bin of the largest instances.  The sample must fill the GPU
+ * (a few blocks per SM) for the timing to reflect throughput. */
 qp_status qp_batch_tune(qp_batch* bt, const qp_options* o, int32_t sample_count,
                         int32_t sample_iters, int32_t* threads_out);
 

@@ -52,8 +52,28 @@ __global__ void k_to_float(const double* __restrict__ in, float* out, long long 
 }
 
 constexpr int kThreadChoices[] = {64, 128, 256, 512};
+constexpr int kMaxBins = 4;
+
+// Default block size for a bin whose largest instance has n variables.
+int default_threads(int max_n) { return max_n <= 128 ? 64 : 128; }
 
 }  // namespace
+
+// Instances of similar size, solved by one launch on their own stream.
+struct BatchBin {
+  int count = 0;
+  std::vector<int32_t> h_order;
+  int32_t* order = nullptr;  // instance ids (device)
+  int max_n = 1, max_m = 1, max_k = 1;
+  size_t block_doubles = 0;  // vector space of one block
+  size_t smem = 0;           // dynamic shared memory per block (0: global workspace)
+  int threads = 128;
+  double* ws = nullptr;      // global workspace when the vectors do not fit shared memory
+  size_t ws_blocks = 0;
+  int* next = nullptr;       // work-queue counter
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+};
 
 struct qp_batch {
   int device = 0;
@@ -64,12 +84,9 @@ struct qp_batch {
   std::vector<std::pair<void*, size_t>> allocs;
   int32_t count = 0;
   int64_t n_total = 0, m_total = 0;
-  int max_n = 1, max_m = 1, max_k = 1;
-  int num_sms = 1, threads = 0;
-  size_t smem = 0;            // dynamic shared memory per block (0: global workspace)
-  size_t block_doubles = 0;   // vector space of one block
-  double* ws = nullptr;       // global workspace when the vectors do not fit shared memory
-  size_t ws_blocks = 0;
+  int num_sms = 1;
+  std::vector<BatchBin> bins;
+  cudaEvent_t fork = nullptr;
   BatchDesc* desc = nullptr;
   double *F64 = nullptr, *qd64 = nullptr, *c = nullptr, *b = nullptr;
   double *Aval64 = nullptr, *Tval64 = nullptr;
@@ -78,7 +95,6 @@ struct qp_batch {
   int32_t *Along = nullptr, *Tlong = nullptr;
   double *x0 = nullptr, *y0 = nullptr, *x_out = nullptr, *y_out = nullptr;
   BatchResult* res = nullptr;
-  int* next = nullptr;
   bool warm_set = false, solved = false;
   std::vector<BatchResult> h_res;
 };
@@ -147,49 +163,50 @@ bool finite_all(const double* v, size_t n) {
 }
 
 template <class V, int NT>
-qp_status launch_batch_nt(qp_batch* h, BatchData<V> B) {
+qp_status launch_batch_nt(qp_batch* h, BatchBin& bin, BatchData<V> B) {
   auto kern = k_batch<V, NT>;
-  BCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(h->smem)));
+  BCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bin.smem)));
   int occ = 0;
-  BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, h->smem));
+  BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, bin.smem));
   if (occ < 1) {
     berror("batch kernel with %d threads and %zu bytes of shared memory cannot be resident", NT,
-           h->smem);
+           bin.smem);
     return QP_ERR_INVALID_ARG;
   }
   const int grid = std::max(1, std::min(B.count, occ * h->num_sms));
-  if (h->smem == 0) {
-    if (h->ws_blocks < size_t(grid)) {
+  if (bin.smem == 0) {
+    if (bin.ws_blocks < size_t(grid)) {
       void* p = nullptr;
-      BTRY(balloc(h, &p, size_t(grid) * h->block_doubles * sizeof(double)));
-      h->ws = static_cast<double*>(p);
-      h->ws_blocks = size_t(grid);
+      BTRY(balloc(h, &p, size_t(grid) * bin.block_doubles * sizeof(double)));
+      bin.ws = static_cast<double*>(p);
+      bin.ws_blocks = size_t(grid);
     }
-    B.ws = h->ws;
-    B.ws_stride = (long long)h->block_doubles;
+    B.ws = bin.ws;
+    B.ws_stride = (long long)bin.block_doubles;
   }
-  kern<<<grid, NT, h->smem, h->stream>>>(B);
+  kern<<<grid, NT, bin.smem, bin.stream>>>(B);
   BCUDA(cudaGetLastError());
   return QP_OK;
 }
 
 template <class V>
-qp_status launch_batch(qp_batch* h, const BatchData<V>& B, int threads) {
+qp_status launch_batch(qp_batch* h, BatchBin& bin, const BatchData<V>& B, int threads) {
   switch (threads) {
-    case 64: return launch_batch_nt<V, 64>(h, B);
-    case 128: return launch_batch_nt<V, 128>(h, B);
-    case 256: return launch_batch_nt<V, 256>(h, B);
-    case 512: return launch_batch_nt<V, 512>(h, B);
+    case 64: return launch_batch_nt<V, 64>(h, bin, B);
+    case 128: return launch_batch_nt<V, 128>(h, bin, B);
+    case 256: return launch_batch_nt<V, 256>(h, bin, B);
+    case 512: return launch_batch_nt<V, 512>(h, bin, B);
   }
   berror("unsupported block size %d", threads);
   return QP_ERR_INVALID_ARG;
 }
 
 template <class V>
-BatchData<V> batch_data(qp_batch* h, const V* F, const V* qd, const V* Av, const V* Tv,
-                        const qp_options* o, int count) {
+BatchData<V> batch_data(qp_batch* h, const BatchBin& bin, const V* F, const V* qd, const V* Av,
+                        const V* Tv, const qp_options* o, int count) {
   BatchData<V> B{};
   B.desc = h->desc;
+  B.order = bin.order;
   B.count = count;
   B.F = F;
   B.qd = qd;
@@ -213,7 +230,7 @@ BatchData<V> batch_data(qp_batch* h, const V* F, const V* qd, const V* Av, const
   B.x_out = h->x_out;
   B.y_out = h->y_out;
   B.res = h->res;
-  B.next = h->next;
+  B.next = bin.next;
   DevOptions& d = B.opt;
   d.tol = o->tol;
   d.max_iter = o->max_iter;
@@ -235,22 +252,38 @@ BatchData<V> batch_data(qp_batch* h, const V* F, const V* qd, const V* Av, const
   d.barrier_timeout_ms = 0;
   B.power_iters = o->power_iters;
   B.eval_freq = o->eval_freq;
-  B.max_n = h->max_n;
-  B.max_m = h->max_m;
-  B.max_k = h->max_k;
+  B.max_n = bin.max_n;
+  B.max_m = bin.max_m;
+  B.max_k = bin.max_k;
   return B;
 }
 
-// One launch over the first `count` instances with the given block size.
-qp_status run_batch(qp_batch* h, const qp_options* o, int threads, int count, double* ms) {
-  BCUDA(cudaMemsetAsync(h->next, 0, sizeof(int), h->stream));
+// One launch per bin, each on the bin's stream, forked from and joined back
+// into the handle's stream.  only_bin >= 0 runs that bin alone, over its
+// first `limit` instances with `threads` (tuning); otherwise every bin, all
+// instances, its own block size.
+qp_status run_batch(qp_batch* h, const qp_options* o, int only_bin, int threads, int limit,
+                    double* ms) {
   BCUDA(cudaEventRecord(h->t0, h->stream));
-  if (o->precision == QP_PREC_MIXED)
-    BTRY(launch_batch<float>(
-        h, batch_data<float>(h, h->F32, h->qd32, h->Aval32, h->Tval32, o, count), threads));
-  else
-    BTRY(launch_batch<double>(
-        h, batch_data<double>(h, h->F64, h->qd64, h->Aval64, h->Tval64, o, count), threads));
+  BCUDA(cudaEventRecord(h->fork, h->stream));
+  for (int bi = 0; bi < int(h->bins.size()); ++bi) {
+    if (only_bin >= 0 && bi != only_bin) continue;
+    BatchBin& bin = h->bins[size_t(bi)];
+    const int count = only_bin >= 0 ? std::min(limit, bin.count) : bin.count;
+    const int nt = only_bin >= 0 ? threads : bin.threads;
+    BCUDA(cudaStreamWaitEvent(bin.stream, h->fork, 0));
+    BCUDA(cudaMemsetAsync(bin.next, 0, sizeof(int), bin.stream));
+    if (o->precision == QP_PREC_MIXED)
+      BTRY(launch_batch<float>(
+          h, bin, batch_data<float>(h, bin, h->F32, h->qd32, h->Aval32, h->Tval32, o, count),
+          nt));
+    else
+      BTRY(launch_batch<double>(
+          h, bin, batch_data<double>(h, bin, h->F64, h->qd64, h->Aval64, h->Tval64, o, count),
+          nt));
+    BCUDA(cudaEventRecord(bin.done, bin.stream));
+    BCUDA(cudaStreamWaitEvent(h->stream, bin.done, 0));
+  }
   BCUDA(cudaEventRecord(h->t1, h->stream));
   BCUDA(cudaEventSynchronize(h->t1));
   float f = 0.f;
@@ -339,18 +372,40 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
       if (tr[size_t(r) + 1] - tr[size_t(r)] > kBatchLongRow) Tlong.push_back(r);
     d.n_Along = int32_t(Along.size()) - d.off_Along;
     d.n_Tlong = int32_t(Tlong.size()) - d.off_Tlong;
-    h->max_n = std::max(h->max_n, q.n);
-    h->max_m = std::max(h->max_m, q.m);
-    h->max_k = std::max(h->max_k, q.k);
   }
   h->n_total = int64_t(c.size());
   h->m_total = int64_t(b.size());
-  h->block_doubles = batch_block_doubles(h->max_n, h->max_m, h->max_k);
+  // bins: instances sorted by n (largest first), cut into equal-count groups
+  std::vector<int32_t> ids(static_cast<size_t>(count));
+  for (int32_t i = 0; i < count; ++i) ids[size_t(i)] = i;
+  std::stable_sort(ids.begin(), ids.end(), [&](int32_t a, int32_t b2) {
+    return desc[size_t(a)].n > desc[size_t(b2)].n;
+  });
   int smem_optin = 0;
   BCUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
   const size_t static_smem = sizeof(DevState) + 512 / 32 * 11 * sizeof(double) + 64;
-  const size_t need = h->block_doubles * sizeof(double);
-  h->smem = need + static_smem <= size_t(smem_optin) ? need : 0;
+  const int nbins = std::min(kMaxBins, int(count));
+  h->bins.resize(size_t(nbins));
+  for (int bi = 0; bi < nbins; ++bi) {
+    BatchBin& bin = h->bins[size_t(bi)];
+    const size_t lo = size_t(count) * size_t(bi) / size_t(nbins);
+    const size_t hi = size_t(count) * size_t(bi + 1) / size_t(nbins);
+    bin.h_order.assign(ids.begin() + long(lo), ids.begin() + long(hi));
+    bin.count = int(bin.h_order.size());
+    for (int32_t id : bin.h_order) {
+      bin.max_n = std::max(bin.max_n, desc[size_t(id)].n);
+      bin.max_m = std::max(bin.max_m, desc[size_t(id)].m);
+      bin.max_k = std::max(bin.max_k, desc[size_t(id)].k);
+    }
+    bin.block_doubles = batch_block_doubles(bin.max_n, bin.max_m, bin.max_k, true);
+    const size_t need = bin.block_doubles * sizeof(double);
+    bin.smem = need + static_smem <= size_t(smem_optin) ? need : 0;
+    bin.threads = default_threads(bin.max_n);
+    BCUDA(cudaStreamCreateWithFlags(&bin.stream, cudaStreamNonBlocking));
+    BCUDA(cudaEventCreateWithFlags(&bin.done, cudaEventDisableTiming));
+    BTRY(bupload(h, &bin.order, bin.h_order));
+    BTRY(balloc(h, reinterpret_cast<void**>(&bin.next), sizeof(int)));
+  }
   BCUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
   BTRY(bupload(h, &h->desc, desc));
   BTRY(bupload(h, &h->F64, F));
@@ -375,8 +430,6 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
   BTRY(bupload(h, &h->x_out, zn));
   BTRY(bupload(h, &h->y_out, zm));
   BTRY(balloc(h, reinterpret_cast<void**>(&h->res), size_t(count) * sizeof(BatchResult)));
-  BTRY(balloc(h, reinterpret_cast<void**>(&h->next), sizeof(int)));
-  h->threads = h->max_n <= 256 ? 128 : 256;
   BCUDA(cudaStreamSynchronize(h->stream));  // the host staging vectors die here
   return QP_OK;
 }
@@ -414,7 +467,8 @@ qp_status qp_batch_create(qp_batch** out, int32_t count, const qp_instance* inst
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_a, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_b, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreate(&h->t0) != cudaSuccess || cudaEventCreate(&h->t1) != cudaSuccess) {
+      cudaEventCreate(&h->t0) != cudaSuccess || cudaEventCreate(&h->t1) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     berror("stream/event creation failed");
     s = QP_ERR_CUDA;
@@ -440,7 +494,12 @@ void qp_batch_destroy(qp_batch* h) {
     else
       cudaFree(a.first);
   }
-  for (cudaEvent_t e : {h->ev_a, h->ev_b, h->t0, h->t1})
+  for (BatchBin& bin : h->bins) {
+    if (bin.stream) cudaStreamSynchronize(bin.stream);
+    if (bin.done) cudaEventDestroy(bin.done);
+    if (bin.stream) cudaStreamDestroy(bin.stream);
+  }
+  for (cudaEvent_t e : {h->ev_a, h->ev_b, h->t0, h->t1, h->fork})
     if (e) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -452,7 +511,7 @@ qp_status qp_batch_solve(qp_batch* h, const qp_options* o, double* device_ms) {
   BTRY(begin(h));
   h->solved = false;
   double ms = 0.0;
-  BTRY(run_batch(h, o, h->threads, h->count, &ms));
+  BTRY(run_batch(h, o, -1, 0, 0, &ms));
   h->h_res.resize(size_t(h->count));
   BCUDA(cudaMemcpyAsync(h->h_res.data(), h->res, size_t(h->count) * sizeof(BatchResult),
                         cudaMemcpyDeviceToHost, h->stream));
@@ -533,17 +592,14 @@ qp_status qp_batch_set_warm_start(qp_batch* h, const double* x0, const double* y
 
 qp_status qp_batch_set_threads(qp_batch* h, int32_t threads) {
   if (!h) return QP_ERR_INVALID_ARG;
-  if (threads == 0) {
-    h->threads = h->max_n <= 256 ? 128 : 256;
-    return QP_OK;
+  bool ok = threads == 0;
+  for (int t : kThreadChoices) ok = ok || t == threads;
+  if (!ok) {
+    berror("unsupported block size %d", threads);
+    return QP_ERR_INVALID_ARG;
   }
-  for (int t : kThreadChoices)
-    if (t == threads) {
-      h->threads = threads;
-      return QP_OK;
-    }
-  berror("unsupported block size %d", threads);
-  return QP_ERR_INVALID_ARG;
+  for (BatchBin& bin : h->bins) bin.threads = threads == 0 ? default_threads(bin.max_n) : threads;
+  return QP_OK;
 }
 
 qp_status qp_batch_tune(qp_batch* h, const qp_options* o, int32_t sample_count,
@@ -552,23 +608,25 @@ qp_status qp_batch_tune(qp_batch* h, const qp_options* o, int32_t sample_count,
   BTRY(validate_batch_options(o));
   qp_options t = *o;
   t.max_iter = std::min<int64_t>(o->max_iter, sample_iters);
-  const int count = std::min(sample_count, h->count);
   BTRY(begin(h));
-  double best = INFINITY;
-  int best_t = h->threads;
-  for (int threads : kThreadChoices) {
-    double ms = 0.0;
-    qp_status s = run_batch(h, &t, threads, count, &ms);
-    if (s == QP_ERR_INVALID_ARG) continue;  // this block size cannot be resident
-    BTRY(s);
-    if (ms < best) {
-      best = ms;
-      best_t = threads;
+  for (int bi = 0; bi < int(h->bins.size()); ++bi) {
+    BatchBin& bin = h->bins[size_t(bi)];
+    double best = INFINITY;
+    int best_t = bin.threads;
+    for (int threads : kThreadChoices) {
+      double ms = 0.0;
+      qp_status s = run_batch(h, &t, bi, threads, sample_count, &ms);
+      if (s == QP_ERR_INVALID_ARG) continue;  // this block size cannot be resident
+      BTRY(s);
+      if (ms < best) {
+        best = ms;
+        best_t = threads;
+      }
     }
+    bin.threads = best_t;
   }
-  h->threads = best_t;
   h->solved = false;  // the sample runs overwrote the outputs
-  if (threads_out) *threads_out = best_t;
+  if (threads_out) *threads_out = h->bins.front().threads;
   return finish(h);
 }
 

@@ -11,7 +11,9 @@
 // setup_finish_decide).
 //
 // Per block: a work queue hands out instance ids (an integer atomic; an
-// instance's result does not depend on which block solves it).  All vectors
+// instance's result does not depend on which block solves it).  The host
+// groups instances of similar size into bins, each its own launch (on its
+// own stream) with shared memory and block size fitted to the bin.  All vectors
 // of the instance live in shared memory in FP64; the matrices stay in global
 // memory (read through L1); an instance too large for shared memory keeps
 // its vectors in a per-block slice of global memory instead.  The value type V of the data and of the Q, A,
@@ -20,6 +22,8 @@
 // evaluation is computed with the FP64 data, so termination is decided on
 // the problem as given.
 #pragma once
+
+#include <type_traits>
 
 #include "state.cuh"
 
@@ -47,6 +51,7 @@ struct BatchResult {
 template <class V>
 struct BatchData {
   const BatchDesc* desc;
+  const int32_t* order;  // instance ids of this launch
   int count;
   const V* F;
   const V* qd;
@@ -79,9 +84,12 @@ struct BatchData {
 };
 
 // Vector space of one block, in doubles: shared memory when it fits, else
-// a slice of a global workspace (same layout, reached through L1).
-inline size_t batch_block_doubles(int max_n, int max_m, int max_k) {
-  return 9 * size_t(max_n) + 6 * size_t(max_m) + size_t(max_k) + 8;
+// a slice of a global workspace (same layout, reached through L1).  FP64
+// vectors, plus (shadow) copies in the value type when that is FP32.
+inline size_t batch_block_doubles(int max_n, int max_m, int max_k, bool shadow) {
+  const size_t d = 9 * size_t(max_n) + 6 * size_t(max_m) + size_t(max_k) + 8;
+  const size_t f = shadow ? 2 * size_t(max_n) + 2 * size_t(max_m) + size_t(max_k) + 8 : 0;
+  return d + (f + 1) / 2;
 }
 
 template <class V>
@@ -104,41 +112,73 @@ __device__ __forceinline__ V warp_sum_v(V v) {
 // out = M v: a thread per short row (entries in order), a warp per long row.
 // The caller synchronises before reading out.
 template <class V, int NT>
-__device__ void cta_spmv(const LocalCsr<V>& M, const double* v, double* out) {
+__device__ void cta_spmv(const LocalCsr<V>& M, const V* v, double* out) {
   for (int i = threadIdx.x; i < M.rows; i += NT) {
     const int b = M.rp[i], e = M.rp[i + 1];
     if (e - b > kBatchLongRow) continue;
     V s = V(0);
-    for (int k = b; k < e; ++k) s = fma(M.val[k], V(v[M.col[k]]), s);
+    for (int k = b; k < e; ++k) s = fma(M.val[k], v[M.col[k]], s);
     out[i] = double(s);
   }
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int t = w; t < M.nlong; t += NT / 32) {
     const int i = M.longr[t];
     V s = V(0);
-    for (int k = M.rp[i] + lane; k < M.rp[i + 1]; k += 32) s = fma(M.val[k], V(v[M.col[k]]), s);
+    for (int k = M.rp[i] + lane; k < M.rp[i + 1]; k += 32) s = fma(M.val[k], v[M.col[k]], s);
     s = warp_sum_v(s);
     if (lane == 0) out[i] = double(s);
   }
 }
 
-// out = (F F' + diag(qd)) p with F column-major: t = F'p by a warp per
-// column, then a thread per row.  Two barriers; out is ready on return.
+// The dual step fused into A x+ (Algorithm 1 y-update): whoever forms row i
+// of A x+ also updates y_i = proj(y_i + sigma(2 (A x+)_i - (A x)_i - b_i)),
+// its value-type copy, the A x cache and the running average.
 template <class V, int NT>
-__device__ void cta_qprod(const V* F, const V* qd, int n, int k, const double* p, double* t,
+__device__ void cta_dual(const LocalCsr<V>& A, const V* xv, const double* b, int m_eq,
+                         double sigma, double inv_j, double* y, V* yv, double* ax, double* ya) {
+  auto row = [&](int i, double s) {
+    double yn = y[i] + sigma * (2.0 * s - ax[i] - b[i]);
+    if (i >= m_eq && yn < 0.0) yn = 0.0;
+    y[i] = yn;
+    yv[i] = V(yn);
+    ax[i] = s;
+    ya[i] += (yn - ya[i]) * inv_j;
+  };
+  for (int i = threadIdx.x; i < A.rows; i += NT) {
+    const int b0 = A.rp[i], e = A.rp[i + 1];
+    if (e - b0 > kBatchLongRow) continue;
+    V s = V(0);
+    for (int k = b0; k < e; ++k) s = fma(A.val[k], xv[A.col[k]], s);
+    row(i, double(s));
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = w; t < A.nlong; t += NT / 32) {
+    const int i = A.longr[t];
+    V s = V(0);
+    for (int k = A.rp[i] + lane; k < A.rp[i + 1]; k += 32) s = fma(A.val[k], xv[A.col[k]], s);
+    s = warp_sum_v(s);
+    if (lane == 0) row(i, double(s));
+  }
+}
+
+// out = (F F' + diag(qd)) p with F column-major: t = F'p by a warp per
+// column, then a thread per row.  p and t are in the value type.  Two
+// barriers; out is ready on return.
+template <class V, int NT>
+__device__ void cta_qprod(const V* F, const V* qd, int n, int k, const V* p, V* t,
                           double* out) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int l = w; l < k; l += NT / 32) {
     const V* Fl = F + size_t(l) * n;
     V s = V(0);
-    for (int j = lane; j < n; j += 32) s = fma(Fl[j], V(p[j]), s);
+    for (int j = lane; j < n; j += 32) s = fma(Fl[j], p[j], s);
     s = warp_sum_v(s);
-    if (lane == 0) t[l] = double(s);
+    if (lane == 0) t[l] = s;
   }
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += NT) {
-    V s = qd[j] * V(p[j]);
-    for (int l = 0; l < k; ++l) s = fma(F[size_t(l) * n + j], V(t[l]), s);
+    V s = qd[j] * p[j];
+    for (int l = 0; l < k; ++l) s = fma(F[size_t(l) * n + j], t[l], s);
     out[j] = double(s);
   }
   __syncthreads();
@@ -198,9 +238,10 @@ __device__ __forceinline__ double cta_sum2(double v0, double v1, double* red, do
 template <class V, int NT>
 __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevState& st,
                                 double* red) {
+  constexpr bool kShadow = !std::is_same<V, double>::value;
   const BatchDesc d = B.desc[id];
   const int n = d.n, m = d.m, k = d.k, tid = threadIdx.x;
-  // shared-memory vectors (FP64)
+  // FP64 vectors
   double* x = sm;
   double* xa = x + B.max_n;   // average
   double* x0 = xa + B.max_n;  // restart point
@@ -217,6 +258,21 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
   double* axe = ax + B.max_m;
   double* axa = axe + B.max_m;
   double* t = axa + B.max_m;
+  // value-type copies read by the products (the FP64 vectors themselves
+  // when V is double)
+  V* pv = reinterpret_cast<V*>(p);
+  V* xv = reinterpret_cast<V*>(x);
+  V* yv = reinterpret_cast<V*>(y);
+  V* uv = reinterpret_cast<V*>(axa);
+  V* tv = reinterpret_cast<V*>(t);
+  if constexpr (kShadow) {
+    V* f = reinterpret_cast<V*>(t + B.max_k + 8);
+    pv = f;
+    xv = pv + B.max_n;
+    yv = xv + B.max_n;
+    uv = yv + B.max_m;
+    tv = uv + B.max_m;
+  }
   // instance data
   const double* c = B.c + d.off_n;
   const double* b = B.b + d.off_m;
@@ -237,12 +293,14 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
     x[j] = v;
     x0[j] = v;
     xa[j] = 0.0;
+    if constexpr (kShadow) xv[j] = V(v);
   }
   for (int i = tid; i < m; i += NT) {
     const double v = B.warm ? B.y0[d.off_m + i] : 0.0;
     y[i] = v;
     y0[i] = v;
     ya[i] = 0.0;
+    if constexpr (kShadow) yv[i] = V(v);
   }
   if (tid == 0) {
     st.opt = B.opt;
@@ -251,17 +309,17 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
   }
   __syncthreads();
   // caches A x, A'y, Q x
-  cta_spmv<V, NT>(A, x, ax);
-  cta_spmv<V, NT>(At, y, aty);
+  cta_spmv<V, NT>(A, xv, ax);
+  cta_spmv<V, NT>(At, yv, aty);
   __syncthreads();
-  cta_qprod<V, NT>(F, qd, n, k, x, t, qx);
+  cta_qprod<V, NT>(F, qd, n, k, xv, tv, qx);
 
   // ---- ||A||_2 by power iteration on A'A from ones/sqrt(n) (Section 3.2)
   {
     const double v0 = 1.0 / sqrt((double)n);
     double cc = 0.0, bb = 0.0;
     for (int j = tid; j < n; j += NT) {
-      p[j] = v0;
+      pv[j] = V(v0);
       cc = fma(c[j], c[j], cc);
     }
     for (int i = tid; i < m; i += NT) bb = fma(b[i], b[i], bb);
@@ -269,15 +327,19 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
     const double nc2 = cta_sum2<NT>(cc, bb, red, &nb2);
     double lam = 0.0;
     for (int it = 0; it < B.power_iters; ++it) {
-      cta_spmv<V, NT>(A, p, axa);  // u = A v
+      cta_spmv<V, NT>(A, pv, axa);  // u = A v
       __syncthreads();
-      cta_spmv<V, NT>(At, axa, q);  // w = A'u
+      if constexpr (kShadow) {
+        for (int i = tid; i < m; i += NT) uv[i] = V(axa[i]);
+        __syncthreads();
+      }
+      cta_spmv<V, NT>(At, uv, q);  // w = A'u
       __syncthreads();
       double ww = 0.0;
       for (int j = tid; j < n; j += NT) ww = fma(q[j], q[j], ww);
       lam = sqrt(cta_sum1<NT>(ww, red));
       const double inv = lam > 0.0 ? 1.0 / lam : 0.0;
-      for (int j = tid; j < n; j += NT) p[j] = q[j] * inv;
+      for (int j = tid; j < n; j += NT) pv[j] = V(q[j] * inv);
       __syncthreads();
     }
     if (tid == 0) {
@@ -342,6 +404,7 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
       const double v = -(qx[j] + c[j] + aty[j]);
       r[j] = v;
       p[j] = v;
+      if constexpr (kShadow) pv[j] = V(v);
       rr = fma(v, v, rr);
     }
     return cta_sum1<NT>(rr, red);
@@ -362,7 +425,7 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
       bool numerr = false;
       const bool skip = (mode == kCgFixed && nfix <= 0) || rr == 0.0;
       while (!skip) {
-        cta_qprod<V, NT>(F, qd, n, k, p, t, q);  // q = Q p
+        cta_qprod<V, NT>(F, qd, n, k, pv, tv, q);  // q = Q p
         double pq = 0.0;
         for (int j = tid; j < n; j += NT) pq = fma(p[j], q[j] + p[j] * inv_tau, pq);
         pq = cta_sum1<NT>(pq, red);
@@ -374,7 +437,9 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         double rn = 0.0;
         for (int j = tid; j < n; j += NT) {
           const double pj = p[j], qpj = q[j];
-          x[j] = __dadd_rn(x[j], __dmul_rn(alpha, pj));
+          const double xn = __dadd_rn(x[j], __dmul_rn(alpha, pj));
+          x[j] = xn;
+          if constexpr (kShadow) xv[j] = V(xn);
           qx[j] = __dadd_rn(qx[j], __dmul_rn(alpha, qpj));
           const double rj = __dsub_rn(r[j], __dmul_rn(alpha, qpj + pj * inv_tau));
           r[j] = rj;
@@ -387,7 +452,11 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         if (stop || rr_new == 0.0) break;
         const double beta = rr_new / rr;
         rr = rr_new;
-        for (int j = tid; j < n; j += NT) p[j] = __dadd_rn(r[j], __dmul_rn(beta, p[j]));
+        for (int j = tid; j < n; j += NT) {
+          const double pn = __dadd_rn(r[j], __dmul_rn(beta, p[j]));
+          p[j] = pn;
+          if constexpr (kShadow) pv[j] = V(pn);
+        }
         __syncthreads();
       }
       if (numerr) {
@@ -406,22 +475,13 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         st.j += 1;
       }
       __syncthreads();
-      // ---- y-step: y+ = proj(y + sigma(2 A x+ - A x - b)), A x cache, y~
-      const double sigma = st.sigma, inv_j = 1.0 / (double)st.j;
-      cta_spmv<V, NT>(A, x, axe);
+      // ---- y-step fused into A x+, then A'y+, x~ and the next CG start
+      const double inv_j = 1.0 / (double)st.j;
+      cta_dual<V, NT>(A, xv, b, d.m_eq, st.sigma, inv_j, y, yv, ax, ya);
       __syncthreads();
-      for (int i = tid; i < m; i += NT) {
-        double yn = y[i] + sigma * (2.0 * axe[i] - ax[i] - b[i]);
-        if (i >= d.m_eq && yn < 0.0) yn = 0.0;
-        y[i] = yn;
-        ax[i] = axe[i];
-        ya[i] += (yn - ya[i]) * inv_j;
-      }
-      __syncthreads();
-      // ---- A'y+, x~ and the next CG start
-      cta_spmv<V, NT>(At, y, aty);
-      __syncthreads();
+      cta_spmv<V, NT>(At, yv, aty);
       for (int j = tid; j < n; j += NT) xa[j] += (x[j] - xa[j]) * inv_j;
+      __syncthreads();
       rr0 = prepare();
     }
     // ---- evaluation, termination, restart (Section 4)
@@ -435,6 +495,7 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         dx = fma(e, e, dx);
         x0[j] = cand;
         x[j] = cand;
+        if constexpr (kShadow) xv[j] = V(cand);
       }
       for (int i = tid; i < m; i += NT) {
         const double cand = pending == 2 ? ya[i] : y[i];
@@ -442,17 +503,18 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         dy = fma(e, e, dy);
         y0[i] = cand;
         y[i] = cand;
+        if constexpr (kShadow) yv[i] = V(cand);
       }
       double dy2;
       const double dx2 = cta_sum2<NT>(dx, dy, red, &dy2);
       if (tid == 0) restart_finish_decide(&st, dx2, dy2);
       __syncthreads();
-      cta_spmv<V, NT>(A, x, ax);
-      cta_spmv<V, NT>(At, y, aty);
+      cta_spmv<V, NT>(A, xv, ax);
+      cta_spmv<V, NT>(At, yv, aty);
       __syncthreads();
     }
     // exact Q x for the tracked cache, then the next CG start
-    cta_qprod<V, NT>(F, qd, n, k, x, t, qx);
+    cta_qprod<V, NT>(F, qd, n, k, xv, tv, qx);
     rr0 = prepare();
   }
 
@@ -475,8 +537,15 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
   __syncthreads();
 }
 
+// Blocks per SM the register budget is sized for (launch bounds): 128
+// registers per thread at every block size.
+template <int NT>
+constexpr int batch_min_blocks() {
+  return NT == 64 ? 8 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1));
+}
+
 template <class V, int NT>
-__global__ void __launch_bounds__(NT) k_batch(BatchData<V> B) {
+__global__ void __launch_bounds__(NT, batch_min_blocks<NT>()) k_batch(BatchData<V> B) {
   extern __shared__ double sm_dyn[];
   double* sm = B.ws ? B.ws + (long long)blockIdx.x * B.ws_stride : sm_dyn;
   __shared__ DevState st;
@@ -485,10 +554,10 @@ __global__ void __launch_bounds__(NT) k_batch(BatchData<V> B) {
   for (;;) {
     if (threadIdx.x == 0) id_s = atomicAdd(B.next, 1);
     __syncthreads();
-    const int id = id_s;
+    const int idx = id_s;
     __syncthreads();
-    if (id >= B.count) break;
-    batch_solve_one<V, NT>(B, id, sm, st, red);
+    if (idx >= B.count) break;
+    batch_solve_one<V, NT>(B, B.order[idx], sm, st, red);
   }
 }
 

@@ -267,8 +267,8 @@ class QPBatch:
     def set_threads(self, threads: int) -> None:
         L.check(self.lib.qp_batch_set_threads(self.h, int(threads)), "qp_batch_set_threads")
 
-    def tune(self, options: QPOptions | None = None, sample_count: int = 256,
-             sample_iters: int = 256, **overrides) -> int:
+    def tune(self, options: QPOptions | None = None, sample_count: int = 1 << 30,
+             sample_iters: int = 128, **overrides) -> int:
         o = options or QPOptions()
         for k, v in overrides.items():
             setattr(o, k, v)

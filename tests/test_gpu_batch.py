@@ -161,7 +161,7 @@ def test_batch_every_block_size_solves(batch, threads):
 
 def test_batch_tune_picks_a_block_size(batch):
     insts, bt = batch
-    t = bt.tune(tol=1e-5, precision=L.PREC_MIXED, sample_count=16, sample_iters=128)
+    t = bt.tune(tol=1e-5, precision=L.PREC_MIXED, sample_iters=64)
     assert t in (64, 128, 256, 512)
     bt.solve(tol=1e-5, precision=L.PREC_MIXED)
     assert all(r["termination"] == L.TERM_SOLVED for r in bt.results())
