@@ -76,8 +76,12 @@ enum { QP_RESTART_ADAPTIVE = 0, QP_RESTART_NONE = 2 };
  * Device memory and stream supplied by the caller (e.g. PyTorch's caching
  * allocator and current stream).  alloc must return 256-byte aligned device
  * memory usable on `stream`, or NULL on failure; free releases it.  A NULL
- * context, or NULL alloc/free, means cudaMalloc/cudaFree; a NULL stream
- * means a non-blocking stream owned by the handle.
+ * context, or NULL alloc/free, means cudaMalloc/cudaFree.  Every handle runs
+ * its work on a non-blocking stream of its own; each call orders that stream
+ * after `stream` on entry and `stream` after it on return (by events), so
+ * device buffers the caller passes are read and written in the caller's
+ * stream order.  A NULL stream (or a NULL context) is the legacy default
+ * stream, PyTorch's default stream.
  */
 typedef struct {
   void* (*alloc)(size_t bytes, void* user, void* stream);
@@ -401,6 +405,40 @@ qp_status qp_batch_set_threads(qp_batch* bt, int32_t threads);
  * (a few blocks per SM) for the timing to reflect throughput. */
 qp_status qp_batch_tune(qp_batch* bt, const qp_options* o, int32_t sample_count,
                         int32_t sample_iters, int32_t* threads_out);
+
+/* ------------------------------------------------ learned warm start (MLP) */
+/*
+ * The network of the learned warm start (not in the paper): a multilayer
+ * perceptron mapping an instance's parameters to a starting point (x0, y0)
+ * for qp_batch_set_warm_start / qp_set_warm_start.  widths[0] inputs,
+ * widths[n_layers] outputs, ReLU after every layer but the last; layer l is
+ * z = a W_l + b_l with W_l row-major (widths[l-1] x widths[l]).  FP32
+ * parameters packed in layer order, each layer W then b.  Activations are
+ * row-major, one sample per row.  The loss is the weighted squared error
+ * (1/B) sum_r sum_j w_j (out_rj - target_rj)^2, trained with Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).  in, out, target, w and grad are
+ * device pointers; params of set/get are host pointers.
+ */
+typedef struct qp_mlp qp_mlp;
+
+/* n_layers in [1, 16], widths in [1, 2^20]; batches of up to max_batch rows.
+ * Parameters start at zero (set them with qp_mlp_set_params). */
+qp_status qp_mlp_create(qp_mlp** out, int32_t n_layers, const int32_t* widths,
+                        int32_t max_batch, const qp_device_ctx* ctx);
+void qp_mlp_destroy(qp_mlp* net);
+int64_t qp_mlp_param_count(const qp_mlp* net);
+/* Host copy in/out of the packed parameters; set also resets Adam's state. */
+qp_status qp_mlp_set_params(qp_mlp* net, const float* params);
+qp_status qp_mlp_get_params(const qp_mlp* net, float* params);
+/* out (batch x widths[n_layers]) = net(in (batch x widths[0])). */
+qp_status qp_mlp_forward(qp_mlp* net, int32_t batch, const float* in, float* out);
+/* The loss on one batch and its gradient (kept for qp_mlp_adam_step; also
+ * copied to grad, param_count floats, when grad is not NULL).  w: per-output
+ * weights or NULL for ones.  *loss (host, may be NULL) waits for the result. */
+qp_status qp_mlp_loss_grad(qp_mlp* net, int32_t batch, const float* in, const float* target,
+                           const float* w, float* grad, double* loss);
+/* One Adam step with the gradient of the last qp_mlp_loss_grad. */
+qp_status qp_mlp_adam_step(qp_mlp* net, float lr);
 
 #ifdef __cplusplus
 }

@@ -4,8 +4,8 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
-from ctypes import (CFUNCTYPE, POINTER, Structure, c_char_p, c_double, c_int32, c_int64, c_size_t,
-                    c_uint32, c_void_p)
+from ctypes import (CFUNCTYPE, POINTER, Structure, c_char_p, c_double, c_float, c_int32, c_int64,
+                    c_size_t, c_uint32, c_void_p)
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libpdhcg.so")
@@ -136,6 +136,15 @@ SIGNATURES = [
     ("qp_batch_set_warm_start", c_int32, [_H, _F64P, _F64P]),
     ("qp_batch_set_threads", c_int32, [_H, c_int32]),
     ("qp_batch_tune", c_int32, [_H, POINTER(QPOptionsC), c_int32, c_int32, _I32P]),
+    ("qp_mlp_create", c_int32, [POINTER(_H), c_int32, _I32P, c_int32, POINTER(QPDeviceCtxC)]),
+    ("qp_mlp_destroy", None, [_H]),
+    ("qp_mlp_param_count", c_int64, [_H]),
+    ("qp_mlp_set_params", c_int32, [_H, POINTER(c_float)]),
+    ("qp_mlp_get_params", c_int32, [_H, POINTER(c_float)]),
+    ("qp_mlp_forward", c_int32, [_H, c_int32, c_void_p, c_void_p]),
+    ("qp_mlp_loss_grad", c_int32, [_H, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   POINTER(c_double)]),
+    ("qp_mlp_adam_step", c_int32, [_H, c_float]),
 ]
 
 _lock = threading.Lock()

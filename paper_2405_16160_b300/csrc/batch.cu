@@ -141,18 +141,15 @@ qp_status to_float(qp_batch* h, const double* in, float** out, size_t n) {
 
 qp_status begin(qp_batch* h) {
   BCUDA(cudaSetDevice(h->device));
-  if (h->user_stream) {
-    BCUDA(cudaEventRecord(h->ev_a, h->user_stream));
-    BCUDA(cudaStreamWaitEvent(h->stream, h->ev_a, 0));
-  }
+  // the caller's stream; 0 is the legacy default stream (PyTorch's default)
+  BCUDA(cudaEventRecord(h->ev_a, h->user_stream));
+  BCUDA(cudaStreamWaitEvent(h->stream, h->ev_a, 0));
   return QP_OK;
 }
 
 qp_status finish(qp_batch* h) {
-  if (h->user_stream) {
-    BCUDA(cudaEventRecord(h->ev_b, h->stream));
-    BCUDA(cudaStreamWaitEvent(h->user_stream, h->ev_b, 0));
-  }
+  BCUDA(cudaEventRecord(h->ev_b, h->stream));
+  BCUDA(cudaStreamWaitEvent(h->user_stream, h->ev_b, 0));
   return QP_OK;
 }
 

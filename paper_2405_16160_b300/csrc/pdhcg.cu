@@ -623,18 +623,15 @@ qp_status ensure_events(qp_handle* h, int iters) {
 
 qp_status begin_call(qp_handle* h) {
   CUDA_TRY(cudaSetDevice(h->device));
-  if (h->user_stream) {
-    CUDA_TRY(cudaEventRecord(h->ev_a, h->user_stream));
-    CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_a, 0));
-  }
+  // the caller's stream; 0 is the legacy default stream (PyTorch's default)
+  CUDA_TRY(cudaEventRecord(h->ev_a, h->user_stream));
+  CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_a, 0));
   return QP_OK;
 }
 
 qp_status end_call(qp_handle* h) {
-  if (h->user_stream) {
-    CUDA_TRY(cudaEventRecord(h->ev_b, h->stream));
-    CUDA_TRY(cudaStreamWaitEvent(h->user_stream, h->ev_b, 0));
-  }
+  CUDA_TRY(cudaEventRecord(h->ev_b, h->stream));
+  CUDA_TRY(cudaStreamWaitEvent(h->user_stream, h->ev_b, 0));
   return QP_OK;
 }
 
