@@ -502,6 +502,101 @@ def run_batch_bench(args):
     return 0
 
 
+WS_WORKLOAD = {
+    "workload": "parametric portfolio family: n=2000, k=50 factors, 30 sector caps, budget and "
+                "long-only rows (m=2031); per instance mu ~ N(0.05, 0.02) and F = F0 + 10% "
+                "Gaussian; network trained on solver solutions of 20000 instances, judged on "
+                "1000 held-out instances",
+    "n": 2000, "train": 20000, "test": 1000, "tol": 1e-4, "hidden": [512, 512],
+}
+WS_METRIC = ("time to 1e-4 rel. KKT on 1000 held-out portfolio QPs (batched PDHCG): "
+             "learned warm start vs cold start")
+
+
+def run_warmstart_bench(args):
+    import numpy as np
+    import torch
+
+    ws, rank = _dist()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from oracle import mlp_oracle as M  # He-normal starting weights from a seeded generator
+    from paper_2405_16160_b300 import _lib as L
+    from paper_2405_16160_b300 import build as B
+    from paper_2405_16160_b300 import warmstart as WS
+    from paper_2405_16160_b300 import workloads as W
+
+    B.build()
+    n, tol = WS_WORKLOAD["n"], WS_WORKLOAD["tol"]
+    # training data: solver solutions, generated and solved in chunks
+    t0 = time.perf_counter()
+    feats, targs, omegas, gen_iters = [], [], [], []
+    chunk = 1000
+    for s0 in range(1, WS_WORKLOAD["train"] + 1, chunk):
+        insts = W.portfolio_family(0, seeds=range(s0, s0 + chunk), n=n)
+        res, xs, ys = WS.solve_family(insts, tol=tol, precision=L.PREC_MIXED)
+        keep = [i for i, r in enumerate(res) if r["termination"] == L.TERM_SOLVED]
+        feats.append(WS.features([insts[i] for i in keep]))
+        targs.append(WS.targets([xs[i] for i in keep], [ys[i] for i in keep]))
+        omegas += [res[i]["omega"] for i in keep]
+        gen_iters += [res[i]["iterations"] for i in keep]
+        del insts
+    gen_s = time.perf_counter() - t0
+    X, T = np.concatenate(feats), np.concatenate(targs)
+    widths = [X.shape[1], *WS_WORKLOAD["hidden"], T.shape[1]]
+    net = WS.WarmStartMLP(widths, max_batch=1024)
+    net.set_params(M.he_init(widths, 0).astype(np.float32))
+    t0 = time.perf_counter()
+    hist = WS.train(net, X, T, epochs=args.train_epochs, batch=256, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    model = WS.WarmStartModel(net, n, float(np.median(omegas)))
+    test = W.portfolio_family(0, seeds=range(WS_WORKLOAD["train"] + 1,
+                                             WS_WORKLOAD["train"] + 1 + WS_WORKLOAD["test"]), n=n)
+    cold_t, warm_t = [], []
+    for step in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cold, _, _ = WS.solve_family(test, tol=tol, precision=L.PREC_MIXED)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        hot, _, _, n_fb = model.solve(test, tol=tol, precision=L.PREC_MIXED)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if step >= args.warmup:
+            cold_t.append(t1 - t0)
+            warm_t.append(t2 - t1)
+    it_c = float(np.mean([r["iterations"] for r in cold]))
+    it_w = float(np.mean([r["iterations"] for r in hot]))
+    value = statistics.mean(warm_t)
+    if rank != 0:
+        return 0
+    out = {
+        "metric": WS_METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 vectors and reductions)",
+        "data": "synthetic",
+        "config": dict(WS_WORKLOAD, cold_start_s=statistics.mean(cold_t),
+                       speedup_vs_cold=statistics.mean(cold_t) / value,
+                       iterations_cold=it_c, iterations_warm=it_w,
+                       iteration_ratio=it_w / it_c, fallbacks=n_fb,
+                       solved_warm=int(sum(r["termination"] == 0 for r in hot)),
+                       omega0=model.omega0, train_loss_first=hist[0], train_loss_last=hist[-1],
+                       train_epochs=args.train_epochs, data_generation_s=gen_s,
+                       data_generation_iterations_mean=float(np.mean(gen_iters)),
+                       training_s=train_s,
+                       timing="wall clock of create + solve + solution per 1000-instance "
+                              "batch, prediction included in the warm arm"),
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": int(sum(
+                    q.F.nbytes + q.qd.nbytes + q.c.nbytes + q.b.nbytes + q.A_val.nbytes
+                    + q.A_col.nbytes + q.A_rowptr.nbytes for q in test)),
+                "d2h_bytes_per_step": int(8 * sum(q.n + q.m for q in test))},
+        "roofline": None, "cpu_baseline": None, "gpu_launches": None, "clocks": None,
+    }
+    print(json.dumps(out), flush=True)
+    net.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -509,12 +604,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sparse_dd", "portfolio_batch"], default="sparse_dd")
+    ap.add_argument("--workload", choices=["sparse_dd", "portfolio_batch", "learned_warm_start"],
+                    default="sparse_dd")
+    ap.add_argument("--train-epochs", type=int, default=30)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "portfolio_batch":
         return run_batch_bench(args)
+    if args.workload == "learned_warm_start":
+        return run_warmstart_bench(args)
     return run_ours(args)
 
 
