@@ -43,6 +43,22 @@ path implements the same one):
   iterations on A'A from the normalised all-ones vector.  If ||A||_2 is not
   above eps_zero (no coupling), ||A||_2 is replaced by eps_zero.
 * omega_0 = ||c||_2 / ||b||_2 when both exceed eps_zero, else 1; x0 = y0 = 0.
+* Adaptive step size (Section 4, optional ``step_mode = STEP_ADAPTIVE``).  The
+  paper prints only the bound eta <= ||dz||_w^2 / (2 dx'A'dy + dx'Q dx) and
+  says the rule follows PDLP.  Reading: one *attempt* runs the whole
+  iteration (CG x-step, dual step) with the current eta into a trial point
+  z' = (x', y'); with dz = z' - z and the primal-weighted norm
+  ||dz||_w^2 = omega ||dx||^2 + ||dy||^2 / omega (the weighting that tau =
+  eta/omega, sigma = eta*omega imply), the limit is
+  L = ||dz||_w^2 / (2 |dy'A dx| + dx'Q dx) (infinite when the denominator is
+  0; the absolute value makes it a bound for either sign of the coupling).
+  The attempt is accepted when eta <= L; either way the next eta is PDLP's
+  min((1 - (a+1)^-0.3) L, (1 + (a+1)^-0.6) eta), a = attempts so far.  A
+  rejected attempt leaves z unchanged.  The averages of the epoch are then
+  step-weighted, sum eta_k z_k / sum eta_k (they are the uniform mean when
+  eta is fixed); the CG precision epsilon advances once per accepted
+  iteration; eval_freq and max_iter count attempts (they equal iterations
+  with the fixed step).
 * Preprocessing (Section 4, optional ``scale``): D1 (constraints) and D2
   (variables) from 10 Ruiz equilibration steps and one Pock-Chambolle step
   (alpha = 1) on the symmetric K = [[Q, A'], [A, 0]]; the iteration runs on
@@ -70,6 +86,9 @@ CG_FIXED = 1
 RESTART_ADAPTIVE = 0
 RESTART_FIXED = 1  # restart to the average every K iterations (Algorithm 1)
 RESTART_NONE = 2
+
+STEP_FIXED = 0
+STEP_ADAPTIVE = 1
 
 SOLVED = 0
 ITER_LIMIT = 1
@@ -288,6 +307,9 @@ class OracleOptions:
     omega0: float = 0.0  # <= 0: ||c||/||b|| rule
     eta: float = 0.0  # <= 0: 1/(2||A||)
     scale: bool = False  # Section 4 preprocessing (Ruiz x10 + Pock-Chambolle)
+    step_mode: int = STEP_FIXED  # STEP_ADAPTIVE: the Section 4 adaptive step size
+    step_reduction_exp: float = 0.3
+    step_growth_exp: float = 0.6
 
 
 @dataclass
@@ -309,6 +331,9 @@ class OracleState:
     n_restarts: int = 0
     cg_total: int = 0
     last_cg_steps: int = 0
+    attempts: int = 0  # steps tried (= k_total with the fixed step)
+    weight_sum: float = 0.0  # sum of the accepted steps' eta in this epoch
+    last_accepted: bool = True
 
     @property
     def tau(self) -> float:
@@ -336,26 +361,70 @@ def initial_state(P: OracleProblem, o: OracleOptions) -> OracleState:
     return OracleState(z(P.n), z(P.m), z(P.n), z(P.m), z(P.n), z(P.m), eta, omega)
 
 
-def inner_step(P: OracleProblem, st: OracleState, o: OracleOptions) -> None:
-    """One PDHCG iteration z^{n,k} -> z^{n,k+1} (Algorithm 1 loop body), in place."""
+def step_limit(P: OracleProblem, x: np.ndarray, y: np.ndarray, x_new: np.ndarray,
+               y_new: np.ndarray, omega: float) -> float:
+    """Section 4 adaptive step-size bound for the trial step z -> z':
+
+    ||dz||_w^2 / (2 |dy' A dx| + dx' Q dx), ||dz||_w^2 = omega ||dx||^2 + ||dy||^2 / omega;
+    infinite when the denominator is zero.
+    """
+    dx, dy = x_new - x, y_new - y
+    movement = omega * float(dx @ dx) + float(dy @ dy) / omega
+    interaction = 2.0 * abs(float(dy @ (P.A @ dx))) + float(dx @ (P.Q @ dx))
+    return movement / interaction if interaction > 0.0 else math.inf
+
+
+def next_step_size(eta: float, limit: float, attempts: int, o: OracleOptions) -> float:
+    """PDLP's step update after an attempt: min((1-(a+1)^-0.3) L, (1+(a+1)^-0.6) eta)."""
+    a1 = float(attempts + 1)
+    return min((1.0 - a1 ** -o.step_reduction_exp) * limit, (1.0 + a1 ** -o.step_growth_exp) * eta)
+
+
+def pdhcg_step(P: OracleProblem, st: OracleState, o: OracleOptions, eps: float):
+    """The Algorithm 1 loop body from z = (x, y) with the current eta: returns (x', y', CG steps)."""
     tau, sigma = st.tau, st.sigma
-    # epsilon_{k+1} = epsilon_k + 0.05 relKKT(z^{n,k})   (Section 4)
-    if o.cg_mode == CG_ADAPTIVE:
-        st.eps = st.eps + o.cg_eps_factor * st.relkkt_last
     # x^{k+1} ~ argmin_x L(x, y^k) + ||x - x^k||^2/(2 tau):  (Q + I/tau) x = x^k/tau - c - A'y^k
     rhs = st.x / tau - P.c - P.A.T @ st.y
-    x_new, steps = cg(P.Q, tau, rhs, st.x, o.cg_mode, o.cg_fixed_n, st.eps, o.cg_max)
+    x_new, steps = cg(P.Q, tau, rhs, st.x, o.cg_mode, o.cg_fixed_n, eps, o.cg_max)
     # y^{k+1} = proj(y^k + sigma (A(2x^{k+1} - x^k) - b)); equality rows unprojected
     y_new = st.y + sigma * (P.A @ (2.0 * x_new - st.x) - P.b)
     y_new[P.m_eq:] = np.maximum(y_new[P.m_eq:], 0.0)
-    # running averages with beta = j (uniform mean of the epoch's iterates)
-    st.j += 1
-    st.x_avg = st.x_avg + (x_new - st.x_avg) / st.j
-    st.y_avg = st.y_avg + (y_new - st.y_avg) / st.j
-    st.x, st.y = x_new, y_new
-    st.k_total += 1
+    return x_new, y_new, steps
+
+
+def inner_step(P: OracleProblem, st: OracleState, o: OracleOptions) -> None:
+    """One attempt of a PDHCG iteration z^{n,k} -> z^{n,k+1} (Algorithm 1 loop body), in place.
+
+    Fixed step: always accepted.  Adaptive step (Section 4): accepted when
+    eta <= step_limit, and eta moves to next_step_size either way.
+    """
+    # epsilon_{k+1} = epsilon_k + 0.05 relKKT(z^{n,k})   (Section 4)
+    eps = st.eps + o.cg_eps_factor * st.relkkt_last if o.cg_mode == CG_ADAPTIVE else st.eps
+    x_new, y_new, steps = pdhcg_step(P, st, o, eps)
+    st.attempts += 1
     st.cg_total += steps
     st.last_cg_steps = steps
+    eta = st.eta
+    if o.step_mode == STEP_ADAPTIVE:
+        limit = step_limit(P, st.x, st.y, x_new, y_new, st.omega)
+        st.eta = next_step_size(eta, limit, st.attempts, o)
+        st.last_accepted = eta <= limit
+        if not st.last_accepted:
+            return
+    st.eps = eps
+    st.j += 1
+    if o.step_mode == STEP_ADAPTIVE:
+        # step-weighted averages: sum eta_k z_k / sum eta_k over the epoch
+        st.weight_sum += eta
+        w = eta / st.weight_sum
+        st.x_avg = st.x_avg + w * (x_new - st.x_avg)
+        st.y_avg = st.y_avg + w * (y_new - st.y_avg)
+    else:
+        # running averages with beta = j (uniform mean of the epoch's iterates)
+        st.x_avg = st.x_avg + (x_new - st.x_avg) / st.j
+        st.y_avg = st.y_avg + (y_new - st.y_avg) / st.j
+    st.x, st.y = x_new, y_new
+    st.k_total += 1
 
 
 def restart_to(P: OracleProblem, st: OracleState, o: OracleOptions, use_avg: bool,
@@ -372,6 +441,7 @@ def restart_to(P: OracleProblem, st: OracleState, o: OracleOptions, use_avg: boo
     st.x, st.y = xc, yc
     st.x_anchor, st.y_anchor = xc.copy(), yc.copy()
     st.j = 0
+    st.weight_sum = 0.0
     st.eps = 0.0
     st.kkt_anchor = kkt_cand
     st.kkt_prev_cand = math.inf
@@ -461,14 +531,14 @@ def solve(P: OracleProblem, o: OracleOptions | None = None,
     best = None
     use_avg = False
     try:
-        while st.k_total < o.max_iter:
+        while st.attempts < o.max_iter:
             inner_step(Pi, st, o)
             if step_hook is not None:
                 step_hook(st)
             if o.restart_mode == RESTART_FIXED and st.j >= o.restart_k:
                 kc = kkt(st.x_avg, st.y_avg)
                 restart_to(Pi, st, o, True, kc.relkkt)
-            if st.k_total % o.eval_freq == 0:
+            if st.attempts % o.eval_freq == 0:
                 done, best, use_avg = evaluate(Pi, st, o, trace, kkt)
                 if done:
                     term = SOLVED

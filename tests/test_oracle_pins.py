@@ -5,7 +5,11 @@ determines: hand-worked relKKT values (Section 4), closed-form QP solutions,
 LAPACK solves, an exhaustive active-set search on tiny QPs, the textbook CG
 error bound (Section 2), Lemma A.2(2) and Theorem 2 of the appendix, and the
 trend of Table 2.  The last group plants mistakes in the oracle and checks
-that a pin catches each one.
+that a pin catches each one.  The adaptive step size of Section 4 is pinned
+by its closed form at the top singular pair of A, a lower bound that follows
+from Cauchy-Schwarz and AM-GM, PDLP's update rule worked by hand, the
+accept/reject invariants, step-weighted averages and the closed-form and
+brute-force solutions reached with it.
 """
 import itertools
 import json
@@ -170,19 +174,21 @@ def _opts(**kw):
     return o
 
 
-def test_solver_unconstrained_m0():
+@pytest.mark.parametrize("step", [O.STEP_FIXED, O.STEP_ADAPTIVE])
+def test_solver_unconstrained_m0(step):
     rng = np.random.default_rng(6)
     n = 25
     Qd = _rand_spd(rng, n, 20.0)
     c = rng.standard_normal(n)
     P = _prob(Qd, np.zeros((0, n)), c, np.zeros(0))
-    res = O.solve(P, _opts())
+    res = O.solve(P, _opts(step_mode=step))
     assert res.termination == O.SOLVED
     xs = -np.linalg.solve(Qd, c)
     assert np.linalg.norm(res.x - xs) <= 1e-8 * (1 + np.linalg.norm(xs))
 
 
-def test_solver_diagonal_box_closed_form():
+@pytest.mark.parametrize("step", [O.STEP_FIXED, O.STEP_ADAPTIVE])
+def test_solver_diagonal_box_closed_form(step):
     rng = np.random.default_rng(7)
     n = 40
     q = rng.uniform(0.5, 2.0, n)
@@ -190,7 +196,7 @@ def test_solver_diagonal_box_closed_form():
     lo, hi = -rng.uniform(0.1, 1, n), rng.uniform(0.1, 1, n)
     Ad = np.vstack([np.eye(n), -np.eye(n)])
     b = np.concatenate([hi, -lo])
-    res = O.solve(_prob(np.diag(q), Ad, c, b), _opts())
+    res = O.solve(_prob(np.diag(q), Ad, c, b), _opts(step_mode=step))
     assert res.termination == O.SOLVED
     xs = np.clip(-c / q, lo, hi)
     g = q * xs + c
@@ -199,13 +205,14 @@ def test_solver_diagonal_box_closed_form():
     assert np.max(np.abs(res.y - ys)) <= 1e-7
 
 
-def test_solver_equality_hyperplane_closed_form():
+@pytest.mark.parametrize("step", [O.STEP_FIXED, O.STEP_ADAPTIVE])
+def test_solver_equality_hyperplane_closed_form(step):
     rng = np.random.default_rng(8)
     n = 30
     a = rng.standard_normal(n)
     c = rng.standard_normal(n)
     beta = 0.7
-    res = O.solve(_prob(np.eye(n), a[None, :], c, [beta], m_eq=1), _opts())
+    res = O.solve(_prob(np.eye(n), a[None, :], c, [beta], m_eq=1), _opts(step_mode=step))
     assert res.termination == O.SOLVED
     xs = -c + a * (beta + a @ c) / (a @ a)
     lam = -(beta + a @ c) / (a @ a)
@@ -213,8 +220,9 @@ def test_solver_equality_hyperplane_closed_form():
     assert res.y[0] == pytest.approx(lam, abs=1e-7)
 
 
+@pytest.mark.parametrize("step", [O.STEP_FIXED, O.STEP_ADAPTIVE])
 @pytest.mark.parametrize("seed,n,m,m_eq", [(10, 4, 6, 0), (11, 5, 8, 0), (12, 6, 7, 2), (13, 3, 8, 1)])
-def test_solver_matches_active_set_brute_force(seed, n, m, m_eq):
+def test_solver_matches_active_set_brute_force(seed, n, m, m_eq, step):
     rng = np.random.default_rng(seed)
     Qd = _rand_spd(rng, n, 10.0)
     Ad = rng.standard_normal((m, n))
@@ -222,7 +230,7 @@ def test_solver_matches_active_set_brute_force(seed, n, m, m_eq):
     x0 = rng.standard_normal(n)
     b = Ad @ x0 + np.concatenate([np.zeros(m_eq), rng.uniform(0, 0.5, m - m_eq)])
     xs, ys = brute_force_qp(Qd, Ad, c, b, m_eq)
-    res = O.solve(_prob(Qd, Ad, c, b, m_eq), _opts())
+    res = O.solve(_prob(Qd, Ad, c, b, m_eq), _opts(step_mode=step))
     assert res.termination == O.SOLVED
     assert np.linalg.norm(res.x - xs) <= 1e-6 * (1 + np.linalg.norm(xs))
     fs = 0.5 * xs @ Qd @ xs + c @ xs
@@ -336,6 +344,7 @@ def _mutated_inner_step(kind):
         st.y_avg = st.y_avg + (y_new - st.y_avg) / w
         st.x, st.y = x_new, y_new
         st.k_total += 1
+        st.attempts += 1
         st.cg_total += steps
     return step
 
@@ -486,16 +495,17 @@ def test_ruiz_equilibrates_rows():
     assert np.all(rn1 > 0) and np.all(rm1 > 0)
 
 
+@pytest.mark.parametrize("step", [O.STEP_FIXED, O.STEP_ADAPTIVE])
 @pytest.mark.parametrize("seed,n,m,m_eq", [(10, 4, 6, 0), (12, 6, 7, 2), (13, 3, 8, 1)])
-def test_scaled_solver_matches_active_set_brute_force(seed, n, m, m_eq):
+def test_scaled_solver_matches_active_set_brute_force(seed, n, m, m_eq, step):
     rng = np.random.default_rng(seed)
-    Qd = _rand_spd(rng, n, 10.0) * np.exp(rng.uniform(-2, 2, n))[:, None]
-    Qd = (Qd + Qd.T) / 2 + np.eye(n) * 0.1
+    dsc = np.exp(rng.uniform(-2, 2, n))  # badly scaled but PSD (Eq. (1)): D Q D + 0.1 I
+    Qd = dsc[:, None] * _rand_spd(rng, n, 10.0) * dsc[None, :] + np.eye(n) * 0.1
     Ad = rng.standard_normal((m, n)) * np.exp(rng.uniform(-2, 2, (m, 1)))
     c = rng.standard_normal(n) * 3
     b = Ad @ rng.standard_normal(n) + np.concatenate([np.zeros(m_eq), rng.uniform(0, 0.5, m - m_eq)])
     xs, ys = brute_force_qp(Qd, Ad, c, b, m_eq)
-    res = O.solve(_prob(Qd, Ad, c, b, m_eq), _opts(scale=True))
+    res = O.solve(_prob(Qd, Ad, c, b, m_eq), _opts(scale=True, step_mode=step))
     assert res.termination == O.SOLVED
     assert np.linalg.norm(res.x - xs) <= 1e-6 * (1 + np.linalg.norm(xs))
     assert O.relkkt(_prob(Qd, Ad, c, b, m_eq), res.x, res.y).relkkt <= 1e-10
@@ -511,3 +521,162 @@ def test_scaled_solver_box_closed_form():
                         np.concatenate([hi, -lo])), _opts(scale=True))
     assert res.termination == O.SOLVED
     assert np.max(np.abs(res.x - np.clip(-c / q, lo, hi))) <= 1e-8
+
+
+# ---------------------------------------------------------------- adaptive step size (Section 4)
+def _svd_top(Ad):
+    U, sv, Vt = np.linalg.svd(Ad)
+    return U[:, 0], sv[0], Vt[0]
+
+
+@pytest.mark.parametrize("omega", [0.3, 1.0, 4.0])
+def test_step_limit_at_the_top_singular_pair(omega):
+    """Q = qI, dx = t v1, dy = -/+ omega t u1 (top singular pair of A, LAPACK SVD):
+    ||dz||_w^2 = 2 omega t^2, |dy'A dx| = omega s1 t^2, dx'Q dx = q t^2, so the
+    limit is 2 omega / (2 omega s1 + q); with q = 0 it is 1/||A||_2 exactly.
+    Both signs of dy: the coupling enters through its absolute value."""
+    rng = np.random.default_rng(30)
+    n, m = 7, 5
+    Ad = rng.standard_normal((m, n))
+    u1, s1, v1 = _svd_top(Ad)
+    x, y = rng.standard_normal(n), rng.standard_normal(m)
+    for q in (0.0, 0.7):
+        P = _prob(q * np.eye(n), Ad, np.zeros(n), np.zeros(m))
+        for sign in (1.0, -1.0):
+            t = 0.37
+            L = O.step_limit(P, x, y, x + t * v1, y + sign * omega * t * u1, omega)
+            assert L == pytest.approx(2 * omega / (2 * omega * s1 + q), rel=1e-12)
+    P0 = _prob(np.zeros((n, n)), Ad, np.zeros(n), np.zeros(m))
+    assert O.step_limit(P0, x, y, x + v1, y + omega * u1, omega) == pytest.approx(1 / s1, rel=1e-12)
+
+
+def test_step_limit_lower_bound_and_no_motion():
+    """2|dy'A dx| <= ||A|| (omega||dx||^2 + ||dy||^2/omega) and dx'Qdx <= ||Q|| ||dx||^2
+    give L >= 1/(||A||_2 + ||Q||_2/omega) for every trial step; no motion gives no limit."""
+    rng = np.random.default_rng(31)
+    n, m = 9, 6
+    Qd = _rand_spd(rng, n, 30.0)
+    Ad = rng.standard_normal((m, n))
+    P = _prob(Qd, Ad, np.zeros(n), np.zeros(m))
+    nA, nQ = np.linalg.norm(Ad, 2), np.linalg.norm(Qd, 2)
+    for _ in range(200):
+        omega = math.exp(rng.uniform(-3, 3))
+        x, y = rng.standard_normal(n), rng.standard_normal(m)
+        dx = rng.standard_normal(n) * math.exp(rng.uniform(-2, 2))
+        dy = rng.standard_normal(m) * math.exp(rng.uniform(-2, 2))
+        L = O.step_limit(P, x, y, x + dx, y + dy, omega)
+        assert L >= (1 - 1e-12) / (nA + nQ / omega)
+    assert O.step_limit(P, x, y, x, y, 1.0) == math.inf
+
+
+def test_next_step_size_worked_by_hand():
+    """PDLP's rule with a = 3 attempts: 4^-0.3 = 0.6597539553864471 and
+    4^-0.6 = 0.43527528164806206 (= 2^-0.6, 2^-1.2)."""
+    o = O.OracleOptions()
+    # reject eta = 0.5 against L = 0.4: min(0.4 * 0.34024604461355, 0.5 * 1.43527528164806)
+    assert O.next_step_size(0.5, 0.4, 3, o) == pytest.approx(0.13609841784542116, rel=1e-14)
+    # accept eta = 0.05 against L = 0.4: the growth term 0.05 * 1.435... is the smaller
+    assert O.next_step_size(0.05, 0.4, 3, o) == pytest.approx(0.0717637640824031, rel=1e-14)
+    # no limit: pure growth
+    assert O.next_step_size(0.1, math.inf, 3, o) == pytest.approx(0.14352752816480621, rel=1e-14)
+
+
+def _adaptive_problem():
+    rng = np.random.default_rng(32)
+    n, m, m_eq = 12, 16, 2
+    Qd = _rand_spd(rng, n, 50.0)
+    Ad = rng.standard_normal((m, n))
+    c = rng.standard_normal(n) * 3
+    b = Ad @ rng.standard_normal(n) + np.concatenate([np.zeros(m_eq), rng.uniform(0, 0.5, m - m_eq)])
+    return _prob(Qd, Ad, c, b, m_eq)
+
+
+def _watch_attempts(monkeypatch, P, o):
+    """Run a solve, recording every attempt: (accepted, eta, limit, k before/after, z before/after)."""
+    seen = []
+    inner = O.inner_step
+
+    def wrapped(Pi, st, oo):
+        x0, y0, eta0, om0, k0 = st.x.copy(), st.y.copy(), st.eta, st.omega, st.k_total
+        xa0, ya0, j0 = st.x_avg.copy(), st.y_avg.copy(), st.j
+        inner(Pi, st, oo)
+        seen.append(dict(acc=st.last_accepted, eta=eta0, eta_next=st.eta, k0=k0, k=st.k_total,
+                         x0=x0, y0=y0, x=st.x.copy(), y=st.y.copy(), j0=j0, j=st.j,
+                         xa0=xa0, ya0=ya0, xa=st.x_avg.copy(), ya=st.y_avg.copy(),
+                         L=O.step_limit(Pi, x0, y0, st.x, st.y, om0) if st.last_accepted else None))
+
+    monkeypatch.setattr(O, "inner_step", wrapped)
+    res = O.solve(P, o)
+    monkeypatch.setattr(O, "inner_step", inner)
+    return res, seen
+
+
+def test_adaptive_step_accept_reject_invariants(monkeypatch):
+    """Every accepted step satisfies eta <= L and advances k by one; every
+    rejected attempt leaves (x, y), k and the averages unchanged and shrinks eta.
+    A start at 40x the fixed step forces rejections."""
+    P = _adaptive_problem()
+    eta0 = 40.0 / (2.0 * O.spectral_norm(P.A, 30))
+    res, seen = _watch_attempts(monkeypatch, P, _opts(step_mode=O.STEP_ADAPTIVE, eta=eta0, tol=1e-8))
+    assert res.termination == O.SOLVED
+    rej = [s for s in seen if not s["acc"]]
+    acc = [s for s in seen if s["acc"]]
+    assert len(rej) >= 1 and len(acc) == res.iterations
+    for s in acc:
+        assert s["eta"] <= s["L"] and s["k"] == s["k0"] + 1
+    for s in rej:
+        assert s["k"] == s["k0"] and s["eta_next"] < s["eta"]
+        assert np.array_equal(s["x"], s["x0"]) and np.array_equal(s["y"], s["y0"])
+        assert np.array_equal(s["xa"], s["xa0"]) and s["j"] == s["j0"]
+
+
+def _weighted_average_error(seen):
+    """Largest deviation of the averages from sum eta_k z_k / sum eta_k over each epoch."""
+    worst, ep = 0.0, []
+    for s in seen:
+        if not s["acc"]:
+            continue
+        if s["j"] == 1:
+            ep = []
+        ep.append(s)
+        w = np.array([e["eta"] for e in ep])
+        xs = np.average(np.array([e["x"] for e in ep]), axis=0, weights=w)
+        ys = np.average(np.array([e["y"] for e in ep]), axis=0, weights=w)
+        worst = max(worst, np.max(np.abs(s["xa"] - xs)) / (1 + np.max(np.abs(xs))),
+                    np.max(np.abs(s["ya"] - ys)) / (1 + np.max(np.abs(ys))))
+    return worst
+
+
+def test_adaptive_averages_are_step_weighted(monkeypatch):
+    P = _adaptive_problem()
+    _, seen = _watch_attempts(monkeypatch, P, _opts(step_mode=O.STEP_ADAPTIVE, tol=1e-8))
+    assert len({round(s["eta"], 12) for s in seen}) > 5  # the step really varies
+    assert _weighted_average_error(seen) <= 1e-12
+
+
+def test_planted_uniform_average_in_adaptive_mode_is_caught(monkeypatch):
+    """The mistake: keep the fixed-step uniform mean while eta varies."""
+    P = _adaptive_problem()
+    real = O.inner_step
+
+    def uniform_avg(Pi, st, oo):
+        xa, ya, j0 = st.x_avg.copy(), st.y_avg.copy(), st.j
+        real(Pi, st, oo)
+        if st.last_accepted:
+            base_x, base_y = (xa, ya) if j0 > 0 else (np.zeros_like(xa), np.zeros_like(ya))
+            st.x_avg = base_x + (st.x - base_x) / st.j
+            st.y_avg = base_y + (st.y - base_y) / st.j
+
+    monkeypatch.setattr(O, "inner_step", uniform_avg)
+    _, seen = _watch_attempts(monkeypatch, P, _opts(step_mode=O.STEP_ADAPTIVE, tol=1e-8, max_iter=600))
+    assert _weighted_average_error(seen) > 1e-6
+
+
+def test_adaptive_step_cuts_iterations_on_a_portfolio_qp():
+    """The reason the rule exists: on a portfolio instance it reaches 1e-4 in fewer iterations."""
+    from paper_2405_16160_b300 import workloads as W
+    P = O.problem_from_instance(W.portfolio(0, 1).to_instance())
+    fixed = O.solve(P, _opts(tol=1e-4))
+    adaptive = O.solve(P, _opts(tol=1e-4, step_mode=O.STEP_ADAPTIVE))
+    assert fixed.termination == adaptive.termination == O.SOLVED
+    assert adaptive.state.attempts < 0.7 * fixed.iterations
