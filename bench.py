@@ -6,9 +6,10 @@ One step = one complete qp_solve (set-up power iteration, every PDHCG
 iteration, relKKT evaluations, restarts, the final FP64 check) of the seeded
 n=1e6, m=5e5 sparse QP (Q diagonally dominant with ~9 nnz/row, A with 10
 uniform nnz/row) in mixed precision, with the problem already resident on
-the device and diagonally scaled as Section 4 prescribes (10 Ruiz steps and
-one Pock-Chambolle step, done once by qp_create).  The same solve in plain
-FP64 is timed beside it.  The solve measured end to end through the C ABI
+the device, diagonally scaled as Section 4 prescribes (10 Ruiz steps and
+one Pock-Chambolle step, done once by qp_create) and with the Section 4
+adaptive step size (``--step fixed``: eta = 1/(2||A||_2)).  The same solve in
+plain FP64 is timed beside it, and both again with the other step rule.  The solve measured end to end through the C ABI
 from host arrays (qp_create with the scaling and the host-to-device copies,
 qp_solve, qp_get_solution, qp_destroy) is reported as ``e2e``.
 
@@ -36,10 +37,13 @@ WORKLOAD = {"workload": "large sparse QP: n=1e6, m=5e5, Q = diag U[0.5,2] + mirr
                         "c ~ N(0,1), b = A x0 + U[0,1]",
             "n": 1_000_000, "m": 500_000, "seed": 0, "tol": 1e-4, "precision": "mixed",
             "scaling": "Section 4: 10 Ruiz steps + Pock-Chambolle on [[Q, A'], [A, 0]]",
+            "step": "Section 4 adaptive step size",
             "l2": "inputs larger than L2 (~470 MB resident working set vs 126 MB L2)"}
 METRIC = "time to 1e-4 rel. KKT (restarted PDHCG; FP32 data/iterates, FP64 reductions) vs plain FP64 GPU PDHCG"
-GOLDEN = os.path.join(ROOT, "tests", "golden",
-                      "sparse_dd_n1000000_m500000_seed0_scaled_trace.json")
+GOLDEN = {"fixed": os.path.join(ROOT, "tests", "golden",
+                                "sparse_dd_n1000000_m500000_seed0_scaled_trace.json"),
+          "adaptive": os.path.join(ROOT, "tests", "golden",
+                                   "sparse_dd_n1000000_m500000_seed0_scaled_adaptive_trace.json")}
 
 
 def _dist():
@@ -145,19 +149,21 @@ def cg_kernel_bytes(nnz_q: int, n: int, launches: int, spmvs: int, cg_steps: int
     return spmvs * spmv + cg_steps * 8.0 * w * n + max(cg_steps - launches, 0) * 3.0 * w * n
 
 
-def mixed_solve_launches(chunks: int, power_iters: int, eval_freq: int) -> int:
+def mixed_solve_launches(chunks: int, power_iters: int, eval_freq: int,
+                         adaptive: bool = True) -> int:
     """Kernel launches of one mixed-precision qp_solve on an instance without
     long rows (each SpMV is then one launch).
 
     set-up: k_init_vectors; cache refresh (k_materialize, A x_a, k_shift_rhs,
     A dx, A'y, Q x, k_prepare); power iteration (k_pow_start, 3 per step,
     k_setup_finish); the first evaluation (k_materialize, 4 SpMVs, k_kkt_n,
-    k_kkt_m, k_control).  Per chunk: 3 per iteration (k_cg, k_dual, k_atv),
-    an evaluation (8), the restart kernels (3) and k_prepare.  At the end the
-    FP64 check: 2 conversions, the FP64 cache refresh (3 SpMVs, k_prepare)
-    and an FP64 evaluation (4 SpMVs, k_kkt_n, k_kkt_m, k_control)."""
+    k_kkt_m, k_control).  Per chunk: 3 per iteration (k_cg, k_dual, k_atv;
+    5 with the adaptive step: k_step and k_commit_m), an evaluation (8), the
+    restart kernels (3) and k_prepare.  At the end the FP64 check: 2
+    conversions, the FP64 cache refresh (3 SpMVs, k_prepare) and an FP64
+    evaluation (4 SpMVs, k_kkt_n, k_kkt_m, k_control)."""
     setup = 1 + 7 + (1 + 3 * power_iters + 1) + 8
-    chunk = 3 * eval_freq + 8 + 3 + 1
+    chunk = (5 if adaptive else 3) * eval_freq + 8 + 3 + 1
     final = 2 + 4 + 7
     return setup + chunks * chunk + final
 
@@ -179,15 +185,16 @@ def _profiled_traffic():
         else None
 
 
-def oracle_sample(inst, iters: int):
-    """The oracle as it stands: its solve (scaling, set-up, iterations with
-    the relKKT evaluations they contain) stopped after `iters` iterations.
-    Returns (setup_s, per_iter_s, cores), split at the end of the first
-    iteration; cores = process CPU time / wall time (numpy and scipy pick
+def oracle_sample(inst, iters: int, step: str = "adaptive"):
+    """The oracle as it stands: its solve (scaling, set-up, attempts with
+    the relKKT evaluations they contain) stopped after `iters` attempts.
+    Returns (setup_s, per_attempt_s, cores), split at the end of the first
+    attempt; cores = process CPU time / wall time (numpy and scipy pick
     their own thread counts)."""
     from oracle import pdhcg_oracle as O
     P = O.problem_from_instance(inst)
-    o = O.OracleOptions(tol=WORKLOAD["tol"], max_iter=iters, eval_freq=64, scale=True)
+    o = O.OracleOptions(tol=WORKLOAD["tol"], max_iter=iters, eval_freq=64, scale=True,
+                        step_mode=O.STEP_ADAPTIVE if step == "adaptive" else O.STEP_FIXED)
     stamps = []
     c0, t0 = time.process_time(), time.perf_counter()
     O.solve(P, o, step_hook=lambda st: stamps.append(time.perf_counter()))
@@ -196,9 +203,11 @@ def oracle_sample(inst, iters: int):
     return stamps[0] - t0 - per_it, per_it, round(cores, 1)
 
 
-def _oracle_iterations():
-    with open(GOLDEN) as f:
-        return int(json.load(f)["iterations"])
+def _oracle_iterations(step: str = "adaptive"):
+    """The oracle's own attempts (= iterations with the fixed step) to 1e-4."""
+    with open(GOLDEN[step]) as f:
+        g = json.load(f)
+    return int(g.get("attempts", g["iterations"]))
 
 
 def run_reference(args):
@@ -207,22 +216,23 @@ def run_reference(args):
         return 0
     from paper_2405_16160_b300 import workloads as W
     inst = W.sparse_dd(WORKLOAD["seed"], n=WORKLOAD["n"], m=WORKLOAD["m"])
-    n_iter = _oracle_iterations()
+    n_iter = _oracle_iterations(args.step)
     sample_iters = 8
     vals, cores = [], []
     for s in range(args.warmup + args.steps):
-        setup, per_it, c = oracle_sample(inst, sample_iters)
+        setup, per_it, c = oracle_sample(inst, sample_iters, args.step)
         if s >= args.warmup:
             vals.append(setup + per_it * n_iter)
             cores.append(c)
     v = statistics.mean(vals)
-    sample = (f"oracle scaling + set-up + {sample_iters} iterations per step on the full "
-              f"instance, scaled by the oracle's own iteration count to 1e-4 ({n_iter})")
+    sample = (f"oracle scaling + set-up + {sample_iters} attempts per step on the full "
+              f"instance, scaled by the oracle's own attempt count to 1e-4 ({n_iter}, "
+              f"{args.step} step)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": WORKLOAD,
+        "data": "synthetic", "config": dict(WORKLOAD, step=args.step),
         "cpu_baseline": {"value": v, "unit": "s", "cores": max(cores), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -263,8 +273,10 @@ def run_ours(args):
     inst = W.sparse_dd(WORKLOAD["seed"] + rank, n=WORKLOAD["n"], m=WORKLOAD["m"])
     tol = WORKLOAD["tol"]
     stream = torch.cuda.current_stream()
-    mixed = dict(tol=tol, precision=L.PREC_MIXED)
-    fp64 = dict(tol=tol, precision=L.PREC_FP64)
+    step = L.STEP_ADAPTIVE if args.step == "adaptive" else L.STEP_FIXED
+    other = L.STEP_FIXED if step == L.STEP_ADAPTIVE else L.STEP_ADAPTIVE
+    mixed = dict(tol=tol, precision=L.PREC_MIXED, step_mode=step)
+    fp64 = dict(tol=tol, precision=L.PREC_FP64, step_mode=step)
 
     # ---- device-resident solves (value): mixed precision, CUDA-graph replay
     solver = QPSolver(inst, scale=True)
@@ -281,6 +293,13 @@ def run_ours(args):
     trace_len = len(solver.trace())
     # the same solve in plain FP64 (the ratio the metric asks for)
     infos64, times64 = _timed_solves(solver, max(1, args.steps // 2), stream, **fp64)
+    # both again with the other step rule
+    oth = {}
+    for name, opts in (("mixed", mixed), ("fp64", fp64)):
+        o2 = dict(opts, step_mode=other)
+        solver.solve(**o2)
+        inf2, t2 = _timed_solves(solver, max(1, args.steps // 4), stream, **o2)
+        oth[name] = (statistics.mean(t2), inf2[-1])
     # the dominant kernel, timed launch by launch with CUDA events on its stream
     kinfos, _ = _timed_solves(solver, max(1, args.steps // 2), stream, kernel_timing=1, **mixed)
     solver.close()
@@ -319,26 +338,34 @@ def run_ours(args):
     steps_per_launch = sum(i["cg_kernel_spmvs"] for i in kinfos) / max(launches, 1)
     if traffic is not None:
         traffic *= steps_per_launch
-    gpu_launches = args.steps * mixed_solve_launches(trace_len, 30, 64)
+    gpu_launches = args.steps * mixed_solve_launches(trace_len, 30, 64,
+                                                     step == L.STEP_ADAPTIVE)
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        setup_s, per_it, cores = oracle_sample(inst, 64)
-        n_iter = _oracle_iterations()
+        setup_s, per_it, cores = oracle_sample(inst, 64, args.step)
+        n_iter = _oracle_iterations(args.step)
         cpu = {"value": setup_s + per_it * n_iter, "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": f"oracle scaling + set-up + 64 PDHCG iterations of the same instance "
-                         f"({setup_s + 64 * per_it:.1f} s), scaled by the oracle's iteration "
-                         f"count to 1e-4 ({n_iter})"}
+               "sample": f"oracle scaling + set-up + 64 PDHCG attempts of the same instance "
+                         f"({setup_s + 64 * per_it:.1f} s), scaled by the oracle's attempt "
+                         f"count to 1e-4 ({n_iter}, {args.step} step)"}
     out = {
         "metric": METRIC, "value": per_solve, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 reductions and scalars)",
         "data": "synthetic",
-        "config": dict(WORKLOAD, iterations=info["iterations"], cg_steps=info["cg_steps"],
+        "config": dict(WORKLOAD, step=args.step, iterations=info["iterations"],
+                       attempts=info["attempts"], cg_steps=info["cg_steps"],
                        restarts=info["restarts"], relkkt_fp64_check=info["check_relkkt"],
                        refine_iterations=info["refine_iterations"],
                        fp64_time_s=per_solve64, fp64_iterations=infos64[-1]["iterations"],
+                       fp64_attempts=infos64[-1]["attempts"],
                        speedup_vs_fp64=per_solve64 / per_solve,
+                       other_step=("fixed" if args.step == "adaptive" else "adaptive"),
+                       other_step_mixed_s=oth["mixed"][0],
+                       other_step_mixed_attempts=oth["mixed"][1]["attempts"],
+                       other_step_fp64_s=oth["fp64"][0],
+                       other_step_fp64_attempts=oth["fp64"][1]["attempts"],
                        parallelism=f"replicas x{ws}"),
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
@@ -403,10 +430,12 @@ def run_batch_bench(args):
     B.build()
     insts = W.portfolio_batch(BATCH_WORKLOAD["seed"] + rank, BATCH_WORKLOAD["count"])
     tol = BATCH_WORKLOAD["tol"]
+    step = L.STEP_ADAPTIVE if args.step == "adaptive" else L.STEP_FIXED
+    other = L.STEP_FIXED if step == L.STEP_ADAPTIVE else L.STEP_ADAPTIVE
     stream = torch.cuda.current_stream()
     bt = QPBatch(insts)
     for _ in range(args.warmup):
-        bt.solve(tol=tol, precision=L.PREC_MIXED)
+        bt.solve(tol=tol, precision=L.PREC_MIXED, step_mode=step)
     with ClockSampler(local) as clocks:
         _barrier(ws)
         torch.cuda.synchronize()
@@ -415,15 +444,17 @@ def run_batch_bench(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            kms.append(bt.solve(tol=tol, precision=L.PREC_MIXED))
+            kms.append(bt.solve(tol=tol, precision=L.PREC_MIXED, step_mode=step))
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
         torch.cuda.synchronize()
         _barrier(ws)
     res = bt.results()
-    fp64_ms = bt.solve(tol=tol, precision=L.PREC_FP64)
+    fp64_ms = bt.solve(tol=tol, precision=L.PREC_FP64, step_mode=step)
     res64 = bt.results()
+    other_ms = bt.solve(tol=tol, precision=L.PREC_MIXED, step_mode=other)
+    res_other = bt.results()
     bt.close()
     value = _max_over_ranks(statistics.mean(times), ws)
     # plain FP64 GPU PDHCG (the single-QP path), one instance at a time, on a sample
@@ -431,10 +462,10 @@ def run_batch_bench(args):
     single = []
     for q in sample:
         with QPSolver(q.to_instance()) as s:
-            s.solve(tol=tol)
+            s.solve(tol=tol, step_mode=step)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s.solve(tol=tol)
+            s.solve(tol=tol, step_mode=step)
             torch.cuda.synchronize()
             single.append(time.perf_counter() - t0)
     single_total = statistics.mean(single) * len(insts)
@@ -444,7 +475,7 @@ def run_batch_bench(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with QPBatch(insts) as b2:
-            b2.solve(tol=tol, precision=L.PREC_MIXED)
+            b2.solve(tol=tol, precision=L.PREC_MIXED, step_mode=step)
             b2.results()
             b2.solution()
         torch.cuda.synchronize()
@@ -462,8 +493,10 @@ def run_batch_bench(args):
     if ws == 1 and not args.no_cpu_baseline:
         from oracle import pdhcg_oracle as O
         c0, t0 = time.process_time(), time.perf_counter()
+        ostep = O.STEP_ADAPTIVE if args.step == "adaptive" else O.STEP_FIXED
         for q in insts[:8]:
-            O.solve(O.problem_from_instance(q.to_instance()), O.OracleOptions(tol=tol))
+            O.solve(O.problem_from_instance(q.to_instance()),
+                    O.OracleOptions(tol=tol, step_mode=ostep))
         wall = time.perf_counter() - t0
         cpu = {"value": wall / 8 * len(insts), "unit": "s",
                "cores": round((time.process_time() - c0) / wall, 1), "kind": "oracle",
@@ -475,8 +508,13 @@ def run_batch_bench(args):
         "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 vectors and reductions)",
         "data": "synthetic",
-        "config": dict(BATCH_WORKLOAD, solved=int(sum(r["termination"] == 0 for r in res)),
+        "config": dict(BATCH_WORKLOAD, step=args.step,
+                       solved=int(sum(r["termination"] == 0 for r in res)),
                        iterations_mean=float(it.mean()), iterations_max=int(it.max()),
+                       attempts_mean=float(np.mean([r["attempts"] for r in res])),
+                       other_step_s=other_ms / 1e3,
+                       other_step_iterations_mean=float(np.mean(
+                           [r["iterations"] for r in res_other])),
                        fp64_batch_s=fp64_ms / 1e3,
                        fp64_solved=int(sum(r["termination"] == 0 for r in res64)),
                        single_qp_fp64_s=single_total,
@@ -527,13 +565,14 @@ def run_warmstart_bench(args):
 
     B.build()
     n, tol = WS_WORKLOAD["n"], WS_WORKLOAD["tol"]
+    step = L.STEP_ADAPTIVE if args.step == "adaptive" else L.STEP_FIXED
     # training data: solver solutions, generated and solved in chunks
     t0 = time.perf_counter()
     feats, targs, omegas, gen_iters = [], [], [], []
     chunk = 1000
     for s0 in range(1, WS_WORKLOAD["train"] + 1, chunk):
         insts = W.portfolio_family(0, seeds=range(s0, s0 + chunk), n=n)
-        res, xs, ys = WS.solve_family(insts, tol=tol, precision=L.PREC_MIXED)
+        res, xs, ys = WS.solve_family(insts, tol=tol, precision=L.PREC_MIXED, step_mode=step)
         keep = [i for i, r in enumerate(res) if r["termination"] == L.TERM_SOLVED]
         feats.append(WS.features([insts[i] for i in keep]))
         targs.append(WS.targets([xs[i] for i in keep], [ys[i] for i in keep]))
@@ -556,10 +595,10 @@ def run_warmstart_bench(args):
     for step in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        cold, _, _ = WS.solve_family(test, tol=tol, precision=L.PREC_MIXED)
+        cold, _, _ = WS.solve_family(test, tol=tol, precision=L.PREC_MIXED, step_mode=step)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        hot, _, _, n_fb = model.solve(test, tol=tol, precision=L.PREC_MIXED)
+        hot, _, _, n_fb = model.solve(test, tol=tol, precision=L.PREC_MIXED, step_mode=step)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         if step >= args.warmup:
@@ -575,7 +614,7 @@ def run_warmstart_bench(args):
         "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 vectors and reductions)",
         "data": "synthetic",
-        "config": dict(WS_WORKLOAD, cold_start_s=statistics.mean(cold_t),
+        "config": dict(WS_WORKLOAD, step=args.step, cold_start_s=statistics.mean(cold_t),
                        speedup_vs_cold=statistics.mean(cold_t) / value,
                        iterations_cold=it_c, iterations_warm=it_w,
                        iteration_ratio=it_w / it_c, fallbacks=n_fb,
@@ -607,6 +646,8 @@ def main():
     ap.add_argument("--workload", choices=["sparse_dd", "portfolio_batch", "learned_warm_start"],
                     default="sparse_dd")
     ap.add_argument("--train-epochs", type=int, default=30)
+    ap.add_argument("--step", choices=["adaptive", "fixed"], default="adaptive",
+                    help="step-size rule (Section 4 adaptive, or eta = 1/(2||A||_2))")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -28,7 +28,7 @@
 extern "C" {
 #endif
 
-#define PDHCG_ABI_VERSION 1
+#define PDHCG_ABI_VERSION 2
 
 typedef struct qp_handle qp_handle;
 
@@ -60,6 +60,17 @@ enum { QP_CG_ADAPTIVE = 0, QP_CG_FIXED = 1 };
  * and, if refine is set and that misses tol, continuing in FP64. */
 enum { QP_PREC_FP64 = 0, QP_PREC_MIXED = 1 };
 enum { QP_RESTART_ADAPTIVE = 0, QP_RESTART_NONE = 2 };
+/* Step size.  FIXED: eta = 1/(2||A||_2) for the whole solve (Section 3.2).
+ * ADAPTIVE: the adaptive step-size rule of Section 4.  Every step is an
+ * attempt from z = (x, y) with the current eta to a trial point z' (the CG
+ * x-step and the dual step); with dz = z' - z, ||dz||_w^2 = omega ||dx||^2 +
+ * ||dy||^2 / omega and L = ||dz||_w^2 / (2 |dy' A dx| + dx' Q dx), the attempt
+ * is accepted when eta <= L, else z is kept.  Either way the next eta is
+ * min((1 - (a+1)^-0.3) L, (1 + (a+1)^-0.6) eta), a = attempts so far (the
+ * PDLP update the paper's rule builds on).  Averages become step-weighted
+ * (sum eta_k z_k / sum eta_k); eval_freq, max_iter and qp_iterate count
+ * attempts (the same as iterations with the fixed step). */
+enum { QP_STEP_FIXED = 0, QP_STEP_ADAPTIVE = 1 };
 
 /* qp_create flags */
 #define QP_CREATE_CHECK_SYMMETRY 1u /* reject Q unless |Q - Q'| <= 1e-12 max|Q| entrywise */
@@ -118,7 +129,10 @@ typedef struct {
   uint32_t debug_flags;       /* QP_DEBUG_* fault injection, 0 by default */
   int32_t precision;          /* QP_PREC_FP64 (default) or QP_PREC_MIXED */
   int32_t refine;             /* mixed: continue in FP64 if the FP64 check misses tol; default 1 */
-  int64_t reserved[7];
+  int32_t step_mode;          /* QP_STEP_FIXED (eta = 1/(2||A||_2), Section 3.2; default) or
+                                 QP_STEP_ADAPTIVE (Section 4 adaptive step size, see below) */
+  int32_t pad1;
+  int64_t reserved[6];
 } qp_options;
 
 /* Result of a solve (also returned by qp_get_stats). */
@@ -145,6 +159,7 @@ typedef struct {
   int64_t refine_iterations;  /* mixed: iterations of the FP64 refinement phase */
   double mixed_relkkt;        /* mixed: relKKT at the end of the binary32 phase */
   double check_relkkt;        /* mixed: relKKT of that iterate with the binary64 data */
+  int64_t attempts;           /* steps tried: iterations + rejected adaptive steps */
 } qp_info;
 
 /* Scalar part of the iteration state (for checkpoint / resume and parity). */
@@ -158,6 +173,8 @@ typedef struct {
   int64_t k_total;            /* inner iterations so far */
   int64_t restarts;
   int64_t cg_total;
+  int64_t attempts;           /* steps tried so far (= k_total with the fixed step) */
+  double weight_sum;          /* adaptive step: sum of the accepted etas of this epoch */
 } qp_state_scalars;
 
 /* Host vectors of the iteration state; NULL entries are skipped on get and
@@ -257,7 +274,8 @@ qp_status qp_set_state(qp_handle* h, const qp_state_vectors* v, const qp_state_s
  * Run exactly `iters` inner PDHCG iterations (Algorithm 1 loop body: CG
  * primal step, projected dual step, averages) from the current state, with
  * no relKKT evaluation, restart or termination test.  Only o's CG settings,
- * precision and debug_flags are used.  qp_set_state fills both precisions;
+ * step_mode, precision and debug_flags are used; with QP_STEP_ADAPTIVE each
+ * of the `iters` is one attempt (accepted or rejected).  qp_set_state fills both precisions;
  * qp_get_state and qp_evaluate then read the precision last iterated.
  */
 qp_status qp_iterate(qp_handle* h, const qp_options* o, int64_t iters);
@@ -363,6 +381,7 @@ typedef struct {
   int64_t iterations, cg_steps, restarts;
   double r_primal, r_dual, r_gap, relkkt, primal_obj, dual_obj;  /* FP64 data */
   double eta, omega, norm_A;
+  int64_t attempts;           /* steps tried (adaptive step: iterations + rejections) */
 } qp_instance_result;
 
 /* Copy count instances to the current device.  Errors: QP_ERR_INVALID_ARG

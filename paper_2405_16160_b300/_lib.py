@@ -18,6 +18,7 @@ TERM_NONE, TERM_SOLVED, TERM_ITER_LIMIT, TERM_TIME_LIMIT, TERM_NUMERICAL = -1, 0
 CG_ADAPTIVE, CG_FIXED = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 RESTART_ADAPTIVE, RESTART_NONE = 0, 2
+STEP_FIXED, STEP_ADAPTIVE = 0, 1
 CREATE_CHECK_SYMMETRY = 1
 CREATE_SCALE = 2
 DEBUG_BARRIER_NEVER_RELEASES = 1
@@ -33,7 +34,8 @@ class QPOptionsC(Structure):
         ("theta_pw", c_double), ("eps_zero", c_double), ("primal_weight_update", c_int32),
         ("warm_start", c_int32), ("omega0", c_double), ("eta", c_double),
         ("kernel_timing", c_int32), ("debug_flags", c_uint32), ("precision", c_int32),
-        ("refine", c_int32), ("reserved", c_int64 * 7),
+        ("refine", c_int32), ("step_mode", c_int32), ("pad1", c_int32),
+        ("reserved", c_int64 * 6),
     ]
 
 
@@ -48,6 +50,7 @@ class QPInfoC(Structure):
         ("cg_kernel_spmvs", c_int64), ("device_error", c_int32), ("cooperative", c_int32),
         ("precision", c_int32), ("pad0", c_int32), ("mixed_iterations", c_int64),
         ("refine_iterations", c_int64), ("mixed_relkkt", c_double), ("check_relkkt", c_double),
+        ("attempts", c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -59,6 +62,7 @@ class QPStateScalarsC(Structure):
         ("eta", c_double), ("omega", c_double), ("eps", c_double), ("relkkt_last", c_double),
         ("kkt_anchor", c_double), ("kkt_prev_cand", c_double), ("j", c_int64),
         ("k_total", c_int64), ("restarts", c_int64), ("cg_total", c_int64),
+        ("attempts", c_int64), ("weight_sum", c_double),
     ]
 
 
@@ -85,7 +89,7 @@ class QPInstanceResultC(Structure):
                 ("cg_steps", c_int64), ("restarts", c_int64), ("r_primal", c_double),
                 ("r_dual", c_double), ("r_gap", c_double), ("relkkt", c_double),
                 ("primal_obj", c_double), ("dual_obj", c_double), ("eta", c_double),
-                ("omega", c_double), ("norm_A", c_double)]
+                ("omega", c_double), ("norm_A", c_double), ("attempts", c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -65,11 +65,13 @@ struct BatchBin {
   std::vector<int32_t> h_order;
   int32_t* order = nullptr;  // instance ids (device)
   int max_n = 1, max_m = 1, max_k = 1;
-  size_t block_doubles = 0;  // vector space of one block
-  size_t smem = 0;           // dynamic shared memory per block (0: global workspace)
+  // vector space of one block and its dynamic shared memory (0: global
+  // workspace), for the fixed [0] and the adaptive [1] step size
+  size_t block_doubles[2] = {0, 0};
+  size_t smem[2] = {0, 0};
   int threads = 128;
   double* ws = nullptr;      // global workspace when the vectors do not fit shared memory
-  size_t ws_blocks = 0;
+  size_t ws_doubles = 0;     // capacity of ws
   int* next = nullptr;       // work-queue counter
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
@@ -162,26 +164,29 @@ bool finite_all(const double* v, size_t n) {
 template <class V, int NT>
 qp_status launch_batch_nt(qp_batch* h, BatchBin& bin, BatchData<V> B) {
   auto kern = k_batch<V, NT>;
-  BCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bin.smem)));
+  const int ad = B.opt.step_mode == kStepAdaptive ? 1 : 0;
+  const size_t smem = bin.smem[ad], bd = bin.block_doubles[ad];
+  BCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   int occ = 0;
-  BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, bin.smem));
+  BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
   if (occ < 1) {
     berror("batch kernel with %d threads and %zu bytes of shared memory cannot be resident", NT,
-           bin.smem);
+           smem);
     return QP_ERR_INVALID_ARG;
   }
   const int grid = std::max(1, std::min(B.count, occ * h->num_sms));
-  if (bin.smem == 0) {
-    if (bin.ws_blocks < size_t(grid)) {
+  B.adaptive = ad;
+  if (smem == 0) {
+    if (bin.ws_doubles < size_t(grid) * bd) {
       void* p = nullptr;
-      BTRY(balloc(h, &p, size_t(grid) * bin.block_doubles * sizeof(double)));
+      BTRY(balloc(h, &p, size_t(grid) * bd * sizeof(double)));
       bin.ws = static_cast<double*>(p);
-      bin.ws_blocks = size_t(grid);
+      bin.ws_doubles = size_t(grid) * bd;
     }
     B.ws = bin.ws;
-    B.ws_stride = (long long)bin.block_doubles;
+    B.ws_stride = (long long)bd;
   }
-  kern<<<grid, NT, bin.smem, bin.stream>>>(B);
+  kern<<<grid, NT, smem, bin.stream>>>(B);
   BCUDA(cudaGetLastError());
   return QP_OK;
 }
@@ -247,6 +252,7 @@ BatchData<V> batch_data(qp_batch* h, const BatchBin& bin, const V* F, const V* q
   d.m_eq = 0;
   d.debug_flags = 0;
   d.barrier_timeout_ms = 0;
+  d.step_mode = o->step_mode;
   B.power_iters = o->power_iters;
   B.eval_freq = o->eval_freq;
   B.max_n = bin.max_n;
@@ -296,7 +302,8 @@ qp_status validate_batch_options(const qp_options* o) {
       (o->restart_mode != QP_RESTART_ADAPTIVE && o->restart_mode != QP_RESTART_NONE) ||
       o->power_iters < 1 || o->power_iters > 100000 || !(o->eps_zero >= 0.0) ||
       !(o->theta_pw >= 0.0 && o->theta_pw <= 1.0) ||
-      (o->precision != QP_PREC_FP64 && o->precision != QP_PREC_MIXED)) {
+      (o->precision != QP_PREC_FP64 && o->precision != QP_PREC_MIXED) ||
+      (o->step_mode != QP_STEP_FIXED && o->step_mode != QP_STEP_ADAPTIVE)) {
     berror("invalid option value");
     return QP_ERR_INVALID_ARG;
   }
@@ -394,9 +401,11 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
       bin.max_m = std::max(bin.max_m, desc[size_t(id)].m);
       bin.max_k = std::max(bin.max_k, desc[size_t(id)].k);
     }
-    bin.block_doubles = batch_block_doubles(bin.max_n, bin.max_m, bin.max_k, true);
-    const size_t need = bin.block_doubles * sizeof(double);
-    bin.smem = need + static_smem <= size_t(smem_optin) ? need : 0;
+    for (int ad = 0; ad < 2; ++ad) {
+      bin.block_doubles[ad] = batch_block_doubles(bin.max_n, bin.max_m, bin.max_k, true, ad != 0);
+      const size_t need = bin.block_doubles[ad] * sizeof(double);
+      bin.smem[ad] = need + static_smem <= size_t(smem_optin) ? need : 0;
+    }
     bin.threads = default_threads(bin.max_n);
     BCUDA(cudaStreamCreateWithFlags(&bin.stream, cudaStreamNonBlocking));
     BCUDA(cudaEventCreateWithFlags(&bin.done, cudaEventDisableTiming));
@@ -541,6 +550,7 @@ qp_status qp_batch_results(const qp_batch* h, qp_instance_result* out) {
     o.eta = r.eta;
     o.omega = r.omega;
     o.norm_A = r.norm_A;
+    o.attempts = r.attempts;
   }
   return QP_OK;
 }

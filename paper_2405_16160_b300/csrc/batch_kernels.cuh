@@ -46,6 +46,7 @@ struct BatchResult {
   long long iterations, cg_steps, restarts;
   double kkt[6];  // r_primal, r_dual, r_gap, relKKT, primal_obj, dual_obj
   double eta, omega, norm_A;
+  long long attempts;
 };
 
 template <class V>
@@ -81,13 +82,18 @@ struct BatchData {
   int max_n, max_m, max_k;
   double* ws;          // per-block vector space in global memory, or null for shared memory
   long long ws_stride;  // doubles per block in ws
+  int adaptive;         // Section 4 adaptive step size (its vectors are in the layout)
 };
 
 // Vector space of one block, in doubles: shared memory when it fits, else
 // a slice of a global workspace (same layout, reached through L1).  FP64
-// vectors, plus (shadow) copies in the value type when that is FP32.
-inline size_t batch_block_doubles(int max_n, int max_m, int max_k, bool shadow) {
-  const size_t d = 9 * size_t(max_n) + 6 * size_t(max_m) + size_t(max_k) + 8;
+// vectors, plus (shadow) copies in the value type when that is FP32; the
+// adaptive step size adds the start of the attempt (x, Q x) and the trial
+// (y, A x).
+inline size_t batch_block_doubles(int max_n, int max_m, int max_k, bool shadow,
+                                  bool adaptive) {
+  const size_t a = adaptive ? 2 * size_t(max_n) + 2 * size_t(max_m) : 0;
+  const size_t d = 9 * size_t(max_n) + 6 * size_t(max_m) + size_t(max_k) + 8 + a;
   const size_t f = shadow ? 2 * size_t(max_n) + 2 * size_t(max_m) + size_t(max_k) + 8 : 0;
   return d + (f + 1) / 2;
 }
@@ -132,13 +138,21 @@ __device__ void cta_spmv(const LocalCsr<V>& M, const V* v, double* out) {
 
 // The dual step fused into A x+ (Algorithm 1 y-update): whoever forms row i
 // of A x+ also updates y_i = proj(y_i + sigma(2 (A x+)_i - (A x)_i - b_i)),
-// its value-type copy, the A x cache and the running average.
+// its value-type copy, the A x cache and the running average.  With the
+// adaptive step size (yn != nullptr) the step is a trial: y+ and A x+ go to
+// yn and axn and nothing else changes.
 template <class V, int NT>
 __device__ void cta_dual(const LocalCsr<V>& A, const V* xv, const double* b, int m_eq,
-                         double sigma, double inv_j, double* y, V* yv, double* ax, double* ya) {
+                         double sigma, double inv_j, double* y, V* yv, double* ax, double* ya,
+                         double* yn_out = nullptr, double* axn = nullptr) {
   auto row = [&](int i, double s) {
     double yn = y[i] + sigma * (2.0 * s - ax[i] - b[i]);
     if (i >= m_eq && yn < 0.0) yn = 0.0;
+    if (yn_out) {
+      yn_out[i] = yn;
+      axn[i] = s;
+      return;
+    }
     y[i] = yn;
     yv[i] = V(yn);
     ax[i] = s;
@@ -257,7 +271,12 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
   double* ax = y0 + B.max_m;
   double* axe = ax + B.max_m;
   double* axa = axe + B.max_m;
-  double* t = axa + B.max_m;
+  // adaptive step size: the attempt's start (x, Q x) and trial (y, A x)
+  double* xs = axa + B.max_m;
+  double* qxs = B.adaptive ? xs + B.max_n : xs;
+  double* yn = B.adaptive ? qxs + B.max_n : xs;
+  double* axn = B.adaptive ? yn + B.max_m : xs;
+  double* t = B.adaptive ? axn + B.max_m : xs;
   // value-type copies read by the products (the FP64 vectors themselves
   // when V is double)
   V* pv = reinterpret_cast<V*>(p);
@@ -410,11 +429,21 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
     return cta_sum1<NT>(rr, red);
   };
 
+  // adaptive step size: (x, Q x) at the start of the next attempt
+  auto save_start = [&]() {
+    if (!B.adaptive) return;
+    for (int j = tid; j < n; j += NT) {
+      xs[j] = x[j];
+      qxs[j] = qx[j];
+    }
+  };
+
   evaluate(0);
   double rr0 = prepare();
+  save_start();
   const int efreq = B.eval_freq;
   while (running(&st)) {
-    for (int it = 0; it < efreq && running(&st) && st.k_total < st.opt.max_iter; ++it) {
+    for (int it = 0; it < efreq && running(&st) && st.attempts < st.opt.max_iter; ++it) {
       // ---- x-step: inexact CG on (Q + I/tau) x = x/tau - c - A'y (Section 2)
       const double tau = st.tau, inv_tau = 1.0 / tau;
       const int mode = st.opt.cg_mode, nfix = st.opt.cg_fixed_n, cgmax = st.opt.cg_max;
@@ -468,13 +497,61 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         break;
       }
       if (tid == 0) {
-        st.eps = eps;
+        st.attempts += 1;
         st.cg_total += steps;
         st.last_cg = steps;
-        st.k_total += 1;
-        st.j += 1;
+        if (B.adaptive) {
+          st.eps_try = eps;
+        } else {
+          st.eps = eps;
+          st.k_total += 1;
+          st.j += 1;
+        }
       }
       __syncthreads();
+      if (B.adaptive) {
+        // ---- trial y-step, the Section 4 step test, then commit or restore
+        cta_dual<V, NT>(A, xv, b, d.m_eq, st.sigma, 0.0, y, yv, ax, ya, yn, axn);
+        __syncthreads();
+        double a4[4] = {0.0, 0.0, 0.0, 0.0}, m1[1] = {0.0};
+        for (int j = tid; j < n; j += NT) {
+          const double dx = x[j] - xs[j];
+          a4[0] = fma(dx, dx, a4[0]);
+          a4[1] = fma(dx, qx[j] - qxs[j], a4[1]);
+        }
+        for (int i = tid; i < m; i += NT) {
+          const double dy = yn[i] - y[i];
+          a4[2] = fma(dy, dy, a4[2]);
+          a4[3] = fma(dy, axn[i] - ax[i], a4[3]);
+        }
+        cta_reduce<NT, 4, 0>(a4, m1, red);
+        if (tid == 0) step_decide(&st, a4[0], a4[1], a4[2], a4[3]);
+        __syncthreads();
+        if (st.accepted) {
+          const double w = st.avg_w;
+          for (int i = tid; i < m; i += NT) {
+            const double v = yn[i];
+            y[i] = v;
+            yv[i] = V(v);
+            ax[i] = axn[i];
+            ya[i] += (v - ya[i]) * w;
+          }
+          __syncthreads();
+          cta_spmv<V, NT>(At, yv, aty);
+          for (int j = tid; j < n; j += NT) xa[j] += (x[j] - xa[j]) * w;
+        } else {
+          for (int j = tid; j < n; j += NT) {
+            x[j] = xs[j];
+            qx[j] = qxs[j];
+            if constexpr (kShadow) xv[j] = V(xs[j]);
+          }
+        }
+        __syncthreads();
+        rr0 = prepare();
+        save_start();
+        __syncthreads();
+        continue;
+      }
       // ---- y-step fused into A x+, then A'y+, x~ and the next CG start
       const double inv_j = 1.0 / (double)st.j;
       cta_dual<V, NT>(A, xv, b, d.m_eq, st.sigma, inv_j, y, yv, ax, ya);
@@ -516,6 +593,8 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
     // exact Q x for the tracked cache, then the next CG start
     cta_qprod<V, NT>(F, qd, n, k, xv, tv, qx);
     rr0 = prepare();
+    save_start();
+    __syncthreads();
   }
 
   // ---- the returned iterate and its statistics
@@ -533,6 +612,7 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
     o.eta = st.eta;
     o.omega = st.omega;
     o.norm_A = st.norm_A;
+    o.attempts = st.attempts;
   }
   __syncthreads();
 }

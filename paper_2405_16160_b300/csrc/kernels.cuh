@@ -492,7 +492,8 @@ __device__ __forceinline__ void store_and_finish_dot(A acc, double* part, unsign
 //   [A] q = Qp + p/tau, p'q
 //   [B] x += a p, qx += a (q - p/tau), r -= a q, r'r
 //   [C] p = r + b p   (only when CG continues)
-// so each step costs one product with Q.  alpha, beta, the stop test and all
+// so each step costs one product with Q.  With the adaptive step size the
+// iteration counters wait for k_step's accept/reject decision.  alpha, beta, the stop test and all
 // dot products are FP64-accurate for both value types.  part holds
 // 2 * gridDim.x doubles.
 // Resident CG blocks of 512 threads per SM (register budget per thread =
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     k_cg(CsrT<T> Q, LongRows LQ, T* qseg, T* qlong, T* x, T* r, T* p, T* q, T* qx,
          const double* r0r0, double* part, DevState* st, GridBarrier* bar, int n) {
   using A = typename Acc<T>::type;
-  const bool active = running(st) && st->k_total < st->opt.max_iter;
+  const bool active = running(st) && st->attempts < st->opt.max_iter;
   if (!active) {
     if (blockIdx.x == 0 && threadIdx.x == 0) st->iter_active = 0;
     return;
@@ -515,6 +516,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
   const double tau = st->tau;
   const T inv_tau = T(1.0 / tau);
   const int mode = st->opt.cg_mode, nfix = st->opt.cg_fixed_n, cgmax = st->opt.cg_max;
+  const bool adaptive_step = st->opt.step_mode == kStepAdaptive;
   const int tmo = st->opt.barrier_timeout_ms;
   bool never_release = (st->opt.debug_flags & kDebugBarrierNeverReleases) != 0u;
   const double eps =
@@ -585,12 +587,17 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
       st->iter_active = 0;
     } else {
       st->iter_active = 1;
-      st->eps = eps;
+      st->attempts += 1;
       st->cg_total += steps;
       st->last_cg = steps;
       st->spmv_total += steps;
-      st->k_total += 1;
-      st->j += 1;
+      if (adaptive_step) {
+        st->eps_try = eps;  // kept by k_step if the attempt is accepted
+      } else {
+        st->eps = eps;
+        st->k_total += 1;
+        st->j += 1;
+      }
     }
   }
 }
@@ -601,15 +608,49 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
 // mixed path passes the displacement dx = x - x_a from the restart point x_a
 // as x, b - A x_a as b and A dx as the cache: the same step, but every FP32
 // quantity it gathers or subtracts is small near convergence.
+//
+// Adaptive step size (y_new != nullptr): the step is a trial.  y, its low
+// word, the A x cache and the average stay as they are; the trial y+ (and its
+// low word) and A x+ go to y_new, yn_lo, ax_new, and each block stores the
+// partial sums of ||y+ - y||^2 and (y+ - y)'(A x+ - A x) at part_step[2 * block]
+// for k_step's test; k_commit_m keeps them if the step is accepted.
 template <int G, class T>
 __global__ void __launch_bounds__(kBlock) k_dual(CsrT<T> A, const T* __restrict__ x,
                                                  const T* __restrict__ b, T* y, T* y_lo, T* ax,
-                                                 T* y_avg, T* ya_lo, const DevState* st) {
+                                                 T* y_avg, T* ya_lo, const DevState* st,
+                                                 T* y_new, T* yn_lo, T* ax_new,
+                                                 double* part_step) {
   if (!st->iter_active) return;
   const T sigma = T(st->sigma);
   const T inv_j = T(1.0 / (double)st->j);
   const bool first = st->j == 1;
   const int m_eq = st->opt.m_eq;
+  if (y_new) {
+    typename Acc<T>::type acc[2];
+    spmv_rows<G>(A, x, [&](int i, T s, bool lead) {
+      if (!lead) return;
+      const T da = s - ax[i];
+      T dy;
+      if constexpr (kSplit<T>) {
+        T hi = y[i], lo = y_lo[i];
+        split_add(hi, lo, sigma * (T(2) * s - ax[i] - b[i]));
+        if (i >= m_eq && hi < T(0)) hi = lo = T(0);
+        dy = (hi - y[i]) + (lo - y_lo[i]);
+        y_new[i] = hi;
+        yn_lo[i] = lo;
+      } else {
+        T yn = y[i] + sigma * (T(2) * s - ax[i] - b[i]);
+        if (i >= m_eq && yn < T(0)) yn = T(0);
+        dy = yn - y[i];
+        y_new[i] = yn;
+      }
+      ax_new[i] = s;
+      acc[0].add_prod(dy, dy);
+      acc[1].add_prod(dy, da);
+    });
+    block_reduce_ms<0, 2, T>(nullptr, acc, part_step + 2 * size_t(blockIdx.x));
+    return;
+  }
   spmv_rows<G>(A, x, [&](int i, T s, bool lead) {
     if (lead) {
       if constexpr (kSplit<T>) {
@@ -641,42 +682,147 @@ __global__ void __launch_bounds__(kBlock) k_dual(CsrT<T> A, const T* __restrict_
 // A' y+ over the explicit transpose, fused with the running average of x and
 // with the next CG's start: r0 = p0 = -(qx + c + A'y+) and r0'r0 partials.
 // (The mixed path averages the displacement dx, see k_dual.)
+//
+// Adaptive step size (x_save != nullptr): after an accepted step the average
+// takes the step weight of k_step and (x, Q x) are saved as the start of the
+// next attempt; after a rejected one x and Q x go back to the saved start and
+// the CG start is formed from the unchanged A'y, with no product.
 template <int G, class T>
 __global__ void __launch_bounds__(kBlock) k_atv(CsrT<T> At, const T* __restrict__ y, T* aty,
-                                                const T* __restrict__ x, T* x_avg,
-                                                const T* __restrict__ qx,
+                                                T* x, T* x_avg, T* qx,
                                                 const T* __restrict__ c, T* r, T* p,
                                                 double* part_r0, unsigned int* ticket,
-                                                const DevState* st) {
+                                                const DevState* st, T* x_save, T* qx_save) {
   if (!st->iter_active) return;
-  const T inv_j = T(1.0 / (double)st->j);
+  const bool adaptive = x_save != nullptr;
   typename Acc<T>::type acc;
-  spmv_rows<G>(At, y, [&](int i, T s, bool lead) {
-    if (lead) {
-      aty[i] = s;
-      x_avg[i] += (x[i] - x_avg[i]) * inv_j;
-      const T ri = -(qx[i] + c[i] + s);
+  if (adaptive && !st->accepted) {
+    for (long long i = grid_tid(); i < At.rows; i += grid_threads()) {
+      const T xs = x_save[i], qs = qx_save[i];
+      x[i] = xs;
+      qx[i] = qs;
+      const T ri = -(qs + c[i] + aty[i]);
       r[i] = ri;
       p[i] = ri;
       acc.add_prod(ri, ri);
+    }
+    store_and_finish_dot(acc, part_r0, ticket);
+    return;
+  }
+  const T w = adaptive ? T(st->avg_w) : T(1.0 / (double)st->j);
+  spmv_rows<G>(At, y, [&](int i, T s, bool lead) {
+    if (lead) {
+      aty[i] = s;
+      const T xi = x[i], qxi = qx[i];
+      x_avg[i] += (xi - x_avg[i]) * w;
+      const T ri = -(qxi + c[i] + s);
+      r[i] = ri;
+      p[i] = ri;
+      acc.add_prod(ri, ri);
+      if (adaptive) {
+        x_save[i] = xi;
+        qx_save[i] = qxi;
+      }
     }
   });
   store_and_finish_dot(acc, part_r0, ticket);
 }
 
+// Adaptive step size, after k_dual: per-block partials of ||x+ - x||^2 and
+// (x+ - x)'(Q x+ - Q x) from the saved start of the attempt (x_save, qx_save)
+// and the tracked Q x, then the last block to finish combines them with
+// k_dual's m-side partials (stride 2, gm blocks) in a fixed order and takes
+// the Section 4 step decision (step_decide).
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_step(const T* __restrict__ x,
+                                                 const T* __restrict__ x_save,
+                                                 const T* __restrict__ qx,
+                                                 const T* __restrict__ qx_save, int n,
+                                                 double* part_n, const double* part_m, int gm,
+                                                 unsigned int* ticket, DevState* st) {
+  if (!st->iter_active) return;
+  typename Acc<T>::type acc[2];
+  for (long long i = grid_tid(); i < n; i += grid_threads()) {
+    const T dx = x[i] - x_save[i], dq = qx[i] - qx_save[i];
+    acc[0].add_prod(dx, dx);
+    acc[1].add_prod(dx, dq);
+  }
+  block_reduce_ms<0, 2, T>(nullptr, acc, part_n + 2 * size_t(blockIdx.x));
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x < 32) {
+    __threadfence();
+    const double dx2 = warp_reduce_partials(part_n, gridDim.x, 2, false);
+    const double dxq = warp_reduce_partials(part_n + 1, gridDim.x, 2, false);
+    const double dy2 = warp_reduce_partials(part_m, gm, 2, false);
+    const double cross = warp_reduce_partials(part_m + 1, gm, 2, false);
+    if (threadIdx.x == 0) {
+      step_decide(st, dx2, dxq, dy2, cross);
+      *ticket = 0u;
+      __threadfence();
+    }
+  }
+}
+
+// Adaptive step size, after k_step: an accepted trial becomes y (with its low
+// word) and the A x cache, and enters the running average of y with the step
+// weight; a rejected one is dropped.
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_commit_m(T* y, T* y_lo, const T* __restrict__ y_new,
+                                                     const T* __restrict__ yn_lo, T* ax,
+                                                     const T* __restrict__ ax_new, T* y_avg,
+                                                     T* ya_lo, int m, const DevState* st) {
+  if (!st->iter_active || !st->accepted) return;
+  const T w = T(st->avg_w);
+  const bool first = st->j == 1;
+  for (long long i = grid_tid(); i < m; i += grid_threads()) {
+    ax[i] = ax_new[i];
+    if constexpr (kSplit<T>) {
+      const T hi = y_new[i], lo = yn_lo[i];
+      y[i] = hi;
+      y_lo[i] = lo;
+      T ah = hi, al = lo;
+      if (!first) {
+        ah = y_avg[i];
+        al = ya_lo[i];
+        split_add(ah, al, ((hi - ah) + (lo - al)) * w);
+      }
+      y_avg[i] = ah;
+      ya_lo[i] = al;
+    } else {
+      const T yn = y_new[i];
+      y[i] = yn;
+      y_avg[i] += (yn - y_avg[i]) * w;
+    }
+  }
+}
+
 // r0 = p0 = -(qx + c + A'y) and r0'r0 partials, for the first CG after a
 // set-up, an evaluation or a restart.  Launched with the grid of k_atv.
+// With the adaptive step size (x_save != nullptr) it also saves (x, Q x) as
+// the start of the next attempt.
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_prepare(const T* __restrict__ qx,
                                                     const T* __restrict__ c,
                                                     const T* __restrict__ aty, T* r, T* p, int n,
-                                                    double* part_r0, unsigned int* ticket) {
+                                                    double* part_r0, unsigned int* ticket,
+                                                    const T* __restrict__ x, T* x_save,
+                                                    T* qx_save) {
   typename Acc<T>::type acc;
   for (long long i = grid_tid(); i < n; i += grid_threads()) {
-    const T ri = -(qx[i] + c[i] + aty[i]);
+    const T qxi = qx[i];
+    const T ri = -(qxi + c[i] + aty[i]);
     r[i] = ri;
     p[i] = ri;
     acc.add_prod(ri, ri);
+    if (x_save) {
+      x_save[i] = x[i];
+      qx_save[i] = qxi;
+    }
   }
   store_and_finish_dot(acc, part_r0, ticket);
 }

@@ -148,6 +148,10 @@ struct VecSet {
   T *x_a_lo = nullptr, *dx = nullptr, *dx_avg = nullptr;
   T *b_shift = nullptr, *ax_d = nullptr;
   T *y_lo = nullptr, *ya_lo = nullptr;
+  // Adaptive step size: the start of the current attempt (x in its iteration
+  // form, and Q x) and the trial y, its low word (FP32 set only) and A x.
+  T *x_save = nullptr, *qx_save = nullptr;
+  T *y_new = nullptr, *yn_lo = nullptr, *ax_new = nullptr;
 };
 
 // The vectors the per-iteration kernels read as x, x~, A x and b: the
@@ -190,6 +194,8 @@ struct qp_handle {
   VecSet<float> v32;
   double *part_cg = nullptr, *part_n = nullptr, *part_m = nullptr, *part_rn = nullptr,
          *part_rm = nullptr, *part_pow = nullptr, *part2 = nullptr, *part_r0 = nullptr;
+  double *part_step_n = nullptr, *part_step_m = nullptr;  // adaptive step test partials
+  int step_mode = QP_STEP_FIXED;  // step rule of the iteration being launched
   DevState* st = nullptr;
   GridBarrier* bar = nullptr;
   DevState* h_st = nullptr;  // pinned mirror
@@ -204,6 +210,7 @@ struct qp_handle {
   std::vector<double> d1, d2;    // the scaling (x = D2 x~, y = D1 y~)
   cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};
   int chunk_iters[2] = {0, 0};
+  int chunk_step[2] = {-1, -1};
   std::vector<cudaEvent_t> ev;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   std::vector<qp_trace_entry> trace;
@@ -301,6 +308,7 @@ void fill_dev_options(qp_handle* h, const qp_options* o, DevOptions* d) {
   d->m_eq = h->m_eq;
   d->debug_flags = o->debug_flags;
   d->barrier_timeout_ms = (o->debug_flags & QP_DEBUG_BARRIER_NEVER_RELEASES) ? 200 : 2000;
+  d->step_mode = o->step_mode;
 }
 
 qp_status validate_options(const qp_options* o) {
@@ -315,7 +323,7 @@ qp_status validate_options(const qp_options* o) {
       o->power_iters < 1 || o->power_iters > 100000 || !(o->eps_zero >= 0.0) ||
       !(o->theta_pw >= 0.0 && o->theta_pw <= 1.0) || !(o->time_limit_s > 0.0) ||
       (o->precision != QP_PREC_FP64 && o->precision != QP_PREC_MIXED) || o->warm_start < 0 ||
-      o->warm_start > 2) {
+      o->warm_start > 2 || (o->step_mode != QP_STEP_FIXED && o->step_mode != QP_STEP_ADAPTIVE)) {
     set_error("invalid option value");
     return QP_ERR_INVALID_ARG;
   }
@@ -364,8 +372,11 @@ qp_status launch_dual(qp_handle* h) {
   launch_long<T>(h, h->A, it_x(v));
   return dispatch_g(lanes<T>(h->A), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    k_dual<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(view<T>(h->A), it_x(v), it_b(v), v.y,
-                                                      v.y_lo, it_ax(v), v.y_avg, v.ya_lo, h->st);
+    const bool ad = h->step_mode == QP_STEP_ADAPTIVE;
+    k_dual<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(
+        view<T>(h->A), it_x(v), it_b(v), v.y, v.y_lo, it_ax(v), v.y_avg, v.ya_lo, h->st,
+        ad ? v.y_new : nullptr, ad ? v.yn_lo : nullptr, ad ? v.ax_new : nullptr,
+        ad ? h->part_step_m : nullptr);
   });
 }
 
@@ -375,10 +386,12 @@ qp_status launch_atv(qp_handle* h) {
   launch_long<T>(h, h->At, v.y);
   return dispatch_g(lanes<T>(h->At), [&](auto g) {
     constexpr int G = decltype(g)::value;
+    const bool ad = h->step_mode == QP_STEP_ADAPTIVE;
     k_atv<G, T><<<h->grid_n, kBlock, 0, h->stream>>>(view<T>(h->At), v.y, v.aty, it_x(v),
                                                      it_x_avg(v), v.qx, v.c, v.r, v.p,
-                                                     h->part_r0, h->ticket,
-                                                     h->st);
+                                                     h->part_r0, h->ticket, h->st,
+                                                     ad ? v.x_save : nullptr,
+                                                     ad ? v.qx_save : nullptr);
   });
 }
 
@@ -444,13 +457,27 @@ template <class T>
 void launch_prepare(qp_handle* h) {
   VecSet<T>& v = vecs<T>(h);
   k_prepare<T><<<h->grid_n, kBlock, 0, h->stream>>>(v.qx, v.c, v.aty, v.r, v.p, h->n, h->part_r0,
-                                                    h->ticket);
+                                                    h->ticket, it_x(v), v.x_save, v.qx_save);
 }
 
+// Adaptive step size, between the dual step and A'y: the step test, then the
+// commit (or drop) of the trial y and A x.
+template <class T>
+void launch_step(qp_handle* h) {
+  VecSet<T>& v = vecs<T>(h);
+  k_step<T><<<h->grid_vec, kBlock, 0, h->stream>>>(it_x(v), v.x_save, v.qx, v.qx_save, h->n,
+                                                   h->part_step_n, h->part_step_m, h->grid_m,
+                                                   h->ticket, h->st);
+  k_commit_m<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.y, v.y_lo, v.y_new, v.yn_lo, it_ax(v),
+                                                       v.ax_new, v.y_avg, v.ya_lo, h->m, h->st);
+}
+
+// One inner iteration (with the adaptive step size: one attempt).
 template <class T>
 qp_status launch_iteration(qp_handle* h, bool coop) {
   QP_TRY(launch_cg<T>(h, coop));
   QP_TRY(launch_dual<T>(h));
+  if (h->step_mode == QP_STEP_ADAPTIVE) launch_step<T>(h);
   QP_TRY(launch_atv<T>(h));
   return QP_OK;
 }
@@ -557,6 +584,7 @@ qp_status enqueue_chunk(qp_handle* h, int iters, bool coop, cudaEvent_t* ev) {
     s = launch_cg<T>(h, coop);
     if (ev) cudaEventRecord(ev[2 * k + 1], h->stream);
     if (s == QP_OK) s = launch_dual<T>(h);
+    if (s == QP_OK && h->step_mode == QP_STEP_ADAPTIVE) launch_step<T>(h);
     if (s == QP_OK) s = launch_atv<T>(h);
   }
   if (s == QP_OK) s = launch_eval<T>(h, 1);
@@ -596,13 +624,15 @@ qp_status capture_chunk(qp_handle* h, int iters, bool coop) {
     return QP_ERR_CUDA;
   }
   h->chunk_iters[pi] = iters;
+  h->chunk_step[pi] = h->step_mode;
   return QP_OK;
 }
 
 template <class T>
 qp_status ensure_chunk(qp_handle* h, int iters) {
   const int pi = std::is_same<T, double>::value ? 0 : 1;
-  if (h->chunk_exec[pi] && h->chunk_iters[pi] == iters) return QP_OK;
+  if (h->chunk_exec[pi] && h->chunk_iters[pi] == iters && h->chunk_step[pi] == h->step_mode)
+    return QP_OK;
   if (h->coop_ok) {
     qp_status s = capture_chunk<T>(h, iters, true);
     if (s == QP_OK) return QP_OK;
@@ -842,11 +872,13 @@ qp_status alloc_vecs(qp_handle* h) {
   VecSet<T>& v = vecs<T>(h);
   const size_t N = size_t(h->n), M = size_t(h->m);
   T** nv[] = {&v.c, &v.x, &v.aty, &v.x_avg, &v.x_anchor, &v.aty_avg, &v.r, &v.p, &v.q, &v.qx,
-              &v.qx_avg, &v.x0, &v.pw_v, &v.pw_w};
+              &v.qx_avg, &v.x0, &v.pw_v, &v.pw_w, &v.x_save, &v.qx_save};
   for (T** p : nv) QP_TRY(dalloc(h, p, N));
-  T** mv[] = {&v.b, &v.y, &v.ax, &v.y_avg, &v.y_anchor, &v.ax_avg, &v.y0, &v.pw_u};
+  T** mv[] = {&v.b, &v.y, &v.ax, &v.y_avg, &v.y_anchor, &v.ax_avg, &v.y0, &v.pw_u, &v.y_new,
+              &v.ax_new};
   for (T** p : mv) QP_TRY(dalloc(h, p, M));
   if (std::is_same<T, float>::value) {
+    QP_TRY(dalloc(h, &v.yn_lo, M));
     T** xn[] = {&v.x_a_lo, &v.dx, &v.dx_avg};
     for (T** p : xn) {
       QP_TRY(dalloc(h, p, N));
@@ -883,6 +915,7 @@ void fill_info_from_state(qp_handle* h, qp_info* info) {
   info->tau = s.tau;
   info->sigma = s.sigma;
   info->cooperative = h->coop_ok ? 1 : 0;
+  info->attempts = s.attempts;
 }
 
 qp_status validate_problem(int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr,
@@ -1010,6 +1043,8 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   QP_TRY(dalloc(h, &h->part_rm, size_t(gmax)));
   QP_TRY(dalloc(h, &h->part_pow, size_t(gmax)));
   QP_TRY(dalloc(h, &h->part2, size_t(2) * gmax));
+  QP_TRY(dalloc(h, &h->part_step_n, size_t(2) * h->grid_vec));
+  QP_TRY(dalloc(h, &h->part_step_m, size_t(2) * h->grid_m));
   QP_TRY(dalloc(h, &h->st, 1));
   QP_TRY(dalloc(h, &h->bar, 1));
   CUDA_TRY(cudaMallocHost(&h->h_st, sizeof(DevState)));
@@ -1131,6 +1166,7 @@ qp_status promote_and_refine(qp_handle* h, const qp_options* o, bool timing,
   if (*term == QP_TERM_SOLVED && !(d.kkt_cur[3] <= o->tol) && o->refine) {
     // FP64 refinement: a new epoch at the promoted iterate.
     d.j = 0;
+    d.weight_sum = 0.0;
     d.eps = 0.0;
     d.kkt_anchor = d.kkt_cur[3];
     d.kkt_prev_cand = INFINITY;
@@ -1231,6 +1267,7 @@ void qp_options_default(qp_options* o) {
   o->debug_flags = 0;
   o->precision = QP_PREC_FP64;
   o->refine = 1;
+  o->step_mode = QP_STEP_FIXED;
 }
 
 qp_status qp_create(qp_handle** out, int32_t n, int32_t m, int32_t m_eq, const int32_t* Q_rowptr,
@@ -1313,6 +1350,7 @@ qp_status qp_solve(qp_handle* h, const qp_options* o, qp_info* info_out) {
   info.precision = o->precision;
   int term = -1;
   QP_TRY(write_options(h, o));
+  h->step_mode = o->step_mode;
   const qp_status status = o->precision == QP_PREC_MIXED
                                ? solve_impl<float>(h, o, t0, &info, &term)
                                : solve_impl<double>(h, o, t0, &info, &term);
@@ -1326,7 +1364,7 @@ qp_status qp_solve(qp_handle* h, const qp_options* o, qp_info* info_out) {
   info.device_error = h->h_st->err;
   if (o->kernel_timing) {
     // launches that did work, and the Q products inside them
-    info.cg_kernel_launches = h->h_st->k_total;
+    info.cg_kernel_launches = h->h_st->attempts;
     info.cg_kernel_spmvs = h->h_st->spmv_total;
   }
   info.solve_ms =
@@ -1483,13 +1521,16 @@ qp_status qp_get_state(const qp_handle* hc, const qp_state_vectors* v, qp_state_
     s->k_total = d.k_total;
     s->restarts = d.n_restarts;
     s->cg_total = d.cg_total;
+    s->attempts = d.attempts;
+    s->weight_sum = d.weight_sum;
   }
   return end_call(h);
 }
 
 qp_status qp_set_state(qp_handle* h, const qp_state_vectors* v, const qp_state_scalars* s) {
   if (!h || !v || !s) return QP_ERR_INVALID_ARG;
-  if (!(s->omega > 0.0) || !(s->eta > 0.0) || s->j < 0 || s->k_total < 0) {
+  if (!(s->omega > 0.0) || !(s->eta > 0.0) || s->j < 0 || s->k_total < 0 ||
+      s->attempts < s->k_total || !(s->weight_sum >= 0.0)) {
     set_error("invalid state scalars");
     return QP_ERR_INVALID_ARG;
   }
@@ -1532,6 +1573,10 @@ qp_status qp_set_state(qp_handle* h, const qp_state_vectors* v, const qp_state_s
   d.k_total = s->k_total;
   d.n_restarts = s->restarts;
   d.cg_total = s->cg_total;
+  d.attempts = s->attempts;
+  d.weight_sum = s->weight_sum;
+  d.avg_w = 1.0;
+  d.accepted = 1;
   d.done = 0;
   d.err = 0;
   d.restart_pending = 0;
@@ -1549,7 +1594,8 @@ qp_status qp_iterate(qp_handle* h, const qp_options* o, int64_t iters) {
   QP_TRY(read_state(h));
   DevState& d = *h->h_st;
   fill_dev_options(h, o, &d.opt);
-  d.opt.max_iter = d.k_total + iters;
+  h->step_mode = o->step_mode;
+  d.opt.max_iter = d.attempts + iters;
   d.done = 0;
   d.err = 0;
   QP_TRY(write_state(h));

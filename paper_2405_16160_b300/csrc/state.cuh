@@ -15,6 +15,12 @@ namespace pdhcg {
 constexpr int kCgAdaptive = 0;
 constexpr int kCgFixed = 1;
 constexpr int kRestartAdaptive = 0;
+constexpr int kStepFixed = 0;
+constexpr int kStepAdaptive = 1;
+// Exponents of PDLP's step update, which the Section 4 adaptive step rule
+// builds on: the next eta is min((1 - (a+1)^-0.3) L, (1 + (a+1)^-0.6) eta).
+constexpr double kStepReductionExp = 0.3;
+constexpr double kStepGrowthExp = 0.6;
 
 // done codes: 0 running, otherwise 1 + qp_termination
 constexpr int kDoneSolved = 1;
@@ -33,6 +39,7 @@ struct DevOptions {
   int pw_update, m_eq;
   unsigned debug_flags;
   int barrier_timeout_ms;
+  int step_mode;
 };
 
 struct DevState {
@@ -48,6 +55,13 @@ struct DevState {
   double kkt_ret[6];              // terms of the iterate a stop now would return
   long long j, k_total, n_restarts, cg_total, last_cg, n_evals, spmv_total;
   int done, returned_avg, iter_active, restart_pending, last_restart, err;
+  // adaptive step size: attempts so far (= k_total with the fixed step), the
+  // sum of the epoch's accepted etas, the averaging weight eta/sum of the
+  // step just accepted, the CG precision of the pending attempt, and whether
+  // the last attempt was accepted
+  long long attempts;
+  double weight_sum, avg_w, eps_try;
+  int accepted;
 };
 
 __device__ __forceinline__ bool running(const DevState* st) { return st->done == 0 && st->err == 0; }
@@ -137,7 +151,39 @@ __device__ inline void control_decide(DevState* st, const KktTerms& kc, const Kk
       st->kkt_prev_cand = b;
     }
   }
-  if (st->k_total >= st->opt.max_iter) st->done = kDoneIterLimit;
+  if (st->attempts >= st->opt.max_iter) st->done = kDoneIterLimit;
+}
+
+// Adaptive step size (Section 4), after an attempt with step eta from z to
+// the trial z': dx2 = ||dx||^2, dxqdx = dx'Q dx, dy2 = ||dy||^2 and cross =
+// dy'A dx.  L = (omega dx2 + dy2/omega) / (2|cross| + dxqdx) (infinite when
+// the denominator is 0); the attempt is accepted when eta <= L; the next eta
+// is min((1 - (a+1)^-0.3) L, (1 + (a+1)^-0.6) eta) with a = st->attempts (this
+// attempt included).  On acceptance the iteration counters advance, the CG
+// precision of the attempt is kept and the averaging weight eta / (sum of
+// the epoch's accepted etas) is set.  Shared by the single-QP step kernel
+// and the batched solver.
+__device__ inline void step_decide(DevState* st, double dx2, double dxqdx, double dy2,
+                                   double cross) {
+  const double eta = st->eta, om = st->omega;
+  const double movement = om * dx2 + dy2 / om;
+  const double interaction = 2.0 * fabs(cross) + dxqdx;
+  const double lim = interaction > 0.0 ? movement / interaction : CUDART_INF;
+  const double a1 = (double)(st->attempts + 1);
+  const double next = fmin((1.0 - pow(a1, -kStepReductionExp)) * lim,
+                           (1.0 + pow(a1, -kStepGrowthExp)) * eta);
+  const bool acc = eta <= lim;
+  st->accepted = acc ? 1 : 0;
+  st->eta = next;
+  st->tau = next / om;
+  st->sigma = next * om;
+  if (acc) {
+    st->eps = st->eps_try;
+    st->j += 1;
+    st->k_total += 1;
+    st->weight_sum += eta;
+    st->avg_w = eta / st->weight_sum;
+  }
 }
 
 // Primal weight (Section 4): omega <- exp(theta log(dy/dx) + (1-theta) log omega),
@@ -153,6 +199,7 @@ __device__ inline void restart_finish_decide(DevState* st, double dx2, double dy
   st->tau = st->eta / st->omega;
   st->sigma = st->eta * st->omega;
   st->j = 0;
+  st->weight_sum = 0.0;
   st->eps = 0.0;
   st->kkt_anchor = st->kkt_cand;
   st->kkt_prev_cand = CUDART_INF;
@@ -191,6 +238,11 @@ __device__ inline void setup_finish_decide(DevState* st, double s0, double s1, i
     st->iter_active = 0;
     st->restart_pending = 0;
     st->last_restart = 0;
+    st->attempts = 0;
+    st->weight_sum = 0.0;
+    st->avg_w = 1.0;
+    st->eps_try = 0.0;
+    st->accepted = 1;
   }
   st->done = 0;
   st->err = 0;

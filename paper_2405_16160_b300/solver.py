@@ -157,7 +157,11 @@ class QPSolver:
         arrs = {k: (_f64(state[k], self.n if k.startswith("x") else self.m)
                     if state.get(k) is not None else None) for k in self._VEC}
         v = L.QPStateVectorsC(*[_ptr(arrs[k], c_double) for k in self._VEC])
-        s = L.QPStateScalarsC(*[state[n] for n, _ in L.QPStateScalarsC._fields_])
+        # a state without the adaptive-step scalars is a fixed-step state:
+        # every iteration was one attempt and the epoch has no step weights
+        defaults = {"attempts": state.get("k_total"), "weight_sum": 0.0}
+        s = L.QPStateScalarsC(*[state[n] if n in state else defaults[n]
+                                for n, _ in L.QPStateScalarsC._fields_])
         L.check(self.lib.qp_set_state(self.h, byref(v), byref(s)), "qp_set_state")
 
     def set_warm_start(self, x0=None, y0=None) -> None:

@@ -43,7 +43,7 @@ def test_every_declared_function_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.qp_abi_version() == 1
+    assert lib.qp_abi_version() == 2
     assert lib.qp_status_string(0) == b"ok"
     assert lib.qp_status_string(5) == b"device barrier timeout"
 

@@ -179,3 +179,49 @@ def test_batch_instance_larger_than_shared_memory():
     for q, r, x, y in zip(small + fam, res, xs, ys):
         assert r["termination"] == L.TERM_SOLVED, q.name
         assert O.relkkt(O.problem_from_instance(q.to_instance()), x, y).relkkt <= 1e-4
+
+
+# ------------------------------------------------- Section 4 adaptive step size
+def test_batch_adaptive_step_matches_oracle(batch):
+    insts, bt = batch
+    tol = 1e-6
+    bt.solve(tol=tol, precision=L.PREC_FP64, step_mode=L.STEP_ADAPTIVE)
+    res = bt.results()
+    xs, ys = bt.solution()
+    same_counts = tot_gpu = tot_oracle = 0
+    for q, r, x, y in zip(insts, res, xs, ys):
+        P, ores = _oracle(q, tol, step_mode=O.STEP_ADAPTIVE)
+        assert ores.termination == O.SOLVED, q.name
+        assert r["termination"] == L.TERM_SOLVED, q.name
+        rescored = O.relkkt(P, x, y)
+        assert rescored.relkkt <= tol, q.name
+        assert r["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-12), q.name
+        assert rescored.primal_obj == pytest.approx(ores.kkt.primal_obj, rel=1e-5, abs=1e-9)
+        assert r["attempts"] >= r["iterations"]
+        same_counts += (r["iterations"] == ores.iterations and
+                        r["attempts"] == ores.state.attempts and r["restarts"] == ores.restarts)
+        tot_gpu += r["attempts"]
+        tot_oracle += ores.state.attempts
+    # eta is a continuous function of the iterates, so the rounding difference
+    # of F(F'p) against the explicit Q p moves more trajectories than with the
+    # fixed step; the work stays the same
+    assert same_counts >= 0.6 * len(insts)
+    assert abs(tot_gpu - tot_oracle) <= 0.05 * tot_oracle
+
+
+def test_batch_adaptive_step_mixed_and_global_memory():
+    """Mixed precision with the adaptive step, including an n = 2000 instance
+    whose vectors (with the step's extra four) live in global memory; the
+    adaptive step takes fewer iterations than the fixed one on the portfolios."""
+    fam = W.portfolio_family(0, seeds=[1])
+    small = W.portfolio_batch(5, count=6, n_lo=100, n_hi=300)
+    with QPBatch(small + fam) as bt:
+        bt.solve(tol=1e-4, precision=L.PREC_MIXED)
+        fixed = bt.results()
+        bt.solve(tol=1e-4, precision=L.PREC_MIXED, step_mode=L.STEP_ADAPTIVE)
+        res = bt.results()
+        xs, ys = bt.solution()
+    for q, r, x, y in zip(small + fam, res, xs, ys):
+        assert r["termination"] == L.TERM_SOLVED, q.name
+        assert O.relkkt(O.problem_from_instance(q.to_instance()), x, y).relkkt <= 1e-4
+    assert sum(r["attempts"] for r in res) < 0.8 * sum(r["iterations"] for r in fixed)

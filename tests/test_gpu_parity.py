@@ -536,3 +536,133 @@ def test_full_size_scaled_solve_matches_oracle_trace():
     assert mix["termination"] == L.TERM_SOLVED
     assert O.relkkt(P, xm, ym).relkkt <= 1e-4
     assert O.relkkt(P, xm, ym).primal_obj == pytest.approx(g["primal_obj"], rel=1e-4)
+
+
+# ------------------------------------------------- Section 4 adaptive step size
+# Each attempt runs the iteration into a trial point, the step test accepts
+# or rejects it (a rejection keeps z) and eta moves either way.  From a
+# shared state the GPU's attempts match the oracle's: the same decisions,
+# eta to 1e-12 and the iterates to 1e-10 (FP64).  A start at 30x the fixed
+# step makes the first attempts rejections.
+ADAPTIVE_ITER_CASES = ["dense_small", "dense_small_eq", "sparse_small", "ragged_eq",
+                       "empty_rows", "single", "long_rows", "zipf_small"]
+
+
+@pytest.mark.parametrize("name", ADAPTIVE_ITER_CASES)
+@pytest.mark.parametrize("eta_mult,iters", [(1.0, 1), (1.0, 4), (30.0, 4)])
+def test_adaptive_step_attempts_match_oracle(built, name, eta_mult, iters):
+    inst, P, s = built(name)
+    st = _shared_state(inst, P, 5)
+    st["eta"] *= eta_mult
+    s.set_state(st)
+    s.iterate(iters, step_mode=L.STEP_ADAPTIVE)
+    got = s.get_state()
+    ost = _oracle_state(st)
+    ost.attempts = st["k_total"]  # a state without attempts counts every iteration as one
+    o = O.OracleOptions(step_mode=O.STEP_ADAPTIVE)
+    for _ in range(iters):
+        O.inner_step(P, ost, o)
+    assert got["k_total"] == ost.k_total and got["j"] == ost.j
+    assert got["attempts"] == ost.attempts == st["k_total"] + iters
+    for key in ("x", "y", "x_avg", "y_avg"):
+        assert _relerr(got[key], getattr(ost, key)) <= 1e-10, key
+    assert got["eta"] == pytest.approx(ost.eta, rel=1e-12)
+    assert got["weight_sum"] == pytest.approx(ost.weight_sum, rel=1e-12)
+    assert got["cg_total"] == ost.cg_total
+    assert got["eps"] == pytest.approx(ost.eps, rel=1e-15)
+    if eta_mult > 1.0 and name != "single":
+        assert ost.k_total < st["k_total"] + iters  # the big start was rejected at least once
+
+
+@pytest.mark.parametrize("name,tol", [("dense_small", 1e-6), ("dense_small_eq", 1e-6),
+                                      ("sparse_small", 1e-4), ("ragged_eq", 1e-4),
+                                      ("all_equalities", 1e-6), ("empty_rows", 1e-6),
+                                      ("single", 1e-8), ("long_rows", 1e-5)])
+def test_adaptive_step_end_to_end_matches_oracle(built, name, tol):
+    inst, P, s = built(name)
+    ores = O.solve(P, O.OracleOptions(tol=tol, step_mode=O.STEP_ADAPTIVE))
+    info = s.solve(tol=tol, step_mode=L.STEP_ADAPTIVE)
+    x, y = s.solution()
+    assert ores.termination == O.SOLVED and info["termination"] == L.TERM_SOLVED
+    rescored = O.relkkt(P, x, y)
+    assert rescored.relkkt <= tol
+    assert info["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-12)
+    assert rescored.primal_obj == pytest.approx(ores.kkt.primal_obj, rel=1e-4, abs=1e-8)
+    trace = s.trace()
+    orestarts = [(r["k"], int(r["restart"]) * (2 if r["cand_avg"] else 1)) for r in ores.trace[1:]]
+    if [(t["k"], t["restart"]) for t in trace] == orestarts:
+        assert info["iterations"] == ores.iterations
+        assert info["attempts"] == ores.state.attempts
+        assert info["restarts"] == ores.restarts
+        assert info["cg_steps"] == ores.cg_steps
+        # the same decisions; eta moves with the iterates, so rounding drifts a
+        # little further than with the fixed step (1e-8 there)
+        assert _relerr(x, ores.x) <= 1e-7
+    else:
+        # eta is a continuous function of the iterates: over thousands of
+        # attempts rounding-level differences (summation order, fused
+        # multiply-adds) can move a restart decision, after which the two
+        # trajectories part.  Attempt-level parity is the test above; here the
+        # work and the answer must agree.
+        assert abs(info["attempts"] - ores.state.attempts) <= 0.15 * ores.state.attempts + 64
+        assert _relerr(x, ores.x) <= 100 * tol
+
+
+@pytest.mark.parametrize("name,tol", [("dense_small", 1e-6), ("sparse_small", 1e-4),
+                                      ("ragged_eq", 1e-4), ("long_rows", 1e-5),
+                                      ("zipf_small", 1e-4)])
+def test_adaptive_step_mixed_meets_tolerance_in_fp64(built, name, tol):
+    inst, P, s = built(name)
+    ores = O.solve(P, O.OracleOptions(tol=tol, step_mode=O.STEP_ADAPTIVE))
+    info = s.solve(tol=tol, precision=L.PREC_MIXED, step_mode=L.STEP_ADAPTIVE)
+    x, y = s.solution()
+    assert info["termination"] == L.TERM_SOLVED
+    rescored = O.relkkt(P, x, y)
+    assert rescored.relkkt <= tol
+    assert rescored.primal_obj == pytest.approx(ores.kkt.primal_obj, rel=1e-4, abs=1e-8)
+    assert info["attempts"] >= info["iterations"] > 0
+
+
+def test_adaptive_step_checkpoint_resume_is_bit_identical(built):
+    inst, P, s = built("sparse_small")
+    s.solve(tol=0.0, max_iter=256, step_mode=L.STEP_ADAPTIVE)
+    full = s.get_state()
+    s.solve(tol=0.0, max_iter=128, step_mode=L.STEP_ADAPTIVE)
+    mid = s.get_state()
+    with QPSolver(inst) as s2:
+        s2.set_state(mid)
+        s2.solve(tol=0.0, max_iter=256, warm_start=2, step_mode=L.STEP_ADAPTIVE)
+        resumed = s2.get_state()
+    for key in ("x", "y", "x_avg", "y_avg", "x_anchor", "y_anchor"):
+        assert np.array_equal(full[key], resumed[key]), key
+    for key in ("eta", "omega", "eps", "j", "k_total", "attempts", "weight_sum", "restarts",
+                "cg_total"):
+        assert full[key] == resumed[key], key
+
+
+GOLDEN_ADAPTIVE = os.path.join(os.path.dirname(__file__), "golden",
+                               "sparse_dd_n1000000_m500000_seed0_scaled_adaptive_trace.json")
+
+
+def test_full_size_scaled_adaptive_step_matches_oracle_trace():
+    """The bench instance (n = 1e6, Section 4 scaling) with the adaptive step:
+    the oracle's attempts, iterations, CG steps and restarts, and its objective."""
+    inst = W.sparse_dd(0)
+    P = O.problem_from_instance(inst)
+    with open(GOLDEN_ADAPTIVE) as f:
+        g = json.load(f)
+    with QPSolver(inst, scale=True) as s:
+        info = s.solve(tol=1e-4, step_mode=L.STEP_ADAPTIVE)
+        x, y = s.solution()
+        assert info["termination"] == L.TERM_SOLVED
+        rescored = O.relkkt(P, x, y)
+        assert rescored.relkkt <= 1e-4
+        assert info["iterations"] == g["iterations"]
+        assert info["attempts"] == g["attempts"]
+        assert info["restarts"] == g["restarts"]
+        assert info["cg_steps"] == g["cg_steps"]
+        assert rescored.primal_obj == pytest.approx(g["primal_obj"], rel=1e-4)
+        mixed = s.solve(tol=1e-4, precision=L.PREC_MIXED, step_mode=L.STEP_ADAPTIVE)
+        xm, ym = s.solution()
+        assert mixed["termination"] == L.TERM_SOLVED
+        assert O.relkkt(P, xm, ym).relkkt <= 1e-4
