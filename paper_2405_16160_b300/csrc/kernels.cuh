@@ -239,45 +239,108 @@ __device__ __forceinline__ void block_dot_store(AccF a, double* out) {
   __syncthreads();
 }
 
-// Fixed-order reduction of n block partials (stride apart) by one warp; every
-// lane returns the same value, and so does every block that calls it.
-__device__ __forceinline__ double warp_reduce_partials(const double* p, int n, int stride,
-                                                       bool is_max) {
-  const int lane = threadIdx.x & 31;
-  double x = 0.0;
-  for (int i = lane; i < n; i += 32) {
-    const double v = __ldcg(p + size_t(i) * stride);
-    x = is_max ? fmax(x, v) : x + v;
+// Fixed-order reductions of block partials by a whole block.  A grid-wide
+// total is read right after a grid barrier or by the last block to finish,
+// so it sits on the critical path: every thread issues its loads together
+// (one round trip to L2 instead of one per partial a lane would walk), then
+// the warps combine by xor shuffles and warp 0 combines the warps in index
+// order.  The order depends only on the partial count and blockDim, so the
+// result is the same on every run and in every block that computes it.
+//
+// Row i of the partials is part + i * stride with K entries; bit k of maxmask
+// marks entry k as a maximum (of non-negative values), the others are sums.
+// Every thread gets the totals.
+template <int K, int RB = (K > 4 ? 2 : 4)>
+__device__ __forceinline__ void block_reduce_rows(const double* part, int nrows, int stride,
+                                                  unsigned maxmask, double (&out)[K]) {
+  __shared__ double sh[K][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (int base = threadIdx.x; base < nrows; base += RB * blockDim.x) {
+    double v[RB][K];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      const int i = base + j * int(blockDim.x);
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[j][k] = i < nrows ? __ldcg(part + size_t(i) * stride + k) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        acc[k] = ((maxmask >> k) & 1u) ? fmax(acc[k], v[j][k]) : acc[k] + v[j][k];
   }
-  return is_max ? warp_max(x) : warp_sum(x);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double x = ((maxmask >> k) & 1u) ? warp_max(acc[k]) : warp_sum(acc[k]);
+    if (lane == 0) sh[k][wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double x = lane < nwarps ? sh[k][lane] : 0.0;
+      x = ((maxmask >> k) & 1u) ? warp_max(x) : warp_sum(x);
+      if (lane == 0) sh[k][0] = x;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = sh[k][0];
+  __syncthreads();
 }
 
-__device__ __forceinline__ double warp_reduce_dot_partials(const double* p, int n, AccD) {
-  return warp_reduce_partials(p, n, 1, false);
+// The total of n block_dot_store partials.  FP64: their plain sum.  FP32:
+// the double-float pairs added two-sum style, on the FP32 pipe.  RB loads in
+// flight per thread (1 where n <= blockDim, as in the persistent CG grid).
+template <int RB>
+__device__ __forceinline__ double block_total_dot(const double* p, int n, AccD) {
+  double t[1];
+  block_reduce_rows<1, RB>(p, n, 1, 0u, t);
+  return t[0];
 }
 
-__device__ __forceinline__ double warp_reduce_dot_partials(const double* p, int n, AccF) {
+template <int RB>
+__device__ __forceinline__ double block_total_dot(const double* p, int n, AccF) {
+  __shared__ float2 sh[32];
+  __shared__ double s_tot;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   AccF a;
-  for (int i = threadIdx.x & 31; i < n; i += 32) {
-    const float2 f = __ldcg(reinterpret_cast<const float2*>(p) + i);
-    a.add2(f.x, f.y);
+  for (int base = threadIdx.x; base < n; base += RB * blockDim.x) {
+    float2 v[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      const int i = base + j * int(blockDim.x);
+      v[j] = i < n ? __ldcg(reinterpret_cast<const float2*>(p) + i) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < RB; ++j) a.add2(v[j].x, v[j].y);
   }
   warp_merge(a);
-  return a.value();
+  if (lane == 0) sh[wid] = make_float2(a.hi, a.lo);
+  __syncthreads();
+  if (wid == 0) {
+    AccF b;
+    if (lane < int(blockDim.x >> 5)) {
+      b.hi = sh[lane].x;
+      b.lo = sh[lane].y;
+    }
+    warp_merge(b);
+    if (lane == 0) s_tot = b.value();
+  }
+  __syncthreads();
+  const double v = s_tot;
+  __syncthreads();
+  return v;
 }
 
 // The total of block_dot_store partials, broadcast to every thread of the block.
-template <class A>
+template <class A, int RB = 4>
 __device__ __forceinline__ double block_all_reduce(const double* p, int n) {
-  __shared__ double s_val;
-  if (threadIdx.x < 32) {
-    const double v = warp_reduce_dot_partials(p, n, A());
-    if (threadIdx.x == 0) s_val = v;
-  }
-  __syncthreads();
-  const double v = s_val;
-  __syncthreads();
-  return v;
+  return block_total_dot<RB>(p, n, A());
 }
 
 // Sense-free generation barrier over all blocks of a co-resident grid.  Every
@@ -441,8 +504,15 @@ __device__ __forceinline__ void long_finish(const LongRows& L, const T* seg_part
   const long long nw = grid_threads() >> 5;
   for (long long r = grid_tid() >> 5; r < L.nlong; r += nw) {
     double s = 0.0;
-    for (int k = __ldg(L.seg_ptr + r) + lane; k < __ldg(L.seg_ptr + r + 1); k += 32)
-      s += (double)__ldcg(seg_part + k);
+    const int e = __ldg(L.seg_ptr + r + 1);
+    // four loads in flight per lane; the additions keep the order k, k+32, ...
+    for (int k = __ldg(L.seg_ptr + r) + lane; k < e; k += 4 * 32) {
+      double v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = k + 32 * j < e ? (double)__ldcg(seg_part + k + 32 * j) : 0.0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s += v[j];
+    }
     s = warp_sum(s);
     if (lane == 0) long_val[r] = T(s);
   }
@@ -473,9 +543,9 @@ __device__ __forceinline__ void store_and_finish_dot(A acc, double* part, unsign
     s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (s_last && threadIdx.x < 32) {
+  if (s_last) {  // the whole last block (the branch is uniform)
     __threadfence();
-    const double total = warp_reduce_dot_partials(part, gridDim.x, A());
+    const double total = block_total_dot<4>(part, gridDim.x, A());
     if (threadIdx.x == 0) {
       part[gridDim.x] = total;
       *ticket = 0u;
@@ -550,7 +620,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     block_dot_store(acc, part_pq + blockIdx.x);
     if (!grid_sync(bar, st, tmo, never_release)) return;
     never_release = false;
-    const double pq = block_all_reduce<A>(part_pq, gridDim.x);
+    const double pq = block_all_reduce<A, 1>(part_pq, gridDim.x);
     if (!(pq > 0.0) || !isfinite(pq)) {
       numerr = true;
       break;
@@ -572,7 +642,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     }
     block_dot_store(acc, part_rr + blockIdx.x);
     if (!grid_sync(bar, st, tmo, false)) return;
-    const double rr_new = block_all_reduce<A>(part_rr, gridDim.x);
+    const double rr_new = block_all_reduce<A, 1>(part_rr, gridDim.x);
     ++steps;
     const bool stop = mode == kCgFixed ? steps >= nfix : (tau * sqrt(rr_new) <= eps || steps >= cgmax);
     if (stop || rr_new == 0.0) break;
@@ -754,14 +824,13 @@ __global__ void __launch_bounds__(kBlock) k_step(const T* __restrict__ x,
     s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (s_last && threadIdx.x < 32) {
+  if (s_last) {  // the whole last block (the branch is uniform)
     __threadfence();
-    const double dx2 = warp_reduce_partials(part_n, gridDim.x, 2, false);
-    const double dxq = warp_reduce_partials(part_n + 1, gridDim.x, 2, false);
-    const double dy2 = warp_reduce_partials(part_m, gm, 2, false);
-    const double cross = warp_reduce_partials(part_m + 1, gm, 2, false);
+    double tn[2], tm[2];
+    block_reduce_rows<2>(part_n, gridDim.x, 2, 0u, tn);
+    block_reduce_rows<2>(part_m, gm, 2, 0u, tm);
     if (threadIdx.x == 0) {
-      step_decide(st, dx2, dxq, dy2, cross);
+      step_decide(st, tn[0], tn[1], tm[0], tm[1]);
       *ticket = 0u;
       __threadfence();
     }
@@ -944,16 +1013,13 @@ __global__ void __launch_bounds__(kBlock) k_kkt_m(const T* __restrict__ ax,
 
 
 
-// One warp: reduce the relKKT partials, then control_decide.
-__global__ void k_control(const double* part_n, int gn, const double* part_m, int gm, DevState* st,
-                          int mode) {
+// One block: reduce the relKKT partials, then control_decide.
+__global__ void __launch_bounds__(kBlock) k_control(const double* part_n, int gn,
+                                                    const double* part_m, int gm, DevState* st,
+                                                    int mode) {
   double rn[11], rm[7];
-#pragma unroll
-  for (int k = 0; k < 11; ++k)
-    rn[k] = warp_reduce_partials(part_n + k, gn, kPartStride, (kKktNMaxMask >> k) & 1u);
-#pragma unroll
-  for (int k = 0; k < 7; ++k)
-    rm[k] = warp_reduce_partials(part_m + k, gm, kPartStride, (kKktMMaxMask >> k) & 1u);
+  block_reduce_rows<11>(part_n, gn, kPartStride, kKktNMaxMask, rn);
+  block_reduce_rows<7>(part_m, gm, kPartStride, kKktMMaxMask, rm);
   if (threadIdx.x != 0) return;
   const KktTerms kc = kkt_from(rm[0], rm[1], rm[6], rn[0], rn[1], rn[2], rn[10], rn[3], rn[4], rm[2]);
   const KktTerms ka = kkt_from(rm[3], rm[4], rm[6], rn[5], rn[6], rn[7], rn[10], rn[8], rn[9], rm[5]);
@@ -1051,13 +1117,15 @@ __global__ void __launch_bounds__(kBlock) k_restart_m(T* y, T* y_lo, const T* __
 }
 
 
-__global__ void k_restart_finish(const double* part_n, int gn, const double* part_m, int gm,
-                                 DevState* st) {
+__global__ void __launch_bounds__(kBlock) k_restart_finish(const double* part_n, int gn,
+                                                           const double* part_m, int gm,
+                                                           DevState* st) {
   if (st->restart_pending == 0) return;
-  const double dx2 = warp_reduce_partials(part_n, gn, 1, false);
-  const double dy2 = warp_reduce_partials(part_m, gm, 1, false);
+  double dx2[1], dy2[1];
+  block_reduce_rows<1>(part_n, gn, 1, 0u, dx2);
+  block_reduce_rows<1>(part_m, gm, 1, 0u, dy2);
   if (threadIdx.x != 0) return;
-  restart_finish_decide(st, dx2, dy2);
+  restart_finish_decide(st, dx2[0], dy2[0]);
 }
 
 // ---------------------------------------------------------- set-up kernels
@@ -1173,19 +1241,12 @@ __global__ void k_shift_rhs(const float* __restrict__ b, const float* __restrict
 }
 
 
-__global__ void k_setup_finish(const double* part2, int g2, DevState* st, int reset) {
-  double s0 = 0.0, s1 = 0.0;
-  {
-    const int lane = threadIdx.x & 31;
-    for (int i = lane; i < g2; i += 32) {
-      s0 += part2[2 * i];
-      s1 += part2[2 * i + 1];
-    }
-    s0 = warp_sum(s0);
-    s1 = warp_sum(s1);
-  }
+__global__ void __launch_bounds__(kBlock) k_setup_finish(const double* part2, int g2,
+                                                         DevState* st, int reset) {
+  double s[2];
+  block_reduce_rows<2>(part2, g2, 2, 0u, s);
   if (threadIdx.x != 0) return;
-  setup_finish_decide(st, s0, s1, reset);
+  setup_finish_decide(st, s[0], s[1], reset);
 }
 
 }  // namespace pdhcg

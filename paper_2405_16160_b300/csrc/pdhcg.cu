@@ -428,7 +428,7 @@ qp_status launch_eval(qp_handle* h, int mode) {
                                                   v.aty_avg, v.c, v.inv_d2, h->n, h->part_n);
   k_kkt_m<T><<<h->grid_m, kBlock, 0, h->stream>>>(v.ax, v.ax_avg, v.b, v.y, v.y_avg, v.inv_d1,
                                                   h->m, h->m_eq, h->part_m);
-  k_control<<<1, 32, 0, h->stream>>>(h->part_n, h->grid_n, h->part_m, h->grid_m, h->st, mode);
+  k_control<<<1, kBlock, 0, h->stream>>>(h->part_n, h->grid_n, h->part_m, h->grid_m, h->st, mode);
   return QP_OK;
 }
 
@@ -447,7 +447,7 @@ qp_status launch_restart(qp_handle* h) {
                                                         v.y_anchor, it_ax(v), v.ax_avg,
                                                         v.b_shift, v.b, h->st, h->m,
                                                         h->part_rm);
-  k_restart_finish<<<1, 32, 0, h->stream>>>(h->part_rn, h->grid_vec, h->part_rm, h->grid_vec,
+  k_restart_finish<<<1, kBlock, 0, h->stream>>>(h->part_rn, h->grid_vec, h->part_rm, h->grid_vec,
                                             h->st);
   return QP_OK;
 }
@@ -493,7 +493,7 @@ qp_status launch_setup(qp_handle* h, int power_iters, int reset) {
     k_pow_scale<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.pw_w, v.pw_v, h->n, h->part_pow,
                                                           h->grid_n, h->st);
   }
-  k_setup_finish<<<1, 32, 0, h->stream>>>(h->part2, h->grid_vec, h->st, reset);
+  k_setup_finish<<<1, kBlock, 0, h->stream>>>(h->part2, h->grid_vec, h->st, reset);
   return QP_OK;
 }
 
