@@ -150,7 +150,7 @@ def cg_kernel_bytes(nnz_q: int, n: int, launches: int, spmvs: int, cg_steps: int
 
 
 def mixed_solve_launches(chunks: int, power_iters: int, eval_freq: int,
-                         adaptive: bool = True) -> int:
+                         adaptive: bool) -> int:
     """Kernel launches of one mixed-precision qp_solve on an instance without
     long rows (each SpMV is then one launch).
 
@@ -158,12 +158,12 @@ def mixed_solve_launches(chunks: int, power_iters: int, eval_freq: int,
     A dx, A'y, Q x, k_prepare); power iteration (k_pow_start, 3 per step,
     k_setup_finish); the first evaluation (k_materialize, 4 SpMVs, k_kkt_n,
     k_kkt_m, k_control).  Per chunk: 3 per iteration (k_cg, k_dual, k_atv;
-    5 with the adaptive step: k_step and k_commit_m), an evaluation (8), the
+    4 per attempt with the adaptive step: k_commit_m), an evaluation (8), the
     restart kernels (3) and k_prepare.  At the end the FP64 check: 2
     conversions, the FP64 cache refresh (3 SpMVs, k_prepare) and an FP64
     evaluation (4 SpMVs, k_kkt_n, k_kkt_m, k_control)."""
     setup = 1 + 7 + (1 + 3 * power_iters + 1) + 8
-    chunk = (5 if adaptive else 3) * eval_freq + 8 + 3 + 1
+    chunk = (4 if adaptive else 3) * eval_freq + 8 + 3 + 1
     final = 2 + 4 + 7
     return setup + chunks * chunk + final
 

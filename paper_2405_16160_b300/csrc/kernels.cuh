@@ -125,6 +125,14 @@ __device__ __forceinline__ void split_add(float& hi, float& lo, float d) {
 template <class T>
 constexpr bool kSplit = std::is_same<T, float>::value;
 
+// 16 bytes of consecutive vector entries (4 floats or 2 doubles), so that the
+// streaming vector phases load and store 128 bits at a time.
+template <class T>
+struct alignas(16) Pack16 {
+  static constexpr int N = 16 / int(sizeof(T));
+  T v[N];
+};
+
 
 // Dot-product accumulators.  AccD: plain FP64.  AccF: an exact FP32 product
 // (two-product via FMA) added into a double-float pair (two-sum), i.e. about
@@ -563,8 +571,9 @@ __device__ __forceinline__ void store_and_finish_dot(A acc, double* part, unsign
 //   [B] x += a p, qx += a (q - p/tau), r -= a q, r'r
 //   [C] p = r + b p   (only when CG continues)
 // so each step costs one product with Q.  With the adaptive step size the
-// iteration counters wait for k_step's accept/reject decision.  alpha, beta, the stop test and all
-// dot products are FP64-accurate for both value types.  part holds
+// iteration counters wait for the accept/reject decision that k_dual's last
+// block takes.  alpha, beta, the stop test and all dot products are
+// FP64-accurate for both value types.  part holds
 // 2 * gridDim.x doubles.
 // Resident CG blocks of 512 threads per SM (register budget per thread =
 // 65536 / (512 * blocks)).  Four FP32 blocks would need 32 registers and
@@ -631,14 +640,43 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     // exactly as the elementwise vector statements of textbook CG; qx follows
     // x through the stored Q p (recovering it as q - p/tau would cancel badly
     // in FP32 when 1/tau dominates Q).
-    for (long long i = t0; i < n; i += nt) {
-      const T pi = p[i], qpi = q[i];
-      const T qi = qpi + pi * inv_tau;
-      x[i] = add_rn(x[i], mul_rn(alpha, pi));
-      qx[i] = add_rn(qx[i], mul_rn(alpha, qpi));
-      const T ri = sub_rn(r[i], mul_rn(alpha, qi));
-      r[i] = ri;
-      acc.add_prod(ri, ri);
+    // FP32: 16-byte packs of the five vectors (every buffer is 256-byte
+    // aligned), then the tail of n mod 4 entries; each entry's arithmetic is
+    // the same either way.  (FP64 packs would not fit the register budget of
+    // three 512-thread blocks per SM.)
+    {
+      using P = Pack16<T>;
+      constexpr int N = P::N;
+      const long long np = kSplit<T> ? n / N : 0;
+      P* xp = reinterpret_cast<P*>(x);
+      P* qxp = reinterpret_cast<P*>(qx);
+      P* rp = reinterpret_cast<P*>(r);
+      const P* pp = reinterpret_cast<const P*>(p);
+      const P* qp = reinterpret_cast<const P*>(q);
+      for (long long i = t0; i < np; i += nt) {
+        const P pv = pp[i], qv = qp[i], xv = xp[i], qxv = qxp[i], rv = rp[i];
+        P xo, qxo, ro;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const T qi = qv.v[j] + pv.v[j] * inv_tau;
+          xo.v[j] = add_rn(xv.v[j], mul_rn(alpha, pv.v[j]));
+          qxo.v[j] = add_rn(qxv.v[j], mul_rn(alpha, qv.v[j]));
+          ro.v[j] = sub_rn(rv.v[j], mul_rn(alpha, qi));
+          acc.add_prod(ro.v[j], ro.v[j]);
+        }
+        xp[i] = xo;
+        qxp[i] = qxo;
+        rp[i] = ro;
+      }
+      for (long long i = np * N + t0; i < n; i += nt) {
+        const T pi = p[i], qpi = q[i];
+        const T qi = qpi + pi * inv_tau;
+        x[i] = add_rn(x[i], mul_rn(alpha, pi));
+        qx[i] = add_rn(qx[i], mul_rn(alpha, qpi));
+        const T ri = sub_rn(r[i], mul_rn(alpha, qi));
+        r[i] = ri;
+        acc.add_prod(ri, ri);
+      }
     }
     block_dot_store(acc, part_rr + blockIdx.x);
     if (!grid_sync(bar, st, tmo, false)) return;
@@ -648,7 +686,21 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     if (stop || rr_new == 0.0) break;
     const T beta = T(rr_new / rr);
     rr = rr_new;
-    for (long long i = t0; i < n; i += nt) p[i] = add_rn(r[i], mul_rn(beta, p[i]));
+    {
+      using P = Pack16<T>;
+      constexpr int N = P::N;
+      const long long np = kSplit<T> ? n / N : 0;
+      P* pp = reinterpret_cast<P*>(p);
+      const P* rp = reinterpret_cast<const P*>(r);
+      for (long long i = t0; i < np; i += nt) {
+        const P rv = rp[i];
+        P pv = pp[i];
+#pragma unroll
+        for (int j = 0; j < N; ++j) pv.v[j] = add_rn(rv.v[j], mul_rn(beta, pv.v[j]));
+        pp[i] = pv;
+      }
+      for (long long i = np * N + t0; i < n; i += nt) p[i] = add_rn(r[i], mul_rn(beta, p[i]));
+    }
     if (!grid_sync(bar, st, tmo, false)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -662,7 +714,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
       st->last_cg = steps;
       st->spmv_total += steps;
       if (adaptive_step) {
-        st->eps_try = eps;  // kept by k_step if the attempt is accepted
+        st->eps_try = eps;  // kept if the attempt is accepted (step_decide)
       } else {
         st->eps = eps;
         st->k_total += 1;
@@ -679,24 +731,51 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
 // as x, b - A x_a as b and A dx as the cache: the same step, but every FP32
 // quantity it gathers or subtracts is small near convergence.
 //
-// Adaptive step size (y_new != nullptr): the step is a trial.  y, its low
+// Adaptive step size (T.y_new != nullptr): the step is a trial.  y, its low
 // word, the A x cache and the average stay as they are; the trial y+ (and its
-// low word) and A x+ go to y_new, yn_lo, ax_new, and each block stores the
-// partial sums of ||y+ - y||^2 and (y+ - y)'(A x+ - A x) at part_step[2 * block]
-// for k_step's test; k_commit_m keeps them if the step is accepted.
+// low word) and A x+ go to T.y_new, T.yn_lo, T.ax_new.  Each block also takes
+// a slice of the n index space for the primal move of the attempt from its
+// saved start (T.x_save, T.qx_save and the tracked Q x), and stores the
+// partial sums ||y+ - y||^2, (y+ - y)'(A x+ - A x), ||x+ - x||^2 and
+// (x+ - x)'(Q x+ - Q x) at part_step[4 * block]; the last block to finish
+// combines them in a fixed order and takes the Section 4 step decision
+// (step_decide).  k_commit_m and k_atv then commit or drop the trial.
+template <class T>
+struct StepTrial {
+  T* y_new = nullptr;
+  T* yn_lo = nullptr;
+  T* ax_new = nullptr;
+  const T* x_save = nullptr;
+  const T* qx_save = nullptr;
+  const T* qx = nullptr;
+  int n = 0;
+  double* part_step = nullptr;
+  unsigned int* ticket = nullptr;
+};
+
+// The SpMV kernels hold 32 (FP32) or 40 (FP64) registers so that 8 or 6
+// blocks of 256 threads stay resident per SM: their gathers need the warps.
+// The FP64 dual step, with the adaptive step's four accumulators, gets 48.
+template <class T>
+constexpr int kSpmvBlocksPerSm = kSplit<T> ? 8 : 6;
+template <class T>
+constexpr int kDualBlocksPerSm = kSplit<T> ? 8 : 5;
+
 template <int G, class T>
-__global__ void __launch_bounds__(kBlock) k_dual(CsrT<T> A, const T* __restrict__ x,
+__global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
+    k_dual(CsrT<T> A, const T* __restrict__ x,
                                                  const T* __restrict__ b, T* y, T* y_lo, T* ax,
-                                                 T* y_avg, T* ya_lo, const DevState* st,
-                                                 T* y_new, T* yn_lo, T* ax_new,
-                                                 double* part_step) {
+                                                 T* y_avg, T* ya_lo, DevState* st,
+                                                 StepTrial<T> tr) {
   if (!st->iter_active) return;
   const T sigma = T(st->sigma);
   const T inv_j = T(1.0 / (double)st->j);
   const bool first = st->j == 1;
   const int m_eq = st->opt.m_eq;
-  if (y_new) {
-    typename Acc<T>::type acc[2];
+  if (tr.y_new) {
+    typename Acc<T>::type acc[4];
+    {
+    typename Acc<T>::type am[2];
     spmv_rows<G>(A, x, [&](int i, T s, bool lead) {
       if (!lead) return;
       const T da = s - ax[i];
@@ -706,19 +785,43 @@ __global__ void __launch_bounds__(kBlock) k_dual(CsrT<T> A, const T* __restrict_
         split_add(hi, lo, sigma * (T(2) * s - ax[i] - b[i]));
         if (i >= m_eq && hi < T(0)) hi = lo = T(0);
         dy = (hi - y[i]) + (lo - y_lo[i]);
-        y_new[i] = hi;
-        yn_lo[i] = lo;
+        tr.y_new[i] = hi;
+        tr.yn_lo[i] = lo;
       } else {
         T yn = y[i] + sigma * (T(2) * s - ax[i] - b[i]);
         if (i >= m_eq && yn < T(0)) yn = T(0);
         dy = yn - y[i];
-        y_new[i] = yn;
+        tr.y_new[i] = yn;
       }
-      ax_new[i] = s;
-      acc[0].add_prod(dy, dy);
-      acc[1].add_prod(dy, da);
+      tr.ax_new[i] = s;
+      am[0].add_prod(dy, dy);
+      am[1].add_prod(dy, da);
     });
-    block_reduce_ms<0, 2, T>(nullptr, acc, part_step + 2 * size_t(blockIdx.x));
+    acc[0] = am[0];
+    acc[1] = am[1];
+    }
+    for (long long i = grid_tid(); i < tr.n; i += grid_threads()) {
+      const T dx = x[i] - tr.x_save[i], dq = tr.qx[i] - tr.qx_save[i];
+      acc[2].add_prod(dx, dx);
+      acc[3].add_prod(dx, dq);
+    }
+    block_reduce_ms<0, 4, T>(nullptr, acc, tr.part_step + 4 * size_t(blockIdx.x));
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicAdd(tr.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {  // the whole last block (the branch is uniform)
+      __threadfence();
+      double t[4];
+      block_reduce_rows<4>(tr.part_step, gridDim.x, 4, 0u, t);
+      if (threadIdx.x == 0) {
+        step_decide(st, t[2], t[3], t[0], t[1]);
+        *tr.ticket = 0u;
+        __threadfence();
+      }
+    }
     return;
   }
   spmv_rows<G>(A, x, [&](int i, T s, bool lead) {
@@ -753,16 +856,16 @@ __global__ void __launch_bounds__(kBlock) k_dual(CsrT<T> A, const T* __restrict_
 // with the next CG's start: r0 = p0 = -(qx + c + A'y+) and r0'r0 partials.
 // (The mixed path averages the displacement dx, see k_dual.)
 //
-// Adaptive step size (x_save != nullptr): after an accepted step the average
-// takes the step weight of k_step and (x, Q x) are saved as the start of the
-// next attempt; after a rejected one x and Q x go back to the saved start and
-// the CG start is formed from the unchanged A'y, with no product.
+// Adaptive step size (x_save != nullptr), after k_dual's decision and
+// k_commit_m: after an accepted step the average takes the step weight and
+// (x, Q x) are saved as the start of the next attempt; after a rejected one x
+// and Q x go back to the saved start and the CG start is formed from the
+// unchanged A'y, with no product.
 template <int G, class T>
-__global__ void __launch_bounds__(kBlock) k_atv(CsrT<T> At, const T* __restrict__ y, T* aty,
-                                                T* x, T* x_avg, T* qx,
-                                                const T* __restrict__ c, T* r, T* p,
-                                                double* part_r0, unsigned int* ticket,
-                                                const DevState* st, T* x_save, T* qx_save) {
+__global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSm<T>)
+    k_atv(CsrT<T> At, const T* __restrict__ y, T* aty, T* x, T* x_avg, T* qx,
+          const T* __restrict__ c, T* r, T* p, double* part_r0, unsigned int* ticket,
+          const DevState* st, T* x_save, T* qx_save) {
   if (!st->iter_active) return;
   const bool adaptive = x_save != nullptr;
   typename Acc<T>::type acc;
@@ -798,48 +901,9 @@ __global__ void __launch_bounds__(kBlock) k_atv(CsrT<T> At, const T* __restrict_
   store_and_finish_dot(acc, part_r0, ticket);
 }
 
-// Adaptive step size, after k_dual: per-block partials of ||x+ - x||^2 and
-// (x+ - x)'(Q x+ - Q x) from the saved start of the attempt (x_save, qx_save)
-// and the tracked Q x, then the last block to finish combines them with
-// k_dual's m-side partials (stride 2, gm blocks) in a fixed order and takes
-// the Section 4 step decision (step_decide).
-template <class T>
-__global__ void __launch_bounds__(kBlock) k_step(const T* __restrict__ x,
-                                                 const T* __restrict__ x_save,
-                                                 const T* __restrict__ qx,
-                                                 const T* __restrict__ qx_save, int n,
-                                                 double* part_n, const double* part_m, int gm,
-                                                 unsigned int* ticket, DevState* st) {
-  if (!st->iter_active) return;
-  typename Acc<T>::type acc[2];
-  for (long long i = grid_tid(); i < n; i += grid_threads()) {
-    const T dx = x[i] - x_save[i], dq = qx[i] - qx_save[i];
-    acc[0].add_prod(dx, dx);
-    acc[1].add_prod(dx, dq);
-  }
-  block_reduce_ms<0, 2, T>(nullptr, acc, part_n + 2 * size_t(blockIdx.x));
-  __shared__ int s_last;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (s_last) {  // the whole last block (the branch is uniform)
-    __threadfence();
-    double tn[2], tm[2];
-    block_reduce_rows<2>(part_n, gridDim.x, 2, 0u, tn);
-    block_reduce_rows<2>(part_m, gm, 2, 0u, tm);
-    if (threadIdx.x == 0) {
-      step_decide(st, tn[0], tn[1], tm[0], tm[1]);
-      *ticket = 0u;
-      __threadfence();
-    }
-  }
-}
-
-// Adaptive step size, after k_step: an accepted trial becomes y (with its low
-// word) and the A x cache, and enters the running average of y with the step
-// weight; a rejected one is dropped.
+// Adaptive step size, after k_dual's decision: an accepted trial becomes y
+// (with its low word) and the A x cache, and enters the running average of y
+// with the step weight; a rejected one is dropped.
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_commit_m(T* y, T* y_lo, const T* __restrict__ y_new,
                                                      const T* __restrict__ yn_lo, T* ax,

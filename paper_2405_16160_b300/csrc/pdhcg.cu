@@ -194,7 +194,7 @@ struct qp_handle {
   VecSet<float> v32;
   double *part_cg = nullptr, *part_n = nullptr, *part_m = nullptr, *part_rn = nullptr,
          *part_rm = nullptr, *part_pow = nullptr, *part2 = nullptr, *part_r0 = nullptr;
-  double *part_step_n = nullptr, *part_step_m = nullptr;  // adaptive step test partials
+  double* part_step_m = nullptr;  // adaptive step test partials (4 per k_dual block)
   int step_mode = QP_STEP_FIXED;  // step rule of the iteration being launched
   DevState* st = nullptr;
   GridBarrier* bar = nullptr;
@@ -372,21 +372,34 @@ qp_status launch_dual(qp_handle* h) {
   launch_long<T>(h, h->A, it_x(v));
   return dispatch_g(lanes<T>(h->A), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    const bool ad = h->step_mode == QP_STEP_ADAPTIVE;
-    k_dual<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(
-        view<T>(h->A), it_x(v), it_b(v), v.y, v.y_lo, it_ax(v), v.y_avg, v.ya_lo, h->st,
-        ad ? v.y_new : nullptr, ad ? v.yn_lo : nullptr, ad ? v.ax_new : nullptr,
-        ad ? h->part_step_m : nullptr);
+    StepTrial<T> tr;
+    if (h->step_mode == QP_STEP_ADAPTIVE) {
+      tr.y_new = v.y_new;
+      tr.yn_lo = v.yn_lo;
+      tr.ax_new = v.ax_new;
+      tr.x_save = v.x_save;
+      tr.qx_save = v.qx_save;
+      tr.qx = v.qx;
+      tr.n = h->n;
+      tr.part_step = h->part_step_m;
+      tr.ticket = h->ticket;
+    }
+    k_dual<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(view<T>(h->A), it_x(v), it_b(v), v.y,
+                                                      v.y_lo, it_ax(v), v.y_avg, v.ya_lo, h->st,
+                                                      tr);
   });
 }
 
 template <class T>
 qp_status launch_atv(qp_handle* h) {
   VecSet<T>& v = vecs<T>(h);
+  const bool ad = h->step_mode == QP_STEP_ADAPTIVE;
+  if (ad)
+    k_commit_m<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.y, v.y_lo, v.y_new, v.yn_lo, it_ax(v),
+                                                         v.ax_new, v.y_avg, v.ya_lo, h->m, h->st);
   launch_long<T>(h, h->At, v.y);
   return dispatch_g(lanes<T>(h->At), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    const bool ad = h->step_mode == QP_STEP_ADAPTIVE;
     k_atv<G, T><<<h->grid_n, kBlock, 0, h->stream>>>(view<T>(h->At), v.y, v.aty, it_x(v),
                                                      it_x_avg(v), v.qx, v.c, v.r, v.p,
                                                      h->part_r0, h->ticket, h->st,
@@ -460,24 +473,12 @@ void launch_prepare(qp_handle* h) {
                                                     h->ticket, it_x(v), v.x_save, v.qx_save);
 }
 
-// Adaptive step size, between the dual step and A'y: the step test, then the
-// commit (or drop) of the trial y and A x.
-template <class T>
-void launch_step(qp_handle* h) {
-  VecSet<T>& v = vecs<T>(h);
-  k_step<T><<<h->grid_vec, kBlock, 0, h->stream>>>(it_x(v), v.x_save, v.qx, v.qx_save, h->n,
-                                                   h->part_step_n, h->part_step_m, h->grid_m,
-                                                   h->ticket, h->st);
-  k_commit_m<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.y, v.y_lo, v.y_new, v.yn_lo, it_ax(v),
-                                                       v.ax_new, v.y_avg, v.ya_lo, h->m, h->st);
-}
-
-// One inner iteration (with the adaptive step size: one attempt).
+// One inner iteration (with the adaptive step size: one attempt, the step
+// test in k_dual's last block and the commit in k_commit_m and k_atv).
 template <class T>
 qp_status launch_iteration(qp_handle* h, bool coop) {
   QP_TRY(launch_cg<T>(h, coop));
   QP_TRY(launch_dual<T>(h));
-  if (h->step_mode == QP_STEP_ADAPTIVE) launch_step<T>(h);
   QP_TRY(launch_atv<T>(h));
   return QP_OK;
 }
@@ -584,7 +585,6 @@ qp_status enqueue_chunk(qp_handle* h, int iters, bool coop, cudaEvent_t* ev) {
     s = launch_cg<T>(h, coop);
     if (ev) cudaEventRecord(ev[2 * k + 1], h->stream);
     if (s == QP_OK) s = launch_dual<T>(h);
-    if (s == QP_OK && h->step_mode == QP_STEP_ADAPTIVE) launch_step<T>(h);
     if (s == QP_OK) s = launch_atv<T>(h);
   }
   if (s == QP_OK) s = launch_eval<T>(h, 1);
@@ -1043,8 +1043,7 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   QP_TRY(dalloc(h, &h->part_rm, size_t(gmax)));
   QP_TRY(dalloc(h, &h->part_pow, size_t(gmax)));
   QP_TRY(dalloc(h, &h->part2, size_t(2) * gmax));
-  QP_TRY(dalloc(h, &h->part_step_n, size_t(2) * h->grid_vec));
-  QP_TRY(dalloc(h, &h->part_step_m, size_t(2) * h->grid_m));
+  QP_TRY(dalloc(h, &h->part_step_m, size_t(4) * h->grid_m));
   QP_TRY(dalloc(h, &h->st, 1));
   QP_TRY(dalloc(h, &h->bar, 1));
   CUDA_TRY(cudaMallocHost(&h->h_st, sizeof(DevState)));
