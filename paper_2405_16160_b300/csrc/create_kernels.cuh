@@ -8,8 +8,8 @@
 
 namespace pdhcg {
 
-// One warp per row throughout, so a row of any length is read with coalesced
-// loads.
+// The transpose kernels take one warp per row, so a row of any length is
+// read with coalesced loads.
 
 // row_of[k] = i for every entry k of row i.
 __global__ void __launch_bounds__(kBlock) k_row_of_entry(const int32_t* __restrict__ rowptr,
@@ -47,6 +47,25 @@ __device__ __forceinline__ double warp_max_d(double v) {
   return v;
 }
 
+// Rows of the scaling kernels go to warps eight at a time: row base + lane/4
+// to a group of four lanes when it has at most kShortRow entries, and every
+// longer row of the eight to the whole warp afterwards, in row order.  Short
+// rows (the common case) keep all lanes busy; a row of any length is still
+// read with coalesced loads.  A group's four partial values are combined
+// with xor shuffles, so a row's norm does not depend on the launch.
+constexpr int kScaleGroup = 4;
+constexpr int kScaleRowsPerWarp = 32 / kScaleGroup;
+constexpr int kShortRow = 64;
+
+__device__ __forceinline__ double group_combine(double v, bool inf) {
+#pragma unroll
+  for (int o = kScaleGroup / 2; o > 0; o >>= 1) {
+    const double u = shfl_xor(v, o);
+    v = inf ? fmax(v, u) : v + u;
+  }
+  return v;
+}
+
 // Section 4 scaling of K = [[Q, A'], [A, 0]] under the current D = diag(D2,
 // D1): the norm of each row of D K D, the inf-norm for a Ruiz step (inf = 1)
 // or the 1-norm for the Pock-Chambolle step.  Variable rows j read row j of
@@ -55,21 +74,50 @@ __global__ void __launch_bounds__(kBlock) k_scale_norms_n(CsrT<double> Q, CsrT<d
                                                           const double* __restrict__ d1,
                                                           const double* __restrict__ d2,
                                                           double* rn, int inf) {
-  const int lane = threadIdx.x & 31;
-  for (long long j = grid_tid() >> 5; j < Q.rows; j += grid_threads() >> 5) {
-    const double dj = d2[j];
+  const int lane = threadIdx.x & 31, sub = lane & (kScaleGroup - 1);
+  const long long nw = grid_threads() >> 5;
+  for (long long base = (grid_tid() >> 5) * kScaleRowsPerWarp; base < Q.rows;
+       base += nw * kScaleRowsPerWarp) {
+    const int j = int(base) + lane / kScaleGroup;
+    bool long_row = false;
     double r = 0.0, ra = 0.0;
-    for (int k = __ldg(Q.rowptr + j) + lane; k < __ldg(Q.rowptr + j + 1); k += 32) {
-      const double v = (dj * fabs(Q.val[k])) * d2[Q.col[k]];
-      r = inf ? fmax(r, v) : r + v;
+    if (j < Q.rows) {
+      const int qb = __ldg(Q.rowptr + j), qe = __ldg(Q.rowptr + j + 1);
+      const int ab = __ldg(At.rowptr + j), ae = __ldg(At.rowptr + j + 1);
+      long_row = (qe - qb) + (ae - ab) > kShortRow;
+      if (!long_row) {
+        const double dj = d2[j];
+        for (int k = qb + sub; k < qe; k += kScaleGroup) {
+          const double v = (dj * fabs(Q.val[k])) * d2[Q.col[k]];
+          r = inf ? fmax(r, v) : r + v;
+        }
+        for (int k = ab + sub; k < ae; k += kScaleGroup) {
+          const double v = (d1[At.col[k]] * fabs(At.val[k])) * dj;
+          ra = inf ? fmax(ra, v) : ra + v;
+        }
+      }
     }
-    for (int k = __ldg(At.rowptr + j) + lane; k < __ldg(At.rowptr + j + 1); k += 32) {
-      const double v = (d1[At.col[k]] * fabs(At.val[k])) * dj;
-      ra = inf ? fmax(ra, v) : ra + v;
+    r = group_combine(r, inf);
+    ra = group_combine(ra, inf);
+    if (j < Q.rows && !long_row && sub == 0) rn[j] = inf ? fmax(r, ra) : r + ra;
+    unsigned lm = __ballot_sync(0xffffffffu, long_row && sub == 0);
+    while (lm) {
+      const int jj = int(base) + (__ffs(lm) - 1) / kScaleGroup;
+      lm &= lm - 1;
+      const double dj = d2[jj];
+      double s = 0.0, sa = 0.0;
+      for (int k = __ldg(Q.rowptr + jj) + lane; k < __ldg(Q.rowptr + jj + 1); k += 32) {
+        const double v = (dj * fabs(Q.val[k])) * d2[Q.col[k]];
+        s = inf ? fmax(s, v) : s + v;
+      }
+      for (int k = __ldg(At.rowptr + jj) + lane; k < __ldg(At.rowptr + jj + 1); k += 32) {
+        const double v = (d1[At.col[k]] * fabs(At.val[k])) * dj;
+        sa = inf ? fmax(sa, v) : sa + v;
+      }
+      s = inf ? warp_max_d(s) : warp_sum(s);
+      sa = inf ? warp_max_d(sa) : warp_sum(sa);
+      if (lane == 0) rn[jj] = inf ? fmax(s, sa) : s + sa;
     }
-    r = inf ? warp_max_d(r) : warp_sum(r);
-    ra = inf ? warp_max_d(ra) : warp_sum(ra);
-    if (lane == 0) rn[j] = inf ? fmax(r, ra) : r + ra;
   }
 }
 
@@ -77,16 +125,39 @@ __global__ void __launch_bounds__(kBlock) k_scale_norms_m(CsrT<double> A,
                                                           const double* __restrict__ d1,
                                                           const double* __restrict__ d2,
                                                           double* rm, int inf) {
-  const int lane = threadIdx.x & 31;
-  for (long long i = grid_tid() >> 5; i < A.rows; i += grid_threads() >> 5) {
-    const double di = d1[i];
+  const int lane = threadIdx.x & 31, sub = lane & (kScaleGroup - 1);
+  const long long nw = grid_threads() >> 5;
+  for (long long base = (grid_tid() >> 5) * kScaleRowsPerWarp; base < A.rows;
+       base += nw * kScaleRowsPerWarp) {
+    const int i = int(base) + lane / kScaleGroup;
+    bool long_row = false;
     double r = 0.0;
-    for (int k = __ldg(A.rowptr + i) + lane; k < __ldg(A.rowptr + i + 1); k += 32) {
-      const double v = (di * fabs(A.val[k])) * d2[A.col[k]];
-      r = inf ? fmax(r, v) : r + v;
+    if (i < A.rows) {
+      const int b = __ldg(A.rowptr + i), e = __ldg(A.rowptr + i + 1);
+      long_row = e - b > kShortRow;
+      if (!long_row) {
+        const double di = d1[i];
+        for (int k = b + sub; k < e; k += kScaleGroup) {
+          const double v = (di * fabs(A.val[k])) * d2[A.col[k]];
+          r = inf ? fmax(r, v) : r + v;
+        }
+      }
     }
-    r = inf ? warp_max_d(r) : warp_sum(r);
-    if (lane == 0) rm[i] = r;
+    r = group_combine(r, inf);
+    if (i < A.rows && !long_row && sub == 0) rm[i] = r;
+    unsigned lm = __ballot_sync(0xffffffffu, long_row && sub == 0);
+    while (lm) {
+      const int ii = int(base) + (__ffs(lm) - 1) / kScaleGroup;
+      lm &= lm - 1;
+      const double di = d1[ii];
+      double s = 0.0;
+      for (int k = __ldg(A.rowptr + ii) + lane; k < __ldg(A.rowptr + ii + 1); k += 32) {
+        const double v = (di * fabs(A.val[k])) * d2[A.col[k]];
+        s = inf ? fmax(s, v) : s + v;
+      }
+      s = inf ? warp_max_d(s) : warp_sum(s);
+      if (lane == 0) rm[ii] = s;
+    }
   }
 }
 
@@ -99,16 +170,33 @@ __global__ void k_scale_apply(double* d2, const double* __restrict__ rn, int n, 
     d1[i] /= sqrt(rm[i] > 0.0 ? rm[i] : 1.0);
 }
 
-// M_ik <- (dr_i M_ik) dc_k in place.
+// M_ik <- (dr_i M_ik) dc_k in place (rows split as in the norm kernels).
 __global__ void __launch_bounds__(kBlock) k_scale_matrix(CsrT<double> M,
                                                          const double* __restrict__ dr,
                                                          const double* __restrict__ dc,
                                                          double* val) {
-  const int lane = threadIdx.x & 31;
-  for (long long i = grid_tid() >> 5; i < M.rows; i += grid_threads() >> 5) {
-    const double di = dr[i];
-    for (int k = __ldg(M.rowptr + i) + lane; k < __ldg(M.rowptr + i + 1); k += 32)
-      val[k] = (di * val[k]) * dc[M.col[k]];
+  const int lane = threadIdx.x & 31, sub = lane & (kScaleGroup - 1);
+  const long long nw = grid_threads() >> 5;
+  for (long long base = (grid_tid() >> 5) * kScaleRowsPerWarp; base < M.rows;
+       base += nw * kScaleRowsPerWarp) {
+    const int i = int(base) + lane / kScaleGroup;
+    bool long_row = false;
+    if (i < M.rows) {
+      const int b = __ldg(M.rowptr + i), e = __ldg(M.rowptr + i + 1);
+      long_row = e - b > kShortRow;
+      if (!long_row) {
+        const double di = dr[i];
+        for (int k = b + sub; k < e; k += kScaleGroup) val[k] = (di * val[k]) * dc[M.col[k]];
+      }
+    }
+    unsigned lm = __ballot_sync(0xffffffffu, long_row && sub == 0);
+    while (lm) {
+      const int ii = int(base) + (__ffs(lm) - 1) / kScaleGroup;
+      lm &= lm - 1;
+      const double di = dr[ii];
+      for (int k = __ldg(M.rowptr + ii) + lane; k < __ldg(M.rowptr + ii + 1); k += 32)
+        val[k] = (di * val[k]) * dc[M.col[k]];
+    }
   }
 }
 

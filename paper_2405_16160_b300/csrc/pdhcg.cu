@@ -833,8 +833,10 @@ qp_status device_scaling(qp_handle* h, int ruiz_iters) {
     step(upload(h, d1, ones.data(), size_t(m) * sizeof(double)));
     step(upload(h, d2, ones.data(), size_t(n) * sizeof(double)));
     const int wave = h->num_sms * 8;
+    // eight rows per warp (see k_scale_norms_n)
     auto warp_grid = [&](int64_t rows) {
-      return int(std::max<int64_t>(1, std::min<int64_t>((rows + kBlock / 32 - 1) / (kBlock / 32),
+      const int64_t per_block = int64_t(kBlock / 32) * kScaleRowsPerWarp;
+      return int(std::max<int64_t>(1, std::min<int64_t>((rows + per_block - 1) / per_block,
                                                         wave)));
     };
     const CsrT<double> Q = view<double>(h->Q), A = view<double>(h->A), At = view<double>(h->At);
