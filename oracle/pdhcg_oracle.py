@@ -59,6 +59,15 @@ path implements the same one):
   eta is fixed); the CG precision epsilon advances once per accepted
   iteration; eval_freq and max_iter count attempts (they equal iterations
   with the fixed step).
+* Augmented penalty (Section 4, optional ``penalty``).  With G x = q the
+  equality rows, the objective gains rho/2 ||G x - q||^2, i.e. the iteration
+  runs on Q + rho G'G and c - rho G'q (the constant is dropped), with
+  rho = 0.1 ||Q||_2 / ||G'G||_2; both norms by 30 power iterations from the
+  normalised all-ones vector (||G'G||_2 = ||G||_2^2).  No equality rows, or
+  ||G'G||_2 <= eps_zero, gives rho = 0.  The penalty and its gradient vanish
+  where G x = q, so the penalised problem has the same KKT points, and every
+  relKKT (termination, restarts, the CG precision) is taken on the problem
+  as given.  With ``scale`` the scaling is computed on the penalised K.
 * Preprocessing (Section 4, optional ``scale``): D1 (constraints) and D2
   (variables) from 10 Ruiz equilibration steps and one Pock-Chambolle step
   (alpha = 1) on the symmetric K = [[Q, A'], [A, 0]]; the iteration runs on
@@ -238,6 +247,44 @@ def spectral_norm(A: sp.csr_matrix, iters: int = 30) -> float:
     return math.sqrt(lam)
 
 
+def symmetric_norm(Q: sp.csr_matrix, iters: int = 30) -> float:
+    """||Q||_2 of a symmetric PSD Q by power iteration on Q, started at ones/sqrt(n):
+    lambda_t = ||Q v_{t-1}||_2, v_t = Q v_{t-1} / lambda_t; returns lambda_iters."""
+    n = Q.shape[0]
+    if n == 0:
+        return 0.0
+    v = np.ones(n) / math.sqrt(n)
+    lam = 0.0
+    for _ in range(iters):
+        w = Q @ v
+        lam = float(np.linalg.norm(w))
+        if lam == 0.0:
+            return 0.0
+        v = w / lam
+    return lam
+
+
+# --------------------------------------------------------------------------
+# Augmented penalty (Section 4): rho/2 ||G x - q||^2 on the equality rows.
+# --------------------------------------------------------------------------
+def penalty_rho(P: OracleProblem, iters: int = 30, eps_zero: float = 1e-10) -> float:
+    """rho = 0.1 ||Q||_2 / ||G'G||_2 with G the equality rows (0 without them)."""
+    if P.m_eq == 0:
+        return 0.0
+    g2 = spectral_norm(P.A[:P.m_eq], iters) ** 2
+    return 0.1 * symmetric_norm(P.Q, iters) / g2 if g2 > eps_zero else 0.0
+
+
+def penalize(P: OracleProblem, rho: float) -> OracleProblem:
+    """The problem with rho/2 ||G x - q||^2 added: Q + rho G'G, c - rho G'q."""
+    if rho == 0.0 or P.m_eq == 0:
+        return P
+    G = P.A[:P.m_eq]
+    Qp = (P.Q + rho * (G.T @ G)).tocsr()
+    Qp.sum_duplicates()
+    return OracleProblem(Qp, P.A, P.c - rho * (G.T @ P.b[:P.m_eq]), P.b, P.m_eq)
+
+
 # --------------------------------------------------------------------------
 # Inexact primal solve: CG on (Q + I/tau) x = rhs (Section 2).
 # --------------------------------------------------------------------------
@@ -308,6 +355,7 @@ class OracleOptions:
     eta: float = 0.0  # <= 0: 1/(2||A||)
     scale: bool = False  # Section 4 preprocessing (Ruiz x10 + Pock-Chambolle)
     step_mode: int = STEP_FIXED  # STEP_ADAPTIVE: the Section 4 adaptive step size
+    penalty: bool = False  # Section 4 augmented penalty rho/2 ||Gx - q||^2 on the equality rows
     step_reduction_exp: float = 0.3
     step_growth_exp: float = 0.6
 
@@ -504,17 +552,19 @@ def solve(P: OracleProblem, o: OracleOptions | None = None,
           state: OracleState | None = None, step_hook=None) -> OracleResult:
     """Restarted PDHCG (Algorithm 1 with the Section 4 heuristics).
 
-    With ``o.scale`` the iteration runs on the scaled problem (``state`` and
-    ``step_hook`` then see scaled iterates), relKKT is taken on P at the
-    unscaled iterate, and the returned x, y are unscaled.
+    With ``o.penalty`` the iteration runs on the penalised problem; with
+    ``o.scale`` on the scaled one (``state`` and ``step_hook`` then see scaled
+    iterates).  relKKT is always taken on P at the unscaled iterate, and the
+    returned x, y are unscaled.
     """
     o = o or OracleOptions()
     t0 = time.perf_counter()
+    Pp = penalize(P, penalty_rho(P, o.power_iters, o.eps_zero)) if o.penalty else P
     if o.scale:
-        d1, d2 = diagonal_scaling(P)
-        Pi = scale_problem(P, d1, d2)
+        d1, d2 = diagonal_scaling(Pp)
+        Pi = scale_problem(Pp, d1, d2)
     else:
-        d1, d2, Pi = np.ones(P.m), np.ones(P.n), P
+        d1, d2, Pi = np.ones(P.m), np.ones(P.n), Pp
     kkt = lambda x, y: relkkt(P, d2 * x, d1 * y)
     st = state.copy() if state is not None else initial_state(Pi, o)
     trace: list = []

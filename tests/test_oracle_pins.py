@@ -9,7 +9,10 @@ that a pin catches each one.  The adaptive step size of Section 4 is pinned
 by its closed form at the top singular pair of A, a lower bound that follows
 from Cauchy-Schwarz and AM-GM, PDLP's update rule worked by hand, the
 accept/reject invariants, step-weighted averages and the closed-form and
-brute-force solutions reached with it.
+brute-force solutions reached with it.  The augmented penalty of Section 4
+is pinned by the exact norms of a diagonal Q and a rank-one G'G, the
+expansion of rho/2 ||Gx - q||^2, and the same closed-form and brute-force
+solutions reached with it on.
 """
 import itertools
 import json
@@ -206,13 +209,15 @@ def test_solver_diagonal_box_closed_form(step):
 
 
 @pytest.mark.parametrize("step", [O.STEP_FIXED, O.STEP_ADAPTIVE])
-def test_solver_equality_hyperplane_closed_form(step):
+@pytest.mark.parametrize("penalty", [False, True])
+def test_solver_equality_hyperplane_closed_form(step, penalty):
     rng = np.random.default_rng(8)
     n = 30
     a = rng.standard_normal(n)
     c = rng.standard_normal(n)
     beta = 0.7
-    res = O.solve(_prob(np.eye(n), a[None, :], c, [beta], m_eq=1), _opts(step_mode=step))
+    res = O.solve(_prob(np.eye(n), a[None, :], c, [beta], m_eq=1),
+                  _opts(step_mode=step, penalty=penalty))
     assert res.termination == O.SOLVED
     xs = -c + a * (beta + a @ c) / (a @ a)
     lam = -(beta + a @ c) / (a @ a)
@@ -222,7 +227,8 @@ def test_solver_equality_hyperplane_closed_form(step):
 
 @pytest.mark.parametrize("step", [O.STEP_FIXED, O.STEP_ADAPTIVE])
 @pytest.mark.parametrize("seed,n,m,m_eq", [(10, 4, 6, 0), (11, 5, 8, 0), (12, 6, 7, 2), (13, 3, 8, 1)])
-def test_solver_matches_active_set_brute_force(seed, n, m, m_eq, step):
+@pytest.mark.parametrize("penalty", [False, True])
+def test_solver_matches_active_set_brute_force(seed, n, m, m_eq, step, penalty):
     rng = np.random.default_rng(seed)
     Qd = _rand_spd(rng, n, 10.0)
     Ad = rng.standard_normal((m, n))
@@ -230,7 +236,7 @@ def test_solver_matches_active_set_brute_force(seed, n, m, m_eq, step):
     x0 = rng.standard_normal(n)
     b = Ad @ x0 + np.concatenate([np.zeros(m_eq), rng.uniform(0, 0.5, m - m_eq)])
     xs, ys = brute_force_qp(Qd, Ad, c, b, m_eq)
-    res = O.solve(_prob(Qd, Ad, c, b, m_eq), _opts(step_mode=step))
+    res = O.solve(_prob(Qd, Ad, c, b, m_eq), _opts(step_mode=step, penalty=penalty))
     assert res.termination == O.SOLVED
     assert np.linalg.norm(res.x - xs) <= 1e-6 * (1 + np.linalg.norm(xs))
     fs = 0.5 * xs @ Qd @ xs + c @ xs
@@ -497,7 +503,8 @@ def test_ruiz_equilibrates_rows():
 
 @pytest.mark.parametrize("step", [O.STEP_FIXED, O.STEP_ADAPTIVE])
 @pytest.mark.parametrize("seed,n,m,m_eq", [(10, 4, 6, 0), (12, 6, 7, 2), (13, 3, 8, 1)])
-def test_scaled_solver_matches_active_set_brute_force(seed, n, m, m_eq, step):
+@pytest.mark.parametrize("penalty", [False, True])
+def test_scaled_solver_matches_active_set_brute_force(seed, n, m, m_eq, step, penalty):
     rng = np.random.default_rng(seed)
     dsc = np.exp(rng.uniform(-2, 2, n))  # badly scaled but PSD (Eq. (1)): D Q D + 0.1 I
     Qd = dsc[:, None] * _rand_spd(rng, n, 10.0) * dsc[None, :] + np.eye(n) * 0.1
@@ -505,7 +512,7 @@ def test_scaled_solver_matches_active_set_brute_force(seed, n, m, m_eq, step):
     c = rng.standard_normal(n) * 3
     b = Ad @ rng.standard_normal(n) + np.concatenate([np.zeros(m_eq), rng.uniform(0, 0.5, m - m_eq)])
     xs, ys = brute_force_qp(Qd, Ad, c, b, m_eq)
-    res = O.solve(_prob(Qd, Ad, c, b, m_eq), _opts(scale=True, step_mode=step))
+    res = O.solve(_prob(Qd, Ad, c, b, m_eq), _opts(scale=True, step_mode=step, penalty=penalty))
     assert res.termination == O.SOLVED
     assert np.linalg.norm(res.x - xs) <= 1e-6 * (1 + np.linalg.norm(xs))
     assert O.relkkt(_prob(Qd, Ad, c, b, m_eq), res.x, res.y).relkkt <= 1e-10
@@ -680,3 +687,41 @@ def test_adaptive_step_cuts_iterations_on_a_portfolio_qp():
     adaptive = O.solve(P, _opts(tol=1e-4, step_mode=O.STEP_ADAPTIVE))
     assert fixed.termination == adaptive.termination == O.SOLVED
     assert adaptive.state.attempts < 0.7 * fixed.iterations
+
+
+# ---------------------------------------------------------------- augmented penalty (Section 4)
+def test_symmetric_norm_of_a_diagonal_q():
+    d = np.array([1.0, 0.1, 0.2, 5.0, -0.3])  # |5| dominates: (1/5)^30 below rounding
+    assert O.symmetric_norm(sp.csr_matrix(np.diag(np.abs(d))), 30) == pytest.approx(5.0, rel=1e-15)
+
+
+def test_penalty_rho_closed_form():
+    """Q = qI and one equality row g: ||Q||_2 = q, G'G = g g' has norm ||g||^2,
+    so rho = 0.1 q / ||g||^2; without equality rows rho = 0."""
+    rng = np.random.default_rng(40)
+    n, q = 9, 3.7
+    g = rng.standard_normal(n)
+    Ad = np.vstack([g, rng.standard_normal((3, n))])
+    P = _prob(q * np.eye(n), Ad, np.zeros(n), np.zeros(4), m_eq=1)
+    assert O.penalty_rho(P) == pytest.approx(0.1 * q / (g @ g), rel=1e-12)
+    assert O.penalty_rho(_prob(q * np.eye(n), Ad, np.zeros(n), np.zeros(4), m_eq=0)) == 0.0
+
+
+def test_penalized_objective_is_the_original_plus_the_penalty():
+    """1/2 x'Q^x + c^'x = 1/2 x'Qx + c'x + rho/2 ||Gx - q||^2 - rho/2 ||q||^2 for every x."""
+    rng = np.random.default_rng(41)
+    n, m, m_eq = 8, 6, 3
+    Qd = _rand_spd(rng, n, 10.0)
+    Ad = rng.standard_normal((m, n))
+    c, b = rng.standard_normal(n), rng.standard_normal(m)
+    P = _prob(Qd, Ad, c, b, m_eq)
+    rho = 0.37
+    Pp = O.penalize(P, rho)
+    for _ in range(5):
+        x = rng.standard_normal(n)
+        f = 0.5 * x @ Qd @ x + c @ x
+        fp = 0.5 * x @ (Pp.Q @ x) + Pp.c @ x
+        r = Ad[:m_eq] @ x - b[:m_eq]
+        assert fp == pytest.approx(f + 0.5 * rho * (r @ r) - 0.5 * rho * (b[:m_eq] @ b[:m_eq]),
+                                   rel=1e-12, abs=1e-12)
+    assert np.array_equal(Pp.A.toarray(), P.A.toarray()) and np.array_equal(Pp.b, P.b)
