@@ -78,6 +78,15 @@ enum { QP_STEP_FIXED = 0, QP_STEP_ADAPTIVE = 1 };
                                        steps and one Pock-Chambolle step on [[Q, A'], [A, 0]];
                                        the solver iterates on D2 Q D2, D1 A D2, D2 c, D1 b and
                                        measures relKKT on the original problem */
+#define QP_CREATE_PENALTY 4u        /* Section 4 augmented penalty on the m_eq equality rows
+                                       G x = q: the iteration runs on Q + rho G'G and
+                                       c - rho G'q with rho = 0.1 ||Q||_2 / ||G'G||_2 (30 power
+                                       iterations each; rho = 0 without equality rows); the
+                                       scaling, when asked for, is computed on the penalised
+                                       problem, and relKKT is always measured on the problem as
+                                       given (the two share their KKT points).  qp_create
+                                       returns QP_ERR_INVALID_ARG when G'G would take more than
+                                       2^28 products (a dense equality row makes Q dense). */
 
 /* debug_flags (fault injection; never used by default) */
 #define QP_DEBUG_BARRIER_NEVER_RELEASES 1u /* the CG kernel's first grid barrier is never
@@ -289,6 +298,10 @@ qp_status qp_evaluate(qp_handle* h, double kkt_cur[6], double kkt_avg[6]);
 
 /* Estimate ||A||_2 by `iters` power iterations on A'A from ones/sqrt(n). */
 qp_status qp_norm_A(qp_handle* h, int32_t iters, double* out);
+
+/* The penalty weight rho of QP_CREATE_PENALTY (Section 4, augmented penalty);
+ * 0 when the flag was not given or the problem has no equality rows. */
+qp_status qp_get_penalty(const qp_handle* h, double* rho);
 
 /* ------------------------------------------------- allocation-free variant */
 

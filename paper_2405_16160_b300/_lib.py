@@ -21,6 +21,7 @@ RESTART_ADAPTIVE, RESTART_NONE = 0, 2
 STEP_FIXED, STEP_ADAPTIVE = 0, 1
 CREATE_CHECK_SYMMETRY = 1
 CREATE_SCALE = 2
+CREATE_PENALTY = 4
 DEBUG_BARRIER_NEVER_RELEASES = 1
 QP_NORM_A_STATIC_MAX_DOUBLES = 1 << 20  # capacity of qp_norm_A_static's static scratch
 
@@ -127,6 +128,7 @@ SIGNATURES = [
     ("qp_iterate", c_int32, [_H, POINTER(QPOptionsC), c_int64]),
     ("qp_evaluate", c_int32, [_H, _F64P, _F64P]),
     ("qp_norm_A", c_int32, [_H, c_int32, _F64P]),
+    ("qp_get_penalty", c_int32, [_H, _F64P]),
     ("qp_norm_A_static", c_int32, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     ("qp_csr_validate", c_int32, [c_int32, c_int32, _I32P, _I32P, _F64P]),

@@ -218,4 +218,123 @@ bool csr_is_symmetric(const HostCsr& M, double rtol) {
   return true;
 }
 
+namespace {
+
+double norm2(const std::vector<double>& v) {
+  double s = 0.0;
+  for (double x : v) s += x * x;
+  return std::sqrt(s);
+}
+
+// y = M v over rows [0, rows) of a canonical CSR view.
+void spmv(const CsrView& M, int32_t rows, const std::vector<double>& v, std::vector<double>* y) {
+  for (int32_t i = 0; i < rows; ++i) {
+    double s = 0.0;
+    for (int32_t k = M.rowptr[i]; k < M.rowptr[i + 1]; ++k) s += M.val[k] * v[size_t(M.col[k])];
+    (*y)[size_t(i)] = s;
+  }
+}
+
+}  // namespace
+
+bool csr_penalize(const CsrView& Q, const CsrView& A, int32_t m_eq, const double* c,
+                  const double* b, int iters, double eps_zero, int64_t max_products,
+                  HostCsr* Qp, std::vector<double>* cp, double* rho, std::string* why) {
+  const int32_t n = Q.rows;
+  *rho = 0.0;
+  cp->assign(c, c + n);
+  if (m_eq <= 0 || n == 0) return true;
+  int64_t products = 0;
+  for (int32_t r = 0; r < m_eq; ++r) {
+    const int64_t len = A.rowptr[r + 1] - A.rowptr[r];
+    products += len * len;
+  }
+  if (products > max_products) {
+    *why = "the augmented penalty would make Q dense: G'G needs " + std::to_string(products) +
+           " products (limit " + std::to_string(max_products) + ")";
+    return false;
+  }
+  // ||Q||_2 and ||G'G||_2 by power iteration from ones/sqrt(n)
+  const double v0 = 1.0 / std::sqrt(double(n));
+  std::vector<double> v(static_cast<size_t>(n), v0);
+  std::vector<double> w(static_cast<size_t>(n), 0.0);
+  std::vector<double> u(static_cast<size_t>(m_eq), 0.0);
+  double lam_q = 0.0;
+  for (int t = 0; t < iters; ++t) {
+    spmv(Q, n, v, &w);
+    lam_q = norm2(w);
+    if (lam_q == 0.0) break;
+    for (int32_t j = 0; j < n; ++j) v[size_t(j)] = w[size_t(j)] / lam_q;
+  }
+  std::fill(v.begin(), v.end(), v0);
+  double lam_g = 0.0;
+  for (int t = 0; t < iters; ++t) {
+    spmv(A, m_eq, v, &u);  // u = G v
+    std::fill(w.begin(), w.end(), 0.0);
+    for (int32_t r = 0; r < m_eq; ++r)  // w = G'u
+      for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k)
+        w[size_t(A.col[k])] += A.val[k] * u[size_t(r)];
+    lam_g = norm2(w);
+    if (lam_g == 0.0) break;
+    for (int32_t j = 0; j < n; ++j) v[size_t(j)] = w[size_t(j)] / lam_g;
+  }
+  if (!(lam_g > eps_zero)) return true;
+  *rho = 0.1 * lam_q / lam_g;
+  // G' (rows of G by column), then Qp row j = Q row j + rho sum_r g_rj G_r
+  std::vector<int32_t> tp(size_t(n) + 1, 0);
+  for (int32_t k = 0; k < A.rowptr[m_eq]; ++k) ++tp[size_t(A.col[k]) + 1];
+  for (int32_t j = 0; j < n; ++j) tp[size_t(j) + 1] += tp[size_t(j)];
+  std::vector<int32_t> trow(size_t(A.rowptr[m_eq])), fill(tp.begin(), tp.end() - 1);
+  std::vector<double> tval(trow.size());
+  for (int32_t r = 0; r < m_eq; ++r)
+    for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) {
+      const int32_t e = fill[size_t(A.col[k])]++;
+      trow[size_t(e)] = r;
+      tval[size_t(e)] = A.val[k];
+    }
+  for (int32_t j = 0; j < n; ++j) {  // c - rho G'q
+    double s = 0.0;
+    for (int32_t e = tp[size_t(j)]; e < tp[size_t(j) + 1]; ++e)
+      s += tval[size_t(e)] * b[size_t(trow[size_t(e)])];
+    (*cp)[size_t(j)] = c[j] - *rho * s;
+  }
+  Qp->rows = Qp->cols = n;
+  Qp->rowptr.assign(size_t(n) + 1, 0);
+  Qp->col.clear();
+  Qp->val.clear();
+  std::vector<double> gg(size_t(n), 0.0), qv(size_t(n), 0.0);
+  std::vector<int32_t> mark(size_t(n), -1), touched;
+  for (int32_t j = 0; j < n; ++j) {
+    touched.clear();
+    for (int32_t k = Q.rowptr[j]; k < Q.rowptr[j + 1]; ++k) {
+      const int32_t col = Q.col[k];
+      mark[size_t(col)] = j;
+      touched.push_back(col);
+      qv[size_t(col)] = Q.val[k];
+      gg[size_t(col)] = 0.0;
+    }
+    for (int32_t e = tp[size_t(j)]; e < tp[size_t(j) + 1]; ++e) {
+      const int32_t r = trow[size_t(e)];
+      const double g = tval[size_t(e)];
+      for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) {
+        const int32_t col = A.col[k];
+        if (mark[size_t(col)] != j) {
+          mark[size_t(col)] = j;
+          touched.push_back(col);
+          qv[size_t(col)] = 0.0;
+          gg[size_t(col)] = 0.0;
+        }
+        gg[size_t(col)] += g * A.val[k];
+      }
+    }
+    std::sort(touched.begin(), touched.end());
+    for (int32_t col : touched) {
+      Qp->col.push_back(col);
+      Qp->val.push_back(qv[size_t(col)] + *rho * gg[size_t(col)]);
+    }
+    Qp->rowptr[size_t(j) + 1] = int32_t(Qp->col.size());
+  }
+  return true;
+}
+
 }  // namespace pdhcg

@@ -52,4 +52,16 @@ void csr_transpose(int32_t rows, int32_t cols, const int32_t* rowptr, const int3
 // True when the canonical square matrix M satisfies |M_ij - M_ji| <= rtol * max|M|.
 bool csr_is_symmetric(const HostCsr& M, double rtol);
 
+// Section 4 augmented penalty on the equality rows G (the first m_eq rows of
+// the canonical A): rho = 0.1 ||Q||_2 / ||G'G||_2, each norm from `iters`
+// power iterations started at ones/sqrt(n) (||Q v|| for the symmetric Q,
+// ||G'G v|| for G'G), and rho = 0 when ||G'G||_2 <= eps_zero.  Then
+// Qp = Q + rho G'G (canonical: every entry Q_jk + rho sum_r g_rj g_rk) and
+// cp = c - rho G'q with q the first m_eq entries of b.  Returns false with
+// *why when G'G would take more than max_products products (sum over the
+// equality rows of their length squared: a dense row makes G'G dense).
+bool csr_penalize(const CsrView& Q, const CsrView& A, int32_t m_eq, const double* c,
+                  const double* b, int iters, double eps_zero, int64_t max_products,
+                  HostCsr* Qp, std::vector<double>* cp, double* rho, std::string* why);
+
 }  // namespace pdhcg

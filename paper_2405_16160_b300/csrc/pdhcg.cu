@@ -152,6 +152,9 @@ struct VecSet {
   // form, and Q x) and the trial y, its low word (FP32 set only) and A x.
   T *x_save = nullptr, *qx_save = nullptr;
   T *y_new = nullptr, *yn_lo = nullptr, *ax_new = nullptr;
+  // Augmented penalty: the problem's own c (the iteration's c is c - rho G'q)
+  // and the products Q x, Q x~ with the problem's own Q, for relKKT.
+  T *ce = nullptr, *qxe = nullptr, *qxae = nullptr;
 };
 
 // The vectors the per-iteration kernels read as x, x~, A x and b: the
@@ -190,6 +193,9 @@ struct qp_handle {
   bool has_alloc = false;
   int32_t n = 0, m = 0, m_eq = 0;
   DevMat Q, A, At;
+  DevMat Qe;            // with QP_CREATE_PENALTY: the problem's own Q (Q holds Q + rho G'G)
+  bool penalty = false;  // rho > 0
+  double rho = 0.0;
   VecSet<double> v64;
   VecSet<float> v32;
   double *part_cg = nullptr, *part_n = nullptr, *part_m = nullptr, *part_rn = nullptr,
@@ -437,8 +443,16 @@ qp_status launch_eval(qp_handle* h, int mode) {
   QP_TRY(launch_spmv<T>(h, h->Q, v.x, v.qx, nullptr, h->grid_n));
   QP_TRY(launch_spmv<T>(h, h->Q, v.x_avg, v.qx_avg, nullptr, h->grid_n));
   QP_TRY(launch_spmv<T>(h, h->A, v.x_avg, v.ax_avg, nullptr, h->grid_m));
-  k_kkt_n<T><<<h->grid_n, kBlock, 0, h->stream>>>(v.x, v.x_avg, v.qx, v.qx_avg, v.aty,
-                                                  v.aty_avg, v.c, v.inv_d2, h->n, h->part_n);
+  if (h->penalty) {
+    // relKKT of the problem as given: its own Q and c
+    QP_TRY(launch_spmv<T>(h, h->Qe, v.x, v.qxe, nullptr, h->grid_n));
+    QP_TRY(launch_spmv<T>(h, h->Qe, v.x_avg, v.qxae, nullptr, h->grid_n));
+    k_kkt_n<T><<<h->grid_n, kBlock, 0, h->stream>>>(v.x, v.x_avg, v.qxe, v.qxae, v.aty,
+                                                    v.aty_avg, v.ce, v.inv_d2, h->n, h->part_n);
+  } else {
+    k_kkt_n<T><<<h->grid_n, kBlock, 0, h->stream>>>(v.x, v.x_avg, v.qx, v.qx_avg, v.aty,
+                                                    v.aty_avg, v.c, v.inv_d2, h->n, h->part_n);
+  }
   k_kkt_m<T><<<h->grid_m, kBlock, 0, h->stream>>>(v.ax, v.ax_avg, v.b, v.y, v.y_avg, v.inv_d1,
                                                   h->m, h->m_eq, h->part_m);
   k_control<<<1, kBlock, 0, h->stream>>>(h->part_n, h->grid_n, h->part_m, h->grid_m, h->st, mode);
@@ -853,6 +867,11 @@ qp_status device_scaling(qp_handle* h, int ruiz_iters) {
       k_scale_vector<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.b, d1, h->v64.inv_d1, m);
     }
     k_scale_vector<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.c, d2, h->v64.inv_d2, n);
+    if (h->penalty) {  // the problem's own Q and c, for relKKT, under the same scaling
+      k_scale_matrix<<<warp_grid(n), kBlock, 0, h->stream>>>(view<double>(h->Qe), d2, d2,
+                                                              h->Qe.val);
+      k_scale_vector<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.ce, d2, h->v64.inv_d2, n);
+    }
     convert(h, h->v64.inv_d1, h->v32.inv_d1, m);
     convert(h, h->v64.inv_d2, h->v32.inv_d2, n);
     h->d1.resize(size_t(m));
@@ -976,6 +995,25 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
     Ac_ = csr_canonical(m, n, Ar, Ac, Av);
     Ah = view_of(Ac_);
   }
+  // Section 4 augmented penalty: the iteration's Q and c; the problem's own
+  // ones stay for relKKT.
+  HostCsr Qpen;
+  std::vector<double> cpen;
+  const CsrView Qown = Qh;
+  const double* c_iter = c;
+  if ((flags & QP_CREATE_PENALTY) && m_eq > 0) {
+    std::string why;
+    if (!csr_penalize(Qh, Ah, m_eq, c, b, 30, 1e-10, int64_t(1) << 28, &Qpen, &cpen, &h->rho,
+                      &why)) {
+      set_error("%s", why.c_str());
+      return QP_ERR_INVALID_ARG;
+    }
+    if (h->rho > 0.0) {
+      h->penalty = true;
+      Qh = view_of(Qpen);
+      c_iter = cpen.data();
+    }
+  }
   h->n = n;
   h->m = m;
   h->m_eq = m_eq;
@@ -987,12 +1025,18 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   // Q and A go to the device as given; A' is built there.
   QP_TRY(upload_csr(h, &h->Q, Qh));
   QP_TRY(upload_csr(h, &h->A, Ah));
+  if (h->penalty) QP_TRY(upload_csr(h, &h->Qe, Qown));
   std::vector<int32_t> t_rowptr;
   QP_TRY(device_transpose(h, n, &t_rowptr));
   QP_TRY(alloc_vecs<double>(h));
   QP_TRY(alloc_vecs<float>(h));
   const size_t N = size_t(n), M = size_t(m);
-  QP_TRY(upload(h, h->v64.c, c, N * sizeof(double)));
+  QP_TRY(upload(h, h->v64.c, c_iter, N * sizeof(double)));
+  if (h->penalty) {
+    for (double** p : {&h->v64.ce, &h->v64.qxe, &h->v64.qxae}) QP_TRY(dalloc(h, p, N));
+    for (float** p : {&h->v32.ce, &h->v32.qxe, &h->v32.qxae}) QP_TRY(dalloc(h, p, N));
+    QP_TRY(upload(h, h->v64.ce, c, N * sizeof(double)));
+  }
   QP_TRY(upload(h, h->v64.b, b, M * sizeof(double)));
   // Section 4 preprocessing: the solver works on D2 Q D2, D1 A D2, D2 c, D1 b.
   h->scaled = (flags & QP_CREATE_SCALE) != 0;
@@ -1005,10 +1049,14 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   QP_TRY(finish_matrix(h, &h->Q, Qh.rowptr));
   QP_TRY(finish_matrix(h, &h->A, Ah.rowptr));
   QP_TRY(finish_matrix(h, &h->At, t_rowptr.data()));
+  if (h->penalty) {
+    QP_TRY(finish_matrix(h, &h->Qe, Qown.rowptr));
+    convert(h, h->v64.ce, h->v32.ce, n);
+  }
   convert(h, h->v64.c, h->v32.c, n);
   convert(h, h->v64.b, h->v32.b, m);
 
-  const int g_n = std::max({h->Q.G64, h->At.G64, h->Q.G32, h->At.G32});
+  const int g_n = std::max({h->Q.G64, h->At.G64, h->Q.G32, h->At.G32, h->Qe.G64, h->Qe.G32});
   const int g_m = std::max(h->A.G64, h->A.G32);
   h->grid_n = blocks_for_rows(std::max(n, 1), g_n, wave);
   h->grid_m = blocks_for_rows(std::max(m, 1), g_m, wave);
@@ -1646,6 +1694,12 @@ qp_status qp_evaluate(qp_handle* h, double kkt_cur[6], double kkt_avg[6]) {
     if (kkt_avg) kkt_avg[k] = h->h_st->kkt_avg[k];
   }
   return end_call(h);
+}
+
+qp_status qp_get_penalty(const qp_handle* h, double* rho) {
+  if (!h || !rho) return QP_ERR_INVALID_ARG;
+  *rho = h->rho;
+  return QP_OK;
 }
 
 qp_status qp_norm_A(qp_handle* h, int32_t iters, double* out) {

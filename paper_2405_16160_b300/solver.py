@@ -67,7 +67,7 @@ class QPSolver:
     """
 
     def __init__(self, inst, torch_memory: bool = True, check_symmetry: bool = False,
-                 scale: bool = False):
+                 scale: bool = False, penalty: bool = False):
         self.lib = L.load_library()
         self.n, self.m, self.m_eq = int(inst.n), int(inst.m), int(inst.m_eq)
         self._keep = []
@@ -84,7 +84,8 @@ class QPSolver:
                                 _ptr(c, c_double), _ptr(b, c_double),
                                 byref(ctx) if ctx is not None else None,
                                 (L.CREATE_CHECK_SYMMETRY if check_symmetry else 0)
-                                | (L.CREATE_SCALE if scale else 0))
+                                | (L.CREATE_SCALE if scale else 0)
+                                | (L.CREATE_PENALTY if penalty else 0))
         L.check(st, "qp_create")
         self.h = h
         self._ctx = ctx
@@ -186,6 +187,11 @@ class QPSolver:
     def norm_A(self, iters: int = 30) -> float:
         out = c_double()
         L.check(self.lib.qp_norm_A(self.h, int(iters), byref(out)), "qp_norm_A")
+        return out.value
+
+    def penalty_rho(self) -> float:
+        out = c_double()
+        L.check(self.lib.qp_get_penalty(self.h, byref(out)), "qp_get_penalty")
         return out.value
 
     def close(self) -> None:

@@ -666,3 +666,60 @@ def test_full_size_scaled_adaptive_step_matches_oracle_trace():
         xm, ym = s.solution()
         assert mixed["termination"] == L.TERM_SOLVED
         assert O.relkkt(P, xm, ym).relkkt <= 1e-4
+
+
+# ------------------------------------------------- Section 4 augmented penalty
+# QP_CREATE_PENALTY: the iteration runs on Q + rho G'G and c - rho G'q
+# (G x = q the equality rows), relKKT is measured on the problem as given.
+PENALTY_CASES = [("dense_small_eq", 1e-6), ("ragged_eq", 1e-4), ("all_equalities", 1e-6)]
+
+
+@pytest.mark.parametrize("name,tol", PENALTY_CASES)
+@pytest.mark.parametrize("scale", [False, True])
+def test_penalty_matches_oracle(name, tol, scale):
+    inst = CASES[name]()
+    P = O.problem_from_instance(inst)
+    ores = O.solve(P, O.OracleOptions(tol=tol, penalty=True, scale=scale))
+    with QPSolver(inst, penalty=True, scale=scale) as s:
+        assert s.penalty_rho() == pytest.approx(O.penalty_rho(P), rel=1e-12)
+        info = s.solve(tol=tol)
+        x, y = s.solution()
+        assert ores.termination == O.SOLVED and info["termination"] == L.TERM_SOLVED
+        rescored = O.relkkt(P, x, y)  # the problem as given
+        assert rescored.relkkt <= tol
+        assert info["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-12)
+        assert rescored.primal_obj == pytest.approx(ores.kkt.primal_obj, rel=1e-4, abs=1e-8)
+        assert info["iterations"] == ores.iterations and info["restarts"] == ores.restarts
+        assert info["cg_steps"] == ores.cg_steps
+        assert _relerr(x, ores.x) <= 1e-8
+        mixed = s.solve(tol=tol, precision=L.PREC_MIXED, step_mode=L.STEP_ADAPTIVE)
+        xm, ym = s.solution()
+        assert mixed["termination"] == L.TERM_SOLVED
+        assert O.relkkt(P, xm, ym).relkkt <= tol
+
+
+def test_penalty_without_equality_rows_changes_nothing(built):
+    inst, P, s = built("sparse_small")
+    s.solve(tol=1e-4)
+    x0, y0 = s.solution()
+    with QPSolver(inst, penalty=True) as s2:
+        assert s2.penalty_rho() == 0.0
+        s2.solve(tol=1e-4)
+        x1, y1 = s2.solution()
+    assert np.array_equal(x0, x1) and np.array_equal(y0, y1)
+
+
+def test_penalty_rejects_a_dense_equality_row():
+    """A budget-like row over 20 000 variables: G'G would need 4e8 products."""
+    import scipy.sparse as sp
+    n = 20_000
+    Q = sp.identity(n, format="csr")
+    A = sp.csr_matrix(np.ones((1, n)))
+    inst = W.QPInstance(n, 1, 1, Q.indptr.astype(np.int32), Q.indices.astype(np.int32), Q.data,
+                        A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data,
+                        np.ones(n), np.ones(1), name="dense equality row")
+    with pytest.raises(L.QPError) as e:
+        QPSolver(inst, penalty=True)
+    assert e.value.status == 1  # QP_ERR_INVALID_ARG
+    with QPSolver(inst) as s:  # without the penalty the same problem is fine
+        assert s.solve(tol=1e-6)["termination"] == L.TERM_SOLVED

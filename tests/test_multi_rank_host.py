@@ -31,8 +31,9 @@ def _run_two_ranks(tmp_path, body: str):
         import bench
         ws, rank = bench._dist()
         out = {{"rank": rank, "ws": ws}}
-    """) + textwrap.dedent(body) + textwrap.dedent("""
-        print("RESULT " + json.dumps(out), flush=True)
+    """) + textwrap.dedent(body) + textwrap.dedent(f"""
+        with open(os.path.join({str(tmp_path)!r}, f"rank{{rank}}.json"), "w") as f:
+            json.dump(out, f)
         dist.destroy_process_group()
     """))
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
@@ -40,9 +41,11 @@ def _run_two_ranks(tmp_path, body: str):
     env = dict(os.environ, OMP_NUM_THREADS="1")
     p = subprocess.run(cmd, capture_output=True, text=True, timeout=240, env=env, cwd=ROOT)
     assert p.returncode == 0, p.stdout + p.stderr
-    res = [json.loads(line.split("RESULT ", 1)[1]) for line in p.stdout.splitlines()
-           if "RESULT " in line]
-    return sorted(res, key=lambda r: r["rank"])
+    res = []
+    for r in range(2):
+        with open(tmp_path / f"rank{r}.json") as f:
+            res.append(json.load(f))
+    return res
 
 
 def test_max_over_ranks_and_barrier_with_two_gloo_ranks(tmp_path):
