@@ -59,6 +59,20 @@ path implements the same one):
   eta is fixed); the CG precision epsilon advances once per accepted
   iteration; eval_freq and max_iter count attempts (they equal iterations
   with the fixed step).
+* Theoretical CG precision (Section 3, eq. stop-criteria; ``cg_mode =
+  CG_THEORY``, an option beside the practical Section 4 rule).  The appendix
+  proofs update y first and pair z^k = (x^k, y^{k+1}), which in Algorithm 1's
+  order (x first) is the iterate (x^k, y^k) itself.  So, per epoch:
+  epsilon^1 = zeta ||y^ - y^{n,0}|| / (1 + tau ||Q||_2), with y^ the dual step
+  from the restart point taken with x_bar = x^{n,0} (the proofs' y^1, which
+  Algorithm 1's order only forms after the first x-step), and
+  epsilon^k = epsilon^{k-1} + zeta ||z^{n,k-1} - z^{n,k-2}|| / (1 + tau ||Q||_2)
+  for k >= 2.  zeta defaults to ||A||_2 / (4 K^2), the largest value the
+  bound 2 zeta <= min{(1 - sqrt(sigma tau)||A||)/(2 sqrt(sigma tau) K^2),
+  (1 - sqrt(sigma tau)||A||)/(2 tau K^2)} allows when sigma = tau =
+  1/(2||A||_2), with K = eval_freq (restarts are decided every eval_freq
+  iterations).  CG stops as in the adaptive rule: tau ||r||_2 <= epsilon^k
+  after at least one step, or at cg_max.
 * Augmented penalty (Section 4, optional ``penalty``).  With G x = q the
   equality rows, the objective gains rho/2 ||G x - q||^2, i.e. the iteration
   runs on Q + rho G'G and c - rho G'q (the constant is dropped), with
@@ -91,6 +105,7 @@ import scipy.sparse as sp
 
 CG_ADAPTIVE = 0
 CG_FIXED = 1
+CG_THEORY = 2  # the CG precision sequence of Section 3 (eq. stop-criteria)
 
 RESTART_ADAPTIVE = 0
 RESTART_FIXED = 1  # restart to the average every K iterations (Algorithm 1)
@@ -321,7 +336,7 @@ def cg(Q: sp.csr_matrix, tau: float, rhs: np.ndarray, x0: np.ndarray, mode: int,
             history.append(x.copy())
         if mode == CG_FIXED:
             stop = steps >= n_fixed
-        else:
+        else:  # CG_ADAPTIVE and CG_THEORY: the precision epsilon of the caller
             stop = tau * math.sqrt(rr_new) <= eps or steps >= cg_max
         if stop or rr_new == 0.0:
             return x, steps
@@ -355,6 +370,7 @@ class OracleOptions:
     eta: float = 0.0  # <= 0: 1/(2||A||)
     scale: bool = False  # Section 4 preprocessing (Ruiz x10 + Pock-Chambolle)
     step_mode: int = STEP_FIXED  # STEP_ADAPTIVE: the Section 4 adaptive step size
+    cg_zeta: float = 0.0  # CG_THEORY: zeta (<= 0: ||A||_2 / (4 eval_freq^2))
     penalty: bool = False  # Section 4 augmented penalty rho/2 ||Gx - q||^2 on the equality rows
     step_reduction_exp: float = 0.3
     step_growth_exp: float = 0.6
@@ -382,6 +398,11 @@ class OracleState:
     attempts: int = 0  # steps tried (= k_total with the fixed step)
     weight_sum: float = 0.0  # sum of the accepted steps' eta in this epoch
     last_accepted: bool = True
+    # CG_THEORY: zeta, ||Q||_2 and the iterate before the last accepted step
+    zeta: float = 0.0
+    norm_Q: float = 0.0
+    x_prev: np.ndarray | None = None
+    y_prev: np.ndarray | None = None
 
     @property
     def tau(self) -> float:
@@ -406,7 +427,23 @@ def initial_state(P: OracleProblem, o: OracleOptions) -> OracleState:
         nc, nb = float(np.linalg.norm(P.c)), float(np.linalg.norm(P.b))
         omega = nc / nb if (nc > o.eps_zero and nb > o.eps_zero) else 1.0
     z = lambda k: np.zeros(k)
-    return OracleState(z(P.n), z(P.m), z(P.n), z(P.m), z(P.n), z(P.m), eta, omega)
+    st = OracleState(z(P.n), z(P.m), z(P.n), z(P.m), z(P.n), z(P.m), eta, omega)
+    if o.cg_mode == CG_THEORY:
+        st.zeta = o.cg_zeta if o.cg_zeta > 0 else normA / (4.0 * o.eval_freq ** 2)
+        st.norm_Q = symmetric_norm(P.Q, o.power_iters)
+    return st
+
+
+def theory_precision(P: OracleProblem, st: OracleState) -> float:
+    """epsilon^k of Section 3 (eq. stop-criteria) for the next iteration of the epoch."""
+    scale = st.zeta / (1.0 + st.tau * st.norm_Q)
+    if st.j == 0:
+        # the proofs' y^1: the dual step from the restart point with x_bar = x^{n,0}
+        y_hat = st.y + st.sigma * (P.A @ st.x - P.b)
+        y_hat[P.m_eq:] = np.maximum(y_hat[P.m_eq:], 0.0)
+        return scale * float(np.linalg.norm(y_hat - st.y))
+    d2 = float(np.sum((st.x - st.x_prev) ** 2) + np.sum((st.y - st.y_prev) ** 2))
+    return st.eps + scale * math.sqrt(d2)
 
 
 def step_limit(P: OracleProblem, x: np.ndarray, y: np.ndarray, x_new: np.ndarray,
@@ -446,8 +483,13 @@ def inner_step(P: OracleProblem, st: OracleState, o: OracleOptions) -> None:
     Fixed step: always accepted.  Adaptive step (Section 4): accepted when
     eta <= step_limit, and eta moves to next_step_size either way.
     """
-    # epsilon_{k+1} = epsilon_k + 0.05 relKKT(z^{n,k})   (Section 4)
-    eps = st.eps + o.cg_eps_factor * st.relkkt_last if o.cg_mode == CG_ADAPTIVE else st.eps
+    # epsilon_{k+1} = epsilon_k + 0.05 relKKT(z^{n,k})   (Section 4), or Section 3's sequence
+    if o.cg_mode == CG_ADAPTIVE:
+        eps = st.eps + o.cg_eps_factor * st.relkkt_last
+    elif o.cg_mode == CG_THEORY:
+        eps = theory_precision(P, st)
+    else:
+        eps = st.eps
     x_new, y_new, steps = pdhcg_step(P, st, o, eps)
     st.attempts += 1
     st.cg_total += steps
@@ -471,6 +513,7 @@ def inner_step(P: OracleProblem, st: OracleState, o: OracleOptions) -> None:
         # running averages with beta = j (uniform mean of the epoch's iterates)
         st.x_avg = st.x_avg + (x_new - st.x_avg) / st.j
         st.y_avg = st.y_avg + (y_new - st.y_avg) / st.j
+    st.x_prev, st.y_prev = st.x, st.y
     st.x, st.y = x_new, y_new
     st.k_total += 1
 

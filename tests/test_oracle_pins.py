@@ -725,3 +725,90 @@ def test_penalized_objective_is_the_original_plus_the_penalty():
         assert fp == pytest.approx(f + 0.5 * rho * (r @ r) - 0.5 * rho * (b[:m_eq] @ b[:m_eq]),
                                    rel=1e-12, abs=1e-12)
     assert np.array_equal(Pp.A.toarray(), P.A.toarray()) and np.array_equal(Pp.b, P.b)
+
+
+# ---------------------------------------------------------------- theoretical CG precision (Section 3)
+def _theory_problem(seed=50, n=10, m=12, cond=30.0):
+    rng = np.random.default_rng(seed)
+    Qd = _rand_spd(rng, n, cond)
+    Ad = rng.standard_normal((m, n))
+    c = rng.standard_normal(n) * 2
+    b = Ad @ rng.standard_normal(n) + rng.uniform(0, 0.5, m)
+    return Qd, Ad, c, b
+
+
+def test_theory_zeta_meets_the_section3_bound():
+    """With sigma = tau = 1/(2||A||) the default zeta = ||A|| / (4 K^2) satisfies
+    2 zeta <= min{(1 - sqrt(st)||A||)/(2 sqrt(st) K^2), (1 - sqrt(st)||A||)/(2 tau K^2)}
+    (with equality), and twice it would not."""
+    Qd, Ad, c, b = _theory_problem()
+    P = _prob(Qd, Ad, c, b)
+    o = _opts(cg_mode=O.CG_THEORY, omega0=1.0)
+    st = O.initial_state(P, o)
+    nA, K = O.spectral_norm(P.A, 30), o.eval_freq
+    sig = tau = st.eta  # omega = 1
+    rst = math.sqrt(sig * tau)
+    bound = min((1 - rst * nA) / (2 * rst * K ** 2), (1 - rst * nA) / (2 * tau * K ** 2))
+    assert 2 * st.zeta <= bound * (1 + 1e-12)
+    assert 2 * (2 * st.zeta) > bound
+    lmax = np.linalg.eigvalsh(Qd)[-1]  # power iteration approaches it from below
+    assert lmax * (1 - 1e-6) <= st.norm_Q <= lmax * (1 + 1e-12)
+
+
+def test_proposition1_bounds_the_cg_steps():
+    """Proposition 1 with the precision sequence of Section 3: after the first
+    iteration of an epoch every CG solve stops within log_r(zeta / (2 tau l_max
+    (1 + tau||A||)(1 + tau||Q||))) steps, r = (sqrt(k) - 1)/(sqrt(k) + 1), k the
+    condition number of Q + I/tau.  (tau l_max, l_max = ||Q + I/tau||, turns
+    the paper's error test into the residual test tau ||r|| <= epsilon used
+    here, through the energy-norm CG bound; exact CG bounds computed with
+    LAPACK eigenvalues.)"""
+    Qd, Ad, c, b = _theory_problem()
+    P = _prob(Qd, Ad, c, b)
+    o = _opts(cg_mode=O.CG_THEORY, cg_max=100_000, omega0=1.0, primal_weight_update=False,
+              restart_mode=O.RESTART_FIXED, restart_k=64, tol=0.0, max_iter=640)
+    seen = []
+    O.solve(P, o, step_hook=lambda st: seen.append((st.j, st.last_cg_steps, st.tau)))
+    ev = np.linalg.eigvalsh(Qd)
+    nA = np.linalg.norm(Ad, 2)
+    checked = 0
+    for j, steps, tau in seen:
+        if j <= 1:  # epsilon^1 comes from the restart point's dual step
+            continue
+        lmin, lmax = ev[0] + 1 / tau, ev[-1] + 1 / tau
+        kappa = lmax / lmin
+        r = (math.sqrt(kappa) - 1) / (math.sqrt(kappa) + 1)
+        zeta = O.initial_state(P, o).zeta
+        bound = math.log(zeta / (2 * tau * lmax * (1 + tau * nA) * (1 + tau * ev[-1]))) / math.log(r)
+        assert steps <= max(1, math.ceil(bound)) + 1, (steps, bound)
+        checked += 1
+    assert checked > 500
+
+
+@pytest.mark.parametrize("seed,n,m,m_eq", [(10, 4, 6, 0), (12, 6, 7, 2)])
+def test_theory_rule_reaches_the_brute_force_solution(seed, n, m, m_eq):
+    rng = np.random.default_rng(seed)
+    Qd = _rand_spd(rng, n, 10.0)
+    Ad = rng.standard_normal((m, n))
+    c = rng.standard_normal(n) * 3
+    b = Ad @ rng.standard_normal(n) + np.concatenate([np.zeros(m_eq), rng.uniform(0, 0.5, m - m_eq)])
+    xs, ys = brute_force_qp(Qd, Ad, c, b, m_eq)
+    res = O.solve(_prob(Qd, Ad, c, b, m_eq), _opts(cg_mode=O.CG_THEORY))
+    assert res.termination == O.SOLVED
+    assert np.linalg.norm(res.x - xs) <= 1e-6 * (1 + np.linalg.norm(xs))
+
+
+def test_theory_precision_grows_within_an_epoch_and_restarts_at_zero_increment(monkeypatch):
+    """epsilon^k is non-decreasing inside an epoch; each epoch's first value is
+    the restart point's own (zeta ||y^ - y|| / (1 + tau||Q||)), not a sum."""
+    Qd, Ad, c, b = _theory_problem(seed=51)
+    P = _prob(Qd, Ad, c, b)
+    o = _opts(cg_mode=O.CG_THEORY, restart_mode=O.RESTART_FIXED, restart_k=64, tol=0.0,
+              max_iter=256)
+    eps = []
+    O.solve(P, o, step_hook=lambda st: eps.append((st.j, st.eps)))
+    for (j0, e0), (j1, e1) in zip(eps, eps[1:]):
+        if j1 == j0 + 1:
+            assert e1 >= e0
+    firsts = [e for j, e in eps if j == 1]
+    assert len(firsts) >= 3 and all(e >= 0 for e in firsts)
