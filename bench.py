@@ -168,6 +168,16 @@ def mixed_solve_launches(chunks: int, power_iters: int, eval_freq: int,
     return setup + chunks * chunk + final
 
 
+def gather_ceiling(count: int, n: int) -> float | None:
+    """The device's random-gather rate (qp_gather_rate) over `count` reads of an
+    n-float vector: the ceiling of an SpMV over uniformly random columns."""
+    from ctypes import byref, c_double
+    from paper_2405_16160_b300 import _lib as L
+    out = c_double()
+    st = L.load_library().qp_gather_rate(int(count), int(n), 10, 1, byref(out))
+    return out.value if st == 0 else None
+
+
 def _profiled_traffic():
     """DRAM bytes per k_cg launch from the committed ncu capture, or None when
     the kernel source has changed since that capture."""
@@ -340,6 +350,9 @@ def run_ours(args):
         traffic *= steps_per_launch
     gpu_launches = args.steps * mixed_solve_launches(trace_len, 30, 64,
                                                      step == L.STEP_ADAPTIVE)
+    ceiling = gather_ceiling(inst.nnz_Q, inst.n)
+    gathers = (sum(i["cg_kernel_spmvs"] for i in kinfos) * inst.nnz_Q / kernel_s
+               if kernel_s > 0 else None)
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -377,9 +390,12 @@ def run_ours(args):
                      "cg_steps_per_launch": steps_per_launch,
                      "traffic_note": "ncu DRAM read+write of a one-CG-step k_cg launch "
                                      "(profiles/k_cg_traffic.json) x CG steps per launch",
-                     "gathers_per_s": (sum(i["cg_kernel_spmvs"] for i in kinfos) * inst.nnz_Q
-                                       / kernel_s) if kernel_s > 0 else None,
-                     "gather_ceiling_per_s": 2.15e11,
+                     "gathers_per_s": gathers,
+                     "gather_ceiling_per_s": ceiling,
+                     "gather_frac": (gathers / ceiling) if gathers and ceiling else None,
+                     "gather_note": "p is gathered at one random column per stored entry of "
+                                    "Q; the ceiling is qp_gather_rate over nnz(Q) reads of an "
+                                    "n-float vector, measured in this run",
                      "avg_launch_us": kernel_s / max(launches, 1) * 1e6,
                      "timing": "CUDA events around every k_cg launch (direct launches) in "
                                "solves run right after the timed region"},
@@ -601,6 +617,8 @@ def run_zipf_bench(args):
                              ki["cg_steps"], 4)
     ks = ki["cg_kernel_ms"] / 1e3
     achieved = kbytes / ks / 1e9 if ks > 0 else None
+    ceiling = gather_ceiling(inst.nnz_Q, inst.n)
+    gathers = ki["cg_kernel_spmvs"] * inst.nnz_Q / ks if ks > 0 else None
     out = {
         "metric": ZIPF_METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
@@ -619,7 +637,9 @@ def run_zipf_bench(args):
         "roofline": {"kernel": "k_cg<float> (persistent CG: Q SpMV + vector phases)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "peak_kind": peak_kind,
+                     "peak_kind": peak_kind, "gathers_per_s": gathers,
+                     "gather_ceiling_per_s": ceiling,
+                     "gather_frac": (gathers / ceiling) if gathers and ceiling else None,
                      "timing": "CUDA events around every k_cg launch of a solve capped at "
                                "640 attempts, run after the timed region"},
         "cpu_baseline": None, "gpu_launches": None, "clocks": clocks.summary(),

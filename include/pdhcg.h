@@ -303,6 +303,22 @@ qp_status qp_norm_A(qp_handle* h, int32_t iters, double* out);
  * 0 when the flag was not given or the problem has no equality rows. */
 qp_status qp_get_penalty(const qp_handle* h, double* rho);
 
+/* ------------------------------------------------------- diagnostics */
+
+/*
+ * The random-gather ceiling of the current device, measured: the best of
+ * `reps` timed launches of a kernel that only sums v[idx[k]] over `count`
+ * pseudo-random indices (a mix of seed and k) into an L2-resident vector of
+ * n floats, with four reads in flight per thread, written to *gathers_per_s.
+ * Uniformly random columns make every SpMV of the method read one 32-byte
+ * sector per stored entry, so this rate, not DRAM bandwidth, bounds them;
+ * benchmarks report the kernels against it.  Not part of a solve: it
+ * allocates its own device buffers (cudaMalloc) and frees them.  Errors:
+ * QP_ERR_INVALID_ARG, QP_ERR_NO_DEVICE, QP_ERR_OOM, QP_ERR_CUDA.
+ */
+qp_status qp_gather_rate(int64_t count, int32_t n, int32_t reps, uint64_t seed,
+                         double* gathers_per_s);
+
 /* ------------------------------------------------- allocation-free variant */
 
 /* Capacity, in doubles, of the static device scratch of qp_norm_A_static (8 MiB). */

@@ -5,7 +5,7 @@ import ctypes
 import os
 import threading
 from ctypes import (CFUNCTYPE, POINTER, Structure, c_char_p, c_double, c_float, c_int32, c_int64,
-                    c_size_t, c_uint32, c_void_p)
+                    c_size_t, c_uint32, c_uint64, c_void_p)
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libpdhcg.so")
@@ -129,6 +129,7 @@ SIGNATURES = [
     ("qp_evaluate", c_int32, [_H, _F64P, _F64P]),
     ("qp_norm_A", c_int32, [_H, c_int32, _F64P]),
     ("qp_get_penalty", c_int32, [_H, _F64P]),
+    ("qp_gather_rate", c_int32, [c_int64, c_int32, c_int32, c_uint64, _F64P]),
     ("qp_norm_A_static", c_int32, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     ("qp_csr_validate", c_int32, [c_int32, c_int32, _I32P, _I32P, _F64P]),

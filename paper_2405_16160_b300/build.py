@@ -15,7 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libpdhcg.so")
-SOURCES = ["pdhcg.cu", "batch.cu", "mlp.cu", "norm_static.cu", "host_csr.cpp"]
+SOURCES = ["pdhcg.cu", "batch.cu", "mlp.cu", "norm_static.cu", "diag.cu", "host_csr.cpp"]
 HEADERS = ["state.cuh", "kernels.cuh", "create_kernels.cuh", "batch_kernels.cuh", "host_csr.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

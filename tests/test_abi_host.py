@@ -161,3 +161,11 @@ def test_parallel_transpose_matches_scipy_and_is_stable(lib):
     assert np.array_equal(tr, ref.indptr)
     assert np.array_equal(tc, ref.indices)  # stable: each output row in input-row order
     assert np.array_equal(tv, ref.data)
+
+
+def test_gather_rate_rejects_bad_arguments(lib):
+    from ctypes import byref, c_double
+    out = c_double()
+    assert lib.qp_gather_rate(0, 10, 1, 1, byref(out)) == 1  # QP_ERR_INVALID_ARG
+    assert lib.qp_gather_rate(10, 0, 1, 1, byref(out)) == 1
+    assert lib.qp_gather_rate(10, 10, 1, 1, None) == 1

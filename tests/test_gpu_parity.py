@@ -723,3 +723,21 @@ def test_penalty_rejects_a_dense_equality_row():
     assert e.value.status == 1  # QP_ERR_INVALID_ARG
     with QPSolver(inst) as s:  # without the penalty the same problem is fine
         assert s.solve(tol=1e-6)["termination"] == L.TERM_SOLVED
+
+
+def test_gather_rate_measures_a_plausible_ceiling():
+    """qp_gather_rate on the bench's shape (9e6 reads of a 1e6-float vector):
+    positive, and no slower than the solver's own SpMV of that shape."""
+    from ctypes import byref, c_double
+    import torch
+    lib = L.load_library()
+    out = c_double()
+    assert lib.qp_gather_rate(9_000_000, 1_000_000, 3, 1, byref(out)) == 0
+    assert 1e10 < out.value < 1e13
+    inst = W.sparse_dd(0, n=1_000_000, m=10)
+    with QPSolver(inst) as s:
+        s.solve(tol=0.0, max_iter=64, kernel_timing=1, precision=L.PREC_MIXED)
+        info = s.solve(tol=0.0, max_iter=64, kernel_timing=1, precision=L.PREC_MIXED)
+    torch.cuda.synchronize()
+    spmv_rate = info["cg_kernel_spmvs"] * inst.nnz_Q / (info["cg_kernel_ms"] / 1e3)
+    assert spmv_rate < 1.05 * out.value
