@@ -73,6 +73,21 @@ path implements the same one):
   1/(2||A||_2), with K = eval_freq (restarts are decided every eval_freq
   iterations).  CG stops as in the adaptive rule: tau ||r||_2 <= epsilon^k
   after at least one step, or at cg_max.
+* Variable bounds lo <= x <= hi (optional ``OracleProblem.lo/hi``, +-inf
+  allowed).  Section 4 switches the primal subproblem to a Barzilai-Borwein
+  projected gradient when box constraints are present: x_{l+1} =
+  P(x_l - g_l/alpha_l) with alpha_l = s'w / s's (s the last step, w its
+  gradient change), alpha_0 the exact steepest-descent step g'Mg / g'g,
+  M = Q + I/tau, from the warm start x^{n,k}.  It stops when the step length
+  ||x_{l+1} - x_l|| is at most the adaptive precision epsilon_k (the
+  criterion the paper states for this switch), after at least one step, or
+  at cg_max (FIXED: exactly N steps).  The iterates stay in the box (x^0 is
+  the projection of 0).  The paper's relKKT has no bound terms; PDLP's
+  reduced costs give them: with g = Qx + A'y + c, lambda_j = g_j where both
+  bounds are finite, max(g_j, 0) with only a lower one, min(g_j, 0) with only
+  an upper one, 0 with none; r_dual measures g - lambda, and the dual
+  objective gains lo'lambda^+ - hi'lambda^- (without bounds both reduce to
+  the definitions above).
 * Augmented penalty (Section 4, optional ``penalty``).  With G x = q the
   equality rows, the objective gains rho/2 ||G x - q||^2, i.e. the iteration
   runs on Q + rho G'G and c - rho G'q (the constant is dropped), with
@@ -131,6 +146,13 @@ class OracleProblem:
     c: np.ndarray
     b: np.ndarray
     m_eq: int = 0
+    lo: np.ndarray | None = None  # variable bounds (+-inf allowed); None: unbounded
+    hi: np.ndarray | None = None
+
+    @property
+    def has_bounds(self) -> bool:
+        return self.lo is not None and (bool(np.any(np.isfinite(self.lo)))
+                                        or bool(np.any(np.isfinite(self.hi))))
 
     @property
     def n(self) -> int:
@@ -154,8 +176,27 @@ def problem_from_csr(n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val,
 
 
 def problem_from_instance(inst) -> OracleProblem:
-    return problem_from_csr(inst.n, inst.m, inst.m_eq, inst.Q_rowptr, inst.Q_col, inst.Q_val,
-                            inst.A_rowptr, inst.A_col, inst.A_val, inst.c, inst.b)
+    P = problem_from_csr(inst.n, inst.m, inst.m_eq, inst.Q_rowptr, inst.Q_col, inst.Q_val,
+                         inst.A_rowptr, inst.A_col, inst.A_val, inst.c, inst.b)
+    lo, hi = getattr(inst, "lo", None), getattr(inst, "hi", None)
+    if lo is not None or hi is not None:
+        P.lo = np.asarray(lo, np.float64).copy() if lo is not None else np.full(P.n, -np.inf)
+        P.hi = np.asarray(hi, np.float64).copy() if hi is not None else np.full(P.n, np.inf)
+    return P
+
+
+def reduced_costs(P: OracleProblem, g: np.ndarray) -> np.ndarray:
+    """Bound multipliers lambda for the gradient g = Qx + A'y + c (PDLP's reduced costs):
+    g where both bounds are finite, max(g, 0) with only a lower bound, min(g, 0) with
+    only an upper bound, 0 without bounds."""
+    if not P.has_bounds:
+        return np.zeros_like(g)
+    lf, hf = np.isfinite(P.lo), np.isfinite(P.hi)
+    lam = np.zeros_like(g)
+    lam[lf & hf] = g[lf & hf]
+    lam[lf & ~hf] = np.maximum(g[lf & ~hf], 0.0)
+    lam[~lf & hf] = np.minimum(g[~lf & hf], 0.0)
+    return lam
 
 
 # --------------------------------------------------------------------------
@@ -182,10 +223,28 @@ def relkkt(P: OracleProblem, x: np.ndarray, y: np.ndarray) -> KKT:
                (|Ax - b| on the equality rows)
     r_dual   = ||Qx + A'y + c||_inf / (1 + max(||Qx||_inf, ||A'y||_inf, ||c||_inf))
     r_gap    = |x'Qx + c'x + b'y| / (1 + max(|1/2 x'Qx + c'x|, |1/2 x'Qx + b'y|))
+
+    With variable bounds, r_dual measures Qx + A'y + c - lambda (reduced_costs)
+    and the dual objective gains lo'lambda^+ - hi'lambda^-.
     """
     Qx = P.Q @ x
     Ax = P.A @ x
     Aty = P.A.T @ y
+    if P.has_bounds:
+        g = Qx + Aty + P.c
+        lam = reduced_costs(P, g)
+        lp, lm = np.maximum(lam, 0.0), np.maximum(-lam, 0.0)
+        lb = float(np.sum(P.lo[lp > 0] * lp[lp > 0]) - np.sum(P.hi[lm > 0] * lm[lm > 0]))
+        viol = Ax - P.b
+        viol[P.m_eq:] = np.maximum(viol[P.m_eq:], 0.0)
+        viol[:P.m_eq] = np.abs(viol[:P.m_eq])
+        r_primal = _inf_norm(viol) / (1.0 + max(_inf_norm(Ax), _inf_norm(P.b)))
+        r_dual = _inf_norm(g - lam) / (1.0 + max(_inf_norm(Qx), _inf_norm(Aty), _inf_norm(P.c)))
+        xQx = float(x @ Qx)
+        pobj = 0.5 * xQx + float(P.c @ x)
+        dobj = -0.5 * xQx - float(P.b @ y) + lb
+        r_gap = abs(pobj - dobj) / (1.0 + max(abs(pobj), abs(dobj)))
+        return KKT(r_primal, r_dual, r_gap, max(r_primal, r_dual, r_gap), pobj, dobj)
     viol = Ax - P.b
     viol[P.m_eq:] = np.maximum(viol[P.m_eq:], 0.0)
     viol[:P.m_eq] = np.abs(viol[:P.m_eq])
@@ -237,7 +296,9 @@ def diagonal_scaling(P: OracleProblem, ruiz_iters: int = 10, pock_chambolle: boo
 def scale_problem(P: OracleProblem, d1: np.ndarray, d2: np.ndarray) -> OracleProblem:
     Q = (sp.diags(d2) @ P.Q @ sp.diags(d2)).tocsr()
     A = (sp.diags(d1) @ P.A @ sp.diags(d2)).tocsr()
-    return OracleProblem(Q, A, d2 * P.c, d1 * P.b, P.m_eq)
+    lo = P.lo / d2 if P.lo is not None else None  # x~ = x / d2
+    hi = P.hi / d2 if P.hi is not None else None
+    return OracleProblem(Q, A, d2 * P.c, d1 * P.b, P.m_eq, lo, hi)
 
 
 # --------------------------------------------------------------------------
@@ -297,7 +358,7 @@ def penalize(P: OracleProblem, rho: float) -> OracleProblem:
     G = P.A[:P.m_eq]
     Qp = (P.Q + rho * (G.T @ G)).tocsr()
     Qp.sum_duplicates()
-    return OracleProblem(Qp, P.A, P.c - rho * (G.T @ P.b[:P.m_eq]), P.b, P.m_eq)
+    return OracleProblem(Qp, P.A, P.c - rho * (G.T @ P.b[:P.m_eq]), P.b, P.m_eq, P.lo, P.hi)
 
 
 # --------------------------------------------------------------------------
@@ -342,6 +403,49 @@ def cg(Q: sp.csr_matrix, tau: float, rhs: np.ndarray, x0: np.ndarray, mode: int,
             return x, steps
         p = r + (rr_new / rr) * p
         rr = rr_new
+
+
+def bb(Q: sp.csr_matrix, tau: float, rhs: np.ndarray, x0: np.ndarray, lo: np.ndarray,
+       hi: np.ndarray, mode: int, n_fixed: int = 0, eps: float = 0.0, bb_max: int = 100):
+    """Projected Barzilai-Borwein gradient method (Section 4) on
+    min_{lo <= x <= hi} 1/2 x'(Q + I/tau)x - rhs'x from x0 (in the box).
+
+    g = M x - rhs, alpha_0 = g'Mg / g'g; then x+ = P(x - g/alpha), s = x+ - x,
+    g += M s, alpha = s'Ms / s's.  FIXED: exactly n_fixed steps; otherwise at
+    least one step and stop when ||s|| <= eps or after bb_max steps (or when s
+    is exactly zero).  Returns (x, steps).
+    """
+    M = lambda v: Q @ v + v / tau
+    x = x0.copy()
+    if mode == CG_FIXED and n_fixed <= 0:
+        return x, 0
+    g = M(x) - rhs
+    gg = float(g @ g)
+    if gg == 0.0:
+        return x, 0
+    gmg = float(g @ M(g))
+    if not gmg > 0.0:
+        raise NumericalError("g'(Q + I/tau)g <= 0: Q is not PSD or the data is not finite")
+    alpha = gmg / gg
+    steps = 0
+    while True:
+        xn = np.minimum(np.maximum(x - g / alpha, lo), hi)
+        s = xn - x
+        ss = float(s @ s)
+        w = M(s)
+        x = xn
+        steps += 1
+        if mode == CG_FIXED:
+            stop = steps >= n_fixed
+        else:
+            stop = math.sqrt(ss) <= eps or steps >= bb_max
+        if stop or ss == 0.0:
+            return x, steps
+        sw = float(s @ w)
+        if not sw > 0.0:
+            raise NumericalError("s'(Q + I/tau)s <= 0: Q is not PSD or the data is not finite")
+        g = g + w
+        alpha = sw / ss
 
 
 # --------------------------------------------------------------------------
@@ -428,6 +532,9 @@ def initial_state(P: OracleProblem, o: OracleOptions) -> OracleState:
         omega = nc / nb if (nc > o.eps_zero and nb > o.eps_zero) else 1.0
     z = lambda k: np.zeros(k)
     st = OracleState(z(P.n), z(P.m), z(P.n), z(P.m), z(P.n), z(P.m), eta, omega)
+    if P.has_bounds:  # x0: the projection of 0 onto the box
+        st.x = np.minimum(np.maximum(st.x, P.lo), P.hi)
+        st.x_anchor = st.x.copy()
     if o.cg_mode == CG_THEORY:
         st.zeta = o.cg_zeta if o.cg_zeta > 0 else normA / (4.0 * o.eval_freq ** 2)
         st.norm_Q = symmetric_norm(P.Q, o.power_iters)
@@ -470,7 +577,10 @@ def pdhcg_step(P: OracleProblem, st: OracleState, o: OracleOptions, eps: float):
     tau, sigma = st.tau, st.sigma
     # x^{k+1} ~ argmin_x L(x, y^k) + ||x - x^k||^2/(2 tau):  (Q + I/tau) x = x^k/tau - c - A'y^k
     rhs = st.x / tau - P.c - P.A.T @ st.y
-    x_new, steps = cg(P.Q, tau, rhs, st.x, o.cg_mode, o.cg_fixed_n, eps, o.cg_max)
+    if P.has_bounds:  # Section 4: BB projected gradient when box constraints are present
+        x_new, steps = bb(P.Q, tau, rhs, st.x, P.lo, P.hi, o.cg_mode, o.cg_fixed_n, eps, o.cg_max)
+    else:
+        x_new, steps = cg(P.Q, tau, rhs, st.x, o.cg_mode, o.cg_fixed_n, eps, o.cg_max)
     # y^{k+1} = proj(y^k + sigma (A(2x^{k+1} - x^k) - b)); equality rows unprojected
     y_new = st.y + sigma * (P.A @ (2.0 * x_new - st.x) - P.b)
     y_new[P.m_eq:] = np.maximum(y_new[P.m_eq:], 0.0)

@@ -5,7 +5,10 @@ determines: hand-worked relKKT values (Section 4), closed-form QP solutions,
 LAPACK solves, an exhaustive active-set search on tiny QPs, the textbook CG
 error bound (Section 2), Lemma A.2(2) and Theorem 2 of the appendix, and the
 trend of Table 2.  The last group plants mistakes in the oracle and checks
-that a pin catches each one.  The adaptive step size of Section 4 is pinned
+that a pin catches each one.  Variable bounds and the BB projected gradient
+of Section 4 are pinned by a box brute force, the linear-system solution
+without bounds, relKKT with bounds worked by hand, the box closed form and
+brute force with the bounds written as rows.  The adaptive step size of Section 4 is pinned
 by its closed form at the top singular pair of A, a lower bound that follows
 from Cauchy-Schwarz and AM-GM, PDLP's update rule worked by hand, the
 accept/reject invariants, step-weighted averages and the closed-form and
@@ -812,3 +815,133 @@ def test_theory_precision_grows_within_an_epoch_and_restarts_at_zero_increment(m
             assert e1 >= e0
     firsts = [e for j, e in eps if j == 1]
     assert len(firsts) >= 3 and all(e >= 0 for e in firsts)
+
+
+# ---------------------------------------------------------------- variable bounds and BB (Section 4)
+def _box_brute_force(M, rhs, lo, hi):
+    """min 1/2 x'Mx - rhs'x over the box, exactly: every assignment of the
+    variables to lower bound / upper bound / free, the free ones solved by
+    LAPACK, kept when feasible with the right multiplier signs."""
+    n = len(rhs)
+    best = None
+    for pat in itertools.product((0, 1, 2), repeat=n):
+        x = np.zeros(n)
+        fixed = [j for j in range(n) if pat[j] != 2]
+        for j in fixed:
+            x[j] = lo[j] if pat[j] == 0 else hi[j]
+        if not np.all(np.isfinite(x[fixed])):
+            continue
+        free = [j for j in range(n) if pat[j] == 2]
+        if free:
+            r = rhs[free] - M[np.ix_(free, fixed)] @ x[fixed]
+            x[free] = np.linalg.solve(M[np.ix_(free, free)], r)
+        if np.any(x < lo - 1e-12) or np.any(x > hi + 1e-12):
+            continue
+        g = M @ x - rhs
+        if any((pat[j] == 0 and g[j] < -1e-10) or (pat[j] == 1 and g[j] > 1e-10) for j in range(n)):
+            continue
+        best = x
+        break
+    assert best is not None
+    return best
+
+
+def test_bb_without_bounds_solves_the_linear_system():
+    rng = np.random.default_rng(60)
+    n = 12
+    Qd = _rand_spd(rng, n, 50.0)
+    rhs = rng.standard_normal(n)
+    tau = 0.7
+    x, steps = O.bb(sp.csr_matrix(Qd), tau, rhs, np.zeros(n), np.full(n, -np.inf),
+                    np.full(n, np.inf), O.CG_ADAPTIVE, eps=1e-13, bb_max=10_000)
+    assert np.allclose(x, np.linalg.solve(Qd + np.eye(n) / tau, rhs), rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [61, 62, 63])
+def test_bb_matches_box_brute_force_and_stays_in_the_box(seed):
+    rng = np.random.default_rng(seed)
+    n = 6
+    Qd = _rand_spd(rng, n, 20.0)
+    rhs = rng.standard_normal(n) * 3
+    lo = np.where(rng.random(n) < 0.7, -rng.uniform(0.1, 1, n), -np.inf)
+    hi = np.where(rng.random(n) < 0.7, rng.uniform(0.1, 1, n), np.inf)
+    tau = 1.3
+    xs = _box_brute_force(Qd + np.eye(n) / tau, rhs, lo, hi)
+    x, steps = O.bb(sp.csr_matrix(Qd), tau, rhs, np.clip(np.zeros(n), lo, hi), lo, hi,
+                    O.CG_ADAPTIVE, eps=1e-14, bb_max=20_000)
+    assert np.all(x >= lo) and np.all(x <= hi)
+    assert np.allclose(x, xs, rtol=1e-9, atol=1e-10)
+
+
+def test_relkkt_with_bounds_worked_by_hand():
+    """min x^2 - 6x on x <= 1 (Q = [2], c = -6, no rows).  At x* = 1: g = -4, the
+    upper bound's multiplier -4 (lambda^- = 4): r_dual = 0, dual objective
+    -1 - 1*4 = -5 = primal objective.  At x = 0.5: g = -5 is still allowed
+    (r_dual = 0) but the gap catches it: pobj = -2.75, dobj = -0.25 - 5 = -5.25,
+    r_gap = 2.5 / (1 + 5.25) = 0.4."""
+    P = _prob([[2.0]], np.zeros((0, 1)), [-6.0], np.zeros(0))
+    P.lo, P.hi = np.array([-np.inf]), np.array([1.0])
+    k = O.relkkt(P, np.array([1.0]), np.zeros(0))
+    assert k.r_dual == 0.0 and k.r_gap == 0.0 and k.primal_obj == -5.0 and k.dual_obj == -5.0
+    k = O.relkkt(P, np.array([0.5]), np.zeros(0))
+    assert k.r_dual == 0.0
+    assert k.primal_obj == -2.75 and k.dual_obj == -5.25
+    assert k.r_gap == pytest.approx(0.4, rel=1e-15)
+    # a lower bound alone cannot absorb a negative gradient: x = 0.5 with x >= 0
+    P.lo, P.hi = np.array([0.0]), np.array([np.inf])
+    k = O.relkkt(P, np.array([0.5]), np.zeros(0))
+    assert k.r_dual == pytest.approx(5.0 / (1.0 + 6.0), rel=1e-15)
+
+
+@pytest.mark.parametrize("step", [O.STEP_FIXED, O.STEP_ADAPTIVE])
+def test_solver_box_bounds_closed_form(step):
+    """Diagonal Q with the box as variable bounds (no rows): x* = clip(-c/q, lo, hi)."""
+    rng = np.random.default_rng(64)
+    n = 40
+    q = rng.uniform(0.5, 2.0, n)
+    c = rng.standard_normal(n) * 2
+    P = _prob(np.diag(q), np.zeros((0, n)), c, np.zeros(0))
+    P.lo, P.hi = -rng.uniform(0.1, 1, n), rng.uniform(0.1, 1, n)
+    res = O.solve(P, _opts(step_mode=step))
+    assert res.termination == O.SOLVED
+    assert np.max(np.abs(res.x - np.clip(-c / q, P.lo, P.hi))) <= 1e-8
+
+
+@pytest.mark.parametrize("seed,n,m,m_eq", [(70, 4, 5, 0), (71, 5, 6, 1), (72, 3, 4, 2)])
+@pytest.mark.parametrize("scale", [False, True])
+def test_solver_with_bounds_matches_brute_force_with_the_bounds_as_rows(seed, n, m, m_eq, scale):
+    rng = np.random.default_rng(seed)
+    Qd = _rand_spd(rng, n, 10.0)
+    Ad = rng.standard_normal((m, n))
+    c = rng.standard_normal(n) * 3
+    x0 = rng.uniform(-0.3, 0.3, n)
+    b = Ad @ x0 + np.concatenate([np.zeros(m_eq), rng.uniform(0, 0.5, m - m_eq)])
+    lo = np.where(rng.random(n) < 0.6, -rng.uniform(0.4, 1, n), -np.inf)
+    hi = np.where(rng.random(n) < 0.6, rng.uniform(0.4, 1, n), np.inf)
+    rows = [j for j in range(n) if np.isfinite(hi[j])], [j for j in range(n) if np.isfinite(lo[j])]
+    Ab = np.vstack([Ad, np.eye(n)[rows[0]], -np.eye(n)[rows[1]]])
+    bb_ = np.concatenate([b, hi[rows[0]], -lo[rows[1]]])
+    xs, _ = brute_force_qp(Qd, Ab, c, bb_, m_eq)
+    P = _prob(Qd, Ad, c, b, m_eq)
+    P.lo, P.hi = lo, hi
+    res = O.solve(P, _opts(scale=scale))
+    assert res.termination == O.SOLVED
+    assert np.all(res.x >= lo - 1e-12) and np.all(res.x <= hi + 1e-12)
+    assert np.linalg.norm(res.x - xs) <= 1e-6 * (1 + np.linalg.norm(xs))
+    assert res.kkt.primal_obj == pytest.approx(0.5 * xs @ Qd @ xs + c @ xs, rel=1e-8, abs=1e-8)
+
+
+def test_long_only_bounds_match_long_only_rows_on_a_portfolio():
+    """The portfolio's long-only rows -x <= 0 as the bound x >= 0: the same solution."""
+    from paper_2405_16160_b300 import workloads as W
+    lr = W.portfolio(0, 5, n_lo=30, n_hi=60)
+    P_rows = O.problem_from_instance(lr.to_instance())
+    keep = [i for i in range(P_rows.m) if not (P_rows.A[i].nnz == 1 and P_rows.A[i].data[0] < 0
+                                                and P_rows.b[i] == 0.0)]
+    P = O.OracleProblem(P_rows.Q, P_rows.A[keep], P_rows.c, P_rows.b[keep], P_rows.m_eq,
+                        np.zeros(P_rows.n), np.full(P_rows.n, np.inf))
+    assert P.m == P_rows.m - P_rows.n
+    r1 = O.solve(P_rows, _opts(tol=1e-9))
+    r2 = O.solve(P, _opts(tol=1e-9))
+    assert r1.termination == r2.termination == O.SOLVED
+    assert np.max(np.abs(r1.x - r2.x)) <= 1e-6
