@@ -299,6 +299,27 @@ qp_status qp_evaluate(qp_handle* h, double kkt_cur[6], double kkt_avg[6]);
 /* Estimate ||A||_2 by `iters` power iterations on A'A from ones/sqrt(n). */
 qp_status qp_norm_A(qp_handle* h, int32_t iters, double* out);
 
+/*
+ * Variable bounds lo <= x <= hi (Section 4: with box constraints the primal
+ * subproblem is solved by the Barzilai-Borwein projected gradient instead of
+ * CG).  lo and hi are host arrays of n entries; NULL means no bound on that
+ * side, and -INFINITY / +INFINITY entries are absent bounds.  They hold for
+ * every later qp_solve and qp_iterate of the handle (all absent: CG again).
+ * The start point and a warm start are projected into the box and every
+ * iterate stays in it.  The paper's relKKT has no bound terms; with bounds
+ * r_dual measures Qx + A'y + c - lambda, where lambda are PDLP's reduced
+ * costs (the gradient where both bounds are finite, its positive part with
+ * only a lower bound, its negative part with only an upper one), and the
+ * dual objective gains lo'lambda^+ - hi'lambda^-.  BB steps: x+ =
+ * min(max(x - g/alpha, lo), hi), alpha_0 = g'Mg / g'g and then s'Ms / s's
+ * (M = Q + I/tau), one product with Q per step; the adaptive rule stops when
+ * the step length ||x+ - x|| is at most eps_k, the fixed rule after N steps;
+ * qp_info.cg_steps counts BB steps.  With QP_CREATE_SCALE the bounds are
+ * scaled with the variables.  Errors: QP_ERR_INVALID_ARG (NaN, lo > hi,
+ * lo = +inf or hi = -inf).
+ */
+qp_status qp_set_bounds(qp_handle* h, const double* lo, const double* hi);
+
 /* The penalty weight rho of QP_CREATE_PENALTY (Section 4, augmented penalty);
  * 0 when the flag was not given or the problem has no equality rows. */
 qp_status qp_get_penalty(const qp_handle* h, double* rho);

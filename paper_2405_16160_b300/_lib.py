@@ -129,6 +129,7 @@ SIGNATURES = [
     ("qp_evaluate", c_int32, [_H, _F64P, _F64P]),
     ("qp_norm_A", c_int32, [_H, c_int32, _F64P]),
     ("qp_get_penalty", c_int32, [_H, _F64P]),
+    ("qp_set_bounds", c_int32, [_H, _F64P, _F64P]),
     ("qp_gather_rate", c_int32, [c_int64, c_int32, c_int32, c_uint64, _F64P]),
     ("qp_norm_A_static", c_int32, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),

@@ -51,7 +51,7 @@ constexpr int kCgBlock = 512;  // persistent CG kernel: fewer, larger blocks
 constexpr int kPartStride = 16;  // doubles per block in the multi-value partial buffers
 
 // Which entries of the relKKT partial buffers are maxima (bit set) or sums.
-constexpr unsigned kKktNMaxMask = 0b10011100111u;  // 11 entries, see k_kkt_n
+constexpr unsigned kKktNMaxMask = 0b0010011100111u;  // 13 entries, see k_kkt_n
 constexpr unsigned kKktMMaxMask = 0b1011011u;      // 7 entries, see k_kkt_m
 
 // Rows with more than kLongRow entries are "long": a pre-pass splits them
@@ -724,6 +724,154 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
   }
 }
 
+// ------------------------------------- BB projected gradient (Section 4)
+// With variable bounds lo <= x <= hi the primal subproblem
+// min_{lo<=x<=hi} 1/2 x'(Q + I/tau)x - rhs'x is solved by the Barzilai-
+// Borwein projected gradient from x^k.  The kernel that forms the CG start
+// (k_atv, k_prepare) leaves r = p = -g0, the negated gradient at x^k, and
+// g0'g0.  Phases:
+//   [0] q = Q p: alpha0 = g0'M g0 / g0'g0 (M = Q + I/tau)
+//   [A] x+ = min(max(x + r/alpha, lo), hi); s = x+ - x into p; x = x+; s's
+//   [B] w = Q s + s/tau; r -= w (the gradient moves by w); qx += Q s; s'w
+// then stop when ||s|| <= eps (adaptive, after at least one step), after
+// cg_max steps, or after N steps (fixed), else alpha = s'w / s's.  One
+// product with Q per step plus the first; the mixed path passes its
+// displacement dx and the bounds shifted by the restart point.
+template <int G, class T>
+__global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
+    k_bb(CsrT<T> Q, LongRows LQ, T* qseg, T* qlong, T* x, T* r, T* p, T* qx,
+         const T* __restrict__ lo, const T* __restrict__ hi, const double* r0r0, double* part,
+         DevState* st, GridBarrier* bar, int n) {
+  using A = typename Acc<T>::type;
+  const bool active = running(st) && st->attempts < st->opt.max_iter;
+  if (!active) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->iter_active = 0;
+    return;
+  }
+  // Every read of st happens before the first barrier; block 0 writes the
+  // counters only after the last one.
+  const double tau = st->tau;
+  const T inv_tau = T(1.0 / tau);
+  const int mode = st->opt.cg_mode, nfix = st->opt.cg_fixed_n, cgmax = st->opt.cg_max;
+  const bool adaptive_step = st->opt.step_mode == kStepAdaptive;
+  const int tmo = st->opt.barrier_timeout_ms;
+  bool never_release = (st->opt.debug_flags & kDebugBarrierNeverReleases) != 0u;
+  const double eps =
+      mode == kCgAdaptive ? st->eps + st->opt.cg_eps_factor * st->relkkt_last : st->eps;
+  double* part_a = part;
+  double* part_b = part + gridDim.x;
+  const long long t0 = grid_tid(), nt = grid_threads();
+  const double rr = __ldcg(r0r0);
+  int steps = 0, products = 0;
+  bool numerr = false, failed = false;
+  // Q p over every row (long rows first), f(i, (Q p)_i) for each row
+  auto qprod = [&](auto&& f) {
+    if (LQ.nlong > 0) {
+      long_segments(Q, p, LQ, qseg);
+      if (!grid_sync(bar, st, tmo, never_release)) return false;
+      never_release = false;
+      long_finish(LQ, qseg, qlong);
+      if (!grid_sync(bar, st, tmo, false)) return false;
+    }
+    spmv_rows<G>(Q, p, [&](int i, T s, bool lead) {
+      if (lead) f(i, s);
+    });
+    ++products;
+    return true;
+  };
+  const bool skip = (mode == kCgFixed && nfix <= 0) || rr == 0.0;
+  if (!skip) {
+    double alpha = 0.0;
+    {
+      A acc;
+      if (!qprod([&](int i, T s) {
+            const T pi = p[i];
+            acc.add_prod(pi, s + pi * inv_tau);
+          }))
+        return;
+      block_dot_store(acc, part_a + blockIdx.x);
+      if (!grid_sync(bar, st, tmo, never_release)) return;
+      never_release = false;
+      const double gmg = block_all_reduce<A, 1>(part_a, gridDim.x);
+      if (!(gmg > 0.0) || !isfinite(gmg)) numerr = true;
+      alpha = gmg / rr;
+    }
+    while (!numerr && !failed) {
+      const T inv_alpha = T(1.0 / alpha);
+      A acc;
+      for (long long i = t0; i < n; i += nt) {
+        const T xi = x[i];
+        const T xn = fmin(fmax(xi + r[i] * inv_alpha, lo[i]), hi[i]);
+        const T si = xn - xi;
+        p[i] = si;
+        x[i] = xn;
+        acc.add_prod(si, si);
+      }
+      block_dot_store(acc, part_a + blockIdx.x);
+      if (!grid_sync(bar, st, tmo, false)) return;
+      const double ss = block_all_reduce<A, 1>(part_a, gridDim.x);
+      A acc2;
+      if (!qprod([&](int i, T s) {
+            const T si = p[i];
+            const T wi = s + si * inv_tau;
+            r[i] = sub_rn(r[i], wi);
+            qx[i] = add_rn(qx[i], s);
+            acc2.add_prod(si, wi);
+          }))
+        return;
+      block_dot_store(acc2, part_b + blockIdx.x);
+      if (!grid_sync(bar, st, tmo, false)) return;
+      const double sw = block_all_reduce<A, 1>(part_b, gridDim.x);
+      ++steps;
+      const bool stop = mode == kCgFixed ? steps >= nfix : (sqrt(ss) <= eps || steps >= cgmax);
+      if (stop || ss == 0.0) break;
+      if (!(sw > 0.0) || !isfinite(sw)) {
+        numerr = true;
+        break;
+      }
+      alpha = sw / ss;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (numerr) {
+      st->done = kDoneNumerical;
+      st->iter_active = 0;
+    } else {
+      st->iter_active = 1;
+      st->attempts += 1;
+      st->cg_total += steps;
+      st->last_cg = steps;
+      st->spmv_total += products;
+      if (adaptive_step) {
+        st->eps_try = eps;
+      } else {
+        st->eps = eps;
+        st->k_total += 1;
+        st->j += 1;
+      }
+    }
+  }
+}
+
+// Mixed path with variable bounds: the bounds of the displacement dx = x - x_a
+// from the restart point, lo - x_a and hi - x_a, formed in FP64 from the FP64
+// bounds and the compensated restart point, then rounded (+-inf stay).
+__global__ void k_bound_shift(const double* __restrict__ lo, const double* __restrict__ hi,
+                              const float* __restrict__ x_a, const float* __restrict__ x_a_lo,
+                              float* lo_d, float* hi_d, int n) {
+  for (long long i = grid_tid(); i < n; i += grid_threads()) {
+    const double xa = (double)x_a[i] + (double)x_a_lo[i];
+    lo_d[i] = float(lo[i] - xa);
+    hi_d[i] = float(hi[i] - xa);
+  }
+}
+
+// x <- min(max(x, lo), hi): a start point or a promoted iterate into the box.
+template <class T>
+__global__ void k_project_box(T* x, const T* __restrict__ lo, const T* __restrict__ hi, int n) {
+  for (long long i = grid_tid(); i < n; i += grid_threads()) x[i] = fmin(fmax(x[i], lo[i]), hi[i]);
+}
+
 // ------------------------------------------- dual step (Algorithm 1, y-update)
 // y+ = y + sigma (2 A x+ - A x - b), projected to >= 0 on rows >= m_eq; the
 // A x cache and the running average of y are updated in the same pass.  The
@@ -977,12 +1125,29 @@ __global__ void __launch_bounds__(kBlock) k_spmv(CsrT<T> M, const T* __restrict_
 // ------------------------------------------------ relKKT terms (Section 4)
 // Per block (stride kPartStride), over the n index space, from the products
 // qx = Q x, qxa = Q x~ and A'y, A'y~ computed just before:
-//  [0] max|Qx + A'y + c|  [1] max|Qx|  [2] max|A'y|  [3] sum x.Qx  [4] sum c.x
+//  [0] max|Qx + A'y + c - lambda|  [1] max|Qx|  [2] max|A'y|  [3] sum x.Qx  [4] sum c.x
 //  [5..9] the same for the average (x~, y~)            [10] max|c|
+//  [11] lb of (x, y)  [12] lb of (x~, y~)
+// With variable bounds (lo != nullptr; +-inf allowed) lambda are the reduced
+// costs of g = Qx + A'y + c: g where both bounds are finite, max(g, 0) with
+// only a lower one, min(g, 0) with only an upper one, 0 with none; and
+// lb = lo'lambda^+ - hi'lambda^- over the finite bounds.  Without bounds
+// lambda = 0 and lb = 0.
 // With diagonal scaling (inv_d2 != nullptr) the iterate is the scaled x~ and
 // the infinity norms are of the original quantities: row j of Qx, A'y, c and
-// Qx + A'y + c is inv_d2[j] times the scaled one; the dot products are
-// invariant under the scaling.
+// Qx + A'y + c is inv_d2[j] times the scaled one; the dot products, the
+// reduced costs' signs and lb are invariant under the scaling.
+template <class T>
+__device__ __forceinline__ T reduced_cost(T g, T lo, T hi) {
+  const bool lf = lo > -CUDART_INF_F, hf = hi < CUDART_INF_F;
+  return lf ? (hf ? g : (g > T(0) ? g : T(0))) : (hf ? (g < T(0) ? g : T(0)) : T(0));
+}
+
+template <class T>
+__device__ __forceinline__ T bound_term(T lam, T lo, T hi) {
+  return lam > T(0) ? lam * lo : (lam < T(0) ? -lam * -hi : T(0));
+}
+
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_kkt_n(const T* __restrict__ x,
                                                   const T* __restrict__ x_avg,
@@ -991,20 +1156,31 @@ __global__ void __launch_bounds__(kBlock) k_kkt_n(const T* __restrict__ x,
                                                   const T* __restrict__ aty,
                                                   const T* __restrict__ aty_avg,
                                                   const T* __restrict__ c,
-                                                  const T* __restrict__ inv_d2, int n,
+                                                  const T* __restrict__ inv_d2,
+                                                  const T* __restrict__ lo,
+                                                  const T* __restrict__ hi, int n,
                                                   double* part) {
   using A = typename Acc<T>::type;
   T mx[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};  // maxima, see the map below
-  A sm[4];                                               // x.Qx, c.x, x~.Qx~, c.x~
+  A sm[6];  // x.Qx, c.x, x~.Qx~, c.x~, lb, lb~
   for (long long i = grid_tid(); i < n; i += grid_threads()) {
     const T ci = c[i], q1 = qx[i], q2 = qxa[i];
     const T w = inv_d2 ? inv_d2[i] : T(1);
-    mx[0] = fmax(mx[0], w * fabs(q1 + aty[i] + ci));
+    const T g1 = q1 + aty[i] + ci, g2 = q2 + aty_avg[i] + ci;
+    T l1 = T(0), l2 = T(0);
+    if (lo) {
+      const T li = lo[i], hi_ = hi[i];
+      l1 = reduced_cost(g1, li, hi_);
+      l2 = reduced_cost(g2, li, hi_);
+      sm[4].add_prod(T(1), bound_term(l1, li, hi_));
+      sm[5].add_prod(T(1), bound_term(l2, li, hi_));
+    }
+    mx[0] = fmax(mx[0], w * fabs(g1 - l1));
     mx[1] = fmax(mx[1], w * fabs(q1));
     mx[2] = fmax(mx[2], w * fabs(aty[i]));
     sm[0].add_prod(x[i], q1);
     sm[1].add_prod(ci, x[i]);
-    mx[3] = fmax(mx[3], w * fabs(q2 + aty_avg[i] + ci));
+    mx[3] = fmax(mx[3], w * fabs(g2 - l2));
     mx[4] = fmax(mx[4], w * fabs(q2));
     mx[5] = fmax(mx[5], w * fabs(aty_avg[i]));
     sm[2].add_prod(x_avg[i], q2);
@@ -1012,11 +1188,11 @@ __global__ void __launch_bounds__(kBlock) k_kkt_n(const T* __restrict__ x,
     mx[6] = fmax(mx[6], w * fabs(ci));
   }
   // fmax drops NaN; a NaN iterate still reaches relKKT through the dot products.
-  __shared__ double out[11];
-  block_reduce_ms<7, 4>(mx, sm, out);
+  __shared__ double out[13];
+  block_reduce_ms<7, 6>(mx, sm, out);
   if (threadIdx.x == 0) {
     double* o = part + size_t(blockIdx.x) * kPartStride;
-    // maxima at 0,1,2,5,6,7,10 and sums at 3,4,8,9 (kKktNMaxMask)
+    // maxima at 0,1,2,5,6,7,10 and sums at 3,4,8,9,11,12 (kKktNMaxMask)
     o[0] = out[0];
     o[1] = out[1];
     o[2] = out[2];
@@ -1028,6 +1204,8 @@ __global__ void __launch_bounds__(kBlock) k_kkt_n(const T* __restrict__ x,
     o[8] = out[9];
     o[9] = out[10];
     o[10] = out[6];
+    o[11] = out[11];
+    o[12] = out[12];
   }
 }
 
@@ -1081,12 +1259,14 @@ __global__ void __launch_bounds__(kBlock) k_kkt_m(const T* __restrict__ ax,
 __global__ void __launch_bounds__(kBlock) k_control(const double* part_n, int gn,
                                                     const double* part_m, int gm, DevState* st,
                                                     int mode) {
-  double rn[11], rm[7];
-  block_reduce_rows<11>(part_n, gn, kPartStride, kKktNMaxMask, rn);
+  double rn[13], rm[7];
+  block_reduce_rows<13>(part_n, gn, kPartStride, kKktNMaxMask, rn);
   block_reduce_rows<7>(part_m, gm, kPartStride, kKktMMaxMask, rm);
   if (threadIdx.x != 0) return;
-  const KktTerms kc = kkt_from(rm[0], rm[1], rm[6], rn[0], rn[1], rn[2], rn[10], rn[3], rn[4], rm[2]);
-  const KktTerms ka = kkt_from(rm[3], rm[4], rm[6], rn[5], rn[6], rn[7], rn[10], rn[8], rn[9], rm[5]);
+  const KktTerms kc =
+      kkt_from(rm[0], rm[1], rm[6], rn[0], rn[1], rn[2], rn[10], rn[3], rn[4], rm[2], rn[11]);
+  const KktTerms ka =
+      kkt_from(rm[3], rm[4], rm[6], rn[5], rn[6], rn[7], rn[10], rn[8], rn[9], rm[5], rn[12]);
   control_decide(st, kc, ka, mode);
 }
 

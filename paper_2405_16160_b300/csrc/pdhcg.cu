@@ -155,6 +155,10 @@ struct VecSet {
   // Augmented penalty: the problem's own c (the iteration's c is c - rho G'q)
   // and the products Q x, Q x~ with the problem's own Q, for relKKT.
   T *ce = nullptr, *qxe = nullptr, *qxae = nullptr;
+  // Variable bounds (scaled like x; +-inf where absent) and, FP32 set only,
+  // their shift by the restart point for the displacement dx.
+  T *lo = nullptr, *hi = nullptr;
+  T *lo_d = nullptr, *hi_d = nullptr;
 };
 
 // The vectors the per-iteration kernels read as x, x~, A x and b: the
@@ -196,6 +200,8 @@ struct qp_handle {
   DevMat Qe;            // with QP_CREATE_PENALTY: the problem's own Q (Q holds Q + rho G'G)
   bool penalty = false;  // rho > 0
   double rho = 0.0;
+  bool bounded = false;  // a finite variable bound is set: BB x-steps (Section 4)
+  std::vector<double> lo_user, hi_user;  // the bounds as given (for the returned x)
   VecSet<double> v64;
   VecSet<float> v32;
   double *part_cg = nullptr, *part_n = nullptr, *part_m = nullptr, *part_rn = nullptr,
@@ -217,6 +223,7 @@ struct qp_handle {
   cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};
   int chunk_iters[2] = {0, 0};
   int chunk_step[2] = {-1, -1};
+  int chunk_bounded[2] = {-1, -1};
   std::vector<cudaEvent_t> ev;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   std::vector<qp_trace_entry> trace;
@@ -365,10 +372,19 @@ qp_status launch_cg(qp_handle* h, bool coop) {
       cfg.attrs = attr;
       cfg.numAttrs = 1;
     }
-    cudaLaunchKernelEx(&cfg, k_cg<G, T>, view<T>(h->Q), long_rows_of(h->Q), seg_buf<T>(h->Q),
-                       long_buf<T>(h->Q), it_x(v), v.r, v.p, v.q, v.qx,
-                       (const double*)(h->part_r0 + h->grid_n), h->part_cg, h->st, h->bar,
-                       (int)h->n);
+    const double* r0r0 = h->part_r0 + h->grid_n;
+    if (h->bounded) {
+      // Section 4: BB projected gradient (the mixed path's bounds are of dx)
+      const bool fp32 = std::is_same<T, float>::value;
+      cudaLaunchKernelEx(&cfg, k_bb<G, T>, view<T>(h->Q), long_rows_of(h->Q), seg_buf<T>(h->Q),
+                         long_buf<T>(h->Q), it_x(v), v.r, v.p, v.qx,
+                         (const T*)(fp32 ? v.lo_d : v.lo), (const T*)(fp32 ? v.hi_d : v.hi),
+                         r0r0, h->part_cg, h->st, h->bar, (int)h->n);
+    } else {
+      cudaLaunchKernelEx(&cfg, k_cg<G, T>, view<T>(h->Q), long_rows_of(h->Q), seg_buf<T>(h->Q),
+                         long_buf<T>(h->Q), it_x(v), v.r, v.p, v.q, v.qx, r0r0, h->part_cg,
+                         h->st, h->bar, (int)h->n);
+    }
   });
 }
 
@@ -448,10 +464,14 @@ qp_status launch_eval(qp_handle* h, int mode) {
     QP_TRY(launch_spmv<T>(h, h->Qe, v.x, v.qxe, nullptr, h->grid_n));
     QP_TRY(launch_spmv<T>(h, h->Qe, v.x_avg, v.qxae, nullptr, h->grid_n));
     k_kkt_n<T><<<h->grid_n, kBlock, 0, h->stream>>>(v.x, v.x_avg, v.qxe, v.qxae, v.aty,
-                                                    v.aty_avg, v.ce, v.inv_d2, h->n, h->part_n);
+                                                    v.aty_avg, v.ce, v.inv_d2,
+                                                    h->bounded ? v.lo : nullptr, v.hi, h->n,
+                                                    h->part_n);
   } else {
     k_kkt_n<T><<<h->grid_n, kBlock, 0, h->stream>>>(v.x, v.x_avg, v.qx, v.qx_avg, v.aty,
-                                                    v.aty_avg, v.c, v.inv_d2, h->n, h->part_n);
+                                                    v.aty_avg, v.c, v.inv_d2,
+                                                    h->bounded ? v.lo : nullptr, v.hi, h->n,
+                                                    h->part_n);
   }
   k_kkt_m<T><<<h->grid_m, kBlock, 0, h->stream>>>(v.ax, v.ax_avg, v.b, v.y, v.y_avg, v.inv_d1,
                                                   h->m, h->m_eq, h->part_m);
@@ -462,10 +482,15 @@ qp_status launch_eval(qp_handle* h, int mode) {
 template <class T>
 qp_status launch_restart(qp_handle* h) {
   VecSet<T>& v = vecs<T>(h);
-  if constexpr (std::is_same<T, float>::value)
+  if constexpr (std::is_same<T, float>::value) {
     k_restart_n_delta<<<h->grid_vec, kBlock, 0, h->stream>>>(
         v.x_anchor, v.x_a_lo, v.dx, v.dx_avg, v.aty, v.aty_avg, v.qx, v.qx_avg, h->st, h->n,
         h->part_rn);
+    // the bounds of dx follow the restart point (unchanged without a restart)
+    if (h->bounded)
+      k_bound_shift<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.lo, h->v64.hi, v.x_anchor,
+                                                           v.x_a_lo, v.lo_d, v.hi_d, h->n);
+  }
   else
     k_restart_n<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.x, v.x_avg, v.x_anchor, v.aty,
                                                           v.aty_avg, v.qx, v.qx_avg, h->st, h->n,
@@ -519,6 +544,9 @@ qp_status recompute_caches(qp_handle* h) {
   if constexpr (std::is_same<T, float>::value) {
     // b_shift = b - A x_anchor, ax_d = A dx; x = the full iterate for Q x
     materialize(h, false);
+    if (h->bounded)
+      k_bound_shift<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.lo, h->v64.hi, v.x_anchor,
+                                                           v.x_a_lo, v.lo_d, v.hi_d, h->n);
     QP_TRY(launch_spmv<T>(h, h->A, v.x_anchor, v.ax, nullptr, h->grid_m));
     if (h->m > 0)
       k_shift_rhs<<<h->grid_vec, kBlock, 0, h->stream>>>(v.b, v.ax, v.b_shift, h->m);
@@ -639,13 +667,15 @@ qp_status capture_chunk(qp_handle* h, int iters, bool coop) {
   }
   h->chunk_iters[pi] = iters;
   h->chunk_step[pi] = h->step_mode;
+  h->chunk_bounded[pi] = h->bounded ? 1 : 0;
   return QP_OK;
 }
 
 template <class T>
 qp_status ensure_chunk(qp_handle* h, int iters) {
   const int pi = std::is_same<T, double>::value ? 0 : 1;
-  if (h->chunk_exec[pi] && h->chunk_iters[pi] == iters && h->chunk_step[pi] == h->step_mode)
+  if (h->chunk_exec[pi] && h->chunk_iters[pi] == iters && h->chunk_step[pi] == h->step_mode &&
+      h->chunk_bounded[pi] == (h->bounded ? 1 : 0))
     return QP_OK;
   if (h->coop_ok) {
     qp_status s = capture_chunk<T>(h, iters, true);
@@ -1064,16 +1094,23 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   // each precision's instantiation.
   for (int fp32 = 0; fp32 < 2; ++fp32) {
     int occ = 0;
+    // the persistent CG and BB kernels share the grid: the smaller residency
+    int occ_bb = 0;
     if (fp32)
       QP_TRY(dispatch_g(h->Q.G32, [&](auto g) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<decltype(g)::value, float>,
+                                                      kCgBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_bb, k_bb<decltype(g)::value, float>,
                                                       kCgBlock, 0);
       }));
     else
       QP_TRY(dispatch_g(h->Q.G64, [&](auto g) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<decltype(g)::value, double>,
                                                       kCgBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_bb, k_bb<decltype(g)::value, double>,
+                                                      kCgBlock, 0);
       }));
+    occ = std::min(occ, occ_bb);
     CUDA_TRY(cudaGetLastError());
     if (occ < 1) {
       set_error("CG kernel cannot be resident");
@@ -1117,6 +1154,10 @@ qp_status start_solve(qp_handle* h, const qp_options* o) {
   k_init_vectors<T><<<h->grid_vec, kBlock, 0, h->stream>>>(
       v.x, v.x_avg, v.x_anchor, warm ? v.x0 : nullptr, h->n, v.y, v.y_avg, v.y_anchor,
       warm ? v.y0 : nullptr, h->m, v.x_a_lo, v.dx, v.dx_avg, v.y_lo, v.ya_lo);
+  if (h->bounded) {  // the start point into the box
+    k_project_box<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.x, v.lo, v.hi, h->n);
+    k_project_box<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.x_anchor, v.lo, v.hi, h->n);
+  }
   QP_TRY(recompute_caches<T>(h));
   QP_TRY(launch_setup<T>(h, o->power_iters, 1));
   QP_TRY(launch_eval<T>(h, 0));
@@ -1193,6 +1234,9 @@ qp_status promote_and_refine(qp_handle* h, const qp_options* o, bool timing,
     k_delta_join<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v32.x_anchor, h->v32.x_a_lo,
                                                         avg ? h->v32.dx_avg : h->v32.dx,
                                                         h->v64.x, h->n);
+  if (h->bounded && h->n > 0)  // FP32 rounding of the bounds of dx: back into the FP64 box
+    k_project_box<double><<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.x, h->v64.lo,
+                                                                 h->v64.hi, h->n);
   convert_split(h, avg ? h->v32.y_avg : h->v32.y, avg ? h->v32.ya_lo : h->v32.y_lo, h->v64.y,
                 (double*)nullptr, h->m);
   CUDA_TRY(cudaMemcpyAsync(h->v64.x_anchor, h->v64.x, size_t(h->n) * sizeof(double),
@@ -1247,6 +1291,10 @@ qp_status solve_impl(qp_handle* h, const qp_options* o, std::chrono::steady_cloc
     h->h_st->restart_pending = 0;
     fill_dev_options(h, o, &h->h_st->opt);
     QP_TRY(write_state(h));
+    if (std::is_same<T, float>::value && h->bounded)  // bounds may be newer than the state
+      k_bound_shift<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.lo, h->v64.hi, h->v32.x_anchor,
+                                                           h->v32.x_a_lo, h->v32.lo_d,
+                                                           h->v32.hi_d, h->n);
     launch_prepare<T>(h);  // the CG start of this precision (its partials are shared)
   } else {
     QP_TRY(start_solve<T>(h, o));
@@ -1445,6 +1493,10 @@ qp_status qp_get_solution(const qp_handle* h, double* x, double* y) {
       for (int32_t j = 0; j < h->n; ++j) x[j] *= h->d2[size_t(j)];
     if (y)
       for (int32_t i = 0; i < h->m; ++i) y[i] *= h->d1[size_t(i)];
+    // (hi / d2) * d2 can round one ulp past hi: keep x in the caller's box
+    if (x && h->bounded)
+      for (int32_t j = 0; j < h->n; ++j)
+        x[j] = std::min(std::max(x[j], h->lo_user[size_t(j)]), h->hi_user[size_t(j)]);
   }
   return QP_OK;
 }
@@ -1700,6 +1752,49 @@ qp_status qp_get_penalty(const qp_handle* h, double* rho) {
   if (!h || !rho) return QP_ERR_INVALID_ARG;
   *rho = h->rho;
   return QP_OK;
+}
+
+qp_status qp_set_bounds(qp_handle* h, const double* lo, const double* hi) {
+  if (!h) return QP_ERR_INVALID_ARG;
+  const size_t N = size_t(h->n);
+  std::vector<double> l(N), u(N);
+  bool any = false;
+  for (size_t j = 0; j < N; ++j) {
+    l[j] = lo ? lo[j] : -INFINITY;
+    u[j] = hi ? hi[j] : INFINITY;
+    if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == INFINITY ||
+        u[j] == -INFINITY) {
+      set_error("invalid bounds at variable %zu: [%g, %g]", j, l[j], u[j]);
+      return QP_ERR_INVALID_ARG;
+    }
+    any = any || std::isfinite(l[j]) || std::isfinite(u[j]);
+  }
+  QP_TRY(begin_call(h));
+  h->solved = false;
+  h->bounded = any;
+  h->lo_user = l;
+  h->hi_user = u;
+  if (any) {
+    if (!h->v64.lo) {
+      for (double** p : {&h->v64.lo, &h->v64.hi}) QP_TRY(dalloc(h, p, N));
+      for (float** p : {&h->v32.lo, &h->v32.hi, &h->v32.lo_d, &h->v32.hi_d})
+        QP_TRY(dalloc(h, p, N));
+    }
+    // the solver's variables are x / D2 under the Section 4 scaling
+    std::vector<float> l32(N), u32(N);
+    for (size_t j = 0; j < N; ++j) {
+      l[j] /= h->d2[j];
+      u[j] /= h->d2[j];
+      l32[j] = float(l[j]);
+      u32[j] = float(u[j]);
+    }
+    QP_TRY(upload(h, h->v64.lo, l.data(), N * sizeof(double)));
+    QP_TRY(upload(h, h->v64.hi, u.data(), N * sizeof(double)));
+    QP_TRY(upload(h, h->v32.lo, l32.data(), N * sizeof(float)));
+    QP_TRY(upload(h, h->v32.hi, u32.data(), N * sizeof(float)));
+    QP_TRY(sync(h));
+  }
+  return end_call(h);
 }
 
 qp_status qp_norm_A(qp_handle* h, int32_t iters, double* out) {

@@ -81,20 +81,24 @@ struct KktTerms {
   double t[6];
 };
 
+// lb = lo'lambda^+ - hi'lambda^-, the variable bounds' share of the dual
+// objective (0 without bounds): dual objective -1/2 x'Qx - b'y + lb.
 __device__ __forceinline__ KktTerms kkt_from(double maxviol, double maxAx, double maxb,
                                              double maxdres, double maxQx, double maxAty,
-                                             double maxc, double xQx, double cx, double by) {
+                                             double maxc, double xQx, double cx, double by,
+                                             double lb = 0.0) {
   KktTerms k;
   k.t[0] = maxviol / (1.0 + fmax(maxAx, maxb));
   k.t[1] = maxdres / (1.0 + fmax(maxQx, fmax(maxAty, maxc)));
   const double pobj = 0.5 * xQx + cx;
-  k.t[2] = fabs(xQx + cx + by) / (1.0 + fmax(fabs(pobj), fabs(0.5 * xQx + by)));
+  const double dobj = -0.5 * xQx - by + lb;
+  k.t[2] = fabs(xQx + cx + by - lb) / (1.0 + fmax(fabs(pobj), fabs(dobj)));
   // relKKT = max of the three; a NaN anywhere must stay visible.
   double m = fmax(k.t[0], fmax(k.t[1], k.t[2]));
   if (isnan(k.t[0]) || isnan(k.t[1]) || isnan(k.t[2])) m = CUDART_NAN;
   k.t[3] = m;
   k.t[4] = pobj;
-  k.t[5] = -0.5 * xQx - by;
+  k.t[5] = dobj;
   return k;
 }
 

@@ -189,6 +189,13 @@ class QPSolver:
         L.check(self.lib.qp_norm_A(self.h, int(iters), byref(out)), "qp_norm_A")
         return out.value
 
+    def set_bounds(self, lo=None, hi=None) -> None:
+        """Variable bounds lo <= x <= hi (None: no bound on that side; +-inf allowed)."""
+        lo = _f64(lo, self.n) if lo is not None else None
+        hi = _f64(hi, self.n) if hi is not None else None
+        L.check(self.lib.qp_set_bounds(self.h, _ptr(lo, c_double), _ptr(hi, c_double)),
+                "qp_set_bounds")
+
     def penalty_rho(self) -> float:
         out = c_double()
         L.check(self.lib.qp_get_penalty(self.h, byref(out)), "qp_get_penalty")

@@ -741,3 +741,145 @@ def test_gather_rate_measures_a_plausible_ceiling():
     torch.cuda.synchronize()
     spmv_rate = info["cg_kernel_spmvs"] * inst.nnz_Q / (info["cg_kernel_ms"] / 1e3)
     assert spmv_rate < 1.05 * out.value
+
+
+# ------------------------------------------- variable bounds, BB x-step (Section 4)
+# qp_set_bounds: with box constraints the x-step is the Barzilai-Borwein
+# projected gradient; relKKT takes the bounds' reduced costs.  The oracle
+# runs the same BB steps from the same points.
+def _random_bounds(n, seed, frac=0.6):
+    rng = np.random.default_rng(seed)
+    lo = np.where(rng.random(n) < frac, -rng.uniform(0.2, 1.5, n), -np.inf)
+    hi = np.where(rng.random(n) < frac, rng.uniform(0.2, 1.5, n), np.inf)
+    return lo, hi
+
+
+def _oracle_bounded(inst, lo, hi):
+    P = O.problem_from_instance(inst)
+    P.lo, P.hi = lo.copy(), hi.copy()
+    return P
+
+
+def _feasible_bounds(inst, seed, frac=0.6):
+    """Bounds around a feasible point x_f (the oracle's solution with another,
+    random cost vector), so the bounded problem stays feasible while, at its own
+    optimum, many bounds are active."""
+    rng = np.random.default_rng(seed)
+    P = O.problem_from_instance(inst)
+    P.c = rng.standard_normal(inst.n)
+    xf = O.solve(P, O.OracleOptions(tol=1e-7)).x
+    n = inst.n
+    lo = np.where(rng.random(n) < frac, xf - rng.uniform(0.02, 0.3, n), -np.inf)
+    hi = np.where(rng.random(n) < frac, xf + rng.uniform(0.02, 0.3, n), np.inf)
+    return lo, hi
+
+
+BB_ITER_CASES = ["dense_small", "dense_small_eq", "sparse_small", "ragged_eq", "long_rows"]
+
+
+@pytest.mark.parametrize("name", BB_ITER_CASES)
+@pytest.mark.parametrize("mode,iters", [("fixed3", 1), ("adaptive", 1), ("adaptive", 3)])
+def test_bb_iterations_match_oracle(built, name, mode, iters):
+    inst, _, s = built(name)
+    lo, hi = _random_bounds(inst.n, 9)
+    P = _oracle_bounded(inst, lo, hi)
+    st = _shared_state(inst, P, 10)
+    for key in ("x", "x_avg", "x_anchor"):
+        st[key] = np.clip(st[key], lo, hi)
+    s.set_bounds(lo, hi)
+    try:
+        s.set_state(st)
+        kw = dict(cg_mode=L.CG_FIXED, cg_fixed_n=3) if mode == "fixed3" else {}
+        s.iterate(iters, **kw)
+        got = s.get_state()
+    finally:
+        s.set_bounds(None, None)
+    ost = _oracle_state(st)
+    o = O.OracleOptions(**({"cg_mode": O.CG_FIXED, "cg_fixed_n": 3} if mode == "fixed3" else {}))
+    for _ in range(iters):
+        O.inner_step(P, ost, o)
+    for key in ("x", "y", "x_avg", "y_avg"):
+        assert _relerr(got[key], getattr(ost, key)) <= 1e-10, key
+    assert got["cg_total"] == ost.cg_total
+    assert np.all(got["x"] >= lo) and np.all(got["x"] <= hi)
+
+
+BOUNDED_CASES = [("dense_small", 1e-6), ("dense_small_eq", 1e-6), ("sparse_small", 1e-4),
+                 ("ragged_eq", 1e-4), ("empty_rows", 1e-6)]
+
+
+@pytest.mark.parametrize("name,tol", BOUNDED_CASES)
+@pytest.mark.parametrize("scale", [False, True])
+def test_bounds_end_to_end_matches_oracle(name, tol, scale):
+    inst = CASES[name]()
+    lo, hi = _feasible_bounds(inst, 11)
+    P = _oracle_bounded(inst, lo, hi)
+    ores = O.solve(P, O.OracleOptions(tol=tol, scale=scale))
+    with QPSolver(inst, scale=scale) as s:
+        s.set_bounds(lo, hi)
+        info = s.solve(tol=tol)
+        x, y = s.solution()
+        assert ores.termination == O.SOLVED and info["termination"] == L.TERM_SOLVED
+        assert np.all(x >= lo) and np.all(x <= hi)
+        active = np.sum(np.isclose(x, lo, atol=1e-9) | np.isclose(x, hi, atol=1e-9))
+        assert active > 0  # the bounds really bind
+        rescored = O.relkkt(P, x, y)  # with the bounds' reduced costs
+        assert rescored.relkkt <= tol
+        assert info["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-12)
+        assert rescored.primal_obj == pytest.approx(ores.kkt.primal_obj, rel=1e-4, abs=1e-8)
+        orestarts = [(r["k"], int(r["restart"]) * (2 if r["cand_avg"] else 1))
+                     for r in ores.trace[1:]]
+        if [(t["k"], t["restart"]) for t in s.trace()] == orestarts:
+            assert info["iterations"] == ores.iterations and info["cg_steps"] == ores.cg_steps
+            assert _relerr(x, ores.x) <= 1e-7
+        else:  # projections decided at rounding level can part long trajectories
+            assert abs(info["iterations"] - ores.iterations) <= 0.15 * ores.iterations + 64
+            assert _relerr(x, ores.x) <= 100 * tol
+        mixed = s.solve(tol=tol, precision=L.PREC_MIXED, step_mode=L.STEP_ADAPTIVE)
+        xm, ym = s.solution()
+        assert mixed["termination"] == L.TERM_SOLVED
+        assert np.all(xm >= lo) and np.all(xm <= hi)
+        assert O.relkkt(P, xm, ym).relkkt <= tol
+
+
+def test_bounds_box_closed_form():
+    """Diagonal Q, no rows, the box as bounds: x* = clip(-c/q, lo, hi)."""
+    rng = np.random.default_rng(12)
+    n = 300
+    q = rng.uniform(0.5, 2.0, n)
+    c = rng.standard_normal(n) * 2
+    lo, hi = -rng.uniform(0.1, 1, n), rng.uniform(0.1, 1, n)
+    inst = W.from_dense(np.diag(q), np.zeros((0, n)), c, np.zeros(0), name="box bounds")
+    with QPSolver(inst) as s:
+        s.set_bounds(lo, hi)
+        # FP64 to 1e-9; mixed to 1e-6 (its FP32 iterate stalls near 5e-9 here)
+        for prec, tol, err in ((L.PREC_FP64, 1e-9, 1e-9), (L.PREC_MIXED, 1e-6, 1e-5)):
+            info = s.solve(tol=tol, precision=prec)
+            x, _ = s.solution()
+            assert info["termination"] == L.TERM_SOLVED
+            assert np.max(np.abs(x - np.clip(-c / q, lo, hi))) <= err
+
+
+def test_clearing_bounds_returns_to_the_cg_path(built):
+    inst, P, s = built("dense_small")
+    s.solve(tol=1e-6)
+    x0, _ = s.solution()
+    lo, hi = _random_bounds(inst.n, 13)
+    s.set_bounds(lo, hi)
+    s.solve(tol=1e-6)
+    s.set_bounds(None, None)
+    s.solve(tol=1e-6)
+    x1, _ = s.solution()
+    assert np.array_equal(x0, x1)
+
+
+def test_set_bounds_rejects_invalid_bounds(built):
+    inst, P, s = built("dense_small")
+    n = inst.n
+    with pytest.raises(L.QPError):
+        s.set_bounds(np.ones(n), np.zeros(n))  # lo > hi
+    with pytest.raises(L.QPError):
+        s.set_bounds(np.full(n, np.inf), None)
+    with pytest.raises(L.QPError):
+        s.set_bounds(np.full(n, np.nan), None)
+    s.set_bounds(None, None)
