@@ -472,6 +472,15 @@ def run_batch_bench(args):
     other_ms = bt.solve(tol=tol, precision=L.PREC_MIXED, step_mode=other)
     res_other = bt.results()
     bt.close()
+    # the same instances with long-only written as the bounds x >= 0 (BB x-steps)
+    bnds = W.portfolio_batch(BATCH_WORKLOAD["seed"] + rank, BATCH_WORKLOAD["count"], bounds=True)
+    with QPBatch(bnds) as bb:
+        bb.solve(tol=tol, precision=L.PREC_MIXED, step_mode=step)
+        bounds_ms = statistics.mean(
+            bb.solve(tol=tol, precision=L.PREC_MIXED, step_mode=step) for _ in range(2))
+        res_b = bb.results()
+    obj_diff = max(abs(u["primal_obj"] - v["primal_obj"]) / max(1.0, abs(u["primal_obj"]))
+                   for u, v in zip(res, res_b))
     value = _max_over_ranks(statistics.mean(times), ws)
     # plain FP64 GPU PDHCG (the single-QP path), one instance at a time, on a sample
     sample = insts[:16]
@@ -538,6 +547,12 @@ def run_batch_bench(args):
                                              "scaled to 4096",
                        speedup_vs_single_fp64=single_total / value,
                        speedup_vs_fp64_batch=(fp64_ms / 1e3) / value,
+                       bounds_form_s=bounds_ms / 1e3,
+                       bounds_form_solved=int(sum(r["termination"] == 0 for r in res_b)),
+                       bounds_form_attempts_mean=float(np.mean([r["attempts"] for r in res_b])),
+                       bounds_form_objective_max_rel_diff=obj_diff,
+                       bounds_form_note="long-only as x >= 0 (Section 4 BB projected-gradient "
+                                        "x-steps, m = 1 + sectors); device time of one launch",
                        parallelism=f"replicas x{ws}",
                        l2="per-instance data ~100 MB in total, L2-resident; one launch"),
         "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": int(h2d),
@@ -649,10 +664,11 @@ def run_zipf_bench(args):
 
 
 WS_WORKLOAD = {
-    "workload": "parametric portfolio family: n=2000, k=50 factors, 30 sector caps, budget and "
-                "long-only rows (m=2031); per instance mu ~ N(0.05, 0.02) and F = F0 + 10% "
-                "Gaussian; network trained on solver solutions of 20000 instances, judged on "
-                "1000 held-out instances",
+    "workload": "parametric portfolio family: n=2000, k=50 factors, 30 sector caps and the "
+                "budget row (m=31), long-only as the variable bounds x >= 0 (Section 4 BB "
+                "x-steps); per instance mu ~ N(0.05, 0.02) and F = F0 + 10% Gaussian; network "
+                "trained on solver solutions of 20000 instances, judged on 1000 held-out "
+                "instances",
     "n": 2000, "train": 20000, "test": 1000, "tol": 1e-4, "hidden": [512, 512],
 }
 WS_METRIC = ("time to 1e-4 rel. KKT on 1000 held-out portfolio QPs (batched PDHCG): "
@@ -679,7 +695,7 @@ def run_warmstart_bench(args):
     feats, targs, omegas, gen_iters = [], [], [], []
     chunk = 1000
     for s0 in range(1, WS_WORKLOAD["train"] + 1, chunk):
-        insts = W.portfolio_family(0, seeds=range(s0, s0 + chunk), n=n)
+        insts = W.portfolio_family(0, seeds=range(s0, s0 + chunk), n=n, bounds=True)
         res, xs, ys = WS.solve_family(insts, tol=tol, precision=L.PREC_MIXED, step_mode=step)
         keep = [i for i, r in enumerate(res) if r["termination"] == L.TERM_SOLVED]
         feats.append(WS.features([insts[i] for i in keep]))
@@ -698,9 +714,10 @@ def run_warmstart_bench(args):
     train_s = time.perf_counter() - t0
     model = WS.WarmStartModel(net, n, float(np.median(omegas)))
     test = W.portfolio_family(0, seeds=range(WS_WORKLOAD["train"] + 1,
-                                             WS_WORKLOAD["train"] + 1 + WS_WORKLOAD["test"]), n=n)
+                                             WS_WORKLOAD["train"] + 1 + WS_WORKLOAD["test"]), n=n,
+                              bounds=True)
     cold_t, warm_t = [], []
-    for step in range(args.warmup + args.steps):
+    for rep_i in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cold, _, _ = WS.solve_family(test, tol=tol, precision=L.PREC_MIXED, step_mode=step)
@@ -709,7 +726,7 @@ def run_warmstart_bench(args):
         hot, _, _, n_fb = model.solve(test, tol=tol, precision=L.PREC_MIXED, step_mode=step)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        if step >= args.warmup:
+        if rep_i >= args.warmup:
             cold_t.append(t1 - t0)
             warm_t.append(t2 - t1)
     it_c = float(np.mean([r["iterations"] for r in cold]))
@@ -735,7 +752,8 @@ def run_warmstart_bench(args):
                               "batch, prediction included in the warm arm"),
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": int(sum(
                     q.F.nbytes + q.qd.nbytes + q.c.nbytes + q.b.nbytes + q.A_val.nbytes
-                    + q.A_col.nbytes + q.A_rowptr.nbytes for q in test)),
+                    + q.A_col.nbytes + q.A_rowptr.nbytes + q.lo.nbytes + q.hi.nbytes
+                    for q in test)),
                 "d2h_bytes_per_step": int(8 * sum(q.n + q.m for q in test))},
         "roofline": None, "cpu_baseline": None, "gpu_launches": None, "clocks": None,
     }

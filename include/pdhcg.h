@@ -458,6 +458,20 @@ qp_status qp_batch_solution(const qp_batch* bt, double* x, double* y);
 /* Packed start points for warm_start = 1 (NULL: zeros). */
 qp_status qp_batch_set_warm_start(qp_batch* bt, const double* x0, const double* y0);
 
+/*
+ * Packed variable bounds lo <= x <= hi for every instance (host arrays of
+ * sum n_i entries in instance order; NULL means no bound on that side,
+ * -INFINITY / +INFINITY entries are absent bounds), as qp_set_bounds for one
+ * problem (Section 4): every x-step of an instance with a finite bound is the
+ * Barzilai-Borwein projected gradient, its start points are projected into
+ * the box, and its relKKT uses the reduced costs; instances whose bounds are
+ * all absent keep CG.  They hold for
+ * every later qp_batch_solve (all absent: CG again).  Errors:
+ * QP_ERR_INVALID_ARG (NaN, lo > hi, lo = +inf or hi = -inf), QP_ERR_OOM,
+ * QP_ERR_CUDA.
+ */
+qp_status qp_batch_set_bounds(qp_batch* bt, const double* lo, const double* hi);
+
 /* qp_batch_create groups the instances by size (n, largest first) into up
  * to 4 bins of equal count; each bin is one launch on its own stream, with
  * shared memory and block size fitted to its largest instance.

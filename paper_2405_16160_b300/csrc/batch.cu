@@ -96,8 +96,9 @@ struct qp_batch {
   int32_t *Arp = nullptr, *Acol = nullptr, *Trp = nullptr, *Tcol = nullptr;
   int32_t *Along = nullptr, *Tlong = nullptr;
   double *x0 = nullptr, *y0 = nullptr, *x_out = nullptr, *y_out = nullptr;
+  double *lo = nullptr, *hi = nullptr;  // packed variable bounds (allocated on first use)
   BatchResult* res = nullptr;
-  bool warm_set = false, solved = false;
+  bool warm_set = false, solved = false, bounded = false;
   std::vector<BatchResult> h_res;
 };
 
@@ -229,6 +230,8 @@ BatchData<V> batch_data(qp_batch* h, const BatchBin& bin, const V* F, const V* q
   B.x0 = h->x0;
   B.y0 = h->y0;
   B.warm = (o->warm_start == 1 && h->warm_set) ? 1 : 0;
+  B.lo = h->bounded ? h->lo : nullptr;
+  B.hi = h->bounded ? h->hi : nullptr;
   B.x_out = h->x_out;
   B.y_out = h->y_out;
   B.res = h->res;
@@ -594,6 +597,38 @@ qp_status qp_batch_set_warm_start(qp_batch* h, const double* x0, const double* y
   }
   BCUDA(cudaStreamSynchronize(h->stream));
   h->warm_set = true;
+  return finish(h);
+}
+
+qp_status qp_batch_set_bounds(qp_batch* h, const double* lo, const double* hi) {
+  if (!h) return QP_ERR_INVALID_ARG;
+  const size_t N = size_t(h->n_total);
+  std::vector<double> l(N), u(N);
+  bool any = false;
+  for (size_t j = 0; j < N; ++j) {
+    l[j] = lo ? lo[j] : -INFINITY;
+    u[j] = hi ? hi[j] : INFINITY;
+    if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == INFINITY ||
+        u[j] == -INFINITY) {
+      berror("invalid bounds at packed variable %zu: [%g, %g]", j, l[j], u[j]);
+      return QP_ERR_INVALID_ARG;
+    }
+    any = any || std::isfinite(l[j]) || std::isfinite(u[j]);
+  }
+  BTRY(begin(h));
+  h->solved = false;
+  h->bounded = any;
+  if (any) {
+    if (!h->lo) {
+      BTRY(balloc(h, reinterpret_cast<void**>(&h->lo), N * sizeof(double)));
+      BTRY(balloc(h, reinterpret_cast<void**>(&h->hi), N * sizeof(double)));
+    }
+    BCUDA(cudaMemcpyAsync(h->lo, l.data(), N * sizeof(double), cudaMemcpyHostToDevice,
+                          h->stream));
+    BCUDA(cudaMemcpyAsync(h->hi, u.data(), N * sizeof(double), cudaMemcpyHostToDevice,
+                          h->stream));
+    BCUDA(cudaStreamSynchronize(h->stream));  // the staging vectors die here
+  }
   return finish(h);
 }
 

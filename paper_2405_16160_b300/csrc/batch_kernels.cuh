@@ -73,6 +73,10 @@ struct BatchData {
   const double* x0;
   const double* y0;
   int warm;
+  // variable bounds, packed like x (+-inf where absent), or null: with them
+  // every x-step is the Section 4 BB projected gradient
+  const double* lo;
+  const double* hi;
   double* x_out;
   double* y_out;
   BatchResult* res;
@@ -306,9 +310,23 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
   const LocalCsr<double> A64{A.rp, A.col, B.Aval64 + d.off_Ann, m, A.longr, A.nlong};
   const LocalCsr<double> At64{At.rp, At.col, B.Tval64 + d.off_Tnn, n, At.longr, At.nlong};
 
-  // ---- start: x = x0 (warm) or 0, empty averages (Algorithm 1 input)
+  // bounds count for this instance when one of them is finite (as for one
+  // problem: all absent means CG x-steps)
+  const double* lo = nullptr;
+  const double* hi = nullptr;
+  if (B.lo) {
+    bool fin = false;
+    for (int j = tid; j < n; j += NT)
+      fin = fin || isfinite(B.lo[d.off_n + j]) || isfinite(B.hi[d.off_n + j]);
+    if (__syncthreads_or(fin)) {
+      lo = B.lo + d.off_n;
+      hi = B.hi + d.off_n;
+    }
+  }
+  // ---- start: x = x0 (warm) or 0 (projected into the box), empty averages
   for (int j = tid; j < n; j += NT) {
-    const double v = B.warm ? B.x0[d.off_n + j] : 0.0;
+    double v = B.warm ? B.x0[d.off_n + j] : 0.0;
+    if (lo) v = fmin(fmax(v, lo[j]), hi[j]);
     x[j] = v;
     x0[j] = v;
     xa[j] = 0.0;
@@ -377,22 +395,30 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
     cta_spmv<double, NT>(A64, x, axe);                 // A x
     cta_spmv<double, NT>(A64, xa, axa);                // A x~
     __syncthreads();
-    double s4[4] = {0.0, 0.0, 0.0, 0.0}, m7[7] = {0, 0, 0, 0, 0, 0, 0};
+    double s4[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, m7[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int j = tid; j < n; j += NT) {
       const double cj = c[j], q1 = r[j], q2 = p[j];
-      m7[0] = fmax(m7[0], fabs(q1 + q[j] + cj));
+      const double g1 = q1 + q[j] + cj, g2 = q2 + wv[j] + cj;
+      double l1 = 0.0, l2 = 0.0;
+      if (lo) {  // reduced costs of the bounds
+        l1 = reduced_cost(g1, lo[j], hi[j]);
+        l2 = reduced_cost(g2, lo[j], hi[j]);
+        s4[4] += bound_term(l1, lo[j], hi[j]);
+        s4[5] += bound_term(l2, lo[j], hi[j]);
+      }
+      m7[0] = fmax(m7[0], fabs(g1 - l1));
       m7[1] = fmax(m7[1], fabs(q1));
       m7[2] = fmax(m7[2], fabs(q[j]));
       s4[0] = fma(x[j], q1, s4[0]);
       s4[1] = fma(cj, x[j], s4[1]);
-      m7[3] = fmax(m7[3], fabs(q2 + wv[j] + cj));
+      m7[3] = fmax(m7[3], fabs(g2 - l2));
       m7[4] = fmax(m7[4], fabs(q2));
       m7[5] = fmax(m7[5], fabs(wv[j]));
       s4[2] = fma(xa[j], q2, s4[2]);
       s4[3] = fma(cj, xa[j], s4[3]);
       m7[6] = fmax(m7[6], fabs(cj));
     }
-    cta_reduce<NT, 4, 7>(s4, m7, red);
+    cta_reduce<NT, 6, 7>(s4, m7, red);
     double s2[2] = {0.0, 0.0}, m5[5] = {0, 0, 0, 0, 0};
     for (int i = tid; i < m; i += NT) {
       const double bi = b[i], dd = axe[i] - bi, da = axa[i] - bi;
@@ -409,9 +435,9 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
     cta_reduce<NT, 2, 5>(s2, m5, red);
     if (tid == 0) {
       const KktTerms kc = kkt_from(m5[0], m5[1], m5[4], m7[0], m7[1], m7[2], m7[6], s4[0], s4[1],
-                                   s2[0]);
+                                   s2[0], s4[4]);
       const KktTerms ka = kkt_from(m5[2], m5[3], m5[4], m7[3], m7[4], m7[5], m7[6], s4[2], s4[3],
-                                   s2[1]);
+                                   s2[1], s4[5]);
       control_decide(&st, kc, ka, mode);
     }
     __syncthreads();
@@ -453,7 +479,54 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
       int steps = 0;
       bool numerr = false;
       const bool skip = (mode == kCgFixed && nfix <= 0) || rr == 0.0;
-      while (!skip) {
+      if (lo && !skip) {
+        // ---- BB projected gradient (Section 4) from x, with r = p = -g:
+        // alpha0 = g'Mg / g'g, then x+ = min(max(x + r/alpha, lo), hi), s = x+ - x,
+        // r -= M s, Q x += Q s, alpha = s'Ms / s's (M = Q + I/tau)
+        cta_qprod<V, NT>(F, qd, n, k, pv, tv, q);
+        double gmg = 0.0;
+        for (int j = tid; j < n; j += NT) gmg = fma(p[j], q[j] + p[j] * inv_tau, gmg);
+        gmg = cta_sum1<NT>(gmg, red);
+        if (!(gmg > 0.0) || !isfinite(gmg)) numerr = true;
+        double alpha = gmg / rr;
+        while (!numerr) {
+          const double inv_alpha = 1.0 / alpha;
+          double ss = 0.0;
+          for (int j = tid; j < n; j += NT) {
+            const double xj = x[j];
+            const double xn = fmin(fmax(xj + r[j] * inv_alpha, lo[j]), hi[j]);
+            const double sj = xn - xj;
+            p[j] = sj;
+            x[j] = xn;
+            if constexpr (kShadow) {
+              pv[j] = V(sj);
+              xv[j] = V(xn);
+            }
+            ss = fma(sj, sj, ss);
+          }
+          ss = cta_sum1<NT>(ss, red);
+          cta_qprod<V, NT>(F, qd, n, k, pv, tv, q);  // q = Q s
+          double sw = 0.0;
+          for (int j = tid; j < n; j += NT) {
+            const double sj = p[j], qj = q[j];
+            const double wj = qj + sj * inv_tau;
+            r[j] -= wj;
+            qx[j] += qj;
+            sw = fma(sj, wj, sw);
+          }
+          sw = cta_sum1<NT>(sw, red);
+          ++steps;
+          const bool stop =
+              mode == kCgFixed ? steps >= nfix : (sqrt(ss) <= eps || steps >= cgmax);
+          if (stop || ss == 0.0) break;
+          if (!(sw > 0.0) || !isfinite(sw)) {
+            numerr = true;
+            break;
+          }
+          alpha = sw / ss;
+        }
+      }
+      while (!skip && !lo) {
         cta_qprod<V, NT>(F, qd, n, k, pv, tv, q);  // q = Q p
         double pq = 0.0;
         for (int j = tid; j < n; j += NT) pq = fma(p[j], q[j] + p[j] * inv_tau, pq);
@@ -629,7 +702,7 @@ __global__ void __launch_bounds__(NT, batch_min_blocks<NT>()) k_batch(BatchData<
   extern __shared__ double sm_dyn[];
   double* sm = B.ws ? B.ws + (long long)blockIdx.x * B.ws_stride : sm_dyn;
   __shared__ DevState st;
-  __shared__ double red[(NT / 32) * 11];
+  __shared__ double red[(NT / 32) * 13];
   __shared__ int id_s;
   for (;;) {
     if (threadIdx.x == 0) id_s = atomicAdd(B.next, 1);

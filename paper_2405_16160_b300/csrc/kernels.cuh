@@ -1138,17 +1138,6 @@ __global__ void __launch_bounds__(kBlock) k_spmv(CsrT<T> M, const T* __restrict_
 // Qx + A'y + c is inv_d2[j] times the scaled one; the dot products, the
 // reduced costs' signs and lb are invariant under the scaling.
 template <class T>
-__device__ __forceinline__ T reduced_cost(T g, T lo, T hi) {
-  const bool lf = lo > -CUDART_INF_F, hf = hi < CUDART_INF_F;
-  return lf ? (hf ? g : (g > T(0) ? g : T(0))) : (hf ? (g < T(0) ? g : T(0)) : T(0));
-}
-
-template <class T>
-__device__ __forceinline__ T bound_term(T lam, T lo, T hi) {
-  return lam > T(0) ? lam * lo : (lam < T(0) ? -lam * -hi : T(0));
-}
-
-template <class T>
 __global__ void __launch_bounds__(kBlock) k_kkt_n(const T* __restrict__ x,
                                                   const T* __restrict__ x_avg,
                                                   const T* __restrict__ qx,

@@ -81,6 +81,21 @@ struct KktTerms {
   double t[6];
 };
 
+// Variable bounds (+-inf where absent): the reduced cost of gradient entry g
+// (g with both bounds finite, max(g, 0) with only a lower one, min(g, 0) with
+// only an upper one, 0 with none) and its term lo lambda^+ - hi lambda^- of
+// the dual objective.
+template <class T>
+__device__ __forceinline__ T reduced_cost(T g, T lo, T hi) {
+  const bool lf = lo > -CUDART_INF_F, hf = hi < CUDART_INF_F;
+  return lf ? (hf ? g : (g > T(0) ? g : T(0))) : (hf ? (g < T(0) ? g : T(0)) : T(0));
+}
+
+template <class T>
+__device__ __forceinline__ T bound_term(T lam, T lo, T hi) {
+  return lam > T(0) ? lam * lo : (lam < T(0) ? -lam * -hi : T(0));
+}
+
 // lb = lo'lambda^+ - hi'lambda^-, the variable bounds' share of the dual
 // objective (0 without bounds): dual objective -1/2 x'Qx - b'y + lb.
 __device__ __forceinline__ KktTerms kkt_from(double maxviol, double maxAx, double maxb,

@@ -64,6 +64,8 @@ class QPSolver:
     object with the same CSR fields) through ``qp_create``.  With
     ``torch_memory=True`` (default) the device buffers come from PyTorch's
     caching allocator and the work is ordered after PyTorch's current stream.
+    Variable bounds the instance carries (``lo``/``hi``, None when absent)
+    are passed on to ``qp_set_bounds``.
     """
 
     def __init__(self, inst, torch_memory: bool = True, check_symmetry: bool = False,
@@ -89,6 +91,9 @@ class QPSolver:
         L.check(st, "qp_create")
         self.h = h
         self._ctx = ctx
+        lo, hi = getattr(inst, "lo", None), getattr(inst, "hi", None)
+        if lo is not None or hi is not None:
+            self.set_bounds(lo, hi)
 
     def _torch_ctx(self):
         import torch
@@ -225,6 +230,8 @@ class QPBatch:
 
     ``instances`` is a list of ``workloads.LowRankQP`` (or objects with the
     same fields).  Solutions and warm starts are lists of per-instance arrays.
+    Variable bounds the instances carry (``lo``/``hi``) are packed and passed
+    on to ``qp_batch_set_bounds``.
     """
 
     def __init__(self, instances, torch_memory: bool = True):
@@ -252,6 +259,10 @@ class QPBatch:
         L.check(st, "qp_batch_create")
         self.h = h
         self._ctx = ctx
+        if any(getattr(q, "lo", None) is not None or getattr(q, "hi", None) is not None
+               for q in instances):
+            self.set_bounds([getattr(q, "lo", None) for q in instances],
+                            [getattr(q, "hi", None) for q in instances])
 
     def solve(self, options: QPOptions | None = None, **overrides) -> float:
         """Solve every instance; returns the launch's device time in ms."""
@@ -280,6 +291,17 @@ class QPBatch:
         y0 = _f64(np.concatenate(ys), sum(self.ms)) if ys is not None else None
         L.check(self.lib.qp_batch_set_warm_start(self.h, _ptr(x0, c_double), _ptr(y0, c_double)),
                 "qp_batch_set_warm_start")
+
+    def set_bounds(self, los=None, his=None) -> None:
+        """Per-instance bounds: lists of arrays (an entry None: no bound on that side)."""
+        def pack(vs, fill):
+            if vs is None:
+                return None
+            return _f64(np.concatenate([np.full(n, fill) if v is None else np.asarray(v, np.float64)
+                                        for v, n in zip(vs, self.ns)]), sum(self.ns))
+        lo, hi = pack(los, -np.inf), pack(his, np.inf)
+        L.check(self.lib.qp_batch_set_bounds(self.h, _ptr(lo, c_double), _ptr(hi, c_double)),
+                "qp_batch_set_bounds")
 
     def set_threads(self, threads: int) -> None:
         L.check(self.lib.qp_batch_set_threads(self.h, int(threads)), "qp_batch_set_threads")

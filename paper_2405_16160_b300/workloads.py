@@ -62,6 +62,8 @@ class QPInstance:
     b: np.ndarray  # float64 [m]
     name: str = ""
     meta: dict = field(default_factory=dict)
+    lo: np.ndarray | None = None  # variable bounds (+-inf where absent); None: none
+    hi: np.ndarray | None = None
 
     @property
     def nnz_Q(self) -> int:
@@ -251,39 +253,56 @@ class LowRankQP:
     b: np.ndarray
     name: str = ""
     meta: dict = field(default_factory=dict)
+    lo: np.ndarray | None = None  # variable bounds (+-inf where absent); None: none
+    hi: np.ndarray | None = None
 
     def to_instance(self) -> QPInstance:
         Qd = self.F @ self.F.T + np.diag(self.qd)
         Qr, Qc, Qv = _csr_arrays(sp.csr_matrix(Qd))
         return QPInstance(self.n, self.m, self.m_eq, Qr, Qc, Qv, self.A_rowptr, self.A_col,
-                          self.A_val, self.c, self.b, name=self.name, meta=dict(self.meta))
+                          self.A_val, self.c, self.b, name=self.name, meta=dict(self.meta),
+                          lo=self.lo, hi=self.hi)
 
 
-def _portfolio_rows(n: int, sector: np.ndarray, s: int):
-    """A = [budget 1'; -I; sector indicator rows], b = [1; 0; 1.5 |S_j| / n]."""
-    rows = [np.zeros(n, np.int64), np.arange(1, n + 1), 1 + n + sector]
-    cols = [np.arange(n), np.arange(n), np.arange(n)]
-    vals = [np.ones(n), -np.ones(n), np.ones(n)]
-    m = 1 + n + s
+def _portfolio_rows(n: int, sector: np.ndarray, s: int, bounds: bool = False):
+    """A = [budget 1'; -I; sector indicator rows], b = [1; 0; 1.5 |S_j| / n].
+
+    ``bounds``: the long-only rows -x <= 0 are left out (they become the
+    variable bounds x >= 0): A = [budget 1'; sector rows]."""
+    rows = [np.zeros(n, np.int64), 1 + sector]
+    cols = [np.arange(n), np.arange(n)]
+    vals = [np.ones(n), np.ones(n)]
+    m = 1 + s
+    if not bounds:
+        rows = [rows[0], np.arange(1, n + 1), 1 + n + sector]
+        cols = [cols[0], np.arange(n), np.arange(n)]
+        vals = [vals[0], -np.ones(n), np.ones(n)]
+        m = 1 + n + s
     A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(m, n))
     A.sort_indices()
     size = np.bincount(sector, minlength=s).astype(np.float64)
-    b = np.concatenate([[1.0], np.zeros(n), 1.5 * size / n])
+    b = np.concatenate([[1.0]] + ([] if bounds else [np.zeros(n)]) + [1.5 * size / n])
     return A, b
 
 
-def _low_rank_qp(F, qd, mu, sector, s, name, meta) -> LowRankQP:
+def _low_rank_qp(F, qd, mu, sector, s, name, meta, bounds: bool = False) -> LowRankQP:
     n, k = F.shape
-    A, b = _portfolio_rows(n, sector, s)
+    A, b = _portfolio_rows(n, sector, s, bounds)
     Ar, Ac, Av = _csr_arrays(A)
+    lo, hi = (np.zeros(n), np.full(n, np.inf)) if bounds else (None, None)
     return LowRankQP(n, A.shape[0], 1, k, np.ascontiguousarray(F, np.float64),
                      np.asarray(qd, np.float64), Ar, Ac, Av, -np.asarray(mu, np.float64), b,
-                     name=name, meta=meta)
+                     name=name + (" bounds" if bounds else ""), meta=meta, lo=lo, hi=hi)
 
 
-def portfolio(seed: int, index: int, n_lo: int = 20, n_hi: int = 400) -> LowRankQP:
-    """Instance ``index`` of ``portfolio_batch`` (its own substream)."""
+def portfolio(seed: int, index: int, n_lo: int = 20, n_hi: int = 400,
+              bounds: bool = False) -> LowRankQP:
+    """Instance ``index`` of ``portfolio_batch`` (its own substream).
+
+    ``bounds``: the same problem with long-only written as the variable
+    bounds x >= 0 instead of n rows of A (Section 4 solves it with BB
+    projected-gradient x-steps)."""
     rng = np.random.default_rng([seed, index])
     n = int(rng.integers(n_lo, n_hi + 1))
     k = max(n // 10, 1)
@@ -293,16 +312,16 @@ def portfolio(seed: int, index: int, n_lo: int = 20, n_hi: int = 400) -> LowRank
     mu = rng.normal(0.05, 0.02, n)
     sector = rng.integers(0, s, n)
     return _low_rank_qp(F, qd, mu, sector, s, f"portfolio(seed={seed},i={index},n={n})",
-                        {"sectors": s})
+                        {"sectors": s}, bounds)
 
 
 def portfolio_batch(seed: int = 0, count: int = 4096, n_lo: int = 20,
-                    n_hi: int = 400) -> list:
-    return [portfolio(seed, i, n_lo, n_hi) for i in range(count)]
+                    n_hi: int = 400, bounds: bool = False) -> list:
+    return [portfolio(seed, i, n_lo, n_hi, bounds) for i in range(count)]
 
 
 def portfolio_family(base_seed: int = 0, seeds=range(1, 21), n: int = 2000, k: int = 50,
-                     sectors: int = 30) -> list:
+                     sectors: int = 30, bounds: bool = False) -> list:
     """Instances of the parametric family: one per seed in ``seeds``."""
     base = np.random.default_rng([base_seed, 0])
     F0 = base.normal(0.0, np.sqrt(1.0 / k), size=(n, k))
@@ -315,7 +334,7 @@ def portfolio_family(base_seed: int = 0, seeds=range(1, 21), n: int = 2000, k: i
         F = F0 + 0.1 * np.sqrt(1.0 / k) * rng.standard_normal((n, k))
         out.append(_low_rank_qp(F, qd, mu, sector, sectors,
                                 f"portfolio_family(base={base_seed},seed={sd})",
-                                {"sectors": sectors, "mu": mu, "seed": int(sd)}))
+                                {"sectors": sectors, "mu": mu, "seed": int(sd)}, bounds))
     return out
 
 

@@ -225,3 +225,161 @@ def test_batch_adaptive_step_mixed_and_global_memory():
         assert r["termination"] == L.TERM_SOLVED, q.name
         assert O.relkkt(O.problem_from_instance(q.to_instance()), x, y).relkkt <= 1e-4
     assert sum(r["attempts"] for r in res) < 0.8 * sum(r["iterations"] for r in fixed)
+
+
+# ---------------------------------------------------------------- bounds
+def _bounded_edge_instances():
+    """A diagonal box QP (x* = clip(-c/qd, lo, hi)), a two-sided box with a
+    low-rank Q and rows, and an instance whose bounds are all absent (CG)."""
+    rng = np.random.default_rng(11)
+    out = []
+    n = 40
+    qd = rng.uniform(0.5, 2.0, n)
+    c = rng.standard_normal(n)
+    lo = np.where(rng.random(n) < 0.7, -0.3, -np.inf)
+    hi = np.where(rng.random(n) < 0.7, 0.4, np.inf)
+    out.append(W.LowRankQP(n, 0, 0, 0, np.zeros((n, 0)), qd, np.zeros(1, np.int32),
+                           np.zeros(0, np.int32), np.zeros(0), c, np.zeros(0), name="box_diag",
+                           lo=lo, hi=hi))
+    p = W.portfolio(9, 0, 30, 60)
+    out.append(W.LowRankQP(p.n, p.m, p.m_eq, p.k, p.F, p.qd, p.A_rowptr, p.A_col, p.A_val,
+                           p.c, p.b, name="two_sided", lo=np.full(p.n, -0.02),
+                           hi=np.full(p.n, 0.05)))
+    p = W.portfolio(9, 1, 30, 60)
+    out.append(W.LowRankQP(p.n, p.m, p.m_eq, p.k, p.F, p.qd, p.A_rowptr, p.A_col, p.A_val,
+                           p.c, p.b, name="unbounded", lo=np.full(p.n, -np.inf),
+                           hi=np.full(p.n, np.inf)))
+    return out
+
+
+@pytest.fixture(scope="module")
+def bounded_batch():
+    insts = W.portfolio_batch(4, count=20, n_lo=20, n_hi=120, bounds=True) + \
+        _bounded_edge_instances()
+    bt = QPBatch(insts)
+    yield insts, bt
+    bt.close()
+
+
+def _in_box(q, x, slack=0.0):
+    return np.all(x >= q.lo - slack) and np.all(x <= q.hi + slack)
+
+
+@pytest.mark.parametrize("step", ["fixed", "adaptive"])
+def test_batch_bounds_fp64_match_oracle(bounded_batch, step):
+    """BB x-steps (Section 4) per instance against the oracle's, with the
+    reduced-cost relKKT re-scored by the oracle."""
+    insts, bt = bounded_batch
+    tol = 1e-6
+    mode = L.STEP_ADAPTIVE if step == "adaptive" else L.STEP_FIXED
+    bt.solve(tol=tol, precision=L.PREC_FP64, step_mode=mode)
+    res = bt.results()
+    xs, ys = bt.solution()
+    same = tot_gpu = tot_oracle = 0
+    for q, r, x, y in zip(insts, res, xs, ys):
+        P, ores = _oracle(q, tol, step_mode=mode)
+        assert ores.termination == O.SOLVED, q.name
+        assert r["termination"] == L.TERM_SOLVED, q.name
+        assert _in_box(q, x), q.name
+        rescored = O.relkkt(P, x, y)
+        assert rescored.relkkt <= tol, q.name
+        assert r["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-12), q.name
+        assert r["dual_obj"] == pytest.approx(rescored.dual_obj, rel=1e-9, abs=1e-12), q.name
+        assert rescored.primal_obj == pytest.approx(ores.kkt.primal_obj, rel=1e-5, abs=1e-9)
+        if step == "fixed":
+            same += (r["iterations"] == ores.iterations and r["cg_steps"] == ores.cg_steps)
+        else:
+            same += r["attempts"] == ores.state.attempts
+        tot_gpu += r["attempts"]
+        tot_oracle += ores.state.attempts
+    if step == "fixed":
+        assert same >= 0.8 * len(insts)
+    else:
+        # a projected step moves the active set, so a last-bit difference in
+        # F(F'p) against the explicit Q p changes eta and the BB steps of more
+        # instances than without bounds; the evaluation points (attempts, in
+        # multiples of 64) still agree on most, and the work within 10%
+        assert same >= 0.6 * len(insts)
+        assert abs(tot_gpu - tot_oracle) <= 0.1 * tot_oracle
+
+
+def test_batch_bounds_box_closed_form(bounded_batch):
+    insts, bt = bounded_batch
+    bt.solve(tol=1e-9, precision=L.PREC_FP64)
+    xs, _ = bt.solution()
+    i = [q.name for q in insts].index("box_diag")
+    q = insts[i]
+    assert np.allclose(xs[i], np.clip(-q.c / q.qd, q.lo, q.hi), rtol=0, atol=1e-8)
+
+
+def test_batch_bounds_equal_long_only_rows():
+    """Long-only written as x >= 0 and as the rows -x <= 0 is one problem:
+    the same optimal objective, the bounds form in far fewer attempts."""
+    rows = W.portfolio_batch(6, count=12, n_lo=50, n_hi=200)
+    bnds = W.portfolio_batch(6, count=12, n_lo=50, n_hi=200, bounds=True)
+    with QPBatch(rows) as a, QPBatch(bnds) as b:
+        a.solve(tol=1e-7, precision=L.PREC_FP64, step_mode=L.STEP_ADAPTIVE)
+        b.solve(tol=1e-7, precision=L.PREC_FP64, step_mode=L.STEP_ADAPTIVE)
+        ra, rb = a.results(), b.results()
+        xb, _ = b.solution()
+    for p, u, v, x in zip(rows, ra, rb, xb):
+        assert u["termination"] == L.TERM_SOLVED and v["termination"] == L.TERM_SOLVED
+        assert v["primal_obj"] == pytest.approx(u["primal_obj"], rel=1e-5, abs=1e-8), p.name
+        assert np.all(x >= 0.0) and abs(x.sum() - 1.0) < 1e-5
+    assert sum(v["attempts"] for v in rb) < 0.5 * sum(u["attempts"] for u in ra)
+
+
+def test_batch_bounds_mixed_meets_tolerance_in_fp64(bounded_batch):
+    insts, bt = bounded_batch
+    tol = 1e-4
+    bt.solve(tol=tol, precision=L.PREC_MIXED, step_mode=L.STEP_ADAPTIVE)
+    res = bt.results()
+    xs, ys = bt.solution()
+    for q, r, x, y in zip(insts, res, xs, ys):
+        P = O.problem_from_instance(q.to_instance())
+        assert r["termination"] == L.TERM_SOLVED, q.name
+        assert _in_box(q, x), q.name
+        rescored = O.relkkt(P, x, y)
+        assert rescored.relkkt <= tol, q.name
+        assert r["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-12), q.name
+
+
+def test_batch_bounds_warm_start_is_projected(bounded_batch):
+    """A warm start outside the box is projected: from the solution moved out
+    of the box the solve still ends in it, at the same objective."""
+    insts, bt = bounded_batch
+    bt.solve(tol=1e-7, precision=L.PREC_FP64)
+    xs, ys = bt.solution()
+    ref = bt.results()
+    bt.set_warm_start([x - 1.0 for x in xs], ys)
+    bt.solve(tol=1e-7, precision=L.PREC_FP64, warm_start=1)
+    res = bt.results()
+    xw, _ = bt.solution()
+    bt.set_warm_start(None, None)
+    for q, r, u, x in zip(insts, res, ref, xw):
+        assert r["termination"] == L.TERM_SOLVED and _in_box(q, x), q.name
+        assert r["primal_obj"] == pytest.approx(u["primal_obj"], rel=1e-5, abs=1e-8), q.name
+
+
+def test_batch_bounds_cleared_and_invalid():
+    insts = W.portfolio_batch(8, count=4, n_lo=20, n_hi=60)
+    with QPBatch(insts) as bt:
+        bt.solve(tol=1e-6, precision=L.PREC_FP64)
+        a = bt.results()
+        bt.set_bounds([np.zeros(q.n) for q in insts], None)
+        bt.solve(tol=1e-6, precision=L.PREC_FP64)
+        bt.set_bounds(None, None)  # every bound absent: CG again
+        bt.solve(tol=1e-6, precision=L.PREC_FP64)
+        c = bt.results()
+        assert [r["iterations"] for r in a] == [r["iterations"] for r in c]
+        assert [r["cg_steps"] for r in a] == [r["cg_steps"] for r in c]
+        n = sum(q.n for q in insts)
+        for lo, hi in ((np.ones(n), np.zeros(n)), (np.full(n, np.nan), None),
+                       (np.full(n, np.inf), None), (None, np.full(n, -np.inf))):
+            with pytest.raises(L.QPError):
+                bt.set_bounds(None if lo is None else _split(lo, insts),
+                              None if hi is None else _split(hi, insts))
+
+
+def _split(v, insts):
+    return np.split(v, np.cumsum([q.n for q in insts])[:-1])

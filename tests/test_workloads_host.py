@@ -41,3 +41,20 @@ def test_portfolio_family_perturbs_a_shared_base():
     assert np.array_equal(f.qd, g.qd) and np.array_equal(f.A_col, g.A_col)
     d = f.F - g.F  # two independent perturbations of std 0.1/sqrt(k)
     assert abs(d.std() - np.sqrt(2) * 0.1 / np.sqrt(50)) < 0.002
+
+
+def test_portfolio_bounds_form_drops_only_the_long_only_rows():
+    for i in range(3):
+        p, q = W.portfolio(0, i), W.portfolio(0, i, bounds=True)
+        s = p.meta["sectors"]
+        assert q.m == 1 + s and q.m_eq == 1 and np.array_equal(p.F, q.F)
+        assert np.array_equal(p.c, q.c) and np.array_equal(p.qd, q.qd)
+        Ap = p.to_instance().scipy_A().toarray()
+        Aq = q.to_instance().scipy_A().toarray()
+        keep = np.r_[0, np.arange(1 + p.n, p.m)]
+        assert np.array_equal(Ap[keep], Aq) and np.array_equal(p.b[keep], q.b)
+        assert np.array_equal(Ap[1:1 + p.n], -np.eye(p.n)) and np.all(p.b[1:1 + p.n] == 0)
+        assert np.all(q.lo == 0) and np.all(np.isinf(q.hi))
+        inst = q.to_instance()
+        assert inst.lo is q.lo and inst.hi is q.hi
+    assert p.lo is None and p.to_instance().lo is None
