@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -49,6 +50,34 @@ __global__ void k_to_float(const double* __restrict__ in, float* out, long long 
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     out[i] = float(in[i]);
+}
+
+// Every instance's F from the caller's row-major n x k layout (uploaded as
+// is) to the column-major one the solver reads, one destination entry per
+// thread (coalesced writes).  The lowest id of an instance holding a
+// non-finite entry goes to *bad (INT_MAX when there is none).
+__global__ void k_F_colmajor(const BatchDesc* __restrict__ desc, int count,
+                             const double* __restrict__ Frow, double* Fcol, long long total,
+                             int* bad) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    // the owning instance: the last one with off_F <= e (instances without
+    // F entries share their successor's offset and are skipped this way)
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (desc[mid].off_F <= e)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const BatchDesc d = desc[lo];
+    const long long t = e - d.off_F;
+    const long long l = t / d.n, j = t - l * d.n;
+    const double v = Frow[d.off_F + j * d.k + l];
+    Fcol[e] = v;
+    if (!isfinite(v)) atomicMin(bad, lo);
+  }
 }
 
 constexpr int kThreadChoices[] = {64, 128, 256, 512};
@@ -122,6 +151,22 @@ qp_status balloc(qp_batch* h, void** out, size_t bytes) {
   h->allocs.emplace_back(ptr, bytes);
   *out = ptr;
   return QP_OK;
+}
+
+// Frees one allocation of the handle now (after the handle's stream is idle).
+qp_status bfree(qp_batch* h, void* ptr) {
+  for (size_t i = 0; i < h->allocs.size(); ++i) {
+    if (h->allocs[i].first != ptr) continue;
+    BCUDA(cudaStreamSynchronize(h->stream));
+    if (h->has_alloc)
+      h->ctx.free(ptr, h->allocs[i].second, h->ctx.user, h->ctx.stream);
+    else
+      BCUDA(cudaFree(ptr));
+    h->allocs.erase(h->allocs.begin() + long(i));
+    return QP_OK;
+  }
+  berror("internal: freeing an unknown allocation");
+  return QP_ERR_CUDA;
 }
 
 template <class T>
@@ -315,7 +360,8 @@ qp_status validate_batch_options(const qp_options* o) {
 
 qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
   std::vector<BatchDesc> desc(static_cast<size_t>(count));
-  std::vector<double> F, qd, c, b, Av, Tv;
+  std::vector<double> qd, c, b, Av, Tv;
+  int64_t F_total = 0;
   std::vector<int32_t> Arp, Acol, Trp, Tcol, Along, Tlong;
   std::string why;
   for (int32_t i = 0; i < count; ++i) {
@@ -329,9 +375,9 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
       berror("instance %d: A: %s", i, why.c_str());
       return QP_ERR_INVALID_ARG;
     }
+    // (F is checked on the device, where it is transposed)
     if (!finite_all(q.qd, size_t(q.n)) || !finite_all(q.c, size_t(q.n)) ||
-        (q.m > 0 && !finite_all(q.b, size_t(q.m))) ||
-        (q.k > 0 && !finite_all(q.F, size_t(q.n) * size_t(q.k)))) {
+        (q.m > 0 && !finite_all(q.b, size_t(q.m)))) {
       berror("instance %d: a value is not finite", i);
       return QP_ERR_INVALID_ARG;
     }
@@ -355,15 +401,14 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
     d.k = q.k;
     d.off_n = int64_t(c.size());
     d.off_m = int64_t(b.size());
-    d.off_F = int64_t(F.size());
+    d.off_F = F_total;
     d.off_Arp = int64_t(Arp.size());
     d.off_Ann = int64_t(Acol.size());
     d.off_Trp = int64_t(Trp.size());
     d.off_Tnn = int64_t(Tcol.size());
     d.off_Along = int32_t(Along.size());
     d.off_Tlong = int32_t(Tlong.size());
-    for (int32_t l = 0; l < q.k; ++l)
-      for (int32_t j = 0; j < q.n; ++j) F.push_back(q.F[size_t(j) * q.k + l]);  // column-major
+    F_total += int64_t(q.n) * q.k;
     qd.insert(qd.end(), q.qd, q.qd + q.n);
     c.insert(c.end(), q.c, q.c + q.n);
     if (q.m > 0) b.insert(b.end(), q.b, q.b + q.m);
@@ -417,7 +462,36 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
   }
   BCUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
   BTRY(bupload(h, &h->desc, desc));
-  BTRY(bupload(h, &h->F64, F));
+  // F: the caller's row-major arrays copied as they are, then transposed and
+  // checked on the device
+  BTRY(balloc(h, reinterpret_cast<void**>(&h->F64), size_t(F_total) * sizeof(double)));
+  if (F_total > 0) {
+    double* Frow = nullptr;
+    int* bad = nullptr;
+    BTRY(balloc(h, reinterpret_cast<void**>(&Frow), size_t(F_total) * sizeof(double)));
+    BTRY(balloc(h, reinterpret_cast<void**>(&bad), sizeof(int)));
+    for (int32_t i = 0; i < count; ++i) {
+      const qp_instance& q = inst[i];
+      if (q.k > 0)
+        BCUDA(cudaMemcpyAsync(Frow + desc[size_t(i)].off_F, q.F,
+                              size_t(q.n) * size_t(q.k) * sizeof(double), cudaMemcpyHostToDevice,
+                              h->stream));
+    }
+    const int big = INT_MAX;
+    BCUDA(cudaMemcpyAsync(bad, &big, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    const int grid = int(std::min<int64_t>((F_total + 255) / 256, int64_t(h->num_sms) * 8));
+    k_F_colmajor<<<grid, 256, 0, h->stream>>>(h->desc, count, Frow, h->F64, (long long)F_total,
+                                              bad);
+    BCUDA(cudaGetLastError());
+    int first_bad = INT_MAX;
+    BCUDA(cudaMemcpyAsync(&first_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    BCUDA(cudaStreamSynchronize(h->stream));
+    BTRY(bfree(h, Frow));
+    if (first_bad != INT_MAX) {
+      berror("instance %d: a value is not finite", first_bad);
+      return QP_ERR_INVALID_ARG;
+    }
+  }
   BTRY(bupload(h, &h->qd64, qd));
   BTRY(bupload(h, &h->c, c));
   BTRY(bupload(h, &h->b, b));
@@ -429,15 +503,18 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
   BTRY(bupload(h, &h->Tval64, Tv));
   BTRY(bupload(h, &h->Along, Along));
   BTRY(bupload(h, &h->Tlong, Tlong));
-  BTRY(to_float(h, h->F64, &h->F32, F.size()));
+  BTRY(to_float(h, h->F64, &h->F32, size_t(F_total)));
   BTRY(to_float(h, h->qd64, &h->qd32, qd.size()));
   BTRY(to_float(h, h->Aval64, &h->Aval32, Av.size()));
   BTRY(to_float(h, h->Tval64, &h->Tval32, Tv.size()));
-  const std::vector<double> zn(size_t(h->n_total), 0.0), zm(size_t(h->m_total), 0.0);
-  BTRY(bupload(h, &h->x0, zn));
-  BTRY(bupload(h, &h->y0, zm));
-  BTRY(bupload(h, &h->x_out, zn));
-  BTRY(bupload(h, &h->y_out, zm));
+  for (double** v : {&h->x0, &h->x_out}) {
+    BTRY(balloc(h, reinterpret_cast<void**>(v), size_t(h->n_total) * sizeof(double)));
+    BCUDA(cudaMemsetAsync(*v, 0, size_t(h->n_total) * sizeof(double), h->stream));
+  }
+  for (double** v : {&h->y0, &h->y_out}) {
+    BTRY(balloc(h, reinterpret_cast<void**>(v), size_t(h->m_total) * sizeof(double)));
+    BCUDA(cudaMemsetAsync(*v, 0, size_t(h->m_total) * sizeof(double), h->stream));
+  }
   BTRY(balloc(h, reinterpret_cast<void**>(&h->res), size_t(count) * sizeof(BatchResult)));
   BCUDA(cudaStreamSynchronize(h->stream));  // the host staging vectors die here
   return QP_OK;

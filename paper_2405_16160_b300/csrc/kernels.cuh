@@ -60,6 +60,10 @@ constexpr unsigned kKktMMaxMask = 0b1011011u;      // 7 entries, see k_kkt_m
 constexpr int kLongRow = 4096;
 constexpr int kSegLen = 2048;
 
+// Rows longer than med_min (and at most kLongRow) are "medium": the row
+// kernels leave them to one whole warp each, after the regular rows, so that
+// a skewed row-length distribution (a few rows of thousands of entries among
+// rows of a handful) does not stall a warp's other row groups.
 template <class T>
 struct CsrT {
   const int32_t* rowptr;
@@ -69,6 +73,9 @@ struct CsrT {
   const int32_t* long_rows = nullptr;  // ascending ids of the long rows
   const T* long_val = nullptr;         // their products, from the pre-pass
   int32_t nlong = 0;
+  const int32_t* med_rows = nullptr;   // ascending ids of the medium rows
+  int32_t nmed = 0;
+  int32_t med_min = 0x7fffffff;
 };
 
 // Segment table of a matrix's long rows: segment s covers entries
@@ -441,8 +448,15 @@ __device__ __forceinline__ int long_slot(const CsrT<T>& M, int i) {
   return lo;
 }
 
-template <int G, class T, class F>
+// The row kernels' template parameter GM is the group size G, plus kMedRows
+// when the matrix has medium rows (so that matrices without them run the
+// plain row loop).
+constexpr int kMedRows = 64;
+
+template <int GM, class T, class F>
 __device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f) {
+  constexpr int G = GM & (kMedRows - 1);
+  constexpr bool kMed = (GM & kMedRows) != 0;
   constexpr int kRowsPerWarp = 32 / G;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (G - 1);
@@ -451,17 +465,29 @@ __device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f) {
   for (long long base = gw * kRowsPerWarp; base < M.rows; base += nw * kRowsPerWarp) {
     const int i = int(base) + lane / G;
     T s = T(0);
-    if (i < M.rows) {
+    bool own = i < M.rows;
+    if (own) {
       const int b = __ldg(M.rowptr + i), e = __ldg(M.rowptr + i + 1);
       if (e - b > kLongRow) {
         if (sub == 0) s = M.long_val[long_slot(M, i)];
+      } else if (kMed && e - b > M.med_min) {
+        own = false;  // a medium row: taken by a whole warp below
       } else {
         s = row_dot<G>(M, v, b, e, sub);
       }
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += shfl_xor(s, o);
-    if (i < M.rows) f(i, s, sub == 0);
+    if (own) f(i, s, sub == 0);
+  }
+  if constexpr (kMed) {
+    for (long long w = gw; w < M.nmed; w += nw) {
+      const int i = __ldg(M.med_rows + w);
+      T s = row_dot<32>(M, v, __ldg(M.rowptr + i), __ldg(M.rowptr + i + 1), lane);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += shfl_xor(s, o);
+      f(i, s, lane == 0);
+    }
   }
 }
 

@@ -83,6 +83,9 @@ struct DevMat {
   int32_t rows = 0;
   int64_t nnz = 0;
   int G64 = 1, G32 = 4;
+  // medium rows (more than 16 G entries, at most kLongRow) per precision
+  int32_t *med64 = nullptr, *med32 = nullptr;
+  int32_t nmed64 = 0, nmed32 = 0, med_min64 = 0x7fffffff, med_min32 = 0x7fffffff;
   // rows longer than kLongRow: segment table and per-precision work buffers
   int32_t nlong = 0, nseg = 0;
   int32_t *long_rows = nullptr, *seg_begin = nullptr, *seg_end = nullptr, *seg_ptr = nullptr;
@@ -93,9 +96,11 @@ struct DevMat {
 template <class T>
 CsrT<T> view(const DevMat& M) {
   if constexpr (std::is_same<T, double>::value)
-    return CsrT<double>{M.rowptr, M.col, M.val, M.rows, M.long_rows, M.long64, M.nlong};
+    return CsrT<double>{M.rowptr, M.col,  M.val,   M.rows,     M.long_rows, M.long64,
+                        M.nlong,  M.med64, M.nmed64, M.med_min64};
   else
-    return CsrT<float>{M.rowptr, M.col, M.val32, M.rows, M.long_rows, M.long32, M.nlong};
+    return CsrT<float>{M.rowptr, M.col,  M.val32, M.rows,     M.long_rows, M.long32,
+                       M.nlong,  M.med32, M.nmed32, M.med_min32};
 }
 
 LongRows long_rows_of(const DevMat& M) {
@@ -126,7 +131,11 @@ T* long_buf(const DevMat& M) {
 
 template <class T>
 int lanes(const DevMat& M) {
-  return std::is_same<T, double>::value ? M.G64 : M.G32;
+  // the group size, with the medium-row flag of the row kernels
+  if constexpr (std::is_same<T, double>::value)
+    return M.G64 | (M.nmed64 > 0 ? kMedRows : 0);
+  else
+    return M.G32 | (M.nmed32 > 0 ? kMedRows : 0);
 }
 
 // Vectors of one precision.
@@ -292,6 +301,10 @@ qp_status dispatch_g(int G, F&& f) {
     case 4: f(std::integral_constant<int, 4>{}); return QP_OK;
     case 8: f(std::integral_constant<int, 8>{}); return QP_OK;
     case 32: f(std::integral_constant<int, 32>{}); return QP_OK;
+    case 1 | kMedRows: f(std::integral_constant<int, 1 | kMedRows>{}); return QP_OK;
+    case 2 | kMedRows: f(std::integral_constant<int, 2 | kMedRows>{}); return QP_OK;
+    case 4 | kMedRows: f(std::integral_constant<int, 4 | kMedRows>{}); return QP_OK;
+    case 8 | kMedRows: f(std::integral_constant<int, 8 | kMedRows>{}); return QP_OK;
     default: set_error("unsupported group size %d", G); return QP_ERR_INVALID_ARG;
   }
 }
@@ -777,6 +790,28 @@ qp_status finish_matrix(qp_handle* h, DevMat* M, const int32_t* host_rowptr) {
     }
     sp.push_back(int32_t(sb.size()));
   }
+  // Medium rows of each precision's row kernels: more than 16 entries per
+  // lane of a row group (none with a whole warp per row).  The FP64 kernels
+  // give short rows one lane each to keep the DFMA slots full, so a warp per
+  // row pays off there only from 64 entries.
+  for (int fp32 = 0; fp32 < 2; ++fp32) {
+    const int G = fp32 ? M->G32 : M->G64;
+    if (G >= 32) continue;
+    const int32_t med_min = fp32 ? 16 * G : std::max(16 * G, 64);
+    std::vector<int32_t> md;
+    for (int32_t i = 0; i < M->rows; ++i) {
+      const int32_t len = host_rowptr[i + 1] - host_rowptr[i];
+      if (len > med_min && len <= kLongRow) md.push_back(i);
+    }
+    (fp32 ? M->med_min32 : M->med_min64) = med_min;
+    (fp32 ? M->nmed32 : M->nmed64) = int32_t(md.size());
+    if (!md.empty()) {
+      int32_t** dst = fp32 ? &M->med32 : &M->med64;
+      QP_TRY(dalloc(h, dst, md.size()));
+      QP_TRY(upload(h, *dst, md.data(), md.size() * sizeof(int32_t)));
+      QP_TRY(sync(h));  // md dies with this scope
+    }
+  }
   M->nlong = int32_t(lr.size());
   M->nseg = int32_t(sb.size());
   if (M->nlong > 0) {
@@ -1097,14 +1132,14 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
     // the persistent CG and BB kernels share the grid: the smaller residency
     int occ_bb = 0;
     if (fp32)
-      QP_TRY(dispatch_g(h->Q.G32, [&](auto g) {
+      QP_TRY(dispatch_g(lanes<float>(h->Q), [&](auto g) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<decltype(g)::value, float>,
                                                       kCgBlock, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_bb, k_bb<decltype(g)::value, float>,
                                                       kCgBlock, 0);
       }));
     else
-      QP_TRY(dispatch_g(h->Q.G64, [&](auto g) {
+      QP_TRY(dispatch_g(lanes<double>(h->Q), [&](auto g) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<decltype(g)::value, double>,
                                                       kCgBlock, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_bb, k_bb<decltype(g)::value, double>,

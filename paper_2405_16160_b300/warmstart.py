@@ -19,6 +19,8 @@ from __future__ import annotations
 
 from ctypes import POINTER, byref, c_double, c_float, c_int32, c_void_p
 
+import time
+
 import numpy as np
 
 from . import _lib as L
@@ -132,9 +134,12 @@ def split_prediction(pred: np.ndarray, n: int, m_eq: int = 1):
     return xs, ys
 
 
-def solve_family(insts, options: QPOptions | None = None, warm=None, **overrides):
+def solve_family(insts, options: QPOptions | None = None, warm=None, phases=None, **overrides):
     """Solve instances with the batched solver (warm = (xs, ys) or None).
-    Returns (results, xs, ys)."""
+    Returns (results, xs, ys).  ``phases`` (a dict, optional) accumulates the
+    wall seconds of create / set_warm_start and of results + solution, and
+    the solve launch's device milliseconds."""
+    t0 = time.perf_counter()
     with QPBatch(insts) as bt:
         o = options or QPOptions()
         for k, v in overrides.items():
@@ -142,19 +147,28 @@ def solve_family(insts, options: QPOptions | None = None, warm=None, **overrides
         if warm is not None:
             bt.set_warm_start(*warm)
             o.warm_start = 1
-        bt.solve(o)
+        t1 = time.perf_counter()
+        ms = bt.solve(o)
+        t2 = time.perf_counter()
         res = bt.results()
         xs, ys = bt.solution()
+        t3 = time.perf_counter()
+    if phases is not None:
+        for key, v in (("create_s", t1 - t0), ("solve_s", t2 - t1), ("solve_device_ms", ms),
+                       ("fetch_s", t3 - t2)):
+            phases[key] = phases.get(key, 0.0) + v
     return res, xs, ys
 
 
-def solve_with_fallback(insts, warm, options: QPOptions | None = None, **overrides):
+def solve_with_fallback(insts, warm, options: QPOptions | None = None, phases=None,
+                        **overrides):
     """Warm-started batched solve; instances it leaves unsolved are solved
     again from the cold start.  Returns (results, xs, ys, n_fallback)."""
-    res, xs, ys = solve_family(insts, options, warm=warm, **overrides)
+    res, xs, ys = solve_family(insts, options, warm=warm, phases=phases, **overrides)
     bad = [i for i, r in enumerate(res) if r["termination"] != L.TERM_SOLVED]
     if bad:
-        res2, xs2, ys2 = solve_family([insts[i] for i in bad], options, **overrides)
+        res2, xs2, ys2 = solve_family([insts[i] for i in bad], options, phases=phases,
+                                      **overrides)
         for j, i in enumerate(bad):
             res[i], xs[i], ys[i] = res2[j], xs2[j], ys2[j]
     return res, xs, ys, len(bad)
@@ -219,7 +233,11 @@ class WarmStartModel:
         """(x0s, y0s) for the instances."""
         return predict(self.net, features(insts), self.n)
 
-    def solve(self, insts, options: QPOptions | None = None, **overrides):
+    def solve(self, insts, options: QPOptions | None = None, phases=None, **overrides):
         """Warm-started batched solve with the cold-start fallback."""
-        return solve_with_fallback(insts, self.propose(insts), options, omega0=self.omega0,
+        t0 = time.perf_counter()
+        warm = self.propose(insts)
+        if phases is not None:
+            phases["propose_s"] = phases.get("propose_s", 0.0) + time.perf_counter() - t0
+        return solve_with_fallback(insts, warm, options, phases=phases, omega0=self.omega0,
                                    **overrides)

@@ -383,3 +383,38 @@ def test_batch_bounds_cleared_and_invalid():
 
 def _split(v, insts):
     return np.split(v, np.cumsum([q.n for q in insts])[:-1])
+
+
+def test_batch_create_rejects_non_finite_F_by_instance():
+    """F is transposed and checked on the device: a NaN is reported with
+    the lowest instance id holding one, and nothing is created."""
+    import dataclasses
+    insts = W.portfolio_batch(8, count=4, n_lo=20, n_hi=40)
+    for i in (1, 3):
+        F = insts[i].F.copy()
+        F[2, 0] = np.nan if i == 1 else np.inf
+        insts[i] = dataclasses.replace(insts[i], F=F)
+    with pytest.raises(L.QPError, match="instance 1"):
+        QPBatch(insts)
+
+
+def test_batch_F_layout_matches_the_explicit_Q():
+    """The device transposition of F: the batched solve of instances with
+    several factor counts (k = 1 .. 7) and k = 0 in between matches the
+    oracle's objective on the explicit Q."""
+    rng = np.random.default_rng(21)
+    insts = []
+    for k in (1, 0, 7, 3, 0, 5):
+        p = W.portfolio(12, len(insts), 20, 50)
+        F = rng.normal(0.0, np.sqrt(1.0 / max(k, 1)), size=(p.n, k))
+        insts.append(W.LowRankQP(p.n, p.m, p.m_eq, k, F, p.qd, p.A_rowptr, p.A_col, p.A_val,
+                                 p.c, p.b, name=f"k{k}_{len(insts)}"))
+    with QPBatch(insts) as bt:
+        bt.solve(tol=1e-7, precision=L.PREC_FP64)
+        res = bt.results()
+        xs, ys = bt.solution()
+    for q, r, x, y in zip(insts, res, xs, ys):
+        P, ores = _oracle(q, 1e-7)
+        assert r["termination"] == L.TERM_SOLVED, q.name
+        assert O.relkkt(P, x, y).relkkt <= 1e-7, q.name
+        assert r["primal_obj"] == pytest.approx(ores.kkt.primal_obj, rel=1e-6, abs=1e-9), q.name
