@@ -35,7 +35,7 @@ class QPOptionsC(Structure):
         ("theta_pw", c_double), ("eps_zero", c_double), ("primal_weight_update", c_int32),
         ("warm_start", c_int32), ("omega0", c_double), ("eta", c_double),
         ("kernel_timing", c_int32), ("debug_flags", c_uint32), ("precision", c_int32),
-        ("refine", c_int32), ("step_mode", c_int32), ("pad1", c_int32),
+        ("refine", c_int32), ("step_mode", c_int32), ("mixed_stall_evals", c_int32),
         ("reserved", c_int64 * 6),
     ]
 

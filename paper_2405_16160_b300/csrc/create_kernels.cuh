@@ -106,13 +106,23 @@ __global__ void __launch_bounds__(kBlock) k_scale_norms_n(CsrT<double> Q, CsrT<d
       lm &= lm - 1;
       const double dj = d2[jj];
       double s = 0.0, sa = 0.0;
-      for (int k = __ldg(Q.rowptr + jj) + lane; k < __ldg(Q.rowptr + jj + 1); k += 32) {
-        const double v = (dj * fabs(Q.val[k])) * d2[Q.col[k]];
-        s = inf ? fmax(s, v) : s + v;
+      const int qb = __ldg(Q.rowptr + jj), qe = __ldg(Q.rowptr + jj + 1);
+      const int ab = __ldg(At.rowptr + jj), ae = __ldg(At.rowptr + jj + 1);
+      if (qe - qb > kLongRow) {  // from the segment pre-pass (k_scale_long_parts)
+        if (lane == 0) s = dj * Q.long_val[long_slot(Q, jj)];
+      } else {
+        for (int k = qb + lane; k < qe; k += 32) {
+          const double v = (dj * fabs(Q.val[k])) * d2[Q.col[k]];
+          s = inf ? fmax(s, v) : s + v;
+        }
       }
-      for (int k = __ldg(At.rowptr + jj) + lane; k < __ldg(At.rowptr + jj + 1); k += 32) {
-        const double v = (d1[At.col[k]] * fabs(At.val[k])) * dj;
-        sa = inf ? fmax(sa, v) : sa + v;
+      if (ae - ab > kLongRow) {
+        if (lane == 0) sa = dj * At.long_val[long_slot(At, jj)];
+      } else {
+        for (int k = ab + lane; k < ae; k += 32) {
+          const double v = (d1[At.col[k]] * fabs(At.val[k])) * dj;
+          sa = inf ? fmax(sa, v) : sa + v;
+        }
       }
       s = inf ? warp_max_d(s) : warp_sum(s);
       sa = inf ? warp_max_d(sa) : warp_sum(sa);
@@ -151,9 +161,14 @@ __global__ void __launch_bounds__(kBlock) k_scale_norms_m(CsrT<double> A,
       lm &= lm - 1;
       const double di = d1[ii];
       double s = 0.0;
-      for (int k = __ldg(A.rowptr + ii) + lane; k < __ldg(A.rowptr + ii + 1); k += 32) {
-        const double v = (di * fabs(A.val[k])) * d2[A.col[k]];
-        s = inf ? fmax(s, v) : s + v;
+      const int b = __ldg(A.rowptr + ii), e = __ldg(A.rowptr + ii + 1);
+      if (e - b > kLongRow) {  // from the segment pre-pass (k_scale_long_parts)
+        if (lane == 0) s = di * A.long_val[long_slot(A, ii)];
+      } else {
+        for (int k = b + lane; k < e; k += 32) {
+          const double v = (di * fabs(A.val[k])) * d2[A.col[k]];
+          s = inf ? fmax(s, v) : s + v;
+        }
       }
       s = inf ? warp_max_d(s) : warp_sum(s);
       if (lane == 0) rm[ii] = s;
@@ -193,10 +208,65 @@ __global__ void __launch_bounds__(kBlock) k_scale_matrix(CsrT<double> M,
     while (lm) {
       const int ii = int(base) + (__ffs(lm) - 1) / kScaleGroup;
       lm &= lm - 1;
+      const int b = __ldg(M.rowptr + ii), e = __ldg(M.rowptr + ii + 1);
+      if (e - b > kLongRow) continue;  // k_scale_long_matrix
       const double di = dr[ii];
-      for (int k = __ldg(M.rowptr + ii) + lane; k < __ldg(M.rowptr + ii + 1); k += 32)
-        val[k] = (di * val[k]) * dc[M.col[k]];
+      for (int k = b + lane; k < e; k += 32) val[k] = (di * val[k]) * dc[M.col[k]];
     }
+  }
+}
+
+// Rows longer than kLongRow in the scaling: one warp per 2048-entry segment
+// (the long-row table of the products), so that a row of millions of entries
+// spreads over the whole GPU instead of one warp.
+//
+// Norm pass, phase 1: seg[s] = the segment's inf- or 1-norm of |M_ik| dc_k
+// (the row's own factor is applied by the row kernels).
+__global__ void __launch_bounds__(kBlock) k_scale_long_parts(CsrT<double> M, LongRows L,
+                                                             const double* __restrict__ dc,
+                                                             double* seg, int inf) {
+  const int lane = threadIdx.x & 31;
+  for (long long sg = grid_tid() >> 5; sg < L.nseg; sg += grid_threads() >> 5) {
+    double v = 0.0;
+    for (int k = __ldg(L.seg_begin + sg) + lane; k < __ldg(L.seg_end + sg); k += 32) {
+      const double a = fabs(M.val[k]) * dc[M.col[k]];
+      v = inf ? fmax(v, a) : v + a;
+    }
+    v = inf ? warp_max_d(v) : warp_sum(v);
+    if (lane == 0) seg[sg] = v;
+  }
+}
+
+// Phase 2: each long row's segments in order.
+__global__ void k_scale_long_totals(LongRows L, const double* __restrict__ seg, double* total,
+                                    int inf) {
+  for (long long r = grid_tid(); r < L.nlong; r += grid_threads()) {
+    double v = 0.0;
+    for (int s = __ldg(L.seg_ptr + r); s < __ldg(L.seg_ptr + r + 1); ++s)
+      v = inf ? fmax(v, seg[s]) : v + seg[s];
+    total[r] = v;
+  }
+}
+
+// The scaled values of the long rows: one warp per segment; a segment's row
+// is found in the row table by binary search.
+__global__ void __launch_bounds__(kBlock) k_scale_long_matrix(CsrT<double> M, LongRows L,
+                                                              const double* __restrict__ dr,
+                                                              const double* __restrict__ dc,
+                                                              double* val) {
+  const int lane = threadIdx.x & 31;
+  for (long long sg = grid_tid() >> 5; sg < L.nseg; sg += grid_threads() >> 5) {
+    int lo = 0, hi = L.nlong - 1;  // the last row r with seg_ptr[r] <= sg
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(L.seg_ptr + mid) <= sg)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const double di = dr[__ldg(M.long_rows + lo)];
+    for (int k = __ldg(L.seg_begin + sg) + lane; k < __ldg(L.seg_end + sg); k += 32)
+      val[k] = (di * val[k]) * dc[M.col[k]];
   }
 }
 

@@ -349,7 +349,8 @@ qp_status validate_options(const qp_options* o) {
       o->power_iters < 1 || o->power_iters > 100000 || !(o->eps_zero >= 0.0) ||
       !(o->theta_pw >= 0.0 && o->theta_pw <= 1.0) || !(o->time_limit_s > 0.0) ||
       (o->precision != QP_PREC_FP64 && o->precision != QP_PREC_MIXED) || o->warm_start < 0 ||
-      o->warm_start > 2 || (o->step_mode != QP_STEP_FIXED && o->step_mode != QP_STEP_ADAPTIVE)) {
+      o->warm_start > 2 || (o->step_mode != QP_STEP_FIXED && o->step_mode != QP_STEP_ADAPTIVE) ||
+      o->mixed_stall_evals < 0) {
     set_error("invalid option value");
     return QP_ERR_INVALID_ARG;
   }
@@ -772,12 +773,9 @@ qp_status upload_csr(qp_handle* h, DevMat* M, const CsrView& H) {
   return QP_OK;
 }
 
-// Once the FP64 values are final: their FP32 copy and the long-row segment
-// table (built from the host copy of the row pointers).
-qp_status finish_matrix(qp_handle* h, DevMat* M, const int32_t* host_rowptr) {
-  if (M->nnz > 0)
-    k_convert<double, float><<<h->grid_vec, kBlock, 0, h->stream>>>(M->val, M->val32,
-                                                                    int(M->nnz));
+// The long-row segment table and the medium-row lists (from the host copy of
+// the row pointers), used by the scaling and by every product.
+qp_status build_row_tables(qp_handle* h, DevMat* M, const int32_t* host_rowptr) {
   // Long rows: fixed-length segments in row order.
   std::vector<int32_t> lr, sb, se, sp(1, 0);
   for (int32_t i = 0; i < M->rows; ++i) {
@@ -830,6 +828,14 @@ qp_status finish_matrix(qp_handle* h, DevMat* M, const int32_t* host_rowptr) {
     // the host vectors die with this call: finish the copies first
     QP_TRY(sync(h));
   }
+  return QP_OK;
+}
+
+// Once the FP64 values are final: their FP32 copy.
+qp_status finish_matrix(qp_handle* h, DevMat* M) {
+  if (M->nnz > 0)
+    k_convert<double, float><<<h->grid_vec, kBlock, 0, h->stream>>>(M->val, M->val32,
+                                                                    int(M->nnz));
   return QP_OK;
 }
 
@@ -919,22 +925,44 @@ qp_status device_scaling(qp_handle* h, int ruiz_iters) {
                                                         wave)));
     };
     const CsrT<double> Q = view<double>(h->Q), A = view<double>(h->A), At = view<double>(h->At);
+    // rows longer than kLongRow: one warp per segment, into the matrix's
+    // FP64 long-row buffer, which the norm kernels read
+    auto long_parts = [&](const DevMat& M, const double* dc, int inf) {
+      if (M.nlong == 0) return;
+      const int gs = std::max(1, std::min(wave, (M.nseg + kBlock / 32 - 1) / (kBlock / 32)));
+      k_scale_long_parts<<<gs, kBlock, 0, h->stream>>>(view<double>(M), long_rows_of(M), dc,
+                                                        M.seg64, inf);
+      k_scale_long_totals<<<std::max(1, (M.nlong + kBlock - 1) / kBlock), kBlock, 0,
+                            h->stream>>>(long_rows_of(M), M.seg64, M.long64, inf);
+    };
+    auto scale_matrix = [&](const DevMat& M, const double* dr, const double* dc) {
+      k_scale_matrix<<<warp_grid(M.rows), kBlock, 0, h->stream>>>(view<double>(M), dr, dc,
+                                                                   M.val);
+      if (M.nlong == 0) return;
+      const int gs = std::max(1, std::min(wave, (M.nseg + kBlock / 32 - 1) / (kBlock / 32)));
+      k_scale_long_matrix<<<gs, kBlock, 0, h->stream>>>(view<double>(M), long_rows_of(M), dr,
+                                                         dc, M.val);
+    };
     for (int it = 0; it <= ruiz_iters; ++it) {
       const int inf = it < ruiz_iters ? 1 : 0;
+      long_parts(h->Q, d2, inf);
+      long_parts(h->At, d1, inf);
       k_scale_norms_n<<<warp_grid(n), kBlock, 0, h->stream>>>(Q, At, d1, d2, rn, inf);
-      if (m > 0) k_scale_norms_m<<<warp_grid(m), kBlock, 0, h->stream>>>(A, d1, d2, rm, inf);
+      if (m > 0) {
+        long_parts(h->A, d2, inf);
+        k_scale_norms_m<<<warp_grid(m), kBlock, 0, h->stream>>>(A, d1, d2, rm, inf);
+      }
       k_scale_apply<<<h->grid_vec, kBlock, 0, h->stream>>>(d2, rn, n, d1, rm, m);
     }
-    k_scale_matrix<<<warp_grid(n), kBlock, 0, h->stream>>>(Q, d2, d2, h->Q.val);
+    scale_matrix(h->Q, d2, d2);
     if (m > 0) {
-      k_scale_matrix<<<warp_grid(m), kBlock, 0, h->stream>>>(A, d1, d2, h->A.val);
-      k_scale_matrix<<<warp_grid(n), kBlock, 0, h->stream>>>(At, d2, d1, h->At.val);
+      scale_matrix(h->A, d1, d2);
+      scale_matrix(h->At, d2, d1);
       k_scale_vector<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.b, d1, h->v64.inv_d1, m);
     }
     k_scale_vector<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.c, d2, h->v64.inv_d2, n);
     if (h->penalty) {  // the problem's own Q and c, for relKKT, under the same scaling
-      k_scale_matrix<<<warp_grid(n), kBlock, 0, h->stream>>>(view<double>(h->Qe), d2, d2,
-                                                              h->Qe.val);
+      scale_matrix(h->Qe, d2, d2);
       k_scale_vector<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.ce, d2, h->v64.inv_d2, n);
     }
     convert(h, h->v64.inv_d1, h->v32.inv_d1, m);
@@ -1093,6 +1121,10 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   if (h->penalty) QP_TRY(upload_csr(h, &h->Qe, Qown));
   std::vector<int32_t> t_rowptr;
   QP_TRY(device_transpose(h, n, &t_rowptr));
+  QP_TRY(build_row_tables(h, &h->Q, Qh.rowptr));
+  QP_TRY(build_row_tables(h, &h->A, Ah.rowptr));
+  QP_TRY(build_row_tables(h, &h->At, t_rowptr.data()));
+  if (h->penalty) QP_TRY(build_row_tables(h, &h->Qe, Qown.rowptr));
   QP_TRY(alloc_vecs<double>(h));
   QP_TRY(alloc_vecs<float>(h));
   const size_t N = size_t(n), M = size_t(m);
@@ -1111,11 +1143,11 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
     h->d1.assign(M, 1.0);
     h->d2.assign(N, 1.0);
   }
-  QP_TRY(finish_matrix(h, &h->Q, Qh.rowptr));
-  QP_TRY(finish_matrix(h, &h->A, Ah.rowptr));
-  QP_TRY(finish_matrix(h, &h->At, t_rowptr.data()));
+  QP_TRY(finish_matrix(h, &h->Q));
+  QP_TRY(finish_matrix(h, &h->A));
+  QP_TRY(finish_matrix(h, &h->At));
   if (h->penalty) {
-    QP_TRY(finish_matrix(h, &h->Qe, Qown.rowptr));
+    QP_TRY(finish_matrix(h, &h->Qe));
     convert(h, h->v64.ce, h->v32.ce, n);
   }
   convert(h, h->v64.c, h->v32.c, n);
@@ -1199,9 +1231,14 @@ qp_status start_solve(qp_handle* h, const qp_options* o) {
   return check_launch();
 }
 
+// Internal termination of the FP32 phase: relKKT stopped improving (the
+// mixed_stall_evals rule), so FP64 refinement takes over.
+constexpr int kTermMixedStall = -2;
+
 // Chunks of eval_freq iterations (each with one relKKT evaluation) until the
-// state says done, a device wait gave up, or the time limit passes.  Sets the
-// termination code in *term (-1 while not terminated).
+// state says done, a device wait gave up, the time limit passes or (FP32
+// phase with refinement) relKKT stalls.  Sets the termination code in *term
+// (-1 while not terminated).
 template <class T>
 qp_status run_chunks(qp_handle* h, const qp_options* o, bool timing,
                      std::chrono::steady_clock::time_point t0, qp_info* info, int* term) {
@@ -1211,6 +1248,10 @@ qp_status run_chunks(qp_handle* h, const qp_options* o, bool timing,
   else QP_TRY(ensure_chunk<T>(h, o->eval_freq));
   const int pi = std::is_same<T, double>::value ? 0 : 1;
   cudaError_t timing_error = cudaSuccess;
+  const bool stall_rule =
+      std::is_same<T, float>::value && o->refine && o->mixed_stall_evals > 0;
+  double best = INFINITY;
+  int since_gain = 0, evals = 0;
   while (true) {
     if (timing) {
       QP_TRY(enqueue_chunk<T>(h, o->eval_freq, h->coop_ok, h->ev.data()));
@@ -1246,6 +1287,19 @@ qp_status run_chunks(qp_handle* h, const qp_options* o, bool timing,
     if (s.done) {
       *term = s.done - 1;
       break;
+    }
+    if (stall_rule) {
+      // the window grows with the solve (a quarter of its evaluations), so a
+      // slow phase of a long solve is not taken for the FP32 floor
+      const double cand = std::min(s.kkt_cur[3], s.kkt_avg[3]);
+      ++evals;
+      if (cand < 0.9 * best) {
+        best = cand;
+        since_gain = 0;
+      } else if (++since_gain >= std::max(o->mixed_stall_evals, evals / 4)) {
+        *term = kTermMixedStall;
+        break;
+      }
     }
     const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (el > o->time_limit_s) {
@@ -1291,7 +1345,9 @@ qp_status promote_and_refine(qp_handle* h, const qp_options* o, bool timing,
   for (int k = 0; k < 6; ++k) d.kkt_ret[k] = d.kkt_cur[k];
   d.returned_avg = 0;
   h->active_prec = kPrecFp64;
-  if (*term == QP_TERM_SOLVED && !(d.kkt_cur[3] <= o->tol) && o->refine) {
+  if (*term == kTermMixedStall && d.kkt_cur[3] <= o->tol) *term = QP_TERM_SOLVED;
+  if ((*term == QP_TERM_SOLVED || *term == kTermMixedStall) && !(d.kkt_cur[3] <= o->tol) &&
+      o->refine) {
     // FP64 refinement: a new epoch at the promoted iterate.
     d.j = 0;
     d.weight_sum = 0.0;
@@ -1400,6 +1456,7 @@ void qp_options_default(qp_options* o) {
   o->precision = QP_PREC_FP64;
   o->refine = 1;
   o->step_mode = QP_STEP_FIXED;
+  o->mixed_stall_evals = 32;
 }
 
 qp_status qp_create(qp_handle** out, int32_t n, int32_t m, int32_t m_eq, const int32_t* Q_rowptr,

@@ -78,6 +78,8 @@ def test_option_defaults_follow_the_paper(lib):
     assert o.cg_eps_factor == 0.05
     assert o.power_iters == 30 and o.eval_freq == 64 and o.tol == 1e-4
     assert o.cg_mode == L.CG_ADAPTIVE and o.restart_mode == L.RESTART_ADAPTIVE
+    # the mixed path's FP64 handover: 32 evaluations without a 10% relKKT gain
+    assert o.refine == 1 and o.mixed_stall_evals == 32
 
 
 def test_csr_validate_rejects_bad_inputs(lib):

@@ -868,6 +868,48 @@ def test_bounds_box_closed_form():
             assert np.max(np.abs(x - np.clip(-c / q, lo, hi))) <= err
 
 
+@pytest.mark.parametrize("bounded", [True, False])
+def test_mixed_stall_hands_over_to_fp64(built, bounded):
+    """Below the FP32 rounding floor the mixed phase stops improving; after
+    mixed_stall_evals evaluations without a 10% gain FP64 refinement takes
+    over and reaches a tolerance the FP32 iterate cannot (the box closed form
+    with bounds; dense_small without).  With the rule off the FP32 phase runs
+    into the iteration limit."""
+    if bounded:
+        rng = np.random.default_rng(12)
+        n = 300
+        q = rng.uniform(0.5, 2.0, n)
+        c = rng.standard_normal(n) * 2
+        lo, hi = -rng.uniform(0.1, 1, n), rng.uniform(0.1, 1, n)
+        inst = W.from_dense(np.diag(q), np.zeros((0, n)), c, np.zeros(0), name="box bounds")
+        s = QPSolver(inst)
+        s.set_bounds(lo, hi)
+        x_star = np.clip(-c / q, lo, hi)
+        P = None
+    else:
+        inst, P, s = built("dense_small")
+        x_star = None
+    tol = 1e-10
+    try:
+        info = s.solve(tol=tol, precision=L.PREC_MIXED, step_mode=L.STEP_ADAPTIVE,
+                       max_iter=200_000)
+        x, y = s.solution()
+        assert info["termination"] == L.TERM_SOLVED
+        assert info["mixed_relkkt"] > tol          # the FP32 phase stalled above tol
+        assert info["refine_iterations"] > 0       # and FP64 finished the solve
+        assert info["relkkt"] <= tol
+        if x_star is not None:
+            assert np.max(np.abs(x - x_star)) <= 1e-9
+        else:
+            assert O.relkkt(P, x, y).relkkt <= tol
+        off = s.solve(tol=tol, precision=L.PREC_MIXED, step_mode=L.STEP_ADAPTIVE,
+                      max_iter=info["mixed_iterations"] + 1024, mixed_stall_evals=0)
+        assert off["termination"] == L.TERM_ITER_LIMIT and off["refine_iterations"] == 0
+    finally:
+        if bounded:
+            s.close()
+
+
 def test_clearing_bounds_returns_to_the_cg_path(built):
     inst, P, s = built("dense_small")
     s.solve(tol=1e-6)
