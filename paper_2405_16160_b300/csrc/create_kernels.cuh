@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kBlock) k_scale_matrix(CsrT<double> M,
   }
 }
 
-// Rows longer than kLongRow in the scaling: one warp per 2048-entry segment
+// Rows longer than kLongRow in the scaling: one warp per kSegLen-entry segment
 // (the long-row table of the products), so that a row of millions of entries
 // spreads over the whole GPU instead of one warp.
 //

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstring>
 #include <numeric>
 #include <thread>
 
@@ -40,8 +41,8 @@ std::vector<int32_t> split_rows(const int32_t* rowptr, int32_t rows, int T) {
 
 }  // namespace
 
-bool csr_validate(int32_t rows, int32_t cols, const int32_t* rowptr, const int32_t* col,
-                  const double* val, std::string* why) {
+bool csr_check(int32_t rows, int32_t cols, const int32_t* rowptr, const int32_t* col,
+               const double* val, std::string* why, bool* canonical) {
   auto fail = [&](const std::string& s) {
     if (why) *why = s;
     return false;
@@ -49,23 +50,56 @@ bool csr_validate(int32_t rows, int32_t cols, const int32_t* rowptr, const int32
   if (rows < 0 || cols < 0) return fail("negative dimension");
   if (!rowptr) return fail("rowptr is NULL");
   if (rowptr[0] != 0) return fail("rowptr[0] != 0");
-  for (int32_t i = 0; i < rows; ++i)
-    if (rowptr[i + 1] < rowptr[i]) return fail("rowptr is not monotone at row " + std::to_string(i));
-  const int64_t nnz = rowptr[rows];
-  if (nnz < 0 || nnz >= (int64_t(1) << 31)) return fail("nnz out of int32 range");
-  if (nnz > 0 && (!col || !val)) return fail("col or val is NULL");
-  // Entries are checked in parallel chunks; the first bad entry is reported.
-  const int T = worker_count(nnz);
-  std::atomic<int64_t> first_bad(nnz);
-  parallel_for(T, [&](int t) {
-    const int64_t lo = nnz * t / T, hi = nnz * (t + 1) / T;
-    for (int64_t k = lo; k < hi; ++k)
-      if (col[k] < 0 || col[k] >= cols || !std::isfinite(val[k])) {
-        int64_t cur = first_bad.load();
-        while (k < cur && !first_bad.compare_exchange_weak(cur, k)) {
+  // rowptr monotone, in parallel chunks of rows; the first bad row is reported
+  const int Tr = worker_count(rows);
+  std::atomic<int64_t> bad_row(rows);
+  parallel_for(Tr, [&](int t) {
+    const int64_t lo = int64_t(rows) * t / Tr, hi = int64_t(rows) * (t + 1) / Tr;
+    for (int64_t i = lo; i < hi; ++i)
+      if (rowptr[i + 1] < rowptr[i]) {
+        int64_t cur = bad_row.load();
+        while (i < cur && !bad_row.compare_exchange_weak(cur, i)) {
         }
         break;
       }
+  });
+  if (bad_row.load() < rows)
+    return fail("rowptr is not monotone at row " + std::to_string(bad_row.load()));
+  const int64_t nnz = rowptr[rows];
+  if (nnz < 0 || nnz >= (int64_t(1) << 31)) return fail("nnz out of int32 range");
+  if (nnz > 0 && (!col || !val)) return fail("col or val is NULL");
+  // Entries, in parallel row ranges of about equal entry counts, in one
+  // branch-free pass: columns in range and finite values (on a failure the
+  // range is scanned again for its first bad entry, and the lowest over the
+  // ranges is reported) and strictly increasing columns in every row.
+  const int T = worker_count(nnz);
+  const std::vector<int32_t> b = split_rows(rowptr, rows, T);
+  std::atomic<int64_t> first_bad(nnz);
+  std::atomic<bool> sorted(true);
+  const uint64_t exp_mask = 0x7ff0000000000000ull;
+  parallel_for(T, [&](int t) {
+    bool bad = false, unsorted = false;
+    for (int32_t i = b[size_t(t)]; i < b[size_t(t) + 1]; ++i) {
+      int32_t prev = -1;
+      for (int64_t k = rowptr[i], e = rowptr[i + 1]; k < e; ++k) {
+        const int32_t j = col[k];
+        uint64_t bits;
+        std::memcpy(&bits, val + k, sizeof bits);
+        bad |= (uint32_t(j) >= uint32_t(cols)) | ((bits & exp_mask) == exp_mask);
+        unsorted |= j <= prev;
+        prev = j;
+      }
+    }
+    if (bad) {
+      for (int64_t k = rowptr[b[size_t(t)]]; k < rowptr[b[size_t(t) + 1]]; ++k)
+        if (col[k] < 0 || col[k] >= cols || !std::isfinite(val[k])) {
+          int64_t cur = first_bad.load();
+          while (k < cur && !first_bad.compare_exchange_weak(cur, k)) {
+          }
+          break;
+        }
+    }
+    if (unsorted) sorted = false;
   });
   const int64_t k = first_bad.load();
   if (k < nnz) {
@@ -73,7 +107,13 @@ bool csr_validate(int32_t rows, int32_t cols, const int32_t* rowptr, const int32
       return fail("column index out of range at entry " + std::to_string(k));
     return fail("non-finite value at entry " + std::to_string(k));
   }
+  if (canonical) *canonical = sorted.load();
   return true;
+}
+
+bool csr_validate(int32_t rows, int32_t cols, const int32_t* rowptr, const int32_t* col,
+                  const double* val, std::string* why) {
+  return csr_check(rows, cols, rowptr, col, val, why, nullptr);
 }
 
 bool csr_is_canonical(int32_t rows, const int32_t* rowptr, const int32_t* col) {

@@ -35,6 +35,12 @@ inline CsrView view_of(const HostCsr& H) {
 bool csr_validate(int32_t rows, int32_t cols, const int32_t* rowptr, const int32_t* col,
                   const double* val, std::string* why);
 
+// csr_validate and, on the same multi-threaded pass over the entries,
+// *canonical = every row's columns strictly increasing (when canonical is
+// not NULL and the matrix is valid).
+bool csr_check(int32_t rows, int32_t cols, const int32_t* rowptr, const int32_t* col,
+               const double* val, std::string* why, bool* canonical);
+
 // True when every row's columns are strictly increasing (sorted, no duplicates).
 bool csr_is_canonical(int32_t rows, const int32_t* rowptr, const int32_t* col);
 

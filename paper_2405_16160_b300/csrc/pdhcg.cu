@@ -776,11 +776,24 @@ qp_status upload_csr(qp_handle* h, DevMat* M, const CsrView& H) {
 // The long-row segment table and the medium-row lists (from the host copy of
 // the row pointers), used by the scaling and by every product.
 qp_status build_row_tables(qp_handle* h, DevMat* M, const int32_t* host_rowptr) {
-  // Long rows: fixed-length segments in row order.
-  std::vector<int32_t> lr, sb, se, sp(1, 0);
+  // One pass over the rows.  Long rows: fixed-length segments in row order.
+  // Medium rows of each precision's row kernels: more than 16 entries per
+  // lane of a row group (none with a whole warp per row).  The FP64 kernels
+  // give short rows one lane each to keep the DFMA slots full, so a warp per
+  // row pays off there only from 64 entries.
+  std::vector<int32_t> lr, sb, se, sp(1, 0), md[2];
+  int32_t med_min[2];
+  for (int fp32 = 0; fp32 < 2; ++fp32) {
+    const int G = fp32 ? M->G32 : M->G64;
+    med_min[fp32] = G >= 32 ? kLongRow : (fp32 ? 16 * G : std::max(16 * G, 64));
+  }
   for (int32_t i = 0; i < M->rows; ++i) {
     const int32_t b = host_rowptr[i], e = host_rowptr[i + 1];
-    if (e - b <= kLongRow) continue;
+    if (e - b <= kLongRow) {
+      if (e - b > med_min[0]) md[0].push_back(i);
+      if (e - b > med_min[1]) md[1].push_back(i);
+      continue;
+    }
     lr.push_back(i);
     for (int32_t k = b; k < e; k += kSegLen) {
       sb.push_back(k);
@@ -788,26 +801,14 @@ qp_status build_row_tables(qp_handle* h, DevMat* M, const int32_t* host_rowptr) 
     }
     sp.push_back(int32_t(sb.size()));
   }
-  // Medium rows of each precision's row kernels: more than 16 entries per
-  // lane of a row group (none with a whole warp per row).  The FP64 kernels
-  // give short rows one lane each to keep the DFMA slots full, so a warp per
-  // row pays off there only from 64 entries.
   for (int fp32 = 0; fp32 < 2; ++fp32) {
-    const int G = fp32 ? M->G32 : M->G64;
-    if (G >= 32) continue;
-    const int32_t med_min = fp32 ? 16 * G : std::max(16 * G, 64);
-    std::vector<int32_t> md;
-    for (int32_t i = 0; i < M->rows; ++i) {
-      const int32_t len = host_rowptr[i + 1] - host_rowptr[i];
-      if (len > med_min && len <= kLongRow) md.push_back(i);
-    }
-    (fp32 ? M->med_min32 : M->med_min64) = med_min;
-    (fp32 ? M->nmed32 : M->nmed64) = int32_t(md.size());
-    if (!md.empty()) {
+    const std::vector<int32_t>& v = md[fp32];
+    (fp32 ? M->med_min32 : M->med_min64) = med_min[fp32];
+    (fp32 ? M->nmed32 : M->nmed64) = int32_t(v.size());
+    if (!v.empty()) {
       int32_t** dst = fp32 ? &M->med32 : &M->med64;
-      QP_TRY(dalloc(h, dst, md.size()));
-      QP_TRY(upload(h, *dst, md.data(), md.size() * sizeof(int32_t)));
-      QP_TRY(sync(h));  // md dies with this scope
+      QP_TRY(dalloc(h, dst, v.size()));
+      QP_TRY(upload(h, *dst, v.data(), v.size() * sizeof(int32_t)));
     }
   }
   M->nlong = int32_t(lr.size());
@@ -825,9 +826,9 @@ qp_status build_row_tables(qp_handle* h, DevMat* M, const int32_t* host_rowptr) 
     QP_TRY(upload(h, M->seg_begin, sb.data(), sb.size() * sizeof(int32_t)));
     QP_TRY(upload(h, M->seg_end, se.data(), se.size() * sizeof(int32_t)));
     QP_TRY(upload(h, M->seg_ptr, sp.data(), sp.size() * sizeof(int32_t)));
-    // the host vectors die with this call: finish the copies first
-    QP_TRY(sync(h));
   }
+  // the host vectors die with this call: finish the copies first
+  if (M->nlong > 0 || !md[0].empty() || !md[1].empty()) QP_TRY(sync(h));
   return QP_OK;
 }
 
@@ -1035,7 +1036,7 @@ void fill_info_from_state(qp_handle* h, qp_info* info) {
 qp_status validate_problem(int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr,
                            const int32_t* Qc, const double* Qv, const int32_t* Ar,
                            const int32_t* Ac, const double* Av, const double* c,
-                           const double* b) {
+                           const double* b, bool* q_canonical, bool* a_canonical) {
   std::string why;
   if (n <= 0 || m < 0 || m_eq < 0 || m_eq > m) {
     set_error("bad sizes n=%d m=%d m_eq=%d", n, m, m_eq);
@@ -1045,11 +1046,11 @@ qp_status validate_problem(int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr
     set_error("c or b is NULL");
     return QP_ERR_INVALID_ARG;
   }
-  if (!csr_validate(n, n, Qr, Qc, Qv, &why)) {
+  if (!csr_check(n, n, Qr, Qc, Qv, &why, q_canonical)) {
     set_error("Q: %s", why.c_str());
     return QP_ERR_INVALID_ARG;
   }
-  if (!csr_validate(m, n, Ar, Ac, Av, &why)) {
+  if (!csr_check(m, n, Ar, Ac, Av, &why, a_canonical)) {
     set_error("A: %s", why.c_str());
     return QP_ERR_INVALID_ARG;
   }
@@ -1068,12 +1069,13 @@ qp_status validate_problem(int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr
 
 qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr,
                       const int32_t* Qc, const double* Qv, const int32_t* Ar, const int32_t* Ac,
-                      const double* Av, const double* c, const double* b, uint32_t flags) {
+                      const double* Av, const double* c, const double* b, uint32_t flags,
+                      bool q_canonical, bool a_canonical) {
   // Rows that are already sorted without duplicates are used in place;
   // otherwise a canonical copy (sorted, duplicates summed) is made.
   HostCsr Qc_, Ac_;
   CsrView Qh{n, n, Qr, Qc, Qv}, Ah{m, n, Ar, Ac, Av};
-  if (!csr_is_canonical(n, Qr, Qc)) {
+  if (!q_canonical) {
     Qc_ = csr_canonical(n, n, Qr, Qc, Qv);
     Qh = view_of(Qc_);
   }
@@ -1084,7 +1086,7 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
       return QP_ERR_INVALID_ARG;
     }
   }
-  if (!csr_is_canonical(m, Ar, Ac)) {
+  if (!a_canonical) {
     Ac_ = csr_canonical(m, n, Ar, Ac, Av);
     Ah = view_of(Ac_);
   }
@@ -1468,7 +1470,9 @@ qp_status qp_create(qp_handle** out, int32_t n, int32_t m, int32_t m_eq, const i
     return QP_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  QP_TRY(validate_problem(n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b));
+  bool q_canonical = false, a_canonical = false;
+  QP_TRY(validate_problem(n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b,
+                          &q_canonical, &a_canonical));
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -1492,7 +1496,8 @@ qp_status qp_create(qp_handle** out, int32_t n, int32_t m, int32_t m_eq, const i
   }
   if (s == QP_OK) s = begin_call(h);
   if (s == QP_OK)
-    s = create_impl(h, n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b, flags);
+    s = create_impl(h, n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b, flags,
+                    q_canonical, a_canonical);
   if (s == QP_OK) s = end_call(h);
   if (s != QP_OK) {
     std::string keep = g_last_error;

@@ -933,3 +933,39 @@ def test_set_bounds_rejects_invalid_bounds(built):
     with pytest.raises(L.QPError):
         s.set_bounds(np.full(n, np.nan), None)
     s.set_bounds(None, None)
+
+
+def test_unsorted_and_duplicate_entries_are_canonicalised():
+    """qp_create accepts rows in any column order with duplicate entries
+    (summed): a shuffled copy of the instance whose every tenth entry is
+    split in two solves to the canonical instance's iterates."""
+    inst = W.sparse_dd(3, n=5_000, m=2_500)
+    rng = np.random.default_rng(4)
+
+    def scramble(rowptr, col, val):
+        rp, cs, vs = [0], [], []
+        for i in range(len(rowptr) - 1):
+            c = col[rowptr[i]:rowptr[i + 1]].copy()
+            v = val[rowptr[i]:rowptr[i + 1]].copy()
+            split = rng.random(len(c)) < 0.1
+            c = np.concatenate([c, c[split]])
+            v = np.concatenate([np.where(split, v * 0.5, v)[:len(split)], v[split] * 0.5])
+            perm = rng.permutation(len(c))
+            cs.append(c[perm])
+            vs.append(v[perm])
+            rp.append(rp[-1] + len(c))
+        return (np.asarray(rp, np.int32), np.concatenate(cs).astype(np.int32),
+                np.concatenate(vs))
+
+    Qr, Qc, Qv = scramble(inst.Q_rowptr, inst.Q_col, inst.Q_val)
+    Ar, Ac, Av = scramble(inst.A_rowptr, inst.A_col, inst.A_val)
+    messy = W.QPInstance(inst.n, inst.m, inst.m_eq, Qr, Qc, Qv, Ar, Ac, Av, inst.c, inst.b)
+    assert len(Qc) > len(inst.Q_col) and len(Ac) > len(inst.A_col)
+    with QPSolver(inst) as a, QPSolver(messy) as b:
+        ia = a.solve(tol=1e-6)
+        ib = b.solve(tol=1e-6)
+        xa, _ = a.solution()
+        xb, _ = b.solution()
+    assert ia["termination"] == ib["termination"] == L.TERM_SOLVED
+    assert ia["iterations"] == ib["iterations"]
+    assert _relerr(xb, xa) <= 1e-10
