@@ -468,6 +468,8 @@ def run_batch_bench(args):
     other = L.STEP_FIXED if step == L.STEP_ADAPTIVE else L.STEP_ADAPTIVE
     stream = torch.cuda.current_stream()
     bt = QPBatch(insts)
+    # block sizes per size bin from the autotuner (whole bins, 128 attempts)
+    threads = bt.tune(tol=tol, precision=L.PREC_MIXED, step_mode=step, sample_iters=128)
     for _ in range(args.warmup):
         bt.solve(tol=tol, precision=L.PREC_MIXED, step_mode=step)
     with ClockSampler(local) as clocks:
@@ -493,6 +495,7 @@ def run_batch_bench(args):
     # the same instances with long-only written as the bounds x >= 0 (BB x-steps)
     bnds = W.portfolio_batch(BATCH_WORKLOAD["seed"] + rank, BATCH_WORKLOAD["count"], bounds=True)
     with QPBatch(bnds) as bb:
+        bb.tune(tol=tol, precision=L.PREC_MIXED, step_mode=step, sample_iters=128)
         bb.solve(tol=tol, precision=L.PREC_MIXED, step_mode=step)
         bounds_ms = statistics.mean(
             bb.solve(tol=tol, precision=L.PREC_MIXED, step_mode=step) for _ in range(2))
@@ -565,6 +568,7 @@ def run_batch_bench(args):
                                              "scaled to 4096",
                        speedup_vs_single_fp64=single_total / value,
                        speedup_vs_fp64_batch=(fp64_ms / 1e3) / value,
+                       tuned_threads_largest_bin=threads,
                        bounds_form_s=bounds_ms / 1e3,
                        bounds_form_solved=int(sum(r["termination"] == 0 for r in res_b)),
                        bounds_form_attempts_mean=float(np.mean([r["attempts"] for r in res_b])),

@@ -485,11 +485,15 @@ qp_status qp_batch_set_bounds(qp_batch* bt, const double* lo, const double* hi);
  * reduction trees differ); a fixed configuration is bit-reproducible. */
 qp_status qp_batch_set_threads(qp_batch* bt, int32_t threads);
 
-/* Autotuner: for each bin, times a bounded solve (o with max_iter capped at
- * sample_iters) of the bin's first sample_count instances for each block
- * size and keeps the fastest; *threads_out (may be NULL) receives the
- * choice for the bin of the largest instances.  The sample must fill the GPU
- * (a few blocks per SM) for the timing to reflect throughput. */
+/* Autotuner: the bins run concurrently and share the SMs, so every
+ * candidate is timed on the whole batch: a bounded solve (o with max_iter
+ * capped at sample_iters) of each bin's first sample_count instances.  Bin
+ * by bin (largest instances first), each block size is tried with the other
+ * bins at their current choice and the fastest is kept.  *threads_out (may
+ * be NULL) receives the choice for the bin of the largest instances.  The
+ * sample must fill the GPU (a few blocks per SM, and several waves) for the
+ * timing to reflect throughput; sample_count >= the bin sizes takes every
+ * instance. */
 qp_status qp_batch_tune(qp_batch* bt, const qp_options* o, int32_t sample_count,
                         int32_t sample_iters, int32_t* threads_out);
 

@@ -309,19 +309,17 @@ BatchData<V> batch_data(qp_batch* h, const BatchBin& bin, const V* F, const V* q
   return B;
 }
 
-// One launch per bin, each on the bin's stream, forked from and joined back
-// into the handle's stream.  only_bin >= 0 runs that bin alone, over its
-// first `limit` instances with `threads` (tuning); otherwise every bin, all
-// instances, its own block size.
-qp_status run_batch(qp_batch* h, const qp_options* o, int only_bin, int threads, int limit,
-                    double* ms) {
+// One launch per bin, each with the bin's block size on the bin's stream,
+// forked from and joined back into the handle's stream, over the first
+// `limit` instances of each bin (limit <= 0: all, as in a solve; the tuner
+// samples); the whole is timed with events.
+qp_status run_batch(qp_batch* h, const qp_options* o, int limit, double* ms) {
   BCUDA(cudaEventRecord(h->t0, h->stream));
   BCUDA(cudaEventRecord(h->fork, h->stream));
   for (int bi = 0; bi < int(h->bins.size()); ++bi) {
-    if (only_bin >= 0 && bi != only_bin) continue;
     BatchBin& bin = h->bins[size_t(bi)];
-    const int count = only_bin >= 0 ? std::min(limit, bin.count) : bin.count;
-    const int nt = only_bin >= 0 ? threads : bin.threads;
+    const int count = limit > 0 ? std::min(limit, bin.count) : bin.count;
+    const int nt = bin.threads;
     BCUDA(cudaStreamWaitEvent(bin.stream, h->fork, 0));
     BCUDA(cudaMemsetAsync(bin.next, 0, sizeof(int), bin.stream));
     if (o->precision == QP_PREC_MIXED)
@@ -597,7 +595,7 @@ qp_status qp_batch_solve(qp_batch* h, const qp_options* o, double* device_ms) {
   BTRY(begin(h));
   h->solved = false;
   double ms = 0.0;
-  BTRY(run_batch(h, o, -1, 0, 0, &ms));
+  BTRY(run_batch(h, o, 0, &ms));
   h->h_res.resize(size_t(h->count));
   BCUDA(cudaMemcpyAsync(h->h_res.data(), h->res, size_t(h->count) * sizeof(BatchResult),
                         cudaMemcpyDeviceToHost, h->stream));
@@ -728,13 +726,17 @@ qp_status qp_batch_tune(qp_batch* h, const qp_options* o, int32_t sample_count,
   qp_options t = *o;
   t.max_iter = std::min<int64_t>(o->max_iter, sample_iters);
   BTRY(begin(h));
+  // The bins run concurrently and share the SMs, so each candidate is timed
+  // on the whole batch: one bin at a time tries every block size with the
+  // others at their current choice (coordinate search, largest bin first).
   for (int bi = 0; bi < int(h->bins.size()); ++bi) {
     BatchBin& bin = h->bins[size_t(bi)];
     double best = INFINITY;
     int best_t = bin.threads;
     for (int threads : kThreadChoices) {
+      bin.threads = threads;
       double ms = 0.0;
-      qp_status s = run_batch(h, &t, bi, threads, sample_count, &ms);
+      qp_status s = run_batch(h, &t, sample_count, &ms);
       if (s == QP_ERR_INVALID_ARG) continue;  // this block size cannot be resident
       BTRY(s);
       if (ms < best) {

@@ -180,9 +180,12 @@ __device__ void cta_dual(const LocalCsr<V>& A, const V* xv, const double* b, int
 }
 
 // out = (F F' + diag(qd)) p with F column-major: t = F'p by a warp per
-// column, then a thread per row.  p and t are in the value type.  Two
-// barriers; out is ready on return.
-template <class V, int NT>
+// column, then a thread per row (row j by thread j mod NT).  p and t are in
+// the value type.  Two barriers, out ready for every thread on return; with
+// kSyncOut = false one barrier, and out[j] is ready for thread j mod NT only
+// (the CG and BB steps read it that way, and a block reduction separates it
+// from the next product's writes of t).
+template <class V, int NT, bool kSyncOut = true>
 __device__ void cta_qprod(const V* F, const V* qd, int n, int k, const V* p, V* t,
                           double* out) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -199,7 +202,7 @@ __device__ void cta_qprod(const V* F, const V* qd, int n, int k, const V* p, V* 
     for (int l = 0; l < k; ++l) s = fma(F[size_t(l) * n + j], t[l], s);
     out[j] = double(s);
   }
-  __syncthreads();
+  if constexpr (kSyncOut) __syncthreads();
 }
 
 // Block-wide sums (S values) and maxima (M values) in one pass; every thread
@@ -483,7 +486,7 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         // ---- BB projected gradient (Section 4) from x, with r = p = -g:
         // alpha0 = g'Mg / g'g, then x+ = min(max(x + r/alpha, lo), hi), s = x+ - x,
         // r -= M s, Q x += Q s, alpha = s'Ms / s's (M = Q + I/tau)
-        cta_qprod<V, NT>(F, qd, n, k, pv, tv, q);
+        cta_qprod<V, NT, false>(F, qd, n, k, pv, tv, q);
         double gmg = 0.0;
         for (int j = tid; j < n; j += NT) gmg = fma(p[j], q[j] + p[j] * inv_tau, gmg);
         gmg = cta_sum1<NT>(gmg, red);
@@ -505,7 +508,7 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
             ss = fma(sj, sj, ss);
           }
           ss = cta_sum1<NT>(ss, red);
-          cta_qprod<V, NT>(F, qd, n, k, pv, tv, q);  // q = Q s
+          cta_qprod<V, NT, false>(F, qd, n, k, pv, tv, q);  // q = Q s
           double sw = 0.0;
           for (int j = tid; j < n; j += NT) {
             const double sj = p[j], qj = q[j];
@@ -527,7 +530,7 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         }
       }
       while (!skip && !lo) {
-        cta_qprod<V, NT>(F, qd, n, k, pv, tv, q);  // q = Q p
+        cta_qprod<V, NT, false>(F, qd, n, k, pv, tv, q);  // q = Q p
         double pq = 0.0;
         for (int j = tid; j < n; j += NT) pq = fma(p[j], q[j] + p[j] * inv_tau, pq);
         pq = cta_sum1<NT>(pq, red);
