@@ -433,7 +433,7 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
   });
   int smem_optin = 0;
   BCUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-  const size_t static_smem = sizeof(DevState) + 512 / 32 * 11 * sizeof(double) + 64;
+  const size_t static_smem = sizeof(DevState) + 512 / 32 * 13 * sizeof(double) + 64;
   const int nbins = std::min(kMaxBins, int(count));
   h->bins.resize(size_t(nbins));
   for (int bi = 0; bi < nbins; ++bi) {

@@ -97,7 +97,7 @@ struct BatchData {
 inline size_t batch_block_doubles(int max_n, int max_m, int max_k, bool shadow,
                                   bool adaptive) {
   const size_t a = adaptive ? 2 * size_t(max_n) + 2 * size_t(max_m) : 0;
-  const size_t d = 9 * size_t(max_n) + 6 * size_t(max_m) + size_t(max_k) + 8 + a;
+  const size_t d = 9 * size_t(max_n) + 6 * size_t(max_m) + size_t(max_k) + 16 + a;
   const size_t f = shadow ? 2 * size_t(max_n) + 2 * size_t(max_m) + size_t(max_k) + 8 : 0;
   return d + (f + 1) / 2;
 }
@@ -205,6 +205,49 @@ __device__ void cta_qprod(const V* F, const V* qd, int n, int k, const V* p, V* 
   if constexpr (kSyncOut) __syncthreads();
 }
 
+// q = (F F' + diag(qd)) p as cta_qprod<V, NT, false> (q[j] ready for thread
+// j mod NT), returning p'(Q + I/tau)p to every thread without a block
+// reduction of its own: p'Q p = ||F'p||^2 + sum qd_j p_j^2, so the warps that
+// form t = F'p also form one more "column", d = sum (qd_j + 1/tau) p_j^2
+// (over the FP64 p), and after the product's one barrier every warp forms
+// ||t||^2 + d with the same lanes and the same shuffle tree.  Used by the BB
+// step, which needs two such products per step; the CG step keeps its block
+// reduction of p'q (measured faster there: the FP64 column lengthens the
+// product's critical path more than the barrier it saves).
+template <class V, int NT>
+__device__ double cta_qprod_pmp(const V* F, const V* qd, int n, int k, const V* p,
+                                const double* p64, double inv_tau, V* t, double* td,
+                                double* out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int l = w; l <= k; l += NT / 32) {
+    if (l < k) {
+      const V* Fl = F + size_t(l) * n;
+      V s = V(0);
+      for (int j = lane; j < n; j += 32) s = fma(Fl[j], p[j], s);
+      s = warp_sum_v(s);
+      if (lane == 0) {
+        t[l] = s;
+        td[l] = double(s);
+      }
+    } else {
+      double s = 0.0;
+      for (int j = lane; j < n; j += 32) s = fma((double(qd[j]) + inv_tau) * p64[j], p64[j], s);
+      s = warp_sum(s);
+      if (lane == 0) td[k] = s;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += NT) {
+    V s = qd[j] * p[j];
+    for (int l = 0; l < k; ++l) s = fma(F[size_t(l) * n + j], t[l], s);
+    out[j] = double(s);
+  }
+  // ||t||^2 by every warp alike: lane partials, then the xor tree
+  double tt = 0.0;
+  for (int l = lane; l < k; l += 32) tt = fma(td[l], td[l], tt);
+  return td[k] + warp_sum(tt);
+}
+
 // Block-wide sums (S values) and maxima (M values) in one pass; every thread
 // gets the results.  Warp partials are combined in warp order.
 template <int NT, int S, int M>
@@ -292,7 +335,7 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
   V* uv = reinterpret_cast<V*>(axa);
   V* tv = reinterpret_cast<V*>(t);
   if constexpr (kShadow) {
-    V* f = reinterpret_cast<V*>(t + B.max_k + 8);
+    V* f = reinterpret_cast<V*>(t + B.max_k + 16);
     pv = f;
     xv = pv + B.max_n;
     yv = xv + B.max_n;
@@ -486,10 +529,7 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         // ---- BB projected gradient (Section 4) from x, with r = p = -g:
         // alpha0 = g'Mg / g'g, then x+ = min(max(x + r/alpha, lo), hi), s = x+ - x,
         // r -= M s, Q x += Q s, alpha = s'Ms / s's (M = Q + I/tau)
-        cta_qprod<V, NT, false>(F, qd, n, k, pv, tv, q);
-        double gmg = 0.0;
-        for (int j = tid; j < n; j += NT) gmg = fma(p[j], q[j] + p[j] * inv_tau, gmg);
-        gmg = cta_sum1<NT>(gmg, red);
+        const double gmg = cta_qprod_pmp<V, NT>(F, qd, n, k, pv, p, inv_tau, tv, t, q);
         if (!(gmg > 0.0) || !isfinite(gmg)) numerr = true;
         double alpha = gmg / rr;
         while (!numerr) {
@@ -508,16 +548,13 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
             ss = fma(sj, sj, ss);
           }
           ss = cta_sum1<NT>(ss, red);
-          cta_qprod<V, NT, false>(F, qd, n, k, pv, tv, q);  // q = Q s
-          double sw = 0.0;
+          // q = Q s and s'(Q + I/tau)s
+          const double sw = cta_qprod_pmp<V, NT>(F, qd, n, k, pv, p, inv_tau, tv, t, q);
           for (int j = tid; j < n; j += NT) {
             const double sj = p[j], qj = q[j];
-            const double wj = qj + sj * inv_tau;
-            r[j] -= wj;
+            r[j] -= qj + sj * inv_tau;
             qx[j] += qj;
-            sw = fma(sj, wj, sw);
           }
-          sw = cta_sum1<NT>(sw, red);
           ++steps;
           const bool stop =
               mode == kCgFixed ? steps >= nfix : (sqrt(ss) <= eps || steps >= cgmax);
