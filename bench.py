@@ -586,7 +586,7 @@ def run_batch_bench(args):
                      "note": "latency-bound: block barriers and dependent loads per "
                              "iteration, not arithmetic"},
         "cpu_baseline": cpu,
-        "gpu_launches": args.steps,
+        "gpu_launches": min(4, len(insts)) * args.steps,  # one k_batch launch per size bin
         "clocks": clocks.summary(),
     }
     print(json.dumps(out), flush=True)
@@ -740,7 +740,10 @@ def run_warmstart_bench(args):
                               bounds=True)
     cold_t, warm_t = [], []
     cold_ph, warm_ph = {}, {}
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     for rep_i in range(args.warmup + args.steps):
+        if rep_i == args.warmup:
+            clocks.__enter__()
         timed = rep_i >= args.warmup
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -755,6 +758,7 @@ def run_warmstart_bench(args):
         if rep_i >= args.warmup:
             cold_t.append(t1 - t0)
             warm_t.append(t2 - t1)
+    clocks.__exit__(None, None, None)
     it_c = float(np.mean([r["iterations"] for r in cold]))
     it_w = float(np.mean([r["iterations"] for r in hot]))
     value = statistics.mean(warm_t)
@@ -783,7 +787,8 @@ def run_warmstart_bench(args):
                     + q.A_col.nbytes + q.A_rowptr.nbytes + q.lo.nbytes + q.hi.nbytes
                     for q in test)),
                 "d2h_bytes_per_step": int(8 * sum(q.n + q.m for q in test))},
-        "roofline": None, "cpu_baseline": None, "gpu_launches": None, "clocks": None,
+        "roofline": None, "cpu_baseline": None, "gpu_launches": None,
+        "clocks": clocks.summary(),
     }
     print(json.dumps(out), flush=True)
     net.close()

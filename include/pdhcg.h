@@ -140,11 +140,12 @@ typedef struct {
   int32_t refine;             /* mixed: continue in FP64 if the FP64 check misses tol; default 1 */
   int32_t step_mode;          /* QP_STEP_FIXED (eta = 1/(2||A||_2), Section 3.2; default) or
                                  QP_STEP_ADAPTIVE (Section 4 adaptive step size, see below) */
-  int32_t mixed_stall_evals;  /* mixed with refine: after max(this, a quarter of the
-                                 evaluations so far) evaluations in a row without a 10% gain
-                                 on the best relKKT, the FP32 phase ends and FP64 refinement
-                                 continues from its iterate (an FP32 rounding floor above
-                                 tol); 0: off; default 32 */
+  int32_t mixed_stall_evals;  /* mixed with refine: once the best relKKT of the FP32 phase
+                                 is below 1000 FP32 epsilons (1.2e-4), after max(this, a
+                                 quarter of the evaluations so far) evaluations in a row
+                                 without a 10% gain on it, the FP32 phase ends and FP64
+                                 refinement continues from its iterate (an FP32 rounding
+                                 floor above tol); 0: off; default 32 */
   int64_t reserved[6];
 } qp_options;
 

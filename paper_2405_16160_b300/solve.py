@@ -36,6 +36,9 @@ def main(argv=None) -> int:
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--step", choices=["adaptive", "fixed"], default="adaptive")
     ap.add_argument("--no-scale", action="store_true")
+    ap.add_argument("--mixed-stall-evals", type=int, default=None,
+                    help="mixed: hand over to FP64 after this many evaluations without a "
+                         "10%% gain (0: off; default: the library's)")
     ap.add_argument("--repeat", type=int, default=1)
     args = ap.parse_args(argv)
 
@@ -54,6 +57,8 @@ def main(argv=None) -> int:
     opts = dict(tol=args.tol, max_iter=args.max_iter,
                 precision=L.PREC_MIXED if args.precision == "mixed" else L.PREC_FP64,
                 step_mode=L.STEP_ADAPTIVE if args.step == "adaptive" else L.STEP_FIXED)
+    if args.mixed_stall_evals is not None:
+        opts["mixed_stall_evals"] = args.mixed_stall_evals
     with solver:
         for r in range(args.repeat):
             e0 = torch.cuda.Event(enable_timing=True)
