@@ -606,10 +606,35 @@ __device__ __forceinline__ void store_and_finish_dot(A acc, double* part, unsign
 // spill; three measured faster.
 constexpr int kCgBlocksPerSm = 3;
 
+// Adaptive step size: the attempt's primal move from its saved start (x_save,
+// qx_save), ||x+ - x||^2 and (x+ - x)'(Q x+ - Q x), summed by the x-step
+// kernel after its last step, when every block's writes of x and Q x are
+// visible (a grid barrier closes each step), into part[2 * block]; k_dual's
+// last block combines them with its own sums.  part == nullptr: fixed step.
+template <class T>
+struct StepStart {
+  const T* x_save = nullptr;
+  const T* qx_save = nullptr;
+  double* part = nullptr;
+};
+
+template <class T, class A>
+__device__ __forceinline__ void step_start_sums(const StepStart<T>& ss, const T* x, const T* qx,
+                                                int n) {
+  A acc[2];
+  for (long long i = grid_tid(); i < n; i += grid_threads()) {
+    const T dx = x[i] - ss.x_save[i], dq = qx[i] - ss.qx_save[i];
+    acc[0].add_prod(dx, dx);
+    acc[1].add_prod(dx, dq);
+  }
+  block_reduce_ms<0, 2, T>(nullptr, acc, ss.part + 2 * size_t(blockIdx.x));
+}
+
 template <int G, class T>
 __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     k_cg(CsrT<T> Q, LongRows LQ, T* qseg, T* qlong, T* x, T* r, T* p, T* q, T* qx,
-         const double* r0r0, double* part, DevState* st, GridBarrier* bar, int n) {
+         const double* r0r0, double* part, DevState* st, GridBarrier* bar, int n,
+         StepStart<T> ss) {
   using A = typename Acc<T>::type;
   const bool active = running(st) && st->attempts < st->opt.max_iter;
   if (!active) {
@@ -729,6 +754,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     }
     if (!grid_sync(bar, st, tmo, false)) return;
   }
+  if (ss.part && !numerr) step_start_sums<T, A>(ss, x, qx, n);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (numerr) {
       st->done = kDoneNumerical;
@@ -767,7 +793,7 @@ template <int G, class T>
 __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     k_bb(CsrT<T> Q, LongRows LQ, T* qseg, T* qlong, T* x, T* r, T* p, T* qx,
          const T* __restrict__ lo, const T* __restrict__ hi, const double* r0r0, double* part,
-         DevState* st, GridBarrier* bar, int n) {
+         DevState* st, GridBarrier* bar, int n, StepStart<T> sstart) {
   using A = typename Acc<T>::type;
   const bool active = running(st) && st->attempts < st->opt.max_iter;
   if (!active) {
@@ -858,6 +884,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
       alpha = sw / ss;
     }
   }
+  if (sstart.part && !numerr) step_start_sums<T, A>(sstart, x, qx, n);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (numerr) {
       st->done = kDoneNumerical;
@@ -907,23 +934,20 @@ __global__ void k_project_box(T* x, const T* __restrict__ lo, const T* __restric
 //
 // Adaptive step size (T.y_new != nullptr): the step is a trial.  y, its low
 // word, the A x cache and the average stay as they are; the trial y+ (and its
-// low word) and A x+ go to T.y_new, T.yn_lo, T.ax_new.  Each block also takes
-// a slice of the n index space for the primal move of the attempt from its
-// saved start (T.x_save, T.qx_save and the tracked Q x), and stores the
-// partial sums ||y+ - y||^2, (y+ - y)'(A x+ - A x), ||x+ - x||^2 and
-// (x+ - x)'(Q x+ - Q x) at part_step[4 * block]; the last block to finish
-// combines them in a fixed order and takes the Section 4 step decision
-// (step_decide).  k_commit_m and k_atv then commit or drop the trial.
+// low word) and A x+ go to T.y_new, T.yn_lo, T.ax_new.  Each block stores the
+// partial sums ||y+ - y||^2 and (y+ - y)'(A x+ - A x) at part_step[2 * block];
+// the last block to finish combines them, and the x-step kernel's partials of
+// ||x+ - x||^2 and (x+ - x)'(Q x+ - Q x) (StepStart: part_n, n_parts blocks),
+// in a fixed order and takes the Section 4 step decision (step_decide).
+// k_commit_m and k_atv then commit or drop the trial.
 template <class T>
 struct StepTrial {
   T* y_new = nullptr;
   T* yn_lo = nullptr;
   T* ax_new = nullptr;
-  const T* x_save = nullptr;
-  const T* qx_save = nullptr;
-  const T* qx = nullptr;
-  int n = 0;
   double* part_step = nullptr;
+  const double* part_n = nullptr;
+  int n_parts = 0;
   unsigned int* ticket = nullptr;
 };
 
@@ -947,9 +971,8 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
   const bool first = st->j == 1;
   const int m_eq = st->opt.m_eq;
   if (tr.y_new) {
-    typename Acc<T>::type acc[4];
-    {
     typename Acc<T>::type am[2];
+    {
     spmv_rows<G>(A, x, [&](int i, T s, bool lead) {
       if (!lead) return;
       const T da = s - ax[i];
@@ -971,15 +994,8 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
       am[0].add_prod(dy, dy);
       am[1].add_prod(dy, da);
     });
-    acc[0] = am[0];
-    acc[1] = am[1];
     }
-    for (long long i = grid_tid(); i < tr.n; i += grid_threads()) {
-      const T dx = x[i] - tr.x_save[i], dq = tr.qx[i] - tr.qx_save[i];
-      acc[2].add_prod(dx, dx);
-      acc[3].add_prod(dx, dq);
-    }
-    block_reduce_ms<0, 4, T>(nullptr, acc, tr.part_step + 4 * size_t(blockIdx.x));
+    block_reduce_ms<0, 2, T>(nullptr, am, tr.part_step + 2 * size_t(blockIdx.x));
     __shared__ int s_last;
     if (threadIdx.x == 0) {
       __threadfence();
@@ -988,10 +1004,11 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
     __syncthreads();
     if (s_last) {  // the whole last block (the branch is uniform)
       __threadfence();
-      double t[4];
-      block_reduce_rows<4>(tr.part_step, gridDim.x, 4, 0u, t);
+      double t[2], u[2];
+      block_reduce_rows<2>(tr.part_step, gridDim.x, 2, 0u, t);
+      block_reduce_rows<2>(tr.part_n, tr.n_parts, 2, 0u, u);
       if (threadIdx.x == 0) {
-        step_decide(st, t[2], t[3], t[0], t[1]);
+        step_decide(st, u[0], u[1], t[0], t[1]);
         *tr.ticket = 0u;
         __threadfence();
       }

@@ -215,7 +215,8 @@ struct qp_handle {
   VecSet<float> v32;
   double *part_cg = nullptr, *part_n = nullptr, *part_m = nullptr, *part_rn = nullptr,
          *part_rm = nullptr, *part_pow = nullptr, *part2 = nullptr, *part_r0 = nullptr;
-  double* part_step_m = nullptr;  // adaptive step test partials (4 per k_dual block)
+  double* part_step_m = nullptr;  // adaptive step test partials (2 per k_dual block)
+  double* part_step_n = nullptr;  // and the primal move's (2 per CG/BB block)
   int step_mode = QP_STEP_FIXED;  // step rule of the iteration being launched
   DevState* st = nullptr;
   GridBarrier* bar = nullptr;
@@ -387,17 +388,23 @@ qp_status launch_cg(qp_handle* h, bool coop) {
       cfg.numAttrs = 1;
     }
     const double* r0r0 = h->part_r0 + h->grid_n;
+    StepStart<T> sstart;  // adaptive step: the primal move's partials for k_dual
+    if (h->step_mode == QP_STEP_ADAPTIVE) {
+      sstart.x_save = v.x_save;
+      sstart.qx_save = v.qx_save;
+      sstart.part = h->part_step_n;
+    }
     if (h->bounded) {
       // Section 4: BB projected gradient (the mixed path's bounds are of dx)
       const bool fp32 = std::is_same<T, float>::value;
       cudaLaunchKernelEx(&cfg, k_bb<G, T>, view<T>(h->Q), long_rows_of(h->Q), seg_buf<T>(h->Q),
                          long_buf<T>(h->Q), it_x(v), v.r, v.p, v.qx,
                          (const T*)(fp32 ? v.lo_d : v.lo), (const T*)(fp32 ? v.hi_d : v.hi),
-                         r0r0, h->part_cg, h->st, h->bar, (int)h->n);
+                         r0r0, h->part_cg, h->st, h->bar, (int)h->n, sstart);
     } else {
       cudaLaunchKernelEx(&cfg, k_cg<G, T>, view<T>(h->Q), long_rows_of(h->Q), seg_buf<T>(h->Q),
                          long_buf<T>(h->Q), it_x(v), v.r, v.p, v.q, v.qx, r0r0, h->part_cg,
-                         h->st, h->bar, (int)h->n);
+                         h->st, h->bar, (int)h->n, sstart);
     }
   });
 }
@@ -413,11 +420,9 @@ qp_status launch_dual(qp_handle* h) {
       tr.y_new = v.y_new;
       tr.yn_lo = v.yn_lo;
       tr.ax_new = v.ax_new;
-      tr.x_save = v.x_save;
-      tr.qx_save = v.qx_save;
-      tr.qx = v.qx;
-      tr.n = h->n;
       tr.part_step = h->part_step_m;
+      tr.part_n = h->part_step_n;
+      tr.n_parts = h->grid_cg[std::is_same<T, double>::value ? 0 : 1];
       tr.ticket = h->ticket;
     }
     k_dual<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(view<T>(h->A), it_x(v), it_b(v), v.y,
@@ -1200,6 +1205,7 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   QP_TRY(dalloc(h, &h->part_pow, size_t(gmax)));
   QP_TRY(dalloc(h, &h->part2, size_t(2) * gmax));
   QP_TRY(dalloc(h, &h->part_step_m, size_t(4) * h->grid_m));
+  QP_TRY(dalloc(h, &h->part_step_n, size_t(2) * std::max(h->grid_cg[0], h->grid_cg[1])));
   QP_TRY(dalloc(h, &h->st, 1));
   QP_TRY(dalloc(h, &h->bar, 1));
   CUDA_TRY(cudaMallocHost(&h->h_st, sizeof(DevState)));
