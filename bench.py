@@ -135,7 +135,7 @@ def _peaks():
 
 
 def cg_kernel_bytes(nnz_q: int, n: int, launches: int, spmvs: int, cg_steps: int,
-                    w: int) -> float:
+                    w: int, adaptive: bool = False) -> float:
     """Algorithmic DRAM bytes of the CG kernel, each array counted once per phase.
 
     w = bytes per value (8 FP64, 4 FP32); indices are int32.
@@ -143,10 +143,13 @@ def cg_kernel_bytes(nnz_q: int, n: int, launches: int, spmvs: int, cg_steps: int
     pointer) + w B/row gathered p + w B/row written q.
     Phase B (per step): reads x, p, q, r, qx and writes x, r, qx: 8w B/row.
     Phase C (per continued step): reads r, p and writes p: 3w B/row.
+    Adaptive step (per launch): the step test's pass over x, Q x and their
+    saved start after the last step: 4w B/row.
     r0 is formed by the A' kernel of the previous iteration, not here.
     """
     spmv = (w + 4.0) * nnz_q + (4.0 + 2.0 * w) * n
-    return spmvs * spmv + cg_steps * 8.0 * w * n + max(cg_steps - launches, 0) * 3.0 * w * n
+    return (spmvs * spmv + cg_steps * 8.0 * w * n + max(cg_steps - launches, 0) * 3.0 * w * n
+            + (launches * 4.0 * w * n if adaptive else 0.0))
 
 
 def mixed_solve_launches(chunks: int, power_iters: int, eval_freq: int,
@@ -355,7 +358,8 @@ def run_ours(args):
     info = infos[-1]
     peak, peak_kind = _peaks()
     bytes_total = sum(cg_kernel_bytes(inst.nnz_Q, inst.n, i["cg_kernel_launches"],
-                                      i["cg_kernel_spmvs"], i["cg_steps"], 4) for i in kinfos)
+                                      i["cg_kernel_spmvs"], i["cg_steps"], 4,
+                                      adaptive=args.step == "adaptive") for i in kinfos)
     launches = sum(i["cg_kernel_launches"] for i in kinfos)
     kernel_s = sum(i["cg_kernel_ms"] for i in kinfos) / 1e3
     achieved = bytes_total / kernel_s / 1e9 if kernel_s > 0 else None
@@ -651,7 +655,7 @@ def run_zipf_bench(args):
     peak, peak_kind = _peaks()
     ki = kinfos[-1]
     kbytes = cg_kernel_bytes(inst.nnz_Q, inst.n, ki["cg_kernel_launches"], ki["cg_kernel_spmvs"],
-                             ki["cg_steps"], 4)
+                             ki["cg_steps"], 4, adaptive=args.step == "adaptive")
     ks = ki["cg_kernel_ms"] / 1e3
     achieved = kbytes / ks / 1e9 if ks > 0 else None
     ceiling = gather_ceiling(inst.nnz_Q, inst.n)
