@@ -491,15 +491,17 @@ __device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f) {
   }
 }
 
-// Segment sum of a long row with the products and the sum carried in FP64
-// (a product of two FP32 numbers is exact in FP64).  A row of millions of
-// entries would otherwise pick up an FP32 rounding error that grows with its
-// length, on exactly the coordinates (high-degree columns of A, i.e. long
-// rows of A') where the scaled residual is smallest.
+// Segment sum of a long row by a whole warp (the warp's total, for every
+// lane), with the sum carried beyond FP32.  A row of millions of entries
+// would otherwise pick up an FP32 rounding error that grows with its length,
+// on exactly the coordinates (high-degree columns of A, i.e. long rows of A')
+// where the scaled residual is smallest.  FP32 values: each product is
+// formed exactly (two-product) and summed in double-float on the FP32 pipe
+// (FP64 arithmetic runs at 1/58 of FP32 here); FP64 values: plain FP64.
 template <class T>
 __device__ __forceinline__ double row_dot_wide(const CsrT<T>& M, const T* v, int b, int e,
                                                int lane) {
-  double s = 0.0;
+  typename Acc<T>::type s;
   for (int k = b + lane; k < e; k += kUnroll * 32) {
     int c[kUnroll];
     T a[kUnroll], xv[kUnroll];
@@ -512,13 +514,14 @@ __device__ __forceinline__ double row_dot_wide(const CsrT<T>& M, const T* v, int
 #pragma unroll
     for (int j = 0; j < kUnroll; ++j) xv[j] = c[j] >= 0 ? v[c[j]] : T(0);
 #pragma unroll
-    for (int j = 0; j < kUnroll; ++j) s = fma((double)a[j], (double)xv[j], s);
+    for (int j = 0; j < kUnroll; ++j) s.add_prod(a[j], xv[j]);
   }
-  return s;
+  warp_merge(s);
+  return s.value();
 }
 
 // Long-row pre-pass, phase 1: one warp per segment (grid-stride over warps).
-// The segment sums are accumulated in FP64 for both value types.
+// Each segment is summed beyond FP32 (row_dot_wide).
 template <class T>
 __device__ __forceinline__ void long_segments(const CsrT<T>& M, const T* v, const LongRows& L,
                                               T* seg_part) {
@@ -526,7 +529,7 @@ __device__ __forceinline__ void long_segments(const CsrT<T>& M, const T* v, cons
   const long long nw = grid_threads() >> 5;
   for (long long sg = grid_tid() >> 5; sg < L.nseg; sg += nw) {
     const int e = __ldg(L.seg_end + sg);
-    const double s = warp_sum(row_dot_wide(M, v, __ldg(L.seg_begin + sg), e, lane));
+    const double s = row_dot_wide(M, v, __ldg(L.seg_begin + sg), e, lane);
     if (lane == 0) seg_part[sg] = T(s);
   }
 }

@@ -25,6 +25,14 @@ def _i32(a):
     return np.ascontiguousarray(a, dtype=np.int32)
 
 
+def _host_f64(n, pinned):
+    """An n-entry float64 host array, page-locked (through PyTorch) if asked."""
+    if pinned and n > 0:
+        import torch
+        return torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    return np.empty(n)
+
+
 def _ptr(a, ctype):
     return a.ctypes.data_as(POINTER(ctype)) if a is not None else None
 
@@ -122,8 +130,10 @@ class QPSolver:
         return info.as_dict()
 
     def solution(self):
-        x = np.empty(self.n)
-        y = np.empty(self.m)
+        """(x, y) in host arrays; page-locked ones when PyTorch has allocated
+        this handle's memory, so that the copies run at DMA speed."""
+        x = _host_f64(self.n, self._ctx is not None)
+        y = _host_f64(self.m, self._ctx is not None)
         L.check(self.lib.qp_get_solution(self.h, _ptr(x, c_double), _ptr(y, c_double)),
                 "qp_get_solution")
         return x, y
