@@ -158,14 +158,14 @@ def mixed_solve_launches(chunks: int, power_iters: int, eval_freq: int,
     long rows (each SpMV is then one launch).
 
     set-up: k_init_vectors; cache refresh (k_materialize, A x_a, k_shift_rhs,
-    A dx, A'y, Q x, k_prepare); power iteration (k_pow_start, 3 per step,
+    A dx, A'y, Q x, k_prepare); power iteration (k_pow_start, 2 per step,
     k_setup_finish); the first evaluation (k_materialize, 4 SpMVs, k_kkt_n,
     k_kkt_m, k_control).  Per chunk: 3 per iteration (k_cg, k_dual, k_atv;
     4 per attempt with the adaptive step: k_commit_m), an evaluation (8), the
     restart kernels (3) and k_prepare.  At the end the FP64 check: 2
     conversions, the FP64 cache refresh (3 SpMVs, k_prepare) and an FP64
     evaluation (4 SpMVs, k_kkt_n, k_kkt_m, k_control)."""
-    setup = 1 + 7 + (1 + 3 * power_iters + 1) + 8
+    setup = 1 + 7 + (1 + 2 * power_iters + 1) + 8
     chunk = (4 if adaptive else 3) * eval_freq + 8 + 3 + 1
     final = 2 + 4 + 7
     return setup + chunks * chunk + final

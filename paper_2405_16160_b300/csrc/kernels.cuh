@@ -1157,15 +1157,26 @@ __global__ void __launch_bounds__(kBlock) k_prepare(const T* __restrict__ qx,
 // Plain out = M v, optionally with per-block partial sums of out_i^2 (double).
 template <int G, class T>
 __global__ void __launch_bounds__(kBlock) k_spmv(CsrT<T> M, const T* __restrict__ v, T* out,
-                                                 double* part_sq) {
+                                                 double* part_sq, unsigned int* ticket,
+                                                 const double* inv_norm_sq) {
+  // out = M v / ||v||_2 when inv_norm_sq points at ||v||_2^2 (the power
+  // iteration's normalisation, applied to the product instead of to v)
+  T scale = T(1);
+  if (inv_norm_sq) {
+    const double l2 = __ldcg(inv_norm_sq);
+    scale = l2 > 0.0 ? T(1.0 / sqrt(l2)) : T(0);
+  }
   typename Acc<T>::type acc;
   spmv_rows<G>(M, v, [&](int i, T s, bool lead) {
     if (lead) {
-      out[i] = s;
-      acc.add_prod(s, s);
+      const T o = s * scale;
+      out[i] = o;
+      acc.add_prod(o, o);
     }
   });
-  if (part_sq) block_sum_store(acc, part_sq + blockIdx.x);
+  // ||out||^2: block partials, and the total (part_sq[gridDim.x]) from the
+  // last block to finish
+  if (part_sq) store_and_finish_dot(acc, part_sq, ticket);
 }
 
 // ------------------------------------------------ relKKT terms (Section 4)
@@ -1453,16 +1464,6 @@ __global__ void k_pow_start(T* v, int n, const T* __restrict__ c, const T* __res
   block_reduce_ms<0, 2, T>(nullptr, a, part2 + size_t(blockIdx.x) * 2);
 }
 
-// v = w / lambda with lambda = ||w||_2 from the partials of the A' u pass.
-template <class T>
-__global__ void k_pow_scale(const T* __restrict__ w, T* v, int n, const double* part, int gp,
-                            DevState* st) {
-  const double lam = sqrt(block_all_reduce<AccD>(part, gp));
-  const T inv_lam = lam > 0.0 ? T(1.0 / lam) : T(0);
-  for (long long i = grid_tid(); i < n; i += grid_threads()) v[i] = w[i] * inv_lam;
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->lam = lam;
-}
-
 // Element-wise type conversion (FP64 <-> FP32 copies of a vector).
 template <class Ti, class To>
 __global__ void k_convert(const Ti* __restrict__ in, To* out, int n) {
@@ -1521,10 +1522,12 @@ __global__ void k_shift_rhs(const float* __restrict__ b, const float* __restrict
 
 
 __global__ void __launch_bounds__(kBlock) k_setup_finish(const double* part2, int g2,
-                                                         DevState* st, int reset) {
+                                                         const double* w_norm_sq, DevState* st,
+                                                         int reset) {
   double s[2];
   block_reduce_rows<2>(part2, g2, 2, 0u, s);
   if (threadIdx.x != 0) return;
+  st->lam = sqrt(__ldcg(w_norm_sq));  // ||A'A v|| of the last power step
   setup_finish_decide(st, s[0], s[1], reset);
 }
 

@@ -450,11 +450,13 @@ qp_status launch_atv(qp_handle* h) {
 }
 
 template <class T>
-qp_status launch_spmv(qp_handle* h, const DevMat& M, const T* x, T* out, double* part, int grid) {
+qp_status launch_spmv(qp_handle* h, const DevMat& M, const T* x, T* out, double* part, int grid,
+                      const double* inv_norm_sq = nullptr) {
   launch_long<T>(h, M, x);
   return dispatch_g(lanes<T>(M), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    k_spmv<G, T><<<grid, kBlock, 0, h->stream>>>(view<T>(M), x, out, part);
+    k_spmv<G, T><<<grid, kBlock, 0, h->stream>>>(view<T>(M), x, out, part, h->ticket,
+                                                 inv_norm_sq);
   });
 }
 
@@ -546,13 +548,16 @@ template <class T>
 qp_status launch_setup(qp_handle* h, int power_iters, int reset) {
   VecSet<T>& v = vecs<T>(h);
   k_pow_start<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.pw_v, h->n, v.c, v.b, h->m, h->part2);
+  // v_{t+1} = w_t / ||w_t|| with w_t = A'A v_t: the normalisation is folded
+  // into the next product with A (its output scaled by 1/||w_t||, the total
+  // the A' pass leaves at part_pow[grid_n]), so v is never written again
+  const double* w_norm_sq = h->part_pow + h->grid_n;
   for (int t = 0; t < power_iters; ++t) {
-    QP_TRY(launch_spmv<T>(h, h->A, v.pw_v, v.pw_u, nullptr, h->grid_m));
+    QP_TRY(launch_spmv<T>(h, h->A, t == 0 ? v.pw_v : v.pw_w, v.pw_u, nullptr, h->grid_m,
+                          t == 0 ? nullptr : w_norm_sq));
     QP_TRY(launch_spmv<T>(h, h->At, v.pw_u, v.pw_w, h->part_pow, h->grid_n));
-    k_pow_scale<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.pw_w, v.pw_v, h->n, h->part_pow,
-                                                          h->grid_n, h->st);
   }
-  k_setup_finish<<<1, kBlock, 0, h->stream>>>(h->part2, h->grid_vec, h->st, reset);
+  k_setup_finish<<<1, kBlock, 0, h->stream>>>(h->part2, h->grid_vec, w_norm_sq, h->st, reset);
   return QP_OK;
 }
 
@@ -1202,7 +1207,7 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   QP_TRY(dalloc(h, &h->part_m, size_t(h->grid_m) * kPartStride));
   QP_TRY(dalloc(h, &h->part_rn, size_t(gmax)));
   QP_TRY(dalloc(h, &h->part_rm, size_t(gmax)));
-  QP_TRY(dalloc(h, &h->part_pow, size_t(gmax)));
+  QP_TRY(dalloc(h, &h->part_pow, size_t(gmax) + 1));
   QP_TRY(dalloc(h, &h->part2, size_t(2) * gmax));
   QP_TRY(dalloc(h, &h->part_step_m, size_t(4) * h->grid_m));
   QP_TRY(dalloc(h, &h->part_step_n, size_t(2) * std::max(h->grid_cg[0], h->grid_cg[1])));
