@@ -792,6 +792,22 @@ qp_status build_row_tables(qp_handle* h, DevMat* M, const int32_t* host_rowptr) 
   // give short rows one lane each to keep the DFMA slots full, so a warp per
   // row pays off there only from 64 entries.
   std::vector<int32_t> lr, sb, se, sp(1, 0), md[2];
+  // On a skewed matrix the lanes per row follow the rows the grouped loop
+  // keeps (at most 64 entries) rather than the overall mean, which the few
+  // long rows inflate (A' of a power-law A: a mean of 4 over rows that mostly
+  // hold 0-2 entries).
+  int64_t short_rows = 0, short_nnz = 0;
+  for (int32_t i = 0; i < M->rows; ++i) {
+    const int32_t len = host_rowptr[i + 1] - host_rowptr[i];
+    if (len <= 64) {
+      ++short_rows;
+      short_nnz += len;
+    }
+  }
+  if (short_rows > 0 && short_rows < M->rows) {
+    M->G64 = group_size_for(short_nnz, short_rows, false);
+    M->G32 = group_size_for(short_nnz, short_rows, true);
+  }
   int32_t med_min[2];
   for (int fp32 = 0; fp32 < 2; ++fp32) {
     const int G = fp32 ? M->G32 : M->G64;
