@@ -692,17 +692,16 @@ qp_status qp_batch_set_bounds(qp_batch* h, const double* lo, const double* hi) {
   }
   BTRY(begin(h));
   h->solved = false;
-  h->bounded = any;
+  h->bounded = false;  // set again only once both arrays hold the new bounds
   if (any) {
-    if (!h->lo) {
-      BTRY(balloc(h, reinterpret_cast<void**>(&h->lo), N * sizeof(double)));
-      BTRY(balloc(h, reinterpret_cast<void**>(&h->hi), N * sizeof(double)));
-    }
+    if (!h->lo) BTRY(balloc(h, reinterpret_cast<void**>(&h->lo), N * sizeof(double)));
+    if (!h->hi) BTRY(balloc(h, reinterpret_cast<void**>(&h->hi), N * sizeof(double)));
     BCUDA(cudaMemcpyAsync(h->lo, l.data(), N * sizeof(double), cudaMemcpyHostToDevice,
                           h->stream));
     BCUDA(cudaMemcpyAsync(h->hi, u.data(), N * sizeof(double), cudaMemcpyHostToDevice,
                           h->stream));
     BCUDA(cudaStreamSynchronize(h->stream));  // the staging vectors die here
+    h->bounded = true;
   }
   return finish(h);
 }

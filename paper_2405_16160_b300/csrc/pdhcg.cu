@@ -1899,17 +1899,15 @@ qp_status qp_set_bounds(qp_handle* h, const double* lo, const double* hi) {
     }
     any = any || std::isfinite(l[j]) || std::isfinite(u[j]);
   }
+  std::vector<double> lo_user_new = l, hi_user_new = u;  // as given (unscaled)
   QP_TRY(begin_call(h));
   h->solved = false;
-  h->bounded = any;
-  h->lo_user = l;
-  h->hi_user = u;
+  h->bounded = false;  // set again only once every bounds array holds the new bounds
   if (any) {
-    if (!h->v64.lo) {
-      for (double** p : {&h->v64.lo, &h->v64.hi}) QP_TRY(dalloc(h, p, N));
-      for (float** p : {&h->v32.lo, &h->v32.hi, &h->v32.lo_d, &h->v32.hi_d})
-        QP_TRY(dalloc(h, p, N));
-    }
+    for (double** p : {&h->v64.lo, &h->v64.hi})
+      if (!*p) QP_TRY(dalloc(h, p, N));
+    for (float** p : {&h->v32.lo, &h->v32.hi, &h->v32.lo_d, &h->v32.hi_d})
+      if (!*p) QP_TRY(dalloc(h, p, N));
     // the solver's variables are x / D2 under the Section 4 scaling
     std::vector<float> l32(N), u32(N);
     for (size_t j = 0; j < N; ++j) {
@@ -1923,7 +1921,10 @@ qp_status qp_set_bounds(qp_handle* h, const double* lo, const double* hi) {
     QP_TRY(upload(h, h->v32.lo, l32.data(), N * sizeof(float)));
     QP_TRY(upload(h, h->v32.hi, u32.data(), N * sizeof(float)));
     QP_TRY(sync(h));
+    h->bounded = true;
   }
+  h->lo_user = std::move(lo_user_new);
+  h->hi_user = std::move(hi_user_new);
   return end_call(h);
 }
 
