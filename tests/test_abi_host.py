@@ -97,6 +97,26 @@ def test_csr_validate_rejects_bad_inputs(lib):
         assert S.csr_validate(*args) == 1, args
 
 
+def test_csr_validate_accepts_any_valid_layout_and_reports_the_first_bad_entry(lib):
+    """Unsorted rows, duplicates and empty rows are valid input (qp_create
+    canonicalises them); on a large matrix, checked in parallel ranges, the
+    error names the lowest bad entry."""
+    assert S.csr_validate(4, 5, [0, 3, 3, 5, 5], [4, 0, 4, 2, 1], [1.0, 2.0, 3.0, 4.0, 5.0]) == 0
+    assert S.csr_validate(3, 3, [0, 0, 0, 0], [], []) == 0
+    rng = np.random.default_rng(0)
+    rows, per = 200_000, 6
+    rp = np.arange(0, rows * per + 1, per, dtype=np.int32)
+    col = rng.integers(0, rows, rows * per).astype(np.int32)
+    val = rng.standard_normal(rows * per)
+    assert S.csr_validate(rows, rows, rp, col, val) == 0
+    col[900_001] = rows         # out of range, late
+    val[500_003] = np.inf       # non-finite, earlier
+    col[700_000] = -3           # out of range, in between
+    assert S.csr_validate(rows, rows, rp, col, val) == 1
+    msg = L.load_library().qp_last_error().decode()
+    assert "500003" in msg and "non-finite" in msg, msg
+
+
 def test_csr_transpose_is_stable_and_exact(lib):
     rng = np.random.default_rng(0)
     M = sp.random(300, 170, density=0.03, random_state=1, format="csr")

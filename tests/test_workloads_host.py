@@ -58,3 +58,22 @@ def test_portfolio_bounds_form_drops_only_the_long_only_rows():
         inst = q.to_instance()
         assert inst.lo is q.lo and inst.hi is q.hi
     assert p.lo is None and p.to_instance().lo is None
+
+
+def test_portfolio_family_bounds_form_shares_its_draws():
+    fam = W.portfolio_family(0, seeds=[3], n=200, k=10, sectors=8)
+    fb = W.portfolio_family(0, seeds=[3], n=200, k=10, sectors=8, bounds=True)
+    p, q = fam[0], fb[0]
+    assert np.array_equal(p.F, q.F) and np.array_equal(p.c, q.c)
+    assert (p.m, q.m) == (1 + 200 + 8, 1 + 8) and q.m_eq == 1
+    assert np.all(q.lo == 0) and np.all(np.isinf(q.hi))
+
+
+def test_cli_parses_its_options():
+    import pytest
+    from paper_2405_16160_b300 import solve as S
+    with pytest.raises(SystemExit) as e:
+        S.main(["--help"])
+    assert e.value.code == 0
+    with pytest.raises(SystemExit):
+        S.main(["--workload", "no_such_workload"])
