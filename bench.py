@@ -707,7 +707,6 @@ def run_warmstart_bench(args):
 
     ws, rank = _dist()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    from oracle import mlp_oracle as M  # He-normal starting weights from a seeded generator
     from paper_2405_16160_b300 import _lib as L
     from paper_2405_16160_b300 import build as B
     from paper_2405_16160_b300 import warmstart as WS
@@ -733,7 +732,7 @@ def run_warmstart_bench(args):
     X, T = np.concatenate(feats), np.concatenate(targs)
     widths = [X.shape[1], *WS_WORKLOAD["hidden"], T.shape[1]]
     net = WS.WarmStartMLP(widths, max_batch=1024)
-    net.set_params(M.he_init(widths, 0).astype(np.float32))
+    net.set_params(WS.he_normal_params(widths, 0))
     t0 = time.perf_counter()
     hist = WS.train(net, X, T, epochs=args.train_epochs, batch=256, lr=1e-3)
     torch.cuda.synchronize()

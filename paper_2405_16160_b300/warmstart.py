@@ -208,6 +208,18 @@ def predict(net: WarmStartMLP, X: np.ndarray, n: int, device: str = "cuda"):
     return split_prediction(np.concatenate(out), n)
 
 
+def he_normal_params(widths, seed: int = 0) -> np.ndarray:
+    """Starting parameters of the network, packed as qp_mlp expects (per layer
+    W row-major, then b): weights drawn from N(0, 2 / fan_in) by a seeded
+    PCG64 stream (He et al., 2015, for ReLU layers), biases zero; float32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    chunks = []
+    for fan_in, fan_out in zip(widths[:-1], widths[1:]):
+        w = rng.standard_normal(fan_in * fan_out) * np.sqrt(2.0 / fan_in)
+        chunks += [w.astype(np.float32), np.zeros(fan_out, np.float32)]
+    return np.concatenate(chunks)
+
+
 class WarmStartModel:
     """A trained network plus the family's starting primal weight."""
 
@@ -216,13 +228,13 @@ class WarmStartModel:
 
     @classmethod
     def fit(cls, insts, results, xs, ys, hidden=(512, 512), epochs: int = 100, batch: int = 128,
-            lr: float = 1e-3, seed: int = 0, init=None):
+            lr: float = 1e-3, seed: int = 0, init=he_normal_params):
         """Train on solved instances; ``init(widths, seed)`` gives the packed
-        starting parameters (e.g. He-normal from a seeded generator)."""
+        starting parameters (default: he_normal_params)."""
         X, T = features(insts), targets(xs, ys)
         widths = [X.shape[1], *hidden, T.shape[1]]
         net = WarmStartMLP(widths, max_batch=max(batch, 256))
-        net.set_params(init(widths, seed))
+        net.set_params(np.asarray(init(widths, seed), dtype=np.float32))
         hist = train(net, X, T, epochs=epochs, batch=batch, lr=lr, seed=seed)
         omega0 = float(np.median([r["omega"] for r in results]))
         model = cls(net, X.shape[1], omega0)

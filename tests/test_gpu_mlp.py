@@ -78,7 +78,7 @@ def test_training_fits_a_planted_map():
     X = rng.standard_normal((512, 8)).astype(np.float32)
     T = np.maximum(X @ rng.standard_normal((8, 4)), 0).astype(np.float32)
     net = WS.WarmStartMLP(widths, max_batch=64)
-    net.set_params(M.he_init(widths, 0).astype(np.float32))
+    net.set_params(WS.he_normal_params(widths, 0))
     hist = WS.train(net, X, T, epochs=60, batch=64, lr=3e-3)
     assert hist[-1] < 0.05 * hist[0]
     net.close()
@@ -93,7 +93,7 @@ def test_learned_warm_start_cuts_iterations():
     res, xs, ys = WS.solve_family(train_set, tol=1e-5, precision=L.PREC_MIXED)
     assert all(r["termination"] == L.TERM_SOLVED for r in res)
     model = WS.WarmStartModel.fit(train_set, res, xs, ys, hidden=(256, 256), epochs=40,
-                                  batch=64, init=lambda w, s: M.he_init(w, s).astype(np.float32))
+                                  batch=64)
     assert model.history[-1] < 0.5 * model.history[0]
     cold, _, _ = WS.solve_family(test_set, tol=1e-4, precision=L.PREC_MIXED)
     hot, xs_h, ys_h, n_fallback = model.solve(test_set, tol=1e-4, precision=L.PREC_MIXED)

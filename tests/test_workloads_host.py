@@ -77,3 +77,27 @@ def test_cli_parses_its_options():
     assert e.value.code == 0
     with pytest.raises(SystemExit):
         S.main(["--workload", "no_such_workload"])
+
+
+def test_warm_start_network_has_its_own_initializer():
+    # the learned warm start's starting weights come from the package, not
+    # from the CPU checker: He-normal (std sqrt(2 / fan_in)) weights and zero
+    # biases, packed per layer as W then b, float32, and fit() defaults to it
+    import inspect
+
+    from paper_2405_16160_b300 import warmstart as WS
+
+    widths = [300, 200, 50]
+    p = WS.he_normal_params(widths, 3)
+    assert p.dtype == np.float32
+    assert p.size == sum(a * b + b for a, b in zip(widths[:-1], widths[1:]))
+    o = 0
+    for a, b in zip(widths[:-1], widths[1:]):
+        W_, bias = p[o:o + a * b], p[o + a * b:o + a * b + b]
+        o += a * b + b
+        assert np.all(bias == 0)
+        assert abs(W_.std() / np.sqrt(2.0 / a) - 1.0) < 0.05
+        assert abs(W_.mean()) < 5 * np.sqrt(2.0 / a) / np.sqrt(a * b)
+    assert np.array_equal(p, WS.he_normal_params(widths, 3))
+    assert not np.array_equal(p, WS.he_normal_params(widths, 4))
+    assert inspect.signature(WS.WarmStartModel.fit).parameters["init"].default is WS.he_normal_params
