@@ -103,11 +103,13 @@ path implements the same one):
   D2 Q D2, D1 A D2, D2 c, D1 b, and every relKKT (termination, restarts, the
   CG precision) is evaluated on the original problem at x = D2 x~, y = D1 y~.
 
-Parity unpinned: ``restart_test`` (the exact restart decisions), the
-primal-weight formula inside ``restart_to`` and the omega_0 rule of
-``initial_state`` have no value in the paper to be pinned against; the
-solver's end results with them enabled are pinned by the closed-form and
-brute-force tests.  Every other function is pinned (tests/test_oracle_pins.py).
+Every function is pinned: tests/test_oracle_pins.py, and for the restart
+decisions (``restart_test``, ``evaluate``), the primal-weight update inside
+``restart_to`` and the omega_0 rule of ``initial_state``,
+tests/test_oracle_restart_pins.py (a decision table and an evaluation
+sequence worked by hand against the printed beta_sufficient = 0.2,
+beta_necessary = 0.8, beta_artificial = 0.2, and hand-computed PWeight
+updates with theta = 0.2 and eps_zero = 1e-10).
 """
 from __future__ import annotations
 
