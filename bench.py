@@ -14,7 +14,8 @@ from host arrays (qp_create with the scaling and the host-to-device copies,
 qp_solve, qp_get_solution, qp_destroy) is reported as ``e2e``.
 
 ``--impl reference`` times the CPU FP64 oracle (the reference arm of this
-build) on a bounded sample of the same workload and scales it to the metric.
+build): every timed step is one complete oracle solve of the same instance
+to 1e-4 on the host's cores.
 Under torchrun (N > 1) every rank solves its own instance (replicas; the
 path has no cross-GPU exchange) and rank 0 prints the max over ranks.
 """
@@ -40,11 +41,6 @@ WORKLOAD = {"workload": "large sparse QP: n=1e6, m=5e5, Q = diag U[0.5,2] + mirr
             "step": "Section 4 adaptive step size",
             "l2": "inputs larger than L2 (~470 MB resident working set vs 126 MB L2)"}
 METRIC = "time to 1e-4 rel. KKT (restarted PDHCG; FP32 data/iterates, FP64 reductions) vs plain FP64 GPU PDHCG"
-GOLDEN = {"fixed": os.path.join(ROOT, "tests", "golden",
-                                "sparse_dd_n1000000_m500000_seed0_scaled_trace.json"),
-          "adaptive": os.path.join(ROOT, "tests", "golden",
-                                   "sparse_dd_n1000000_m500000_seed0_scaled_adaptive_trace.json")}
-
 
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -134,22 +130,16 @@ def _peaks():
         return 6400.0, "fallback"
 
 
-def cg_kernel_bytes(nnz_q: int, n: int, launches: int, spmvs: int, cg_steps: int,
-                    w: int, adaptive: bool = False) -> float:
-    """Algorithmic DRAM bytes of the CG kernel, each array counted once per phase.
-
-    w = bytes per value (8 FP64, 4 FP32); indices are int32.
-    Q product (per CG step): (w + 4) B/nnz (value + column) + 4 B/row (row
-    pointer) + w B/row gathered p + w B/row written q.
-    Phase B (per step): reads x, p, q, r, qx and writes x, r, qx: 8w B/row.
-    Phase C (per continued step): reads r, p and writes p: 3w B/row.
-    Adaptive step (per launch): the step test's pass over x, Q x and their
-    saved start after the last step: 4w B/row.
-    r0 is formed by the A' kernel of the previous iteration, not here.
-    """
-    spmv = (w + 4.0) * nnz_q + (4.0 + 2.0 * w) * n
-    return (spmvs * spmv + cg_steps * 8.0 * w * n + max(cg_steps - launches, 0) * 3.0 * w * n
-            + (launches * 4.0 * w * n if adaptive else 0.0))
+def cg_kernel_bytes(nnz_q: int, n: int, cg_steps: int, w: int, k_v: int = 11) -> float:
+    """Algorithmic DRAM bytes of the CG kernel: per CG step, one product with
+    Q, (w + 4) B per stored entry (value + int32 column) and 4 (n + 1) B of
+    row pointers, plus k_v vector streams of n values of w bytes.  k_v = 11
+    counts textbook CG's vector statements with each operand read once and
+    each result written once (q = Q p: read p, write q; x += a p: 3;
+    r -= a q: 3; p = r + b p: 3); k_v = 6 is the fully fused floor (p, q, x
+    and r each once, x and r written back).  Streams the implementation adds
+    (the tracked Q x, the adaptive step's sums) are not counted."""
+    return cg_steps * ((w + 4.0) * nnz_q + 4.0 * (n + 1) + k_v * float(w) * n)
 
 
 def mixed_solve_launches(chunks: int, power_iters: int, eval_freq: int,
@@ -198,56 +188,102 @@ def _profiled_traffic():
         else None
 
 
-def oracle_sample(inst, iters: int, step: str = "adaptive"):
-    """The oracle as it stands: its solve (scaling, set-up, attempts with
-    the relKKT evaluations they contain) stopped after `iters` attempts.
-    Returns (setup_s, per_attempt_s, cores), split at the end of the first
-    attempt; cores = process CPU time / wall time (numpy and scipy pick
-    their own thread counts)."""
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+               "NUMEXPR_NUM_THREADS")
+
+
+def host_cpu():
+    """(logical cores this process may use, CPU model name) of the host."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return cores, model
+
+
+def oracle_full_solve(step: str = "adaptive", max_iter: int = 100_000, inst=None) -> dict:
+    """The oracle as it stands, one complete solve of the bench instance to
+    relKKT <= 1e-4: its Section 4 scaling, set-up (power iteration, omega_0),
+    every attempt, the relKKT evaluations and restarts.  Instance generation
+    is outside the timed region.  max_iter caps the attempts (untimed
+    warm-ups only)."""
     from oracle import pdhcg_oracle as O
+    from paper_2405_16160_b300 import workloads as W
+    if inst is None:
+        inst = W.sparse_dd(WORKLOAD["seed"], n=WORKLOAD["n"], m=WORKLOAD["m"])
     P = O.problem_from_instance(inst)
-    o = O.OracleOptions(tol=WORKLOAD["tol"], max_iter=iters, eval_freq=64, scale=True,
+    o = O.OracleOptions(tol=WORKLOAD["tol"], max_iter=max_iter, eval_freq=64, scale=True,
                         step_mode=O.STEP_ADAPTIVE if step == "adaptive" else O.STEP_FIXED)
-    stamps = []
     c0, t0 = time.process_time(), time.perf_counter()
-    O.solve(P, o, step_hook=lambda st: stamps.append(time.perf_counter()))
-    cores = (time.process_time() - c0) / max(time.perf_counter() - t0, 1e-9)
-    per_it = (stamps[-1] - stamps[0]) / max(len(stamps) - 1, 1)
-    return stamps[0] - t0 - per_it, per_it, round(cores, 1)
+    r = O.solve(P, o)
+    wall = time.perf_counter() - t0
+    return {"s": wall, "cpu_s": time.process_time() - c0, "attempts": r.state.attempts,
+            "iterations": r.iterations, "relkkt": r.kkt.relkkt, "termination": r.termination}
 
 
-def _oracle_iterations(step: str = "adaptive"):
-    """The oracle's own attempts (= iterations with the fixed step) to 1e-4."""
-    with open(GOLDEN[step]) as f:
-        g = json.load(f)
-    return int(g.get("attempts", g["iterations"]))
+def oracle_solve_subprocess(threads: int, step: str) -> dict:
+    """oracle_full_solve in a fresh interpreter whose BLAS/OpenMP pools are
+    limited to `threads` (the variables must be set before numpy loads)."""
+    env = dict(os.environ)
+    for v in THREAD_VARS:
+        env[v] = str(threads)
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-solve",
+                          "--step", step], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_record(step: str) -> dict:
+    """The oracle's time to 1e-4 on the host: one full solve with every core
+    available to its BLAS/OpenMP pools (value) and one with them pinned to
+    a single thread."""
+    cores, model = host_cpu()
+    full = oracle_solve_subprocess(cores, step)
+    one = oracle_solve_subprocess(1, step)
+    return {"value": full["s"], "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"one full oracle solve of the same instance to relKKT <= 1e-4 (Section 4 "
+                      f"scaling, set-up, {full['attempts']} attempts, final relKKT "
+                      f"{full['relkkt']:.2e}), numpy/scipy with BLAS/OpenMP threads = {cores}",
+            "cpu_model": model, "process_cpu_s": full["cpu_s"],
+            "single_thread_s": one["s"], "single_thread_attempts": one["attempts"],
+            "single_thread_note": "the same full solve with every BLAS/OpenMP pool limited to "
+                                  "one thread"}
 
 
 def run_reference(args):
+    """The CPU FP64 oracle, as it stands, on the bench instance: every timed
+    step is one complete solve to relKKT <= 1e-4 on the host's cores; the
+    untimed warm-up steps run the same solve capped at 8 attempts (imports,
+    scipy set-up, first touch of the instance)."""
     ws, rank = _dist()
     if rank != 0:
         return 0
     from paper_2405_16160_b300 import workloads as W
     inst = W.sparse_dd(WORKLOAD["seed"], n=WORKLOAD["n"], m=WORKLOAD["m"])
-    n_iter = _oracle_iterations(args.step)
-    sample_iters = 8
-    vals, cores = [], []
-    for s in range(args.warmup + args.steps):
-        setup, per_it, c = oracle_sample(inst, sample_iters, args.step)
-        if s >= args.warmup:
-            vals.append(setup + per_it * n_iter)
-            cores.append(c)
-    v = statistics.mean(vals)
-    sample = (f"oracle scaling + set-up + {sample_iters} attempts per step on the full "
-              f"instance, scaled by the oracle's own attempt count to 1e-4 ({n_iter}, "
-              f"{args.step} step)")
+    cores, model = host_cpu()
+    for _ in range(args.warmup):
+        oracle_full_solve(args.step, max_iter=8, inst=inst)
+    runs = [oracle_full_solve(args.step, inst=inst) for _ in range(args.steps)]
+    v = statistics.mean(r["s"] for r in runs)
+    sample = (f"one full oracle solve of the instance to relKKT <= 1e-4 per step ("
+              f"{runs[-1]['attempts']} attempts, final relKKT {runs[-1]['relkkt']:.2e}); "
+              f"warm-up steps capped at 8 attempts")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": dict(WORKLOAD, step=args.step),
-        "cpu_baseline": {"value": v, "unit": "s", "cores": max(cores), "kind": "oracle",
-                         "sample": sample},
+        "data": "synthetic", "config": dict(WORKLOAD, step=args.step, precision="fp64 (oracle)"),
+        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+                         "sample": sample, "cpu_model": model,
+                         "process_cpu_s": statistics.mean(r["cpu_s"] for r in runs)},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
     return 0
@@ -266,6 +302,54 @@ def _timed_solves(solver, steps, stream, **opts):
         times.append(e0.elapsed_time(e1) / 1e3)
         infos.append(info)
     return infos, times
+
+
+LARGEST = {"workload": "largest single QP: n=1e7, m=5e6, Q ~5 nnz/row diagonally dominant, A 8 "
+                       "nnz/row with Zipf(1.1) column popularity, Section 4 scaling",
+           "n": 10_000_000, "m": 5_000_000, "seed": 0, "attempts": 256}
+
+
+def largest_qp_record(stream, step: int, steps: int = 2) -> dict:
+    """The largest single QP (n = 1e7, m = 5e6) on the same GPU: the first
+    LARGEST['attempts'] attempts of its solve, timed in mixed precision and in
+    plain FP64 (ms per attempt and their ratio), and the CG kernel's
+    roofline over a kernel-timed run of the same attempts.  A full solve of
+    this instance takes about 40 s (bench.py --workload zipf_dd)."""
+    import torch
+
+    from paper_2405_16160_b300 import _lib as L
+    from paper_2405_16160_b300 import workloads as W
+    from paper_2405_16160_b300.solver import QPSolver
+
+    inst = W.zipf_dd(LARGEST["seed"], n=LARGEST["n"], m=LARGEST["m"])
+    cap = LARGEST["attempts"]
+    out = {"workload": LARGEST["workload"], "attempts_timed": cap}
+    with QPSolver(inst, scale=True) as s:
+        runs = {}
+        for name, prec in (("mixed", L.PREC_MIXED), ("fp64", L.PREC_FP64)):
+            opts = dict(tol=1e-4, precision=prec, step_mode=step, max_iter=cap)
+            s.solve(**opts)  # warm-up: graph capture
+            infos, times = _timed_solves(s, steps, stream, **opts)
+            runs[name] = statistics.mean(times)
+            out[f"{name}_ms_per_attempt"] = runs[name] * 1e3 / infos[-1]["attempts"]
+            out[f"{name}_relkkt_after"] = infos[-1]["relkkt"]
+        out["fp64_over_mixed"] = runs["fp64"] / runs["mixed"]
+        kinfos, _ = _timed_solves(s, 1, stream, tol=1e-4, precision=L.PREC_MIXED, step_mode=step,
+                                  max_iter=cap, kernel_timing=1)
+    ki = kinfos[-1]
+    ks = ki["cg_kernel_ms"] / 1e3
+    peak, peak_kind = _peaks()
+    if ks > 0:
+        achieved = cg_kernel_bytes(inst.nnz_Q, inst.n, ki["cg_kernel_spmvs"], 4) / ks / 1e9
+        out["roofline"] = {"kernel": "k_cg<float>", "bound": "hbm", "achieved": achieved,
+                           "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                           "peak_kind": peak_kind,
+                           "avg_launch_us": ks / max(ki["cg_kernel_launches"], 1) * 1e6,
+                           "cg_steps_per_launch": ki["cg_kernel_spmvs"]
+                           / max(ki["cg_kernel_launches"], 1)}
+    del inst
+    torch.cuda.synchronize()
+    return out
 
 
 def run_ours(args):
@@ -352,14 +436,16 @@ def run_ours(args):
         if s > 0:
             e2e_times.append(time.perf_counter() - t0)
     e2e = _max_over_ranks(statistics.mean(e2e_times), ws)
+    largest = None if args.no_largest else largest_qp_record(stream, step)
 
     if rank != 0:
         return 0
     info = infos[-1]
     peak, peak_kind = _peaks()
-    bytes_total = sum(cg_kernel_bytes(inst.nnz_Q, inst.n, i["cg_kernel_launches"],
-                                      i["cg_kernel_spmvs"], i["cg_steps"], 4,
-                                      adaptive=args.step == "adaptive") for i in kinfos)
+    bytes_total = sum(cg_kernel_bytes(inst.nnz_Q, inst.n, i["cg_kernel_spmvs"], 4)
+                      for i in kinfos)
+    bytes_floor = sum(cg_kernel_bytes(inst.nnz_Q, inst.n, i["cg_kernel_spmvs"], 4, k_v=6)
+                      for i in kinfos)
     launches = sum(i["cg_kernel_launches"] for i in kinfos)
     kernel_s = sum(i["cg_kernel_ms"] for i in kinfos) / 1e3
     achieved = bytes_total / kernel_s / 1e9 if kernel_s > 0 else None
@@ -376,12 +462,7 @@ def run_ours(args):
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        setup_s, per_it, cores = oracle_sample(inst, 64, args.step)
-        n_iter = _oracle_iterations(args.step)
-        cpu = {"value": setup_s + per_it * n_iter, "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": f"oracle scaling + set-up + 64 PDHCG attempts of the same instance "
-                         f"({setup_s + 64 * per_it:.1f} s), scaled by the oracle's attempt "
-                         f"count to 1e-4 ({n_iter}, {args.step} step)"}
+        cpu = cpu_baseline_record(args.step)
     out = {
         "metric": METRIC, "value": per_solve, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": False,
@@ -409,6 +490,10 @@ def run_ours(args):
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_total / max(launches, 1),
+                     "bytes_note": "per CG step (w+4) nnz(Q) + 4(n+1) + 11 n w (w = 4): the "
+                                   "matrix stream and textbook CG's vector statements",
+                     "frac_fused_floor": (bytes_floor / kernel_s / 1e9 / peak)
+                     if kernel_s > 0 else None,
                      "cg_steps_per_launch": steps_per_launch,
                      "traffic_note": "ncu DRAM read+write of a one-CG-step k_cg launch "
                                      "(profiles/k_cg_traffic.json) x CG steps per launch",
@@ -424,6 +509,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "gpu_launches": gpu_launches,
         "clocks": clocks.summary(),
+        "largest_qp": largest,
     }
     print(json.dumps(out), flush=True)
     return 0
@@ -654,8 +740,7 @@ def run_zipf_bench(args):
     info, oi = infos[-1], oinfo[-1]
     peak, peak_kind = _peaks()
     ki = kinfos[-1]
-    kbytes = cg_kernel_bytes(inst.nnz_Q, inst.n, ki["cg_kernel_launches"], ki["cg_kernel_spmvs"],
-                             ki["cg_steps"], 4, adaptive=args.step == "adaptive")
+    kbytes = cg_kernel_bytes(inst.nnz_Q, inst.n, ki["cg_kernel_spmvs"], 4)
     ks = ki["cg_kernel_ms"] / 1e3
     achieved = kbytes / ks / 1e9 if ks > 0 else None
     ceiling = gather_ceiling(inst.nnz_Q, inst.n)
@@ -805,12 +890,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-largest", action="store_true",
+                    help="skip the largest-QP (n = 1e7) per-attempt record of the default run")
     ap.add_argument("--workload", choices=["sparse_dd", "portfolio_batch", "learned_warm_start",
                                            "zipf_dd"], default="sparse_dd")
     ap.add_argument("--train-epochs", type=int, default=30)
     ap.add_argument("--step", choices=["adaptive", "fixed"], default="adaptive",
                     help="step-size rule (Section 4 adaptive, or eta = 1/(2||A||_2))")
+    ap.add_argument("--oracle-solve", action="store_true",
+                    help="internal: one full oracle solve of the bench instance, as JSON")
     args = ap.parse_args()
+    if args.oracle_solve:
+        print(json.dumps(oracle_full_solve(args.step)), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "portfolio_batch":

@@ -92,7 +92,9 @@ struct alignas(128) GridBarrier {
   unsigned int count;
   unsigned int pad0[31];
   unsigned int gen;
-  unsigned int pad1[31];
+  unsigned int pad1;
+  double total;  // grid_sync_sum: the reduced value, published with the generation
+  unsigned int pad2[28];
 };
 
 // ------------------------------------------------------------------ helpers
@@ -352,18 +354,27 @@ __device__ __forceinline__ double block_total_dot(const double* p, int n, AccF) 
   return v;
 }
 
-// The total of block_dot_store partials, broadcast to every thread of the block.
-template <class A, int RB = 4>
-__device__ __forceinline__ double block_all_reduce(const double* p, int n) {
-  return block_total_dot<RB>(p, n, A());
+
+// Sense-free generation barrier over all blocks of a co-resident grid.  Each
+// block's thread 0 holds the barrier's generation in `gen` (grid_gen at the
+// kernel's start, then advanced by every grid_sync), so arriving costs one
+// atomic round trip: fence, count, and either release (the last arrival:
+// reset the count, publish the next generation) or poll until the
+// generation moves.  Every wait is bounded: after opt.barrier_timeout_ms
+// (globaltimer) or 2^27 polls the block records kErrBarrierTimeout and the
+// kernel winds down; a block that sees the error flag stops waiting too.
+// Returns false on error.
+__device__ __forceinline__ unsigned int grid_gen(GridBarrier* bar) {
+  unsigned int g = 0u;
+  if (threadIdx.x == 0) {
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(bar->gen);
+    g = gen.load(cuda::memory_order_acquire);
+  }
+  return g;
 }
 
-// Sense-free generation barrier over all blocks of a co-resident grid.  Every
-// wait is bounded: after opt.barrier_timeout_ms (globaltimer) or 2^27 polls the
-// block records kErrBarrierTimeout and the kernel winds down; a block that
-// sees the error flag stops waiting too.  Returns false on error.
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int timeout_ms,
-                                          bool never_release) {
+                                          bool never_release, unsigned int& gen_local) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -371,12 +382,12 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int ti
     cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(bar->count);
     cuda::atomic_ref<int, cuda::thread_scope_device> err(st->err);
     int ok = 1;
-    const unsigned int g = gen.load(cuda::memory_order_acquire);
+    const unsigned int g = gen_local;
     __threadfence();
     const unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
     if (arrived == gridDim.x - 1 && !never_release) {
       cnt.store(0u, cuda::memory_order_relaxed);
-      gen.fetch_add(1u, cuda::memory_order_release);
+      gen.store(g + 1u, cuda::memory_order_release);
     } else {
       const unsigned long long t0 = global_ns();
       const unsigned long long limit = (unsigned long long)timeout_ms * 1000000ull;
@@ -393,11 +404,81 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int ti
             break;
           }
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
+    gen_local = g + 1u;
     __threadfence();
     s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// A grid barrier that also reduces one partial per block (block_dot_store
+// layout) to a total every thread of every block receives.  The block that
+// arrives last sums the partials in index order (block_total_dot, so the
+// value does not depend on which block arrives last) and
+// publishes the total in the barrier's generation line before releasing it;
+// the others read that one value after the release.  One block reads the
+// partials instead of every block, so the L2 lines holding them are not
+// read by the whole grid at once.  Waits are bounded as in grid_sync.
+//
+// on_total(total) runs in thread 0 of every block once the total is known,
+// before the block's closing barrier: the place to derive the method's FP64
+// scalars once per block and share them through shared memory (the FP64
+// pipe of B300 runs at 1/58 of FP32, so a division or square root evaluated
+// by every thread of a persistent grid costs microseconds).
+template <class A, class F>
+__device__ __forceinline__ bool grid_sync_sum(GridBarrier* bar, DevState* st, int timeout_ms,
+                                              bool never_release, unsigned int& gen_local,
+                                              const double* part, F&& on_total) {
+  __shared__ int s_ok, s_last;
+  __syncthreads();
+  cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(bar->gen);
+  cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(bar->count);
+  cuda::atomic_ref<double, cuda::thread_scope_device> tot(bar->total);
+  const unsigned int g = gen_local;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
+    s_last = arrived == gridDim.x - 1 && !never_release;
+    s_ok = 1;
+  }
+  __syncthreads();
+  if (s_last) {  // the whole last block (the branch is uniform)
+    __threadfence();
+    const double t = block_total_dot<1>(part, gridDim.x, A());
+    if (threadIdx.x == 0) {
+      tot.store(t, cuda::memory_order_relaxed);
+      cnt.store(0u, cuda::memory_order_relaxed);
+      gen.store(g + 1u, cuda::memory_order_release);
+      on_total(t);
+    }
+  } else if (threadIdx.x == 0) {
+    cuda::atomic_ref<int, cuda::thread_scope_device> err(st->err);
+    const unsigned long long t0 = global_ns();
+    const unsigned long long limit = (unsigned long long)timeout_ms * 1000000ull;
+    unsigned int polls = 0;
+    while (gen.load(cuda::memory_order_acquire) == g) {
+      if (err.load(cuda::memory_order_relaxed) != 0) {
+        s_ok = 0;
+        break;
+      }
+      if ((++polls & 255u) == 0u) {
+        if (global_ns() - t0 > limit || polls > (1u << 27)) {
+          err.fetch_or(kErrBarrierTimeout, cuda::memory_order_relaxed);
+          s_ok = 0;
+          break;
+        }
+      }
+      __nanosleep(32);
+    }
+    if (s_ok) on_total(tot.load(cuda::memory_order_relaxed));
+  }
+  if (threadIdx.x == 0) {
+    gen_local = g + 1u;
+    __threadfence();
   }
   __syncthreads();
   return s_ok != 0;
@@ -462,10 +543,13 @@ __device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f) {
   const int sub = lane & (G - 1);
   const long long gw = grid_tid() >> 5;
   const long long nw = grid_threads() >> 5;
-  for (long long base = gw * kRowsPerWarp; base < M.rows; base += nw * kRowsPerWarp) {
-    const int i = int(base) + lane / G;
+  // warp gw takes the contiguous rows [r0, r1): every warp gets the same
+  // number of rows to within one, so no SM is left with a larger share
+  const int r0 = int((long long)M.rows * gw / nw), r1 = int((long long)M.rows * (gw + 1) / nw);
+  for (int base = r0; base < r1; base += kRowsPerWarp) {
+    const int i = base + lane / G;
     T s = T(0);
-    bool own = i < M.rows;
+    bool own = i < r1;
     if (own) {
       const int b = __ldg(M.rowptr + i), e = __ldg(M.rowptr + i + 1);
       if (e - b > kLongRow) {
@@ -595,15 +679,21 @@ __device__ __forceinline__ void store_and_finish_dot(A acc, double* part, unsign
 // Inexact CG on (Q + I/tau) x = x^k/tau - c - A'y^k warm-started at x^k.  Its
 // initial residual simplifies to r0 = -(Q x^k + c + A'y^k); the kernel that
 // produces A'y^k (k_atv, or k_prepare after a set-up, evaluation or restart)
-// also forms r0 = p0 and r0'r0 (one value, r0r0) from a tracked qx = Q x.  Phases per CG step:
-//   [A] q = Qp + p/tau, p'q
-//   [B] x += a p, qx += a (q - p/tau), r -= a q, r'r
-//   [C] p = r + b p   (only when CG continues)
-// so each step costs one product with Q.  With the adaptive step size the
-// iteration counters wait for the accept/reject decision that k_dual's last
-// block takes.  alpha, beta, the stop test and all dot products are
-// FP64-accurate for both value types.  part holds
-// 2 * gridDim.x doubles.
+// also forms r0 = p0 and r0'r0 (one value, r0r0) from a tracked qx = Q x.
+// Two grid barriers per CG step:
+//   [A] gather r: Q r.  First step (p = r): Qp = Q r.  Later steps:
+//       Qp = Q r + beta Qp and p = r + beta p, formed row by row in the
+//       product's epilogue; then q = Qp + p/tau and p'q.          | barrier
+//   [B] x += a p, qx += a Qp, r -= a q, r'r.                       | barrier
+// The product of a continued step reads r, which is complete after [B]'s
+// barrier, instead of the new p, which would need a separate pass and a
+// third barrier; Q p = Q r + beta Q p_old is the same vector in exact
+// arithmetic (textbook CG's p = r + beta p_old, multiplied by Q), so alpha,
+// beta and the iterates are those of textbook CG up to rounding.  Each step
+// costs one product with Q.  With the adaptive step size the iteration
+// counters wait for the accept/reject decision that k_dual's last block
+// takes.  alpha, beta, the stop test and all dot products are FP64-accurate
+// for both value types.  part holds 2 * gridDim.x doubles.
 // Resident CG blocks of 512 threads per SM (register budget per thread =
 // 65536 / (512 * blocks)).  Four FP32 blocks would need 32 registers and
 // spill; three measured faster.
@@ -645,51 +735,79 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     return;
   }
   // Every read of st happens before the first barrier; block 0 writes the
-  // counters only after the last one.
-  const double tau = st->tau;
-  const T inv_tau = T(1.0 / tau);
+  // counters only after the last one.  The FP64 scalars (tau, eps, r'r,
+  // alpha, beta, the stop test) live in thread 0 of each block, which shares
+  // what the other threads need through shared memory.
   const int mode = st->opt.cg_mode, nfix = st->opt.cg_fixed_n, cgmax = st->opt.cg_max;
   const bool adaptive_step = st->opt.step_mode == kStepAdaptive;
   const int tmo = st->opt.barrier_timeout_ms;
   bool never_release = (st->opt.debug_flags & kDebugBarrierNeverReleases) != 0u;
-  const double eps =
-      mode == kCgAdaptive ? st->eps + st->opt.cg_eps_factor * st->relkkt_last : st->eps;
+  __shared__ double s_tau, s_eps, s_rr;  // thread 0's
+  __shared__ T s_inv_tau, s_coef;        // 1/tau; alpha, then beta
+  __shared__ int s_flag;                 // skip / numerical error / stop
+  if (threadIdx.x == 0) {
+    s_tau = st->tau;
+    s_eps = mode == kCgAdaptive ? st->eps + st->opt.cg_eps_factor * st->relkkt_last : st->eps;
+    s_rr = __ldcg(r0r0);
+    s_inv_tau = T(1.0 / s_tau);
+    s_flag = (mode == kCgFixed && nfix <= 0) || s_rr == 0.0;
+  }
+  __syncthreads();
+  const T inv_tau = s_inv_tau;
+  const bool skip = s_flag != 0;
   double* part_rr = part;
   double* part_pq = part + gridDim.x;
   const long long t0 = grid_tid(), nt = grid_threads();
-  double rr = __ldcg(r0r0);
+  unsigned int gen = grid_gen(bar);
+  // adaptive step: the primal move's sums of the latest step, per thread
+  A mv[2];
+  const bool move_sums = ss.part != nullptr;
 
   int steps = 0;
   bool numerr = false;
-  const bool skip = (mode == kCgFixed && nfix <= 0) || rr == 0.0;
+  T beta = T(0);  // 0 in the first step, where p = r
   while (!skip) {
     if (LQ.nlong > 0) {
       // long rows of Q: segment sums, then per-row totals, before the row pass
-      long_segments(Q, p, LQ, qseg);
-      if (!grid_sync(bar, st, tmo, never_release)) return;
+      long_segments(Q, r, LQ, qseg);
+      if (!grid_sync(bar, st, tmo, never_release, gen)) return;
       never_release = false;
       long_finish(LQ, qseg, qlong);
-      if (!grid_sync(bar, st, tmo, false)) return;
+      if (!grid_sync(bar, st, tmo, false, gen)) return;
     }
     A acc;
-    spmv_rows<G>(Q, p, [&](int i, T s, bool lead) {
+    const bool first = steps == 0;
+    spmv_rows<G>(Q, r, [&](int i, T s, bool lead) {
       if (lead) {
-        const T pi = p[i];
-        const T qi = s + pi * inv_tau;
-        q[i] = s;  // Q p itself; q = Q p + p/tau is re-formed from it below
-        acc.add_prod(pi, qi);
+        T qpi, pi;
+        if (first) {  // p = r = r0: Q p is the product itself
+          qpi = s;
+          pi = p[i];
+        } else {      // Q p = Q r + beta Q p_old, p = r + beta p_old
+          qpi = add_rn(s, mul_rn(beta, q[i]));
+          pi = add_rn(r[i], mul_rn(beta, p[i]));
+          p[i] = pi;
+        }
+        q[i] = qpi;  // Q p itself; q = Q p + p/tau is re-formed from it below
+        acc.add_prod(pi, qpi + pi * inv_tau);
       }
     });
     block_dot_store(acc, part_pq + blockIdx.x);
-    if (!grid_sync(bar, st, tmo, never_release)) return;
+    if (!grid_sync_sum<A>(bar, st, tmo, never_release, gen, part_pq, [&](double pq) {
+          const bool bad = !(pq > 0.0) || !isfinite(pq);
+          s_flag = bad;
+          s_coef = bad ? T(0) : T(s_rr / pq);
+        }))
+      return;
     never_release = false;
-    const double pq = block_all_reduce<A, 1>(part_pq, gridDim.x);
-    if (!(pq > 0.0) || !isfinite(pq)) {
+    if (s_flag) {
       numerr = true;
       break;
     }
-    const T alpha = T(rr / pq);
+    const T alpha = s_coef;
     acc = A();
+    mv[0] = A();
+    mv[1] = A();
     // x += alpha p, r -= alpha q with a rounded product then a rounded sum,
     // exactly as the elementwise vector statements of textbook CG; qx follows
     // x through the stored Q p (recovering it as q - p/tau would cancel badly
@@ -707,6 +825,8 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
       P* rp = reinterpret_cast<P*>(r);
       const P* pp = reinterpret_cast<const P*>(p);
       const P* qp = reinterpret_cast<const P*>(q);
+      const P* xsp = reinterpret_cast<const P*>(ss.x_save);
+      const P* qxsp = reinterpret_cast<const P*>(ss.qx_save);
       for (long long i = t0; i < np; i += nt) {
         const P pv = pp[i], qv = qp[i], xv = xp[i], qxv = qxp[i], rv = rp[i];
         P xo, qxo, ro;
@@ -721,43 +841,51 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
         xp[i] = xo;
         qxp[i] = qxo;
         rp[i] = ro;
+        if (move_sums) {  // ||x+ - x||^2 and (x+ - x)'(Q x+ - Q x) from the attempt's start
+          const P xs = xsp[i], qxs = qxsp[i];
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const T dx = xo.v[j] - xs.v[j];
+            mv[0].add_prod(dx, dx);
+            mv[1].add_prod(dx, qxo.v[j] - qxs.v[j]);
+          }
+        }
       }
       for (long long i = np * N + t0; i < n; i += nt) {
         const T pi = p[i], qpi = q[i];
         const T qi = qpi + pi * inv_tau;
-        x[i] = add_rn(x[i], mul_rn(alpha, pi));
-        qx[i] = add_rn(qx[i], mul_rn(alpha, qpi));
+        const T xn = add_rn(x[i], mul_rn(alpha, pi));
+        const T qxn = add_rn(qx[i], mul_rn(alpha, qpi));
+        x[i] = xn;
+        qx[i] = qxn;
         const T ri = sub_rn(r[i], mul_rn(alpha, qi));
         r[i] = ri;
         acc.add_prod(ri, ri);
+        if (move_sums) {
+          const T dx = xn - ss.x_save[i];
+          mv[0].add_prod(dx, dx);
+          mv[1].add_prod(dx, qxn - ss.qx_save[i]);
+        }
       }
     }
     block_dot_store(acc, part_rr + blockIdx.x);
-    if (!grid_sync(bar, st, tmo, false)) return;
-    const double rr_new = block_all_reduce<A, 1>(part_rr, gridDim.x);
+    if (!grid_sync_sum<A>(bar, st, tmo, false, gen, part_rr, [&](double rr_new) {
+          const int done_steps = steps + 1;
+          const bool stop = mode == kCgFixed
+                                ? done_steps >= nfix
+                                : (s_tau * sqrt(rr_new) <= s_eps || done_steps >= cgmax);
+          s_flag = stop || rr_new == 0.0;
+          s_coef = T(rr_new / s_rr);
+          s_rr = rr_new;
+        }))
+      return;
     ++steps;
-    const bool stop = mode == kCgFixed ? steps >= nfix : (tau * sqrt(rr_new) <= eps || steps >= cgmax);
-    if (stop || rr_new == 0.0) break;
-    const T beta = T(rr_new / rr);
-    rr = rr_new;
-    {
-      using P = Pack16<T>;
-      constexpr int N = P::N;
-      const long long np = kSplit<T> ? n / N : 0;
-      P* pp = reinterpret_cast<P*>(p);
-      const P* rp = reinterpret_cast<const P*>(r);
-      for (long long i = t0; i < np; i += nt) {
-        const P rv = rp[i];
-        P pv = pp[i];
-#pragma unroll
-        for (int j = 0; j < N; ++j) pv.v[j] = add_rn(rv.v[j], mul_rn(beta, pv.v[j]));
-        pp[i] = pv;
-      }
-      for (long long i = np * N + t0; i < n; i += nt) p[i] = add_rn(r[i], mul_rn(beta, p[i]));
-    }
-    if (!grid_sync(bar, st, tmo, false)) return;
+    if (s_flag) break;
+    beta = s_coef;
   }
-  if (ss.part && !numerr) step_start_sums<T, A>(ss, x, qx, n);
+  // the sums of the last step are the attempt's primal move (a launch with no
+  // step leaves x = x_save: both sums are zero)
+  if (move_sums && !numerr) block_reduce_ms<0, 2, T>(nullptr, mv, ss.part + 2 * size_t(blockIdx.x));
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (numerr) {
       st->done = kDoneNumerical;
@@ -769,9 +897,9 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
       st->last_cg = steps;
       st->spmv_total += steps;
       if (adaptive_step) {
-        st->eps_try = eps;  // kept if the attempt is accepted (step_decide)
+        st->eps_try = s_eps;  // kept if the attempt is accepted (step_decide)
       } else {
-        st->eps = eps;
+        st->eps = s_eps;
         st->k_total += 1;
         st->j += 1;
       }
@@ -804,29 +932,39 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     return;
   }
   // Every read of st happens before the first barrier; block 0 writes the
-  // counters only after the last one.
-  const double tau = st->tau;
-  const T inv_tau = T(1.0 / tau);
+  // counters only after the last one.  The FP64 scalars live in thread 0 of
+  // each block, which shares 1/tau, 1/alpha and the flags through shared
+  // memory (see grid_sync_sum).
   const int mode = st->opt.cg_mode, nfix = st->opt.cg_fixed_n, cgmax = st->opt.cg_max;
   const bool adaptive_step = st->opt.step_mode == kStepAdaptive;
   const int tmo = st->opt.barrier_timeout_ms;
   bool never_release = (st->opt.debug_flags & kDebugBarrierNeverReleases) != 0u;
-  const double eps =
-      mode == kCgAdaptive ? st->eps + st->opt.cg_eps_factor * st->relkkt_last : st->eps;
+  __shared__ double s_eps, s_rr, s_ss;  // thread 0's
+  __shared__ T s_inv_tau, s_inv_alpha;
+  __shared__ int s_flag;  // skip / numerical error / stop
+  if (threadIdx.x == 0) {
+    s_eps = mode == kCgAdaptive ? st->eps + st->opt.cg_eps_factor * st->relkkt_last : st->eps;
+    s_rr = __ldcg(r0r0);
+    s_inv_tau = T(1.0 / st->tau);
+    s_flag = (mode == kCgFixed && nfix <= 0) || s_rr == 0.0;
+  }
+  __syncthreads();
+  const T inv_tau = s_inv_tau;
+  const bool skip = s_flag != 0;
   double* part_a = part;
   double* part_b = part + gridDim.x;
   const long long t0 = grid_tid(), nt = grid_threads();
-  const double rr = __ldcg(r0r0);
   int steps = 0, products = 0;
   bool numerr = false, failed = false;
+  unsigned int gen = grid_gen(bar);
   // Q p over every row (long rows first), f(i, (Q p)_i) for each row
   auto qprod = [&](auto&& f) {
     if (LQ.nlong > 0) {
       long_segments(Q, p, LQ, qseg);
-      if (!grid_sync(bar, st, tmo, never_release)) return false;
+      if (!grid_sync(bar, st, tmo, never_release, gen)) return false;
       never_release = false;
       long_finish(LQ, qseg, qlong);
-      if (!grid_sync(bar, st, tmo, false)) return false;
+      if (!grid_sync(bar, st, tmo, false, gen)) return false;
     }
     spmv_rows<G>(Q, p, [&](int i, T s, bool lead) {
       if (lead) f(i, s);
@@ -834,9 +972,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     ++products;
     return true;
   };
-  const bool skip = (mode == kCgFixed && nfix <= 0) || rr == 0.0;
   if (!skip) {
-    double alpha = 0.0;
     {
       A acc;
       if (!qprod([&](int i, T s) {
@@ -845,14 +981,16 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
           }))
         return;
       block_dot_store(acc, part_a + blockIdx.x);
-      if (!grid_sync(bar, st, tmo, never_release)) return;
+      if (!grid_sync_sum<A>(bar, st, tmo, never_release, gen, part_a, [&](double gmg) {
+            s_flag = !(gmg > 0.0) || !isfinite(gmg);
+            s_inv_alpha = T(s_rr / gmg);  // 1/alpha, alpha = g'M g / g'g
+          }))
+        return;
       never_release = false;
-      const double gmg = block_all_reduce<A, 1>(part_a, gridDim.x);
-      if (!(gmg > 0.0) || !isfinite(gmg)) numerr = true;
-      alpha = gmg / rr;
+      numerr = s_flag != 0;
     }
     while (!numerr && !failed) {
-      const T inv_alpha = T(1.0 / alpha);
+      const T inv_alpha = s_inv_alpha;
       A acc;
       for (long long i = t0; i < n; i += nt) {
         const T xi = x[i];
@@ -863,8 +1001,8 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
         acc.add_prod(si, si);
       }
       block_dot_store(acc, part_a + blockIdx.x);
-      if (!grid_sync(bar, st, tmo, false)) return;
-      const double ss = block_all_reduce<A, 1>(part_a, gridDim.x);
+      if (!grid_sync_sum<A>(bar, st, tmo, false, gen, part_a, [&](double t) { s_ss = t; }))
+        return;
       A acc2;
       if (!qprod([&](int i, T s) {
             const T si = p[i];
@@ -875,16 +1013,27 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
           }))
         return;
       block_dot_store(acc2, part_b + blockIdx.x);
-      if (!grid_sync(bar, st, tmo, false)) return;
-      const double sw = block_all_reduce<A, 1>(part_b, gridDim.x);
+      // flag: 0 continue, 1 stop, 2 numerical error
+      if (!grid_sync_sum<A>(bar, st, tmo, false, gen, part_b, [&](double sw) {
+            const int done_steps = steps + 1;
+            const bool stop = mode == kCgFixed ? done_steps >= nfix
+                                               : (sqrt(s_ss) <= s_eps || done_steps >= cgmax);
+            if (stop || s_ss == 0.0) {
+              s_flag = 1;
+            } else if (!(sw > 0.0) || !isfinite(sw)) {
+              s_flag = 2;
+            } else {
+              s_flag = 0;
+              s_inv_alpha = T(s_ss / sw);  // 1/alpha, alpha = s'w / s's
+            }
+          }))
+        return;
       ++steps;
-      const bool stop = mode == kCgFixed ? steps >= nfix : (sqrt(ss) <= eps || steps >= cgmax);
-      if (stop || ss == 0.0) break;
-      if (!(sw > 0.0) || !isfinite(sw)) {
+      if (s_flag == 1) break;
+      if (s_flag == 2) {
         numerr = true;
         break;
       }
-      alpha = sw / ss;
     }
   }
   if (sstart.part && !numerr) step_start_sums<T, A>(sstart, x, qx, n);
@@ -899,9 +1048,9 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
       st->last_cg = steps;
       st->spmv_total += products;
       if (adaptive_step) {
-        st->eps_try = eps;
+        st->eps_try = s_eps;
       } else {
-        st->eps = eps;
+        st->eps = s_eps;
         st->k_total += 1;
         st->j += 1;
       }
@@ -969,8 +1118,15 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
                                                  T* y_avg, T* ya_lo, DevState* st,
                                                  StepTrial<T> tr) {
   if (!st->iter_active) return;
-  const T sigma = T(st->sigma);
-  const T inv_j = T(1.0 / (double)st->j);
+  // FP64 scalars once per block (thread 0), not once per thread
+  __shared__ T s_sigma, s_inv_j;
+  if (threadIdx.x == 0) {
+    s_sigma = T(st->sigma);
+    s_inv_j = T(1.0 / (double)st->j);
+  }
+  __syncthreads();
+  const T sigma = s_sigma;
+  const T inv_j = s_inv_j;
   const bool first = st->j == 1;
   const int m_eq = st->opt.m_eq;
   if (tr.y_new) {
@@ -1076,7 +1232,10 @@ __global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSm<T>)
     store_and_finish_dot(acc, part_r0, ticket);
     return;
   }
-  const T w = adaptive ? T(st->avg_w) : T(1.0 / (double)st->j);
+  __shared__ T s_w;  // the average's weight, once per block
+  if (threadIdx.x == 0) s_w = adaptive ? T(st->avg_w) : T(1.0 / (double)st->j);
+  __syncthreads();
+  const T w = s_w;
   spmv_rows<G>(At, y, [&](int i, T s, bool lead) {
     if (lead) {
       aty[i] = s;
@@ -1104,7 +1263,10 @@ __global__ void __launch_bounds__(kBlock) k_commit_m(T* y, T* y_lo, const T* __r
                                                      const T* __restrict__ ax_new, T* y_avg,
                                                      T* ya_lo, int m, const DevState* st) {
   if (!st->iter_active || !st->accepted) return;
-  const T w = T(st->avg_w);
+  __shared__ T s_w;  // the step weight, converted once per block
+  if (threadIdx.x == 0) s_w = T(st->avg_w);
+  __syncthreads();
+  const T w = s_w;
   const bool first = st->j == 1;
   for (long long i = grid_tid(); i < m; i += grid_threads()) {
     ax[i] = ax_new[i];

@@ -1,4 +1,5 @@
-"""qp_norm_A_static: the allocation-free ||A||_2 estimate, checked against qp_norm_A.
+"""qp_norm_A_static: the allocation-free ||A||_2 estimate, checked against
+qp_norm_A and against the CPU oracle's power iteration.
 
 Callers that cannot allocate device memory (a control loop held to a memory
 budget fixed at start-up, code running while another framework owns all
@@ -12,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import pdhcg_oracle as O
 from paper_2405_16160_b300 import _lib as L
 from paper_2405_16160_b300 import workloads as W
 from paper_2405_16160_b300.solver import QPSolver
@@ -58,6 +60,9 @@ def test_static_norm_matches_handle_norm_on_two_calls(torch_cuda):
         with QPSolver(inst) as s:
             ref = s.norm_A(30)
         assert got == pytest.approx(ref, rel=1e-12)
+        # the same 30 power iterations from the normalised all-ones vector, in
+        # FP64 on the CPU (Section 3.2's ||A||_2 of the step size)
+        assert got == pytest.approx(O.spectral_norm(inst.scipy_A().tocsr(), 30), rel=1e-12)
 
 
 def test_static_norm_rejects_sizes_beyond_its_scratch(torch_cuda):
