@@ -325,6 +325,7 @@ def largest_qp_record(stream, step: int, steps: int = 2) -> dict:
     cap = LARGEST["attempts"]
     out = {"workload": LARGEST["workload"], "attempts_timed": cap}
     with QPSolver(inst, scale=True) as s:
+        out["tuned_shapes"] = s.tune(reps=5)
         runs = {}
         for name, prec in (("mixed", L.PREC_MIXED), ("fp64", L.PREC_FP64)):
             opts = dict(tol=1e-4, precision=prec, step_mode=step, max_iter=cap)
@@ -375,8 +376,16 @@ def run_ours(args):
     mixed = dict(tol=tol, precision=L.PREC_MIXED, step_mode=step)
     fp64 = dict(tol=tol, precision=L.PREC_FP64, step_mode=step)
 
-    # ---- device-resident solves (value): mixed precision, CUDA-graph replay
+    # ---- device-resident solves (value): mixed precision, CUDA-graph replay,
+    # with the row kernels' launch shapes picked by qp_tune (the solve with
+    # the mean-row-length rule's shapes is timed first, for the comparison)
     solver = QPSolver(inst, scale=True)
+    for _ in range(args.warmup):
+        solver.solve(**mixed)
+    _, rule_times = _timed_solves(solver, max(2, args.steps // 2), stream, **mixed)
+    t_tune = time.perf_counter()
+    shapes = solver.tune(reps=20)
+    tune_s = time.perf_counter() - t_tune
     for _ in range(args.warmup):
         solver.solve(**mixed)
     solver.solve(**fp64)
@@ -480,6 +489,11 @@ def run_ours(args):
                        other_step_mixed_attempts=oth["mixed"][1]["attempts"],
                        other_step_fp64_s=oth["fp64"][0],
                        other_step_fp64_attempts=oth["fp64"][1]["attempts"],
+                       rule_shapes_s=statistics.mean(rule_times),
+                       tuned_shapes=shapes, tune_s=tune_s,
+                       shapes_note="value: row kernels at qp_tune's launch shapes (lanes per "
+                                   "row, row layout, waves); rule_shapes_s: the same solve at "
+                                   "the mean-row-length rule's shapes, timed before tuning",
                        parallelism=f"replicas x{ws}"),
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
@@ -720,6 +734,7 @@ def run_zipf_bench(args):
     solver = QPSolver(inst, scale=True)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
+    shapes = solver.tune(reps=5)
     for _ in range(args.warmup):
         solver.solve(tol=tol, precision=L.PREC_MIXED, step_mode=step, max_iter=128)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
@@ -758,7 +773,8 @@ def run_zipf_bench(args):
                        other_step_s=otimes[-1], other_step_termination=oi["termination"],
                        other_step_relkkt=oi["relkkt"], other_step_attempts=oi["attempts"],
                        warmup_note="each warm-up solve capped at 128 attempts",
-                       generate_s=gen_s, create_s=create_s, parallelism=f"replicas x{ws}"),
+                       generate_s=gen_s, create_s=create_s, tuned_shapes=shapes,
+                       parallelism=f"replicas x{ws}"),
         "e2e": None,
         "roofline": {"kernel": "k_cg<float> (persistent CG: Q SpMV + vector phases)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -329,6 +329,58 @@ qp_status qp_set_bounds(qp_handle* h, const double* lo, const double* hi);
  * 0 when the flag was not given or the problem has no equality rows. */
 qp_status qp_get_penalty(const qp_handle* h, double* rho);
 
+/* ---------------------------------------------- launch-shape autotuner */
+
+/*
+ * Launch shapes of the row kernels, the CUDA products with Q, A and A' that
+ * carry every step of Algorithm 1 (the CG kernel's Q p, the dual step's
+ * A x+, the A'y+ kernel, the relKKT products).  Index [p][k]: p = 0 FP64,
+ * 1 FP32 (mixed precision); k = 0 Q, 1 A, 2 A'.
+ *   lanes        lanes per row in use: G threads share one CSR row, so a
+ *                warp takes 32 / G rows at a time; rows longer than 16 G
+ *                entries (64 at least in FP64) go to one whole warp each
+ *   lanes_rule   the choice of the mean-row-length rule applied at qp_create
+ *   layout       how rows go to warps: 0 groups of 32 / G rows across the grid
+ *                in turn, 1 a contiguous range per warp (the default), 2 a
+ *                contiguous range per block whose groups its warps take in turn
+ *   product_us   one product at the shape in use, microseconds (qp_tune's
+ *                best-of-three timing; 0 before qp_tune)
+ *   product_us_rule  the same product at the rule's lanes
+ *   waves        grid of the non-persistent row kernels in waves of
+ *                co-resident blocks (1 at qp_create)
+ *   waves_us[w]  qp_tune: the three products of the mixed path (Q, A, A'
+ *                at the chosen lanes) with 1, 2 and 4 waves, microseconds
+ *   tuned        1 once qp_tune has run
+ */
+typedef struct {
+  int32_t lanes[2][3];
+  int32_t lanes_rule[2][3];
+  int32_t layout[2][3];
+  double product_us[2][3];
+  double product_us_rule[2][3];
+  int32_t waves;
+  int32_t tuned;
+  double waves_us[3];
+} qp_shapes;
+
+/*
+ * Autotuner.  Times, on this handle's own matrices, one product with each of
+ * Q, A and A' in both precisions at 1, 2, 4, 8 and 32 lanes per row (each
+ * with its own medium-row table) and, for A and A', each row layout (Q keeps
+ * the warp ranges, the layout of its persistent CG kernel), then the row
+ * kernels' grid at 1, 2 and 4 waves, and keeps the fastest shape of each (the
+ * rule's unless another is faster by more than 1%).  Each timing is the best of three runs of `reps` products (reps in
+ * 1..1000) on scratch vectors the call allocates and frees; the iterate,
+ * warm start, bounds and statistics of the handle are left as they were.
+ * The solve graphs captured so far are rebuilt by the next qp_solve.  The
+ * shapes in use afterwards are written to *out (may be NULL) and returned
+ * by qp_get_shapes.  Errors: QP_ERR_INVALID_ARG, QP_ERR_OOM, QP_ERR_CUDA.
+ */
+qp_status qp_tune(qp_handle* h, int32_t reps, qp_shapes* out);
+
+/* The launch shapes in use (qp_create's rule, or qp_tune's choice). */
+qp_status qp_get_shapes(const qp_handle* h, qp_shapes* out);
+
 /* ------------------------------------------------------- diagnostics */
 
 /*

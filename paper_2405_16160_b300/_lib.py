@@ -96,6 +96,20 @@ class QPInstanceResultC(Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class QPShapesC(Structure):
+    _fields_ = [("lanes", (c_int32 * 3) * 2), ("lanes_rule", (c_int32 * 3) * 2),
+                ("layout", (c_int32 * 3) * 2), ("product_us", (c_double * 3) * 2), ("product_us_rule", (c_double * 3) * 2),
+                ("waves", c_int32), ("tuned", c_int32), ("waves_us", c_double * 3)]
+
+    def as_dict(self) -> dict:
+        grid = lambda a: [list(row) for row in a]
+        return {"lanes": grid(self.lanes), "lanes_rule": grid(self.lanes_rule),
+                "layout": grid(self.layout),
+                "product_us": grid(self.product_us),
+                "product_us_rule": grid(self.product_us_rule), "waves": self.waves,
+                "tuned": self.tuned, "waves_us": list(self.waves_us)}
+
+
 ALLOC_FN = CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
 FREE_FN = CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
 
@@ -130,6 +144,8 @@ SIGNATURES = [
     ("qp_norm_A", c_int32, [_H, c_int32, _F64P]),
     ("qp_get_penalty", c_int32, [_H, _F64P]),
     ("qp_set_bounds", c_int32, [_H, _F64P, _F64P]),
+    ("qp_tune", c_int32, [_H, c_int32, POINTER(QPShapesC)]),
+    ("qp_get_shapes", c_int32, [_H, POINTER(QPShapesC)]),
     ("qp_gather_rate", c_int32, [c_int64, c_int32, c_int32, c_uint64, _F64P]),
     ("qp_norm_A_static", c_int32, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),

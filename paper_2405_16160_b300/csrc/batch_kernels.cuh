@@ -283,6 +283,27 @@ __device__ void cta_reduce(double (&sum)[S > 0 ? S : 1], double (&mx)[M > 0 ? M 
   __syncthreads();
 }
 
+// A block-wide sum whose total only thread 0 forms (the warp partials added
+// in warp order, exactly as cta_reduce does) and hands to f(total) before the
+// closing barrier; f writes what the block needs into shared memory.  The
+// method's FP64 scalars (alpha, beta, the stop test) are then derived once
+// per block instead of once per thread: B300's FP64 pipe runs at 1/58 of
+// FP32, and a division or square root is dozens of its instructions.
+template <int NT, class F>
+__device__ __forceinline__ void cta_sum_t0(double v, double* red, F&& f) {
+  constexpr int NW = NT / 32;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  v = warp_sum(v);
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int i = 0; i < NW; ++i) a += red[i];
+    f(a);
+  }
+  __syncthreads();
+}
+
 template <int NT>
 __device__ __forceinline__ double cta_sum1(double v, double* red) {
   double s[1] = {v}, m[1] = {0.0};
@@ -305,6 +326,10 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
   constexpr bool kShadow = !std::is_same<V, double>::value;
   const BatchDesc d = B.desc[id];
   const int n = d.n, m = d.m, k = d.k, tid = threadIdx.x;
+  // the FP64 scalars of the method, derived by thread 0 and read by all
+  // (cta_sum_t0); s_flag: 0 go on, 1 stop, 2 numerical error
+  __shared__ double s_sc[6];  // tau, 1/tau, eps, r'r (or s's), alpha or 1/alpha, beta
+  __shared__ int s_flag;
   // FP64 vectors
   double* x = sm;
   double* xa = x + B.max_n;   // average
@@ -420,12 +445,16 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
       __syncthreads();
       double ww = 0.0;
       for (int j = tid; j < n; j += NT) ww = fma(q[j], q[j], ww);
-      lam = sqrt(cta_sum1<NT>(ww, red));
-      const double inv = lam > 0.0 ? 1.0 / lam : 0.0;
+      cta_sum_t0<NT>(ww, red, [&](double t) {
+        s_sc[0] = sqrt(t);
+        s_sc[1] = s_sc[0] > 0.0 ? 1.0 / s_sc[0] : 0.0;
+      });
+      const double inv = s_sc[1];
       for (int j = tid; j < n; j += NT) pv[j] = V(q[j] * inv);
       __syncthreads();
     }
     if (tid == 0) {
+      lam = s_sc[0];
       st.lam = lam;
       setup_finish_decide(&st, nc2, nb2, 1);
     }
@@ -517,23 +546,32 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
   while (running(&st)) {
     for (int it = 0; it < efreq && running(&st) && st.attempts < st.opt.max_iter; ++it) {
       // ---- x-step: inexact CG on (Q + I/tau) x = x/tau - c - A'y (Section 2)
-      const double tau = st.tau, inv_tau = 1.0 / tau;
       const int mode = st.opt.cg_mode, nfix = st.opt.cg_fixed_n, cgmax = st.opt.cg_max;
-      const double eps =
-          mode == kCgAdaptive ? st.eps + st.opt.cg_eps_factor * st.relkkt_last : st.eps;
-      double rr = rr0;
+      if (tid == 0) {
+        s_sc[0] = st.tau;
+        s_sc[1] = 1.0 / st.tau;
+        s_sc[2] = mode == kCgAdaptive ? st.eps + st.opt.cg_eps_factor * st.relkkt_last : st.eps;
+        s_sc[3] = rr0;
+        s_flag = (mode == kCgFixed && nfix <= 0) || rr0 == 0.0;
+      }
+      __syncthreads();
+      const double inv_tau = s_sc[1];
       int steps = 0;
       bool numerr = false;
-      const bool skip = (mode == kCgFixed && nfix <= 0) || rr == 0.0;
+      const bool skip = s_flag != 0;
       if (lo && !skip) {
         // ---- BB projected gradient (Section 4) from x, with r = p = -g:
         // alpha0 = g'Mg / g'g, then x+ = min(max(x + r/alpha, lo), hi), s = x+ - x,
         // r -= M s, Q x += Q s, alpha = s'Ms / s's (M = Q + I/tau)
         const double gmg = cta_qprod_pmp<V, NT>(F, qd, n, k, pv, p, inv_tau, tv, t, q);
-        if (!(gmg > 0.0) || !isfinite(gmg)) numerr = true;
-        double alpha = gmg / rr;
+        if (tid == 0) {
+          s_flag = !(gmg > 0.0) || !isfinite(gmg) ? 2 : 0;
+          s_sc[4] = 1.0 / (gmg / s_sc[3]);  // 1/alpha, alpha = g'Mg / g'g
+        }
+        __syncthreads();
+        numerr = s_flag == 2;
         while (!numerr) {
-          const double inv_alpha = 1.0 / alpha;
+          const double inv_alpha = s_sc[4];
           double ss = 0.0;
           for (int j = tid; j < n; j += NT) {
             const double xj = x[j];
@@ -547,7 +585,7 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
             }
             ss = fma(sj, sj, ss);
           }
-          ss = cta_sum1<NT>(ss, red);
+          cta_sum_t0<NT>(ss, red, [&](double t) { s_sc[3] = t; });
           // q = Q s and s'(Q + I/tau)s
           const double sw = cta_qprod_pmp<V, NT>(F, qd, n, k, pv, p, inv_tau, tv, t, q);
           for (int j = tid; j < n; j += NT) {
@@ -555,27 +593,41 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
             r[j] -= qj + sj * inv_tau;
             qx[j] += qj;
           }
+          if (tid == 0) {
+            const double ssv = s_sc[3];
+            const bool stop = mode == kCgFixed ? steps + 1 >= nfix
+                                               : (sqrt(ssv) <= s_sc[2] || steps + 1 >= cgmax);
+            if (stop || ssv == 0.0) {
+              s_flag = 1;
+            } else if (!(sw > 0.0) || !isfinite(sw)) {
+              s_flag = 2;
+            } else {
+              s_flag = 0;
+              s_sc[4] = 1.0 / (sw / ssv);  // 1/alpha, alpha = s'w / s's
+            }
+          }
+          __syncthreads();
           ++steps;
-          const bool stop =
-              mode == kCgFixed ? steps >= nfix : (sqrt(ss) <= eps || steps >= cgmax);
-          if (stop || ss == 0.0) break;
-          if (!(sw > 0.0) || !isfinite(sw)) {
+          if (s_flag == 1) break;
+          if (s_flag == 2) {
             numerr = true;
             break;
           }
-          alpha = sw / ss;
         }
       }
       while (!skip && !lo) {
         cta_qprod<V, NT, false>(F, qd, n, k, pv, tv, q);  // q = Q p
         double pq = 0.0;
         for (int j = tid; j < n; j += NT) pq = fma(p[j], q[j] + p[j] * inv_tau, pq);
-        pq = cta_sum1<NT>(pq, red);
-        if (!(pq > 0.0) || !isfinite(pq)) {
+        cta_sum_t0<NT>(pq, red, [&](double t) {
+          s_flag = !(t > 0.0) || !isfinite(t) ? 2 : 0;
+          s_sc[4] = s_sc[3] / t;  // alpha = r'r / p'q
+        });
+        if (s_flag == 2) {
           numerr = true;
           break;
         }
-        const double alpha = rr / pq;
+        const double alpha = s_sc[4];
         double rn = 0.0;
         for (int j = tid; j < n; j += NT) {
           const double pj = p[j], qpj = q[j];
@@ -587,13 +639,17 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
           r[j] = rj;
           rn = fma(rj, rj, rn);
         }
-        const double rr_new = cta_sum1<NT>(rn, red);
+        cta_sum_t0<NT>(rn, red, [&](double rr_new) {
+          const bool stop = mode == kCgFixed
+                                ? steps + 1 >= nfix
+                                : (s_sc[0] * sqrt(rr_new) <= s_sc[2] || steps + 1 >= cgmax);
+          s_flag = stop || rr_new == 0.0;
+          s_sc[5] = rr_new / s_sc[3];  // beta
+          s_sc[3] = rr_new;
+        });
         ++steps;
-        const bool stop =
-            mode == kCgFixed ? steps >= nfix : (tau * sqrt(rr_new) <= eps || steps >= cgmax);
-        if (stop || rr_new == 0.0) break;
-        const double beta = rr_new / rr;
-        rr = rr_new;
+        if (s_flag) break;
+        const double beta = s_sc[5];
         for (int j = tid; j < n; j += NT) {
           const double pn = __dadd_rn(r[j], __dmul_rn(beta, p[j]));
           p[j] = pn;
@@ -614,9 +670,9 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         st.cg_total += steps;
         st.last_cg = steps;
         if (B.adaptive) {
-          st.eps_try = eps;
+          st.eps_try = s_sc[2];
         } else {
-          st.eps = eps;
+          st.eps = s_sc[2];
           st.k_total += 1;
           st.j += 1;
         }
@@ -666,7 +722,9 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         continue;
       }
       // ---- y-step fused into A x+, then A'y+, x~ and the next CG start
-      const double inv_j = 1.0 / (double)st.j;
+      if (tid == 0) s_sc[5] = 1.0 / (double)st.j;
+      __syncthreads();
+      const double inv_j = s_sc[5];
       cta_dual<V, NT>(A, xv, b, d.m_eq, st.sigma, inv_j, y, yv, ax, ya);
       __syncthreads();
       cta_spmv<V, NT>(At, yv, aty);

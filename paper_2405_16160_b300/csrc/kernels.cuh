@@ -64,6 +64,15 @@ constexpr int kSegLen = 2048;
 // kernels leave them to one whole warp each, after the regular rows, so that
 // a skewed row-length distribution (a few rows of thousands of entries among
 // rows of a handful) does not stall a warp's other row groups.
+// How the row kernels hand rows to warps (a runtime choice per matrix and
+// precision, picked by qp_tune): rows in groups of 32/G across the whole grid
+// in turn; each warp a contiguous range of its own, the same size for every
+// warp to within one group; or each block a contiguous range whose groups
+// its warps take in turn.
+constexpr int kRowsGridStride = 0;
+constexpr int kRowsWarpRange = 1;
+constexpr int kRowsBlockRange = 2;
+
 template <class T>
 struct CsrT {
   const int32_t* rowptr;
@@ -76,6 +85,7 @@ struct CsrT {
   const int32_t* med_rows = nullptr;   // ascending ids of the medium rows
   int32_t nmed = 0;
   int32_t med_min = 0x7fffffff;
+  int32_t layout = kRowsWarpRange;
 };
 
 // Segment table of a matrix's long rows: segment s covers entries
@@ -88,13 +98,20 @@ struct LongRows {
 };
 
 
+// Grid barrier state.  Barrier number g (gen before it) publishes its value
+// (a reduced total, or 0) in slot[g % 2], which holds kSlotOpen while the
+// barrier is open; waiting blocks poll that slot, so one load both releases
+// them and hands them the value.  The host resets the barrier with
+// reset_barrier-style memsets: count 0, gen 0, both slots kSlotOpen.
+constexpr unsigned long long kSlotOpen = ~0ull;
+
 struct alignas(128) GridBarrier {
   unsigned int count;
   unsigned int pad0[31];
-  unsigned int gen;
-  unsigned int pad1;
-  double total;  // grid_sync_sum: the reduced value, published with the generation
-  unsigned int pad2[28];
+  unsigned int gen;  // barriers completed, read by a kernel at its start
+  unsigned int pad1[31];
+  unsigned long long slot[2];
+  unsigned long long pad2[14];
 };
 
 // ------------------------------------------------------------------ helpers
@@ -355,15 +372,104 @@ __device__ __forceinline__ double block_total_dot(const double* p, int n, AccF) 
 }
 
 
-// Sense-free generation barrier over all blocks of a co-resident grid.  Each
-// block's thread 0 holds the barrier's generation in `gen` (grid_gen at the
-// kernel's start, then advanced by every grid_sync), so arriving costs one
-// atomic round trip: fence, count, and either release (the last arrival:
-// reset the count, publish the next generation) or poll until the
-// generation moves.  Every wait is bounded: after opt.barrier_timeout_ms
-// (globaltimer) or 2^27 polls the block records kErrBarrierTimeout and the
-// kernel winds down; a block that sees the error flag stops waiting too.
-// Returns false on error.
+// KS sums per block in the layout of block_dot_store: for AccF each total is
+// a double-float pair in its 8-byte slot, so the consumer also combines them
+// on the FP32 pipe; for AccD plain doubles.  Thread 0 writes out[0..KS).
+template <int KS, class A>
+__device__ __forceinline__ void block_pairs_store(A (&a)[KS], double* out) {
+  if constexpr (std::is_same<A, AccF>::value) {
+    __shared__ float2 sh[KS][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      warp_merge(a[k]);
+      if (lane == 0) sh[k][wid] = make_float2(a[k].hi, a[k].lo);
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        AccF b;
+        if (lane < int(blockDim.x >> 5)) {
+          b.hi = sh[k][lane].x;
+          b.lo = sh[k][lane].y;
+        }
+        warp_merge(b);
+        if (lane == 0) reinterpret_cast<float2*>(out)[k] = make_float2(b.hi, b.lo);
+      }
+    }
+    __syncthreads();
+  } else {
+    block_reduce_ms<0, KS, double, AccD>(nullptr, a, out);
+  }
+}
+
+// The totals of nrows rows of K block_pairs_store partials (row r at
+// part + r * K), combined in index order by the whole block; every thread
+// gets them.  AccF: double-float pairs on the FP32 pipe; AccD: doubles.
+template <int K, class A>
+__device__ __forceinline__ void block_pairs_total(const double* part, int nrows, double (&out)[K]) {
+  if constexpr (std::is_same<A, AccF>::value) {
+    __shared__ float2 sh[K][32];
+    __shared__ double s_out[K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    AccF acc[K];
+    const float2* p2 = reinterpret_cast<const float2*>(part);
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+      float2 v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = __ldcg(p2 + size_t(r) * K + k);
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k].add2(v[k].x, v[k].y);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      warp_merge(acc[k]);
+      if (lane == 0) sh[k][wid] = make_float2(acc[k].hi, acc[k].lo);
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        AccF b;
+        if (lane < int(blockDim.x >> 5)) {
+          b.hi = sh[k][lane].x;
+          b.lo = sh[k][lane].y;
+        }
+        warp_merge(b);
+        if (lane == 0) s_out[k] = b.value();
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = s_out[k];
+    __syncthreads();
+  } else {
+    block_reduce_rows<K>(part, nrows, K, 0u, out);
+  }
+}
+
+// Barrier over all blocks of a co-resident grid that can also reduce one
+// partial per block (block_dot_store layout) to a total.  Each block's
+// thread 0 holds the barrier number in gen_local (grid_gen at the kernel's
+// start, then advanced by every barrier).  Arriving: fence, then count.  The
+// block that arrives last sums the partials in index order
+// (block_total_dot, so the value does not depend on which block is last),
+// re-opens the next barrier's slot, resets the count and publishes the total
+// in this barrier's slot with release order; the others poll that slot.  One
+// block reads the partials instead of every block, so their L2 lines are not
+// read by the whole grid at once, and the waiting blocks get the total with
+// the same load that releases them.
+//
+// on_total(total) runs in thread 0 of every block once the total is known,
+// before the block's closing barrier: the place to derive the method's FP64
+// scalars once per block and share them through shared memory (the FP64
+// pipe of B300 runs at 1/58 of FP32, so a division or square root evaluated
+// by every thread of a persistent grid costs microseconds).
+//
+// Every wait is bounded: after opt.barrier_timeout_ms (globaltimer) or 2^27
+// polls the block records kErrBarrierTimeout and the kernel winds down; a
+// block that sees the error flag stops waiting too.  Returns false on error.
 __device__ __forceinline__ unsigned int grid_gen(GridBarrier* bar) {
   unsigned int g = 0u;
   if (threadIdx.x == 0) {
@@ -373,72 +479,15 @@ __device__ __forceinline__ unsigned int grid_gen(GridBarrier* bar) {
   return g;
 }
 
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int timeout_ms,
-                                          bool never_release, unsigned int& gen_local) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(bar->gen);
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(bar->count);
-    cuda::atomic_ref<int, cuda::thread_scope_device> err(st->err);
-    int ok = 1;
-    const unsigned int g = gen_local;
-    __threadfence();
-    const unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
-    if (arrived == gridDim.x - 1 && !never_release) {
-      cnt.store(0u, cuda::memory_order_relaxed);
-      gen.store(g + 1u, cuda::memory_order_release);
-    } else {
-      const unsigned long long t0 = global_ns();
-      const unsigned long long limit = (unsigned long long)timeout_ms * 1000000ull;
-      unsigned int polls = 0;
-      while (gen.load(cuda::memory_order_acquire) == g) {
-        if (err.load(cuda::memory_order_relaxed) != 0) {
-          ok = 0;
-          break;
-        }
-        if ((++polls & 255u) == 0u) {
-          if (global_ns() - t0 > limit || polls > (1u << 27)) {
-            err.fetch_or(kErrBarrierTimeout, cuda::memory_order_relaxed);
-            ok = 0;
-            break;
-          }
-        }
-        __nanosleep(32);
-      }
-    }
-    gen_local = g + 1u;
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// A grid barrier that also reduces one partial per block (block_dot_store
-// layout) to a total every thread of every block receives.  The block that
-// arrives last sums the partials in index order (block_total_dot, so the
-// value does not depend on which block arrives last) and
-// publishes the total in the barrier's generation line before releasing it;
-// the others read that one value after the release.  One block reads the
-// partials instead of every block, so the L2 lines holding them are not
-// read by the whole grid at once.  Waits are bounded as in grid_sync.
-//
-// on_total(total) runs in thread 0 of every block once the total is known,
-// before the block's closing barrier: the place to derive the method's FP64
-// scalars once per block and share them through shared memory (the FP64
-// pipe of B300 runs at 1/58 of FP32, so a division or square root evaluated
-// by every thread of a persistent grid costs microseconds).
 template <class A, class F>
 __device__ __forceinline__ bool grid_sync_sum(GridBarrier* bar, DevState* st, int timeout_ms,
                                               bool never_release, unsigned int& gen_local,
                                               const double* part, F&& on_total) {
   __shared__ int s_ok, s_last;
   __syncthreads();
-  cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(bar->gen);
-  cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(bar->count);
-  cuda::atomic_ref<double, cuda::thread_scope_device> tot(bar->total);
   const unsigned int g = gen_local;
+  cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(bar->count);
+  cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> slot(bar->slot[g & 1u]);
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
@@ -448,19 +497,26 @@ __device__ __forceinline__ bool grid_sync_sum(GridBarrier* bar, DevState* st, in
   __syncthreads();
   if (s_last) {  // the whole last block (the branch is uniform)
     __threadfence();
-    const double t = block_total_dot<1>(part, gridDim.x, A());
+    const double t = part ? block_total_dot<1>(part, gridDim.x, A()) : 0.0;
     if (threadIdx.x == 0) {
-      tot.store(t, cuda::memory_order_relaxed);
+      cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> next(
+          bar->slot[(g + 1u) & 1u]);
+      cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(bar->gen);
+      unsigned long long bits = (unsigned long long)__double_as_longlong(t);
+      if (bits == kSlotOpen) bits = 0x7ff8000000000000ull;  // a NaN either way
+      next.store(kSlotOpen, cuda::memory_order_relaxed);
       cnt.store(0u, cuda::memory_order_relaxed);
-      gen.store(g + 1u, cuda::memory_order_release);
-      on_total(t);
+      gen.store(g + 1u, cuda::memory_order_relaxed);
+      slot.store(bits, cuda::memory_order_release);
+      on_total(__longlong_as_double((long long)bits));
     }
   } else if (threadIdx.x == 0) {
     cuda::atomic_ref<int, cuda::thread_scope_device> err(st->err);
     const unsigned long long t0 = global_ns();
     const unsigned long long limit = (unsigned long long)timeout_ms * 1000000ull;
     unsigned int polls = 0;
-    while (gen.load(cuda::memory_order_acquire) == g) {
+    unsigned long long v;
+    while ((v = slot.load(cuda::memory_order_acquire)) == kSlotOpen) {
       if (err.load(cuda::memory_order_relaxed) != 0) {
         s_ok = 0;
         break;
@@ -474,7 +530,7 @@ __device__ __forceinline__ bool grid_sync_sum(GridBarrier* bar, DevState* st, in
       }
       __nanosleep(32);
     }
-    if (s_ok) on_total(tot.load(cuda::memory_order_relaxed));
+    if (s_ok) on_total(__longlong_as_double((long long)v));
   }
   if (threadIdx.x == 0) {
     gen_local = g + 1u;
@@ -482,6 +538,13 @@ __device__ __forceinline__ bool grid_sync_sum(GridBarrier* bar, DevState* st, in
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// The plain barrier: no partials to reduce.
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int timeout_ms,
+                                          bool never_release, unsigned int& gen_local) {
+  return grid_sync_sum<AccD>(bar, st, timeout_ms, never_release, gen_local, nullptr,
+                             [](double) {});
 }
 
 // Row-group CSR SpMV: G lanes share a row (G in {1,2,4,8,16,32}); all 32 lanes
@@ -543,13 +606,25 @@ __device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f) {
   const int sub = lane & (G - 1);
   const long long gw = grid_tid() >> 5;
   const long long nw = grid_threads() >> 5;
-  // warp gw takes the contiguous rows [r0, r1): every warp gets the same
-  // number of rows to within one, so no SM is left with a larger share
-  const int r0 = int((long long)M.rows * gw / nw), r1 = int((long long)M.rows * (gw + 1) / nw);
-  for (int base = r0; base < r1; base += kRowsPerWarp) {
+  int start, end, step;  // the warp's row groups: base = start, start + step, ... < end
+  if (M.layout == kRowsGridStride) {
+    start = int(gw) * kRowsPerWarp;
+    end = M.rows;
+    step = int(nw) * kRowsPerWarp;
+  } else if (M.layout == kRowsWarpRange) {
+    start = int((long long)M.rows * gw / nw);
+    end = int((long long)M.rows * (gw + 1) / nw);
+    step = kRowsPerWarp;
+  } else {
+    const int wpb = int(blockDim.x >> 5);
+    start = int((long long)M.rows * blockIdx.x / gridDim.x) + int(threadIdx.x >> 5) * kRowsPerWarp;
+    end = int((long long)M.rows * (blockIdx.x + 1) / gridDim.x);
+    step = wpb * kRowsPerWarp;
+  }
+  for (int base = start; base < end; base += step) {
     const int i = base + lane / G;
     T s = T(0);
-    bool own = i < r1;
+    bool own = i < end;
     if (own) {
       const int b = __ldg(M.rowptr + i), e = __ldg(M.rowptr + i + 1);
       if (e - b > kLongRow) {
@@ -720,7 +795,7 @@ __device__ __forceinline__ void step_start_sums(const StepStart<T>& ss, const T*
     acc[0].add_prod(dx, dx);
     acc[1].add_prod(dx, dq);
   }
-  block_reduce_ms<0, 2, T>(nullptr, acc, ss.part + 2 * size_t(blockIdx.x));
+  block_pairs_store<2>(acc, ss.part + 2 * size_t(blockIdx.x));
 }
 
 template <int G, class T>
@@ -885,7 +960,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
   }
   // the sums of the last step are the attempt's primal move (a launch with no
   // step leaves x = x_save: both sums are zero)
-  if (move_sums && !numerr) block_reduce_ms<0, 2, T>(nullptr, mv, ss.part + 2 * size_t(blockIdx.x));
+  if (move_sums && !numerr) block_pairs_store<2>(mv, ss.part + 2 * size_t(blockIdx.x));
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (numerr) {
       st->done = kDoneNumerical;
@@ -983,7 +1058,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
       block_dot_store(acc, part_a + blockIdx.x);
       if (!grid_sync_sum<A>(bar, st, tmo, never_release, gen, part_a, [&](double gmg) {
             s_flag = !(gmg > 0.0) || !isfinite(gmg);
-            s_inv_alpha = T(s_rr / gmg);  // 1/alpha, alpha = g'M g / g'g
+            s_inv_alpha = T(1.0 / (gmg / s_rr));  // alpha = g'M g / g'g
           }))
         return;
       never_release = false;
@@ -1024,7 +1099,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
               s_flag = 2;
             } else {
               s_flag = 0;
-              s_inv_alpha = T(s_ss / sw);  // 1/alpha, alpha = s'w / s's
+              s_inv_alpha = T(1.0 / (sw / s_ss));  // alpha = s'w / s's
             }
           }))
         return;
@@ -1100,6 +1175,7 @@ struct StepTrial {
   double* part_step = nullptr;
   const double* part_n = nullptr;
   int n_parts = 0;
+  const double* pow_table = nullptr;  // step_decide's (a+1)^-0.3, (a+1)^-0.6
   unsigned int* ticket = nullptr;
 };
 
@@ -1154,7 +1230,7 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
       am[1].add_prod(dy, da);
     });
     }
-    block_reduce_ms<0, 2, T>(nullptr, am, tr.part_step + 2 * size_t(blockIdx.x));
+    block_pairs_store<2>(am, tr.part_step + 2 * size_t(blockIdx.x));
     __shared__ int s_last;
     if (threadIdx.x == 0) {
       __threadfence();
@@ -1164,10 +1240,10 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
     if (s_last) {  // the whole last block (the branch is uniform)
       __threadfence();
       double t[2], u[2];
-      block_reduce_rows<2>(tr.part_step, gridDim.x, 2, 0u, t);
-      block_reduce_rows<2>(tr.part_n, tr.n_parts, 2, 0u, u);
+      block_pairs_total<2, typename Acc<T>::type>(tr.part_step, gridDim.x, t);
+      block_pairs_total<2, typename Acc<T>::type>(tr.part_n, tr.n_parts, u);
       if (threadIdx.x == 0) {
-        step_decide(st, u[0], u[1], t[0], t[1]);
+        step_decide(st, u[0], u[1], t[0], t[1], tr.pow_table);
         *tr.ticket = 0u;
         __threadfence();
       }
@@ -1323,11 +1399,13 @@ __global__ void __launch_bounds__(kBlock) k_spmv(CsrT<T> M, const T* __restrict_
                                                  const double* inv_norm_sq) {
   // out = M v / ||v||_2 when inv_norm_sq points at ||v||_2^2 (the power
   // iteration's normalisation, applied to the product instead of to v)
-  T scale = T(1);
-  if (inv_norm_sq) {
-    const double l2 = __ldcg(inv_norm_sq);
-    scale = l2 > 0.0 ? T(1.0 / sqrt(l2)) : T(0);
+  __shared__ T s_scale;  // 1/||v||_2, formed once per block (FP64 sqrt and division)
+  if (threadIdx.x == 0) {
+    const double l2 = inv_norm_sq ? __ldcg(inv_norm_sq) : 1.0;
+    s_scale = l2 > 0.0 ? T(1.0 / sqrt(l2)) : T(0);
   }
+  __syncthreads();
+  const T scale = s_scale;
   typename Acc<T>::type acc;
   spmv_rows<G>(M, v, [&](int i, T s, bool lead) {
     if (lead) {
@@ -1616,7 +1694,10 @@ __global__ void k_init_vectors(T* x, T* x_avg, T* x_anchor, const T* __restrict_
 template <class T>
 __global__ void k_pow_start(T* v, int n, const T* __restrict__ c, const T* __restrict__ b, int m,
                             double* part2) {
-  const T v0 = T(1.0 / sqrt((double)n));
+  __shared__ T s_v0;  // 1/sqrt(n), once per block
+  if (threadIdx.x == 0) s_v0 = T(1.0 / sqrt((double)n));
+  __syncthreads();
+  const T v0 = s_v0;
   typename Acc<T>::type a[2];
   for (long long i = grid_tid(); i < n; i += grid_threads()) {
     v[i] = v0;
@@ -1624,6 +1705,15 @@ __global__ void k_pow_start(T* v, int n, const T* __restrict__ c, const T* __res
   }
   for (long long i = grid_tid(); i < m; i += grid_threads()) a[1].add_prod(b[i], b[i]);
   block_reduce_ms<0, 2, T>(nullptr, a, part2 + size_t(blockIdx.x) * 2);
+}
+
+// step_decide's table: t[2 a] = (a+1)^-0.3, t[2 a + 1] = (a+1)^-0.6.
+__global__ void k_step_pow(double* t, int count) {
+  for (long long a = grid_tid(); a < count; a += grid_threads()) {
+    const double a1 = (double)(a + 1);
+    t[2 * a] = pow(a1, -kStepReductionExp);
+    t[2 * a + 1] = pow(a1, -kStepGrowthExp);
+  }
 }
 
 // Element-wise type conversion (FP64 <-> FP32 copies of a vector).

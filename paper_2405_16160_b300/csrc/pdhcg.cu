@@ -83,6 +83,7 @@ struct DevMat {
   int32_t rows = 0;
   int64_t nnz = 0;
   int G64 = 1, G32 = 4;
+  int layout64 = kRowsWarpRange, layout32 = kRowsWarpRange;  // rows to warps (qp_tune)
   // medium rows (more than 16 G entries, at most kLongRow) per precision
   int32_t *med64 = nullptr, *med32 = nullptr;
   int32_t nmed64 = 0, nmed32 = 0, med_min64 = 0x7fffffff, med_min32 = 0x7fffffff;
@@ -96,11 +97,11 @@ struct DevMat {
 template <class T>
 CsrT<T> view(const DevMat& M) {
   if constexpr (std::is_same<T, double>::value)
-    return CsrT<double>{M.rowptr, M.col,  M.val,   M.rows,     M.long_rows, M.long64,
-                        M.nlong,  M.med64, M.nmed64, M.med_min64};
+    return CsrT<double>{M.rowptr, M.col,   M.val,    M.rows,       M.long_rows, M.long64,
+                        M.nlong,  M.med64, M.nmed64, M.med_min64, M.layout64};
   else
-    return CsrT<float>{M.rowptr, M.col,  M.val32, M.rows,     M.long_rows, M.long32,
-                       M.nlong,  M.med32, M.nmed32, M.med_min32};
+    return CsrT<float>{M.rowptr, M.col,   M.val32,  M.rows,       M.long_rows, M.long32,
+                       M.nlong,  M.med32, M.nmed32, M.med_min32, M.layout32};
 }
 
 LongRows long_rows_of(const DevMat& M) {
@@ -217,6 +218,7 @@ struct qp_handle {
          *part_rm = nullptr, *part_pow = nullptr, *part2 = nullptr, *part_r0 = nullptr;
   double* part_step_m = nullptr;  // adaptive step test partials (2 per k_dual block)
   double* part_step_n = nullptr;  // and the primal move's (2 per CG/BB block)
+  double* step_pow = nullptr;     // step_decide's power table (kStepPowTable pairs)
   int step_mode = QP_STEP_FIXED;  // step rule of the iteration being launched
   DevState* st = nullptr;
   GridBarrier* bar = nullptr;
@@ -224,6 +226,8 @@ struct qp_handle {
   int num_sms = 0;
   int grid_n = 1, grid_m = 1, grid_vec = 1;
   int grid_cg[2] = {1, 1};  // persistent CG grid per precision (FP64, FP32)
+  int waves = 1;            // grid of the non-persistent row kernels, in resident waves
+  qp_shapes shapes{};       // launch shapes in use (lanes per row, waves) and qp_tune's timings
   unsigned int* ticket = nullptr;  // last-block counter of the r0'r0 reduction
   bool coop_ok = true;
   bool warm_set = false;
@@ -309,6 +313,9 @@ qp_status dispatch_g(int G, F&& f) {
     default: set_error("unsupported group size %d", G); return QP_ERR_INVALID_ARG;
   }
 }
+
+// Largest grid of the non-persistent row kernels qp_tune may pick, in waves.
+constexpr int kMaxWaves = 4;
 
 int blocks_for_rows(int64_t rows, int G, int cap, int block = kBlock) {
   const int64_t rows_per_block = int64_t(block / 32) * (32 / G);
@@ -422,6 +429,7 @@ qp_status launch_dual(qp_handle* h) {
       tr.ax_new = v.ax_new;
       tr.part_step = h->part_step_m;
       tr.part_n = h->part_step_n;
+      tr.pow_table = h->step_pow;
       tr.n_parts = h->grid_cg[std::is_same<T, double>::value ? 0 : 1];
       tr.ticket = h->ticket;
     }
@@ -738,11 +746,19 @@ qp_status sync(qp_handle* h) {
   return QP_OK;
 }
 
+// The grid barrier of the persistent kernels, open at barrier 0: count 0,
+// generation 0, both value slots kSlotOpen (all bits set).
+qp_status reset_barrier(qp_handle* h) {
+  CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->bar->slot, 0xff, sizeof(h->bar->slot), h->stream));
+  return QP_OK;
+}
+
 qp_status write_options(qp_handle* h, const qp_options* o) {
   fill_dev_options(h, o, &h->h_st->opt);
   CUDA_TRY(cudaMemcpyAsync(&h->st->opt, &h->h_st->opt, sizeof(DevOptions), cudaMemcpyHostToDevice,
                            h->stream));
-  CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->stream));
+  QP_TRY(reset_barrier(h));
   return QP_OK;
 }
 
@@ -1093,6 +1109,56 @@ qp_status validate_problem(int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr
   return QP_OK;
 }
 
+// Launch geometry from the lanes per row in use and h->waves: the
+// non-persistent row kernels take h->waves resident waves of blocks (each
+// warp a contiguous share of the rows, so more blocks than fit at once let
+// the block scheduler give the faster SMs more of them); the persistent CG
+// kernel takes the co-resident block count of its instantiation.
+qp_status compute_grids(qp_handle* h) {
+  const int n = h->n, m = h->m;
+  const int wave = h->num_sms * 8 * h->waves;
+  const int g_n = std::max({h->Q.G64, h->At.G64, h->Q.G32, h->At.G32, h->Qe.G64, h->Qe.G32});
+  const int g_m = std::max(h->A.G64, h->A.G32);
+  h->grid_n = blocks_for_rows(std::max(n, 1), g_n, wave);
+  h->grid_m = blocks_for_rows(std::max(m, 1), g_m, wave);
+  for (int fp32 = 0; fp32 < 2; ++fp32) {
+    int occ = 0;
+    // the persistent CG and BB kernels share the grid: the smaller residency
+    int occ_bb = 0;
+    if (fp32)
+      QP_TRY(dispatch_g(lanes<float>(h->Q), [&](auto g) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<decltype(g)::value, float>,
+                                                      kCgBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_bb, k_bb<decltype(g)::value, float>,
+                                                      kCgBlock, 0);
+      }));
+    else
+      QP_TRY(dispatch_g(lanes<double>(h->Q), [&](auto g) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<decltype(g)::value, double>,
+                                                      kCgBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_bb, k_bb<decltype(g)::value, double>,
+                                                      kCgBlock, 0);
+      }));
+    occ = std::min(occ, occ_bb);
+    CUDA_TRY(cudaGetLastError());
+    if (occ < 1) {
+      set_error("CG kernel cannot be resident");
+      return QP_ERR_CUDA;
+    }
+    h->grid_cg[fp32] = blocks_for_rows(n, fp32 ? h->Q.G32 : h->Q.G64,
+                                       std::min(occ, 2048 / kCgBlock) * h->num_sms, kCgBlock);
+  }
+  const DevMat* mats[3] = {&h->Q, &h->A, &h->At};
+  for (int k = 0; k < 3; ++k) {
+    h->shapes.lanes[0][k] = mats[k]->G64;
+    h->shapes.lanes[1][k] = mats[k]->G32;
+    h->shapes.layout[0][k] = mats[k]->layout64;
+    h->shapes.layout[1][k] = mats[k]->layout32;
+  }
+  h->shapes.waves = h->waves;
+  return QP_OK;
+}
+
 qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr,
                       const int32_t* Qc, const double* Qv, const int32_t* Ar, const int32_t* Ac,
                       const double* Av, const double* c, const double* b, uint32_t flags,
@@ -1181,58 +1247,39 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   convert(h, h->v64.c, h->v32.c, n);
   convert(h, h->v64.b, h->v32.b, m);
 
-  const int g_n = std::max({h->Q.G64, h->At.G64, h->Q.G32, h->At.G32, h->Qe.G64, h->Qe.G32});
-  const int g_m = std::max(h->A.G64, h->A.G32);
-  h->grid_n = blocks_for_rows(std::max(n, 1), g_n, wave);
-  h->grid_m = blocks_for_rows(std::max(m, 1), g_m, wave);
-  // The CG kernel is persistent: its grid is the co-resident block count of
-  // each precision's instantiation.
-  for (int fp32 = 0; fp32 < 2; ++fp32) {
-    int occ = 0;
-    // the persistent CG and BB kernels share the grid: the smaller residency
-    int occ_bb = 0;
-    if (fp32)
-      QP_TRY(dispatch_g(lanes<float>(h->Q), [&](auto g) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<decltype(g)::value, float>,
-                                                      kCgBlock, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_bb, k_bb<decltype(g)::value, float>,
-                                                      kCgBlock, 0);
-      }));
-    else
-      QP_TRY(dispatch_g(lanes<double>(h->Q), [&](auto g) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg<decltype(g)::value, double>,
-                                                      kCgBlock, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_bb, k_bb<decltype(g)::value, double>,
-                                                      kCgBlock, 0);
-      }));
-    occ = std::min(occ, occ_bb);
-    CUDA_TRY(cudaGetLastError());
-    if (occ < 1) {
-      set_error("CG kernel cannot be resident");
-      return QP_ERR_CUDA;
-    }
-    h->grid_cg[fp32] = blocks_for_rows(n, fp32 ? h->Q.G32 : h->Q.G64, occ * h->num_sms, kCgBlock);
+  // lanes per row of the mean-row-length rule, then the launch geometry
+  const DevMat* mats[3] = {&h->Q, &h->A, &h->At};
+  for (int k = 0; k < 3; ++k) {
+    h->shapes.lanes_rule[0][k] = mats[k]->G64;
+    h->shapes.lanes_rule[1][k] = mats[k]->G32;
   }
-  const int gcg = std::max(h->grid_cg[0], h->grid_cg[1]);
-  const int gmax = std::max({h->grid_n, h->grid_m, h->grid_vec, gcg});
+  QP_TRY(compute_grids(h));
+  // partial buffers sized for the largest grids any lanes per row or wave
+  // count of qp_tune can give (32 lanes per row: 8 rows per 256-thread block)
+  const int gn_max = blocks_for_rows(std::max(n, 1), 32, wave * kMaxWaves);
+  const int gm_max = blocks_for_rows(std::max(m, 1), 32, wave * kMaxWaves);
+  const int gcg = (2048 / kCgBlock) * h->num_sms;
+  const int gmax = std::max({gn_max, gm_max, h->grid_vec, gcg});
   QP_TRY(dalloc(h, &h->part_cg, size_t(2) * gcg));
-  QP_TRY(dalloc(h, &h->part_r0, size_t(h->grid_n) + 1));
+  QP_TRY(dalloc(h, &h->part_r0, size_t(gn_max) + 1));
   QP_TRY(dalloc(h, &h->ticket, 1));
   CUDA_TRY(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream));
-  QP_TRY(dalloc(h, &h->part_n, size_t(h->grid_n) * kPartStride));
-  QP_TRY(dalloc(h, &h->part_m, size_t(h->grid_m) * kPartStride));
+  QP_TRY(dalloc(h, &h->part_n, size_t(gn_max) * kPartStride));
+  QP_TRY(dalloc(h, &h->part_m, size_t(gm_max) * kPartStride));
   QP_TRY(dalloc(h, &h->part_rn, size_t(gmax)));
   QP_TRY(dalloc(h, &h->part_rm, size_t(gmax)));
   QP_TRY(dalloc(h, &h->part_pow, size_t(gmax) + 1));
   QP_TRY(dalloc(h, &h->part2, size_t(2) * gmax));
-  QP_TRY(dalloc(h, &h->part_step_m, size_t(4) * h->grid_m));
-  QP_TRY(dalloc(h, &h->part_step_n, size_t(2) * std::max(h->grid_cg[0], h->grid_cg[1])));
+  QP_TRY(dalloc(h, &h->part_step_m, size_t(4) * gm_max));
+  QP_TRY(dalloc(h, &h->part_step_n, size_t(2) * gcg));
+  QP_TRY(dalloc(h, &h->step_pow, size_t(2) * kStepPowTable));
+  k_step_pow<<<h->num_sms * 4, kBlock, 0, h->stream>>>(h->step_pow, kStepPowTable);
   QP_TRY(dalloc(h, &h->st, 1));
   QP_TRY(dalloc(h, &h->bar, 1));
   CUDA_TRY(cudaMallocHost(&h->h_st, sizeof(DevState)));
   std::memset(h->h_st, 0, sizeof(DevState));
   CUDA_TRY(cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
-  CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->stream));
+  QP_TRY(reset_barrier(h));
   QP_TRY(check_launch());
   return sync(h);
 }
@@ -1445,6 +1492,164 @@ qp_status solve_impl(qp_handle* h, const qp_options* o, std::chrono::steady_cloc
 }  // namespace
 
 // ====================================================================== C ABI
+// ------------------------------------------------ launch-shape autotuner
+namespace {
+
+// The medium rows of a matrix at lanes per row G (the rule of
+// build_row_tables): more than 16 G entries (64 at least for FP64's
+// one-lane rows), at most kLongRow; *min_out gets the threshold.
+std::vector<int32_t> medium_rows(const std::vector<int32_t>& rp, int G, bool fp32,
+                                 int32_t* min_out) {
+  const int32_t mn = G >= 32 ? kLongRow : (fp32 ? 16 * G : std::max(16 * G, 64));
+  *min_out = mn;
+  std::vector<int32_t> out;
+  for (size_t i = 0; i + 1 < rp.size(); ++i) {
+    const int32_t len = rp[i + 1] - rp[i];
+    if (len <= kLongRow && len > mn) out.push_back(int32_t(i));
+  }
+  return out;
+}
+
+// Lanes per row G for one precision of M, with its medium-row table.
+qp_status set_lanes(qp_handle* h, DevMat* M, bool fp32, int G, const std::vector<int32_t>& rp) {
+  int32_t mn = 0;
+  const std::vector<int32_t> md = medium_rows(rp, G, fp32, &mn);
+  int32_t** dst = fp32 ? &M->med32 : &M->med64;
+  QP_TRY(sync(h));  // no kernel may still read the table being replaced
+  if (*dst) dev_free(h, *dst);
+  *dst = nullptr;
+  (fp32 ? M->nmed32 : M->nmed64) = int32_t(md.size());
+  (fp32 ? M->med_min32 : M->med_min64) = mn;
+  (fp32 ? M->G32 : M->G64) = G;
+  if (!md.empty()) {
+    QP_TRY(dalloc(h, dst, md.size()));
+    QP_TRY(upload(h, *dst, md.data(), md.size() * sizeof(int32_t)));
+    QP_TRY(sync(h));  // md dies with this call
+  }
+  return QP_OK;
+}
+
+// Best of three timings of `reps` rounds of products (mats[k] times in[k]
+// into out[k], k < count) at grids of `waves` resident waves; microseconds
+// per round.
+template <class T>
+qp_status time_products(qp_handle* h, DevMat* const* mats, int count, T* const* in, T* const* out,
+                        int waves, int reps, double* us) {
+  const int cap = h->num_sms * 8 * waves;
+  int grid[3];
+  for (int k = 0; k < count; ++k) {
+    const int G = std::is_same<T, double>::value ? mats[k]->G64 : mats[k]->G32;
+    grid[k] = blocks_for_rows(std::max(mats[k]->rows, 1), G, cap);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  qp_status st = cudaEventCreate(&e1) == cudaSuccess ? QP_OK : QP_ERR_CUDA;
+  double best = INFINITY;
+  for (int k = 0; k < count && st == QP_OK; ++k)  // warm-up
+    st = launch_spmv<T>(h, *mats[k], in[k], out[k], nullptr, grid[k]);
+  for (int trial = 0; trial < 3 && st == QP_OK; ++trial) {
+    cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < reps && st == QP_OK; ++r)
+      for (int k = 0; k < count && st == QP_OK; ++k)
+        st = launch_spmv<T>(h, *mats[k], in[k], out[k], nullptr, grid[k]);
+    cudaEventRecord(e1, h->stream);
+    if (st != QP_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+      st = QP_ERR_CUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, double(ms) * 1e3 / reps);
+  }
+  if (st == QP_OK && cudaGetLastError() != cudaSuccess) st = QP_ERR_CUDA;
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st != QP_OK) set_error("qp_tune: a timed product failed");
+  *us = best;
+  return st;
+}
+
+// Lanes per row (1, 2, 4, 8, 32) and row layout of each matrix in one
+// precision.  Q keeps the warp ranges: its products run inside the
+// persistent CG kernel, where they measured fastest, and a plain product
+// does not time that kernel's layout; A and A' try all three layouts.
+template <class T>
+qp_status tune_lanes(qp_handle* h, int pi, DevMat* const* mats, const std::vector<int32_t>* rps,
+                     T* const* in, T* const* out, int reps) {
+  constexpr bool fp32 = std::is_same<T, float>::value;
+  static const int kLanes[5] = {1, 2, 4, 8, 32};
+  for (int k = 0; k < 3; ++k) {
+    DevMat* M = mats[k];
+    if (M->rows == 0 || M->nnz == 0) continue;
+    int& layout = fp32 ? M->layout32 : M->layout64;
+    const int rule = h->shapes.lanes_rule[pi][k];
+    const int nlayouts = k == 0 ? 1 : 3;
+    const int layouts[3] = {kRowsWarpRange, kRowsGridStride, kRowsBlockRange};
+    int best_g = rule, best_l = kRowsWarpRange;
+    double t_best = INFINITY, t_rule = INFINITY;
+    for (int c = 0; c < 5; ++c) {
+      QP_TRY(set_lanes(h, M, fp32, kLanes[c], rps[k]));
+      for (int l = 0; l < nlayouts; ++l) {
+        layout = layouts[l];
+        double t = 0.0;
+        QP_TRY(time_products<T>(h, &mats[k], 1, &in[k], &out[k], h->waves, reps, &t));
+        if (kLanes[c] == rule && layouts[l] == kRowsWarpRange) t_rule = t;
+        if (t < t_best) {
+          t_best = t;
+          best_g = kLanes[c];
+          best_l = layouts[l];
+        }
+      }
+    }
+    // the rule's shape unless another was faster by more than 1%
+    if (!(t_best < 0.99 * t_rule)) {
+      best_g = rule;
+      best_l = kRowsWarpRange;
+      t_best = t_rule;
+    }
+    QP_TRY(set_lanes(h, M, fp32, best_g, rps[k]));
+    layout = best_l;
+    h->shapes.product_us[pi][k] = t_best;
+    h->shapes.product_us_rule[pi][k] = t_rule;
+    h->shapes.layout[pi][k] = best_l;
+  }
+  return QP_OK;
+}
+
+qp_status tune_impl(qp_handle* h, int reps, float* const* in32, float* const* out32,
+                    double* const* in64, double* const* out64) {
+  DevMat* mats[3] = {&h->Q, &h->A, &h->At};
+  std::vector<int32_t> rps[3];
+  for (int k = 0; k < 3; ++k) {
+    rps[k].resize(size_t(mats[k]->rows) + 1);
+    CUDA_TRY(cudaMemcpyAsync(rps[k].data(), mats[k]->rowptr, rps[k].size() * sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, h->stream));
+  }
+  QP_TRY(sync(h));
+  QP_TRY(tune_lanes<double>(h, 0, mats, rps, in64, out64, reps));
+  QP_TRY(tune_lanes<float>(h, 1, mats, rps, in32, out32, reps));
+  // the grid of the non-persistent row kernels, on the mixed path's products
+  static const int kWaves[3] = {1, 2, 4};
+  double t[3];
+  for (int w = 0; w < 3; ++w)
+    QP_TRY(time_products<float>(h, mats, 3, in32, out32, kWaves[w], reps, &t[w]));
+  int best = 0;
+  for (int w = 1; w < 3; ++w)
+    if (t[w] < 0.99 * t[best]) best = w;
+  for (int w = 0; w < 3; ++w) h->shapes.waves_us[w] = t[w];
+  h->waves = kWaves[best];
+  QP_TRY(compute_grids(h));
+  // the captured solve graphs hold the old shapes: rebuilt by the next solve
+  for (auto& e : h->chunk_exec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
+  h->shapes.tuned = 1;
+  return QP_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* qp_status_string(qp_status s) {
@@ -1830,7 +2035,7 @@ qp_status qp_iterate(qp_handle* h, const qp_options* o, int64_t iters) {
   d.done = 0;
   d.err = 0;
   QP_TRY(write_state(h));
-  CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->stream));
+  QP_TRY(reset_barrier(h));
   const bool mixed = o->precision == QP_PREC_MIXED;
   if (mixed != (h->active_prec == kPrecMixed)) {
     // iterating in the other precision: bring its copy of the iterate over
@@ -1881,6 +2086,52 @@ qp_status qp_evaluate(qp_handle* h, double kkt_cur[6], double kkt_avg[6]) {
 qp_status qp_get_penalty(const qp_handle* h, double* rho) {
   if (!h || !rho) return QP_ERR_INVALID_ARG;
   *rho = h->rho;
+  return QP_OK;
+}
+
+qp_status qp_tune(qp_handle* h, int32_t reps, qp_shapes* out) {
+  if (!h || reps < 1 || reps > 1000) {
+    set_error("qp_tune: reps must be in 1..1000");
+    return QP_ERR_INVALID_ARG;
+  }
+  QP_TRY(begin_call(h));
+  const size_t N = std::max<size_t>(size_t(h->n), 1), M = std::max<size_t>(size_t(h->m), 1);
+  float *xn32 = nullptr, *xm32 = nullptr, *on32 = nullptr, *om32 = nullptr;
+  double *xn64 = nullptr, *xm64 = nullptr, *on64 = nullptr, *om64 = nullptr;
+  qp_status st = QP_OK;
+  for (float** p : {&xn32, &on32})
+    if (st == QP_OK) st = dalloc(h, p, N);
+  for (float** p : {&xm32, &om32})
+    if (st == QP_OK) st = dalloc(h, p, M);
+  for (double** p : {&xn64, &on64})
+    if (st == QP_OK) st = dalloc(h, p, N);
+  for (double** p : {&xm64, &om64})
+    if (st == QP_OK) st = dalloc(h, p, M);
+  if (st == QP_OK) {
+    // any finite input will do: a gather costs the same whatever it reads
+    cudaMemsetAsync(xn32, 0x3f, N * sizeof(float), h->stream);
+    cudaMemsetAsync(xm32, 0x3f, M * sizeof(float), h->stream);
+    cudaMemsetAsync(xn64, 0x3f, N * sizeof(double), h->stream);
+    cudaMemsetAsync(xm64, 0x3f, M * sizeof(double), h->stream);
+    // Q and A read x (n), A' reads y (m); Q and A' write n entries, A writes m
+    float* in32[3] = {xn32, xn32, xm32};
+    float* out32[3] = {on32, om32, on32};
+    double* in64[3] = {xn64, xn64, xm64};
+    double* out64[3] = {on64, om64, on64};
+    st = tune_impl(h, reps, in32, out32, in64, out64);
+  }
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : {(void*)xn32, (void*)xm32, (void*)on32, (void*)om32, (void*)xn64, (void*)xm64,
+                  (void*)on64, (void*)om64})
+    dev_free(h, p);
+  if (st != QP_OK) return st;
+  if (out) *out = h->shapes;
+  return end_call(h);
+}
+
+qp_status qp_get_shapes(const qp_handle* h, qp_shapes* out) {
+  if (!h || !out) return QP_ERR_INVALID_ARG;
+  *out = h->shapes;
   return QP_OK;
 }
 

@@ -182,15 +182,25 @@ __device__ inline void control_decide(DevState* st, const KktTerms& kc, const Kk
 // precision of the attempt is kept and the averaging weight eta / (sum of
 // the epoch's accepted etas) is set.  Shared by the single-QP step kernel
 // and the batched solver.
+//
+// pow_table (may be null): pow_table[2 a] = (a+1)^-0.3 and pow_table[2 a + 1]
+// = (a+1)^-0.6 for a < kStepPowTable, filled by k_step_pow with the same
+// pow calls, so that the thread deciding (alone on its SM, on B300's narrow
+// FP64 pipe) reads them instead of evaluating two FP64 powers.
+constexpr int kStepPowTable = 1 << 17;
+
 __device__ inline void step_decide(DevState* st, double dx2, double dxqdx, double dy2,
-                                   double cross) {
+                                   double cross, const double* pow_table = nullptr) {
   const double eta = st->eta, om = st->omega;
   const double movement = om * dx2 + dy2 / om;
   const double interaction = 2.0 * fabs(cross) + dxqdx;
   const double lim = interaction > 0.0 ? movement / interaction : CUDART_INF;
-  const double a1 = (double)(st->attempts + 1);
-  const double next = fmin((1.0 - pow(a1, -kStepReductionExp)) * lim,
-                           (1.0 + pow(a1, -kStepGrowthExp)) * eta);
+  const long long a = st->attempts;
+  const double a1 = (double)(a + 1);
+  const bool tab = pow_table != nullptr && a >= 0 && a < kStepPowTable;
+  const double pr = tab ? pow_table[2 * a] : pow(a1, -kStepReductionExp);
+  const double pg = tab ? pow_table[2 * a + 1] : pow(a1, -kStepGrowthExp);
+  const double next = fmin((1.0 - pr) * lim, (1.0 + pg) * eta);
   const bool acc = eta <= lim;
   st->accepted = acc ? 1 : 0;
   st->eta = next;

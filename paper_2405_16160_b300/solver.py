@@ -216,6 +216,19 @@ class QPSolver:
         L.check(self.lib.qp_get_penalty(self.h, byref(out)), "qp_get_penalty")
         return out.value
 
+    def tune(self, reps: int = 20) -> dict:
+        """qp_tune: time the row kernels' launch shapes on this problem's
+        matrices and keep the fastest; returns the shapes in use."""
+        out = L.QPShapesC()
+        L.check(self.lib.qp_tune(self.h, int(reps), byref(out)), "qp_tune")
+        return out.as_dict()
+
+    def shapes(self) -> dict:
+        """qp_get_shapes: the launch shapes in use."""
+        out = L.QPShapesC()
+        L.check(self.lib.qp_get_shapes(self.h, byref(out)), "qp_get_shapes")
+        return out.as_dict()
+
     def close(self) -> None:
         if getattr(self, "h", None):
             self.lib.qp_destroy(self.h)

@@ -52,7 +52,8 @@ def test_abi_version_and_status_strings(lib):
 def test_struct_layouts_match_ctypes(tmp_path):
     structs = {"qp_options": L.QPOptionsC, "qp_info": L.QPInfoC,
                "qp_state_scalars": L.QPStateScalarsC, "qp_state_vectors": L.QPStateVectorsC,
-               "qp_trace_entry": L.QPTraceEntryC, "qp_device_ctx": L.QPDeviceCtxC}
+               "qp_trace_entry": L.QPTraceEntryC, "qp_device_ctx": L.QPDeviceCtxC,
+               "qp_shapes": L.QPShapesC}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdhcg.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -191,3 +192,10 @@ def test_gather_rate_rejects_bad_arguments(lib):
     assert lib.qp_gather_rate(0, 10, 1, 1, byref(out)) == 1  # QP_ERR_INVALID_ARG
     assert lib.qp_gather_rate(10, 0, 1, 1, byref(out)) == 1
     assert lib.qp_gather_rate(10, 10, 1, 1, None) == 1
+
+
+def test_tuner_rejects_bad_arguments(lib):
+    from ctypes import byref
+    out = L.QPShapesC()
+    assert lib.qp_tune(None, 10, byref(out)) == 1  # QP_ERR_INVALID_ARG
+    assert lib.qp_get_shapes(None, byref(out)) == 1
