@@ -746,6 +746,9 @@ def run_zipf_bench(args):
         _barrier(ws)
     oinfo, otimes = _timed_solves(solver, 1, stream, tol=tol, precision=L.PREC_MIXED,
                                   step_mode=other, time_limit_s=300.0)
+    # plain FP64 with the same step rule, allowed to reach the tolerance
+    finfo, ftimes = _timed_solves(solver, 1, stream, tol=tol, precision=L.PREC_FP64,
+                                  step_mode=step, time_limit_s=600.0)
     kinfos, _ = _timed_solves(solver, 1, stream, tol=tol, precision=L.PREC_MIXED, step_mode=step,
                               kernel_timing=1, max_iter=640)
     solver.close()
@@ -772,6 +775,9 @@ def run_zipf_bench(args):
                        other_step=("fixed" if args.step == "adaptive" else "adaptive"),
                        other_step_s=otimes[-1], other_step_termination=oi["termination"],
                        other_step_relkkt=oi["relkkt"], other_step_attempts=oi["attempts"],
+                       fp64_s=ftimes[-1], fp64_termination=finfo[-1]["termination"],
+                       fp64_relkkt=finfo[-1]["relkkt"], fp64_attempts=finfo[-1]["attempts"],
+                       speedup_vs_fp64=ftimes[-1] / value,
                        warmup_note="each warm-up solve capped at 128 attempts",
                        generate_s=gen_s, create_s=create_s, tuned_shapes=shapes,
                        parallelism=f"replicas x{ws}"),

@@ -415,12 +415,22 @@ __device__ __forceinline__ void block_pairs_total(const double* part, int nrows,
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     AccF acc[K];
     const float2* p2 = reinterpret_cast<const float2*>(part);
-    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
-      float2 v[K];
+    // rows t, t + blockDim, t + 2 blockDim, ... in that order, eight rows'
+    // loads in flight at once (a row past the end adds an exact zero)
+    constexpr int RB = 8;
+    for (int base = threadIdx.x; base < nrows; base += RB * int(blockDim.x)) {
+      float2 v[RB][K];
 #pragma unroll
-      for (int k = 0; k < K; ++k) v[k] = __ldcg(p2 + size_t(r) * K + k);
+      for (int j = 0; j < RB; ++j) {
+        const int r = base + j * int(blockDim.x);
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc[k].add2(v[k].x, v[k].y);
+        for (int k = 0; k < K; ++k)
+          v[j][k] = r < nrows ? __ldcg(p2 + size_t(r) * K + k) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int j = 0; j < RB; ++j)
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k].add2(v[j][k].x, v[j][k].y);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
