@@ -112,6 +112,7 @@ struct alignas(128) GridBarrier {
   unsigned int pad1[31];
   unsigned long long slot[2];
   unsigned long long pad2[14];
+  double extra[16];  // totals 2..K of a K-value barrier (written before the slot's release)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -489,7 +490,10 @@ __device__ __forceinline__ unsigned int grid_gen(GridBarrier* bar) {
   return g;
 }
 
-template <class A, class F>
+// K > 1: K totals per barrier (block_pairs_store layout, K per block); the
+// last block publishes the first in the slot and the others in the barrier's
+// extra line, which the waiting blocks read after the slot releases them.
+template <class A, int K = 1, class F>
 __device__ __forceinline__ bool grid_sync_sum(GridBarrier* bar, DevState* st, int timeout_ms,
                                               bool never_release, unsigned int& gen_local,
                                               const double* part, F&& on_total) {
@@ -507,18 +511,26 @@ __device__ __forceinline__ bool grid_sync_sum(GridBarrier* bar, DevState* st, in
   __syncthreads();
   if (s_last) {  // the whole last block (the branch is uniform)
     __threadfence();
-    const double t = part ? block_total_dot<1>(part, gridDim.x, A()) : 0.0;
+    double t[K];
+    if constexpr (K == 1) {
+      t[0] = part ? block_total_dot<1>(part, gridDim.x, A()) : 0.0;
+    } else {
+      block_pairs_total<K, A>(part, gridDim.x, t);
+    }
     if (threadIdx.x == 0) {
       cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> next(
           bar->slot[(g + 1u) & 1u]);
       cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(bar->gen);
-      unsigned long long bits = (unsigned long long)__double_as_longlong(t);
+      unsigned long long bits = (unsigned long long)__double_as_longlong(t[0]);
       if (bits == kSlotOpen) bits = 0x7ff8000000000000ull;  // a NaN either way
+      t[0] = __longlong_as_double((long long)bits);
+#pragma unroll
+      for (int k = 1; k < K; ++k) bar->extra[k - 1] = t[k];
       next.store(kSlotOpen, cuda::memory_order_relaxed);
       cnt.store(0u, cuda::memory_order_relaxed);
       gen.store(g + 1u, cuda::memory_order_relaxed);
       slot.store(bits, cuda::memory_order_release);
-      on_total(__longlong_as_double((long long)bits));
+      on_total(static_cast<const double*>(t));
     }
   } else if (threadIdx.x == 0) {
     cuda::atomic_ref<int, cuda::thread_scope_device> err(st->err);
@@ -540,7 +552,13 @@ __device__ __forceinline__ bool grid_sync_sum(GridBarrier* bar, DevState* st, in
       }
       __nanosleep(32);
     }
-    if (s_ok) on_total(__longlong_as_double((long long)v));
+    if (s_ok) {
+      double t[K];
+      t[0] = __longlong_as_double((long long)v);
+#pragma unroll
+      for (int k = 1; k < K; ++k) t[k] = __ldcg(&bar->extra[k - 1]);
+      on_total(static_cast<const double*>(t));
+    }
   }
   if (threadIdx.x == 0) {
     gen_local = g + 1u;
@@ -554,7 +572,7 @@ __device__ __forceinline__ bool grid_sync_sum(GridBarrier* bar, DevState* st, in
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int timeout_ms,
                                           bool never_release, unsigned int& gen_local) {
   return grid_sync_sum<AccD>(bar, st, timeout_ms, never_release, gen_local, nullptr,
-                             [](double) {});
+                             [](const double*) {});
 }
 
 // Row-group CSR SpMV: G lanes share a row (G in {1,2,4,8,16,32}); all 32 lanes
@@ -785,10 +803,12 @@ __device__ __forceinline__ void store_and_finish_dot(A acc, double* part, unsign
 constexpr int kCgBlocksPerSm = 3;
 
 // Adaptive step size: the attempt's primal move from its saved start (x_save,
-// qx_save), ||x+ - x||^2 and (x+ - x)'(Q x+ - Q x), summed by the x-step
-// kernel after its last step, when every block's writes of x and Q x are
-// visible (a grid barrier closes each step), into part[2 * block]; k_dual's
-// last block combines them with its own sums.  part == nullptr: fixed step.
+// qx_save), ||x+ - x||^2 and (x+ - x)'(Q x+ - Q x).  The CG kernel sums them
+// in each step's phase B and totals them in that step's closing barrier;
+// block 0 writes the last step's two totals to part[0..1].  The BB kernel
+// sums them in a pass after its last step into part[2 * block] (block
+// partials).  k_dual's last block combines them with its own sums.
+// part == nullptr: fixed step.
 template <class T>
 struct StepStart {
   const T* x_save = nullptr;
@@ -828,9 +848,12 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
   const int tmo = st->opt.barrier_timeout_ms;
   bool never_release = (st->opt.debug_flags & kDebugBarrierNeverReleases) != 0u;
   __shared__ double s_tau, s_eps, s_rr;  // thread 0's
+  __shared__ double s_mv[2];             // the latest step's primal move sums (totals)
   __shared__ T s_inv_tau, s_coef;        // 1/tau; alpha, then beta
   __shared__ int s_flag;                 // skip / numerical error / stop
   if (threadIdx.x == 0) {
+    s_mv[0] = 0.0;  // no step: x is the attempt's start
+    s_mv[1] = 0.0;
     s_tau = st->tau;
     s_eps = mode == kCgAdaptive ? st->eps + st->opt.cg_eps_factor * st->relkkt_last : st->eps;
     s_rr = __ldcg(r0r0);
@@ -840,8 +863,8 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
   __syncthreads();
   const T inv_tau = s_inv_tau;
   const bool skip = s_flag != 0;
-  double* part_rr = part;
-  double* part_pq = part + gridDim.x;
+  double* part_pq = part;                 // one partial per block
+  double* part_rr = part + gridDim.x;     // three per block: r'r and the move sums
   const long long t0 = grid_tid(), nt = grid_threads();
   unsigned int gen = grid_gen(bar);
   // adaptive step: the primal move's sums of the latest step, per thread
@@ -878,7 +901,8 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
       }
     });
     block_dot_store(acc, part_pq + blockIdx.x);
-    if (!grid_sync_sum<A>(bar, st, tmo, never_release, gen, part_pq, [&](double pq) {
+    if (!grid_sync_sum<A>(bar, st, tmo, never_release, gen, part_pq, [&](const double* t) {
+          const double pq = t[0];
           const bool bad = !(pq > 0.0) || !isfinite(pq);
           s_flag = bad;
           s_coef = bad ? T(0) : T(s_rr / pq);
@@ -953,8 +977,12 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
         }
       }
     }
-    block_dot_store(acc, part_rr + blockIdx.x);
-    if (!grid_sync_sum<A>(bar, st, tmo, false, gen, part_rr, [&](double rr_new) {
+    A sums[3] = {acc, mv[0], mv[1]};
+    block_pairs_store<3>(sums, part_rr + 3 * size_t(blockIdx.x));
+    if (!grid_sync_sum<A, 3>(bar, st, tmo, false, gen, part_rr, [&](const double* t) {
+          const double rr_new = t[0];
+          s_mv[0] = t[1];
+          s_mv[1] = t[2];
           const int done_steps = steps + 1;
           const bool stop = mode == kCgFixed
                                 ? done_steps >= nfix
@@ -968,9 +996,12 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
     if (s_flag) break;
     beta = s_coef;
   }
-  // the sums of the last step are the attempt's primal move (a launch with no
-  // step leaves x = x_save: both sums are zero)
-  if (move_sums && !numerr) block_pairs_store<2>(mv, ss.part + 2 * size_t(blockIdx.x));
+  // the totals of the last step's move sums are the attempt's primal move (a
+  // launch with no step leaves x = x_save: both are zero)
+  if (move_sums && !numerr && blockIdx.x == 0 && threadIdx.x == 0) {
+    ss.part[0] = s_mv[0];
+    ss.part[1] = s_mv[1];
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (numerr) {
       st->done = kDoneNumerical;
@@ -1066,7 +1097,8 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
           }))
         return;
       block_dot_store(acc, part_a + blockIdx.x);
-      if (!grid_sync_sum<A>(bar, st, tmo, never_release, gen, part_a, [&](double gmg) {
+      if (!grid_sync_sum<A>(bar, st, tmo, never_release, gen, part_a, [&](const double* t) {
+            const double gmg = t[0];
             s_flag = !(gmg > 0.0) || !isfinite(gmg);
             s_inv_alpha = T(1.0 / (gmg / s_rr));  // alpha = g'M g / g'g
           }))
@@ -1086,7 +1118,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
         acc.add_prod(si, si);
       }
       block_dot_store(acc, part_a + blockIdx.x);
-      if (!grid_sync_sum<A>(bar, st, tmo, false, gen, part_a, [&](double t) { s_ss = t; }))
+      if (!grid_sync_sum<A>(bar, st, tmo, false, gen, part_a, [&](const double* t) { s_ss = t[0]; }))
         return;
       A acc2;
       if (!qprod([&](int i, T s) {
@@ -1099,7 +1131,8 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
         return;
       block_dot_store(acc2, part_b + blockIdx.x);
       // flag: 0 continue, 1 stop, 2 numerical error
-      if (!grid_sync_sum<A>(bar, st, tmo, false, gen, part_b, [&](double sw) {
+      if (!grid_sync_sum<A>(bar, st, tmo, false, gen, part_b, [&](const double* t) {
+            const double sw = t[0];
             const int done_steps = steps + 1;
             const bool stop = mode == kCgFixed ? done_steps >= nfix
                                                : (sqrt(s_ss) <= s_eps || done_steps >= cgmax);
@@ -1174,7 +1207,8 @@ __global__ void k_project_box(T* x, const T* __restrict__ lo, const T* __restric
 // low word) and A x+ go to T.y_new, T.yn_lo, T.ax_new.  Each block stores the
 // partial sums ||y+ - y||^2 and (y+ - y)'(A x+ - A x) at part_step[2 * block];
 // the last block to finish combines them, and the x-step kernel's partials of
-// ||x+ - x||^2 and (x+ - x)'(Q x+ - Q x) (StepStart: part_n, n_parts blocks),
+// ||x+ - x||^2 and (x+ - x)'(Q x+ - Q x) (StepStart: part_n, n_parts block
+// partials, or the two totals when n_parts is 0),
 // in a fixed order and takes the Section 4 step decision (step_decide).
 // k_commit_m and k_atv then commit or drop the trial.
 template <class T>
@@ -1251,7 +1285,12 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
       __threadfence();
       double t[2], u[2];
       block_pairs_total<2, typename Acc<T>::type>(tr.part_step, gridDim.x, t);
-      block_pairs_total<2, typename Acc<T>::type>(tr.part_n, tr.n_parts, u);
+      if (tr.n_parts > 0) {  // per-block partials (the BB kernel)
+        block_pairs_total<2, typename Acc<T>::type>(tr.part_n, tr.n_parts, u);
+      } else {               // the CG kernel's totals
+        u[0] = __ldcg(tr.part_n);
+        u[1] = __ldcg(tr.part_n + 1);
+      }
       if (threadIdx.x == 0) {
         step_decide(st, u[0], u[1], t[0], t[1], tr.pow_table);
         *tr.ticket = 0u;

@@ -430,7 +430,8 @@ qp_status launch_dual(qp_handle* h) {
       tr.part_step = h->part_step_m;
       tr.part_n = h->part_step_n;
       tr.pow_table = h->step_pow;
-      tr.n_parts = h->grid_cg[std::is_same<T, double>::value ? 0 : 1];
+      // the BB kernel leaves block partials, the CG kernel the two totals
+      tr.n_parts = h->bounded ? h->grid_cg[std::is_same<T, double>::value ? 0 : 1] : 0;
       tr.ticket = h->ticket;
     }
     k_dual<G, T><<<h->grid_m, kBlock, 0, h->stream>>>(view<T>(h->A), it_x(v), it_b(v), v.y,
@@ -1260,7 +1261,7 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   const int gm_max = blocks_for_rows(std::max(m, 1), 32, wave * kMaxWaves);
   const int gcg = (2048 / kCgBlock) * h->num_sms;
   const int gmax = std::max({gn_max, gm_max, h->grid_vec, gcg});
-  QP_TRY(dalloc(h, &h->part_cg, size_t(2) * gcg));
+  QP_TRY(dalloc(h, &h->part_cg, size_t(4) * gcg));  // the CG kernel: 1 + 3 per block
   QP_TRY(dalloc(h, &h->part_r0, size_t(gn_max) + 1));
   QP_TRY(dalloc(h, &h->ticket, 1));
   CUDA_TRY(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream));
