@@ -384,7 +384,9 @@ def run_ours(args):
         solver.solve(**mixed)
     _, rule_times = _timed_solves(solver, max(2, args.steps // 2), stream, **mixed)
     t_tune = time.perf_counter()
-    shapes = solver.tune(reps=20)
+    # --shapes rule keeps the rule's shapes (profiling: under ncu the tuner's
+    # timings, and so its choices, are not those of a plain run)
+    shapes = solver.tune(reps=20) if args.shapes == "tuned" else solver.shapes()
     tune_s = time.perf_counter() - t_tune
     for _ in range(args.warmup):
         solver.solve(**mixed)
@@ -912,6 +914,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shapes", choices=["tuned", "rule"], default="tuned",
+                    help="row kernels' launch shapes: qp_tune's (default) or the rule's")
     ap.add_argument("--no-largest", action="store_true",
                     help="skip the largest-QP (n = 1e7) per-attempt record of the default run")
     ap.add_argument("--workload", choices=["sparse_dd", "portfolio_batch", "learned_warm_start",
