@@ -142,21 +142,20 @@ def cg_kernel_bytes(nnz_q: int, n: int, cg_steps: int, w: int, k_v: int = 11) ->
     return cg_steps * ((w + 4.0) * nnz_q + 4.0 * (n + 1) + k_v * float(w) * n)
 
 
-def mixed_solve_launches(chunks: int, power_iters: int, eval_freq: int,
-                         adaptive: bool) -> int:
+def mixed_solve_launches(chunks: int, power_iters: int, eval_freq: int) -> int:
     """Kernel launches of one mixed-precision qp_solve on an instance without
     long rows (each SpMV is then one launch).
 
     set-up: k_init_vectors; cache refresh (k_materialize, A x_a, k_shift_rhs,
     A dx, A'y, Q x, k_prepare); power iteration (k_pow_start, 2 per step,
     k_setup_finish); the first evaluation (k_materialize, 4 SpMVs, k_kkt_n,
-    k_kkt_m, k_control).  Per chunk: 3 per iteration (k_cg, k_dual, k_atv;
-    4 per attempt with the adaptive step: k_commit_m), an evaluation (8), the
+    k_kkt_m, k_control).  Per chunk: 3 per iteration or attempt (k_cg, k_dual,
+    k_atv; the adaptive step commits inside k_atv), an evaluation (8), the
     restart kernels (3) and k_prepare.  At the end the FP64 check: 2
     conversions, the FP64 cache refresh (3 SpMVs, k_prepare) and an FP64
     evaluation (4 SpMVs, k_kkt_n, k_kkt_m, k_control)."""
     setup = 1 + 7 + (1 + 2 * power_iters + 1) + 8
-    chunk = (4 if adaptive else 3) * eval_freq + 8 + 3 + 1
+    chunk = 3 * eval_freq + 8 + 3 + 1
     final = 2 + 4 + 7
     return setup + chunks * chunk + final
 
@@ -465,8 +464,7 @@ def run_ours(args):
     steps_per_launch = sum(i["cg_kernel_spmvs"] for i in kinfos) / max(launches, 1)
     if traffic is not None:
         traffic *= steps_per_launch
-    gpu_launches = args.steps * mixed_solve_launches(trace_len, 30, 64,
-                                                     step == L.STEP_ADAPTIVE)
+    gpu_launches = args.steps * mixed_solve_launches(trace_len, 30, 64)
     ceiling = gather_ceiling(inst.nnz_Q, inst.n)
     gathers = (sum(i["cg_kernel_spmvs"] for i in kinfos) * inst.nnz_Q / kernel_s
                if kernel_s > 0 else None)

@@ -625,15 +625,18 @@ __device__ __forceinline__ int long_slot(const CsrT<T>& M, int i) {
 // plain row loop).
 constexpr int kMedRows = 64;
 
+// blocks: how many blocks of the grid (the first ones) share the rows; by
+// default the whole grid.
 template <int GM, class T, class F>
-__device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f) {
+__device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f, int blocks = 0) {
   constexpr int G = GM & (kMedRows - 1);
   constexpr bool kMed = (GM & kMedRows) != 0;
   constexpr int kRowsPerWarp = 32 / G;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (G - 1);
+  const int nb = blocks > 0 ? blocks : int(gridDim.x);
   const long long gw = grid_tid() >> 5;
-  const long long nw = grid_threads() >> 5;
+  const long long nw = ((long long)nb * blockDim.x) >> 5;
   int start, end, step;  // the warp's row groups: base = start, start + step, ... < end
   if (M.layout == kRowsGridStride) {
     start = int(gw) * kRowsPerWarp;
@@ -645,8 +648,8 @@ __device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f) {
     step = kRowsPerWarp;
   } else {
     const int wpb = int(blockDim.x >> 5);
-    start = int((long long)M.rows * blockIdx.x / gridDim.x) + int(threadIdx.x >> 5) * kRowsPerWarp;
-    end = int((long long)M.rows * (blockIdx.x + 1) / gridDim.x);
+    start = int((long long)M.rows * blockIdx.x / nb) + int(threadIdx.x >> 5) * kRowsPerWarp;
+    end = int((long long)M.rows * (blockIdx.x + 1) / nb);
     step = wpb * kRowsPerWarp;
   }
   for (int base = start; base < end; base += step) {
@@ -742,10 +745,15 @@ __device__ __forceinline__ void long_finish(const LongRows& L, const T* seg_part
   }
 }
 
+// v_trial (may be null): the vector to read instead of v after an accepted
+// attempt of the adaptive step (the trial y, before it is committed).
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_long_segments(CsrT<T> M, const T* __restrict__ v,
-                                                          LongRows L, T* seg_part) {
-  long_segments(M, v, L, seg_part);
+                                                          LongRows L, T* seg_part,
+                                                          const T* __restrict__ v_trial = nullptr,
+                                                          const DevState* st = nullptr) {
+  const bool trial = v_trial != nullptr && st->iter_active && st->accepted;
+  long_segments(M, trial ? v_trial : v, L, seg_part);
 }
 
 template <class T>
@@ -758,20 +766,23 @@ __global__ void __launch_bounds__(kBlock) k_long_finish(LongRows L, const T* seg
 // finish (ticket counter, reset by that block) into part[gridDim.x], so the
 // CG kernel reads one value.  The summation order is fixed: the last block
 // reduces all partials in index order.
+// blocks: the blocks taking part (the first ones; default the whole grid).
 template <class A>
-__device__ __forceinline__ void store_and_finish_dot(A acc, double* part, unsigned int* ticket) {
+__device__ __forceinline__ void store_and_finish_dot(A acc, double* part, unsigned int* ticket,
+                                                     int blocks = 0) {
   __shared__ int s_last;
+  const int nb = blocks > 0 ? blocks : int(gridDim.x);
   block_dot_store(acc, part + blockIdx.x);
   if (threadIdx.x == 0) {
     __threadfence();
-    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    s_last = atomicAdd(ticket, 1u) == unsigned(nb) - 1u;
   }
   __syncthreads();
   if (s_last) {  // the whole last block (the branch is uniform)
     __threadfence();
-    const double total = block_total_dot<4>(part, gridDim.x, A());
+    const double total = block_total_dot<4>(part, nb, A());
     if (threadIdx.x == 0) {
-      part[gridDim.x] = total;
+      part[nb] = total;
       *ticket = 0u;
       __threadfence();
     }
@@ -1210,7 +1221,7 @@ __global__ void k_project_box(T* x, const T* __restrict__ lo, const T* __restric
 // ||x+ - x||^2 and (x+ - x)'(Q x+ - Q x) (StepStart: part_n, n_parts block
 // partials, or the two totals when n_parts is 0),
 // in a fixed order and takes the Section 4 step decision (step_decide).
-// k_commit_m and k_atv then commit or drop the trial.
+// k_atv then commits or drops the trial.
 template <class T>
 struct StepTrial {
   T* y_new = nullptr;
@@ -1327,25 +1338,83 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
   });
 }
 
+// Adaptive step size, after k_dual's decision: an accepted trial becomes y
+// (with its low word) and the A x cache, and enters the running average of y
+// with the step weight; a rejected one is dropped.  Run by the last `blocks`
+// blocks of the k_atv launch (block b of them: index b).
+template <class T>
+struct Commit {
+  T* y = nullptr;
+  T* y_lo = nullptr;
+  const T* y_new = nullptr;
+  const T* yn_lo = nullptr;
+  T* ax = nullptr;
+  const T* ax_new = nullptr;
+  T* y_avg = nullptr;
+  T* ya_lo = nullptr;
+  int m = 0;
+  int blocks = 0;  // 0: no commit (fixed step)
+};
+
+template <class T>
+__device__ __forceinline__ void commit_m(const Commit<T>& cm, const DevState* st, int b) {
+  if (!st->accepted) return;
+  __shared__ T s_w;  // the step weight, converted once per block
+  if (threadIdx.x == 0) s_w = T(st->avg_w);
+  __syncthreads();
+  const T w = s_w;
+  const bool first = st->j == 1;
+  const long long nt = (long long)cm.blocks * blockDim.x;
+  for (long long i = (long long)b * blockDim.x + threadIdx.x; i < cm.m; i += nt) {
+    cm.ax[i] = cm.ax_new[i];
+    if constexpr (kSplit<T>) {
+      const T hi = cm.y_new[i], lo = cm.yn_lo[i];
+      cm.y[i] = hi;
+      cm.y_lo[i] = lo;
+      T ah = hi, al = lo;
+      if (!first) {
+        ah = cm.y_avg[i];
+        al = cm.ya_lo[i];
+        split_add(ah, al, ((hi - ah) + (lo - al)) * w);
+      }
+      cm.y_avg[i] = ah;
+      cm.ya_lo[i] = al;
+    } else {
+      const T yn = cm.y_new[i];
+      cm.y[i] = yn;
+      cm.y_avg[i] += (yn - cm.y_avg[i]) * w;
+    }
+  }
+}
+
 // A' y+ over the explicit transpose, fused with the running average of x and
 // with the next CG's start: r0 = p0 = -(qx + c + A'y+) and r0'r0 partials.
 // (The mixed path averages the displacement dx, see k_dual.)
 //
-// Adaptive step size (x_save != nullptr), after k_dual's decision and
-// k_commit_m: after an accepted step the average takes the step weight and
-// (x, Q x) are saved as the start of the next attempt; after a rejected one x
-// and Q x go back to the saved start and the CG start is formed from the
-// unchanged A'y, with no product.
+// Adaptive step size (x_save != nullptr), after k_dual's decision: after an
+// accepted step the product reads the trial y+ (y_trial), the average takes
+// the step weight and (x, Q x) are saved as the start of the next attempt,
+// while the launch's last cm.blocks blocks commit the trial into y, A x and
+// the average of y (neither side reads what the other writes); after a
+// rejected one x and Q x go back to the saved start and the CG start is
+// formed from the unchanged A'y, with no product.
 template <int G, class T>
 __global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSm<T>)
     k_atv(CsrT<T> At, const T* __restrict__ y, T* aty, T* x, T* x_avg, T* qx,
           const T* __restrict__ c, T* r, T* p, double* part_r0, unsigned int* ticket,
-          const DevState* st, T* x_save, T* qx_save) {
+          const DevState* st, T* x_save, T* qx_save, const T* __restrict__ y_trial,
+          Commit<T> cm) {
   if (!st->iter_active) return;
+  const int nb = int(gridDim.x) - cm.blocks;  // the product's blocks
+  if (int(blockIdx.x) >= nb) {
+    commit_m(cm, st, int(blockIdx.x) - nb);
+    return;
+  }
   const bool adaptive = x_save != nullptr;
   typename Acc<T>::type acc;
   if (adaptive && !st->accepted) {
-    for (long long i = grid_tid(); i < At.rows; i += grid_threads()) {
+    const long long nt = (long long)nb * blockDim.x;
+    for (long long i = grid_tid(); i < At.rows; i += nt) {
       const T xs = x_save[i], qs = qx_save[i];
       x[i] = xs;
       qx[i] = qs;
@@ -1354,14 +1423,15 @@ __global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSm<T>)
       p[i] = ri;
       acc.add_prod(ri, ri);
     }
-    store_and_finish_dot(acc, part_r0, ticket);
+    store_and_finish_dot(acc, part_r0, ticket, nb);
     return;
   }
   __shared__ T s_w;  // the average's weight, once per block
   if (threadIdx.x == 0) s_w = adaptive ? T(st->avg_w) : T(1.0 / (double)st->j);
   __syncthreads();
   const T w = s_w;
-  spmv_rows<G>(At, y, [&](int i, T s, bool lead) {
+  const T* yv = adaptive && y_trial != nullptr ? y_trial : y;
+  spmv_rows<G>(At, yv, [&](int i, T s, bool lead) {
     if (lead) {
       aty[i] = s;
       const T xi = x[i], qxi = qx[i];
@@ -1375,44 +1445,8 @@ __global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSm<T>)
         qx_save[i] = qxi;
       }
     }
-  });
-  store_and_finish_dot(acc, part_r0, ticket);
-}
-
-// Adaptive step size, after k_dual's decision: an accepted trial becomes y
-// (with its low word) and the A x cache, and enters the running average of y
-// with the step weight; a rejected one is dropped.
-template <class T>
-__global__ void __launch_bounds__(kBlock) k_commit_m(T* y, T* y_lo, const T* __restrict__ y_new,
-                                                     const T* __restrict__ yn_lo, T* ax,
-                                                     const T* __restrict__ ax_new, T* y_avg,
-                                                     T* ya_lo, int m, const DevState* st) {
-  if (!st->iter_active || !st->accepted) return;
-  __shared__ T s_w;  // the step weight, converted once per block
-  if (threadIdx.x == 0) s_w = T(st->avg_w);
-  __syncthreads();
-  const T w = s_w;
-  const bool first = st->j == 1;
-  for (long long i = grid_tid(); i < m; i += grid_threads()) {
-    ax[i] = ax_new[i];
-    if constexpr (kSplit<T>) {
-      const T hi = y_new[i], lo = yn_lo[i];
-      y[i] = hi;
-      y_lo[i] = lo;
-      T ah = hi, al = lo;
-      if (!first) {
-        ah = y_avg[i];
-        al = ya_lo[i];
-        split_add(ah, al, ((hi - ah) + (lo - al)) * w);
-      }
-      y_avg[i] = ah;
-      ya_lo[i] = al;
-    } else {
-      const T yn = y_new[i];
-      y[i] = yn;
-      y_avg[i] += (yn - y_avg[i]) * w;
-    }
-  }
+  }, nb);
+  store_and_finish_dot(acc, part_r0, ticket, nb);
 }
 
 // r0 = p0 = -(qx + c + A'y) and r0'r0 partials, for the first CG after a

@@ -367,14 +367,16 @@ qp_status validate_options(const qp_options* o) {
 
 // --------------------------------------------------------------- launches
 // Segment pass over the long rows of M for the product M v (nothing for
-// matrices without long rows).
+// matrices without long rows).  v_trial: read instead of v when the adaptive
+// step accepted its trial (the trial y before its commit).
 template <class T>
-void launch_long(qp_handle* h, const DevMat& M, const T* v) {
+void launch_long(qp_handle* h, const DevMat& M, const T* v, const T* v_trial = nullptr) {
   if (M.nlong == 0) return;
   const int wave = h->num_sms * 8;
   const int gs = std::max(1, std::min(wave, (M.nseg + kBlock / 32 - 1) / (kBlock / 32)));
   const int gl = std::max(1, std::min(wave, (M.nlong + kBlock / 32 - 1) / (kBlock / 32)));
-  k_long_segments<T><<<gs, kBlock, 0, h->stream>>>(view<T>(M), v, long_rows_of(M), seg_buf<T>(M));
+  k_long_segments<T><<<gs, kBlock, 0, h->stream>>>(view<T>(M), v, long_rows_of(M), seg_buf<T>(M),
+                                                   v_trial, h->st);
   k_long_finish<T><<<gl, kBlock, 0, h->stream>>>(long_rows_of(M), seg_buf<T>(M), long_buf<T>(M));
 }
 
@@ -444,17 +446,28 @@ template <class T>
 qp_status launch_atv(qp_handle* h) {
   VecSet<T>& v = vecs<T>(h);
   const bool ad = h->step_mode == QP_STEP_ADAPTIVE;
-  if (ad)
-    k_commit_m<T><<<h->grid_vec, kBlock, 0, h->stream>>>(v.y, v.y_lo, v.y_new, v.yn_lo, it_ax(v),
-                                                         v.ax_new, v.y_avg, v.ya_lo, h->m, h->st);
-  launch_long<T>(h, h->At, v.y);
+  // adaptive step: the commit of an accepted trial rides in the same launch
+  // (its last blocks), and the product reads the trial y directly
+  Commit<T> cm;
+  if (ad) {
+    cm.y = v.y;
+    cm.y_lo = v.y_lo;
+    cm.y_new = v.y_new;
+    cm.yn_lo = v.yn_lo;
+    cm.ax = it_ax(v);
+    cm.ax_new = v.ax_new;
+    cm.y_avg = v.y_avg;
+    cm.ya_lo = v.ya_lo;
+    cm.m = int(h->m);
+    cm.blocks = std::max(1, std::min(h->num_sms * 2, (int(h->m) + 4 * kBlock - 1) / (4 * kBlock)));
+  }
+  launch_long<T>(h, h->At, v.y, ad ? v.y_new : nullptr);
   return dispatch_g(lanes<T>(h->At), [&](auto g) {
     constexpr int G = decltype(g)::value;
-    k_atv<G, T><<<h->grid_n, kBlock, 0, h->stream>>>(view<T>(h->At), v.y, v.aty, it_x(v),
-                                                     it_x_avg(v), v.qx, v.c, v.r, v.p,
-                                                     h->part_r0, h->ticket, h->st,
-                                                     ad ? v.x_save : nullptr,
-                                                     ad ? v.qx_save : nullptr);
+    k_atv<G, T><<<h->grid_n + cm.blocks, kBlock, 0, h->stream>>>(
+        view<T>(h->At), v.y, v.aty, it_x(v), it_x_avg(v), v.qx, v.c, v.r, v.p, h->part_r0,
+        h->ticket, h->st, ad ? v.x_save : nullptr, ad ? v.qx_save : nullptr,
+        ad ? v.y_new : nullptr, cm);
   });
 }
 
@@ -543,7 +556,7 @@ void launch_prepare(qp_handle* h) {
 }
 
 // One inner iteration (with the adaptive step size: one attempt, the step
-// test in k_dual's last block and the commit in k_commit_m and k_atv).
+// test in k_dual's last block and the commit in k_atv).
 template <class T>
 qp_status launch_iteration(qp_handle* h, bool coop) {
   QP_TRY(launch_cg<T>(h, coop));
