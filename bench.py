@@ -533,8 +533,8 @@ BATCH_WORKLOAD = {
     "workload": "4096 portfolio QPs: n ~ U{20..400}, k = n/10 factors, Q = F F' + diag U[0.01,0.1], "
                 "F ~ N(0, 1/k); budget equality, long-only and U{5..20} sector-cap rows; "
                 "c = -mu, mu ~ N(0.05, 0.02)",
-    "count": 4096, "seed": 0, "tol": 1e-4, "precision": "mixed (FP32 data and products, FP64 "
-    "vectors, reductions and scalars; relKKT on the FP64 data)",
+    "count": 4096, "seed": 0, "tol": 1e-4, "precision": "mixed (FP32 data, products and attempt "
+    "vectors; FP64 iterates, averages, block totals and scalars; relKKT on the FP64 data)",
 }
 BATCH_METRIC = ("time to 1e-4 rel. KKT for 4096 portfolio QPs (batched PDHCG, one launch) "
                 "vs plain FP64 GPU PDHCG one instance at a time")
@@ -656,7 +656,7 @@ def run_batch_bench(args):
     out = {
         "metric": BATCH_METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 vectors and reductions)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 iterates and block totals)",
         "data": "synthetic",
         "config": dict(BATCH_WORKLOAD, step=args.step,
                        solved=int(sum(r["termination"] == 0 for r in res)),

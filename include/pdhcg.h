@@ -460,9 +460,12 @@ qp_status qp_csr_transpose(int32_t rows, int32_t cols, const int32_t* rowptr,
  * (Algorithm 1 with the Section 4 heuristics, the same readings as
  * qp_solve).  Each instance has Q = F F' + diag(qd), the low-rank-plus-
  * diagonal form whose products cost 2nk (the P'P acceleration of Section
- * 5.2).  An instance's vectors (9 n + 6 m + k doubles) live in shared
- * memory when the largest instance fits one block (about 225 KB on B300),
- * else in a per-block slice of global memory.  No diagonal scaling.
+ * 5.2).  An instance's vectors live in shared memory when the largest
+ * instance of its size bin fits one block (about 225 KB on B300), else in a
+ * per-block slice of global memory: in FP64 (9 n + 6 m + k doubles, 11 n +
+ * 8 m + k with the adaptive step size), or in mixed precision FP64 iterates,
+ * averages and restart points with FP32 attempt vectors (7 n + 5.5 m + 1.5 k
+ * doubles).  No diagonal scaling.
  */
 typedef struct qp_batch qp_batch;
 

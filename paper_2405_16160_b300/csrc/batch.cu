@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pdhcg.h"
@@ -95,9 +96,10 @@ struct BatchBin {
   int32_t* order = nullptr;  // instance ids (device)
   int max_n = 1, max_m = 1, max_k = 1;
   // vector space of one block and its dynamic shared memory (0: global
-  // workspace), for the fixed [0] and the adaptive [1] step size
-  size_t block_doubles[2] = {0, 0};
-  size_t smem[2] = {0, 0};
+  // workspace), for FP64 [0] and mixed [1] precision, each with the fixed
+  // [0] and the adaptive [1] step size
+  size_t block_doubles[2][2] = {{0, 0}, {0, 0}};
+  size_t smem[2][2] = {{0, 0}, {0, 0}};
   int threads = 128;
   double* ws = nullptr;      // global workspace when the vectors do not fit shared memory
   size_t ws_doubles = 0;     // capacity of ws
@@ -122,10 +124,12 @@ struct qp_batch {
   double *F64 = nullptr, *qd64 = nullptr, *c = nullptr, *b = nullptr;
   double *Aval64 = nullptr, *Tval64 = nullptr;
   float *F32 = nullptr, *qd32 = nullptr, *Aval32 = nullptr, *Tval32 = nullptr;
+  float *c32 = nullptr, *b32 = nullptr;
   int32_t *Arp = nullptr, *Acol = nullptr, *Trp = nullptr, *Tcol = nullptr;
   int32_t *Along = nullptr, *Tlong = nullptr;
   double *x0 = nullptr, *y0 = nullptr, *x_out = nullptr, *y_out = nullptr;
   double *lo = nullptr, *hi = nullptr;  // packed variable bounds (allocated on first use)
+  float *lo32 = nullptr, *hi32 = nullptr;  // and their FP32 copies
   BatchResult* res = nullptr;
   bool warm_set = false, solved = false, bounded = false;
   std::vector<BatchResult> h_res;
@@ -178,13 +182,19 @@ qp_status bupload(qp_batch* h, T** dst, const std::vector<T>& src) {
   return QP_OK;
 }
 
-qp_status to_float(qp_batch* h, const double* in, float** out, size_t n) {
-  BTRY(balloc(h, reinterpret_cast<void**>(out), n * sizeof(float)));
+// out = FP32 copy of in (n values), on the handle's stream.
+qp_status convert_float(qp_batch* h, const double* in, float* out, size_t n) {
   if (n > 0) {
     const int grid = int(std::min<size_t>((n + 255) / 256, size_t(h->num_sms) * 8));
-    k_to_float<<<grid, 256, 0, h->stream>>>(in, *out, (long long)n);
+    k_to_float<<<grid, 256, 0, h->stream>>>(in, out, (long long)n);
+    BCUDA(cudaGetLastError());
   }
   return QP_OK;
+}
+
+qp_status to_float(qp_batch* h, const double* in, float** out, size_t n) {
+  BTRY(balloc(h, reinterpret_cast<void**>(out), n * sizeof(float)));
+  return convert_float(h, in, *out, n);
 }
 
 qp_status begin(qp_batch* h) {
@@ -211,7 +221,8 @@ template <class V, int NT>
 qp_status launch_batch_nt(qp_batch* h, BatchBin& bin, BatchData<V> B) {
   auto kern = k_batch<V, NT>;
   const int ad = B.opt.step_mode == kStepAdaptive ? 1 : 0;
-  const size_t smem = bin.smem[ad], bd = bin.block_doubles[ad];
+  const int mx = std::is_same<V, float>::value ? 1 : 0;
+  const size_t smem = bin.smem[mx][ad], bd = bin.block_doubles[mx][ad];
   BCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   int occ = 0;
   BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
@@ -262,6 +273,8 @@ BatchData<V> batch_data(qp_batch* h, const BatchBin& bin, const V* F, const V* q
   B.qd64 = h->qd64;
   B.c = h->c;
   B.b = h->b;
+  B.c32 = h->c32;
+  B.b32 = h->b32;
   B.Arp = h->Arp;
   B.Acol = h->Acol;
   B.Aval = Av;
@@ -277,6 +290,8 @@ BatchData<V> batch_data(qp_batch* h, const BatchBin& bin, const V* F, const V* q
   B.warm = (o->warm_start == 1 && h->warm_set) ? 1 : 0;
   B.lo = h->bounded ? h->lo : nullptr;
   B.hi = h->bounded ? h->hi : nullptr;
+  B.lo32 = h->bounded ? h->lo32 : nullptr;
+  B.hi32 = h->bounded ? h->hi32 : nullptr;
   B.x_out = h->x_out;
   B.y_out = h->y_out;
   B.res = h->res;
@@ -448,9 +463,13 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
       bin.max_k = std::max(bin.max_k, desc[size_t(id)].k);
     }
     for (int ad = 0; ad < 2; ++ad) {
-      bin.block_doubles[ad] = batch_block_doubles(bin.max_n, bin.max_m, bin.max_k, true, ad != 0);
-      const size_t need = bin.block_doubles[ad] * sizeof(double);
-      bin.smem[ad] = need + static_smem <= size_t(smem_optin) ? need : 0;
+      bin.block_doubles[0][ad] =
+          batch_block_doubles(bin.max_n, bin.max_m, bin.max_k, false, ad != 0);
+      bin.block_doubles[1][ad] = batch_block_doubles_mixed(bin.max_n, bin.max_m, bin.max_k);
+      for (int mx = 0; mx < 2; ++mx) {
+        const size_t need = bin.block_doubles[mx][ad] * sizeof(double);
+        bin.smem[mx][ad] = need + static_smem <= size_t(smem_optin) ? need : 0;
+      }
     }
     bin.threads = default_threads(bin.max_n);
     BCUDA(cudaStreamCreateWithFlags(&bin.stream, cudaStreamNonBlocking));
@@ -505,6 +524,8 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
   BTRY(to_float(h, h->qd64, &h->qd32, qd.size()));
   BTRY(to_float(h, h->Aval64, &h->Aval32, Av.size()));
   BTRY(to_float(h, h->Tval64, &h->Tval32, Tv.size()));
+  BTRY(to_float(h, h->c, &h->c32, c.size()));
+  BTRY(to_float(h, h->b, &h->b32, b.size()));
   for (double** v : {&h->x0, &h->x_out}) {
     BTRY(balloc(h, reinterpret_cast<void**>(v), size_t(h->n_total) * sizeof(double)));
     BCUDA(cudaMemsetAsync(*v, 0, size_t(h->n_total) * sizeof(double), h->stream));
@@ -700,6 +721,10 @@ qp_status qp_batch_set_bounds(qp_batch* h, const double* lo, const double* hi) {
                           h->stream));
     BCUDA(cudaMemcpyAsync(h->hi, u.data(), N * sizeof(double), cudaMemcpyHostToDevice,
                           h->stream));
+    if (!h->lo32) BTRY(balloc(h, reinterpret_cast<void**>(&h->lo32), N * sizeof(float)));
+    if (!h->hi32) BTRY(balloc(h, reinterpret_cast<void**>(&h->hi32), N * sizeof(float)));
+    BTRY(convert_float(h, h->lo, h->lo32, N));
+    BTRY(convert_float(h, h->hi, h->hi32, N));
     BCUDA(cudaStreamSynchronize(h->stream));  // the staging vectors die here
     h->bounded = true;
   }

@@ -60,6 +60,8 @@ struct BatchData {
   const double* qd64;
   const double* c;
   const double* b;
+  const float* c32;  // FP32 copies of c and b (mixed precision)
+  const float* b32;
   const int32_t* Arp;
   const int32_t* Acol;
   const V* Aval;
@@ -77,6 +79,8 @@ struct BatchData {
   // every x-step is the Section 4 BB projected gradient
   const double* lo;
   const double* hi;
+  const float* lo32;  // their FP32 copies (mixed precision)
+  const float* hi32;
   double* x_out;
   double* y_out;
   BatchResult* res;
@@ -121,14 +125,14 @@ __device__ __forceinline__ V warp_sum_v(V v) {
 
 // out = M v: a thread per short row (entries in order), a warp per long row.
 // The caller synchronises before reading out.
-template <class V, int NT>
-__device__ void cta_spmv(const LocalCsr<V>& M, const V* v, double* out) {
+template <class V, int NT, class O = double>
+__device__ void cta_spmv(const LocalCsr<V>& M, const V* v, O* out) {
   for (int i = threadIdx.x; i < M.rows; i += NT) {
     const int b = M.rp[i], e = M.rp[i + 1];
     if (e - b > kBatchLongRow) continue;
     V s = V(0);
     for (int k = b; k < e; ++k) s = fma(M.val[k], v[M.col[k]], s);
-    out[i] = double(s);
+    out[i] = O(s);
   }
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int t = w; t < M.nlong; t += NT / 32) {
@@ -136,7 +140,7 @@ __device__ void cta_spmv(const LocalCsr<V>& M, const V* v, double* out) {
     V s = V(0);
     for (int k = M.rp[i] + lane; k < M.rp[i + 1]; k += 32) s = fma(M.val[k], v[M.col[k]], s);
     s = warp_sum_v(s);
-    if (lane == 0) out[i] = double(s);
+    if (lane == 0) out[i] = O(s);
   }
 }
 
@@ -185,9 +189,8 @@ __device__ void cta_dual(const LocalCsr<V>& A, const V* xv, const double* b, int
 // kSyncOut = false one barrier, and out[j] is ready for thread j mod NT only
 // (the CG and BB steps read it that way, and a block reduction separates it
 // from the next product's writes of t).
-template <class V, int NT, bool kSyncOut = true>
-__device__ void cta_qprod(const V* F, const V* qd, int n, int k, const V* p, V* t,
-                          double* out) {
+template <class V, int NT, bool kSyncOut = true, class O = double>
+__device__ void cta_qprod(const V* F, const V* qd, int n, int k, const V* p, V* t, O* out) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int l = w; l < k; l += NT / 32) {
     const V* Fl = F + size_t(l) * n;
@@ -200,7 +203,7 @@ __device__ void cta_qprod(const V* F, const V* qd, int n, int k, const V* p, V* 
   for (int j = threadIdx.x; j < n; j += NT) {
     V s = qd[j] * p[j];
     for (int l = 0; l < k; ++l) s = fma(F[size_t(l) * n + j], t[l], s);
-    out[j] = double(s);
+    out[j] = O(s);
   }
   if constexpr (kSyncOut) __syncthreads();
 }
@@ -319,11 +322,84 @@ __device__ __forceinline__ double cta_sum2(double v0, double v1, double* red, do
   return s[0];
 }
 
-// One instance, solved by the whole block.
-template <class V, int NT>
-__device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevState& st,
-                                double* red) {
-  constexpr bool kShadow = !std::is_same<V, double>::value;
+// FP64 products of the data with (x, y) and with the averages (x~, y~),
+// and F'x: the evaluation's scratch (4n + 2m + k doubles).
+struct EvalScratch {
+  double *Qx, *Qxa, *Aty, *Atya, *Ax, *Axa, *t;
+};
+
+// relKKT of (x, y) and of (x~, y~) with the FP64 data (Section 4), then the
+// termination / restart decision (control_decide); every thread returns
+// after it.
+template <int NT>
+__device__ void batch_evaluate(const double* F64, const double* qd64, const LocalCsr<double>& A64,
+                               const LocalCsr<double>& At64, const double* c, const double* b,
+                               const double* lo, const double* hi, const BatchDesc& d,
+                               const double* x, const double* xa, const double* y,
+                               const double* ya, const EvalScratch& e, DevState& st, double* red,
+                               int mode) {
+  const int n = d.n, m = d.m, k = d.k, tid = threadIdx.x;
+  cta_qprod<double, NT>(F64, qd64, n, k, x, e.t, e.Qx);    // Q x
+  cta_qprod<double, NT>(F64, qd64, n, k, xa, e.t, e.Qxa);  // Q x~
+  cta_spmv<double, NT>(At64, y, e.Aty);                    // A'y
+  cta_spmv<double, NT>(At64, ya, e.Atya);                  // A'y~
+  cta_spmv<double, NT>(A64, x, e.Ax);                      // A x
+  cta_spmv<double, NT>(A64, xa, e.Axa);                    // A x~
+  __syncthreads();
+  double s4[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, m7[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int j = tid; j < n; j += NT) {
+    const double cj = c[j], q1 = e.Qx[j], q2 = e.Qxa[j];
+    const double g1 = q1 + e.Aty[j] + cj, g2 = q2 + e.Atya[j] + cj;
+    double l1 = 0.0, l2 = 0.0;
+    if (lo) {  // reduced costs of the bounds
+      l1 = reduced_cost(g1, lo[j], hi[j]);
+      l2 = reduced_cost(g2, lo[j], hi[j]);
+      s4[4] += bound_term(l1, lo[j], hi[j]);
+      s4[5] += bound_term(l2, lo[j], hi[j]);
+    }
+    m7[0] = fmax(m7[0], fabs(g1 - l1));
+    m7[1] = fmax(m7[1], fabs(q1));
+    m7[2] = fmax(m7[2], fabs(e.Aty[j]));
+    s4[0] = fma(x[j], q1, s4[0]);
+    s4[1] = fma(cj, x[j], s4[1]);
+    m7[3] = fmax(m7[3], fabs(g2 - l2));
+    m7[4] = fmax(m7[4], fabs(q2));
+    m7[5] = fmax(m7[5], fabs(e.Atya[j]));
+    s4[2] = fma(xa[j], q2, s4[2]);
+    s4[3] = fma(cj, xa[j], s4[3]);
+    m7[6] = fmax(m7[6], fabs(cj));
+  }
+  cta_reduce<NT, 6, 7>(s4, m7, red);
+  double s2[2] = {0.0, 0.0}, m5[5] = {0, 0, 0, 0, 0};
+  for (int i = tid; i < m; i += NT) {
+    const double bi = b[i], dd = e.Ax[i] - bi, da = e.Axa[i] - bi;
+    const double vc = i < d.m_eq ? fabs(dd) : (dd > 0.0 ? dd : 0.0);
+    const double va = i < d.m_eq ? fabs(da) : (da > 0.0 ? da : 0.0);
+    m5[0] = fmax(m5[0], vc);
+    m5[1] = fmax(m5[1], fabs(e.Ax[i]));
+    s2[0] = fma(bi, y[i], s2[0]);
+    m5[2] = fmax(m5[2], va);
+    m5[3] = fmax(m5[3], fabs(e.Axa[i]));
+    s2[1] = fma(bi, ya[i], s2[1]);
+    m5[4] = fmax(m5[4], fabs(bi));
+  }
+  cta_reduce<NT, 2, 5>(s2, m5, red);
+  if (tid == 0) {
+    const KktTerms kc = kkt_from(m5[0], m5[1], m5[4], m7[0], m7[1], m7[2], m7[6], s4[0], s4[1],
+                                 s2[0], s4[4]);
+    const KktTerms ka = kkt_from(m5[2], m5[3], m5[4], m7[3], m7[4], m7[5], m7[6], s4[2], s4[3],
+                                 s2[1], s4[5]);
+    control_decide(&st, kc, ka, mode);
+  }
+  __syncthreads();
+}
+
+// One instance, solved by the whole block in FP64 (data, products, vectors
+// and scalars).
+template <int NT>
+__device__ void batch_solve_fp64(const BatchData<double>& B, int id, double* sm, DevState& st,
+                                 double* red) {
+  using V = double;
   const BatchDesc d = B.desc[id];
   const int n = d.n, m = d.m, k = d.k, tid = threadIdx.x;
   // the FP64 scalars of the method, derived by thread 0 and read by all
@@ -352,21 +428,12 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
   double* yn = B.adaptive ? qxs + B.max_n : xs;
   double* axn = B.adaptive ? yn + B.max_m : xs;
   double* t = B.adaptive ? axn + B.max_m : xs;
-  // value-type copies read by the products (the FP64 vectors themselves
-  // when V is double)
-  V* pv = reinterpret_cast<V*>(p);
-  V* xv = reinterpret_cast<V*>(x);
-  V* yv = reinterpret_cast<V*>(y);
-  V* uv = reinterpret_cast<V*>(axa);
-  V* tv = reinterpret_cast<V*>(t);
-  if constexpr (kShadow) {
-    V* f = reinterpret_cast<V*>(t + B.max_k + 16);
-    pv = f;
-    xv = pv + B.max_n;
-    yv = xv + B.max_n;
-    uv = yv + B.max_m;
-    tv = uv + B.max_m;
-  }
+  // the vectors the products read
+  V* pv = p;
+  V* xv = x;
+  V* yv = y;
+  V* uv = axa;
+  V* tv = t;
   // instance data
   const double* c = B.c + d.off_n;
   const double* b = B.b + d.off_m;
@@ -401,14 +468,12 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
     x[j] = v;
     x0[j] = v;
     xa[j] = 0.0;
-    if constexpr (kShadow) xv[j] = V(v);
   }
   for (int i = tid; i < m; i += NT) {
     const double v = B.warm ? B.y0[d.off_m + i] : 0.0;
     y[i] = v;
     y0[i] = v;
     ya[i] = 0.0;
-    if constexpr (kShadow) yv[i] = V(v);
   }
   if (tid == 0) {
     st.opt = B.opt;
@@ -437,10 +502,6 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
     for (int it = 0; it < B.power_iters; ++it) {
       cta_spmv<V, NT>(A, pv, axa);  // u = A v
       __syncthreads();
-      if constexpr (kShadow) {
-        for (int i = tid; i < m; i += NT) uv[i] = V(axa[i]);
-        __syncthreads();
-      }
       cta_spmv<V, NT>(At, uv, q);  // w = A'u
       __syncthreads();
       double ww = 0.0;
@@ -462,60 +523,9 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
   }
 
   // ---- relKKT of (x, y) and (x~, y~) with the FP64 data (Section 4)
+  const EvalScratch es{r, p, q, wv, axe, axa, t};
   auto evaluate = [&](int mode) {
-    cta_qprod<double, NT>(F64, qd64, n, k, x, t, r);   // Q x
-    cta_qprod<double, NT>(F64, qd64, n, k, xa, t, p);  // Q x~
-    cta_spmv<double, NT>(At64, y, q);                  // A'y
-    cta_spmv<double, NT>(At64, ya, wv);                // A'y~
-    cta_spmv<double, NT>(A64, x, axe);                 // A x
-    cta_spmv<double, NT>(A64, xa, axa);                // A x~
-    __syncthreads();
-    double s4[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, m7[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int j = tid; j < n; j += NT) {
-      const double cj = c[j], q1 = r[j], q2 = p[j];
-      const double g1 = q1 + q[j] + cj, g2 = q2 + wv[j] + cj;
-      double l1 = 0.0, l2 = 0.0;
-      if (lo) {  // reduced costs of the bounds
-        l1 = reduced_cost(g1, lo[j], hi[j]);
-        l2 = reduced_cost(g2, lo[j], hi[j]);
-        s4[4] += bound_term(l1, lo[j], hi[j]);
-        s4[5] += bound_term(l2, lo[j], hi[j]);
-      }
-      m7[0] = fmax(m7[0], fabs(g1 - l1));
-      m7[1] = fmax(m7[1], fabs(q1));
-      m7[2] = fmax(m7[2], fabs(q[j]));
-      s4[0] = fma(x[j], q1, s4[0]);
-      s4[1] = fma(cj, x[j], s4[1]);
-      m7[3] = fmax(m7[3], fabs(g2 - l2));
-      m7[4] = fmax(m7[4], fabs(q2));
-      m7[5] = fmax(m7[5], fabs(wv[j]));
-      s4[2] = fma(xa[j], q2, s4[2]);
-      s4[3] = fma(cj, xa[j], s4[3]);
-      m7[6] = fmax(m7[6], fabs(cj));
-    }
-    cta_reduce<NT, 6, 7>(s4, m7, red);
-    double s2[2] = {0.0, 0.0}, m5[5] = {0, 0, 0, 0, 0};
-    for (int i = tid; i < m; i += NT) {
-      const double bi = b[i], dd = axe[i] - bi, da = axa[i] - bi;
-      const double vc = i < d.m_eq ? fabs(dd) : (dd > 0.0 ? dd : 0.0);
-      const double va = i < d.m_eq ? fabs(da) : (da > 0.0 ? da : 0.0);
-      m5[0] = fmax(m5[0], vc);
-      m5[1] = fmax(m5[1], fabs(axe[i]));
-      s2[0] = fma(bi, y[i], s2[0]);
-      m5[2] = fmax(m5[2], va);
-      m5[3] = fmax(m5[3], fabs(axa[i]));
-      s2[1] = fma(bi, ya[i], s2[1]);
-      m5[4] = fmax(m5[4], fabs(bi));
-    }
-    cta_reduce<NT, 2, 5>(s2, m5, red);
-    if (tid == 0) {
-      const KktTerms kc = kkt_from(m5[0], m5[1], m5[4], m7[0], m7[1], m7[2], m7[6], s4[0], s4[1],
-                                   s2[0], s4[4]);
-      const KktTerms ka = kkt_from(m5[2], m5[3], m5[4], m7[3], m7[4], m7[5], m7[6], s4[2], s4[3],
-                                   s2[1], s4[5]);
-      control_decide(&st, kc, ka, mode);
-    }
-    __syncthreads();
+    batch_evaluate<NT>(F64, qd64, A64, At64, c, b, lo, hi, d, x, xa, y, ya, es, st, red, mode);
   };
   // r0 = p0 = -(Qx + c + A'y): the CG start of the next iteration
   auto prepare = [&]() -> double {
@@ -524,7 +534,6 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
       const double v = -(qx[j] + c[j] + aty[j]);
       r[j] = v;
       p[j] = v;
-      if constexpr (kShadow) pv[j] = V(v);
       rr = fma(v, v, rr);
     }
     return cta_sum1<NT>(rr, red);
@@ -579,10 +588,6 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
             const double sj = xn - xj;
             p[j] = sj;
             x[j] = xn;
-            if constexpr (kShadow) {
-              pv[j] = V(sj);
-              xv[j] = V(xn);
-            }
             ss = fma(sj, sj, ss);
           }
           cta_sum_t0<NT>(ss, red, [&](double t) { s_sc[3] = t; });
@@ -633,7 +638,6 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
           const double pj = p[j], qpj = q[j];
           const double xn = __dadd_rn(x[j], __dmul_rn(alpha, pj));
           x[j] = xn;
-          if constexpr (kShadow) xv[j] = V(xn);
           qx[j] = __dadd_rn(qx[j], __dmul_rn(alpha, qpj));
           const double rj = __dsub_rn(r[j], __dmul_rn(alpha, qpj + pj * inv_tau));
           r[j] = rj;
@@ -653,7 +657,6 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         for (int j = tid; j < n; j += NT) {
           const double pn = __dadd_rn(r[j], __dmul_rn(beta, p[j]));
           p[j] = pn;
-          if constexpr (kShadow) pv[j] = V(pn);
         }
         __syncthreads();
       }
@@ -712,7 +715,6 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
           for (int j = tid; j < n; j += NT) {
             x[j] = xs[j];
             qx[j] = qxs[j];
-            if constexpr (kShadow) xv[j] = V(xs[j]);
           }
         }
         __syncthreads();
@@ -743,7 +745,6 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         dx = fma(e, e, dx);
         x0[j] = cand;
         x[j] = cand;
-        if constexpr (kShadow) xv[j] = V(cand);
       }
       for (int i = tid; i < m; i += NT) {
         const double cand = pending == 2 ? ya[i] : y[i];
@@ -751,7 +752,6 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
         dy = fma(e, e, dy);
         y0[i] = cand;
         y[i] = cand;
-        if constexpr (kShadow) yv[i] = V(cand);
       }
       double dy2;
       const double dx2 = cta_sum2<NT>(dx, dy, red, &dy2);
@@ -765,6 +765,502 @@ __device__ void batch_solve_one(const BatchData<V>& B, int id, double* sm, DevSt
     cta_qprod<V, NT>(F, qd, n, k, xv, tv, qx);
     rr0 = prepare();
     save_start();
+    __syncthreads();
+  }
+
+  // ---- the returned iterate and its statistics
+  const bool avg = st.returned_avg != 0;
+  for (int j = tid; j < n; j += NT) B.x_out[d.off_n + j] = avg ? xa[j] : x[j];
+  for (int i = tid; i < m; i += NT) B.y_out[d.off_m + i] = avg ? ya[i] : y[i];
+  if (tid == 0) {
+    BatchResult& o = B.res[id];
+    o.termination = st.done > 0 ? st.done - 1 : 1;
+    o.returned_avg = st.returned_avg;
+    o.iterations = st.k_total;
+    o.cg_steps = st.cg_total;
+    o.restarts = st.n_restarts;
+    for (int s = 0; s < 6; ++s) o.kkt[s] = st.kkt_ret[s];
+    o.eta = st.eta;
+    o.omega = st.omega;
+    o.norm_A = st.norm_A;
+    o.attempts = st.attempts;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ mixed mode
+// Vector space of one block of the mixed-precision solve, in doubles.  FP64:
+// the iterates x and y, their running averages and the restart points
+// (3n + 3m).  The rest is one region used two ways.  During the iterations it
+// holds the adaptive step's trial y (FP64, m), F't's FP64 copy (k + 16) and
+// the FP32 working vectors: x for the products, r, p, q, the tracked Q x,
+// A'y, and the attempt's moves of x and of Q x (8n); y for the products, the
+// A x cache and the trial A x (3m); F'p (k + 16).  During an evaluation it
+// holds the FP64 products of (x, y) and of the averages (4n + 2m) and F'x
+// (k + 16); the FP32 vectors are formed again from the FP64 iterates after
+// it.
+inline size_t batch_block_doubles_mixed(int max_n, int max_m, int max_k) {
+  const size_t n = size_t(max_n), m = size_t(max_m), k = size_t(max_k) + 16;
+  const size_t iter = m + k + (8 * n + 3 * m + k + 1) / 2;
+  const size_t eval = 4 * n + 2 * m + k;
+  return 3 * n + 3 * m + (iter > eval ? iter : eval);
+}
+
+// q = (F F' + diag(qd)) p in FP32 as cta_qprod<float, NT, false, float>,
+// returning p'(Q + I/tau)p = ||F'p||^2 + sum (qd_j + 1/tau) p_j^2 to every
+// thread: the warps that form t = F'p form the diagonal sum as one more
+// column, and after the product's one barrier every warp adds the squares of
+// t (FP64) with the same lanes and shuffle tree.  The mixed BB step's product.
+template <int NT>
+__device__ double cta_qprod_pmp_f(const float* F, const float* qd, int n, int k, const float* p,
+                                  float inv_tau, float* t, double* td, float* out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int l = w; l <= k; l += NT / 32) {
+    float s = 0.f;
+    if (l < k) {
+      const float* Fl = F + size_t(l) * n;
+      for (int j = lane; j < n; j += 32) s = fmaf(Fl[j], p[j], s);
+    } else {
+      for (int j = lane; j < n; j += 32) s = fmaf((qd[j] + inv_tau) * p[j], p[j], s);
+    }
+    s = warp_sum_v(s);
+    if (lane == 0) {
+      if (l < k) t[l] = s;
+      td[l] = double(s);
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += NT) {
+    float s = qd[j] * p[j];
+    for (int l = 0; l < k; ++l) s = fmaf(F[size_t(l) * n + j], t[l], s);
+    out[j] = s;
+  }
+  double tt = 0.0;
+  for (int l = lane; l < k; l += 32) tt = fma(td[l], td[l], tt);
+  return td[k] + warp_sum(tt);
+}
+
+// The mixed dual step fused into A x+: the move sigma (2 (A x+)_i - (A x)_i -
+// b_i) in FP32, added to the FP64 y_i and projected.  With the adaptive step
+// size (yn != nullptr) the result is a trial: y+ and A x+ go to yn and axn.
+template <int NT>
+__device__ void cta_dual_mixed(const LocalCsr<float>& A, const float* xv, const float* b,
+                               int m_eq, float sigma, double w, double* y, float* yv, float* ax,
+                               double* ya, double* yn = nullptr, float* axn = nullptr) {
+  auto row = [&](int i, float s) {
+    const float mv = sigma * (2.f * s - ax[i] - b[i]);
+    double v = y[i] + double(mv);
+    if (i >= m_eq && v < 0.0) v = 0.0;
+    if (yn) {
+      yn[i] = v;
+      axn[i] = s;
+      return;
+    }
+    y[i] = v;
+    yv[i] = float(v);
+    ax[i] = s;
+    ya[i] += (v - ya[i]) * w;
+  };
+  for (int i = threadIdx.x; i < A.rows; i += NT) {
+    const int b0 = A.rp[i], e = A.rp[i + 1];
+    if (e - b0 > kBatchLongRow) continue;
+    float s = 0.f;
+    for (int k = b0; k < e; ++k) s = fmaf(A.val[k], xv[A.col[k]], s);
+    row(i, s);
+  }
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = wp; t < A.nlong; t += NT / 32) {
+    const int i = A.longr[t];
+    float s = 0.f;
+    for (int k = A.rp[i] + lane; k < A.rp[i + 1]; k += 32) s = fmaf(A.val[k], xv[A.col[k]], s);
+    s = warp_sum_v(s);
+    if (lane == 0) row(i, s);
+  }
+}
+
+// One instance in mixed precision, solved by the whole block.  The data of
+// the iterations (F, qd, A, A', c, b and the bounds) and every vector of an
+// attempt are FP32: the CG and BB steps run on the FP32 pipe alone (B300's
+// FP64 pipe is 1/58 of it), with per-thread FP32 partial sums whose block
+// totals are FP64.  x and y, their averages and the restart points stay FP64:
+// an attempt moves x by the FP32 displacement dx it accumulates (x += dx
+// once, when the attempt is kept), so the iterates carry no FP32 rounding
+// from step to step.  Every evaluation uses the FP64 data and iterates
+// (batch_evaluate), as the FP64 solve does, so termination is decided on the
+// problem as given.  The method and its decisions are those of
+// batch_solve_fp64.
+template <int NT>
+__device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm, DevState& st,
+                                  double* red) {
+  const BatchDesc d = B.desc[id];
+  const int n = d.n, m = d.m, k = d.k, tid = threadIdx.x;
+  const int Nn = B.max_n, Mm = B.max_m, Kk = B.max_k + 16;
+  // FP64 scalars derived by thread 0 (cta_sum_t0) and their FP32 copies;
+  // s_flag: 0 go on, 1 stop, 2 numerical error
+  __shared__ double s_sc[6];  // tau, 1/tau, eps, r'r (or s's), alpha or 1/alpha, beta
+  __shared__ float s_f[3];    // 1/tau, alpha or 1/alpha, beta
+  __shared__ int s_flag;
+  double* x = sm;
+  double* xa = x + Nn;   // average
+  double* x0 = xa + Nn;  // restart point
+  double* y = x0 + Nn;
+  double* ya = y + Mm;
+  double* y0 = ya + Mm;
+  double* U = y0 + Mm;
+  // the iterations' view of U
+  double* yn = U;       // trial y (adaptive step)
+  double* td = U + Mm;  // F'p in FP64 (BB step)
+  float* xv = reinterpret_cast<float*>(td + Kk);
+  float* r = xv + Nn;
+  float* p = r + Nn;
+  float* q = p + Nn;
+  float* qx = q + Nn;   // tracked Q x
+  float* aty = qx + Nn;
+  float* dx = aty + Nn;  // the attempt's move of x
+  float* dq = dx + Nn;   // and of Q x
+  float* yv = dq + Nn;
+  float* ax = yv + Mm;   // A x cache
+  float* axn = ax + Mm;  // trial A x
+  float* t = axn + Mm;   // F'p
+  // the evaluation's view of U
+  const EvalScratch es{U, U + Nn, U + 2 * Nn, U + 3 * Nn, U + 4 * Nn, U + 4 * Nn + Mm,
+                       U + 4 * Nn + 2 * Mm};
+  // instance data
+  const double* c = B.c + d.off_n;
+  const double* b = B.b + d.off_m;
+  const float* c32 = B.c32 + d.off_n;
+  const float* b32 = B.b32 + d.off_m;
+  const float* F = B.F + d.off_F;
+  const float* qd = B.qd + d.off_n;
+  const double* F64 = B.F64 + d.off_F;
+  const double* qd64 = B.qd64 + d.off_n;
+  const LocalCsr<float> A{B.Arp + d.off_Arp, B.Acol + d.off_Ann, B.Aval + d.off_Ann, m,
+                          B.Along + d.off_Along, d.n_Along};
+  const LocalCsr<float> At{B.Trp + d.off_Trp, B.Tcol + d.off_Tnn, B.Tval + d.off_Tnn, n,
+                           B.Tlong + d.off_Tlong, d.n_Tlong};
+  const LocalCsr<double> A64{A.rp, A.col, B.Aval64 + d.off_Ann, m, A.longr, A.nlong};
+  const LocalCsr<double> At64{At.rp, At.col, B.Tval64 + d.off_Tnn, n, At.longr, At.nlong};
+
+  const double* lo = nullptr;
+  const double* hi = nullptr;
+  const float* lo32 = nullptr;
+  const float* hi32 = nullptr;
+  if (B.lo) {
+    bool fin = false;
+    for (int j = tid; j < n; j += NT)
+      fin = fin || isfinite(B.lo[d.off_n + j]) || isfinite(B.hi[d.off_n + j]);
+    if (__syncthreads_or(fin)) {
+      lo = B.lo + d.off_n;
+      hi = B.hi + d.off_n;
+      lo32 = B.lo32 + d.off_n;
+      hi32 = B.hi32 + d.off_n;
+    }
+  }
+  // ---- start: x = x0 (warm) or 0 (projected into the box), empty averages
+  for (int j = tid; j < n; j += NT) {
+    double v = B.warm ? B.x0[d.off_n + j] : 0.0;
+    if (lo) v = fmin(fmax(v, lo[j]), hi[j]);
+    x[j] = v;
+    x0[j] = v;
+    xa[j] = 0.0;
+  }
+  for (int i = tid; i < m; i += NT) {
+    const double v = B.warm ? B.y0[d.off_m + i] : 0.0;
+    y[i] = v;
+    y0[i] = v;
+    ya[i] = 0.0;
+  }
+  if (tid == 0) {
+    st.opt = B.opt;
+    st.opt.m_eq = d.m_eq;
+    st.lam = 0.0;
+  }
+  __syncthreads();
+
+  // ---- ||A||_2 by power iteration on A'A from ones/sqrt(n) (Section 3.2)
+  {
+    const float v0 = float(1.0 / sqrt((double)n));
+    double cc = 0.0, bb = 0.0;
+    for (int j = tid; j < n; j += NT) {
+      p[j] = v0;
+      cc = fma(c[j], c[j], cc);
+    }
+    for (int i = tid; i < m; i += NT) bb = fma(b[i], b[i], bb);
+    double nb2;
+    const double nc2 = cta_sum2<NT>(cc, bb, red, &nb2);
+    for (int it = 0; it < B.power_iters; ++it) {
+      cta_spmv<float, NT, float>(A, p, ax);  // u = A v
+      __syncthreads();
+      cta_spmv<float, NT, float>(At, ax, q);  // w = A'u
+      __syncthreads();
+      float ww = 0.f;
+      for (int j = tid; j < n; j += NT) ww = fmaf(q[j], q[j], ww);
+      cta_sum_t0<NT>(double(ww), red, [&](double tt) {
+        s_sc[0] = sqrt(tt);
+        s_f[0] = s_sc[0] > 0.0 ? float(1.0 / s_sc[0]) : 0.f;
+      });
+      const float inv = s_f[0];
+      for (int j = tid; j < n; j += NT) p[j] = q[j] * inv;
+      __syncthreads();
+    }
+    if (tid == 0) {
+      st.lam = s_sc[0];
+      setup_finish_decide(&st, nc2, nb2, 1);
+    }
+    __syncthreads();
+  }
+
+  auto evaluate = [&](int mode) {
+    batch_evaluate<NT>(F64, qd64, A64, At64, c, b, lo, hi, d, x, xa, y, ya, es, st, red, mode);
+  };
+  // the FP32 vectors from the FP64 iterates: x and y for the products, the
+  // A x, A'y and Q x caches
+  auto refresh = [&]() {
+    for (int j = tid; j < n; j += NT) xv[j] = float(x[j]);
+    for (int i = tid; i < m; i += NT) yv[i] = float(y[i]);
+    __syncthreads();
+    cta_spmv<float, NT, float>(A, xv, ax);
+    cta_spmv<float, NT, float>(At, yv, aty);
+    __syncthreads();
+    cta_qprod<float, NT, true, float>(F, qd, n, k, xv, t, qx);
+  };
+  // r0 = p0 = -(Qx + c + A'y), the next attempt's CG start, and empty moves
+  auto prepare = [&]() -> double {
+    float rr = 0.f;
+    for (int j = tid; j < n; j += NT) {
+      const float v = -(qx[j] + c32[j] + aty[j]);
+      r[j] = v;
+      p[j] = v;
+      dx[j] = 0.f;
+      dq[j] = 0.f;
+      rr = fmaf(v, v, rr);
+    }
+    return cta_sum1<NT>(double(rr), red);
+  };
+  // an attempt is kept: x += dx (FP64, projected into the box when there is
+  // one), Q x += dq, and the running average of x with weight w
+  auto commit_x = [&](double w) {
+    for (int j = tid; j < n; j += NT) {
+      double v = x[j] + double(dx[j]);
+      if (lo) v = fmin(fmax(v, lo[j]), hi[j]);
+      x[j] = v;
+      xv[j] = float(v);
+      qx[j] += dq[j];
+      xa[j] += (v - xa[j]) * w;
+    }
+  };
+
+  evaluate(0);
+  refresh();
+  double rr0 = prepare();
+  const int efreq = B.eval_freq;
+  while (running(&st)) {
+    for (int it = 0; it < efreq && running(&st) && st.attempts < st.opt.max_iter; ++it) {
+      // ---- x-step: inexact CG on (Q + I/tau) x = x/tau - c - A'y (Section 2)
+      const int mode = st.opt.cg_mode, nfix = st.opt.cg_fixed_n, cgmax = st.opt.cg_max;
+      if (tid == 0) {
+        s_sc[0] = st.tau;
+        s_sc[1] = 1.0 / st.tau;
+        s_f[0] = float(s_sc[1]);
+        s_sc[2] = mode == kCgAdaptive ? st.eps + st.opt.cg_eps_factor * st.relkkt_last : st.eps;
+        s_sc[3] = rr0;
+        s_flag = (mode == kCgFixed && nfix <= 0) || rr0 == 0.0;
+      }
+      __syncthreads();
+      const float inv_tau = s_f[0];
+      int steps = 0;
+      bool numerr = false;
+      const bool skip = s_flag != 0;
+      if (lo && !skip) {
+        // ---- BB projected gradient (Section 4) from x, with r = p = -g, on
+        // the FP32 copy of x (xv), whose moves add up in dx
+        const double gmg = cta_qprod_pmp_f<NT>(F, qd, n, k, p, inv_tau, t, td, q);
+        if (tid == 0) {
+          s_flag = !(gmg > 0.0) || !isfinite(gmg) ? 2 : 0;
+          s_f[1] = float(1.0 / (gmg / s_sc[3]));  // 1/alpha, alpha = g'Mg / g'g
+        }
+        __syncthreads();
+        numerr = s_flag == 2;
+        while (!numerr) {
+          const float inv_alpha = s_f[1];
+          float ss = 0.f;
+          for (int j = tid; j < n; j += NT) {
+            const float xj = xv[j];
+            const float xn = fminf(fmaxf(fmaf(r[j], inv_alpha, xj), lo32[j]), hi32[j]);
+            const float sj = xn - xj;
+            p[j] = sj;
+            xv[j] = xn;
+            dx[j] += sj;
+            ss = fmaf(sj, sj, ss);
+          }
+          cta_sum_t0<NT>(double(ss), red, [&](double tt) { s_sc[3] = tt; });
+          // q = Q s and s'(Q + I/tau)s
+          const double sw = cta_qprod_pmp_f<NT>(F, qd, n, k, p, inv_tau, t, td, q);
+          for (int j = tid; j < n; j += NT) {
+            const float sj = p[j], qj = q[j];
+            r[j] -= fmaf(sj, inv_tau, qj);
+            dq[j] += qj;
+          }
+          if (tid == 0) {
+            const double ssv = s_sc[3];
+            const bool stop = mode == kCgFixed ? steps + 1 >= nfix
+                                               : (sqrt(ssv) <= s_sc[2] || steps + 1 >= cgmax);
+            if (stop || ssv == 0.0) {
+              s_flag = 1;
+            } else if (!(sw > 0.0) || !isfinite(sw)) {
+              s_flag = 2;
+            } else {
+              s_flag = 0;
+              s_f[1] = float(1.0 / (sw / ssv));  // 1/alpha, alpha = s'w / s's
+            }
+          }
+          __syncthreads();
+          ++steps;
+          if (s_flag == 1) break;
+          if (s_flag == 2) {
+            numerr = true;
+            break;
+          }
+        }
+      }
+      while (!skip && !lo) {
+        cta_qprod<float, NT, false, float>(F, qd, n, k, p, t, q);  // q = Q p
+        float pq = 0.f;
+        for (int j = tid; j < n; j += NT) pq = fmaf(p[j], fmaf(p[j], inv_tau, q[j]), pq);
+        cta_sum_t0<NT>(double(pq), red, [&](double tt) {
+          s_flag = !(tt > 0.0) || !isfinite(tt) ? 2 : 0;
+          s_f[1] = float(s_sc[3] / tt);  // alpha = r'r / p'q
+        });
+        if (s_flag == 2) {
+          numerr = true;
+          break;
+        }
+        const float alpha = s_f[1];
+        float rn = 0.f;
+        for (int j = tid; j < n; j += NT) {
+          const float pj = p[j], qj = q[j];
+          dx[j] = fmaf(alpha, pj, dx[j]);
+          dq[j] = fmaf(alpha, qj, dq[j]);
+          const float rj = fmaf(-alpha, fmaf(pj, inv_tau, qj), r[j]);
+          r[j] = rj;
+          rn = fmaf(rj, rj, rn);
+        }
+        cta_sum_t0<NT>(double(rn), red, [&](double rr_new) {
+          const bool stop = mode == kCgFixed
+                                ? steps + 1 >= nfix
+                                : (s_sc[0] * sqrt(rr_new) <= s_sc[2] || steps + 1 >= cgmax);
+          s_flag = stop || rr_new == 0.0;
+          s_f[2] = float(rr_new / s_sc[3]);  // beta
+          s_sc[3] = rr_new;
+        });
+        ++steps;
+        if (s_flag) break;
+        const float beta = s_f[2];
+        for (int j = tid; j < n; j += NT) p[j] = fmaf(beta, p[j], r[j]);
+        __syncthreads();
+      }
+      if (numerr) {
+        if (tid == 0) {
+          st.done = kDoneNumerical;
+          st.iter_active = 0;
+        }
+        __syncthreads();
+        break;
+      }
+      if (tid == 0) {
+        st.attempts += 1;
+        st.cg_total += steps;
+        st.last_cg = steps;
+        if (B.adaptive) {
+          st.eps_try = s_sc[2];
+        } else {
+          st.eps = s_sc[2];
+          st.k_total += 1;
+          st.j += 1;
+        }
+      }
+      __syncthreads();
+      const float sigma = float(st.sigma);
+      if (B.adaptive) {
+        // ---- trial y-step at x + dx, the Section 4 step test on the moves,
+        // then keep or drop the attempt
+        float f4[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int j = tid; j < n; j += NT) {
+          const float mj = dx[j];
+          if (!lo) xv[j] += mj;  // the BB step already moved xv
+          f4[0] = fmaf(mj, mj, f4[0]);
+          f4[1] = fmaf(mj, dq[j], f4[1]);
+        }
+        __syncthreads();
+        cta_dual_mixed<NT>(A, xv, b32, d.m_eq, sigma, 0.0, y, yv, ax, ya, yn, axn);
+        __syncthreads();
+        for (int i = tid; i < m; i += NT) {
+          const float dy = float(yn[i] - y[i]);
+          f4[2] = fmaf(dy, dy, f4[2]);
+          f4[3] = fmaf(dy, axn[i] - ax[i], f4[3]);
+        }
+        double a4[4] = {f4[0], f4[1], f4[2], f4[3]}, m1[1] = {0.0};
+        cta_reduce<NT, 4, 0>(a4, m1, red);
+        if (tid == 0) step_decide(&st, a4[0], a4[1], a4[2], a4[3]);
+        __syncthreads();
+        if (st.accepted) {
+          const double w = st.avg_w;
+          for (int i = tid; i < m; i += NT) {
+            const double v = yn[i];
+            y[i] = v;
+            yv[i] = float(v);
+            ax[i] = axn[i];
+            ya[i] += (v - ya[i]) * w;
+          }
+          commit_x(w);
+          __syncthreads();
+          cta_spmv<float, NT, float>(At, yv, aty);
+        } else {
+          for (int j = tid; j < n; j += NT) xv[j] = float(x[j]);
+        }
+        __syncthreads();
+        rr0 = prepare();
+        continue;
+      }
+      // ---- keep the x-step, then the y-step fused into A x+, A'y+ and the
+      // next CG start
+      if (tid == 0) s_sc[5] = 1.0 / (double)st.j;
+      __syncthreads();
+      const double inv_j = s_sc[5];
+      commit_x(inv_j);
+      __syncthreads();
+      cta_dual_mixed<NT>(A, xv, b32, d.m_eq, sigma, inv_j, y, yv, ax, ya);
+      __syncthreads();
+      cta_spmv<float, NT, float>(At, yv, aty);
+      __syncthreads();
+      rr0 = prepare();
+    }
+    // ---- evaluation, termination, restart (Section 4)
+    evaluate(1);
+    const int pending = st.restart_pending;
+    if (pending != 0) {
+      double ex = 0.0, ey = 0.0;
+      for (int j = tid; j < n; j += NT) {
+        const double cand = pending == 2 ? xa[j] : x[j];
+        const double e = cand - x0[j];
+        ex = fma(e, e, ex);
+        x0[j] = cand;
+        x[j] = cand;
+      }
+      for (int i = tid; i < m; i += NT) {
+        const double cand = pending == 2 ? ya[i] : y[i];
+        const double e = cand - y0[i];
+        ey = fma(e, e, ey);
+        y0[i] = cand;
+        y[i] = cand;
+      }
+      double dy2;
+      const double dx2 = cta_sum2<NT>(ex, ey, red, &dy2);
+      if (tid == 0) restart_finish_decide(&st, dx2, dy2);
+      __syncthreads();
+    }
+    refresh();
+    rr0 = prepare();
     __syncthreads();
   }
 
@@ -808,7 +1304,10 @@ __global__ void __launch_bounds__(NT, batch_min_blocks<NT>()) k_batch(BatchData<
     const int idx = id_s;
     __syncthreads();
     if (idx >= B.count) break;
-    batch_solve_one<V, NT>(B, B.order[idx], sm, st, red);
+    if constexpr (std::is_same<V, float>::value)
+      batch_solve_mixed<NT>(B, B.order[idx], sm, st, red);
+    else
+      batch_solve_fp64<NT>(B, B.order[idx], sm, st, red);
   }
 }
 
