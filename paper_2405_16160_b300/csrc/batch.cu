@@ -219,13 +219,11 @@ bool finite_all(const double* v, size_t n) {
 
 template <class V, int NT>
 qp_status launch_batch_nt(qp_batch* h, BatchBin& bin, BatchData<V> B) {
-  auto kern = k_batch<V, NT>;
   const int ad = B.opt.step_mode == kStepAdaptive ? 1 : 0;
   const int mx = std::is_same<V, float>::value ? 1 : 0;
   const size_t smem = bin.smem[mx][ad], bd = bin.block_doubles[mx][ad];
-  BCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   int occ = 0;
-  BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
+  BCUDA((BatchLaunch<V, NT>::prepare(smem, &occ)));
   if (occ < 1) {
     berror("batch kernel with %d threads and %zu bytes of shared memory cannot be resident", NT,
            smem);
@@ -243,8 +241,7 @@ qp_status launch_batch_nt(qp_batch* h, BatchBin& bin, BatchData<V> B) {
     B.ws = bin.ws;
     B.ws_stride = (long long)bd;
   }
-  kern<<<grid, NT, smem, bin.stream>>>(B);
-  BCUDA(cudaGetLastError());
+  BCUDA((BatchLaunch<V, NT>::launch(grid, smem, bin.stream, B)));
   return QP_OK;
 }
 

@@ -1286,18 +1286,16 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
 
 // Blocks per SM the register budget is sized for (launch bounds): 128
 // registers per thread at every block size.
-template <int NT>
+template <class V, int NT>
 constexpr int batch_min_blocks() {
   return NT == 64 ? 8 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1));
 }
 
+// The work queue of one block: instances until the queue is empty, each
+// solved with its vectors at sm.
 template <class V, int NT>
-__global__ void __launch_bounds__(NT, batch_min_blocks<NT>()) k_batch(BatchData<V> B) {
-  extern __shared__ double sm_dyn[];
-  double* sm = B.ws ? B.ws + (long long)blockIdx.x * B.ws_stride : sm_dyn;
-  __shared__ DevState st;
-  __shared__ double red[(NT / 32) * 13];
-  __shared__ int id_s;
+__device__ __forceinline__ void batch_queue(const BatchData<V>& B, double* sm, DevState& st,
+                                            double* red, int& id_s) {
   for (;;) {
     if (threadIdx.x == 0) id_s = atomicAdd(B.next, 1);
     __syncthreads();
@@ -1310,5 +1308,30 @@ __global__ void __launch_bounds__(NT, batch_min_blocks<NT>()) k_batch(BatchData<
       batch_solve_fp64<NT>(B, B.order[idx], sm, st, red);
   }
 }
+
+// Two call sites, so that in the shared-memory one (the common case) every
+// vector pointer is known to address shared memory: 32-bit shared loads and
+// stores, and half the registers per pointer.
+template <class V, int NT>
+__global__ void __launch_bounds__(NT, batch_min_blocks<V, NT>()) k_batch(BatchData<V> B) {
+  extern __shared__ double sm_dyn[];
+  __shared__ DevState st;
+  __shared__ double red[(NT / 32) * 13];
+  __shared__ int id_s;
+  if (B.ws)
+    batch_queue<V, NT>(B, B.ws + (long long)blockIdx.x * B.ws_stride, st, red, id_s);
+  else
+    batch_queue<V, NT>(B, sm_dyn, st, red, id_s);
+}
+
+// Host entry points of k_batch<V, NT>.  batch_inst.cu defines them and is
+// compiled once per (V, NT), so that the eight instantiations of the solver
+// compile in parallel; the host code (batch.cu) only calls these.
+template <class V, int NT>
+struct BatchLaunch {
+  // allow smem bytes of dynamic shared memory; *occupancy = resident blocks per SM
+  static cudaError_t prepare(size_t smem, int* occupancy);
+  static cudaError_t launch(int grid, size_t smem, cudaStream_t stream, const BatchData<V>& B);
+};
 
 }  // namespace pdhcg
