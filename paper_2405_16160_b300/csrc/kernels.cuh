@@ -463,8 +463,10 @@ __device__ __forceinline__ void block_pairs_total(const double* part, int nrows,
 // Barrier over all blocks of a co-resident grid that can also reduce one
 // partial per block (block_dot_store layout) to a total.  Each block's
 // thread 0 holds the barrier number in gen_local (grid_gen at the kernel's
-// start, then advanced by every barrier).  Arriving: fence, then count.  The
-// block that arrives last sums the partials in index order
+// start, then advanced by every barrier).  Arriving: after the block's
+// __syncthreads, thread 0 counts with an acquire-release add, which makes
+// the block's writes visible to whoever acquires the count after it (no
+// separate fence).  The block that arrives last sums the partials in index order
 // (block_total_dot, so the value does not depend on which block is last),
 // re-opens the next barrier's slot, resets the count and publishes the total
 // in this barrier's slot with release order; the others poll that slot.  One
@@ -492,7 +494,9 @@ __device__ __forceinline__ unsigned int grid_gen(GridBarrier* bar) {
 
 // K > 1: K totals per barrier (block_pairs_store layout, K per block); the
 // last block publishes the first in the slot and the others in the barrier's
-// extra line, which the waiting blocks read after the slot releases them.
+// extra line, which block 0 alone reads after the slot releases it (the
+// other blocks see 0 for them: one dependent L2 load fewer on their way
+// out).
 template <class A, int K = 1, class F>
 __device__ __forceinline__ bool grid_sync_sum(GridBarrier* bar, DevState* st, int timeout_ms,
                                               bool never_release, unsigned int& gen_local,
@@ -503,14 +507,12 @@ __device__ __forceinline__ bool grid_sync_sum(GridBarrier* bar, DevState* st, in
   cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(bar->count);
   cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> slot(bar->slot[g & 1u]);
   if (threadIdx.x == 0) {
-    __threadfence();
     const unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
     s_last = arrived == gridDim.x - 1 && !never_release;
     s_ok = 1;
   }
   __syncthreads();
   if (s_last) {  // the whole last block (the branch is uniform)
-    __threadfence();
     double t[K];
     if constexpr (K == 1) {
       t[0] = part ? block_total_dot<1>(part, gridDim.x, A()) : 0.0;
@@ -556,14 +558,11 @@ __device__ __forceinline__ bool grid_sync_sum(GridBarrier* bar, DevState* st, in
       double t[K];
       t[0] = __longlong_as_double((long long)v);
 #pragma unroll
-      for (int k = 1; k < K; ++k) t[k] = __ldcg(&bar->extra[k - 1]);
+      for (int k = 1; k < K; ++k) t[k] = blockIdx.x == 0 ? __ldcg(&bar->extra[k - 1]) : 0.0;
       on_total(static_cast<const double*>(t));
     }
   }
-  if (threadIdx.x == 0) {
-    gen_local = g + 1u;
-    __threadfence();
-  }
+  if (threadIdx.x == 0) gen_local = g + 1u;
   __syncthreads();
   return s_ok != 0;
 }
@@ -859,7 +858,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
   const int tmo = st->opt.barrier_timeout_ms;
   bool never_release = (st->opt.debug_flags & kDebugBarrierNeverReleases) != 0u;
   __shared__ double s_tau, s_eps, s_rr;  // thread 0's
-  __shared__ double s_mv[2];             // the latest step's primal move sums (totals)
+  __shared__ double s_mv[2];             // the latest step's primal move sums (block 0's totals)
   __shared__ T s_inv_tau, s_coef;        // 1/tau; alpha, then beta
   __shared__ int s_flag;                 // skip / numerical error / stop
   if (threadIdx.x == 0) {
