@@ -766,24 +766,29 @@ __global__ void __launch_bounds__(kBlock) k_long_finish(LongRows L, const T* seg
 // CG kernel reads one value.  The summation order is fixed: the last block
 // reduces all partials in index order.
 // blocks: the blocks taking part (the first ones; default the whole grid).
+// The "last block finishes" ticket: called by thread 0 after the block's
+// __syncthreads, it counts the block with an acquire-release add, which
+// publishes the block's writes to the block that counts last and lets that
+// block see every other block's (no separate fences).  True for the block
+// that takes the last of n tickets.
+__device__ __forceinline__ bool take_ticket(unsigned int* ticket, unsigned int n) {
+  cuda::atomic_ref<unsigned int, cuda::thread_scope_device> t(*ticket);
+  return t.fetch_add(1u, cuda::memory_order_acq_rel) == n - 1u;
+}
+
 template <class A>
 __device__ __forceinline__ void store_and_finish_dot(A acc, double* part, unsigned int* ticket,
                                                      int blocks = 0) {
   __shared__ int s_last;
   const int nb = blocks > 0 ? blocks : int(gridDim.x);
   block_dot_store(acc, part + blockIdx.x);
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(ticket, 1u) == unsigned(nb) - 1u;
-  }
+  if (threadIdx.x == 0) s_last = take_ticket(ticket, unsigned(nb));
   __syncthreads();
   if (s_last) {  // the whole last block (the branch is uniform)
-    __threadfence();
     const double total = block_total_dot<4>(part, nb, A());
     if (threadIdx.x == 0) {
       part[nb] = total;
-      *ticket = 0u;
-      __threadfence();
+      *ticket = 0u;  // for the next launch (ordered by the kernel boundary)
     }
   }
 }
@@ -1286,13 +1291,9 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
     }
     block_pairs_store<2>(am, tr.part_step + 2 * size_t(blockIdx.x));
     __shared__ int s_last;
-    if (threadIdx.x == 0) {
-      __threadfence();
-      s_last = atomicAdd(tr.ticket, 1u) == gridDim.x - 1;
-    }
+    if (threadIdx.x == 0) s_last = take_ticket(tr.ticket, gridDim.x);
     __syncthreads();
     if (s_last) {  // the whole last block (the branch is uniform)
-      __threadfence();
       double t[2], u[2];
       block_pairs_total<2, typename Acc<T>::type>(tr.part_step, gridDim.x, t);
       if (tr.n_parts > 0) {  // per-block partials (the BB kernel)
@@ -1303,8 +1304,7 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
       }
       if (threadIdx.x == 0) {
         step_decide(st, u[0], u[1], t[0], t[1], tr.pow_table);
-        *tr.ticket = 0u;
-        __threadfence();
+        *tr.ticket = 0u;  // for the next launch (ordered by the kernel boundary)
       }
     }
     return;
