@@ -47,6 +47,12 @@ void berror(const char* fmt, ...) {
     if (s_ != QP_OK) return s_; \
   } while (0)
 
+__global__ void k_batch_step_pow(double* t, int count) {
+  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < count;
+       a += (long long)gridDim.x * blockDim.x)
+    step_pow_entry(t, a);
+}
+
 __global__ void k_to_float(const double* __restrict__ in, float* out, long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -131,6 +137,7 @@ struct qp_batch {
   double *lo = nullptr, *hi = nullptr;  // packed variable bounds (allocated on first use)
   float *lo32 = nullptr, *hi32 = nullptr;  // and their FP32 copies
   BatchResult* res = nullptr;
+  double* step_pow = nullptr;  // step_decide's power table (kStepPowTable pairs)
   bool warm_set = false, solved = false, bounded = false;
   std::vector<BatchResult> h_res;
 };
@@ -313,6 +320,7 @@ BatchData<V> batch_data(qp_batch* h, const BatchBin& bin, const V* F, const V* q
   d.debug_flags = 0;
   d.barrier_timeout_ms = 0;
   d.step_mode = o->step_mode;
+  B.pow_table = h->step_pow;
   B.power_iters = o->power_iters;
   B.eval_freq = o->eval_freq;
   B.max_n = bin.max_n;
@@ -532,6 +540,9 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
     BCUDA(cudaMemsetAsync(*v, 0, size_t(h->m_total) * sizeof(double), h->stream));
   }
   BTRY(balloc(h, reinterpret_cast<void**>(&h->res), size_t(count) * sizeof(BatchResult)));
+  BTRY(balloc(h, reinterpret_cast<void**>(&h->step_pow), size_t(2) * kStepPowTable * sizeof(double)));
+  k_batch_step_pow<<<h->num_sms * 4, 256, 0, h->stream>>>(h->step_pow, kStepPowTable);
+  BCUDA(cudaGetLastError());
   BCUDA(cudaStreamSynchronize(h->stream));  // the host staging vectors die here
   return QP_OK;
 }

@@ -91,6 +91,7 @@ struct BatchData {
   double* ws;          // per-block vector space in global memory, or null for shared memory
   long long ws_stride;  // doubles per block in ws
   int adaptive;         // Section 4 adaptive step size (its vectors are in the layout)
+  const double* pow_table;  // step_decide's powers (kStepPowTable pairs)
 };
 
 // Vector space of one block, in doubles: shared memory when it fits, else
@@ -697,7 +698,7 @@ __device__ void batch_solve_fp64(const BatchData<double>& B, int id, double* sm,
           a4[3] = fma(dy, axn[i] - ax[i], a4[3]);
         }
         cta_reduce<NT, 4, 0>(a4, m1, red);
-        if (tid == 0) step_decide(&st, a4[0], a4[1], a4[2], a4[3]);
+        if (tid == 0) step_decide(&st, a4[0], a4[1], a4[2], a4[3], B.pow_table);
         __syncthreads();
         if (st.accepted) {
           const double w = st.avg_w;
@@ -789,20 +790,20 @@ __device__ void batch_solve_fp64(const BatchData<double>& B, int id, double* sm,
 }
 
 // ------------------------------------------------------------ mixed mode
-// Vector space of one block of the mixed-precision solve, in doubles.  FP64:
-// the iterates x and y, their running averages and the restart points
-// (3n + 3m).  The rest is one region used two ways.  During the iterations it
-// holds the adaptive step's trial y (FP64, m), F't's FP64 copy (k + 16) and
-// the FP32 working vectors: x for the products, r, p, q, the tracked Q x,
-// A'y, and the attempt's moves of x and of Q x (8n); y for the products, the
-// A x cache and the trial A x (3m); F'p (k + 16).  During an evaluation it
-// holds the FP64 products of (x, y) and of the averages (4n + 2m) and F'x
-// (k + 16); the FP32 vectors are formed again from the FP64 iterates after
-// it.
+// Vector space of one block of the mixed-precision solve, in doubles.  The
+// restart points x0, y0 in FP64 (n + m).  The iterates x and y and their
+// running averages as FP32 pairs hi + lo (split_add; 2n + 2m).  The rest is
+// one region used two ways.  During the attempts it holds F'p's FP64 copy
+// (k + 16) and the FP32 working vectors: the trial x the products read, r,
+// p, q, the tracked Q x, A'y, the attempt's moves dx of x and dq of Q x (8n);
+// the A x cache, the trial A x and the trial y pair (4m); F'p (k + 16).
+// During an evaluation it holds the FP64 products of (x, y) and of the
+// averages (4n + 2m), F'x (k + 16) and the FP64 values of x, y and the
+// averages (2n + 2m); the FP32 vectors are formed again after it.
 inline size_t batch_block_doubles_mixed(int max_n, int max_m, int max_k) {
   const size_t n = size_t(max_n), m = size_t(max_m), k = size_t(max_k) + 16;
-  const size_t iter = m + k + (8 * n + 3 * m + k + 1) / 2;
-  const size_t eval = 4 * n + 2 * m + k;
+  const size_t iter = k + (8 * n + 4 * m + k + 1) / 2;
+  const size_t eval = 6 * n + 4 * m + k;
   return 3 * n + 3 * m + (iter > eval ? iter : eval);
 }
 
@@ -840,26 +841,52 @@ __device__ double cta_qprod_pmp_f(const float* F, const float* qd, int n, int k,
   return td[k] + warp_sum(tt);
 }
 
+// A pair's value, and a value as a pair (hi the nearest float).
+__device__ __forceinline__ double pair_value(float hi, float lo) {
+  return double(hi) + double(lo);
+}
+__device__ __forceinline__ void pair_set(double v, float& hi, float& lo) {
+  hi = float(v);
+  lo = float(v - double(hi));
+}
+// The running average (ah, al) += ((h, l) - (ah, al)) w; weight 1 (the first
+// point after a start or restart) copies the pair exactly.
+__device__ __forceinline__ void pair_average(float& ah, float& al, float h, float l, float w) {
+  if (w == 1.f) {
+    ah = h;
+    al = l;
+  } else {
+    float a = ah, b = al;
+    split_add(a, b, ((h - a) + (l - b)) * w);
+    ah = a;
+    al = b;
+  }
+}
+
 // The mixed dual step fused into A x+: the move sigma (2 (A x+)_i - (A x)_i -
-// b_i) in FP32, added to the FP64 y_i and projected.  With the adaptive step
-// size (yn != nullptr) the result is a trial: y+ and A x+ go to yn and axn.
+// b_i), added to the pair y_i and projected, all in FP32.  With the adaptive
+// step size (ynh != nullptr) the result is a trial: y+ and A x+ go to
+// (ynh, ynl) and axn.  Otherwise y, the A x cache and the running average of
+// y (weight w) are updated.
 template <int NT>
 __device__ void cta_dual_mixed(const LocalCsr<float>& A, const float* xv, const float* b,
-                               int m_eq, float sigma, double w, double* y, float* yv, float* ax,
-                               double* ya, double* yn = nullptr, float* axn = nullptr) {
+                               int m_eq, float sigma, float w, float* yh, float* yl, float* ax,
+                               float* yah, float* yal, float* ynh = nullptr,
+                               float* ynl = nullptr, float* axn = nullptr) {
   auto row = [&](int i, float s) {
-    const float mv = sigma * (2.f * s - ax[i] - b[i]);
-    double v = y[i] + double(mv);
-    if (i >= m_eq && v < 0.0) v = 0.0;
-    if (yn) {
-      yn[i] = v;
+    float h = yh[i], l = yl[i];
+    split_add(h, l, sigma * (2.f * s - ax[i] - b[i]));
+    if (i >= m_eq && h < 0.f) h = l = 0.f;
+    if (ynh) {
+      ynh[i] = h;
+      ynl[i] = l;
       axn[i] = s;
       return;
     }
-    y[i] = v;
-    yv[i] = float(v);
+    yh[i] = h;
+    yl[i] = l;
     ax[i] = s;
-    ya[i] += (v - ya[i]) * w;
+    pair_average(yah[i], yal[i], h, l, w);
   };
   for (int i = threadIdx.x; i < A.rows; i += NT) {
     const int b0 = A.rp[i], e = A.rp[i + 1];
@@ -880,51 +907,63 @@ __device__ void cta_dual_mixed(const LocalCsr<float>& A, const float* xv, const 
 
 // One instance in mixed precision, solved by the whole block.  The data of
 // the iterations (F, qd, A, A', c, b and the bounds) and every vector of an
-// attempt are FP32: the CG and BB steps run on the FP32 pipe alone (B300's
-// FP64 pipe is 1/58 of it), with per-thread FP32 partial sums whose block
-// totals are FP64.  x and y, their averages and the restart points stay FP64:
-// an attempt moves x by the FP32 displacement dx it accumulates (x += dx
-// once, when the attempt is kept), so the iterates carry no FP32 rounding
-// from step to step.  Every evaluation uses the FP64 data and iterates
-// (batch_evaluate), as the FP64 solve does, so termination is decided on the
-// problem as given.  The method and its decisions are those of
-// batch_solve_fp64.
+// attempt are FP32, with per-thread FP32 partial sums whose block totals
+// and the method's scalars are FP64.  The iterates x and y and their running
+// averages are FP32 pairs (split_add), whose high words the products read:
+// an attempt adds up its move dx of x and leaves x alone, a kept attempt adds
+// dx to x once, a rejected one is dropped with nothing to restore.  So every
+// per-element operation of an attempt runs on the FP32 pipe (B300's FP64
+// pipe is 1/58 of it).  Each evaluation forms x, y and the averages in FP64
+// and uses the FP64 data (batch_evaluate), as the FP64 solve does, so
+// termination is decided on the problem as given; the restart points are
+// FP64.  The method and its decisions are those of batch_solve_fp64.
 template <int NT>
 __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm, DevState& st,
                                   double* red) {
   const BatchDesc d = B.desc[id];
   const int n = d.n, m = d.m, k = d.k, tid = threadIdx.x;
   const int Nn = B.max_n, Mm = B.max_m, Kk = B.max_k + 16;
-  // FP64 scalars derived by thread 0 (cta_sum_t0) and their FP32 copies;
-  // s_flag: 0 go on, 1 stop, 2 numerical error
-  __shared__ double s_sc[6];  // tau, 1/tau, eps, r'r (or s's), alpha or 1/alpha, beta
-  __shared__ float s_f[3];    // 1/tau, alpha or 1/alpha, beta
+  // The scalars of an attempt, derived by thread 0 from the FP64 block
+  // totals (cta_sum_t0) in FP32, the precision they are applied in (FP64
+  // division and square root on one thread would hold up the block for
+  // microseconds); s_flag: 0 go on, 1 stop, 2 numerical error
+  __shared__ double s_sc[1];  // ||A|| of the power iteration
+  // 1/tau, alpha or 1/alpha, beta, sigma, average weight, tau, eps, r'r (or s's)
+  __shared__ float s_f[8];
   __shared__ int s_flag;
-  double* x = sm;
-  double* xa = x + Nn;   // average
-  double* x0 = xa + Nn;  // restart point
-  double* y = x0 + Nn;
-  double* ya = y + Mm;
-  double* y0 = ya + Mm;
-  double* U = y0 + Mm;
-  // the iterations' view of U
-  double* yn = U;       // trial y (adaptive step)
-  double* td = U + Mm;  // F'p in FP64 (BB step)
-  float* xv = reinterpret_cast<float*>(td + Kk);
+  double* x0 = sm;  // restart points
+  double* y0 = x0 + Nn;
+  float* xh = reinterpret_cast<float*>(y0 + Mm);  // x = xh + xl
+  float* xl = xh + Nn;
+  float* xah = xl + Nn;  // its running average
+  float* xal = xah + Nn;
+  float* yh = xal + Nn;  // y = yh + yl
+  float* yl = yh + Mm;
+  float* yah = yl + Mm;
+  float* yal = yah + Mm;
+  double* U = y0 + Mm + 2 * Nn + 2 * Mm;
+  // the attempts' view of U
+  double* td = U;  // F'p in FP64 (BB step)
+  float* xv = reinterpret_cast<float*>(td + Kk);  // x as the products read it (trial x)
   float* r = xv + Nn;
   float* p = r + Nn;
   float* q = p + Nn;
-  float* qx = q + Nn;   // tracked Q x
+  float* qx = q + Nn;  // tracked Q x
   float* aty = qx + Nn;
   float* dx = aty + Nn;  // the attempt's move of x
   float* dq = dx + Nn;   // and of Q x
-  float* yv = dq + Nn;
-  float* ax = yv + Mm;   // A x cache
+  float* ax = dq + Nn;   // A x cache
   float* axn = ax + Mm;  // trial A x
-  float* t = axn + Mm;   // F'p
+  float* ynh = axn + Mm;  // trial y
+  float* ynl = ynh + Mm;
+  float* t = ynl + Mm;  // F'p
   // the evaluation's view of U
   const EvalScratch es{U, U + Nn, U + 2 * Nn, U + 3 * Nn, U + 4 * Nn, U + 4 * Nn + Mm,
                        U + 4 * Nn + 2 * Mm};
+  double* x64 = U + 4 * Nn + 2 * Mm + Kk;
+  double* xa64 = x64 + Nn;
+  double* y64 = xa64 + Nn;
+  double* ya64 = y64 + Mm;
   // instance data
   const double* c = B.c + d.off_n;
   const double* b = B.b + d.off_m;
@@ -960,15 +999,17 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
   for (int j = tid; j < n; j += NT) {
     double v = B.warm ? B.x0[d.off_n + j] : 0.0;
     if (lo) v = fmin(fmax(v, lo[j]), hi[j]);
-    x[j] = v;
     x0[j] = v;
-    xa[j] = 0.0;
+    pair_set(v, xh[j], xl[j]);
+    xah[j] = 0.f;
+    xal[j] = 0.f;
   }
   for (int i = tid; i < m; i += NT) {
     const double v = B.warm ? B.y0[d.off_m + i] : 0.0;
-    y[i] = v;
     y0[i] = v;
-    ya[i] = 0.0;
+    pair_set(v, yh[i], yl[i]);
+    yah[i] = 0.f;
+    yal[i] = 0.f;
   }
   if (tid == 0) {
     st.opt = B.opt;
@@ -1010,17 +1051,27 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
     __syncthreads();
   }
 
+  // relKKT of the FP64 values of the pairs, with the FP64 data
   auto evaluate = [&](int mode) {
-    batch_evaluate<NT>(F64, qd64, A64, At64, c, b, lo, hi, d, x, xa, y, ya, es, st, red, mode);
+    for (int j = tid; j < n; j += NT) {
+      x64[j] = pair_value(xh[j], xl[j]);
+      xa64[j] = pair_value(xah[j], xal[j]);
+    }
+    for (int i = tid; i < m; i += NT) {
+      y64[i] = pair_value(yh[i], yl[i]);
+      ya64[i] = pair_value(yah[i], yal[i]);
+    }
+    __syncthreads();
+    batch_evaluate<NT>(F64, qd64, A64, At64, c, b, lo, hi, d, x64, xa64, y64, ya64, es, st, red,
+                       mode);
   };
-  // the FP32 vectors from the FP64 iterates: x and y for the products, the
-  // A x, A'y and Q x caches
+  // the FP32 vectors from the iterates: x for the products, the A x, A'y and
+  // Q x caches
   auto refresh = [&]() {
-    for (int j = tid; j < n; j += NT) xv[j] = float(x[j]);
-    for (int i = tid; i < m; i += NT) yv[i] = float(y[i]);
+    for (int j = tid; j < n; j += NT) xv[j] = xh[j];
     __syncthreads();
     cta_spmv<float, NT, float>(A, xv, ax);
-    cta_spmv<float, NT, float>(At, yv, aty);
+    cta_spmv<float, NT, float>(At, yh, aty);
     __syncthreads();
     cta_qprod<float, NT, true, float>(F, qd, n, k, xv, t, qx);
   };
@@ -1037,16 +1088,21 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
     }
     return cta_sum1<NT>(double(rr), red);
   };
-  // an attempt is kept: x += dx (FP64, projected into the box when there is
-  // one), Q x += dq, and the running average of x with weight w
-  auto commit_x = [&](double w) {
+  // an attempt is kept: x += dx (projected into the box when there is one),
+  // Q x += dq, and the running average of x with weight w
+  auto commit_x = [&](float w) {
     for (int j = tid; j < n; j += NT) {
-      double v = x[j] + double(dx[j]);
-      if (lo) v = fmin(fmax(v, lo[j]), hi[j]);
-      x[j] = v;
-      xv[j] = float(v);
+      float h = xh[j], l = xl[j];
+      split_add(h, l, dx[j]);
+      if (lo && (h <= lo32[j] || h >= hi32[j])) {  // at or past a bound: project in FP64
+        const double v = pair_value(h, l);
+        if (v < lo[j] || v > hi[j]) pair_set(fmin(fmax(v, lo[j]), hi[j]), h, l);
+      }
+      xh[j] = h;
+      xl[j] = l;
+      xv[j] = h;
       qx[j] += dq[j];
-      xa[j] += (v - xa[j]) * w;
+      pair_average(xah[j], xal[j], h, l, w);
     }
   };
 
@@ -1059,11 +1115,17 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
       // ---- x-step: inexact CG on (Q + I/tau) x = x/tau - c - A'y (Section 2)
       const int mode = st.opt.cg_mode, nfix = st.opt.cg_fixed_n, cgmax = st.opt.cg_max;
       if (tid == 0) {
-        s_sc[0] = st.tau;
-        s_sc[1] = 1.0 / st.tau;
-        s_f[0] = float(s_sc[1]);
-        s_sc[2] = mode == kCgAdaptive ? st.eps + st.opt.cg_eps_factor * st.relkkt_last : st.eps;
-        s_sc[3] = rr0;
+        const double eps =
+            mode == kCgAdaptive ? st.eps + st.opt.cg_eps_factor * st.relkkt_last : st.eps;
+        if (B.adaptive)
+          st.eps_try = eps;
+        else
+          st.eps = eps;
+        s_f[5] = float(st.tau);
+        s_f[0] = 1.f / s_f[5];
+        s_f[3] = float(st.sigma);
+        s_f[6] = float(eps);
+        s_f[7] = float(rr0);
         s_flag = (mode == kCgFixed && nfix <= 0) || rr0 == 0.0;
       }
       __syncthreads();
@@ -1073,11 +1135,11 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
       const bool skip = s_flag != 0;
       if (lo && !skip) {
         // ---- BB projected gradient (Section 4) from x, with r = p = -g, on
-        // the FP32 copy of x (xv), whose moves add up in dx
+        // the FP32 x the products read (xv), whose moves add up in dx
         const double gmg = cta_qprod_pmp_f<NT>(F, qd, n, k, p, inv_tau, t, td, q);
         if (tid == 0) {
           s_flag = !(gmg > 0.0) || !isfinite(gmg) ? 2 : 0;
-          s_f[1] = float(1.0 / (gmg / s_sc[3]));  // 1/alpha, alpha = g'Mg / g'g
+          s_f[1] = s_f[7] / float(gmg);  // 1/alpha, alpha = g'Mg / g'g
         }
         __syncthreads();
         numerr = s_flag == 2;
@@ -1093,7 +1155,7 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
             dx[j] += sj;
             ss = fmaf(sj, sj, ss);
           }
-          cta_sum_t0<NT>(double(ss), red, [&](double tt) { s_sc[3] = tt; });
+          cta_sum_t0<NT>(double(ss), red, [&](double tt) { s_f[7] = float(tt); });
           // q = Q s and s'(Q + I/tau)s
           const double sw = cta_qprod_pmp_f<NT>(F, qd, n, k, p, inv_tau, t, td, q);
           for (int j = tid; j < n; j += NT) {
@@ -1102,16 +1164,16 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
             dq[j] += qj;
           }
           if (tid == 0) {
-            const double ssv = s_sc[3];
+            const float ssv = s_f[7];
             const bool stop = mode == kCgFixed ? steps + 1 >= nfix
-                                               : (sqrt(ssv) <= s_sc[2] || steps + 1 >= cgmax);
-            if (stop || ssv == 0.0) {
+                                               : (sqrtf(ssv) <= s_f[6] || steps + 1 >= cgmax);
+            if (stop || ssv == 0.f) {
               s_flag = 1;
             } else if (!(sw > 0.0) || !isfinite(sw)) {
               s_flag = 2;
             } else {
               s_flag = 0;
-              s_f[1] = float(1.0 / (sw / ssv));  // 1/alpha, alpha = s'w / s's
+              s_f[1] = ssv / float(sw);  // 1/alpha, alpha = s'w / s's
             }
           }
           __syncthreads();
@@ -1129,7 +1191,7 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
         for (int j = tid; j < n; j += NT) pq = fmaf(p[j], fmaf(p[j], inv_tau, q[j]), pq);
         cta_sum_t0<NT>(double(pq), red, [&](double tt) {
           s_flag = !(tt > 0.0) || !isfinite(tt) ? 2 : 0;
-          s_f[1] = float(s_sc[3] / tt);  // alpha = r'r / p'q
+          s_f[1] = s_f[7] / float(tt);  // alpha = r'r / p'q
         });
         if (s_flag == 2) {
           numerr = true;
@@ -1146,12 +1208,13 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
           rn = fmaf(rj, rj, rn);
         }
         cta_sum_t0<NT>(double(rn), red, [&](double rr_new) {
+          const float rn32 = float(rr_new);
           const bool stop = mode == kCgFixed
                                 ? steps + 1 >= nfix
-                                : (s_sc[0] * sqrt(rr_new) <= s_sc[2] || steps + 1 >= cgmax);
+                                : (s_f[5] * sqrtf(rn32) <= s_f[6] || steps + 1 >= cgmax);
           s_flag = stop || rr_new == 0.0;
-          s_f[2] = float(rr_new / s_sc[3]);  // beta
-          s_sc[3] = rr_new;
+          s_f[2] = rn32 / s_f[7];  // beta
+          s_f[7] = rn32;
         });
         ++steps;
         if (s_flag) break;
@@ -1171,16 +1234,14 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
         st.attempts += 1;
         st.cg_total += steps;
         st.last_cg = steps;
-        if (B.adaptive) {
-          st.eps_try = s_sc[2];
-        } else {
-          st.eps = s_sc[2];
+        if (!B.adaptive) {
           st.k_total += 1;
           st.j += 1;
+          s_f[4] = 1.f / float(st.j);
         }
       }
       __syncthreads();
-      const float sigma = float(st.sigma);
+      const float sigma = s_f[3];
       if (B.adaptive) {
         // ---- trial y-step at x + dx, the Section 4 step test on the moves,
         // then keep or drop the attempt
@@ -1192,31 +1253,34 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
           f4[1] = fmaf(mj, dq[j], f4[1]);
         }
         __syncthreads();
-        cta_dual_mixed<NT>(A, xv, b32, d.m_eq, sigma, 0.0, y, yv, ax, ya, yn, axn);
+        cta_dual_mixed<NT>(A, xv, b32, d.m_eq, sigma, 0.f, yh, yl, ax, yah, yal, ynh, ynl, axn);
         __syncthreads();
         for (int i = tid; i < m; i += NT) {
-          const float dy = float(yn[i] - y[i]);
+          const float dy = (ynh[i] - yh[i]) + (ynl[i] - yl[i]);
           f4[2] = fmaf(dy, dy, f4[2]);
           f4[3] = fmaf(dy, axn[i] - ax[i], f4[3]);
         }
         double a4[4] = {f4[0], f4[1], f4[2], f4[3]}, m1[1] = {0.0};
         cta_reduce<NT, 4, 0>(a4, m1, red);
-        if (tid == 0) step_decide(&st, a4[0], a4[1], a4[2], a4[3]);
+        if (tid == 0) {
+          step_decide(&st, a4[0], a4[1], a4[2], a4[3], B.pow_table);
+          s_f[4] = float(st.avg_w);
+        }
         __syncthreads();
         if (st.accepted) {
-          const double w = st.avg_w;
+          const float w = s_f[4];
           for (int i = tid; i < m; i += NT) {
-            const double v = yn[i];
-            y[i] = v;
-            yv[i] = float(v);
+            const float h = ynh[i], l = ynl[i];
+            yh[i] = h;
+            yl[i] = l;
             ax[i] = axn[i];
-            ya[i] += (v - ya[i]) * w;
+            pair_average(yah[i], yal[i], h, l, w);
           }
           commit_x(w);
           __syncthreads();
-          cta_spmv<float, NT, float>(At, yv, aty);
+          cta_spmv<float, NT, float>(At, yh, aty);
         } else {
-          for (int j = tid; j < n; j += NT) xv[j] = float(x[j]);
+          for (int j = tid; j < n; j += NT) xv[j] = xh[j];
         }
         __syncthreads();
         rr0 = prepare();
@@ -1224,14 +1288,12 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
       }
       // ---- keep the x-step, then the y-step fused into A x+, A'y+ and the
       // next CG start
-      if (tid == 0) s_sc[5] = 1.0 / (double)st.j;
-      __syncthreads();
-      const double inv_j = s_sc[5];
+      const float inv_j = s_f[4];
       commit_x(inv_j);
       __syncthreads();
-      cta_dual_mixed<NT>(A, xv, b32, d.m_eq, sigma, inv_j, y, yv, ax, ya);
+      cta_dual_mixed<NT>(A, xv, b32, d.m_eq, sigma, inv_j, yh, yl, ax, yah, yal);
       __syncthreads();
-      cta_spmv<float, NT, float>(At, yv, aty);
+      cta_spmv<float, NT, float>(At, yh, aty);
       __syncthreads();
       rr0 = prepare();
     }
@@ -1241,18 +1303,24 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
     if (pending != 0) {
       double ex = 0.0, ey = 0.0;
       for (int j = tid; j < n; j += NT) {
-        const double cand = pending == 2 ? xa[j] : x[j];
+        const double cand = pending == 2 ? xa64[j] : x64[j];
         const double e = cand - x0[j];
         ex = fma(e, e, ex);
         x0[j] = cand;
-        x[j] = cand;
+        if (pending == 2) {
+          xh[j] = xah[j];
+          xl[j] = xal[j];
+        }
       }
       for (int i = tid; i < m; i += NT) {
-        const double cand = pending == 2 ? ya[i] : y[i];
+        const double cand = pending == 2 ? ya64[i] : y64[i];
         const double e = cand - y0[i];
         ey = fma(e, e, ey);
         y0[i] = cand;
-        y[i] = cand;
+        if (pending == 2) {
+          yh[i] = yah[i];
+          yl[i] = yal[i];
+        }
       }
       double dy2;
       const double dx2 = cta_sum2<NT>(ex, ey, red, &dy2);
@@ -1266,8 +1334,10 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
 
   // ---- the returned iterate and its statistics
   const bool avg = st.returned_avg != 0;
-  for (int j = tid; j < n; j += NT) B.x_out[d.off_n + j] = avg ? xa[j] : x[j];
-  for (int i = tid; i < m; i += NT) B.y_out[d.off_m + i] = avg ? ya[i] : y[i];
+  for (int j = tid; j < n; j += NT)
+    B.x_out[d.off_n + j] = avg ? pair_value(xah[j], xal[j]) : pair_value(xh[j], xl[j]);
+  for (int i = tid; i < m; i += NT)
+    B.y_out[d.off_m + i] = avg ? pair_value(yah[i], yal[i]) : pair_value(yh[i], yl[i]);
   if (tid == 0) {
     BatchResult& o = B.res[id];
     o.termination = st.done > 0 ? st.done - 1 : 1;

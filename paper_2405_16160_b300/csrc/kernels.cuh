@@ -136,19 +136,6 @@ __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 
-// Compensated FP32 storage on the mixed path (y, its running average and the
-// x restart point): the value is hi + lo, the SpMVs read hi, and lo keeps the
-// rounding error of every update (two-sum, then the pair renormalised so that
-// |lo| <= ulp(hi)/2).  Without it a step below half an ulp of hi is lost.
-__device__ __forceinline__ void split_add(float& hi, float& lo, float d) {
-  const float s = __fadd_rn(hi, d);
-  const float bb = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
-  const float t = __fadd_rn(lo, e);
-  hi = __fadd_rn(s, t);
-  lo = __fsub_rn(t, __fsub_rn(hi, s));
-}
-
 template <class T>
 constexpr bool kSplit = std::is_same<T, float>::value;
 
@@ -1791,11 +1778,7 @@ __global__ void k_pow_start(T* v, int n, const T* __restrict__ c, const T* __res
 
 // step_decide's table: t[2 a] = (a+1)^-0.3, t[2 a + 1] = (a+1)^-0.6.
 __global__ void k_step_pow(double* t, int count) {
-  for (long long a = grid_tid(); a < count; a += grid_threads()) {
-    const double a1 = (double)(a + 1);
-    t[2 * a] = pow(a1, -kStepReductionExp);
-    t[2 * a + 1] = pow(a1, -kStepGrowthExp);
-  }
+  for (long long a = grid_tid(); a < count; a += grid_threads()) step_pow_entry(t, a);
 }
 
 // Element-wise type conversion (FP64 <-> FP32 copies of a vector).

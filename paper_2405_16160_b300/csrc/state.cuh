@@ -12,6 +12,20 @@
 
 namespace pdhcg {
 
+// Compensated FP32 storage on the mixed paths (the iterates, their running
+// averages and restart points): the value is hi + lo, the products read hi,
+// and lo keeps the rounding error of every update (two-sum, then the pair
+// renormalised so that |lo| <= ulp(hi)/2).  Without it a step below half an
+// ulp of hi is lost.  Every operation runs on the FP32 pipe.
+__device__ __forceinline__ void split_add(float& hi, float& lo, float d) {
+  const float s = __fadd_rn(hi, d);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+  const float t = __fadd_rn(lo, e);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
 constexpr int kCgAdaptive = 0;
 constexpr int kCgFixed = 1;
 constexpr int kRestartAdaptive = 0;
@@ -184,10 +198,17 @@ __device__ inline void control_decide(DevState* st, const KktTerms& kc, const Kk
 // and the batched solver.
 //
 // pow_table (may be null): pow_table[2 a] = (a+1)^-0.3 and pow_table[2 a + 1]
-// = (a+1)^-0.6 for a < kStepPowTable, filled by k_step_pow with the same
-// pow calls, so that the thread deciding (alone on its SM, on B300's narrow
+// = (a+1)^-0.6 for a < kStepPowTable, filled with step_pow_entry (the same
+// pow calls), so that the thread deciding (alone on its SM, on B300's narrow
 // FP64 pipe) reads them instead of evaluating two FP64 powers.
 constexpr int kStepPowTable = 1 << 17;
+
+// Entry a of the table (the same pow calls step_decide makes without it).
+__device__ __forceinline__ void step_pow_entry(double* t, long long a) {
+  const double a1 = (double)(a + 1);
+  t[2 * a] = pow(a1, -kStepReductionExp);
+  t[2 * a + 1] = pow(a1, -kStepGrowthExp);
+}
 
 __device__ inline void step_decide(DevState* st, double dx2, double dxqdx, double dy2,
                                    double cross, const double* pow_table = nullptr) {
