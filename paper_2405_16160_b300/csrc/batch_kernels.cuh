@@ -308,6 +308,44 @@ __device__ __forceinline__ void cta_sum_t0(double v, double* red, F&& f) {
   __syncthreads();
 }
 
+// FP32 forms of the block sums, for the mixed solve: warp partials by xor
+// shuffles, combined in warp order.  cta_sum_f gives every thread the S
+// totals; cta_sum_t0f hands thread 0's total to f before the closing
+// barrier, like cta_sum_t0.
+template <int NT, int S>
+__device__ __forceinline__ void cta_sum_f(float (&v)[S], float* red) {
+  constexpr int NW = NT / 32;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const float x = warp_sum_v(v[s]);
+    if (lane == 0) red[w * S + s] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    float a = 0.f;
+    for (int i = 0; i < NW; ++i) a += red[i * S + s];
+    v[s] = a;
+  }
+  __syncthreads();
+}
+
+template <int NT, class F>
+__device__ __forceinline__ void cta_sum_t0f(float v, float* red, F&& f) {
+  constexpr int NW = NT / 32;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  v = warp_sum_v(v);
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.f;
+    for (int i = 0; i < NW; ++i) a += red[i];
+    f(a);
+  }
+  __syncthreads();
+}
+
 template <int NT>
 __device__ __forceinline__ double cta_sum1(double v, double* red) {
   double s[1] = {v}, m[1] = {0.0};
@@ -923,10 +961,11 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
   const BatchDesc d = B.desc[id];
   const int n = d.n, m = d.m, k = d.k, tid = threadIdx.x;
   const int Nn = B.max_n, Mm = B.max_m, Kk = B.max_k + 16;
-  // The scalars of an attempt, derived by thread 0 from the FP64 block
-  // totals (cta_sum_t0) in FP32, the precision they are applied in (FP64
-  // division and square root on one thread would hold up the block for
-  // microseconds); s_flag: 0 go on, 1 stop, 2 numerical error
+  // The scalars of an attempt, derived by thread 0 from the FP32 block
+  // sums (cta_sum_t0f) in FP32, the precision they are applied in (FP64
+  // divisions and square roots on one thread would hold up the block for
+  // microseconds on B300's narrow FP64 pipe); s_flag: 0 go on, 1 stop,
+  // 2 numerical error
   __shared__ double s_sc[1];  // ||A|| of the power iteration
   // 1/tau, alpha or 1/alpha, beta, sigma, average weight, tau, eps, r'r (or s's)
   __shared__ float s_f[8];
@@ -1075,8 +1114,9 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
     __syncthreads();
     cta_qprod<float, NT, true, float>(F, qd, n, k, xv, t, qx);
   };
+  float* redf = reinterpret_cast<float*>(red);
   // r0 = p0 = -(Qx + c + A'y), the next attempt's CG start, and empty moves
-  auto prepare = [&]() -> double {
+  auto prepare = [&]() -> float {
     float rr = 0.f;
     for (int j = tid; j < n; j += NT) {
       const float v = -(qx[j] + c32[j] + aty[j]);
@@ -1086,7 +1126,9 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
       dq[j] = 0.f;
       rr = fmaf(v, v, rr);
     }
-    return cta_sum1<NT>(double(rr), red);
+    float t1[1] = {rr};
+    cta_sum_f<NT, 1>(t1, redf);
+    return t1[0];
   };
   // an attempt is kept: x += dx (projected into the box when there is one),
   // Q x += dq, and the running average of x with weight w
@@ -1108,7 +1150,7 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
 
   evaluate(0);
   refresh();
-  double rr0 = prepare();
+  float rr0 = prepare();
   const int efreq = B.eval_freq;
   while (running(&st)) {
     for (int it = 0; it < efreq && running(&st) && st.attempts < st.opt.max_iter; ++it) {
@@ -1125,8 +1167,8 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
         s_f[0] = 1.f / s_f[5];
         s_f[3] = float(st.sigma);
         s_f[6] = float(eps);
-        s_f[7] = float(rr0);
-        s_flag = (mode == kCgFixed && nfix <= 0) || rr0 == 0.0;
+        s_f[7] = rr0;
+        s_flag = (mode == kCgFixed && nfix <= 0) || rr0 == 0.f;
       }
       __syncthreads();
       const float inv_tau = s_f[0];
@@ -1155,7 +1197,7 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
             dx[j] += sj;
             ss = fmaf(sj, sj, ss);
           }
-          cta_sum_t0<NT>(double(ss), red, [&](double tt) { s_f[7] = float(tt); });
+          cta_sum_t0f<NT>(ss, redf, [&](float tt) { s_f[7] = tt; });
           // q = Q s and s'(Q + I/tau)s
           const double sw = cta_qprod_pmp_f<NT>(F, qd, n, k, p, inv_tau, t, td, q);
           for (int j = tid; j < n; j += NT) {
@@ -1189,9 +1231,9 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
         cta_qprod<float, NT, false, float>(F, qd, n, k, p, t, q);  // q = Q p
         float pq = 0.f;
         for (int j = tid; j < n; j += NT) pq = fmaf(p[j], fmaf(p[j], inv_tau, q[j]), pq);
-        cta_sum_t0<NT>(double(pq), red, [&](double tt) {
-          s_flag = !(tt > 0.0) || !isfinite(tt) ? 2 : 0;
-          s_f[1] = s_f[7] / float(tt);  // alpha = r'r / p'q
+        cta_sum_t0f<NT>(pq, redf, [&](float tt) {
+          s_flag = !(tt > 0.f) || !isfinite(tt) ? 2 : 0;
+          s_f[1] = s_f[7] / tt;  // alpha = r'r / p'q
         });
         if (s_flag == 2) {
           numerr = true;
@@ -1207,14 +1249,13 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
           r[j] = rj;
           rn = fmaf(rj, rj, rn);
         }
-        cta_sum_t0<NT>(double(rn), red, [&](double rr_new) {
-          const float rn32 = float(rr_new);
+        cta_sum_t0f<NT>(rn, redf, [&](float rr_new) {
           const bool stop = mode == kCgFixed
                                 ? steps + 1 >= nfix
-                                : (s_f[5] * sqrtf(rn32) <= s_f[6] || steps + 1 >= cgmax);
-          s_flag = stop || rr_new == 0.0;
-          s_f[2] = rn32 / s_f[7];  // beta
-          s_f[7] = rn32;
+                                : (s_f[5] * sqrtf(rr_new) <= s_f[6] || steps + 1 >= cgmax);
+          s_flag = stop || rr_new == 0.f;
+          s_f[2] = rr_new / s_f[7];  // beta
+          s_f[7] = rr_new;
         });
         ++steps;
         if (s_flag) break;
@@ -1260,10 +1301,9 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
           f4[2] = fmaf(dy, dy, f4[2]);
           f4[3] = fmaf(dy, axn[i] - ax[i], f4[3]);
         }
-        double a4[4] = {f4[0], f4[1], f4[2], f4[3]}, m1[1] = {0.0};
-        cta_reduce<NT, 4, 0>(a4, m1, red);
+        cta_sum_f<NT, 4>(f4, redf);
         if (tid == 0) {
-          step_decide(&st, a4[0], a4[1], a4[2], a4[3], B.pow_table);
+          step_decide_f(&st, f4[0], f4[1], f4[2], f4[3], B.pow_table);
           s_f[4] = float(st.avg_w);
         }
         __syncthreads();

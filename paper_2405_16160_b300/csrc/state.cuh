@@ -236,6 +236,41 @@ __device__ inline void step_decide(DevState* st, double dx2, double dxqdx, doubl
   }
 }
 
+// step_decide with FP32 arithmetic, for the mixed batched solve, whose
+// deciding thread would otherwise spend microseconds per attempt in FP64
+// divisions on B300's narrow FP64 pipe while its block waits: the same rule
+// and the same state updates, the sums and the limit in FP32, the epoch's
+// weight sum kept in FP64.
+__device__ inline void step_decide_f(DevState* st, float dx2, float dxqdx, float dy2, float cross,
+                                     const double* pow_table) {
+  const float eta = float(st->eta), om = float(st->omega);
+  const float movement = om * dx2 + dy2 / om;
+  const float interaction = 2.f * fabsf(cross) + dxqdx;
+  const float lim = interaction > 0.f ? movement / interaction : CUDART_INF_F;
+  const long long a = st->attempts;
+  float pr, pg;
+  if (pow_table != nullptr && a >= 0 && a < kStepPowTable) {
+    pr = float(pow_table[2 * a]);
+    pg = float(pow_table[2 * a + 1]);
+  } else {
+    pr = powf(float(a + 1), -float(kStepReductionExp));
+    pg = powf(float(a + 1), -float(kStepGrowthExp));
+  }
+  const float next = fminf((1.f - pr) * lim, (1.f + pg) * eta);
+  const bool acc = eta <= lim;
+  st->accepted = acc ? 1 : 0;
+  st->eta = next;
+  st->tau = next / om;
+  st->sigma = next * om;
+  if (acc) {
+    st->eps = st->eps_try;
+    st->j += 1;
+    st->k_total += 1;
+    st->weight_sum += eta;
+    st->avg_w = eta / float(st->weight_sum);
+  }
+}
+
 // Primal weight (Section 4): omega <- exp(theta log(dy/dx) + (1-theta) log omega),
 // from the squared distances of the new restart point to the previous one;
 // a new epoch starts.  Shared by the single-QP kernel below and the batched
