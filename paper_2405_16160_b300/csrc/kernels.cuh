@@ -139,6 +139,35 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 template <class T>
 constexpr bool kSplit = std::is_same<T, float>::value;
 
+// The CG and BB scalars from their FP64 totals, derived by thread 0 of every
+// block right after a grid barrier while the block waits.  FP32 values: in
+// FP32, the precision they are applied in (an FP64 division or square root
+// is dozens of cycles per instruction on B300's narrow FP64 pipe, on the
+// critical path of every barrier).  FP64 values: in FP64, rounded as the
+// oracle rounds them.
+template <class T>
+__device__ __forceinline__ T ratio(double a, double b) {  // a / b
+  if constexpr (kSplit<T>)
+    return float(a) / float(b);
+  else
+    return a / b;
+}
+template <class T>
+__device__ __forceinline__ T inv_ratio(double a, double b) {  // 1 / (a / b)
+  if constexpr (kSplit<T>)
+    return float(b) / float(a);
+  else
+    return 1.0 / (a / b);
+}
+template <class T>
+__device__ __forceinline__ bool scaled_norm_le(double scale, double sq, double bound) {
+  // scale * sqrt(sq) <= bound
+  if constexpr (kSplit<T>)
+    return float(scale) * sqrtf(float(sq)) <= float(bound);
+  else
+    return scale * sqrt(sq) <= bound;
+}
+
 // 16 bytes of consecutive vector entries (4 floats or 2 doubles), so that the
 // streaming vector phases load and store 128 bits at a time.
 template <class T>
@@ -797,8 +826,9 @@ __device__ __forceinline__ void store_and_finish_dot(A acc, double* part, unsign
 // beta and the iterates are those of textbook CG up to rounding.  Each step
 // costs one product with Q.  With the adaptive step size the iteration
 // counters wait for the accept/reject decision that k_dual's last block
-// takes.  alpha, beta, the stop test and all dot products are FP64-accurate
-// for both value types.  part holds 2 * gridDim.x doubles.
+// takes.  Every dot product is FP64-accurate for both value types; alpha,
+// beta and the stop test are derived from them in the value type's precision
+// (ratio, scaled_norm_le).  part holds 2 * gridDim.x doubles.
 // Resident CG blocks of 512 threads per SM (register budget per thread =
 // 65536 / (512 * blocks)).  Four FP32 blocks would need 32 registers and
 // spill; three measured faster.
@@ -907,7 +937,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
           const double pq = t[0];
           const bool bad = !(pq > 0.0) || !isfinite(pq);
           s_flag = bad;
-          s_coef = bad ? T(0) : T(s_rr / pq);
+          s_coef = bad ? T(0) : ratio<T>(s_rr, pq);
         }))
       return;
     never_release = false;
@@ -988,9 +1018,10 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
           const int done_steps = steps + 1;
           const bool stop = mode == kCgFixed
                                 ? done_steps >= nfix
-                                : (s_tau * sqrt(rr_new) <= s_eps || done_steps >= cgmax);
+                                : (scaled_norm_le<T>(s_tau, rr_new, s_eps) ||
+                                   done_steps >= cgmax);
           s_flag = stop || rr_new == 0.0;
-          s_coef = T(rr_new / s_rr);
+          s_coef = ratio<T>(rr_new, s_rr);
           s_rr = rr_new;
         }))
       return;
@@ -1102,7 +1133,7 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
       if (!grid_sync_sum<A>(bar, st, tmo, never_release, gen, part_a, [&](const double* t) {
             const double gmg = t[0];
             s_flag = !(gmg > 0.0) || !isfinite(gmg);
-            s_inv_alpha = T(1.0 / (gmg / s_rr));  // alpha = g'M g / g'g
+            s_inv_alpha = inv_ratio<T>(gmg, s_rr);  // alpha = g'M g / g'g
           }))
         return;
       never_release = false;
@@ -1137,14 +1168,15 @@ __global__ void __launch_bounds__(kCgBlock, kCgBlocksPerSm)
             const double sw = t[0];
             const int done_steps = steps + 1;
             const bool stop = mode == kCgFixed ? done_steps >= nfix
-                                               : (sqrt(s_ss) <= s_eps || done_steps >= cgmax);
+                                               : (scaled_norm_le<T>(1.0, s_ss, s_eps) ||
+                                                  done_steps >= cgmax);
             if (stop || s_ss == 0.0) {
               s_flag = 1;
             } else if (!(sw > 0.0) || !isfinite(sw)) {
               s_flag = 2;
             } else {
               s_flag = 0;
-              s_inv_alpha = T(1.0 / (sw / s_ss));  // alpha = s'w / s's
+              s_inv_alpha = inv_ratio<T>(sw, s_ss);  // alpha = s'w / s's
             }
           }))
         return;
@@ -1290,7 +1322,10 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
         u[1] = __ldcg(tr.part_n + 1);
       }
       if (threadIdx.x == 0) {
-        step_decide(st, u[0], u[1], t[0], t[1], tr.pow_table);
+        if constexpr (kSplit<T>)  // FP32 arithmetic, as the values are applied in
+          step_decide_f(st, float(u[0]), float(u[1]), float(t[0]), float(t[1]), tr.pow_table);
+        else
+          step_decide(st, u[0], u[1], t[0], t[1], tr.pow_table);
         *tr.ticket = 0u;  // for the next launch (ordered by the kernel boundary)
       }
     }
