@@ -1227,41 +1227,64 @@ __device__ void batch_solve_mixed(const BatchData<float>& B, int id, double* sm,
           }
         }
       }
-      while (!skip && !lo) {
-        cta_qprod<float, NT, false, float>(F, qd, n, k, p, t, q);  // q = Q p
-        float pq = 0.f;
-        for (int j = tid; j < n; j += NT) pq = fmaf(p[j], fmaf(p[j], inv_tau, q[j]), pq);
-        cta_sum_t0f<NT>(pq, redf, [&](float tt) {
-          s_flag = !(tt > 0.f) || !isfinite(tt) ? 2 : 0;
-          s_f[1] = s_f[7] / tt;  // alpha = r'r / p'q
-        });
-        if (s_flag == 2) {
-          numerr = true;
-          break;
+      // CG with one barrier per product: the warps that form t = F'p (with
+      // p = r + beta p, i.e. t = F'r + beta t) also form the diagonal part
+      // sum (qd_j + 1/tau) p_j^2 as one more column; after the barrier every
+      // warp forms p'(Q + I/tau)p = ||t||^2 + that sum with the same lanes and
+      // shuffle tree, so alpha needs no block reduction; one pass over the
+      // rows then forms p, q = Q p and the updates, and r'r is the step's one
+      // block sum.
+      if (!skip && !lo) {
+        const int wp = tid >> 5, lane = tid & 31;
+        float beta = 0.f;  // the first step: p = r
+        for (;;) {
+          for (int l = wp; l <= k; l += NT / 32) {
+            float sa = 0.f;
+            if (l < k) {
+              const float* Fl = F + size_t(l) * n;
+              for (int j = lane; j < n; j += 32) sa = fmaf(Fl[j], r[j], sa);
+            } else {
+              for (int j = lane; j < n; j += 32) {
+                const float pj = fmaf(beta, p[j], r[j]);
+                sa = fmaf((qd[j] + inv_tau) * pj, pj, sa);
+              }
+            }
+            sa = warp_sum_v(sa);
+            if (lane == 0) t[l] = (l < k && beta != 0.f) ? fmaf(beta, t[l], sa) : sa;
+          }
+          __syncthreads();
+          float tt = 0.f;
+          for (int l = lane; l < k; l += 32) tt = fmaf(t[l], t[l], tt);
+          const float pq = warp_sum_v(tt) + t[k];
+          if (!(pq > 0.f) || !isfinite(pq)) {  // the same value in every thread
+            numerr = true;
+            break;
+          }
+          const float alpha = s_f[7] / pq;  // alpha = r'r / p'(Q + I/tau)p
+          float rn = 0.f;
+          for (int j = tid; j < n; j += NT) {
+            const float pj = fmaf(beta, p[j], r[j]);
+            float qj = qd[j] * pj;
+            for (int l = 0; l < k; ++l) qj = fmaf(F[size_t(l) * n + j], t[l], qj);
+            p[j] = pj;
+            dx[j] = fmaf(alpha, pj, dx[j]);
+            dq[j] = fmaf(alpha, qj, dq[j]);
+            const float rj = fmaf(-alpha, fmaf(pj, inv_tau, qj), r[j]);
+            r[j] = rj;
+            rn = fmaf(rj, rj, rn);
+          }
+          cta_sum_t0f<NT>(rn, redf, [&](float rr_new) {
+            const bool stop = mode == kCgFixed
+                                  ? steps + 1 >= nfix
+                                  : (s_f[5] * sqrtf(rr_new) <= s_f[6] || steps + 1 >= cgmax);
+            s_flag = stop || rr_new == 0.f;
+            s_f[2] = rr_new / s_f[7];  // beta
+            s_f[7] = rr_new;
+          });
+          ++steps;
+          if (s_flag) break;
+          beta = s_f[2];
         }
-        const float alpha = s_f[1];
-        float rn = 0.f;
-        for (int j = tid; j < n; j += NT) {
-          const float pj = p[j], qj = q[j];
-          dx[j] = fmaf(alpha, pj, dx[j]);
-          dq[j] = fmaf(alpha, qj, dq[j]);
-          const float rj = fmaf(-alpha, fmaf(pj, inv_tau, qj), r[j]);
-          r[j] = rj;
-          rn = fmaf(rj, rj, rn);
-        }
-        cta_sum_t0f<NT>(rn, redf, [&](float rr_new) {
-          const bool stop = mode == kCgFixed
-                                ? steps + 1 >= nfix
-                                : (s_f[5] * sqrtf(rr_new) <= s_f[6] || steps + 1 >= cgmax);
-          s_flag = stop || rr_new == 0.f;
-          s_f[2] = rr_new / s_f[7];  // beta
-          s_f[7] = rr_new;
-        });
-        ++steps;
-        if (s_flag) break;
-        const float beta = s_f[2];
-        for (int j = tid; j < n; j += NT) p[j] = fmaf(beta, p[j], r[j]);
-        __syncthreads();
       }
       if (numerr) {
         if (tid == 0) {
