@@ -225,9 +225,12 @@ void qp_options_default(qp_options* o);
  * Q_*: n x n CSR, both triangles stored; A_*: m x n CSR; c: n; b: m (host
  * pointers, read only during the call; the caller keeps ownership).
  * Validation: n > 0, m >= 0, 0 <= m_eq <= m, nnz < 2^31, rowptr[0] = 0 and
- * monotone, columns in [0, cols), all values finite.  Duplicate (i, j)
- * entries are summed; rows are sorted.  A' is built on the host (stable
- * counting sort) and stored explicitly.  ctx may be NULL.
+ * monotone, columns in [0, cols), all values finite.  With a device visible
+ * the entries are checked on it right after the copy (with QP_CREATE_PENALTY
+ * or QP_CREATE_CHECK_SYMMETRY, and without a device, on the host first); the
+ * error and its message are the same either way.  Duplicate (i, j) entries
+ * are summed; rows are sorted.  A' is built on the device (a stable sort of
+ * A's entries by column) and stored explicitly.  ctx may be NULL.
  * Errors: QP_ERR_INVALID_ARG, QP_ERR_NO_DEVICE, QP_ERR_OOM, QP_ERR_CUDA;
  * *out is NULL on failure.
  */

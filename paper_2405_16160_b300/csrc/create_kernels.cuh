@@ -271,6 +271,52 @@ __global__ void __launch_bounds__(kBlock) k_scale_long_matrix(CsrT<double> M, Lo
 }
 
 // v <- d v and inv = 1/d.
+// ---- qp_create's checks of the problem as given, on the device copies.
+// Row pointers: the lowest row whose pointer decreases to *bad_row, and a
+// mark at the first entry of every non-empty row (marks only at offsets in
+// [0, nnz), so the entry pass stays in bounds whatever the pointers hold).
+__global__ void k_check_rows(const int32_t* __restrict__ rowptr, int rows, long long nnz,
+                             uint8_t* first, unsigned long long* bad_row) {
+  for (long long i = grid_tid(); i < rows; i += grid_threads()) {
+    const int32_t a = rowptr[i], e = rowptr[i + 1];
+    if (e < a) atomicMin(bad_row, (unsigned long long)i);
+    if (a < e && a >= 0 && a < nnz) first[a] = 1;
+  }
+}
+
+// Entries: the lowest one with a column outside [0, cols) or a non-finite
+// value to *bad_entry; *unsorted = 1 if a column does not exceed its
+// predecessor within a row.
+__global__ void k_check_entries(const int32_t* __restrict__ col, const double* __restrict__ val,
+                                long long nnz, int cols, const uint8_t* __restrict__ first,
+                                unsigned long long* bad_entry, int* unsorted) {
+  bool uns = false;
+  for (long long k = grid_tid(); k < nnz; k += grid_threads()) {
+    const int32_t j = col[k];
+    if (uint32_t(j) >= uint32_t(cols) || !isfinite(val[k]))
+      atomicMin(bad_entry, (unsigned long long)k);
+    uns |= k > 0 && !first[k] && j <= col[k - 1];
+  }
+  if (uns) *unsorted = 1;
+}
+
+// The lowest index of a non-finite value to *bad.
+__global__ void k_check_finite(const double* __restrict__ v, long long n,
+                               unsigned long long* bad) {
+  for (long long i = grid_tid(); i < n; i += grid_threads())
+    if (!isfinite(v[i])) atomicMin(bad, (unsigned long long)i);
+}
+
+__global__ void k_fill(double* v, double a, int n) {
+  for (long long i = grid_tid(); i < n; i += grid_threads()) v[i] = a;
+}
+
+// out = v * d elementwise: a solution back in the caller's variables.
+__global__ void k_unscale(double* out, const double* __restrict__ v, const double* __restrict__ d,
+                          int n) {
+  for (long long i = grid_tid(); i < n; i += grid_threads()) out[i] = v[i] * d[i];
+}
+
 __global__ void k_scale_vector(double* v, const double* __restrict__ d, double* inv, int n) {
   for (long long i = grid_tid(); i < n; i += grid_threads()) {
     v[i] *= d[i];

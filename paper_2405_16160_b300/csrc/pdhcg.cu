@@ -233,7 +233,9 @@ struct qp_handle {
   bool warm_set = false;
   int active_prec = kPrecFp64;  // precision of the iterate last produced
   bool scaled = false;           // Section 4 diagonal scaling applied at create
-  std::vector<double> d1, d2;    // the scaling (x = D2 x~, y = D1 y~)
+  std::vector<double> d1, d2;    // the scaling (x = D2 x~, y = D1 y~), host copy (host_scaling)
+  double *dev_d1 = nullptr, *dev_d2 = nullptr;  // the scaling on the device
+  double *sol_x = nullptr, *sol_y = nullptr;    // qp_get_solution's unscaled copies
   cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};
   int chunk_iters[2] = {0, 0};
   int chunk_step[2] = {-1, -1};
@@ -805,6 +807,14 @@ qp_status alloc_matrix(qp_handle* h, DevMat* M, int32_t rows, int64_t nnz) {
   return QP_OK;
 }
 
+void free_matrix(qp_handle* h, DevMat* M) {
+  for (void* p : {(void*)M->rowptr, (void*)M->col, (void*)M->val, (void*)M->val32}) dev_free(h, p);
+  M->rowptr = nullptr;
+  M->col = nullptr;
+  M->val = nullptr;
+  M->val32 = nullptr;
+}
+
 qp_status upload_csr(qp_handle* h, DevMat* M, const CsrView& H) {
   QP_TRY(alloc_matrix(h, M, H.rows, H.nnz()));
   QP_TRY(upload(h, M->rowptr, H.rowptr, (size_t(H.rows) + 1) * sizeof(int32_t)));
@@ -971,9 +981,8 @@ qp_status device_scaling(qp_handle* h, int ruiz_iters) {
   step(dalloc(h, &h->v32.inv_d1, std::max(m, 1)));
   step(dalloc(h, &h->v32.inv_d2, n));
   if (st == QP_OK) {
-    const std::vector<double> ones(size_t(std::max(n, m)), 1.0);
-    step(upload(h, d1, ones.data(), size_t(m) * sizeof(double)));
-    step(upload(h, d2, ones.data(), size_t(n) * sizeof(double)));
+    if (m > 0) k_fill<<<h->grid_vec, kBlock, 0, h->stream>>>(d1, 1.0, m);
+    k_fill<<<h->grid_vec, kBlock, 0, h->stream>>>(d2, 1.0, n);
     const int wave = h->num_sms * 8;
     // eight rows per warp (see k_scale_norms_n)
     auto warp_grid = [&](int64_t rows) {
@@ -1024,18 +1033,38 @@ qp_status device_scaling(qp_handle* h, int ruiz_iters) {
     }
     convert(h, h->v64.inv_d1, h->v32.inv_d1, m);
     convert(h, h->v64.inv_d2, h->v32.inv_d2, n);
-    h->d1.resize(size_t(m));
-    h->d2.resize(size_t(n));
-    if (m > 0)
-      CUDA_TRY(cudaMemcpyAsync(h->d1.data(), d1, size_t(m) * sizeof(double),
-                               cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(cudaMemcpyAsync(h->d2.data(), d2, size_t(n) * sizeof(double),
-                             cudaMemcpyDeviceToHost, h->stream));
+    h->dev_d1 = d1;  // kept on the device; the host copy is made on first use
+    h->dev_d2 = d2;
     st = check_launch();
     if (st == QP_OK) st = sync(h);
   }
-  for (void* p : {(void*)d1, (void*)d2, (void*)rn, (void*)rm}) dev_free(h, p);
+  if (st != QP_OK)
+    for (void* p : {(void*)d1, (void*)d2}) dev_free(h, p);
+  for (void* p : {(void*)rn, (void*)rm}) dev_free(h, p);
   return st;
+}
+
+// D1 and D2 on the host, copied from the device on their first use (a
+// warm start, bounds, qp_get_scaling, a bounded solution): most solves never
+// need them there.  Without the scaling both are ones.
+qp_status host_scaling(qp_handle* h) {
+  const size_t N = size_t(h->n), M = size_t(h->m);
+  if (h->d2.size() == N && h->d1.size() == M) return QP_OK;
+  if (!h->scaled) {
+    h->d1.assign(M, 1.0);
+    h->d2.assign(N, 1.0);
+    return QP_OK;
+  }
+  std::vector<double> d1(M), d2(N);
+  if (M > 0)
+    CUDA_TRY(cudaMemcpyAsync(d1.data(), h->dev_d1, M * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+  CUDA_TRY(cudaMemcpyAsync(d2.data(), h->dev_d2, N * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+  QP_TRY(sync(h));
+  h->d1.swap(d1);
+  h->d2.swap(d2);
+  return QP_OK;
 }
 
 template <class T>
@@ -1123,6 +1152,121 @@ qp_status validate_problem(int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr
   return QP_OK;
 }
 
+// The host part of qp_create's checks when the entries are checked on the
+// device (device_validate): sizes, pointers, rowptr[0] = 0 and nnz = rowptr
+// [rows] in int32 range, with the messages of csr_check and validate_problem.
+qp_status validate_shapes(int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr,
+                          const int32_t* Qc, const double* Qv, const int32_t* Ar,
+                          const int32_t* Ac, const double* Av, const double* c,
+                          const double* b) {
+  if (n <= 0 || m < 0 || m_eq < 0 || m_eq > m) {
+    set_error("bad sizes n=%d m=%d m_eq=%d", n, m, m_eq);
+    return QP_ERR_INVALID_ARG;
+  }
+  if (!c || (m > 0 && !b)) {
+    set_error("c or b is NULL");
+    return QP_ERR_INVALID_ARG;
+  }
+  const char* names[2] = {"Q", "A"};
+  const int32_t* rp[2] = {Qr, Ar};
+  const int32_t* cp[2] = {Qc, Ac};
+  const double* vp[2] = {Qv, Av};
+  const int32_t rows[2] = {n, m};
+  for (int k = 0; k < 2; ++k) {
+    if (!rp[k]) {
+      set_error("%s: rowptr is NULL", names[k]);
+      return QP_ERR_INVALID_ARG;
+    }
+    if (rp[k][0] != 0) {
+      set_error("%s: rowptr[0] != 0", names[k]);
+      return QP_ERR_INVALID_ARG;
+    }
+    if (rp[k][rows[k]] < 0) {
+      set_error("%s: nnz out of int32 range", names[k]);
+      return QP_ERR_INVALID_ARG;
+    }
+    if (rp[k][rows[k]] > 0 && (!cp[k] || !vp[k])) {
+      set_error("%s: col or val is NULL", names[k]);
+      return QP_ERR_INVALID_ARG;
+    }
+  }
+  return QP_OK;
+}
+
+// qp_create's checks of the entries, on the device copies of Q, A (uploaded
+// as given), c and b: one pass over the row pointers and one over the
+// entries of each matrix (k_check_rows, k_check_entries), one over c and b.
+// The first failure in csr_check's and validate_problem's order (Q, then A,
+// then c, then b; row pointers before entries; the lowest index) becomes the
+// error, with their messages.  *q_canonical / *a_canonical: every row's
+// columns strictly increase.  The entry marks use each matrix's FP32 value
+// array, which finish_matrix fills later.
+qp_status device_validate(qp_handle* h, const int32_t* Qc, const int32_t* Ac,
+                          bool* q_canonical, bool* a_canonical) {
+  // per matrix: bad row, bad entry, unsorted flag (as a 64-bit word); then c, b
+  unsigned long long* res = nullptr;
+  QP_TRY(dalloc(h, &res, 8));
+  const DevMat* mats[2] = {&h->Q, &h->A};
+  unsigned long long init[8];
+  for (int k = 0; k < 2; ++k) {
+    init[3 * k] = (unsigned long long)mats[k]->rows;
+    init[3 * k + 1] = (unsigned long long)mats[k]->nnz;
+    init[3 * k + 2] = 0ull;
+  }
+  init[6] = (unsigned long long)h->n;
+  init[7] = (unsigned long long)h->m;
+  QP_TRY(upload(h, res, init, sizeof(init)));
+  const int wave = h->num_sms * 8;
+  for (int k = 0; k < 2; ++k) {
+    const DevMat& M = *mats[k];
+    uint8_t* first = reinterpret_cast<uint8_t*>(M.val32);
+    if (M.nnz > 0) CUDA_TRY(cudaMemsetAsync(first, 0, size_t(M.nnz), h->stream));
+    if (M.rows > 0)
+      k_check_rows<<<std::max(1, std::min(wave, (M.rows + kBlock - 1) / kBlock)), kBlock, 0,
+                     h->stream>>>(M.rowptr, M.rows, M.nnz, first, res + 3 * k);
+    if (M.nnz > 0)
+      k_check_entries<<<int(std::max<int64_t>(1, std::min<int64_t>(wave, (M.nnz + kBlock - 1) /
+                                                                             kBlock))),
+                        kBlock, 0, h->stream>>>(M.col, M.val, M.nnz, h->n, first, res + 3 * k + 1,
+                                                reinterpret_cast<int*>(res + 3 * k + 2));
+  }
+  k_check_finite<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.c, h->n, res + 6);
+  if (h->m > 0) k_check_finite<<<h->grid_vec, kBlock, 0, h->stream>>>(h->v64.b, h->m, res + 7);
+  QP_TRY(check_launch());
+  unsigned long long out[8];
+  CUDA_TRY(cudaMemcpyAsync(out, res, sizeof(out), cudaMemcpyDeviceToHost, h->stream));
+  QP_TRY(sync(h));
+  dev_free(h, res);
+  const char* names[2] = {"Q", "A"};
+  const int32_t* cols[2] = {Qc, Ac};
+  for (int k = 0; k < 2; ++k) {
+    if (out[3 * k] < (unsigned long long)mats[k]->rows) {
+      set_error("%s: rowptr is not monotone at row %llu", names[k], out[3 * k]);
+      return QP_ERR_INVALID_ARG;
+    }
+    const unsigned long long e = out[3 * k + 1];
+    if (e < (unsigned long long)mats[k]->nnz) {
+      const int32_t j = cols[k][e];
+      if (j < 0 || j >= h->n)
+        set_error("%s: column index out of range at entry %llu", names[k], e);
+      else
+        set_error("%s: non-finite value at entry %llu", names[k], e);
+      return QP_ERR_INVALID_ARG;
+    }
+  }
+  if (out[6] < (unsigned long long)h->n) {
+    set_error("c[%llu] is not finite", out[6]);
+    return QP_ERR_INVALID_ARG;
+  }
+  if (out[7] < (unsigned long long)h->m) {
+    set_error("b[%llu] is not finite", out[7]);
+    return QP_ERR_INVALID_ARG;
+  }
+  *q_canonical = (out[2] & 0xffffffffull) == 0;
+  *a_canonical = (out[5] & 0xffffffffull) == 0;
+  return QP_OK;
+}
+
 // Launch geometry from the lanes per row in use and h->waves: the
 // non-persistent row kernels take h->waves resident waves of blocks (each
 // warp a contiguous share of the rows, so more blocks than fit at once let
@@ -1173,15 +1317,18 @@ qp_status compute_grids(qp_handle* h) {
   return QP_OK;
 }
 
+// device_check: the entries were not checked on the host (validate_shapes
+// only); device_validate checks them after the upload, and q_canonical /
+// a_canonical come from it.
 qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const int32_t* Qr,
                       const int32_t* Qc, const double* Qv, const int32_t* Ar, const int32_t* Ac,
                       const double* Av, const double* c, const double* b, uint32_t flags,
-                      bool q_canonical, bool a_canonical) {
+                      bool q_canonical, bool a_canonical, bool device_check) {
   // Rows that are already sorted without duplicates are used in place;
   // otherwise a canonical copy (sorted, duplicates summed) is made.
   HostCsr Qc_, Ac_;
   CsrView Qh{n, n, Qr, Qc, Qv}, Ah{m, n, Ar, Ac, Av};
-  if (!q_canonical) {
+  if (!device_check && !q_canonical) {
     Qc_ = csr_canonical(n, n, Qr, Qc, Qv);
     Qh = view_of(Qc_);
   }
@@ -1192,7 +1339,7 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
       return QP_ERR_INVALID_ARG;
     }
   }
-  if (!a_canonical) {
+  if (!device_check && !a_canonical) {
     Ac_ = csr_canonical(m, n, Ar, Ac, Av);
     Ah = view_of(Ac_);
   }
@@ -1223,16 +1370,9 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   const int wave = h->num_sms * 8;
   h->grid_vec =
       int(std::max<int64_t>(1, std::min<int64_t>((std::max(n, m) + kBlock - 1) / kBlock, wave)));
-  // Q and A go to the device as given; A' is built there.
+  // Q, A, c and b go to the device as given; A' is built there.
   QP_TRY(upload_csr(h, &h->Q, Qh));
   QP_TRY(upload_csr(h, &h->A, Ah));
-  if (h->penalty) QP_TRY(upload_csr(h, &h->Qe, Qown));
-  std::vector<int32_t> t_rowptr;
-  QP_TRY(device_transpose(h, n, &t_rowptr));
-  QP_TRY(build_row_tables(h, &h->Q, Qh.rowptr));
-  QP_TRY(build_row_tables(h, &h->A, Ah.rowptr));
-  QP_TRY(build_row_tables(h, &h->At, t_rowptr.data()));
-  if (h->penalty) QP_TRY(build_row_tables(h, &h->Qe, Qown.rowptr));
   QP_TRY(alloc_vecs<double>(h));
   QP_TRY(alloc_vecs<float>(h));
   const size_t N = size_t(n), M = size_t(m);
@@ -1243,14 +1383,32 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
     QP_TRY(upload(h, h->v64.ce, c, N * sizeof(double)));
   }
   QP_TRY(upload(h, h->v64.b, b, M * sizeof(double)));
+  if (device_check) {
+    QP_TRY(device_validate(h, Qc, Ac, &q_canonical, &a_canonical));
+    // rows not sorted (or with duplicates): the canonical copy replaces the upload
+    if (!q_canonical) {
+      Qc_ = csr_canonical(n, n, Qr, Qc, Qv);
+      Qh = view_of(Qc_);
+      free_matrix(h, &h->Q);
+      QP_TRY(upload_csr(h, &h->Q, Qh));
+    }
+    if (!a_canonical) {
+      Ac_ = csr_canonical(m, n, Ar, Ac, Av);
+      Ah = view_of(Ac_);
+      free_matrix(h, &h->A);
+      QP_TRY(upload_csr(h, &h->A, Ah));
+    }
+  }
+  if (h->penalty) QP_TRY(upload_csr(h, &h->Qe, Qown));
+  std::vector<int32_t> t_rowptr;
+  QP_TRY(device_transpose(h, n, &t_rowptr));
+  QP_TRY(build_row_tables(h, &h->Q, Qh.rowptr));
+  QP_TRY(build_row_tables(h, &h->A, Ah.rowptr));
+  QP_TRY(build_row_tables(h, &h->At, t_rowptr.data()));
+  if (h->penalty) QP_TRY(build_row_tables(h, &h->Qe, Qown.rowptr));
   // Section 4 preprocessing: the solver works on D2 Q D2, D1 A D2, D2 c, D1 b.
   h->scaled = (flags & QP_CREATE_SCALE) != 0;
-  if (h->scaled) {
-    QP_TRY(device_scaling(h, 10));
-  } else {
-    h->d1.assign(M, 1.0);
-    h->d2.assign(N, 1.0);
-  }
+  if (h->scaled) QP_TRY(device_scaling(h, 10));
   QP_TRY(finish_matrix(h, &h->Q));
   QP_TRY(finish_matrix(h, &h->A));
   QP_TRY(finish_matrix(h, &h->At));
@@ -1723,11 +1881,21 @@ qp_status qp_create(qp_handle** out, int32_t n, int32_t m, int32_t m_eq, const i
   }
   *out = nullptr;
   bool q_canonical = false, a_canonical = false;
-  QP_TRY(validate_problem(n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b,
-                          &q_canonical, &a_canonical));
+  // With a device, the entries are checked there after the upload (one pass
+  // over them), except where the host needs them valid first (the penalty's
+  // products, the symmetry check); without one, on the host, so that an
+  // invalid problem reports QP_ERR_INVALID_ARG either way.
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-    cudaGetLastError();
+  const bool have_device = cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0;
+  if (!have_device) cudaGetLastError();
+  const bool device_check =
+      have_device && (flags & (QP_CREATE_PENALTY | QP_CREATE_CHECK_SYMMETRY)) == 0;
+  if (device_check)
+    QP_TRY(validate_shapes(n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b));
+  else
+    QP_TRY(validate_problem(n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b,
+                            &q_canonical, &a_canonical));
+  if (!have_device) {
     set_error("no CUDA device visible");
     return QP_ERR_NO_DEVICE;
   }
@@ -1749,7 +1917,7 @@ qp_status qp_create(qp_handle** out, int32_t n, int32_t m, int32_t m_eq, const i
   if (s == QP_OK) s = begin_call(h);
   if (s == QP_OK)
     s = create_impl(h, n, m, m_eq, Q_rowptr, Q_col, Q_val, A_rowptr, A_col, A_val, c, b, flags,
-                    q_canonical, a_canonical);
+                    q_canonical, a_canonical, device_check);
   if (s == QP_OK) s = end_call(h);
   if (s != QP_OK) {
     std::string keep = g_last_error;
@@ -1830,28 +1998,37 @@ qp_status qp_get_solution(const qp_handle* h, double* x, double* y) {
   qp_handle* hh = const_cast<qp_handle*>(h);
   CUDA_TRY(cudaSetDevice(h->device));
   const bool avg = h->info.returned_avg != 0;
-  if (x)
-    CUDA_TRY(cudaMemcpyAsync(x, avg ? h->v64.x_avg : h->v64.x, size_t(h->n) * sizeof(double),
-                             cudaMemcpyDeviceToHost, h->stream));
-  if (y && h->m > 0)
-    CUDA_TRY(cudaMemcpyAsync(y, avg ? h->v64.y_avg : h->v64.y, size_t(h->m) * sizeof(double),
-                             cudaMemcpyDeviceToHost, h->stream));
-  QP_TRY(sync(hh));
-  if (h->scaled) {  // back to the caller's variables: x = D2 x~, y = D1 y~
-    if (x)
-      for (int32_t j = 0; j < h->n; ++j) x[j] *= h->d2[size_t(j)];
-    if (y)
-      for (int32_t i = 0; i < h->m; ++i) y[i] *= h->d1[size_t(i)];
-    // (hi / d2) * d2 can round one ulp past hi: keep x in the caller's box
-    if (x && h->bounded)
-      for (int32_t j = 0; j < h->n; ++j)
-        x[j] = std::min(std::max(x[j], h->lo_user[size_t(j)]), h->hi_user[size_t(j)]);
+  const double* xs = avg ? h->v64.x_avg : h->v64.x;
+  const double* ys = avg ? h->v64.y_avg : h->v64.y;
+  // back to the caller's variables, x = D2 x~ and y = D1 y~, on the device
+  if (h->scaled) {
+    if (!hh->sol_x) QP_TRY(dalloc(hh, &hh->sol_x, size_t(h->n)));
+    if (!hh->sol_y && h->m > 0) QP_TRY(dalloc(hh, &hh->sol_y, size_t(h->m)));
+    if (x) k_unscale<<<h->grid_vec, kBlock, 0, h->stream>>>(hh->sol_x, xs, h->dev_d2, h->n);
+    if (y && h->m > 0)
+      k_unscale<<<h->grid_vec, kBlock, 0, h->stream>>>(hh->sol_y, ys, h->dev_d1, h->m);
+    QP_TRY(check_launch());
+    xs = hh->sol_x;
+    ys = hh->sol_y;
   }
+  if (x)
+    CUDA_TRY(cudaMemcpyAsync(x, xs, size_t(h->n) * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+  if (y && h->m > 0)
+    CUDA_TRY(cudaMemcpyAsync(y, ys, size_t(h->m) * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+  QP_TRY(sync(hh));
+  // (hi / d2) * d2 can round one ulp past hi: keep x in the caller's box
+  if (x && h->scaled && h->bounded)
+    for (int32_t j = 0; j < h->n; ++j)
+      x[j] = std::min(std::max(x[j], h->lo_user[size_t(j)]), h->hi_user[size_t(j)]);
   return QP_OK;
 }
 
 qp_status qp_get_scaling(const qp_handle* h, double* d1, double* d2) {
   if (!h) return QP_ERR_INVALID_ARG;
+  CUDA_TRY(cudaSetDevice(h->device));
+  QP_TRY(host_scaling(const_cast<qp_handle*>(h)));
   if (d1) std::copy(h->d1.begin(), h->d1.end(), d1);
   if (d2) std::copy(h->d2.begin(), h->d2.end(), d2);
   return QP_OK;
@@ -1874,6 +2051,7 @@ qp_status qp_get_trace(const qp_handle* h, qp_trace_entry* out, int64_t cap, int
 qp_status qp_set_warm_start(qp_handle* h, const double* x0, const double* y0) {
   if (!h) return QP_ERR_INVALID_ARG;
   QP_TRY(begin_call(h));
+  QP_TRY(host_scaling(h));
   std::vector<double> xs, ys;  // into the solver's variables: x~ = x / D2, y~ = y / D1
   if (x0 && h->scaled) {
     xs.resize(size_t(h->n));
@@ -2166,6 +2344,7 @@ qp_status qp_set_bounds(qp_handle* h, const double* lo, const double* hi) {
   }
   std::vector<double> lo_user_new = l, hi_user_new = u;  // as given (unscaled)
   QP_TRY(begin_call(h));
+  QP_TRY(host_scaling(h));
   h->solved = false;
   h->bounded = false;  // set again only once every bounds array holds the new bounds
   if (any) {
