@@ -4,12 +4,16 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstring>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -51,6 +55,12 @@ __global__ void k_batch_step_pow(double* t, int count) {
   for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < count;
        a += (long long)gridDim.x * blockDim.x)
     step_pow_entry(t, a);
+}
+
+__global__ void k_fill_f64(double* v, double a, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    v[i] = a;
 }
 
 __global__ void k_to_float(const double* __restrict__ in, float* out, long long n) {
@@ -197,6 +207,104 @@ qp_status convert_float(qp_batch* h, const double* in, float* out, size_t n) {
     BCUDA(cudaGetLastError());
   }
   return QP_OK;
+}
+
+// f(i) for every i in [0, count), in contiguous ranges on up to `threads`
+// host threads.
+template <class F>
+void host_parallel(int64_t count, int threads, F&& f) {
+  const int T = int(std::max<int64_t>(1, std::min<int64_t>(threads, count)));
+  auto run = [&](int t) {
+    for (int64_t i = count * t / T; i < count * (t + 1) / T; ++i) f(i);
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < T; ++t) th.emplace_back(run, t);
+  run(0);
+  for (auto& x : th) x.join();
+}
+
+int host_threads() {
+  return int(std::max(1u, std::min(std::thread::hardware_concurrency(), 16u)));
+}
+
+// Host-to-device copies through pinned staging, shared by the batch handles
+// of the process (two chunks per device, allocated on first use).  The
+// sources, pieces laid out one after another in the destination, are packed
+// into a chunk by several host threads and copied from there; a chunk's copy
+// overlaps the packing of the next.  (A copy from pageable memory goes
+// through the driver's own staging, about 10 GB/s on one thread.)  The
+// sources may be freed on return.
+struct HostPiece {
+  const void* src;
+  size_t bytes;
+};
+
+constexpr size_t kStageChunk = size_t(64) << 20;
+constexpr int kStageDevices = 64;
+
+struct Staging {
+  std::mutex mu;
+  char* buf[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+};
+
+Staging& staging(int device) {
+  static Staging s[kStageDevices];
+  return s[device];
+}
+
+qp_status staged_upload(qp_batch* h, void* dst, const std::vector<HostPiece>& pieces) {
+  std::vector<size_t> off(pieces.size() + 1, 0);
+  for (size_t i = 0; i < pieces.size(); ++i) off[i + 1] = off[i] + pieces[i].bytes;
+  const size_t total = off.back();
+  if (total == 0) return QP_OK;
+  if (h->device < 0 || h->device >= kStageDevices) {
+    berror("device %d beyond the staging table", h->device);
+    return QP_ERR_CUDA;
+  }
+  Staging& S = staging(h->device);
+  std::lock_guard<std::mutex> lock(S.mu);
+  for (int k = 0; k < 2; ++k) {
+    if (!S.buf[k]) BCUDA(cudaMallocHost(&S.buf[k], kStageChunk));
+    if (!S.done[k]) BCUDA(cudaEventCreateWithFlags(&S.done[k], cudaEventDisableTiming));
+  }
+  const int T = host_threads();
+  int slot = 0;
+  for (size_t start = 0; start < total; start += kStageChunk, slot ^= 1) {
+    const size_t len = std::min(kStageChunk, total - start);
+    BCUDA(cudaEventSynchronize(S.done[slot]));  // the chunk's previous copy has finished
+    char* chunk = S.buf[slot];
+    host_parallel(T, T, [&](int64_t t) {
+      const size_t a = start + len * size_t(t) / size_t(T);
+      const size_t e = start + len * size_t(t + 1) / size_t(T);
+      size_t i = size_t(std::upper_bound(off.begin(), off.end(), a) - off.begin()) - 1;
+      for (size_t pos = a; pos < e; ++i) {
+        const size_t take = std::min(e, off[i + 1]) - pos;
+        std::memcpy(chunk + (pos - start), static_cast<const char*>(pieces[i].src) + (pos - off[i]),
+                    take);
+        pos += take;
+      }
+    });
+    BCUDA(cudaMemcpyAsync(static_cast<char*>(dst) + start, chunk, len, cudaMemcpyHostToDevice,
+                          h->stream));
+    BCUDA(cudaEventRecord(S.done[slot], h->stream));
+  }
+  return QP_OK;
+}
+
+// A grow-only pinned host buffer of the process for the packed arrays of a
+// batch: qp_batch_create writes them there from its host threads and copies
+// them to the device from there (a pinned source, no staging).  Its mutex is
+// held until those copies have finished.
+struct HostArena {
+  std::mutex mu;
+  char* p = nullptr;
+  size_t cap = 0;
+};
+
+HostArena& host_arena() {
+  static HostArena a;
+  return a;
 }
 
 qp_status to_float(qp_batch* h, const double* in, float** out, size_t n) {
@@ -378,73 +486,109 @@ qp_status validate_batch_options(const qp_options* o) {
 
 qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
   std::vector<BatchDesc> desc(static_cast<size_t>(count));
-  std::vector<double> qd, c, b, Av, Tv;
-  int64_t F_total = 0;
-  std::vector<int32_t> Arp, Acol, Trp, Tcol, Along, Tlong;
-  std::string why;
+  // 1. Every instance on its own, on host threads: the checks, whether A is
+  // canonical (else a canonical copy), its entry count and the long rows of
+  // A and A' (A' is built in step 3).  The lowest failing instance gives the
+  // error.
+  struct Prep {
+    HostCsr A;  // the canonical copy, only where A is not canonical
+    bool copy = false;
+    int64_t nnz = 0;
+    int32_t n_along = 0, n_tlong = 0;
+  };
+  std::vector<Prep> prep(static_cast<size_t>(count));
+  std::vector<std::string> err(static_cast<size_t>(count));
+  std::atomic<int32_t> first_bad(INT32_MAX);
+  auto fail = [&](int32_t i, std::string why) {
+    err[size_t(i)] = std::move(why);
+    int32_t cur = first_bad.load();
+    while (i < cur && !first_bad.compare_exchange_weak(cur, i)) {
+    }
+  };
+  static const int32_t kZeroRowptr[1] = {0};
+  // the CSR of instance i's A as used (the caller's arrays or the copy)
+  auto a_view = [&](int32_t i) {
+    const qp_instance& q = inst[i];
+    const Prep& P = prep[size_t(i)];
+    if (P.copy) return view_of(P.A);
+    return CsrView{q.m, q.n, q.m > 0 ? q.A_rowptr : kZeroRowptr, q.A_col, q.A_val};
+  };
+  const int nth = host_threads();
+  host_parallel(nth, nth, [&](int64_t t) {
+    std::vector<int32_t> colcount;  // this thread's, reused across its instances
+    for (int64_t ii = int64_t(count) * t / nth; ii < int64_t(count) * (t + 1) / nth; ++ii) {
+      const int32_t i = int32_t(ii);
+      if (i > first_bad.load()) return;
+      const qp_instance& q = inst[i];
+      if (q.n < 1 || q.m < 0 || q.m_eq < 0 || q.m_eq > q.m || q.k < 0 || !q.qd || !q.c ||
+          (q.k > 0 && !q.F) || (q.m > 0 && (!q.b || !q.A_rowptr))) {
+        fail(i, "bad sizes or NULL arrays");
+        continue;
+      }
+      std::string why;
+      bool canonical = true;
+      if (q.m > 0 && !csr_check(q.m, q.n, q.A_rowptr, q.A_col, q.A_val, &why, &canonical)) {
+        fail(i, "A: " + why);
+        continue;
+      }
+      // (F is checked on the device, where it is transposed)
+      if (!finite_all(q.qd, size_t(q.n)) || !finite_all(q.c, size_t(q.n)) ||
+          (q.m > 0 && !finite_all(q.b, size_t(q.m)))) {
+        fail(i, "a value is not finite");
+        continue;
+      }
+      Prep& P = prep[size_t(i)];
+      if (!canonical) {
+        P.A = csr_canonical(q.m, q.n, q.A_rowptr, q.A_col, q.A_val);
+        P.copy = true;
+      }
+      const CsrView V = a_view(i);
+      P.nnz = V.nnz();
+      for (int32_t r = 0; r < q.m; ++r)
+        P.n_along += V.rowptr[r + 1] - V.rowptr[r] > kBatchLongRow;
+      colcount.assign(size_t(q.n), 0);
+      for (int64_t k = 0; k < P.nnz; ++k) colcount[size_t(V.col[k])]++;
+      for (int32_t j = 0; j < q.n; ++j) P.n_tlong += colcount[size_t(j)] > kBatchLongRow;
+    }
+  });
+  if (first_bad.load() < count) {
+    berror("instance %d: %s", first_bad.load(), err[size_t(first_bad.load())].c_str());
+    return QP_ERR_INVALID_ARG;
+  }
+  // 2. Offsets of every instance in the packed arrays (instance order).
+  int64_t n_total = 0, m_total = 0, F_total = 0, arp = 0, ann = 0, trp = 0, tnn = 0;
+  int32_t al = 0, tl = 0;
   for (int32_t i = 0; i < count; ++i) {
     const qp_instance& q = inst[i];
-    if (q.n < 1 || q.m < 0 || q.m_eq < 0 || q.m_eq > q.m || q.k < 0 || !q.qd || !q.c ||
-        (q.k > 0 && !q.F) || (q.m > 0 && (!q.b || !q.A_rowptr))) {
-      berror("instance %d: bad sizes or NULL arrays", i);
-      return QP_ERR_INVALID_ARG;
-    }
-    if (q.m > 0 && !csr_validate(q.m, q.n, q.A_rowptr, q.A_col, q.A_val, &why)) {
-      berror("instance %d: A: %s", i, why.c_str());
-      return QP_ERR_INVALID_ARG;
-    }
-    // (F is checked on the device, where it is transposed)
-    if (!finite_all(q.qd, size_t(q.n)) || !finite_all(q.c, size_t(q.n)) ||
-        (q.m > 0 && !finite_all(q.b, size_t(q.m)))) {
-      berror("instance %d: a value is not finite", i);
-      return QP_ERR_INVALID_ARG;
-    }
-    HostCsr Ac;
-    if (q.m > 0) {
-      Ac = csr_canonical(q.m, q.n, q.A_rowptr, q.A_col, q.A_val);
-    } else {
-      Ac.rows = 0;
-      Ac.cols = q.n;
-      Ac.rowptr.assign(1, 0);
-    }
-    const int64_t nnz = Ac.nnz();
-    std::vector<int32_t> tr(size_t(q.n) + 1), tc(size_t(std::max<int64_t>(nnz, 1)));
-    std::vector<double> tv(size_t(std::max<int64_t>(nnz, 1)));
-    csr_transpose(q.m, q.n, Ac.rowptr.data(), Ac.col.data(), Ac.val.data(), tr.data(), tc.data(),
-                  tv.data());
+    const Prep& P = prep[size_t(i)];
     BatchDesc& d = desc[size_t(i)];
     d.n = q.n;
     d.m = q.m;
     d.m_eq = q.m_eq;
     d.k = q.k;
-    d.off_n = int64_t(c.size());
-    d.off_m = int64_t(b.size());
+    d.off_n = n_total;
+    d.off_m = m_total;
     d.off_F = F_total;
-    d.off_Arp = int64_t(Arp.size());
-    d.off_Ann = int64_t(Acol.size());
-    d.off_Trp = int64_t(Trp.size());
-    d.off_Tnn = int64_t(Tcol.size());
-    d.off_Along = int32_t(Along.size());
-    d.off_Tlong = int32_t(Tlong.size());
+    d.off_Arp = arp;
+    d.off_Ann = ann;
+    d.off_Trp = trp;
+    d.off_Tnn = tnn;
+    d.off_Along = al;
+    d.off_Tlong = tl;
+    d.n_Along = P.n_along;
+    d.n_Tlong = P.n_tlong;
+    n_total += q.n;
+    m_total += q.m;
     F_total += int64_t(q.n) * q.k;
-    qd.insert(qd.end(), q.qd, q.qd + q.n);
-    c.insert(c.end(), q.c, q.c + q.n);
-    if (q.m > 0) b.insert(b.end(), q.b, q.b + q.m);
-    Arp.insert(Arp.end(), Ac.rowptr.begin(), Ac.rowptr.end());
-    Acol.insert(Acol.end(), Ac.col.begin(), Ac.col.end());
-    Av.insert(Av.end(), Ac.val.begin(), Ac.val.end());
-    Trp.insert(Trp.end(), tr.begin(), tr.end());
-    Tcol.insert(Tcol.end(), tc.begin(), tc.begin() + nnz);
-    Tv.insert(Tv.end(), tv.begin(), tv.begin() + nnz);
-    for (int32_t r = 0; r < q.m; ++r)
-      if (Ac.rowptr[size_t(r) + 1] - Ac.rowptr[size_t(r)] > kBatchLongRow) Along.push_back(r);
-    for (int32_t r = 0; r < q.n; ++r)
-      if (tr[size_t(r) + 1] - tr[size_t(r)] > kBatchLongRow) Tlong.push_back(r);
-    d.n_Along = int32_t(Along.size()) - d.off_Along;
-    d.n_Tlong = int32_t(Tlong.size()) - d.off_Tlong;
+    arp += int64_t(q.m) + 1;
+    ann += P.nnz;
+    trp += int64_t(q.n) + 1;
+    tnn += P.nnz;
+    al += d.n_Along;
+    tl += d.n_Tlong;
   }
-  h->n_total = int64_t(c.size());
-  h->m_total = int64_t(b.size());
+  h->n_total = n_total;
+  h->m_total = m_total;
   // bins: instances sorted by n (largest first), cut into equal-count groups
   std::vector<int32_t> ids(static_cast<size_t>(count));
   for (int32_t i = 0; i < count; ++i) ids[size_t(i)] = i;
@@ -492,13 +636,10 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
     int* bad = nullptr;
     BTRY(balloc(h, reinterpret_cast<void**>(&Frow), size_t(F_total) * sizeof(double)));
     BTRY(balloc(h, reinterpret_cast<void**>(&bad), sizeof(int)));
-    for (int32_t i = 0; i < count; ++i) {
-      const qp_instance& q = inst[i];
-      if (q.k > 0)
-        BCUDA(cudaMemcpyAsync(Frow + desc[size_t(i)].off_F, q.F,
-                              size_t(q.n) * size_t(q.k) * sizeof(double), cudaMemcpyHostToDevice,
-                              h->stream));
-    }
+    std::vector<HostPiece> fp;
+    for (int32_t i = 0; i < count; ++i)
+      if (inst[i].k > 0) fp.push_back({inst[i].F, size_t(inst[i].n) * size_t(inst[i].k) * 8});
+    BTRY(staged_upload(h, Frow, fp));
     const int big = INT_MAX;
     BCUDA(cudaMemcpyAsync(bad, &big, sizeof(int), cudaMemcpyHostToDevice, h->stream));
     const int grid = int(std::min<int64_t>((F_total + 255) / 256, int64_t(h->num_sms) * 8));
@@ -514,23 +655,88 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
       return QP_ERR_INVALID_ARG;
     }
   }
-  BTRY(bupload(h, &h->qd64, qd));
-  BTRY(bupload(h, &h->c, c));
-  BTRY(bupload(h, &h->b, b));
-  BTRY(bupload(h, &h->Arp, Arp));
-  BTRY(bupload(h, &h->Acol, Acol));
-  BTRY(bupload(h, &h->Aval64, Av));
-  BTRY(bupload(h, &h->Trp, Trp));
-  BTRY(bupload(h, &h->Tcol, Tcol));
-  BTRY(bupload(h, &h->Tval64, Tv));
-  BTRY(bupload(h, &h->Along, Along));
-  BTRY(bupload(h, &h->Tlong, Tlong));
+  // 3. The packed arrays, written by the host threads into the pinned arena
+  // (A as used, A' by a stable transpose, the vectors, the long-row lists),
+  // then copied to the device from there.
+  {
+    struct Arr {
+      void** dst;
+      size_t bytes;
+      size_t off = 0;
+    };
+    Arr arrs[] = {{reinterpret_cast<void**>(&h->qd64), size_t(n_total) * 8},
+                  {reinterpret_cast<void**>(&h->c), size_t(n_total) * 8},
+                  {reinterpret_cast<void**>(&h->b), size_t(m_total) * 8},
+                  {reinterpret_cast<void**>(&h->Arp), size_t(arp) * 4},
+                  {reinterpret_cast<void**>(&h->Acol), size_t(ann) * 4},
+                  {reinterpret_cast<void**>(&h->Aval64), size_t(ann) * 8},
+                  {reinterpret_cast<void**>(&h->Trp), size_t(trp) * 4},
+                  {reinterpret_cast<void**>(&h->Tcol), size_t(tnn) * 4},
+                  {reinterpret_cast<void**>(&h->Tval64), size_t(tnn) * 8},
+                  {reinterpret_cast<void**>(&h->Along), size_t(al) * 4},
+                  {reinterpret_cast<void**>(&h->Tlong), size_t(tl) * 4}};
+    size_t total = 0;
+    for (Arr& x : arrs) {
+      x.off = total;
+      total += (x.bytes + 255) & ~size_t(255);
+    }
+    HostArena& H = host_arena();
+    std::lock_guard<std::mutex> lock(H.mu);
+    if (H.cap < total) {
+      const size_t cap = std::max(total, H.cap * 2);
+      if (H.p) BCUDA(cudaFreeHost(H.p));
+      H.p = nullptr;
+      H.cap = 0;
+      BCUDA(cudaHostAlloc(reinterpret_cast<void**>(&H.p), cap, cudaHostAllocPortable));
+      H.cap = cap;
+    }
+    double* qd = reinterpret_cast<double*>(H.p + arrs[0].off);
+    double* cc = reinterpret_cast<double*>(H.p + arrs[1].off);
+    double* bb = reinterpret_cast<double*>(H.p + arrs[2].off);
+    int32_t* Arp = reinterpret_cast<int32_t*>(H.p + arrs[3].off);
+    int32_t* Acol = reinterpret_cast<int32_t*>(H.p + arrs[4].off);
+    double* Av = reinterpret_cast<double*>(H.p + arrs[5].off);
+    int32_t* Trp = reinterpret_cast<int32_t*>(H.p + arrs[6].off);
+    int32_t* Tcol = reinterpret_cast<int32_t*>(H.p + arrs[7].off);
+    double* Tv = reinterpret_cast<double*>(H.p + arrs[8].off);
+    int32_t* Along = reinterpret_cast<int32_t*>(H.p + arrs[9].off);
+    int32_t* Tlong = reinterpret_cast<int32_t*>(H.p + arrs[10].off);
+    host_parallel(count, nth, [&](int64_t ii) {
+      const int32_t i = int32_t(ii);
+      const qp_instance& q = inst[i];
+      const BatchDesc& d = desc[size_t(i)];
+      const CsrView V = a_view(i);
+      const size_t nz = size_t(prep[size_t(i)].nnz);
+      std::memcpy(qd + d.off_n, q.qd, size_t(q.n) * 8);
+      std::memcpy(cc + d.off_n, q.c, size_t(q.n) * 8);
+      if (q.m > 0) std::memcpy(bb + d.off_m, q.b, size_t(q.m) * 8);
+      std::memcpy(Arp + d.off_Arp, V.rowptr, (size_t(q.m) + 1) * 4);
+      if (nz > 0) {
+        std::memcpy(Acol + d.off_Ann, V.col, nz * 4);
+        std::memcpy(Av + d.off_Ann, V.val, nz * 8);
+      }
+      int32_t* tr = Trp + d.off_Trp;
+      csr_transpose(q.m, q.n, V.rowptr, V.col, V.val, tr, Tcol + d.off_Tnn, Tv + d.off_Tnn);
+      int32_t* la = Along + d.off_Along;
+      for (int32_t r = 0; r < q.m; ++r)
+        if (V.rowptr[r + 1] - V.rowptr[r] > kBatchLongRow) *la++ = r;
+      int32_t* lt = Tlong + d.off_Tlong;
+      for (int32_t r = 0; r < q.n; ++r)
+        if (tr[r + 1] - tr[r] > kBatchLongRow) *lt++ = r;
+    });
+    for (Arr& x : arrs) {
+      BTRY(balloc(h, x.dst, x.bytes));
+      if (x.bytes > 0)
+        BCUDA(cudaMemcpyAsync(*x.dst, H.p + x.off, x.bytes, cudaMemcpyHostToDevice, h->stream));
+    }
+    BCUDA(cudaStreamSynchronize(h->stream));  // the arena is free again after this
+  }
   BTRY(to_float(h, h->F64, &h->F32, size_t(F_total)));
-  BTRY(to_float(h, h->qd64, &h->qd32, qd.size()));
-  BTRY(to_float(h, h->Aval64, &h->Aval32, Av.size()));
-  BTRY(to_float(h, h->Tval64, &h->Tval32, Tv.size()));
-  BTRY(to_float(h, h->c, &h->c32, c.size()));
-  BTRY(to_float(h, h->b, &h->b32, b.size()));
+  BTRY(to_float(h, h->qd64, &h->qd32, size_t(n_total)));
+  BTRY(to_float(h, h->Aval64, &h->Aval32, size_t(ann)));
+  BTRY(to_float(h, h->Tval64, &h->Tval32, size_t(tnn)));
+  BTRY(to_float(h, h->c, &h->c32, size_t(n_total)));
+  BTRY(to_float(h, h->b, &h->b32, size_t(m_total)));
   for (double** v : {&h->x0, &h->x_out}) {
     BTRY(balloc(h, reinterpret_cast<void**>(v), size_t(h->n_total) * sizeof(double)));
     BCUDA(cudaMemsetAsync(*v, 0, size_t(h->n_total) * sizeof(double), h->stream));
@@ -682,20 +888,27 @@ qp_status qp_batch_solution(const qp_batch* hc, double* x, double* y) {
 
 qp_status qp_batch_set_warm_start(qp_batch* h, const double* x0, const double* y0) {
   if (!h) return QP_ERR_INVALID_ARG;
-  if ((x0 && !finite_all(x0, size_t(h->n_total))) ||
-      (y0 && !finite_all(y0, size_t(h->m_total)))) {
+  // the check on host threads: warm starts of whole batches are millions of values
+  std::atomic<bool> ok(true);
+  const int nth = host_threads();
+  host_parallel(nth, nth, [&](int64_t t) {
+    const int64_t N = h->n_total, M = h->m_total;
+    if (x0 && !finite_all(x0 + N * t / nth, size_t(N * (t + 1) / nth - N * t / nth))) ok = false;
+    if (y0 && !finite_all(y0 + M * t / nth, size_t(M * (t + 1) / nth - M * t / nth))) ok = false;
+  });
+  if (!ok.load()) {
     berror("warm start holds a non-finite value");
     return QP_ERR_INVALID_ARG;
   }
   BTRY(begin(h));
   const size_t nb = size_t(h->n_total) * sizeof(double), mb = size_t(h->m_total) * sizeof(double);
   if (x0)
-    BCUDA(cudaMemcpyAsync(h->x0, x0, nb, cudaMemcpyHostToDevice, h->stream));
+    BTRY(staged_upload(h, h->x0, {{x0, nb}}));
   else
     BCUDA(cudaMemsetAsync(h->x0, 0, nb, h->stream));
   if (mb) {
     if (y0)
-      BCUDA(cudaMemcpyAsync(h->y0, y0, mb, cudaMemcpyHostToDevice, h->stream));
+      BTRY(staged_upload(h, h->y0, {{y0, mb}}));
     else
       BCUDA(cudaMemsetAsync(h->y0, 0, mb, h->stream));
   }
@@ -706,34 +919,52 @@ qp_status qp_batch_set_warm_start(qp_batch* h, const double* x0, const double* y
 
 qp_status qp_batch_set_bounds(qp_batch* h, const double* lo, const double* hi) {
   if (!h) return QP_ERR_INVALID_ARG;
-  const size_t N = size_t(h->n_total);
-  std::vector<double> l(N), u(N);
-  bool any = false;
-  for (size_t j = 0; j < N; ++j) {
-    l[j] = lo ? lo[j] : -INFINITY;
-    u[j] = hi ? hi[j] : INFINITY;
-    if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == INFINITY ||
-        u[j] == -INFINITY) {
-      berror("invalid bounds at packed variable %zu: [%g, %g]", j, l[j], u[j]);
-      return QP_ERR_INVALID_ARG;
+  const int64_t N = h->n_total;
+  // the checks, on host threads over the caller's arrays; the lowest bad
+  // variable is reported
+  std::atomic<int64_t> bad(N);
+  std::atomic<bool> any(false);
+  const int nth = host_threads();
+  host_parallel(nth, nth, [&](int64_t t) {
+    bool fin = false;
+    for (int64_t j = N * t / nth; j < N * (t + 1) / nth; ++j) {
+      const double l = lo ? lo[j] : -INFINITY, u = hi ? hi[j] : INFINITY;
+      if (std::isnan(l) || std::isnan(u) || l > u || l == INFINITY || u == -INFINITY) {
+        int64_t cur = bad.load();
+        while (j < cur && !bad.compare_exchange_weak(cur, j)) {
+        }
+        break;
+      }
+      fin = fin || std::isfinite(l) || std::isfinite(u);
     }
-    any = any || std::isfinite(l[j]) || std::isfinite(u[j]);
+    if (fin) any = true;
+  });
+  if (bad.load() < N) {
+    const int64_t j = bad.load();
+    berror("invalid bounds at packed variable %lld: [%g, %g]", (long long)j,
+           lo ? lo[j] : -INFINITY, hi ? hi[j] : INFINITY);
+    return QP_ERR_INVALID_ARG;
   }
   BTRY(begin(h));
   h->solved = false;
   h->bounded = false;  // set again only once both arrays hold the new bounds
-  if (any) {
-    if (!h->lo) BTRY(balloc(h, reinterpret_cast<void**>(&h->lo), N * sizeof(double)));
-    if (!h->hi) BTRY(balloc(h, reinterpret_cast<void**>(&h->hi), N * sizeof(double)));
-    BCUDA(cudaMemcpyAsync(h->lo, l.data(), N * sizeof(double), cudaMemcpyHostToDevice,
-                          h->stream));
-    BCUDA(cudaMemcpyAsync(h->hi, u.data(), N * sizeof(double), cudaMemcpyHostToDevice,
-                          h->stream));
-    if (!h->lo32) BTRY(balloc(h, reinterpret_cast<void**>(&h->lo32), N * sizeof(float)));
-    if (!h->hi32) BTRY(balloc(h, reinterpret_cast<void**>(&h->hi32), N * sizeof(float)));
-    BTRY(convert_float(h, h->lo, h->lo32, N));
-    BTRY(convert_float(h, h->hi, h->hi32, N));
-    BCUDA(cudaStreamSynchronize(h->stream));  // the staging vectors die here
+  if (any.load()) {
+    if (!h->lo) BTRY(balloc(h, reinterpret_cast<void**>(&h->lo), size_t(N) * sizeof(double)));
+    if (!h->hi) BTRY(balloc(h, reinterpret_cast<void**>(&h->hi), size_t(N) * sizeof(double)));
+    if (!h->lo32) BTRY(balloc(h, reinterpret_cast<void**>(&h->lo32), size_t(N) * sizeof(float)));
+    if (!h->hi32) BTRY(balloc(h, reinterpret_cast<void**>(&h->hi32), size_t(N) * sizeof(float)));
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, int64_t(h->num_sms) * 8)));
+    if (lo)
+      BTRY(staged_upload(h, h->lo, {{lo, size_t(N) * sizeof(double)}}));
+    else
+      k_fill_f64<<<grid, 256, 0, h->stream>>>(h->lo, -INFINITY, (long long)N);
+    if (hi)
+      BTRY(staged_upload(h, h->hi, {{hi, size_t(N) * sizeof(double)}}));
+    else
+      k_fill_f64<<<grid, 256, 0, h->stream>>>(h->hi, INFINITY, (long long)N);
+    BTRY(convert_float(h, h->lo, h->lo32, size_t(N)));
+    BTRY(convert_float(h, h->hi, h->hi32, size_t(N)));
+    BCUDA(cudaStreamSynchronize(h->stream));
     h->bounded = true;
   }
   return finish(h);
