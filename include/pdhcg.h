@@ -539,8 +539,10 @@ qp_status qp_batch_set_bounds(qp_batch* bt, const double* lo, const double* hi);
  * to 4 bins of equal count; each bin is one launch on its own stream, with
  * shared memory and block size fitted to its largest instance.
  * qp_batch_set_threads sets every bin's threads per block: 0 restores the
- * built-in default (64 up to n = 128, else 128); otherwise 64, 128, 256 or
- * 512.  Results can differ from another block size in the last bits (the
+ * built-in default (the smallest of 64, 128, 256, 512 that keeps about 16
+ * warps per SM resident given the bin's shared memory per block, and at
+ * least n/8 threads: 64 up to n ~ 130, 128 up to n ~ 900, 512 at n = 2000
+ * with m ~ 30); otherwise 64, 128, 256 or 512.  Results can differ from another block size in the last bits (the
  * reduction trees differ); a fixed configuration is bit-reproducible. */
 qp_status qp_batch_set_threads(qp_batch* bt, int32_t threads);
 

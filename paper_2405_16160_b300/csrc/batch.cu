@@ -100,8 +100,23 @@ __global__ void k_F_colmajor(const BatchDesc* __restrict__ desc, int count,
 constexpr int kThreadChoices[] = {64, 128, 256, 512};
 constexpr int kMaxBins = 4;
 
-// Default block size for a bin whose largest instance has n variables.
-int default_threads(int max_n) { return max_n <= 128 ? 64 : 128; }
+// Default block size of a bin: the smallest that keeps about 16 warps per
+// SM resident, given the blocks per SM that its vector space in shared memory
+// (smem bytes per block of the mixed adaptive layout, 0 for the global
+// workspace) and the 128-register launch bounds allow, and at least n/8
+// threads for the largest instance (n variables).  The batched kernel is
+// latency-bound, so the warps per SM are what count (measured: 128 threads
+// for n <= 400 at 4 blocks per SM).
+int default_threads(int max_n, size_t smem) {
+  const int per_sm_smem = 228 * 1024;
+  for (int t : kThreadChoices) {
+    const int by_regs = 65536 / (t * 128);
+    const int by_smem = smem > 0 ? int(size_t(per_sm_smem) / (smem + 2048)) : by_regs;
+    const int warps = std::min(by_regs, by_smem) * (t / 32);
+    if (warps >= 16 && t >= std::min(512, max_n / 8)) return t;
+  }
+  return kThreadChoices[3];
+}
 
 }  // namespace
 
@@ -620,7 +635,7 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
         bin.smem[mx][ad] = need + static_smem <= size_t(smem_optin) ? need : 0;
       }
     }
-    bin.threads = default_threads(bin.max_n);
+    bin.threads = default_threads(bin.max_n, bin.smem[1][1]);
     BCUDA(cudaStreamCreateWithFlags(&bin.stream, cudaStreamNonBlocking));
     BCUDA(cudaEventCreateWithFlags(&bin.done, cudaEventDisableTiming));
     BTRY(bupload(h, &bin.order, bin.h_order));
@@ -978,7 +993,8 @@ qp_status qp_batch_set_threads(qp_batch* h, int32_t threads) {
     berror("unsupported block size %d", threads);
     return QP_ERR_INVALID_ARG;
   }
-  for (BatchBin& bin : h->bins) bin.threads = threads == 0 ? default_threads(bin.max_n) : threads;
+  for (BatchBin& bin : h->bins)
+    bin.threads = threads == 0 ? default_threads(bin.max_n, bin.smem[1][1]) : threads;
   return QP_OK;
 }
 

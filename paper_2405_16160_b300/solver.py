@@ -310,8 +310,15 @@ class QPBatch:
                                                               np.cumsum(self.ms)[:-1])
 
     def set_warm_start(self, xs=None, ys=None) -> None:
-        x0 = _f64(np.concatenate(xs), sum(self.ns)) if xs is not None else None
-        y0 = _f64(np.concatenate(ys), sum(self.ms)) if ys is not None else None
+        """Per-instance starting points: lists of arrays, or the packed arrays
+        (instance after instance) as they are."""
+        def pack(vs, total):
+            if vs is None:
+                return None
+            if isinstance(vs, np.ndarray) and vs.ndim == 1:
+                return _f64(vs, total)
+            return _f64(np.concatenate(vs), total)
+        x0, y0 = pack(xs, sum(self.ns)), pack(ys, sum(self.ms))
         L.check(self.lib.qp_batch_set_warm_start(self.h, _ptr(x0, c_double), _ptr(y0, c_double)),
                 "qp_batch_set_warm_start")
 

@@ -122,16 +122,15 @@ def targets(xs, ys) -> np.ndarray:
 
 
 def split_prediction(pred: np.ndarray, n: int, m_eq: int = 1):
-    """Network outputs -> (x0, y0) lists in the solver's variables, projected
-    onto x >= 0 and y >= 0 on the inequality rows."""
+    """Network outputs (one row per instance) -> the packed (x0, y0) of the
+    batch in the solver's variables, instance after instance, projected onto
+    x >= 0 and y >= 0 on the inequality rows (whole-array operations: a batch
+    is thousands of instances)."""
     pred = np.asarray(pred, np.float64)
-    xs = [np.maximum(p[:n] / n, 0.0) for p in pred]
-    ys = []
-    for p in pred:
-        y = p[n:] * Y_SCALE
-        y[m_eq:] = np.maximum(y[m_eq:], 0.0)
-        ys.append(y)
-    return xs, ys
+    x = np.maximum(pred[:, :n] / n, 0.0)
+    y = pred[:, n:] * Y_SCALE
+    y[:, m_eq:] = np.maximum(y[:, m_eq:], 0.0)
+    return x.reshape(-1), y.reshape(-1)
 
 
 def solve_family(insts, options: QPOptions | None = None, warm=None, phases=None, **overrides):
@@ -198,14 +197,22 @@ def train(net: WarmStartMLP, X: np.ndarray, T: np.ndarray, epochs: int, batch: i
     return hist
 
 
-def predict(net: WarmStartMLP, X: np.ndarray, n: int, device: str = "cuda"):
+def predict(net: WarmStartMLP, X: np.ndarray, n: int, device: str = "cuda", m_eq: int = 1):
+    """The packed (x0, y0) of split_prediction for the rows of X, formed on
+    the device from the network's outputs (the same operations, in FP64) and
+    copied to the host once."""
     import torch
 
-    out = []
+    xs, ys = [], []
     for s in range(0, X.shape[0], net.max_batch):
-        out.append(net.forward(torch.as_tensor(X[s:s + net.max_batch], device=device)
-                               .contiguous()).cpu().numpy())
-    return split_prediction(np.concatenate(out), n)
+        pred = net.forward(torch.as_tensor(X[s:s + net.max_batch], device=device)
+                           .contiguous()).double()
+        x = torch.clamp(pred[:, :n] / n, min=0.0)
+        y = pred[:, n:] * Y_SCALE
+        y[:, m_eq:] = torch.clamp(y[:, m_eq:], min=0.0)
+        xs.append(x.reshape(-1))
+        ys.append(y.reshape(-1))
+    return torch.cat(xs).cpu().numpy(), torch.cat(ys).cpu().numpy()
 
 
 def he_normal_params(widths, seed: int = 0) -> np.ndarray:
@@ -242,7 +249,7 @@ class WarmStartModel:
         return model
 
     def propose(self, insts):
-        """(x0s, y0s) for the instances."""
+        """The packed (x0, y0) for the instances (QPBatch.set_warm_start)."""
         return predict(self.net, features(insts), self.n)
 
     def solve(self, insts, options: QPOptions | None = None, phases=None, **overrides):
