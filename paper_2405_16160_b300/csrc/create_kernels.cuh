@@ -57,6 +57,36 @@ constexpr int kScaleGroup = 4;
 constexpr int kScaleRowsPerWarp = 32 / kScaleGroup;
 constexpr int kShortRow = 64;
 
+// A lane's share of a short row's norm: entries b + sub, b + sub + G, ... of
+// the row, four per trip (the column and value loads issued first, then the
+// four gathers of the scaling factor, then the four terms combined in entry
+// order, so the result is that of the plain strided loop).  term(a, dc)
+// gives the entry's term from its value and the gathered factor.
+template <class Term>
+__device__ __forceinline__ double scale_row_part(const CsrT<double>& M, const double* d, int b,
+                                                 int e, int sub, bool inf, Term&& term) {
+  double r = 0.0;
+  for (int k = b + sub; k < e; k += 4 * kScaleGroup) {
+    int c[4];
+    double a[4], dc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int kk = k + u * kScaleGroup;
+      c[u] = kk < e ? __ldg(M.col + kk) : -1;
+      a[u] = kk < e ? __ldg(M.val + kk) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) dc[u] = c[u] >= 0 ? d[c[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (c[u] >= 0) {
+        const double v = term(a[u], dc[u]);
+        r = inf ? fmax(r, v) : r + v;
+      }
+  }
+  return r;
+}
+
 __device__ __forceinline__ double group_combine(double v, bool inf) {
 #pragma unroll
   for (int o = kScaleGroup / 2; o > 0; o >>= 1) {
@@ -87,14 +117,10 @@ __global__ void __launch_bounds__(kBlock) k_scale_norms_n(CsrT<double> Q, CsrT<d
       long_row = (qe - qb) + (ae - ab) > kShortRow;
       if (!long_row) {
         const double dj = d2[j];
-        for (int k = qb + sub; k < qe; k += kScaleGroup) {
-          const double v = (dj * fabs(Q.val[k])) * d2[Q.col[k]];
-          r = inf ? fmax(r, v) : r + v;
-        }
-        for (int k = ab + sub; k < ae; k += kScaleGroup) {
-          const double v = (d1[At.col[k]] * fabs(At.val[k])) * dj;
-          ra = inf ? fmax(ra, v) : ra + v;
-        }
+        r = scale_row_part(Q, d2, qb, qe, sub, inf,
+                           [&](double a, double dc) { return (dj * fabs(a)) * dc; });
+        ra = scale_row_part(At, d1, ab, ae, sub, inf,
+                            [&](double a, double dc) { return (dc * fabs(a)) * dj; });
       }
     }
     r = group_combine(r, inf);
@@ -147,10 +173,8 @@ __global__ void __launch_bounds__(kBlock) k_scale_norms_m(CsrT<double> A,
       long_row = e - b > kShortRow;
       if (!long_row) {
         const double di = d1[i];
-        for (int k = b + sub; k < e; k += kScaleGroup) {
-          const double v = (di * fabs(A.val[k])) * d2[A.col[k]];
-          r = inf ? fmax(r, v) : r + v;
-        }
+        r = scale_row_part(A, d2, b, e, sub, inf,
+                           [&](double a, double dc) { return (di * fabs(a)) * dc; });
       }
     }
     r = group_combine(r, inf);
