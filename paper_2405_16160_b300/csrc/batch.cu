@@ -228,14 +228,9 @@ qp_status convert_float(qp_batch* h, const double* in, float* out, size_t n) {
 // host threads.
 template <class F>
 void host_parallel(int64_t count, int threads, F&& f) {
-  const int T = int(std::max<int64_t>(1, std::min<int64_t>(threads, count)));
-  auto run = [&](int t) {
-    for (int64_t i = count * t / T; i < count * (t + 1) / T; ++i) f(i);
-  };
-  std::vector<std::thread> th;
-  for (int t = 1; t < T; ++t) th.emplace_back(run, t);
-  run(0);
-  for (auto& x : th) x.join();
+  parallel_ranges(count, threads, 1, [&](int, int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) f(i);
+  });
 }
 
 int host_threads() {

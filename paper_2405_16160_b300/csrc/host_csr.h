@@ -4,8 +4,10 @@
 // check itself.  Plain C++, no CUDA.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <string>
+#include <thread>
 #include <vector>
 
 namespace pdhcg {
@@ -69,5 +71,21 @@ bool csr_is_symmetric(const HostCsr& M, double rtol);
 bool csr_penalize(const CsrView& Q, const CsrView& A, int32_t m_eq, const double* c,
                   const double* b, int iters, double eps_zero, int64_t max_products,
                   HostCsr* Qp, std::vector<double>* cp, double* rho, std::string* why);
+
+// f(t, lo, hi) for T contiguous ranges [lo, hi) covering [0, n), range t on
+// host thread t (t = 0 on the caller's), T = min(max_threads, the hardware
+// threads, n / min_per_thread), at least 1.  Returns T.
+template <class F>
+int parallel_ranges(int64_t n, int max_threads, int64_t min_per_thread, F&& f) {
+  const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
+  const int T = int(std::max<int64_t>(
+      1, std::min<int64_t>({int64_t(max_threads), hw, n / std::max<int64_t>(1, min_per_thread)})));
+  auto run = [&](int t) { f(t, n * t / T, n * (t + 1) / T); };
+  std::vector<std::thread> th;
+  for (int t = 1; t < T; ++t) th.emplace_back(run, t);
+  run(0);
+  for (auto& x : th) x.join();
+  return T;
+}
 
 }  // namespace pdhcg

@@ -826,23 +826,36 @@ qp_status upload_csr(qp_handle* h, DevMat* M, const CsrView& H) {
 // The long-row segment table and the medium-row lists (from the host copy of
 // the row pointers), used by the scaling and by every product.
 qp_status build_row_tables(qp_handle* h, DevMat* M, const int32_t* host_rowptr) {
-  // One pass over the rows.  Long rows: fixed-length segments in row order.
+  // Two passes over the rows.  Long rows: fixed-length segments in row order.
   // Medium rows of each precision's row kernels: more than 16 entries per
   // lane of a row group (none with a whole warp per row).  The FP64 kernels
   // give short rows one lane each to keep the DFMA slots full, so a warp per
   // row pays off there only from 64 entries.
-  std::vector<int32_t> lr, sb, se, sp(1, 0), md[2];
+  // Both passes run on host threads over contiguous row ranges, whose
+  // lists are joined in range order (the same lists as one pass in order).
+  constexpr int kMaxThreads = 16;
+  constexpr int64_t kMinRows = 1 << 16;
   // On a skewed matrix the lanes per row follow the rows the grouped loop
   // keeps (at most 64 entries) rather than the overall mean, which the few
   // long rows inflate (A' of a power-law A: a mean of 4 over rows that mostly
   // hold 0-2 entries).
-  int64_t short_rows = 0, short_nnz = 0;
-  for (int32_t i = 0; i < M->rows; ++i) {
-    const int32_t len = host_rowptr[i + 1] - host_rowptr[i];
-    if (len <= 64) {
-      ++short_rows;
-      short_nnz += len;
+  int64_t part_rows[kMaxThreads] = {}, part_nnz[kMaxThreads] = {};
+  const int T1 = parallel_ranges(M->rows, kMaxThreads, kMinRows, [&](int t, int64_t lo, int64_t hi) {
+    int64_t r = 0, z = 0;
+    for (int64_t i = lo; i < hi; ++i) {
+      const int32_t len = host_rowptr[i + 1] - host_rowptr[i];
+      if (len <= 64) {
+        ++r;
+        z += len;
+      }
     }
+    part_rows[t] = r;
+    part_nnz[t] = z;
+  });
+  int64_t short_rows = 0, short_nnz = 0;
+  for (int t = 0; t < T1; ++t) {
+    short_rows += part_rows[t];
+    short_nnz += part_nnz[t];
   }
   if (short_rows > 0 && short_rows < M->rows) {
     M->G64 = group_size_for(short_nnz, short_rows, false);
@@ -853,19 +866,37 @@ qp_status build_row_tables(qp_handle* h, DevMat* M, const int32_t* host_rowptr) 
     const int G = fp32 ? M->G32 : M->G64;
     med_min[fp32] = G >= 32 ? kLongRow : (fp32 ? 16 * G : std::max(16 * G, 64));
   }
-  for (int32_t i = 0; i < M->rows; ++i) {
-    const int32_t b = host_rowptr[i], e = host_rowptr[i + 1];
-    if (e - b <= kLongRow) {
-      if (e - b > med_min[0]) md[0].push_back(i);
-      if (e - b > med_min[1]) md[1].push_back(i);
-      continue;
+  struct Lists {
+    std::vector<int32_t> lr, sb, se, nseg, md[2];
+  };
+  Lists part[kMaxThreads];
+  const int T2 = parallel_ranges(M->rows, kMaxThreads, kMinRows, [&](int t, int64_t lo, int64_t hi) {
+    Lists& L = part[t];
+    for (int64_t ii = lo; ii < hi; ++ii) {
+      const int32_t i = int32_t(ii);
+      const int32_t b = host_rowptr[i], e = host_rowptr[i + 1];
+      if (e - b <= kLongRow) {
+        if (e - b > med_min[0]) L.md[0].push_back(i);
+        if (e - b > med_min[1]) L.md[1].push_back(i);
+        continue;
+      }
+      L.lr.push_back(i);
+      int32_t ns = 0;
+      for (int32_t k = b; k < e; k += kSegLen, ++ns) {
+        L.sb.push_back(k);
+        L.se.push_back(std::min(e, k + kSegLen));
+      }
+      L.nseg.push_back(ns);
     }
-    lr.push_back(i);
-    for (int32_t k = b; k < e; k += kSegLen) {
-      sb.push_back(k);
-      se.push_back(std::min(e, k + kSegLen));
-    }
-    sp.push_back(int32_t(sb.size()));
+  });
+  std::vector<int32_t> lr, sb, se, sp(1, 0), md[2];
+  for (int t = 0; t < T2; ++t) {
+    const Lists& L = part[t];
+    lr.insert(lr.end(), L.lr.begin(), L.lr.end());
+    sb.insert(sb.end(), L.sb.begin(), L.sb.end());
+    se.insert(se.end(), L.se.begin(), L.se.end());
+    for (int32_t ns : L.nseg) sp.push_back(sp.back() + ns);
+    for (int f = 0; f < 2; ++f) md[f].insert(md[f].end(), L.md[f].begin(), L.md[f].end());
   }
   for (int fp32 = 0; fp32 < 2; ++fp32) {
     const std::vector<int32_t>& v = md[fp32];
@@ -1741,10 +1772,92 @@ qp_status time_products(qp_handle* h, DevMat* const* mats, int count, T* const* 
   return st;
 }
 
+// Q's products run only inside the persistent CG kernel (512-thread
+// blocks, 3 per SM, two grid barriers per step), whose lanes per row a plain
+// product does not time well (2 and 4 lanes: within noise of each other as
+// plain products, 109 against 120 us per CG launch on the bench instance).
+// So Q's candidates are timed by the CG kernel itself: launches of two fixed
+// CG steps on scratch vectors and a scratch state, each from r = p = ones and
+// x = Q x = 0, the handle's own solve state untouched.
+template <class T>
+qp_status time_cg(qp_handle* h, int reps, double* us) {
+  const int n = h->n;
+  const size_t N = size_t(n);
+  T *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *qx = nullptr, *r0 = nullptr;
+  double *ones = nullptr, *r0r0 = nullptr;
+  DevState* st = nullptr;
+  qp_status s = QP_OK;
+  for (T** v : {&x, &r, &p, &q, &qx, &r0})
+    if (s == QP_OK) s = dalloc(h, v, N);
+  if (s == QP_OK) s = dalloc(h, &ones, N);
+  if (s == QP_OK) s = dalloc(h, &r0r0, 1);
+  if (s == QP_OK) s = dalloc(h, &st, 1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (s == QP_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    s = QP_ERR_CUDA;
+  if (s == QP_OK) {
+    k_fill<<<h->grid_vec, kBlock, 0, h->stream>>>(ones, 1.0, n);
+    convert(h, (const double*)ones, r0, n);
+    DevState hs{};
+    hs.opt.max_iter = 1ll << 40;
+    hs.opt.cg_mode = kCgFixed;
+    hs.opt.cg_fixed_n = 2;
+    hs.opt.cg_max = 2;
+    hs.opt.barrier_timeout_ms = 2000;
+    hs.opt.step_mode = kStepFixed;
+    hs.tau = 1.0;
+    const double rr = double(n);  // r0'r0 of the ones
+    s = upload(h, st, &hs, sizeof(hs));
+    if (s == QP_OK) s = upload(h, r0r0, &rr, sizeof(rr));
+  }
+  double best = INFINITY;
+  for (int trial = -1; trial < 3 && s == QP_OK; ++trial) {  // trial -1: warm-up
+    double total = 0.0;
+    for (int k = 0; k < reps && s == QP_OK; ++k) {
+      cudaMemcpyAsync(r, r0, N * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
+      cudaMemcpyAsync(p, r0, N * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
+      cudaMemsetAsync(x, 0, N * sizeof(T), h->stream);
+      cudaMemsetAsync(qx, 0, N * sizeof(T), h->stream);
+      cudaEventRecord(e0, h->stream);
+      s = dispatch_g(lanes<T>(h->Q), [&](auto g) {
+        constexpr int G = decltype(g)::value;
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3(h->grid_cg[std::is_same<T, double>::value ? 0 : 1]);
+        cfg.blockDim = dim3(kCgBlock);
+        cfg.stream = h->stream;
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_cg<G, T>, view<T>(h->Q), long_rows_of(h->Q), seg_buf<T>(h->Q),
+                           long_buf<T>(h->Q), x, r, p, q, qx, (const double*)r0r0, h->part_cg,
+                           st, h->bar, n, StepStart<T>{});
+      });
+      cudaEventRecord(e1, h->stream);
+      if (s == QP_OK && cudaEventSynchronize(e1) != cudaSuccess) s = QP_ERR_CUDA;
+      float ms = 0.f;
+      if (s == QP_OK) cudaEventElapsedTime(&ms, e0, e1);
+      total += ms;
+    }
+    if (trial >= 0) best = std::min(best, total * 1e3 / reps);
+  }
+  if (s == QP_OK && cudaGetLastError() != cudaSuccess) s = QP_ERR_CUDA;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* v : {(void*)x, (void*)r, (void*)p, (void*)q, (void*)qx, (void*)r0, (void*)ones,
+                  (void*)r0r0, (void*)st})
+    dev_free(h, v);
+  if (s != QP_OK) set_error("qp_tune: a timed CG launch failed");
+  *us = best;
+  return s;
+}
+
 // Lanes per row (1, 2, 4, 8, 32) and row layout of each matrix in one
-// precision.  Q keeps the warp ranges: its products run inside the
-// persistent CG kernel, where they measured fastest, and a plain product
-// does not time that kernel's layout; A and A' try all three layouts.
+// precision.  Q is timed in the CG kernel (time_cg) and keeps the warp
+// ranges, which measured fastest there; A and A' are timed as plain products
+// in all three layouts.
 template <class T>
 qp_status tune_lanes(qp_handle* h, int pi, DevMat* const* mats, const std::vector<int32_t>* rps,
                      T* const* in, T* const* out, int reps) {
@@ -1764,7 +1877,12 @@ qp_status tune_lanes(qp_handle* h, int pi, DevMat* const* mats, const std::vecto
       for (int l = 0; l < nlayouts; ++l) {
         layout = layouts[l];
         double t = 0.0;
-        QP_TRY(time_products<T>(h, &mats[k], 1, &in[k], &out[k], h->waves, reps, &t));
+        if (k == 0) {  // Q: the CG kernel at these lanes, on its grid
+          QP_TRY(compute_grids(h));
+          QP_TRY(time_cg<T>(h, reps, &t));
+        } else {
+          QP_TRY(time_products<T>(h, &mats[k], 1, &in[k], &out[k], h->waves, reps, &t));
+        }
         if (kLanes[c] == rule && layouts[l] == kRowsWarpRange) t_rule = t;
         if (t < t_best) {
           t_best = t;
