@@ -495,3 +495,28 @@ def test_batch_full_size_range_mixed_meets_tolerance(full_range):
         rescored = O.relkkt(O.problem_from_instance(q.to_instance()), x, y)
         assert rescored.relkkt <= 1e-4, q.name
         assert r["relkkt"] == pytest.approx(rescored.relkkt, rel=1e-9, abs=1e-12), q.name
+
+
+def test_batch_staging_across_chunks_gives_the_same_data():
+    """qp_batch_create copies F through pinned staging chunks of 64 MB: 20
+    instances with n = 2000 and k = 300 (about 96 MB of F, one instance's F
+    spanning the first chunk's end) must solve exactly as the same instances
+    in two batches of 10 (under one chunk each), instance by instance."""
+    insts = W.portfolio_family(3, seeds=range(1, 21), n=2000, k=300, bounds=True)
+    assert sum(q.F.nbytes for q in insts) > 64 << 20
+    with QPBatch(insts) as bt:
+        bt.solve(tol=1e-4, precision=L.PREC_MIXED, step_mode=L.STEP_ADAPTIVE)
+        whole = bt.results()
+        xw, yw = bt.solution()
+    parts = []
+    for half in (insts[:10], insts[10:]):
+        with QPBatch(half) as bt:
+            bt.solve(tol=1e-4, precision=L.PREC_MIXED, step_mode=L.STEP_ADAPTIVE)
+            parts.append((bt.results(), *bt.solution()))
+    res = parts[0][0] + parts[1][0]
+    xs = parts[0][1] + parts[1][1]
+    ys = parts[0][2] + parts[1][2]
+    for i, (a, b) in enumerate(zip(whole, res)):
+        assert a["termination"] == L.TERM_SOLVED, i
+        assert a["attempts"] == b["attempts"] and a["iterations"] == b["iterations"], i
+        assert np.array_equal(xw[i], xs[i]) and np.array_equal(yw[i], ys[i]), i

@@ -101,3 +101,23 @@ def test_warm_start_network_has_its_own_initializer():
     assert np.array_equal(p, WS.he_normal_params(widths, 3))
     assert not np.array_equal(p, WS.he_normal_params(widths, 4))
     assert inspect.signature(WS.WarmStartModel.fit).parameters["init"].default is WS.he_normal_params
+
+
+def test_split_prediction_is_the_per_instance_projection():
+    """The batch's packed warm start from the network's outputs: row i of
+    the outputs gives x_i = max(p[:n] / n, 0) and y_i = p[n:] * Y_SCALE with
+    the inequality rows (after the first m_eq) projected onto y >= 0,
+    instance after instance."""
+    from paper_2405_16160_b300 import warmstart as WS
+    rng = np.random.default_rng(4)
+    count, n, m, m_eq = 6, 9, 5, 2
+    pred = rng.normal(size=(count, n + m)).astype(np.float32)
+    x0, y0 = WS.split_prediction(pred, n, m_eq)
+    assert x0.shape == (count * n,) and y0.shape == (count * m,)
+    for i in range(count):
+        p = pred[i].astype(np.float64)
+        xi = np.array([max(v / n, 0.0) for v in p[:n]])
+        yi = np.array([v * WS.Y_SCALE if r < m_eq else max(v * WS.Y_SCALE, 0.0)
+                       for r, v in enumerate(p[n:])])
+        assert np.array_equal(x0[i * n:(i + 1) * n], xi)
+        assert np.array_equal(y0[i * m:(i + 1) * m], yi)
