@@ -696,6 +696,76 @@ __device__ __forceinline__ void spmv_rows(const CsrT<T>& M, const T* v, F&& f, i
   }
 }
 
+// Rows handed out in chunks: a block takes chunk after chunk of kChunkRows
+// rows from *counter (an atomic, zero at the launch; the kernel's last block
+// puts it back to zero) until none is left, so the SMs that run faster take
+// more of them and the launch ends with the slowest SM's last chunk rather
+// than with its fixed share.  A chunk's rows go to the block's warps as in
+// the block-range layout; chunk_end(c) runs once a chunk is done (the place
+// to store the chunk's partial sums: they are indexed by chunk, so the sums
+// do not depend on which block took which chunk).  Medium rows are left to
+// the caller (spmv_rows' second loop), long rows read the segment pass.
+constexpr int kChunkRows = 512;
+
+template <int GM, class T, class F, class E>
+__device__ __forceinline__ void spmv_rows_chunked(const CsrT<T>& M, const T* v,
+                                                  unsigned int* counter, F&& f, E&& chunk_end) {
+  constexpr int G = GM & (kMedRows - 1);
+  constexpr bool kMed = (GM & kMedRows) != 0;
+  constexpr int kRowsPerWarp = 32 / G;
+  __shared__ int s_chunk;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane & (G - 1);
+  const int wpb = int(blockDim.x >> 5);
+  const int nchunks = (M.rows + kChunkRows - 1) / kChunkRows;
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = int(atomicAdd(counter, 1u));
+    __syncthreads();
+    const int c = s_chunk;
+    if (c >= nchunks) break;
+    const int end = min(M.rows, (c + 1) * kChunkRows);
+    for (int base = c * kChunkRows + int(threadIdx.x >> 5) * kRowsPerWarp; base < end;
+         base += wpb * kRowsPerWarp) {
+      const int i = base + lane / G;
+      T sum = T(0);
+      bool own = i < end;
+      if (own) {
+        const int b = __ldg(M.rowptr + i), e = __ldg(M.rowptr + i + 1);
+        if (e - b > kLongRow) {
+          if (sub == 0) sum = M.long_val[long_slot(M, i)];
+        } else if (kMed && e - b > M.med_min) {
+          own = false;  // a medium row: taken by a whole warp in the caller's pass
+        } else {
+          sum = row_dot<G>(M, v, b, e, sub);
+        }
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) sum += shfl_xor(sum, o);
+      if (own) f(i, sum, sub == 0);
+    }
+    chunk_end(c);  // synchronises the block before s_chunk is written again
+  }
+}
+
+// The medium rows of M (a whole warp each), over the first `blocks` blocks
+// of the grid: spmv_rows' second loop on its own.
+template <int GM, class T, class F>
+__device__ __forceinline__ void spmv_medium_rows(const CsrT<T>& M, const T* v, F&& f,
+                                                 int blocks) {
+  if constexpr ((GM & kMedRows) != 0) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = grid_tid() >> 5;
+    const long long nw = ((long long)blocks * blockDim.x) >> 5;
+    for (long long w = gw; w < M.nmed; w += nw) {
+      const int i = __ldg(M.med_rows + w);
+      T sum = row_dot<32>(M, v, __ldg(M.rowptr + i), __ldg(M.rowptr + i + 1), lane);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += shfl_xor(sum, o);
+      f(i, sum, lane == 0);
+    }
+  }
+}
+
 // Segment sum of a long row by a whole warp (the warp's total, for every
 // lane), with the sum carried beyond FP32.  A row of millions of entries
 // would otherwise pick up an FP32 rounding error that grows with its length,
@@ -1285,7 +1355,6 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
   const int m_eq = st->opt.m_eq;
   if (tr.y_new) {
     typename Acc<T>::type am[2];
-    {
     spmv_rows<G>(A, x, [&](int i, T s, bool lead) {
       if (!lead) return;
       const T da = s - ax[i];
@@ -1307,7 +1376,6 @@ __global__ void __launch_bounds__(kBlock, kDualBlocksPerSm<T>)
       am[0].add_prod(dy, dy);
       am[1].add_prod(dy, da);
     });
-    }
     block_pairs_store<2>(am, tr.part_step + 2 * size_t(blockIdx.x));
     __shared__ int s_last;
     if (threadIdx.x == 0) s_last = take_ticket(tr.ticket, gridDim.x);
@@ -1424,7 +1492,7 @@ __global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSm<T>)
     k_atv(CsrT<T> At, const T* __restrict__ y, T* aty, T* x, T* x_avg, T* qx,
           const T* __restrict__ c, T* r, T* p, double* part_r0, unsigned int* ticket,
           const DevState* st, T* x_save, T* qx_save, const T* __restrict__ y_trial,
-          Commit<T> cm) {
+          Commit<T> cm, double* part_chunk, unsigned int* chunk_ctr) {
   if (!st->iter_active) return;
   const int nb = int(gridDim.x) - cm.blocks;  // the product's blocks
   if (int(blockIdx.x) >= nb) {
@@ -1452,7 +1520,7 @@ __global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSm<T>)
   __syncthreads();
   const T w = s_w;
   const T* yv = adaptive && y_trial != nullptr ? y_trial : y;
-  spmv_rows<G>(At, yv, [&](int i, T s, bool lead) {
+  auto row = [&](int i, T s, bool lead) {
     if (lead) {
       aty[i] = s;
       const T xi = x[i], qxi = qx[i];
@@ -1466,8 +1534,30 @@ __global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSm<T>)
         qx_save[i] = qxi;
       }
     }
-  }, nb);
-  store_and_finish_dot(acc, part_r0, ticket, nb);
+  };
+  // short and long rows in chunks, r0'r0 partial per chunk; then the medium
+  // rows, r0'r0 partial per block; the last block adds the chunks' partials
+  // in chunk order, then the blocks'
+  spmv_rows_chunked<G>(At, yv, chunk_ctr, row, [&](int ch) {
+    block_dot_store(acc, part_chunk + ch);
+    acc = typename Acc<T>::type();
+  });
+  spmv_medium_rows<G>(At, yv, row, nb);
+  __shared__ int s_last;
+  block_dot_store(acc, part_r0 + blockIdx.x);
+  if (threadIdx.x == 0) s_last = take_ticket(ticket, unsigned(nb));
+  __syncthreads();
+  if (s_last) {  // the whole last block (the branch is uniform)
+    const int nchunks = (At.rows + kChunkRows - 1) / kChunkRows;
+    using A = typename Acc<T>::type;
+    const double t_chunks = block_total_dot<8>(part_chunk, nchunks, A());
+    const double t_blocks = block_total_dot<8>(part_r0, nb, A());
+    if (threadIdx.x == 0) {
+      part_r0[nb] = t_chunks + t_blocks;
+      *ticket = 0u;     // for the next launch (ordered by the kernel boundary)
+      *chunk_ctr = 0u;
+    }
+  }
 }
 
 // r0 = p0 = -(qx + c + A'y) and r0'r0 partials, for the first CG after a

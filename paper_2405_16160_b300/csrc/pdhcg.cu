@@ -216,6 +216,8 @@ struct qp_handle {
   VecSet<float> v32;
   double *part_cg = nullptr, *part_n = nullptr, *part_m = nullptr, *part_rn = nullptr,
          *part_rm = nullptr, *part_pow = nullptr, *part2 = nullptr, *part_r0 = nullptr;
+  double* part_chunk = nullptr;       // per-chunk partials of the chunked row kernels
+  unsigned int* chunk_ctr = nullptr;  // their chunk counter (zero between launches)
   double* part_step_m = nullptr;  // adaptive step test partials (2 per k_dual block)
   double* part_step_n = nullptr;  // and the primal move's (2 per CG/BB block)
   double* step_pow = nullptr;     // step_decide's power table (kStepPowTable pairs)
@@ -469,7 +471,7 @@ qp_status launch_atv(qp_handle* h) {
     k_atv<G, T><<<h->grid_n + cm.blocks, kBlock, 0, h->stream>>>(
         view<T>(h->At), v.y, v.aty, it_x(v), it_x_avg(v), v.qx, v.c, v.r, v.p, h->part_r0,
         h->ticket, h->st, ad ? v.x_save : nullptr, ad ? v.qx_save : nullptr,
-        ad ? v.y_new : nullptr, cm);
+        ad ? v.y_new : nullptr, cm, h->part_chunk, h->chunk_ctr);
   });
 }
 
@@ -1467,6 +1469,9 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   QP_TRY(dalloc(h, &h->part_r0, size_t(gn_max) + 1));
   QP_TRY(dalloc(h, &h->ticket, 1));
   CUDA_TRY(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream));
+  QP_TRY(dalloc(h, &h->part_chunk, size_t(std::max(n, m)) / kChunkRows + 2));
+  QP_TRY(dalloc(h, &h->chunk_ctr, 1));
+  CUDA_TRY(cudaMemsetAsync(h->chunk_ctr, 0, sizeof(unsigned int), h->stream));
   QP_TRY(dalloc(h, &h->part_n, size_t(gn_max) * kPartStride));
   QP_TRY(dalloc(h, &h->part_m, size_t(gm_max) * kPartStride));
   QP_TRY(dalloc(h, &h->part_rn, size_t(gmax)));
