@@ -1535,14 +1535,20 @@ __global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSm<T>)
       }
     }
   };
-  // short and long rows in chunks, r0'r0 partial per chunk; then the medium
-  // rows, r0'r0 partial per block; the last block adds the chunks' partials
-  // in chunk order, then the blocks'
+  if constexpr ((G & kMedRows) != 0) {
+    // rows of very uneven lengths (A' of a power-law A): chunks would make
+    // the warps of a block wait for each other at every chunk (measured
+    // slower), so the fixed shares of spmv_rows
+    spmv_rows<G>(At, yv, row, nb);
+    store_and_finish_dot(acc, part_r0, ticket, nb);
+    return;
+  }
+  // short and long rows in chunks, r0'r0 partial per chunk; the last block
+  // adds the chunks' partials in chunk order, then the blocks' (zero here)
   spmv_rows_chunked<G>(At, yv, chunk_ctr, row, [&](int ch) {
     block_dot_store(acc, part_chunk + ch);
     acc = typename Acc<T>::type();
   });
-  spmv_medium_rows<G>(At, yv, row, nb);
   __shared__ int s_last;
   block_dot_store(acc, part_r0 + blockIdx.x);
   if (threadIdx.x == 0) s_last = take_ticket(ticket, unsigned(nb));

@@ -766,9 +766,13 @@ qp_status sync(qp_handle* h) {
 
 // The grid barrier of the persistent kernels, open at barrier 0: count 0,
 // generation 0, both value slots kSlotOpen (all bits set).
+// Before every solve or iteration call: the grid barrier, and the chunk
+// counter of the chunked row pass (k_atv puts it back to zero itself; this
+// covers a call that ended early).
 qp_status reset_barrier(qp_handle* h) {
   CUDA_TRY(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->stream));
   CUDA_TRY(cudaMemsetAsync(h->bar->slot, 0xff, sizeof(h->bar->slot), h->stream));
+  if (h->chunk_ctr) CUDA_TRY(cudaMemsetAsync(h->chunk_ctr, 0, sizeof(unsigned int), h->stream));
   return QP_OK;
 }
 
