@@ -431,9 +431,10 @@ def run_ours(args):
         k: pinned(getattr(inst, k)) for k in ("Q_rowptr", "Q_col", "Q_val", "A_rowptr",
                                               "A_col", "A_val", "c", "b")})
     e2e_times = []
+    # what qp_create copies: Q, A, c and b as given (A' is built on the device)
     h2d = (inst.Q_rowptr.nbytes + inst.Q_col.nbytes + inst.Q_val.nbytes
-           + 2 * (inst.A_rowptr.nbytes + inst.A_col.nbytes + inst.A_val.nbytes)
-           + inst.c.nbytes + inst.b.nbytes + 4 * (inst.n - inst.m))
+           + inst.A_rowptr.nbytes + inst.A_col.nbytes + inst.A_val.nbytes
+           + inst.c.nbytes + inst.b.nbytes)
     d2h = 8 * (inst.n + inst.m)
     e2e_steps = max(1, min(args.steps, 3))
     for s in range(1 + e2e_steps):

@@ -8,6 +8,59 @@
 
 namespace pdhcg {
 
+// ------------------------------------------------------ row tables
+// Row census of a CSR matrix for the row kernels' tables: out[0] = the rows
+// of at most kRuleRowMax entries, out[1] = their entries (the inputs of the
+// lanes-per-row rule), out[2] = the rows of more than kCandidateMin entries
+// (every medium or long row at any lanes per row is among them).  Integer
+// atomics, one per warp: the totals do not depend on the order.
+constexpr int kRuleRowMax = 64;
+constexpr int kCandidateMin = 16;
+
+__global__ void __launch_bounds__(kBlock) k_row_census(const int32_t* __restrict__ rowptr,
+                                                       int rows, unsigned long long* out) {
+  unsigned long long r = 0, z = 0, c = 0;
+  for (long long i = grid_tid(); i < rows; i += grid_threads()) {
+    const int len = __ldg(rowptr + i + 1) - __ldg(rowptr + i);
+    if (len <= kRuleRowMax) {
+      ++r;
+      z += (unsigned long long)len;
+    }
+    c += len > kCandidateMin;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    r += __shfl_xor_sync(0xffffffffu, r, o);
+    z += __shfl_xor_sync(0xffffffffu, z, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (r | z | c) != 0) {
+    atomicAdd(out, r);
+    atomicAdd(out + 1, z);
+    atomicAdd(out + 2, c);
+  }
+}
+
+// The rows of more than min_len entries (a stream-compaction predicate
+// over row indices).
+struct RowLongerThan {
+  const int32_t* rowptr;
+  int32_t min_len;
+  __host__ __device__ __forceinline__ bool operator()(const int32_t& i) const {
+    return rowptr[i + 1] - rowptr[i] > min_len;
+  }
+};
+
+// The first and one-past-last entry of each listed row.
+__global__ void k_row_bounds(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ list,
+                             int count, int32_t* b, int32_t* e) {
+  for (long long k = grid_tid(); k < count; k += grid_threads()) {
+    const int32_t i = list[k];
+    b[k] = rowptr[i];
+    e[k] = rowptr[i + 1];
+  }
+}
+
 // The transpose kernels take one warp per row, so a row of any length is
 // read with coalesced loads.
 

@@ -10,6 +10,8 @@
 
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
+#include <cub/device/device_select.cuh>
+#include <thrust/iterator/counting_iterator.h>
 
 #include <algorithm>
 #include <chrono>
@@ -829,80 +831,111 @@ qp_status upload_csr(qp_handle* h, DevMat* M, const CsrView& H) {
   return QP_OK;
 }
 
-// The long-row segment table and the medium-row lists (from the host copy of
-// the row pointers), used by the scaling and by every product.
-qp_status build_row_tables(qp_handle* h, DevMat* M, const int32_t* host_rowptr) {
-  // Two passes over the rows.  Long rows: fixed-length segments in row order.
-  // Medium rows of each precision's row kernels: more than 16 entries per
-  // lane of a row group (none with a whole warp per row).  The FP64 kernels
-  // give short rows one lane each to keep the DFMA slots full, so a warp per
-  // row pays off there only from 64 entries.
-  // Both passes run on host threads over contiguous row ranges, whose
-  // lists are joined in range order (the same lists as one pass in order).
-  constexpr int kMaxThreads = 16;
-  constexpr int64_t kMinRows = 1 << 16;
-  // On a skewed matrix the lanes per row follow the rows the grouped loop
-  // keeps (at most 64 entries) rather than the overall mean, which the few
-  // long rows inflate (A' of a power-law A: a mean of 4 over rows that mostly
-  // hold 0-2 entries).
-  int64_t part_rows[kMaxThreads] = {}, part_nnz[kMaxThreads] = {};
-  const int T1 = parallel_ranges(M->rows, kMaxThreads, kMinRows, [&](int t, int64_t lo, int64_t hi) {
-    int64_t r = 0, z = 0;
-    for (int64_t i = lo; i < hi; ++i) {
-      const int32_t len = host_rowptr[i + 1] - host_rowptr[i];
-      if (len <= 64) {
-        ++r;
-        z += len;
-      }
-    }
-    part_rows[t] = r;
-    part_nnz[t] = z;
-  });
-  int64_t short_rows = 0, short_nnz = 0;
-  for (int t = 0; t < T1; ++t) {
-    short_rows += part_rows[t];
-    short_nnz += part_nnz[t];
-  }
+// The medium-row threshold at G lanes per row: more than 16 entries per lane
+// of a row group (none with a whole warp per row).  The FP64 kernels give
+// short rows one lane each to keep the DFMA slots full, so a warp per row
+// pays off there only from 64 entries.
+int32_t medium_min(int G, bool fp32) {
+  return G >= 32 ? kLongRow : (fp32 ? 16 * G : std::max(16 * G, 64));
+}
+
+// The long-row segment table and the medium-row lists, used by the scaling
+// and by every product.
+qp_status build_row_tables(qp_handle* h, DevMat* M) {
+  // Long rows: fixed-length segments in row order.  Medium rows of each
+  // precision's row kernels: more than medium_min entries.  On a skewed
+  // matrix the lanes per row follow the rows the grouped loop keeps (at most
+  // kRuleRowMax entries) rather than the overall mean, which the few long
+  // rows inflate (A' of a power-law A: a mean of 4 over rows that mostly hold
+  // 0-2 entries).  The rows are counted and the longer ones listed, in row
+  // order, on the device, where the row pointers already are; only the
+  // totals and those rows' bounds come back.
+  if (M->rows <= 0) return QP_OK;
+  unsigned long long* tot = nullptr;
+  QP_TRY(dalloc(h, &tot, 3));
+  CUDA_TRY(cudaMemsetAsync(tot, 0, 3 * sizeof(unsigned long long), h->stream));
+  const int wave = h->num_sms * 8;
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>((int64_t(M->rows) + kBlock - 1) / kBlock, wave)));
+  k_row_census<<<grid, kBlock, 0, h->stream>>>(M->rowptr, M->rows, tot);
+  unsigned long long ht[3] = {0, 0, 0};
+  CUDA_TRY(cudaMemcpyAsync(ht, tot, sizeof(ht), cudaMemcpyDeviceToHost, h->stream));
+  qp_status st = sync(h);
+  dev_free(h, tot);
+  QP_TRY(st);
+  const int64_t short_rows = int64_t(ht[0]), short_nnz = int64_t(ht[1]), ncand = int64_t(ht[2]);
   if (short_rows > 0 && short_rows < M->rows) {
     M->G64 = group_size_for(short_nnz, short_rows, false);
     M->G32 = group_size_for(short_nnz, short_rows, true);
   }
-  int32_t med_min[2];
-  for (int fp32 = 0; fp32 < 2; ++fp32) {
-    const int G = fp32 ? M->G32 : M->G64;
-    med_min[fp32] = G >= 32 ? kLongRow : (fp32 ? 16 * G : std::max(16 * G, 64));
-  }
-  struct Lists {
-    std::vector<int32_t> lr, sb, se, nseg, md[2];
-  };
-  Lists part[kMaxThreads];
-  const int T2 = parallel_ranges(M->rows, kMaxThreads, kMinRows, [&](int t, int64_t lo, int64_t hi) {
-    Lists& L = part[t];
-    for (int64_t ii = lo; ii < hi; ++ii) {
-      const int32_t i = int32_t(ii);
-      const int32_t b = host_rowptr[i], e = host_rowptr[i + 1];
-      if (e - b <= kLongRow) {
-        if (e - b > med_min[0]) L.md[0].push_back(i);
-        if (e - b > med_min[1]) L.md[1].push_back(i);
-        continue;
+  const int32_t med_min[2] = {medium_min(M->G64, false), medium_min(M->G32, true)};
+  // the rows longer than the smaller threshold (both are at least
+  // kCandidateMin, so ncand bounds their count), with their bounds
+  std::vector<int32_t> rows, rb, re;
+  const int32_t thr = std::min(med_min[0], med_min[1]);
+  if (ncand > 0) {
+    int32_t *sel = nullptr, *num = nullptr, *db = nullptr, *de = nullptr;
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0;
+    const thrust::counting_iterator<int32_t> first(0);
+    const RowLongerThan pred{M->rowptr, thr};
+    CUDA_TRY(cub::DeviceSelect::If(nullptr, tmp_bytes, first, sel, num, M->rows, pred, h->stream));
+    auto step = [&](qp_status s2) {
+      if (st == QP_OK) st = s2;
+    };
+    step(dalloc(h, &sel, size_t(ncand)));
+    step(dalloc(h, &num, 1));
+    step(dev_alloc(h, &tmp, std::max<size_t>(tmp_bytes, 1)));
+    int32_t k = 0;
+    if (st == QP_OK &&
+        cub::DeviceSelect::If(tmp, tmp_bytes, first, sel, num, M->rows, pred, h->stream) !=
+            cudaSuccess)
+      step(QP_ERR_CUDA);
+    if (st == QP_OK && cudaMemcpyAsync(&k, num, sizeof(k), cudaMemcpyDeviceToHost, h->stream) !=
+                           cudaSuccess)
+      step(QP_ERR_CUDA);
+    if (st == QP_OK) step(sync(h));
+    if (st == QP_OK && k > 0) {
+      step(dalloc(h, &db, size_t(k)));
+      step(dalloc(h, &de, size_t(k)));
+      if (st == QP_OK) {
+        k_row_bounds<<<std::max(1, std::min((k + kBlock - 1) / kBlock, wave)), kBlock, 0,
+                       h->stream>>>(M->rowptr, sel, k, db, de);
+        rows.resize(size_t(k));
+        rb.resize(size_t(k));
+        re.resize(size_t(k));
+        const size_t bytes = size_t(k) * sizeof(int32_t);
+        if (cudaMemcpyAsync(rows.data(), sel, bytes, cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(rb.data(), db, bytes, cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(re.data(), de, bytes, cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess)
+          step(QP_ERR_CUDA);
+        step(sync(h));
       }
-      L.lr.push_back(i);
-      int32_t ns = 0;
-      for (int32_t k = b; k < e; k += kSegLen, ++ns) {
-        L.sb.push_back(k);
-        L.se.push_back(std::min(e, k + kSegLen));
-      }
-      L.nseg.push_back(ns);
     }
-  });
+    cudaStreamSynchronize(h->stream);  // no kernel may still use what is freed
+    for (void* p : {(void*)sel, (void*)num, (void*)db, (void*)de, tmp}) dev_free(h, p);
+    if (st != QP_OK) {
+      cudaGetLastError();
+      set_error("row tables: device census failed");
+      return st;
+    }
+  }
   std::vector<int32_t> lr, sb, se, sp(1, 0), md[2];
-  for (int t = 0; t < T2; ++t) {
-    const Lists& L = part[t];
-    lr.insert(lr.end(), L.lr.begin(), L.lr.end());
-    sb.insert(sb.end(), L.sb.begin(), L.sb.end());
-    se.insert(se.end(), L.se.begin(), L.se.end());
-    for (int32_t ns : L.nseg) sp.push_back(sp.back() + ns);
-    for (int f = 0; f < 2; ++f) md[f].insert(md[f].end(), L.md[f].begin(), L.md[f].end());
+  for (size_t k = 0; k < rows.size(); ++k) {
+    const int32_t i = rows[k], b = rb[k], e = re[k];
+    if (e - b <= kLongRow) {
+      if (e - b > med_min[0]) md[0].push_back(i);
+      if (e - b > med_min[1]) md[1].push_back(i);
+      continue;
+    }
+    lr.push_back(i);
+    for (int32_t j = b; j < e; j += kSegLen) {
+      sb.push_back(j);
+      se.push_back(std::min(e, j + kSegLen));
+    }
+    sp.push_back(int32_t(sb.size()));
   }
   for (int fp32 = 0; fp32 < 2; ++fp32) {
     const std::vector<int32_t>& v = md[fp32];
@@ -947,7 +980,7 @@ qp_status finish_matrix(qp_handle* h, DevMat* M) {
 // A' lists increasing rows of A, the order of the host transpose), with the
 // row pointers from per-column counts.  The row pointers also come back to
 // the host for the long-row table.
-qp_status device_transpose(qp_handle* h, int32_t n, std::vector<int32_t>* t_rowptr) {
+qp_status device_transpose(qp_handle* h, int32_t n) {
   const DevMat& A = h->A;
   const int64_t nnz = A.nnz;
   QP_TRY(alloc_matrix(h, &h->At, n, nnz));
@@ -987,10 +1020,7 @@ qp_status device_transpose(qp_handle* h, int32_t n, std::vector<int32_t>* t_rowp
     }
     size_t b = tmp_scan;
     CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, b, count, T.rowptr, n + 1, h->stream));
-    t_rowptr->resize(size_t(n) + 1);
-    CUDA_TRY(cudaMemcpyAsync(t_rowptr->data(), T.rowptr, (size_t(n) + 1) * sizeof(int32_t),
-                             cudaMemcpyDeviceToHost, h->stream));
-    st = sync(h);
+    st = sync(h);  // the temporaries are freed below
   }
   for (void* p : {(void*)count, (void*)row_of, (void*)perm_in, (void*)perm, (void*)keys, tmp})
     dev_free(h, p);
@@ -1437,12 +1467,11 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
     }
   }
   if (h->penalty) QP_TRY(upload_csr(h, &h->Qe, Qown));
-  std::vector<int32_t> t_rowptr;
-  QP_TRY(device_transpose(h, n, &t_rowptr));
-  QP_TRY(build_row_tables(h, &h->Q, Qh.rowptr));
-  QP_TRY(build_row_tables(h, &h->A, Ah.rowptr));
-  QP_TRY(build_row_tables(h, &h->At, t_rowptr.data()));
-  if (h->penalty) QP_TRY(build_row_tables(h, &h->Qe, Qown.rowptr));
+  QP_TRY(device_transpose(h, n));
+  QP_TRY(build_row_tables(h, &h->Q));
+  QP_TRY(build_row_tables(h, &h->A));
+  QP_TRY(build_row_tables(h, &h->At));
+  if (h->penalty) QP_TRY(build_row_tables(h, &h->Qe));
   // Section 4 preprocessing: the solver works on D2 Q D2, D1 A D2, D2 c, D1 b.
   h->scaled = (flags & QP_CREATE_SCALE) != 0;
   if (h->scaled) QP_TRY(device_scaling(h, 10));
@@ -1712,7 +1741,7 @@ namespace {
 // one-lane rows), at most kLongRow; *min_out gets the threshold.
 std::vector<int32_t> medium_rows(const std::vector<int32_t>& rp, int G, bool fp32,
                                  int32_t* min_out) {
-  const int32_t mn = G >= 32 ? kLongRow : (fp32 ? 16 * G : std::max(16 * G, 64));
+  const int32_t mn = medium_min(G, fp32);
   *min_out = mn;
   std::vector<int32_t> out;
   for (size_t i = 0; i + 1 < rp.size(); ++i) {
