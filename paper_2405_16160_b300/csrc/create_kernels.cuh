@@ -110,15 +110,48 @@ constexpr int kScaleGroup = 4;
 constexpr int kScaleRowsPerWarp = 32 / kScaleGroup;
 constexpr int kShortRow = 64;
 
-// A lane's share of a short row's norm: entries b + sub, b + sub + G, ... of
-// the row, four per trip (the column and value loads issued first, then the
-// four gathers of the scaling factor, then the four terms combined in entry
-// order, so the result is that of the plain strided loop).  term(a, dc)
-// gives the entry's term from its value and the gathered factor.
-template <class Term>
-__device__ __forceinline__ double scale_row_part(const CsrT<double>& M, const double* d, int b,
-                                                 int e, int sub, bool inf, Term&& term) {
-  double r = 0.0;
+// Row-norm accumulators of the scaling.  The inf-norm keeps the bit pattern
+// of its largest term: non-negative doubles order as their bit patterns, so
+// the maximum is an integer one and stays off the FP64 pipe (a small fraction
+// of the FP32 rate on this GPU); the 1-norm is a plain FP64 sum of fused
+// products.  Either way a stored entry costs one FP64 instruction.
+template <bool kInf>
+struct NormAcc;
+
+template <>
+struct NormAcc<true> {
+  long long v = 0;  // +0.0
+  __device__ __forceinline__ void add_prod(double a, double b) {
+    v = max(v, __double_as_longlong(a * b));
+  }
+  __device__ __forceinline__ void add(double t) { v = max(v, __double_as_longlong(t)); }
+  __device__ __forceinline__ void merge_shfl(int o) {
+    v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  __device__ __forceinline__ void merge(const NormAcc& o) { v = max(v, o.v); }
+  __device__ __forceinline__ double value() const { return __longlong_as_double(v); }
+};
+
+template <>
+struct NormAcc<false> {
+  double v = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ void add(double t) { v += t; }
+  __device__ __forceinline__ void merge_shfl(int o) {
+    v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  __device__ __forceinline__ void merge(const NormAcc& o) { v += o.v; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
+// A lane's share of a short row's norm of |M_ik| d_k (the row's own factor is
+// applied once to the row's total): entries b + sub, b + sub + G, ... of the
+// row, four per trip (the column and value loads issued first, then the four
+// gathers of the scaling factor, then the four terms in entry order).
+template <bool kInf>
+__device__ __forceinline__ NormAcc<kInf> scale_row_part(const CsrT<double>& M, const double* d,
+                                                        int b, int e, int sub) {
+  NormAcc<kInf> r;
   for (int k = b + sub; k < e; k += 4 * kScaleGroup) {
     int c[4];
     double a[4], dc[4];
@@ -132,134 +165,122 @@ __device__ __forceinline__ double scale_row_part(const CsrT<double>& M, const do
     for (int u = 0; u < 4; ++u) dc[u] = c[u] >= 0 ? d[c[u]] : 0.0;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      if (c[u] >= 0) {
-        const double v = term(a[u], dc[u]);
-        r = inf ? fmax(r, v) : r + v;
-      }
+      if (c[u] >= 0) r.add_prod(fabs(a[u]), dc[u]);
   }
   return r;
 }
 
-__device__ __forceinline__ double group_combine(double v, bool inf) {
+template <bool kInf>
+__device__ __forceinline__ NormAcc<kInf> group_combine(NormAcc<kInf> v) {
 #pragma unroll
-  for (int o = kScaleGroup / 2; o > 0; o >>= 1) {
-    const double u = shfl_xor(v, o);
-    v = inf ? fmax(v, u) : v + u;
-  }
+  for (int o = kScaleGroup / 2; o > 0; o >>= 1) v.merge_shfl(o);
   return v;
 }
 
+template <bool kInf>
+__device__ __forceinline__ NormAcc<kInf> warp_combine(NormAcc<kInf> v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v.merge_shfl(o);
+  return v;
+}
+
+// A row of more than kShortRow entries by a whole warp: the norm of
+// |M_ik| d_k over the row (from the segment pre-pass for rows longer than
+// kLongRow), on every lane.
+template <bool kInf>
+__device__ __forceinline__ NormAcc<kInf> scale_warp_row(const CsrT<double>& M, const double* d,
+                                                        int row, int lane) {
+  const int b = __ldg(M.rowptr + row), e = __ldg(M.rowptr + row + 1);
+  NormAcc<kInf> s;
+  if (e - b > kLongRow) {  // from the segment pre-pass (k_scale_long_parts)
+    if (lane == 0) s.add(M.long_val[long_slot(M, row)]);
+  } else {
+    for (int k = b + lane; k < e; k += 32) s.add_prod(fabs(M.val[k]), d[M.col[k]]);
+  }
+  return warp_combine(s);
+}
+
 // Section 4 scaling of K = [[Q, A'], [A, 0]] under the current D = diag(D2,
-// D1): the norm of each row of D K D, the inf-norm for a Ruiz step (inf = 1)
-// or the 1-norm for the Pock-Chambolle step.  Variable rows j read row j of
-// Q and row j of A'; constraint rows i read row i of A.
+// D1): the norm of each row of D K D, the inf-norm for a Ruiz step (kInf) or
+// the 1-norm for the Pock-Chambolle step.  Variable rows j read row j of Q
+// and row j of A'; constraint rows i read row i of A.  Row j's norm is
+// D2_j times the norm of |K_jk| D_k (the row factor is common to its terms).
+template <bool kInf>
 __global__ void __launch_bounds__(kBlock) k_scale_norms_n(CsrT<double> Q, CsrT<double> At,
                                                           const double* __restrict__ d1,
                                                           const double* __restrict__ d2,
-                                                          double* rn, int inf) {
+                                                          double* rn) {
   const int lane = threadIdx.x & 31, sub = lane & (kScaleGroup - 1);
   const long long nw = grid_threads() >> 5;
   for (long long base = (grid_tid() >> 5) * kScaleRowsPerWarp; base < Q.rows;
        base += nw * kScaleRowsPerWarp) {
     const int j = int(base) + lane / kScaleGroup;
     bool long_row = false;
-    double r = 0.0, ra = 0.0;
+    NormAcc<kInf> r, ra;
     if (j < Q.rows) {
       const int qb = __ldg(Q.rowptr + j), qe = __ldg(Q.rowptr + j + 1);
       const int ab = __ldg(At.rowptr + j), ae = __ldg(At.rowptr + j + 1);
       long_row = (qe - qb) + (ae - ab) > kShortRow;
       if (!long_row) {
-        const double dj = d2[j];
-        r = scale_row_part(Q, d2, qb, qe, sub, inf,
-                           [&](double a, double dc) { return (dj * fabs(a)) * dc; });
-        ra = scale_row_part(At, d1, ab, ae, sub, inf,
-                            [&](double a, double dc) { return (dc * fabs(a)) * dj; });
+        r = scale_row_part<kInf>(Q, d2, qb, qe, sub);
+        ra = scale_row_part<kInf>(At, d1, ab, ae, sub);
       }
     }
-    r = group_combine(r, inf);
-    ra = group_combine(ra, inf);
-    if (j < Q.rows && !long_row && sub == 0) rn[j] = inf ? fmax(r, ra) : r + ra;
+    r = group_combine(r);
+    ra = group_combine(ra);
+    if (j < Q.rows && !long_row && sub == 0) {
+      r.merge(ra);
+      rn[j] = d2[j] * r.value();
+    }
     unsigned lm = __ballot_sync(0xffffffffu, long_row && sub == 0);
     while (lm) {
       const int jj = int(base) + (__ffs(lm) - 1) / kScaleGroup;
       lm &= lm - 1;
-      const double dj = d2[jj];
-      double s = 0.0, sa = 0.0;
-      const int qb = __ldg(Q.rowptr + jj), qe = __ldg(Q.rowptr + jj + 1);
-      const int ab = __ldg(At.rowptr + jj), ae = __ldg(At.rowptr + jj + 1);
-      if (qe - qb > kLongRow) {  // from the segment pre-pass (k_scale_long_parts)
-        if (lane == 0) s = dj * Q.long_val[long_slot(Q, jj)];
-      } else {
-        for (int k = qb + lane; k < qe; k += 32) {
-          const double v = (dj * fabs(Q.val[k])) * d2[Q.col[k]];
-          s = inf ? fmax(s, v) : s + v;
-        }
-      }
-      if (ae - ab > kLongRow) {
-        if (lane == 0) sa = dj * At.long_val[long_slot(At, jj)];
-      } else {
-        for (int k = ab + lane; k < ae; k += 32) {
-          const double v = (d1[At.col[k]] * fabs(At.val[k])) * dj;
-          sa = inf ? fmax(sa, v) : sa + v;
-        }
-      }
-      s = inf ? warp_max_d(s) : warp_sum(s);
-      sa = inf ? warp_max_d(sa) : warp_sum(sa);
-      if (lane == 0) rn[jj] = inf ? fmax(s, sa) : s + sa;
+      NormAcc<kInf> s = scale_warp_row<kInf>(Q, d2, jj, lane);
+      s.merge(scale_warp_row<kInf>(At, d1, jj, lane));
+      if (lane == 0) rn[jj] = d2[jj] * s.value();
     }
   }
 }
 
+template <bool kInf>
 __global__ void __launch_bounds__(kBlock) k_scale_norms_m(CsrT<double> A,
                                                           const double* __restrict__ d1,
                                                           const double* __restrict__ d2,
-                                                          double* rm, int inf) {
+                                                          double* rm) {
   const int lane = threadIdx.x & 31, sub = lane & (kScaleGroup - 1);
   const long long nw = grid_threads() >> 5;
   for (long long base = (grid_tid() >> 5) * kScaleRowsPerWarp; base < A.rows;
        base += nw * kScaleRowsPerWarp) {
     const int i = int(base) + lane / kScaleGroup;
     bool long_row = false;
-    double r = 0.0;
+    NormAcc<kInf> r;
     if (i < A.rows) {
       const int b = __ldg(A.rowptr + i), e = __ldg(A.rowptr + i + 1);
       long_row = e - b > kShortRow;
-      if (!long_row) {
-        const double di = d1[i];
-        r = scale_row_part(A, d2, b, e, sub, inf,
-                           [&](double a, double dc) { return (di * fabs(a)) * dc; });
-      }
+      if (!long_row) r = scale_row_part<kInf>(A, d2, b, e, sub);
     }
-    r = group_combine(r, inf);
-    if (i < A.rows && !long_row && sub == 0) rm[i] = r;
+    r = group_combine(r);
+    if (i < A.rows && !long_row && sub == 0) rm[i] = d1[i] * r.value();
     unsigned lm = __ballot_sync(0xffffffffu, long_row && sub == 0);
     while (lm) {
       const int ii = int(base) + (__ffs(lm) - 1) / kScaleGroup;
       lm &= lm - 1;
-      const double di = d1[ii];
-      double s = 0.0;
-      const int b = __ldg(A.rowptr + ii), e = __ldg(A.rowptr + ii + 1);
-      if (e - b > kLongRow) {  // from the segment pre-pass (k_scale_long_parts)
-        if (lane == 0) s = di * A.long_val[long_slot(A, ii)];
-      } else {
-        for (int k = b + lane; k < e; k += 32) {
-          const double v = (di * fabs(A.val[k])) * d2[A.col[k]];
-          s = inf ? fmax(s, v) : s + v;
-        }
-      }
-      s = inf ? warp_max_d(s) : warp_sum(s);
-      if (lane == 0) rm[ii] = s;
+      const NormAcc<kInf> s = scale_warp_row<kInf>(A, d2, ii, lane);
+      if (lane == 0) rm[ii] = d1[ii] * s.value();
     }
   }
 }
 
-// D <- D / sqrt(row norm); an all-zero row keeps its scale.
+// D <- D / sqrt(row norm), as D times the reciprocal square root (one
+// library call instead of a square root and a division, both long FP64
+// sequences on this GPU); an all-zero row keeps its scale.
 __global__ void k_scale_apply(double* d2, const double* __restrict__ rn, int n, double* d1,
                               const double* __restrict__ rm, int m) {
   for (long long j = grid_tid(); j < n; j += grid_threads())
-    d2[j] /= sqrt(rn[j] > 0.0 ? rn[j] : 1.0);
+    d2[j] *= rsqrt(rn[j] > 0.0 ? rn[j] : 1.0);
   for (long long i = grid_tid(); i < m; i += grid_threads())
-    d1[i] /= sqrt(rm[i] > 0.0 ? rm[i] : 1.0);
+    d1[i] *= rsqrt(rm[i] > 0.0 ? rm[i] : 1.0);
 }
 
 // M_ik <- (dr_i M_ik) dc_k in place (rows split as in the norm kernels).
@@ -299,29 +320,27 @@ __global__ void __launch_bounds__(kBlock) k_scale_matrix(CsrT<double> M,
 //
 // Norm pass, phase 1: seg[s] = the segment's inf- or 1-norm of |M_ik| dc_k
 // (the row's own factor is applied by the row kernels).
+template <bool kInf>
 __global__ void __launch_bounds__(kBlock) k_scale_long_parts(CsrT<double> M, LongRows L,
                                                              const double* __restrict__ dc,
-                                                             double* seg, int inf) {
+                                                             double* seg) {
   const int lane = threadIdx.x & 31;
   for (long long sg = grid_tid() >> 5; sg < L.nseg; sg += grid_threads() >> 5) {
-    double v = 0.0;
-    for (int k = __ldg(L.seg_begin + sg) + lane; k < __ldg(L.seg_end + sg); k += 32) {
-      const double a = fabs(M.val[k]) * dc[M.col[k]];
-      v = inf ? fmax(v, a) : v + a;
-    }
-    v = inf ? warp_max_d(v) : warp_sum(v);
-    if (lane == 0) seg[sg] = v;
+    NormAcc<kInf> v;
+    for (int k = __ldg(L.seg_begin + sg) + lane; k < __ldg(L.seg_end + sg); k += 32)
+      v.add_prod(fabs(M.val[k]), dc[M.col[k]]);
+    v = warp_combine(v);
+    if (lane == 0) seg[sg] = v.value();
   }
 }
 
 // Phase 2: each long row's segments in order.
-__global__ void k_scale_long_totals(LongRows L, const double* __restrict__ seg, double* total,
-                                    int inf) {
+template <bool kInf>
+__global__ void k_scale_long_totals(LongRows L, const double* __restrict__ seg, double* total) {
   for (long long r = grid_tid(); r < L.nlong; r += grid_threads()) {
-    double v = 0.0;
-    for (int s = __ldg(L.seg_ptr + r); s < __ldg(L.seg_ptr + r + 1); ++s)
-      v = inf ? fmax(v, seg[s]) : v + seg[s];
-    total[r] = v;
+    NormAcc<kInf> v;
+    for (int s = __ldg(L.seg_ptr + r); s < __ldg(L.seg_ptr + r + 1); ++s) v.add(seg[s]);
+    total[r] = v.value();
   }
 }
 

@@ -1060,13 +1060,26 @@ qp_status device_scaling(qp_handle* h, int ruiz_iters) {
     const CsrT<double> Q = view<double>(h->Q), A = view<double>(h->A), At = view<double>(h->At);
     // rows longer than kLongRow: one warp per segment, into the matrix's
     // FP64 long-row buffer, which the norm kernels read
-    auto long_parts = [&](const DevMat& M, const double* dc, int inf) {
+    auto long_parts = [&](const DevMat& M, const double* dc, auto inf) {
+      constexpr bool kInf = decltype(inf)::value;
       if (M.nlong == 0) return;
       const int gs = std::max(1, std::min(wave, (M.nseg + kBlock / 32 - 1) / (kBlock / 32)));
-      k_scale_long_parts<<<gs, kBlock, 0, h->stream>>>(view<double>(M), long_rows_of(M), dc,
-                                                        M.seg64, inf);
-      k_scale_long_totals<<<std::max(1, (M.nlong + kBlock - 1) / kBlock), kBlock, 0,
-                            h->stream>>>(long_rows_of(M), M.seg64, M.long64, inf);
+      k_scale_long_parts<kInf><<<gs, kBlock, 0, h->stream>>>(view<double>(M), long_rows_of(M),
+                                                              dc, M.seg64);
+      k_scale_long_totals<kInf><<<std::max(1, (M.nlong + kBlock - 1) / kBlock), kBlock, 0,
+                                  h->stream>>>(long_rows_of(M), M.seg64, M.long64);
+    };
+    // one norm pass: the inf-norm of a Ruiz step or the 1-norm of the
+    // Pock-Chambolle step
+    auto norm_pass = [&](auto inf) {
+      constexpr bool kInf = decltype(inf)::value;
+      long_parts(h->Q, d2, inf);
+      long_parts(h->At, d1, inf);
+      k_scale_norms_n<kInf><<<warp_grid(n), kBlock, 0, h->stream>>>(Q, At, d1, d2, rn);
+      if (m > 0) {
+        long_parts(h->A, d2, inf);
+        k_scale_norms_m<kInf><<<warp_grid(m), kBlock, 0, h->stream>>>(A, d1, d2, rm);
+      }
     };
     auto scale_matrix = [&](const DevMat& M, const double* dr, const double* dc) {
       k_scale_matrix<<<warp_grid(M.rows), kBlock, 0, h->stream>>>(view<double>(M), dr, dc,
@@ -1077,14 +1090,10 @@ qp_status device_scaling(qp_handle* h, int ruiz_iters) {
                                                          dc, M.val);
     };
     for (int it = 0; it <= ruiz_iters; ++it) {
-      const int inf = it < ruiz_iters ? 1 : 0;
-      long_parts(h->Q, d2, inf);
-      long_parts(h->At, d1, inf);
-      k_scale_norms_n<<<warp_grid(n), kBlock, 0, h->stream>>>(Q, At, d1, d2, rn, inf);
-      if (m > 0) {
-        long_parts(h->A, d2, inf);
-        k_scale_norms_m<<<warp_grid(m), kBlock, 0, h->stream>>>(A, d1, d2, rm, inf);
-      }
+      if (it < ruiz_iters)
+        norm_pass(std::true_type{});
+      else
+        norm_pass(std::false_type{});
       k_scale_apply<<<h->grid_vec, kBlock, 0, h->stream>>>(d2, rn, n, d1, rm, m);
     }
     scale_matrix(h->Q, d2, d2);
