@@ -344,11 +344,12 @@ qp_status qp_get_penalty(const qp_handle* h, double* rho);
  *                entries (64 at least in FP64) go to one whole warp each
  *   lanes_rule   the choice of the mean-row-length rule applied at qp_create
  *   layout       how rows go to warps: 0 groups of 32 / G rows across the grid
- *                in turn, 1 a contiguous range per warp (the default), 2 a
- *                contiguous range per block whose groups its warps take in turn
+ *                in turn (the default for A and A'), 1 a contiguous range per
+ *                warp (the default for Q), 2 a contiguous range per block whose
+ *                groups its warps take in turn
  *   product_us   one product at the shape in use, microseconds (qp_tune's
  *                best-of-three timing; 0 before qp_tune)
- *   product_us_rule  the same product at the rule's lanes
+ *   product_us_rule  the same product at the rule's lanes and layout
  *   waves        grid of the non-persistent row kernels in waves of
  *                co-resident blocks (1 at qp_create)
  *   waves_us[w]  qp_tune: the three products of the mixed path (Q, A, A'

@@ -62,8 +62,17 @@ void set_error(const char* fmt, ...) {
 // runs at ~1/58 of FP32), so short rows get one lane each: every DFMA issues
 // with most lanes busy and no shuffle-add tree is needed.  FP32: the kernels
 // are bound by memory, so rows of ~10 entries share 4 lanes for coalescing.
-int group_size_for(int64_t nnz, int64_t rows, bool fp32) {
+// FP32 Q in the CG kernel (cg): the fewest lanes that take a row of the mean
+// length in at most two trips of the four-entry unroll (8 G entries), as
+// qp_tune measured there on both workload families (9 entries per row: 2
+// lanes, 9% faster than 4; 6 entries: 1 lane, 22% faster than 4).
+int group_size_for(int64_t nnz, int64_t rows, bool fp32, bool cg = false) {
   const double avg = rows > 0 ? double(nnz) / double(rows) : 0.0;
+  if (fp32 && cg) {
+    for (int g : {1, 2, 4, 8})
+      if (avg <= 8.0 * g) return g;
+    return 32;
+  }
   if (fp32) {
     if (avg <= 3.0) return 1;
     if (avg <= 6.0) return 2;
@@ -86,6 +95,7 @@ struct DevMat {
   int64_t nnz = 0;
   int G64 = 1, G32 = 4;
   int layout64 = kRowsWarpRange, layout32 = kRowsWarpRange;  // rows to warps (qp_tune)
+  bool cg = false;  // Q: its products run in the CG kernel (its own lanes rule)
   // medium rows (more than 16 G entries, at most kLongRow) per precision
   int32_t *med64 = nullptr, *med32 = nullptr;
   int32_t nmed64 = 0, nmed32 = 0, med_min64 = 0x7fffffff, med_min32 = 0x7fffffff;
@@ -319,6 +329,10 @@ qp_status dispatch_g(int G, F&& f) {
     default: set_error("unsupported group size %d", G); return QP_ERR_INVALID_ARG;
   }
 }
+
+// The rule's row layout: warp ranges for Q (its CG kernel), grid-stride row
+// groups for A and A'.
+int rule_layout(bool q) { return q ? kRowsWarpRange : kRowsGridStride; }
 
 // Largest grid of the non-persistent row kernels qp_tune may pick, in waves.
 constexpr int kMaxWaves = 4;
@@ -807,7 +821,7 @@ qp_status alloc_matrix(qp_handle* h, DevMat* M, int32_t rows, int64_t nnz) {
   M->rows = rows;
   M->nnz = nnz;
   M->G64 = group_size_for(nnz, rows, false);
-  M->G32 = group_size_for(nnz, rows, true);
+  M->G32 = group_size_for(nnz, rows, true, M->cg);
   QP_TRY(dalloc(h, &M->rowptr, size_t(rows) + 1));
   QP_TRY(dalloc(h, &M->col, size_t(nnz)));
   QP_TRY(dalloc(h, &M->val, size_t(nnz)));
@@ -865,7 +879,7 @@ qp_status build_row_tables(qp_handle* h, DevMat* M) {
   const int64_t short_rows = int64_t(ht[0]), short_nnz = int64_t(ht[1]), ncand = int64_t(ht[2]);
   if (short_rows > 0 && short_rows < M->rows) {
     M->G64 = group_size_for(short_nnz, short_rows, false);
-    M->G32 = group_size_for(short_nnz, short_rows, true);
+    M->G32 = group_size_for(short_nnz, short_rows, true, M->cg);
   }
   const int32_t med_min[2] = {medium_min(M->G64, false), medium_min(M->G32, true)};
   // the rows longer than the smaller threshold (both are at least
@@ -1447,6 +1461,7 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   h->grid_vec =
       int(std::max<int64_t>(1, std::min<int64_t>((std::max(n, m) + kBlock - 1) / kBlock, wave)));
   // Q, A, c and b go to the device as given; A' is built there.
+  h->Q.cg = true;
   QP_TRY(upload_csr(h, &h->Q, Qh));
   QP_TRY(upload_csr(h, &h->A, Ah));
   QP_TRY(alloc_vecs<double>(h));
@@ -1481,6 +1496,10 @@ qp_status create_impl(qp_handle* h, int32_t n, int32_t m, int32_t m_eq, const in
   QP_TRY(build_row_tables(h, &h->A));
   QP_TRY(build_row_tables(h, &h->At));
   if (h->penalty) QP_TRY(build_row_tables(h, &h->Qe));
+  // A and A' (products in the non-persistent row kernels): groups of rows
+  // across the grid, which qp_tune measured fastest for both on both
+  // workload families; Q keeps the warp ranges of its CG kernel.
+  for (DevMat* M : {&h->A, &h->At}) M->layout64 = M->layout32 = rule_layout(false);
   // Section 4 preprocessing: the solver works on D2 Q D2, D1 A D2, D2 c, D1 b.
   h->scaled = (flags & QP_CREATE_SCALE) != 0;
   if (h->scaled) QP_TRY(device_scaling(h, 10));
@@ -1917,7 +1936,8 @@ qp_status tune_lanes(qp_handle* h, int pi, DevMat* const* mats, const std::vecto
     const int rule = h->shapes.lanes_rule[pi][k];
     const int nlayouts = k == 0 ? 1 : 3;
     const int layouts[3] = {kRowsWarpRange, kRowsGridStride, kRowsBlockRange};
-    int best_g = rule, best_l = kRowsWarpRange;
+    const int rule_l = rule_layout(k == 0);
+    int best_g = rule, best_l = rule_l;
     double t_best = INFINITY, t_rule = INFINITY;
     for (int c = 0; c < 5; ++c) {
       QP_TRY(set_lanes(h, M, fp32, kLanes[c], rps[k]));
@@ -1930,7 +1950,7 @@ qp_status tune_lanes(qp_handle* h, int pi, DevMat* const* mats, const std::vecto
         } else {
           QP_TRY(time_products<T>(h, &mats[k], 1, &in[k], &out[k], h->waves, reps, &t));
         }
-        if (kLanes[c] == rule && layouts[l] == kRowsWarpRange) t_rule = t;
+        if (kLanes[c] == rule && layouts[l] == rule_l) t_rule = t;
         if (t < t_best) {
           t_best = t;
           best_g = kLanes[c];
@@ -1941,7 +1961,7 @@ qp_status tune_lanes(qp_handle* h, int pi, DevMat* const* mats, const std::vecto
     // the rule's shape unless another was faster by more than 1%
     if (!(t_best < 0.99 * t_rule)) {
       best_g = rule;
-      best_l = kRowsWarpRange;
+      best_l = rule_l;
       t_best = t_rule;
     }
     QP_TRY(set_lanes(h, M, fp32, best_g, rps[k]));

@@ -117,16 +117,22 @@ def test_unsorted_rows_and_duplicates_solve_as_the_canonical_problem():
     assert np.max(np.abs(y1 - y0)) <= 1e-12 * max(1.0, np.max(np.abs(y0)))
 
 
-def _rule_lanes(lens, fp32):
+def _rule_lanes(lens, fp32, cg=False):
     """The mean-row-length rule of qp_create: the mean over the rows of at
-    most 64 entries when some rows are longer, else over all rows."""
+    most 64 entries when some rows are longer, else over all rows; FP32 Q
+    (cg, its products in the CG kernel) takes the fewest lanes G with a mean
+    of at most 8 G entries."""
     short = lens <= 64
     if 0 < short.sum() < lens.size:
         avg = lens[short].sum() / short.sum()
     else:
         avg = lens.sum() / max(lens.size, 1)
-    steps = [(3.0, 1), (6.0, 2), (20.0, 4), (64.0, 8)] if fp32 else \
-        [(24.0, 1), (64.0, 4), (256.0, 8)]
+    if fp32 and cg:
+        steps = [(8.0, 1), (16.0, 2), (32.0, 4), (64.0, 8)]
+    elif fp32:
+        steps = [(3.0, 1), (6.0, 2), (20.0, 4), (64.0, 8)]
+    else:
+        steps = [(24.0, 1), (64.0, 4), (256.0, 8)]
     for bound, g in steps:
         if avg <= bound:
             return g
@@ -139,11 +145,16 @@ def _rule_lanes(lens, fp32):
                          ids=["uniform", "power_law", "dense"])
 def test_row_census_gives_the_rule_of_the_row_lengths(make):
     """The row counts behind the lanes per row are taken on the device; the
-    choice must be the rule applied to the row lengths of Q, A and A'."""
+    choice must be the rule applied to the row lengths of Q, A and A', and
+    the row layouts the rule's: warp ranges for Q, grid-stride groups for A
+    and A'."""
     inst = make()
     lens = [np.diff(inst.Q_rowptr), np.diff(inst.A_rowptr),
             np.bincount(inst.A_col, minlength=inst.n)]
     with QPSolver(inst) as s:
-        rule = s.shapes()["lanes_rule"]
+        sh = s.shapes()
+    rule = sh["lanes_rule"]
     for p, fp32 in ((0, False), (1, True)):
-        assert rule[p] == [_rule_lanes(l, fp32) for l in lens], (p, rule)
+        assert rule[p] == [_rule_lanes(l, fp32, k == 0) for k, l in enumerate(lens)], (p, rule)
+        assert sh["lanes"][p] == rule[p]
+        assert sh["layout"][p] == [1, 0, 0], sh["layout"]
