@@ -737,12 +737,17 @@ qp_status capture_chunk(qp_handle* h, int iters, bool coop) {
   return QP_OK;
 }
 
+// A captured chunk of this precision, length, step rule and bounds form exists.
+template <class T>
+bool chunk_ready(const qp_handle* h, int iters) {
+  const int pi = std::is_same<T, double>::value ? 0 : 1;
+  return h->chunk_exec[pi] && h->chunk_iters[pi] == iters && h->chunk_step[pi] == h->step_mode &&
+         h->chunk_bounded[pi] == (h->bounded ? 1 : 0);
+}
+
 template <class T>
 qp_status ensure_chunk(qp_handle* h, int iters) {
-  const int pi = std::is_same<T, double>::value ? 0 : 1;
-  if (h->chunk_exec[pi] && h->chunk_iters[pi] == iters && h->chunk_step[pi] == h->step_mode &&
-      h->chunk_bounded[pi] == (h->bounded ? 1 : 0))
-    return QP_OK;
+  if (chunk_ready<T>(h, iters)) return QP_OK;
   if (h->coop_ok) {
     qp_status s = capture_chunk<T>(h, iters, true);
     if (s == QP_OK) return QP_OK;
@@ -1593,9 +1598,14 @@ template <class T>
 qp_status run_chunks(qp_handle* h, const qp_options* o, bool timing,
                      std::chrono::steady_clock::time_point t0, qp_info* info, int* term) {
   // Graph replay normally; with kernel_timing the same chunk is launched
-  // directly so that events can bracket each CG launch on its stream.
+  // directly so that events can bracket each CG launch on its stream.  With
+  // no graph of this shape yet, the first chunk is launched directly too and
+  // the graph is captured and instantiated while the GPU runs it (capture
+  // only records; the work already queued on the stream runs meanwhile), so
+  // a fresh handle does not wait for the capture, and a solve that ends
+  // within one chunk needs none.
   if (timing) QP_TRY(ensure_events(h, o->eval_freq));
-  else QP_TRY(ensure_chunk<T>(h, o->eval_freq));
+  bool direct_first = !timing && !chunk_ready<T>(h, o->eval_freq);
   const int pi = std::is_same<T, double>::value ? 0 : 1;
   cudaError_t timing_error = cudaSuccess;
   const bool stall_rule =
@@ -1606,6 +1616,11 @@ qp_status run_chunks(qp_handle* h, const qp_options* o, bool timing,
     if (timing) {
       QP_TRY(enqueue_chunk<T>(h, o->eval_freq, h->coop_ok, h->ev.data()));
       QP_TRY(check_launch());
+    } else if (direct_first) {
+      direct_first = false;
+      QP_TRY(enqueue_chunk<T>(h, o->eval_freq, h->coop_ok, nullptr));
+      QP_TRY(check_launch());
+      QP_TRY(ensure_chunk<T>(h, o->eval_freq));
     } else {
       CUDA_TRY(cudaGraphLaunch(h->chunk_exec[pi], h->stream));
     }
