@@ -536,6 +536,17 @@ qp_status qp_batch_set_warm_start(qp_batch* bt, const double* x0, const double* 
  */
 qp_status qp_batch_set_bounds(qp_batch* bt, const double* lo, const double* hi);
 
+/*
+ * The same bounds from one host array per instance instead of packed ones:
+ * lo and hi are NULL (no bound on that side for any instance) or arrays of
+ * count pointers, entry i NULL (instance i has no bound on that side) or n_i
+ * values.  The arrays are read during the call only and copied to the device
+ * through pinned staging without a packed host copy.  Errors as
+ * qp_batch_set_bounds (the bad variable reported by its packed index).
+ */
+qp_status qp_batch_set_bounds_each(qp_batch* bt, const double* const* lo,
+                                   const double* const* hi);
+
 /* qp_batch_create groups the instances by size (n, largest first) into up
  * to 4 bins of equal count; each bin is one launch on its own stream, with
  * shared memory and block size fitted to its largest instance.

@@ -159,6 +159,7 @@ SIGNATURES = [
     ("qp_batch_solution", c_int32, [_H, _F64P, _F64P]),
     ("qp_batch_set_warm_start", c_int32, [_H, _F64P, _F64P]),
     ("qp_batch_set_bounds", c_int32, [_H, _F64P, _F64P]),
+    ("qp_batch_set_bounds_each", c_int32, [_H, c_void_p, c_void_p]),
     ("qp_batch_set_threads", c_int32, [_H, c_int32]),
     ("qp_batch_tune", c_int32, [_H, POINTER(QPOptionsC), c_int32, c_int32, _I32P]),
     ("qp_mlp_create", c_int32, [POINTER(_H), c_int32, _I32P, c_int32, POINTER(QPDeviceCtxC)]),

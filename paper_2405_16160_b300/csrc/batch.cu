@@ -165,6 +165,7 @@ struct qp_batch {
   double* step_pow = nullptr;  // step_decide's power table (kStepPowTable pairs)
   bool warm_set = false, solved = false, bounded = false;
   std::vector<BatchResult> h_res;
+  std::vector<int64_t> h_off;  // instance i's variables: packed [h_off[i], h_off[i + 1])
 };
 
 namespace {
@@ -234,7 +235,7 @@ void host_parallel(int64_t count, int threads, F&& f) {
 }
 
 int host_threads() {
-  return int(std::max(1u, std::min(std::thread::hardware_concurrency(), 16u)));
+  return std::min(hw_threads(), 16);
 }
 
 // Host-to-device copies through pinned staging, shared by the batch handles
@@ -599,6 +600,9 @@ qp_status create_batch(qp_batch* h, int32_t count, const qp_instance* inst) {
   }
   h->n_total = n_total;
   h->m_total = m_total;
+  h->h_off.resize(size_t(count) + 1);
+  for (int32_t i = 0; i < count; ++i) h->h_off[size_t(i)] = desc[size_t(i)].off_n;
+  h->h_off[size_t(count)] = n_total;
   // bins: instances sorted by n (largest first), cut into equal-count groups
   std::vector<int32_t> ids(static_cast<size_t>(count));
   for (int32_t i = 0; i < count; ++i) ids[size_t(i)] = i;
@@ -927,32 +931,52 @@ qp_status qp_batch_set_warm_start(qp_batch* h, const double* x0, const double* y
   return finish(h);
 }
 
-qp_status qp_batch_set_bounds(qp_batch* h, const double* lo, const double* hi) {
-  if (!h) return QP_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// The bounds of every instance: lo_of(i) / hi_of(i) give instance i's n_i
+// values or NULL (that side unbounded); any_lo / any_hi: some instance has
+// that side.  The checks run on host threads over the caller's arrays (the
+// lowest bad packed variable is reported); the values go through the pinned
+// staging chunks straight from those arrays.
+template <class LoOf, class HiOf>
+qp_status set_bounds_impl(qp_batch* h, LoOf lo_of, HiOf hi_of, bool any_lo, bool any_hi) {
   const int64_t N = h->n_total;
-  // the checks, on host threads over the caller's arrays; the lowest bad
-  // variable is reported
+  const int32_t count = h->count;
   std::atomic<int64_t> bad(N);
   std::atomic<bool> any(false);
   const int nth = host_threads();
   host_parallel(nth, nth, [&](int64_t t) {
     bool fin = false;
-    for (int64_t j = N * t / nth; j < N * (t + 1) / nth; ++j) {
-      const double l = lo ? lo[j] : -INFINITY, u = hi ? hi[j] : INFINITY;
-      if (std::isnan(l) || std::isnan(u) || l > u || l == INFINITY || u == -INFINITY) {
-        int64_t cur = bad.load();
-        while (j < cur && !bad.compare_exchange_weak(cur, j)) {
+    for (int64_t ii = int64_t(count) * t / nth; ii < int64_t(count) * (t + 1) / nth; ++ii) {
+      const int32_t i = int32_t(ii);
+      const double* lo = any_lo ? lo_of(i) : nullptr;
+      const double* hi = any_hi ? hi_of(i) : nullptr;
+      if (!lo && !hi) continue;
+      const int64_t o = h->h_off[size_t(i)], n = h->h_off[size_t(i) + 1] - o;
+      for (int64_t v = 0; v < n; ++v) {
+        const double l = lo ? lo[v] : -INFINITY, u = hi ? hi[v] : INFINITY;
+        if (std::isnan(l) || std::isnan(u) || l > u || l == INFINITY || u == -INFINITY) {
+          int64_t cur = bad.load();
+          while (o + v < cur && !bad.compare_exchange_weak(cur, o + v)) {
+          }
+          break;
         }
-        break;
+        fin = fin || std::isfinite(l) || std::isfinite(u);
       }
-      fin = fin || std::isfinite(l) || std::isfinite(u);
     }
     if (fin) any = true;
   });
   if (bad.load() < N) {
     const int64_t j = bad.load();
+    const int32_t i = int32_t(std::upper_bound(h->h_off.begin(), h->h_off.end(), j) -
+                              h->h_off.begin()) - 1;
+    const int64_t v = j - h->h_off[size_t(i)];
+    const double* lo = any_lo ? lo_of(i) : nullptr;
+    const double* hi = any_hi ? hi_of(i) : nullptr;
     berror("invalid bounds at packed variable %lld: [%g, %g]", (long long)j,
-           lo ? lo[j] : -INFINITY, hi ? hi[j] : INFINITY);
+           lo ? lo[v] : -INFINITY, hi ? hi[v] : INFINITY);
     return QP_ERR_INVALID_ARG;
   }
   BTRY(begin(h));
@@ -964,20 +988,53 @@ qp_status qp_batch_set_bounds(qp_batch* h, const double* lo, const double* hi) {
     if (!h->lo32) BTRY(balloc(h, reinterpret_cast<void**>(&h->lo32), size_t(N) * sizeof(float)));
     if (!h->hi32) BTRY(balloc(h, reinterpret_cast<void**>(&h->hi32), size_t(N) * sizeof(float)));
     const int grid = int(std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, int64_t(h->num_sms) * 8)));
-    if (lo)
-      BTRY(staged_upload(h, h->lo, {{lo, size_t(N) * sizeof(double)}}));
-    else
-      k_fill_f64<<<grid, 256, 0, h->stream>>>(h->lo, -INFINITY, (long long)N);
-    if (hi)
-      BTRY(staged_upload(h, h->hi, {{hi, size_t(N) * sizeof(double)}}));
-    else
-      k_fill_f64<<<grid, 256, 0, h->stream>>>(h->hi, INFINITY, (long long)N);
+    int64_t max_n = 0;
+    for (int32_t i = 0; i < count; ++i)
+      max_n = std::max(max_n, h->h_off[size_t(i) + 1] - h->h_off[size_t(i)]);
+    // the pieces of one side, an instance without it read from a run of the fill value
+    auto upload_side = [&](auto of, bool present, double fill, double* dst) -> qp_status {
+      if (!present) {
+        k_fill_f64<<<grid, 256, 0, h->stream>>>(dst, fill, (long long)N);
+        return QP_OK;
+      }
+      const std::vector<double> fills(size_t(std::max<int64_t>(max_n, 1)), fill);
+      std::vector<HostPiece> pieces(static_cast<size_t>(count));
+      for (int32_t i = 0; i < count; ++i) {
+        const double* v = of(i);
+        pieces[size_t(i)] = {v ? static_cast<const void*>(v) : fills.data(),
+                             size_t(h->h_off[size_t(i) + 1] - h->h_off[size_t(i)]) * sizeof(double)};
+      }
+      BTRY(staged_upload(h, dst, pieces));
+      BCUDA(cudaStreamSynchronize(h->stream));  // fills dies with this call
+      return QP_OK;
+    };
+    BTRY(upload_side(lo_of, any_lo, -INFINITY, h->lo));
+    BTRY(upload_side(hi_of, any_hi, INFINITY, h->hi));
     BTRY(convert_float(h, h->lo, h->lo32, size_t(N)));
     BTRY(convert_float(h, h->hi, h->hi32, size_t(N)));
     BCUDA(cudaStreamSynchronize(h->stream));
     h->bounded = true;
   }
   return finish(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+qp_status qp_batch_set_bounds(qp_batch* h, const double* lo, const double* hi) {
+  if (!h) return QP_ERR_INVALID_ARG;
+  const std::vector<int64_t>& off = h->h_off;
+  return set_bounds_impl(
+      h, [&](int32_t i) { return lo + off[size_t(i)]; },
+      [&](int32_t i) { return hi + off[size_t(i)]; }, lo != nullptr, hi != nullptr);
+}
+
+qp_status qp_batch_set_bounds_each(qp_batch* h, const double* const* lo, const double* const* hi) {
+  if (!h) return QP_ERR_INVALID_ARG;
+  return set_bounds_impl(
+      h, [&](int32_t i) { return lo[i]; }, [&](int32_t i) { return hi[i]; }, lo != nullptr,
+      hi != nullptr);
 }
 
 qp_status qp_batch_set_threads(qp_batch* h, int32_t threads) {

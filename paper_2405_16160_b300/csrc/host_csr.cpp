@@ -14,7 +14,7 @@ namespace {
 // Worker threads for `work` items: at most the hardware threads (<= 32) and
 // at least ~256K items each.
 int worker_count(int64_t work) {
-  const unsigned hc = std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
+  const unsigned hc = unsigned(std::min(hw_threads(), 32));
   return int(std::max<int64_t>(1, std::min<int64_t>(hc, work / (int64_t(1) << 18))));
 }
 

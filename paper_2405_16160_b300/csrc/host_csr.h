@@ -72,12 +72,20 @@ bool csr_penalize(const CsrView& Q, const CsrView& A, int32_t m_eq, const double
                   const double* b, int iters, double eps_zero, int64_t max_products,
                   HostCsr* Qp, std::vector<double>* cp, double* rho, std::string* why);
 
+// The host's hardware threads, asked once per process: the standard call
+// reads the system's CPU lists on every use (tens of microseconds), which
+// adds up where thousands of small instances are checked one by one.
+inline int hw_threads() {
+  static const int n = int(std::max(1u, std::thread::hardware_concurrency()));
+  return n;
+}
+
 // f(t, lo, hi) for T contiguous ranges [lo, hi) covering [0, n), range t on
 // host thread t (t = 0 on the caller's), T = min(max_threads, the hardware
 // threads, n / min_per_thread), at least 1.  Returns T.
 template <class F>
 int parallel_ranges(int64_t n, int max_threads, int64_t min_per_thread, F&& f) {
-  const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
+  const int64_t hw = hw_threads();
   const int T = int(std::max<int64_t>(
       1, std::min<int64_t>({int64_t(max_threads), hw, n / std::max<int64_t>(1, min_per_thread)})));
   auto run = [&](int t) { f(t, n * t / T, n * (t + 1) / T); };

@@ -37,6 +37,18 @@ def _ptr(a, ctype):
     return a.ctypes.data_as(POINTER(ctype)) if a is not None else None
 
 
+def _addr(a):
+    """The address of an array's data (0, NULL, for None), as _ptr gives it."""
+    return 0 if a is None else a.__array_interface__["data"][0]
+
+
+# struct qp_instance of include/pdhcg.h: four int32 sizes, then seven pointers
+_INSTANCE_DTYPE = np.dtype([("n", np.int32), ("m", np.int32), ("m_eq", np.int32), ("k", np.int32),
+                            ("F", np.uint64), ("qd", np.uint64), ("A_rowptr", np.uint64),
+                            ("A_col", np.uint64), ("A_val", np.uint64), ("c", np.uint64),
+                            ("b", np.uint64)])
+
+
 class QPOptions:
     """Solver options (see qp_options in include/pdhcg.h); defaults from the library."""
 
@@ -264,21 +276,30 @@ class QPBatch:
         self.ms = [int(q.m) for q in instances]
         self._keep = []  # the allocator callbacks (alive as long as the handle)
         arrays = []      # instance arrays (read during qp_batch_create only)
-        arr = (L.QPInstanceC * self.count)()
+        # the qp_instance table as a structured array with the C layout (its
+        # pointers are the arrays' addresses, 0 for NULL): no ctypes object
+        # per array, which dominates the marshalling of thousands of instances
+        table = np.zeros(self.count, dtype=_INSTANCE_DTYPE)
+        ints = np.empty((self.count, 4), dtype=np.int32)
+        ptrs = np.zeros((self.count, 7), dtype=np.uint64)
         for i, q in enumerate(instances):
             F = _f64(q.F).reshape(-1) if q.k > 0 else None
             qd, c = _f64(q.qd, q.n), _f64(q.c, q.n)
             b = _f64(q.b, q.m)
             Ar, Ac, Av = _i32(q.A_rowptr), _i32(q.A_col), _f64(q.A_val)
             arrays += [F, qd, c, b, Ar, Ac, Av]
-            arr[i] = L.QPInstanceC(int(q.n), int(q.m), int(q.m_eq), int(q.k), _ptr(F, c_double),
-                                   _ptr(qd, c_double), _ptr(Ar, c_int32), _ptr(Ac, c_int32),
-                                   _ptr(Av, c_double), _ptr(c, c_double), _ptr(b, c_double))
+            ints[i] = (q.n, q.m, q.m_eq, q.k)
+            ptrs[i] = [_addr(a) for a in (F, qd, Ar, Ac, Av, c, b)]
+        for j, name in enumerate(("n", "m", "m_eq", "k")):
+            table[name] = ints[:, j]
+        for j, name in enumerate(("F", "qd", "A_rowptr", "A_col", "A_val", "c", "b")):
+            table[name] = ptrs[:, j]
         ctx = QPSolver._torch_ctx(self) if torch_memory else None
         h = c_void_p()
-        st = self.lib.qp_batch_create(byref(h), self.count, arr,
+        st = self.lib.qp_batch_create(byref(h), self.count,
+                                      table.ctypes.data_as(POINTER(L.QPInstanceC)),
                                       byref(ctx) if ctx is not None else None, 0)
-        del arrays
+        del arrays, table
         L.check(st, "qp_batch_create")
         self.h = h
         self._ctx = ctx
@@ -323,15 +344,22 @@ class QPBatch:
                 "qp_batch_set_warm_start")
 
     def set_bounds(self, los=None, his=None) -> None:
-        """Per-instance bounds: lists of arrays (an entry None: no bound on that side)."""
-        def pack(vs, fill):
+        """Per-instance bounds: lists of arrays (an entry None: no bound on
+        that side), passed as one pointer per instance (qp_batch_set_bounds_each:
+        no packed copy on either side of the call)."""
+        def table(vs):
             if vs is None:
-                return None
-            return _f64(np.concatenate([np.full(n, fill) if v is None else np.asarray(v, np.float64)
-                                        for v, n in zip(vs, self.ns)]), sum(self.ns))
-        lo, hi = pack(los, -np.inf), pack(his, np.inf)
-        L.check(self.lib.qp_batch_set_bounds(self.h, _ptr(lo, c_double), _ptr(hi, c_double)),
-                "qp_batch_set_bounds")
+                return None, None
+            if len(vs) != self.count:
+                raise ValueError(f"expected {self.count} bound arrays, got {len(vs)}")
+            arrs = [None if v is None else _f64(v, n) for v, n in zip(vs, self.ns)]
+            return arrs, np.array([_addr(a) for a in arrs], dtype=np.uint64)
+        lo_keep, lo = table(los)
+        hi_keep, hi = table(his)
+        L.check(self.lib.qp_batch_set_bounds_each(
+            self.h, None if lo is None else lo.ctypes.data, None if hi is None else hi.ctypes.data),
+            "qp_batch_set_bounds_each")
+        del lo_keep, hi_keep
 
     def set_threads(self, threads: int) -> None:
         L.check(self.lib.qp_batch_set_threads(self.h, int(threads)), "qp_batch_set_threads")

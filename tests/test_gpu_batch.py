@@ -385,6 +385,46 @@ def _split(v, insts):
     return np.split(v, np.cumsum([q.n for q in insts])[:-1])
 
 
+def test_batch_bounds_packed_and_per_instance_agree():
+    """qp_batch_set_bounds (packed) and qp_batch_set_bounds_each (one array
+    per instance, some of them NULL) set the same bounds: bit-identical
+    solves; and both report the same first invalid variable by its packed
+    index."""
+    from ctypes import POINTER, c_double
+    insts = W.portfolio_batch(9, count=6, n_lo=20, n_hi=80)
+    rng = np.random.default_rng(9)
+    los = [None if i % 3 == 1 else np.zeros(q.n) for i, q in enumerate(insts)]
+    his = [None if i % 2 == 0 else rng.uniform(0.3, 1.0, q.n) for i, q in enumerate(insts)]
+    n = sum(q.n for q in insts)
+    lo_p = np.concatenate([np.full(q.n, -np.inf) if v is None else v for v, q in zip(los, insts)])
+    hi_p = np.concatenate([np.full(q.n, np.inf) if v is None else v for v, q in zip(his, insts)])
+    assert lo_p.size == hi_p.size == n
+    out = []
+    with QPBatch(insts) as bt:
+        for form in ("packed", "each"):
+            if form == "packed":
+                L.check(bt.lib.qp_batch_set_bounds(bt.h, lo_p.ctypes.data_as(POINTER(c_double)),
+                                                   hi_p.ctypes.data_as(POINTER(c_double))),
+                        "qp_batch_set_bounds")
+            else:
+                bt.set_bounds(los, his)
+            bt.solve(tol=1e-7, precision=L.PREC_FP64, step_mode=L.STEP_ADAPTIVE)
+            out.append((bt.results(), bt.solution()[0]))
+        assert [r["attempts"] for r in out[0][0]] == [r["attempts"] for r in out[1][0]]
+        for a, b in zip(out[0][1], out[1][1]):
+            assert np.array_equal(a, b)
+        # a bad variable in instance 4: the same packed index either way
+        j = int(sum(q.n for q in insts[:4])) + 3
+        bad_lo = lo_p.copy()
+        bad_lo[j] = np.nan
+        with pytest.raises(L.QPError) as e1:
+            L.check(bt.lib.qp_batch_set_bounds(bt.h, bad_lo.ctypes.data_as(POINTER(c_double)),
+                                               None), "qp_batch_set_bounds")
+        with pytest.raises(L.QPError) as e2:
+            bt.set_bounds(_split(bad_lo, insts), None)
+        assert f"packed variable {j}:" in str(e1.value) and f"packed variable {j}:" in str(e2.value)
+
+
 def test_batch_create_rejects_non_finite_F_by_instance():
     """F is transposed and checked on the device: a NaN is reported with
     the lowest instance id holding one, and nothing is created."""
