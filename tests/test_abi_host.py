@@ -53,7 +53,8 @@ def test_struct_layouts_match_ctypes(tmp_path):
     structs = {"qp_options": L.QPOptionsC, "qp_info": L.QPInfoC,
                "qp_state_scalars": L.QPStateScalarsC, "qp_state_vectors": L.QPStateVectorsC,
                "qp_trace_entry": L.QPTraceEntryC, "qp_device_ctx": L.QPDeviceCtxC,
-               "qp_shapes": L.QPShapesC}
+               "qp_shapes": L.QPShapesC, "qp_instance": L.QPInstanceC,
+               "qp_instance_result": L.QPInstanceResultC}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdhcg.h"', "int main(void){"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -70,6 +71,11 @@ def test_struct_layouts_match_ctypes(tmp_path):
         assert int(got[f"{cname} size"]) == __import__("ctypes").sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
+    # QPBatch passes its instance table as a numpy structured array
+    dt = S._INSTANCE_DTYPE
+    assert dt.itemsize == int(got["qp_instance size"])
+    for f, _ in L.QPInstanceC._fields_:
+        assert dt.fields[f][1] == int(got[f"qp_instance.{f}"]), f
 
 
 def test_option_defaults_follow_the_paper(lib):
