@@ -47,7 +47,7 @@
 namespace pdhcg {
 
 constexpr int kBlock = 256;
-constexpr int kCgBlock = 512;  // persistent CG kernel: fewer, larger blocks
+constexpr int kCgBlock = 768;  // persistent CG kernel: fewer, larger blocks
 constexpr int kPartStride = 16;  // doubles per block in the multi-value partial buffers
 
 // Which entries of the relKKT partial buffers are maxima (bit set) or sums.
@@ -899,10 +899,11 @@ __device__ __forceinline__ void store_and_finish_dot(A acc, double* part, unsign
 // takes.  Every dot product is FP64-accurate for both value types; alpha,
 // beta and the stop test are derived from them in the value type's precision
 // (ratio, scaled_norm_le).  part holds 2 * gridDim.x doubles.
-// Resident CG blocks of 512 threads per SM (register budget per thread =
-// 65536 / (512 * blocks)).  Four FP32 blocks would need 32 registers and
-// spill; three measured faster.
-constexpr int kCgBlocksPerSm = 3;
+// Resident CG blocks per SM: two of 768 threads, 48 warps per SM at 40
+// registers a thread (65536 / (768 * 2)), the warps of three 512-thread
+// blocks with a third fewer blocks arriving at every grid barrier (measured
+// slightly faster); four blocks of 512 would need 32 registers and spill.
+constexpr int kCgBlocksPerSm = 2;
 
 // Adaptive step size: the attempt's primal move from its saved start (x_save,
 // qx_save), ||x+ - x||^2 and (x+ - x)'(Q x+ - Q x).  The CG kernel sums them

@@ -1853,8 +1853,8 @@ qp_status time_products(qp_handle* h, DevMat* const* mats, int count, T* const* 
   return st;
 }
 
-// Q's products run only inside the persistent CG kernel (512-thread
-// blocks, 3 per SM, two grid barriers per step), whose lanes per row a plain
+// Q's products run only inside the persistent CG kernel (768-thread
+// blocks, 2 per SM, two grid barriers per step), whose lanes per row a plain
 // product does not time well (2 and 4 lanes: within noise of each other as
 // plain products, 109 against 120 us per CG launch on the bench instance).
 // So Q's candidates are timed by the CG kernel itself: launches of two fixed
