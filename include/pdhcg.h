@@ -342,7 +342,10 @@ qp_status qp_get_penalty(const qp_handle* h, double* rho);
  *   lanes        lanes per row in use: G threads share one CSR row, so a
  *                warp takes 32 / G rows at a time; rows longer than 16 G
  *                entries (64 at least in FP64) go to one whole warp each
- *   lanes_rule   the choice of the mean-row-length rule applied at qp_create
+ *   lanes_rule   the choice of qp_create's rule: by the mean row length (over
+ *                the rows of at most 64 entries when some are longer); FP32 Q,
+ *                whose products run in the CG kernel, takes the fewest lanes G
+ *                with a mean of at most 8 G entries
  *   layout       how rows go to warps: 0 groups of 32 / G rows across the grid
  *                in turn (the default for A and A'), 1 a contiguous range per
  *                warp (the default for Q), 2 a contiguous range per block whose
