@@ -167,6 +167,19 @@ def test_create_without_gpu_reports_no_device(lib):
     assert e.value.status == 6
 
 
+def test_batch_create_without_gpu_reports_no_device(lib):
+    """The batch binding builds its instance table (a structured array of
+    addresses) for many instances and the library reports the missing
+    device, on a machine without one."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    insts = W.portfolio_batch(3, count=300, n_lo=20, n_hi=60, bounds=True)
+    with pytest.raises(L.QPError) as e:
+        S.QPBatch(insts, torch_memory=False)
+    assert e.value.status == 6
+
+
 def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(FileNotFoundError):
         L.load_library(str(tmp_path / "libpdhcg.so"))
